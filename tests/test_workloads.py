@@ -1,0 +1,61 @@
+"""The synthetic inputs: meshes are valid and the manufactured data satisfy eq. 1.1."""
+import numpy as np
+import pytest
+
+from workloads import boundary_faces, get_problem, kuhn_cube
+from workloads.problems import batch_problems, grf_field, grf_sample
+
+
+@pytest.mark.parametrize("s,jit", [(4, 0.0), (5, 0.2)])
+def test_kuhn_cube(s, jit):
+    c, e = kuhn_cube(s, jitter=jit, seed=0)
+    v = c[e]
+    det = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0])
+    assert e.shape == (6 * s ** 3, 4) and np.all(det > 0)
+    assert abs(det.sum() / 6 - 1) < 1e-12
+    d, n = boundary_faces(c, e, lambda ax, val: "D" if ax == 0 else "N")
+    assert len(d) == 4 * s * s and len(n) == 8 * s * s
+
+
+def _div(F, x, y, z, h=1e-5):
+    return sum((F(*(p + h * (i == a) for i, p in enumerate((x, y, z))))[a]
+                - F(*(p - h * (i == a) for i, p in enumerate((x, y, z))))[a]) / (2 * h) for a in range(3))
+
+
+def _grad(u, x, y, z, h=1e-5):
+    return tuple((u(*(p + h * (i == a) for i, p in enumerate((x, y, z))))
+                  - u(*(p - h * (i == a) for i, p in enumerate((x, y, z))))) / (2 * h) for a in range(3))
+
+
+@pytest.mark.parametrize("name", ["cube4_k1", "cube16_k3", "cube48_k2_conv"])
+def test_manufactured_data(name):
+    prob = get_problem(name)
+    rng = np.random.default_rng(0)
+    x, y, z = rng.uniform(0.05, 0.95, size=(3, 40))
+    g = _grad(prob.u, x, y, z)
+    q = prob.q(x, y, z)
+    kap = prob.kappa(x, y, z)
+    for a in range(3):  # eq. 1.1a: kappa^-1 q + grad u = 0
+        assert np.allclose(q[a] / kap + g[a], 0, atol=1e-6)
+    flux = prob.q
+    if prob.beta is not None:  # conservative convection: div(q + beta u) + c u = f
+        flux = lambda x, y, z: tuple(qa + ba * prob.u(x, y, z) for qa, ba in zip(prob.q(x, y, z), prob.beta(x, y, z)))  # noqa: E731
+    lhs = _div(flux, x, y, z) + prob.c(x, y, z) * prob.u(x, y, z)  # eq. 1.1b
+    assert np.allclose(lhs, prob.f(x, y, z), rtol=1e-6, atol=1e-5)
+    if prob.gN is not None:  # eq. 1.1d: -q.nu = g_N.nu
+        gn = prob.gN(x, y, z)
+        for a in range(3):
+            assert np.allclose(-q[a], gn[a])
+
+
+def test_grf_statistics():
+    # pointwise variance sigma^2 = 1 over many samples
+    x = np.array([0.3, 0.7]); y = np.array([0.5, 0.1]); z = np.array([0.2, 0.9])
+    vals = np.array([grf_field(grf_sample(i))(x, y, z) for i in range(400)])
+    assert abs(vals.var(axis=0).mean() - 1.0) < 0.2
+
+
+def test_batch_sampler():
+    probs = batch_problems()
+    assert len(probs) == 64
+    assert all(8 <= p.s <= 24 and 1 <= p.k <= 4 for p in probs)
