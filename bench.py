@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the HDG hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (N=1): unit cube, 16^3 subcubes x 6 Kuhn tetrahedra (24,576 elements), k = 3,
+kappa = 1 + 0.5 sin(2 pi x) cos(2 pi y), c = 1 + x^2, manufactured u = (1 + x^2 + yz)
+exp(0.5x - y + z), Dirichlet on x = 0 and x = 1, Neumann elsewhere.  Synthetic, seeded.
+
+One step = the whole hot path on one batch of resident inputs:
+  assemble + condense (K1)  ->  trace solve to ||b - H u||/||b|| <= 1e-10 (FP32 inner PCG with
+  FP64 refinement)  ->  recover (K2)  ->  postprocess (K5).
+value = elements/s over the metric's phases (assemble + condense + recover), timed with CUDA
+events on the launching stream; the trace solve's time-to-1e-10 is reported beside it for the
+plain FP64 block-Jacobi PCG (zero start) and for the mixed-precision solve.
+L2 is flushed (256 MiB write) before every step; the inputs (74 MB) are smaller than L2.
+With --impl reference the FP64 CPU oracle is timed on the host cores on the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="cube16_k3", s=16, k=3)
+METRIC = "elements/sec (assemble+condense+recover) & time-to-1e-10 solve vs plain FP64 GPU"
+UNIT = "elements/s"
+# FP64 peak of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_MEASURED_TFLOPS = 1.19  # FMA-chain microbenchmark on this machine's GB300 (1 block/SM saturates)
+
+# DRAM traffic of one K1 launch at this workload, from the ncu capture recorded in
+# profiles/assemble_kernel_cube16_k3.md, valid while assemble.cu is unchanged.
+K1_TRAFFIC = {"sha256": None, "bytes": None}
+
+
+def flops_per_element_k1(k):
+    """FP64 flops per element of the K1 algorithm (structured elimination), FMA = 2."""
+    n = (k + 1) * (k + 2) * (k + 3) // 6
+    d2 = (k + 1) * (k + 2) // 2
+    m = 4 * d2
+    nq = (k + 2) ** 3
+    NP, MP = n * (n + 1) // 2, m * (m + 1) // 2
+    chol = sum(2 * j + 3 + (n - j - 1) * (2 * j + 1) for j in range(n))
+    f = 4 * nq                      # |K| w / kappa, |K| w c, |K| w f
+    f += NP * (5 * nq + 8)          # M_{kappa^-1}, M_c (shared product), tauPP
+    f += 2 * n * nq                 # f^K
+    f += 18 * n * n                 # C_*^T from C_hat and the cofactors
+    f += chol                       # L L^T = M
+    f += (3 * n + m) * n * n        # W_* = L^-1 C_*^T, V = L^-1 E^T
+    f += NP * (6 * n + 1)           # S_u += sum W^T W
+    f += 20 * n * n                 # sum_* n_{l*} W_*
+    f += MP * (2 * n + 7)           # (n.n) V^T V + tauDD
+    f += chol                       # L_s L_s^T = S_u
+    f += n * m * (2 * n + 1)        # G
+    f += (m + 1) * n * n + m * n * n + 3 * n * n * n  # H|h, Y, MC
+    f += MP * (2 * n + 1) + 2 * m * n  # C -= H^T H, C_f
+    f += (m + 1) * n * n            # R_u | r_u
+    return f
+
+
+def k1_bytes_per_element(k):
+    """Algorithmic HBM bytes of K1 per element: kappa, c, f, geometry, perms, tau in;
+    C^K (full), C_f^K and the recovery record out."""
+    n = (k + 1) * (k + 2) * (k + 3) // 6
+    m = 2 * (k + 1) * (k + 2)
+    nq = (k + 2) ** 3
+    rec = n * (m + 1) + n * m + 3 * n * n + 12
+    return 8 * (3 * nq + 12) + 4 * 4 + 8 * (m * m + m + rec)
+
+
+def _sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle timing (CPU)
+_ORACLE = {}
+
+
+def _oracle_init(name):
+    """Worker set-up: the workload's mesh, tables and coefficients, built once per process."""
+    from oracle import hdg as ohdg
+    from oracle.geometry import ExpandedMesh
+    from workloads import boundary_faces, get_problem, kuhn_cube
+
+    prob = get_problem(name)
+    c, e = kuhn_cube(prob.s)
+    d, n = boundary_faces(c, e, prob.classify)
+    mesh = ExpandedMesh(c, e, d, n)
+    tab = ohdg.Tables(prob.k)
+    X, Y, Z = ohdg.volume_nodes(mesh, tab)
+    _ORACLE.update(mesh=mesh, tab=tab, kap=prob.kappa(X, Y, Z), c=prob.c(X, Y, Z), f=prob.f(X, Y, Z),
+                   uhat=np.zeros((mesh.nfc, tab.d2)))
+
+
+def _oracle_chunk(idx):
+    """Oracle assemble + condense + recover on a chunk of elements (one worker process)."""
+    from oracle import hdg as ohdg
+    o = _ORACLE
+    blk = ohdg.local_blocks(o["mesh"], o["tab"], o["kap"], o["c"], o["f"], tau=1.0, elems=idx)
+    CK, Cf, X2, xf = ohdg.local_solvers(blk)
+    ohdg.recover(o["mesh"], X2, xf, o["uhat"], elems=idx)
+    return len(idx)
+
+
+def oracle_baseline(sample_elems, steps=1, warmup=0):
+    """Time the oracle as it stands on the host cores: elements/s (assemble+condense+recover)."""
+    import multiprocessing as mp
+
+    nelt = 6 * WORKLOAD["s"] ** 3
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(0)
+    ctx = mp.get_context("spawn")
+    env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_backup:
+        os.environ[k] = "1"
+    try:
+        with ctx.Pool(cores, initializer=_oracle_init, initargs=(WORKLOAD["name"],)) as pool:
+            pool.map(_oracle_chunk, [np.arange(2)] * cores)  # wait for every worker's set-up
+
+            def one():
+                idx = np.sort(rng.choice(nelt, size=sample_elems, replace=False))
+                t0 = time.perf_counter()
+                done = sum(pool.map(_oracle_chunk, np.array_split(idx, cores)))
+                return done, time.perf_counter() - t0
+            for _ in range(warmup):
+                one()
+            tot_e, tot_t = 0, 0.0
+            for _ in range(steps):
+                ne, dt = one()
+                tot_e += ne
+                tot_t += dt
+    finally:
+        for k, v in env_backup.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"value": tot_e / tot_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_elems} random elements of the {nelt}-element mesh per step "
+                      f"x {steps} step(s); numpy FP64 literal blocks + LU of A_1 + recovery, "
+                      f"{cores} spawn workers with 1 BLAS thread each"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1305_1489_gb300 import HDG_FP64, HDG_MIXED_FP32, HDGMesh, build
+    from workloads import boundary_faces, get_problem, kuhn_cube
+
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1305_1489_gb300", "libhdg.so")):
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = get_problem(WORKLOAD["name"])
+    c, e = kuhn_cube(prob.s)
+    d, n = boundary_faces(c, e, prob.classify)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    M = HDGMesh(c, e, d, n, prob.k, stream=stream)
+    nelt = M.nelt
+    X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+    FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
+    host = {
+        "kappa": prob.kappa(X, Y, Z), "c": prob.c(X, Y, Z), "f": prob.f(X, Y, Z),
+        "uD": prob.uD(FX, FY, FZ), "gN": np.stack(prob.gN(FX, FY, FZ)),
+    }
+    dv = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in host.items()}
+    M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
+    M.set_boundary_data(dv["uD"], dv["gN"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def step(rec=None):
+        flush.fill_(1.0)
+        e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
+        e0.record(stream)
+        M.assemble_condense()
+        e1.record(stream)
+        uhat, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
+        e2.record(stream)
+        q, u = M.recover(uhat)
+        e3.record(stream)
+        M.postprocess(q, u)
+        e4.record(stream)
+        if rec is not None:
+            rec.append((e0, e1, e2, e3, e4, it, rr))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    recs = []
+    launches0 = M.launches
+    clk = ClockSampler(local_rank)
+    clk.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tstart = ev()
+    tstart.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    tend = ev()
+    tend.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    launches = M.launches - launches0
+    total_ms = tstart.elapsed_time(tend)
+    t_asm = [a.elapsed_time(b) for a, b, *_ in recs]
+    t_sol = [b.elapsed_time(c_) for _, b, c_, *_ in recs]
+    t_rec = [c_.elapsed_time(d_) for _, _, c_, d_, *_ in recs]
+    t_pp = [d_.elapsed_time(e_) for _, _, _, d_, e_, *_ in recs]
+    phase_ms = sum(t_asm) + sum(t_rec)
+    if world > 1:
+        tt = torch.tensor([phase_ms, total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        phase_ms, total_ms = tt.tolist()
+    value = world * nelt * args.steps / (phase_ms / 1e3)
+
+    # time-to-1e-10: plain FP64 zero-start block-Jacobi PCG vs mixed precision
+    solve = {}
+    for name, prec in (("plain_fp64", HDG_FP64), ("mixed_fp32_fp64", HDG_MIXED_FP32)):
+        ts, its = [], []
+        for _ in range(2):
+            a, b = ev(), ev()
+            a.record(stream)
+            uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=prec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+            its.append(it)
+        solve[name] = {"ms": min(ts), "iterations": its[-1], "relres": rr}
+    solve["speedup_mixed_vs_plain"] = solve["plain_fp64"]["ms"] / solve["mixed_fp32_fp64"]["ms"]
+
+    # end to end through the public API with host buffers (pinned) and copies in the region
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    hq = torch.empty((nelt, 3, M.n), dtype=torch.float64).pin_memory()
+    hu = torch.empty((nelt, M.n), dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in pin.values())
+    d2h = (hq.numel() + hu.numel()) * 8
+    e2e_ms = 0.0
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        a, b, cc, dd = ev(), ev(), ev(), ev()
+        a.record(stream)
+        for k_, v in pin.items():
+            dv[k_].copy_(v, non_blocking=True)
+        M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
+        M.set_boundary_data(dv["uD"], dv["gN"])
+        M.assemble_condense()
+        b.record(stream)
+        uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
+        cc.record(stream)
+        q, u = M.recover(uh)
+        hq.copy_(q, non_blocking=True)
+        hu.copy_(u, non_blocking=True)
+        dd.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms += a.elapsed_time(b) + cc.elapsed_time(dd)
+    e2e = {"value": world * nelt * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "phases": "H2D of kappa,c,f,u_D,g_N + assemble_condense + recover + D2H of q,u "
+                     "(the trace solve runs between them and is excluded, as in value)"}
+
+    # roofline of the dominant kernel (K1, FP64-ALU bound)
+    k1_ms = float(np.mean(t_asm))
+    flops = flops_per_element_k1(prob.k) * nelt
+    achieved = flops / (k1_ms / 1e3) / 1e12
+    sha = _sha(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", "assemble.cu"))
+    traffic = K1_TRAFFIC["bytes"] if K1_TRAFFIC["sha256"] == sha else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "assemble_kernel<3,256> (K1, FP64)",
+                "flops_per_element": flops_per_element_k1(prob.k),
+                "algorithmic_bytes_per_launch": k1_bytes_per_element(prob.k) * nelt,
+                "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived); measured FMA "
+                             f"microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s",
+                "frac_of_measured": achieved / FP64_MEASURED_TFLOPS}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD['name']}: unit cube 16^3x6 Kuhn tets ({nelt} elements), k=3, "
+                               "variable kappa and c, Dirichlet x=0,1 + Neumann elsewhere",
+                   "nelt": nelt, "nfc": M.nfc, "trace_dofs": M.nfc * M.d2, "k": prob.k,
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "solve_in_step": "mixed FP32/FP64 PCG to 1e-10 relative residual"},
+        "phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
+                      "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
+        "solve_time_to_1e-10": solve,
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
+        "wall_s_timed": wall,
+    }
+    return out
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    base = oracle_baseline(sample_elems=args.ref_sample, steps=args.steps, warmup=min(args.warmup, 1))
+    return {
+        "impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD['name']}: unit cube 16^3x6 Kuhn tets (24576 elements), k=3",
+                   "impl": "FP64 CPU oracle (numpy), host cores"},
+        "cpu_baseline": base,
+        "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=12288, help="oracle elements per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_baseline(sample_elems=args.ref_sample, steps=1, warmup=1)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

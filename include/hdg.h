@@ -1,0 +1,175 @@
+/*
+ * hdg.h -- C ABI of libhdg: the data-parallel hot path of the hybridizable discontinuous
+ * Galerkin (HDG) method for variable-coefficient reaction-diffusion on conforming
+ * tetrahedral meshes at a fixed polynomial degree k (Fu, Gatica, Sayas, "Matlab tools for
+ * HDG in three dimensions", arXiv 1305.1489), on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (eq. 1.1):  kappa^-1 q + grad u = 0,  div q + c u = f  in Omega,
+ *                     u = u_D on Gamma_D,  -q.nu = g_N.nu on Gamma_N.
+ * Unknowns (eq. 1.2): q_h in P_k(K)^3, u_h in P_k(K) per element, u_hat in P_k(e) per face.
+ *
+ * Conventions shared by every call
+ *  - All indices are 0-based.  Host arrays are row-major (C order).
+ *  - "device" pointers are CUDA global-memory pointers on the device that was current when
+ *    hdg_mesh_create ran; "host" pointers are ordinary CPU memory.
+ *  - Element-major layout ("SoA per element"): an array documented [Nelt][Nq] holds the Nq
+ *    values of element 0, then of element 1, ...
+ *  - Quadrature: volume nodes are the conical Gauss-Jacobi rule with (k+2)^3 nodes (exact
+ *    to degree 2k+3); face nodes the (k+2)^2-node rule on each face (eq. 3.1, Section 4).
+ *  - Bases: orthonormal hierarchical Dubiner bases, int_K P_i P_j = |K| delta_ij and
+ *    int_e D_i D_j = |e| delta_ij (eq. 3.3, Section 4), ordered by degree then (p,q[,r]).
+ *  - Global faces are numbered in lexicographic order of their sorted vertex triples; a
+ *    face's parametrisation phi_e uses its vertices in ascending order (Section 2).
+ *  - Every call returns an hdg_status (0 = success).  No call throws.  On failure the
+ *    message of the last error of the calling thread is available from hdg_last_error.
+ *  - Work is enqueued on the CUDA stream given to hdg_mesh_create.  Calls returning values
+ *    to the host (iteration counts, residuals, status counts) synchronise that stream.
+ *  - A mesh handle may be used by one host thread at a time.
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_ERR_ARG = 1,             /* invalid argument (null pointer, size, degree ...)        */
+  HDG_ERR_ORIENTATION = 2,     /* an element has det B_K <= 0 (Section 2 requires > 0)     */
+  HDG_ERR_NONCONFORMING = 3,   /* a face shared by >2 elements, or a boundary face missing
+                                  from both boundary lists, or a listed face not in the mesh */
+  HDG_ERR_CUDA = 4,            /* a CUDA runtime call failed                                */
+  HDG_ERR_STATE = 5,           /* calls out of order (e.g. solve before assemble)           */
+  HDG_ERR_LOCAL_SINGULAR = 6,  /* a local factorisation met a non-positive pivot           */
+  HDG_ERR_NOT_CONVERGED = 7,   /* the trace solve hit maxit before the tolerance            */
+  HDG_ERR_COEFF = 8,           /* kappa <= 0 or c < 0 or a non-finite coefficient value     */
+  HDG_ERR_UNSUPPORTED = 9      /* option not built (e.g. degree outside 1..4)               */
+} hdg_status;
+
+typedef enum {
+  HDG_FP64 = 0,        /* every operation in IEEE double                                   */
+  HDG_MIXED_FP32 = 1   /* FP32 inner solve with FP64 residuals and refinement (solve only) */
+} hdg_precision;
+
+typedef struct hdg_mesh hdg_mesh;
+
+typedef struct {
+  int64_t nelt, nfc, ndir, nneu, nver;
+  int32_t k;      /* polynomial degree                                    */
+  int32_t n;      /* d3 = (k+1)(k+2)(k+3)/6, dim P_k(K)                    */
+  int32_t d2;     /* (k+1)(k+2)/2, dim P_k(e)                              */
+  int32_t m;      /* 4 d2, dim R_k(dK) (local trace space, Section 5)      */
+  int32_t n1;     /* d3(k+1), dim P_{k+1}(K) for the postprocess u*        */
+  int32_t nq;     /* volume quadrature nodes per element, (k+2)^3          */
+  int32_t nf;     /* face quadrature nodes per face, (k+2)^2               */
+  int32_t has_convection;
+} hdg_mesh_info;
+
+/* Build the expanded mesh (Section 2: faces, facebyele, perm, normals) from the basic one.
+ *   coords [nver][3] host f64; elems [nelt][4] host int32, positively oriented;
+ *   dir [ndir][3], neu [nneu][3] host int32 vertex triples (any order within a triple).
+ *   k in 1..4.  stream: cudaStream_t to use (NULL = legacy default stream).
+ * The library copies what it needs; the caller's arrays may be freed on return.
+ * Every boundary face must be listed exactly once in dir or neu (Gamma = Gamma_D U Gamma_N).
+ * Errors: HDG_ERR_ARG, HDG_ERR_ORIENTATION, HDG_ERR_NONCONFORMING, HDG_ERR_CUDA.          */
+int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, int64_t nelt,
+                    const int32_t* dir, int64_t ndir, const int32_t* neu, int64_t nneu,
+                    int k, void* stream, hdg_mesh** out);
+
+/* Release every device and host resource of the handle (NULL is accepted). */
+int hdg_mesh_destroy(hdg_mesh* mesh);
+
+/* Sizes of the discrete spaces (host struct filled in). */
+int hdg_mesh_get_info(const hdg_mesh* mesh, hdg_mesh_info* info);
+
+/* Expanded-mesh fields, host outputs (any may be NULL):
+ *   faces [nfc][4] int32: sorted vertex triple + type (0 interior, 1 Dirichlet, 2 Neumann);
+ *   facebyele [nelt][4] int32 (global face of local face l, eq. 2.1 order);
+ *   perm [nelt][4] int32 in 1..6 (eq. 2.3).                                               */
+int hdg_mesh_get_faces(const hdg_mesh* mesh, int32_t* faces, int32_t* facebyele, int32_t* perm);
+
+/* Quadrature nodes where the caller evaluates the PDE data (eq. 3.4 and eq. 6.2).
+ *   X, Y, Z: device f64 [nelt][nq] volume nodes p_q^K = F_K(p_hat_q);
+ *   FX, FY, FZ: device f64 [nfc][nf] face nodes q_r^e = phi_e(q_hat_r).
+ * Either triple may be NULL.                                                              */
+int hdg_quadrature_nodes(hdg_mesh* mesh, double* X, double* Y, double* Z,
+                         double* FX, double* FY, double* FZ);
+
+/* PDE coefficients at the volume nodes (device f64, borrowed: they must stay valid until
+ * the next hdg_assemble_condense and hdg_postprocess that use them have completed).
+ *   kappa [nelt][nq] > 0, c [nelt][nq] >= 0, f [nelt][nq];
+ *   beta: must be NULL (convection is not part of this build);
+ *   tau [nelt][4] >= 0 per element face (eq. 4.22), or NULL for tau = 1.
+ * Positivity is checked in hdg_assemble_condense (HDG_ERR_COEFF).                         */
+int hdg_set_coefficients(hdg_mesh* mesh, const double* kappa, const double* c,
+                         const double* beta, const double* f, const double* tau);
+
+/* Boundary data at the face nodes (device f64, borrowed like the coefficients):
+ *   uD [nfc][nf]: u_D at the face nodes (read on Dirichlet faces only), or NULL for u_D = 0;
+ *   gN [3][nfc][nf]: the vector field g_N (read on Neumann faces only), or NULL for g_N = 0.
+ * Neumann data enter through eq. 6.4 with the outward normal of the face's element.      */
+int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
+
+/* Per-element assembly of the local blocks and static condensation (Sections 3-5):
+ * C^K = A3 A1^-1 A2 + tauDD (eq. 5.5), C_f^K = A3 A1^-1 A_f (eq. 5.6), and the operators of
+ * the local recovery (eq. 5.3), into library-owned device memory.  FP64 throughout.
+ * precision must be HDG_FP64.  Asynchronous; synchronises only to report
+ * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
+int hdg_assemble_condense(hdg_mesh* mesh, int precision);
+
+/* Copy the condensed local matrices out (tests): C [nelt][m][m], Cf [nelt][m] device f64. */
+int hdg_get_condensed(const hdg_mesh* mesh, double* C, double* Cf);
+
+/* Global trace system H u_hat = F + G_N (eq. 6.5), Dirichlet faces eliminated (Section 6),
+ * solved matrix-free element by element with block-Jacobi preconditioned CG to
+ *   ||b - H u_hat||_2 <= rtol ||b||_2  (FP64 residual over the free dofs).
+ *   precision: HDG_FP64 (plain PCG) or HDG_MIXED_FP32 (FP32 inner PCG, FP64 refinement).
+ *   x0: device f64 [nfc][d2] initial guess or NULL (zero start).
+ *   uhat: device f64 [nfc][d2] output; Dirichlet faces receive u_hat_D of eq. 6.3.
+ *   iters, relres: host outputs (may be NULL): iterations (inner iterations for the mixed
+ *   path) and the final FP64 relative residual.
+ * Returns HDG_ERR_NOT_CONVERGED (with uhat holding the last iterate) when maxit is hit.    */
+int hdg_solve_trace(hdg_mesh* mesh, int precision, double rtol, int maxit, const double* x0,
+                    double* uhat, int* iters, double* relres);
+
+/* Residual check (tests): r = b - H x over the free dofs, device f64 [nfc][d2]; returns
+ * ||r||_2 and ||b||_2 through the host pointers.                                          */
+int hdg_trace_residual(hdg_mesh* mesh, const double* x, double* r, double* rnorm, double* bnorm);
+
+/* Local recovery (eq. 5.3): q [nelt][3][n], u [nelt][n] device f64 outputs from the trace
+ * uhat [nfc][d2] (device f64).                                                            */
+int hdg_recover(hdg_mesh* mesh, const double* uhat, double* q, double* u);
+
+/* Superconvergent postprocess (eq. 9.11): ustar [nelt][n1] device f64 (coefficients in the
+ * degree-(k+1) Dubiner basis) from q, u of hdg_recover; kappa as set by
+ * hdg_set_coefficients.                                                                   */
+int hdg_postprocess(hdg_mesh* mesh, const double* q, const double* u, double* ustar);
+
+/* Copy the message of the calling thread's last error into buf (NUL-terminated). */
+int hdg_last_error(char* buf, size_t len);
+
+/* Number of kernel launches this handle has enqueued so far (instrumentation). */
+int64_t hdg_launch_count(const hdg_mesh* mesh);
+
+/* Host-only helpers (no GPU needed), used to check the library's host logic.
+ * hdg_host_table: copy the reference table `name` of degree k into out (host f64, at least
+ *   *size entries; out may be NULL to query *size).  Names and layouts (row-major):
+ *   vol_pts [nq][3], vol_w [nq], P [nq][n], Pd [3][nq][n], Chat [3][n][n] (eq. 3.5-3.7),
+ *   face_pts [nf][2], face_w [nf], Pl [4][nf][n], D [nf][d2], Dmu [6][nf][d2] (eq. 4.4, 4.7),
+ *   S [4][n][n] (eq. 4.5 pieces), E [4][6][d2][n] (eq. 4.10 pieces),
+ *   P1 [nq][n1], G1 [3][nq][n1], Shat1 [6][n1][n1] (degree k+1, eq. 9.11).
+ * hdg_host_expand_mesh: the expanded mesh of Section 2 on the host.  faces needs room for
+ *   4 nelt rows of 4 (nfc <= 4 nelt), facebyele and perm [nelt][4]; *nfc receives the count. */
+int hdg_host_table(int k, const char* name, double* out, int64_t capacity, int64_t* size);
+int hdg_host_expand_mesh(const double* coords, int64_t nver, const int32_t* elems, int64_t nelt,
+                         const int32_t* dir, int64_t ndir, const int32_t* neu, int64_t nneu,
+                         int64_t* nfc, int32_t* faces, int32_t* facebyele, int32_t* perm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_H */

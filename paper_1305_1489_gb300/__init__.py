@@ -1,0 +1,235 @@
+"""GB300-native HDG hot path (Fu, Gatica, Sayas, arXiv 1305.1489) -- Python binding.
+
+Thin marshalling layer over the C ABI of libhdg (include/hdg.h): the functions below carry
+the C names and only convert torch tensors / numpy arrays into pointers.  Every step of the
+computation runs in the CUDA kernels of libhdg; there is no CPU path.  PyTorch provides
+device memory and the CUDA stream.
+
+    mesh = HDGMesh(coords, elements, dirichlet, neumann, k)   # hdg_mesh_create
+    X, Y, Z = mesh.volume_nodes()                             # hdg_quadrature_nodes
+    mesh.set_coefficients(kappa, c, f)                        # hdg_set_coefficients
+    mesh.set_boundary_data(uD, gN)                            # hdg_set_boundary_data
+    mesh.assemble_condense()                                  # hdg_assemble_condense
+    uhat, iters, relres = mesh.solve_trace(1e-10)             # hdg_solve_trace
+    q, u = mesh.recover(uhat)                                 # hdg_recover
+    ustar = mesh.postprocess(q, u)                            # hdg_postprocess
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import HDG_FP64, HDG_MIXED_FP32, HDGError  # noqa: F401
+
+__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "build", "load_library"]
+
+
+def build(**kw):
+    from .build import build as _b
+    return _b(**kw)
+
+
+def load_library():
+    return _lib.load()
+
+
+def _ptr(t):
+    """Device/host pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensors passed to libhdg must be contiguous"
+    return t.data_ptr()
+
+
+def _dev_f64(t, shape, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.contiguous()
+
+
+# ---------------------------------------------------------------- C-named thin wrappers
+def hdg_mesh_create(coords, elems, dirichlet, neumann, k, stream=0):
+    lib = _lib.load()
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    dirichlet = np.ascontiguousarray(np.asarray(dirichlet).reshape(-1, 3), dtype=np.int32)
+    neumann = np.ascontiguousarray(np.asarray(neumann).reshape(-1, 3), dtype=np.int32)
+    h = C.c_void_p()
+    _lib.check(lib.hdg_mesh_create(
+        _ptr(coords), coords.shape[0], _ptr(elems), elems.shape[0],
+        _ptr(dirichlet) if len(dirichlet) else None, len(dirichlet),
+        _ptr(neumann) if len(neumann) else None, len(neumann), int(k), C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def hdg_mesh_destroy(h):
+    return _lib.check(_lib.load().hdg_mesh_destroy(h))
+
+
+def hdg_mesh_get_info(h):
+    info = _lib.MeshInfo()
+    _lib.check(_lib.load().hdg_mesh_get_info(h, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in _lib.MeshInfo._fields_}
+
+
+def hdg_mesh_get_faces(h, nelt, nfc):
+    faces = np.zeros((nfc, 4), np.int32)
+    fbe = np.zeros((nelt, 4), np.int32)
+    perm = np.zeros((nelt, 4), np.int32)
+    _lib.check(_lib.load().hdg_mesh_get_faces(h, _ptr(faces), _ptr(fbe), _ptr(perm)))
+    return faces, fbe, perm
+
+
+def hdg_quadrature_nodes(h, X, Y, Z, FX, FY, FZ):
+    return _lib.check(_lib.load().hdg_quadrature_nodes(h, _ptr(X), _ptr(Y), _ptr(Z), _ptr(FX), _ptr(FY), _ptr(FZ)))
+
+
+def hdg_set_coefficients(h, kappa, c, beta, f, tau):
+    return _lib.check(_lib.load().hdg_set_coefficients(h, _ptr(kappa), _ptr(c), _ptr(beta), _ptr(f), _ptr(tau)))
+
+
+def hdg_set_boundary_data(h, uD, gN):
+    return _lib.check(_lib.load().hdg_set_boundary_data(h, _ptr(uD), _ptr(gN)))
+
+
+def hdg_assemble_condense(h, precision=HDG_FP64):
+    return _lib.check(_lib.load().hdg_assemble_condense(h, precision))
+
+
+def hdg_get_condensed(h, Cm, Cf):
+    return _lib.check(_lib.load().hdg_get_condensed(h, _ptr(Cm), _ptr(Cf)))
+
+
+def hdg_solve_trace(h, precision, rtol, maxit, x0, uhat):
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    code = _lib.load().hdg_solve_trace(h, precision, float(rtol), int(maxit), _ptr(x0), _ptr(uhat),
+                                       C.byref(it), C.byref(rr))
+    return code, it.value, rr.value
+
+
+def hdg_trace_residual(h, x, r):
+    rn = C.c_double(0.0)
+    bn = C.c_double(0.0)
+    _lib.check(_lib.load().hdg_trace_residual(h, _ptr(x), _ptr(r), C.byref(rn), C.byref(bn)))
+    return rn.value, bn.value
+
+
+def hdg_recover(h, uhat, q, u):
+    return _lib.check(_lib.load().hdg_recover(h, _ptr(uhat), _ptr(q), _ptr(u)))
+
+
+def hdg_postprocess(h, q, u, ustar):
+    return _lib.check(_lib.load().hdg_postprocess(h, _ptr(q), _ptr(u), _ptr(ustar)))
+
+
+def hdg_launch_count(h):
+    return int(_lib.load().hdg_launch_count(h))
+
+
+# ---------------------------------------------------------------- convenience handle
+class HDGMesh:
+    """Owns one hdg_mesh handle; tensors passed in are kept alive while the library borrows them."""
+
+    def __init__(self, coords, elements, dirichlet, neumann, k, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("HDGMesh needs a CUDA device: libhdg has no CPU path")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = hdg_mesh_create(coords, elements, dirichlet, neumann, k, self.stream.cuda_stream)
+        self.info = hdg_mesh_get_info(self._h)
+        for key in ("nelt", "nfc", "k", "n", "d2", "m", "n1", "nq", "nf"):
+            setattr(self, key, self.info[key])
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            hdg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, *shape):
+        import torch
+        return torch.empty(*shape, dtype=torch.float64, device="cuda")
+
+    def faces(self):
+        """(faces [nfc,4], facebyele [nelt,4], perm [nelt,4]) as numpy int32."""
+        return hdg_mesh_get_faces(self._h, self.nelt, self.nfc)
+
+    def volume_nodes(self):
+        X, Y, Z = (self._empty(self.nelt, self.nq) for _ in range(3))
+        hdg_quadrature_nodes(self._h, X, Y, Z, None, None, None)
+        return X, Y, Z
+
+    def face_nodes(self):
+        X, Y, Z = (self._empty(self.nfc, self.nf) for _ in range(3))
+        hdg_quadrature_nodes(self._h, None, None, None, X, Y, Z)
+        return X, Y, Z
+
+    def set_coefficients(self, kappa, c, f, tau=None):
+        kappa = _dev_f64(kappa, (self.nelt, self.nq), "kappa")
+        c = _dev_f64(c, (self.nelt, self.nq), "c")
+        f = _dev_f64(f, (self.nelt, self.nq), "f")
+        if tau is not None:
+            tau = _dev_f64(tau, (self.nelt, 4), "tau")
+        self._keep.update(kappa=kappa, c=c, f=f, tau=tau)
+        hdg_set_coefficients(self._h, kappa, c, None, f, tau)
+
+    def set_boundary_data(self, uD=None, gN=None):
+        if uD is not None:
+            uD = _dev_f64(uD, (self.nfc, self.nf), "uD")
+        if gN is not None:
+            gN = _dev_f64(gN, (3, self.nfc, self.nf), "gN")
+        self._keep.update(uD=uD, gN=gN)
+        hdg_set_boundary_data(self._h, uD, gN)
+
+    def assemble_condense(self):
+        hdg_assemble_condense(self._h, HDG_FP64)
+
+    def condensed(self):
+        Cm = self._empty(self.nelt, self.m, self.m)
+        Cf = self._empty(self.nelt, self.m)
+        hdg_get_condensed(self._h, Cm, Cf)
+        return Cm, Cf
+
+    def solve_trace(self, rtol=1e-10, maxit=20000, x0=None, precision=HDG_FP64, raise_on_fail=True):
+        uhat = self._empty(self.nfc, self.d2)
+        if x0 is not None:
+            x0 = _dev_f64(x0, (self.nfc, self.d2), "x0")
+        code, it, rr = hdg_solve_trace(self._h, precision, rtol, maxit, x0, uhat)
+        if code != 0 and raise_on_fail:
+            raise HDGError(code, _lib.last_error())
+        return uhat, it, rr
+
+    def residual(self, x):
+        r = self._empty(self.nfc, self.d2)
+        rn, bn = hdg_trace_residual(self._h, _dev_f64(x, (self.nfc, self.d2), "x"), r)
+        return r, rn, bn
+
+    def recover(self, uhat):
+        q = self._empty(self.nelt, 3, self.n)
+        u = self._empty(self.nelt, self.n)
+        hdg_recover(self._h, _dev_f64(uhat, (self.nfc, self.d2), "uhat"), q, u)
+        return q, u
+
+    def postprocess(self, q, u):
+        ustar = self._empty(self.nelt, self.n1)
+        hdg_postprocess(self._h, _dev_f64(q, (self.nelt, 3, self.n), "q"),
+                        _dev_f64(u, (self.nelt, self.n), "u"), ustar)
+        return ustar
+
+    @property
+    def launches(self):
+        return hdg_launch_count(self._h)

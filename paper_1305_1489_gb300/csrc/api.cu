@@ -1,0 +1,296 @@
+// C ABI of libhdg (declared in include/hdg.h): argument checking, ownership, dispatch.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hdg_internal.h"
+
+namespace hdg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int build_mesh(hdg_mesh* M, const double* coords, const int32_t* elems, const int32_t* dir,
+               const int32_t* neu);
+int build_mesh_host(hdg_mesh* M, const double* coords, const int32_t* elems, const int32_t* dir,
+                    const int32_t* neu, std::vector<int32_t>* owner_out);
+int64_t rec_stride_of(int k);
+
+template <typename T>
+static int upload(T** d, const std::vector<T>& h) {
+  HDG_CUDA_TRY(cudaMalloc(d, sizeof(T) * (h.empty() ? 1 : h.size())));
+  if (!h.empty()) HDG_CUDA_TRY(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return HDG_OK;
+}
+
+static std::vector<int16_t> pair_list(int n, int first) {
+  std::vector<int16_t> v;
+  for (int i = first; i < n; ++i)
+    for (int j = i; j < n; ++j) {
+      v.push_back((int16_t)(i - first));
+      v.push_back((int16_t)(j - first));
+    }
+  return v;
+}
+
+static int upload_tables(hdg_mesh* M) {
+  const Tables& T = M->tab;
+  DevTables& D = M->dt;
+  int rc;
+  if ((rc = upload(&D.P, T.P)) || (rc = upload(&D.Pd, T.Pd)) || (rc = upload(&D.Chat, T.Chat)) ||
+      (rc = upload(&D.S, T.S)) || (rc = upload(&D.E, T.E)) || (rc = upload(&D.vol_w, T.vol_w)) ||
+      (rc = upload(&D.lam, T.lam)) || (rc = upload(&D.face_w, T.face_w)) || (rc = upload(&D.xi, T.xi)) ||
+      (rc = upload(&D.D, T.D)) || (rc = upload(&D.P1, T.P1)) || (rc = upload(&D.G1, T.G1)) ||
+      (rc = upload(&D.Shat1, T.Shat1)))
+    return rc;
+  if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
+      (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
+    return rc;
+  return HDG_OK;
+}
+
+static void release(hdg_mesh* M) {
+  void* ptrs[] = {M->d_vx, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
+                  M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
+                  M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
+                  M->d_p32, M->d_q32, M->dt.P, M->dt.Pd, M->dt.Chat, M->dt.S, M->dt.E, M->dt.vol_w, M->dt.lam,
+                  M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
+                  M->dt.pairs_m, M->dt.pairs_n1};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (M->graph64) cudaGraphExecDestroy(M->graph64);
+  if (M->graph32) cudaGraphExecDestroy(M->graph32);
+  if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
+}
+
+static int check_status(hdg_mesh* M) {
+  int32_t st[4];
+  HDG_CUDA_TRY(cudaMemcpyAsync(st, M->d_status, sizeof(st), cudaMemcpyDeviceToHost, M->stream));
+  HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  if (st[1]) return fail(HDG_ERR_COEFF, std::to_string(st[1]) + " element(s) with kappa <= 0, c < 0 or non-finite data");
+  if (st[0]) return fail(HDG_ERR_LOCAL_SINGULAR, std::to_string(st[0]) + " element(s) with a non-positive local pivot");
+  if (st[2]) return fail(HDG_ERR_LOCAL_SINGULAR, std::to_string(st[2]) + " element(s) with a singular postprocess system");
+  if (st[3]) return fail(HDG_ERR_LOCAL_SINGULAR, std::to_string(st[3]) + " face block(s) not positive definite");
+  return HDG_OK;
+}
+
+}  // namespace hdg
+
+using namespace hdg;
+
+extern "C" {
+
+int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, int64_t nelt, const int32_t* dir,
+                    int64_t ndir, const int32_t* neu, int64_t nneu, int k, void* stream, hdg_mesh** out) {
+  if (!out) return fail(HDG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!coords || !elems || nver < 4 || nelt < 1 || ndir < 0 || nneu < 0 || (ndir && !dir) || (nneu && !neu))
+    return fail(HDG_ERR_ARG, "invalid mesh arrays or sizes");
+  if (k < 1 || k > 4) return fail(HDG_ERR_UNSUPPORTED, "degree k must be in 1..4");
+  if (nelt > (int64_t)1 << 30) return fail(HDG_ERR_ARG, "too many elements");
+  hdg_mesh* M = new (std::nothrow) hdg_mesh();
+  if (!M) return fail(HDG_ERR_ARG, "out of host memory");
+  M->k = k;
+  M->nver = nver;
+  M->nelt = nelt;
+  M->ndir = ndir;
+  M->nneu = nneu;
+  M->stream = (cudaStream_t)stream;
+  std::string err;
+  int rc = HDG_OK;
+  if (!build_tables(k, &M->tab, &err)) rc = fail(HDG_ERR_ARG, err);
+  if (!rc) rc = build_mesh(M, coords, elems, dir, neu);
+  if (!rc) rc = upload_tables(M);
+  if (!rc) {
+    const int m = M->tab.m;
+    M->rec_stride = rec_stride_of(k);
+    cudaError_t e = cudaMalloc(&M->d_C, sizeof(double) * nelt * m * m);
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_Cf, sizeof(double) * nelt * m);
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_rec, sizeof(double) * nelt * M->rec_stride);
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_status, sizeof(int32_t) * 4);
+    if (e != cudaSuccess) rc = fail(HDG_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  if (rc) {
+    release(M);
+    delete M;
+    return rc;
+  }
+  *out = M;
+  return HDG_OK;
+}
+
+int hdg_mesh_destroy(hdg_mesh* M) {
+  if (!M) return HDG_OK;
+  if (M->stream) cudaStreamSynchronize(M->stream);
+  release(M);
+  delete M;
+  return HDG_OK;
+}
+
+int hdg_mesh_get_info(const hdg_mesh* M, hdg_mesh_info* info) {
+  if (!M || !info) return fail(HDG_ERR_ARG, "NULL argument");
+  info->nelt = M->nelt;
+  info->nfc = M->nfc;
+  info->ndir = M->ndir;
+  info->nneu = M->nneu;
+  info->nver = M->nver;
+  info->k = M->k;
+  info->n = M->tab.n;
+  info->d2 = M->tab.d2;
+  info->m = M->tab.m;
+  info->n1 = M->tab.n1;
+  info->nq = M->tab.nq;
+  info->nf = M->tab.nf;
+  info->has_convection = 0;
+  return HDG_OK;
+}
+
+int hdg_mesh_get_faces(const hdg_mesh* M, int32_t* faces, int32_t* facebyele, int32_t* perm) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  if (faces) std::memcpy(faces, M->h_faces.data(), sizeof(int32_t) * M->h_faces.size());
+  if (facebyele) std::memcpy(facebyele, M->h_facebyele.data(), sizeof(int32_t) * M->h_facebyele.size());
+  if (perm) std::memcpy(perm, M->h_perm.data(), sizeof(int32_t) * M->h_perm.size());
+  return HDG_OK;
+}
+
+int hdg_quadrature_nodes(hdg_mesh* M, double* X, double* Y, double* Z, double* FX, double* FY, double* FZ) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  if ((X && (!Y || !Z)) || (FX && (!FY || !FZ))) return fail(HDG_ERR_ARG, "incomplete node triple");
+  HDG_CUDA_TRY(launch_qnodes(M, X, Y, Z, FX, FY, FZ));
+  return HDG_OK;
+}
+
+int hdg_set_coefficients(hdg_mesh* M, const double* kappa, const double* c, const double* beta, const double* f,
+                         const double* tau) {
+  if (!M || !kappa || !c || !f) return fail(HDG_ERR_ARG, "kappa, c and f are required");
+  if (beta) return fail(HDG_ERR_UNSUPPORTED, "convection (beta) is not part of this build");
+  M->kappa = kappa;
+  M->c = c;
+  M->f = f;
+  M->tau = tau;
+  M->assembled = false;
+  M->rhs_ready = false;
+  return HDG_OK;
+}
+
+int hdg_set_boundary_data(hdg_mesh* M, const double* uD, const double* gN) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  M->uD = uD;
+  M->gN = gN;
+  M->rhs_ready = false;
+  return HDG_OK;
+}
+
+int hdg_assemble_condense(hdg_mesh* M, int precision) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
+  if (precision != HDG_FP64) return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64");
+  HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
+  HDG_CUDA_TRY(launch_assemble(M));
+  M->assembled = true;
+  M->rhs_ready = false;
+  return check_status(M);
+}
+
+int hdg_get_condensed(const hdg_mesh* M, double* C, double* Cf) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  if (!M->assembled) return fail(HDG_ERR_STATE, "not assembled");
+  const int m = M->tab.m;
+  if (C) HDG_CUDA_TRY(cudaMemcpyAsync(C, M->d_C, sizeof(double) * M->nelt * m * m, cudaMemcpyDeviceToDevice, M->stream));
+  if (Cf) HDG_CUDA_TRY(cudaMemcpyAsync(Cf, M->d_Cf, sizeof(double) * M->nelt * m, cudaMemcpyDeviceToDevice, M->stream));
+  HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  return HDG_OK;
+}
+
+int hdg_solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0, double* uhat, int* iters,
+                    double* relres) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  int rc = solve_trace(M, precision, rtol, maxit, x0, uhat, iters, relres);
+  if (rc == HDG_OK) rc = check_status(M);
+  return rc;
+}
+
+int hdg_trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {
+  if (!M || !x || !r) return fail(HDG_ERR_ARG, "NULL argument");
+  return trace_residual(M, x, r, rnorm, bnorm);
+}
+
+int hdg_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
+  if (!M || !uhat || !q || !u) return fail(HDG_ERR_ARG, "NULL argument");
+  if (!M->assembled) return fail(HDG_ERR_STATE, "hdg_recover before hdg_assemble_condense");
+  HDG_CUDA_TRY(launch_recover(M, uhat, q, u));
+  return HDG_OK;
+}
+
+int hdg_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar) {
+  if (!M || !q || !u || !ustar) return fail(HDG_ERR_ARG, "NULL argument");
+  if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
+  HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 2, 0, sizeof(int32_t), M->stream));
+  HDG_CUDA_TRY(launch_postprocess(M, q, u, ustar));
+  return HDG_OK;
+}
+
+int hdg_last_error(char* buf, size_t len) {
+  if (!buf || !len) return HDG_ERR_ARG;
+  std::snprintf(buf, len, "%s", g_last_error.c_str());
+  return HDG_OK;
+}
+
+int64_t hdg_launch_count(const hdg_mesh* M) { return M ? M->launches : -1; }
+
+int hdg_host_table(int k, const char* name, double* out, int64_t capacity, int64_t* size) {
+  if (!name || !size) return fail(HDG_ERR_ARG, "NULL argument");
+  Tables T;
+  std::string err;
+  if (!build_tables(k, &T, &err)) return fail(HDG_ERR_UNSUPPORTED, err);
+  const std::string s(name);
+  const std::vector<double>* v = nullptr;
+  if (s == "vol_pts") v = &T.vol_pts;
+  else if (s == "vol_w") v = &T.vol_w;
+  else if (s == "P") v = &T.P;
+  else if (s == "Pd") v = &T.Pd;
+  else if (s == "Chat") v = &T.Chat;
+  else if (s == "face_pts") v = &T.face_pts;
+  else if (s == "face_w") v = &T.face_w;
+  else if (s == "Pl") v = &T.Pl;
+  else if (s == "D") v = &T.D;
+  else if (s == "Dmu") v = &T.Dmu;
+  else if (s == "S") v = &T.S;
+  else if (s == "E") v = &T.E;
+  else if (s == "P1") v = &T.P1;
+  else if (s == "G1") v = &T.G1;
+  else if (s == "Shat1") v = &T.Shat1;
+  else return fail(HDG_ERR_ARG, "unknown table " + s);
+  *size = (int64_t)v->size();
+  if (out) {
+    if (capacity < *size) return fail(HDG_ERR_ARG, "capacity too small");
+    std::memcpy(out, v->data(), sizeof(double) * v->size());
+  }
+  return HDG_OK;
+}
+
+int hdg_host_expand_mesh(const double* coords, int64_t nver, const int32_t* elems, int64_t nelt,
+                         const int32_t* dir, int64_t ndir, const int32_t* neu, int64_t nneu, int64_t* nfc,
+                         int32_t* faces, int32_t* facebyele, int32_t* perm) {
+  if (!coords || !elems || !nfc || nver < 4 || nelt < 1) return fail(HDG_ERR_ARG, "invalid mesh arrays");
+  hdg_mesh M;
+  M.nver = nver;
+  M.nelt = nelt;
+  M.ndir = ndir;
+  M.nneu = nneu;
+  std::vector<int32_t> own;
+  int rc = build_mesh_host(&M, coords, elems, dir, neu, &own);
+  if (rc) return rc;
+  *nfc = M.nfc;
+  if (faces) std::memcpy(faces, M.h_faces.data(), sizeof(int32_t) * M.h_faces.size());
+  if (facebyele) std::memcpy(facebyele, M.h_facebyele.data(), sizeof(int32_t) * M.h_facebyele.size());
+  if (perm) std::memcpy(perm, M.h_perm.data(), sizeof(int32_t) * M.h_perm.size());
+  return HDG_OK;
+}
+
+}  // extern "C"

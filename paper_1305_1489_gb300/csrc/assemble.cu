@@ -1,0 +1,337 @@
+// K1: per-element quadrature assembly of the local blocks and static condensation, FP64.
+//
+// For each element K (one CTA per element) this forms, from kappa, c, f at the volume nodes:
+//   M = M_{kappa^-1}, M_c (eq. 3.55), C_* (eq. 3.56), tauPP (eq. 4.5), tauDD (eq. 4.8),
+//   n_*DP = diag(n_*) E and tauDP = diag(T) E with E the perm-selected face tables (eq. 4.10),
+//   f^K (Section 3 "Source terms"),
+// and eliminates (q, u) from the local system of eq. 5.1-5.2 by two Cholesky factorisations
+// instead of an LU of the 4n x 4n matrix A_1 (same C^K and C_f^K to rounding):
+//   L L^T = M;  W_* = L^-1 C_*^T;  V = L^-1 E^T
+//   S_u = M_c + tauPP + sum_* W_*^T W_*          (Schur complement of the q block)
+//   G = diag(T) E + sum_* diag(n_*) V^T W_*      (face block l: V_l^T (sum_* n_{l*} W_*))
+//   L_s L_s^T = S_u;  H = L_s^-1 G^T;  h = L_s^-1 f
+//   C^K = (n_l . n_l') o (V^T V) - H^T H + tauDD   (eq. 5.5)
+//   C_f^K = H^T h                                 (eq. 5.6)
+// and stores the recovery operators of eq. 5.3:
+//   u = R_u u_dK + r_u with [R_u | r_u] = L_s^-T [H | h];
+//   q_* = MC_* u - Y (n_* o u_dK) with MC_* = L^-T W_* = M^-1 C_*^T, Y = L^-T V = M^-1 E^T.
+#include "device_common.cuh"
+#include "hdg_internal.h"
+
+namespace hdg {
+
+struct AsmArgs {
+  const double* vx;
+  const int32_t* perm;
+  const double *kappa, *c, *f, *tau;
+  const double *P, *Chat, *S, *E, *w;
+  const int16_t *pairs_n, *pairs_m;
+  double *C, *Cf, *rec;
+  int32_t* status;
+  int64_t nelt;
+};
+
+template <int K>
+struct AsmSmem {
+  using D = Dims<K>;
+  static constexpr int n = D::n, m = D::m, nq = D::nq;
+  static constexpr int o_kw = 0, o_cw = o_kw + nq, o_fw = o_cw + nq;
+  static constexpr int o_M = o_fw + nq;          // n*n   M -> L
+  static constexpr int o_S = o_M + n * n;        // n*n   S_u -> L_s
+  static constexpr int o_W = o_S + n * n;        // 3 n n W_*[l][c] -> MC_*
+  static constexpr int o_V = o_W + 3 * n * n;    // n*m   V[l][r] -> Y
+  static constexpr int o_Wt = o_V + n * m;       // 4 n n (sum_* n_{l*} W_*)[l'][j]
+  static constexpr int o_G = o_Wt + 4 * n * n;   // n*(m+1) G^T | f -> H | h -> R_u | r_u
+  static constexpr int o_C = o_G + n * (m + 1);  // m*m
+  static constexpr int total = o_C + m * m;
+  static constexpr size_t bytes = sizeof(double) * total;
+};
+
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
+  using D = Dims<K>;
+  using SM = AsmSmem<K>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq;
+  constexpr int NP = n * (n + 1) / 2, MP = m * (m + 1) / 2;
+  extern __shared__ double sm[];
+  double* kw = sm + SM::o_kw;
+  double* cw = sm + SM::o_cw;
+  double* fw = sm + SM::o_fw;
+  double* Ms = sm + SM::o_M;
+  double* Ss = sm + SM::o_S;
+  double* W = sm + SM::o_W;
+  double* V = sm + SM::o_V;
+  double* Wt = sm + SM::o_Wt;
+  double* Gt = sm + SM::o_G;
+  double* Cs = sm + SM::o_C;
+  __shared__ double s_a[3][3], s_nrm[4][3], s_T[4], s_vol;
+  __shared__ double invdM[n], invdS[n];
+  __shared__ int s_perm[4];
+  __shared__ int s_bad, s_coef;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int64_t Ke = blockIdx.x;
+
+  if (tid == 0) {
+    Geo g;
+    element_geometry(A.vx, A.nelt, Ke, g);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) s_a[i][j] = g.a[i][j];
+    for (int l = 0; l < 4; ++l) {
+      for (int d = 0; d < 3; ++d) s_nrm[l][d] = g.nrm[l][d];
+      double tau = A.tau ? A.tau[Ke * 4 + l] : 1.0;
+      s_T[l] = tau * g.area[l];  // T_l = tau_l |e_l|, eq. 4.22
+      s_perm[l] = A.perm[Ke * 4 + l] - 1;
+    }
+    s_vol = g.vol;
+    s_bad = 0;
+    s_coef = 0;
+  }
+  __syncthreads();
+
+  // coefficients weighted by |K| omega_q (eq. 3.2, 3.55)
+  for (int q = tid; q < nq; q += NT) {
+    double kap = A.kappa[Ke * nq + q], cc = A.c[Ke * nq + q], ff = A.f[Ke * nq + q];
+    if (!(kap > 0.0) || !(cc >= 0.0) || !isfinite(kap) || !isfinite(cc) || !isfinite(ff)) s_coef = 1;
+    double vw = s_vol * A.w[q];
+    kw[q] = vw / kap;
+    cw[q] = vw * cc;
+    fw[q] = vw * ff;
+  }
+  __syncthreads();
+
+  // masses M_{kappa^-1}, M_c + tauPP (lower+upper), f^K, C_*^T, E^T
+  for (int t = tid; t < NP; t += NT) {
+    const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
+    double s1 = 0.0, s2 = 0.0;
+#pragma unroll 5
+    for (int q = 0; q < nq; ++q) {
+      double pp = __ldg(A.P + q * n + i) * __ldg(A.P + q * n + j);
+      s1 = fma(kw[q], pp, s1);
+      s2 = fma(cw[q], pp, s2);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) s2 = fma(s_T[l], __ldg(A.S + (l * n + i) * n + j), s2);
+    Ms[i * n + j] = s1;
+    Ms[j * n + i] = s1;
+    Ss[i * n + j] = s2;
+    Ss[j * n + i] = s2;
+  }
+  for (int i = tid; i < n; i += NT) {
+    double s = 0.0;
+    for (int q = 0; q < nq; ++q) s = fma(fw[q], __ldg(A.P + q * n + i), s);
+    Gt[i * (m + 1) + m] = s;
+  }
+  for (int t = tid; t < 3 * n * n; t += NT) {
+    const int st = t / (n * n), rem = t - st * n * n, l = rem / n, cidx = rem - l * n;
+    // (C_*^T)[l][c] = C_*[c][l] = sum_# a_{*#} C_hat^#[c][l]
+    double s = 0.0;
+#pragma unroll
+    for (int h = 0; h < 3; ++h) s = fma(s_a[st][h], __ldg(A.Chat + (h * n + cidx) * n + l), s);
+    W[t] = s;
+  }
+  for (int t = tid; t < n * m; t += NT) {
+    const int l = t / m, r = t - l * m, fl = r / d2, a = r - fl * d2;
+    V[t] = __ldg(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + l);  // E^T
+  }
+  __syncthreads();
+
+  // L L^T = M (one warp)
+  if (warp == 0) {
+    bool ok = warp_cholesky<n>(Ms, invdM, lane);
+    if (!ok && lane == 0) s_bad = 1;
+  }
+  __syncthreads();
+
+  // W_* = L^-1 C_*^T (3n columns), V = L^-1 E^T (m columns)
+  for (int t = tid; t < 3 * n + m; t += NT) {
+    double* base;
+    int col, stride;
+    if (t < 3 * n) {
+      base = W + (t / n) * n * n;
+      col = t % n;
+      stride = n;
+    } else {
+      base = V;
+      col = t - 3 * n;
+      stride = m;
+    }
+    double x[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = base[l * stride + col];
+    fwd_subst<n>(Ms, invdM, x);
+#pragma unroll
+    for (int l = 0; l < n; ++l) base[l * stride + col] = x[l];
+  }
+  __syncthreads();
+
+  // S_u += sum_* W_*^T W_*;  Wt_l = sum_* n_{l*} W_*;  C = (n_l . n_l') (V^T V) + tauDD
+  for (int t = tid; t < NP; t += NT) {
+    const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
+    double s = 0.0;
+#pragma unroll
+    for (int st = 0; st < 3; ++st)
+#pragma unroll 4
+      for (int l = 0; l < n; ++l) s = fma(W[st * n * n + l * n + i], W[st * n * n + l * n + j], s);
+    Ss[i * n + j] += s;
+    if (i != j) Ss[j * n + i] += s;
+  }
+  for (int t = tid; t < 4 * n * n; t += NT) {
+    const int fl = t / (n * n), rem = t - fl * n * n;
+    Wt[t] = s_nrm[fl][0] * W[rem] + s_nrm[fl][1] * W[n * n + rem] + s_nrm[fl][2] * W[2 * n * n + rem];
+  }
+  for (int t = tid; t < MP; t += NT) {
+    const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
+    const int fr = r / d2, fs = s / d2;
+    double b = 0.0;
+#pragma unroll 4
+    for (int l = 0; l < n; ++l) b = fma(V[l * m + r], V[l * m + s], b);
+    const double nn = s_nrm[fr][0] * s_nrm[fs][0] + s_nrm[fr][1] * s_nrm[fs][1] + s_nrm[fr][2] * s_nrm[fs][2];
+    double cv = nn * b + (r == s ? s_T[fr] : 0.0);
+    Cs[r * m + s] = cv;
+    Cs[s * m + r] = cv;
+  }
+  __syncthreads();
+
+  // warp 0: L_s L_s^T = S_u;  other warps: G^T[j][r] = T_l E[r][j] + sum_l' V[l'][r] Wt_l[l'][j]
+  if (warp == 0) {
+    bool ok = warp_cholesky<n>(Ss, invdS, lane);
+    if (!ok && lane == 0) s_bad = 1;
+  } else {
+    for (int t = tid - 32; t < n * m; t += NT - 32) {
+      const int j = t / m, r = t - j * m, fl = r / d2, a = r - fl * d2;
+      double g = s_T[fl] * __ldg(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + j);
+      const double* wt = Wt + fl * n * n;
+#pragma unroll 4
+      for (int l = 0; l < n; ++l) g = fma(V[l * m + r], wt[l * n + j], g);
+      Gt[j * (m + 1) + r] = g;
+    }
+  }
+  __syncthreads();
+
+  // [H | h] = L_s^-1 [G^T | f];  Y = L^-T V;  MC_* = L^-T W_*
+  for (int t = tid; t < (m + 1) + m + 3 * n; t += NT) {
+    double x[n];
+    if (t < m + 1) {
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
+      fwd_subst<n>(Ss, invdS, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+    } else if (t < 2 * m + 1) {
+      const int col = t - (m + 1);
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = V[l * m + col];
+      bwd_subst<n>(Ms, invdM, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
+    } else {
+      const int tt = t - (2 * m + 1);
+      double* base = W + (tt / n) * n * n;
+      const int col = tt % n;
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = base[l * n + col];
+      bwd_subst<n>(Ms, invdM, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) base[l * n + col] = x[l];
+    }
+  }
+  __syncthreads();
+
+  // C -= H^T H;  C_f = H^T h
+  for (int t = tid; t < MP; t += NT) {
+    const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
+    double hh = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) hh = fma(Gt[j * (m + 1) + r], Gt[j * (m + 1) + s], hh);
+    Cs[r * m + s] -= hh;
+    if (r != s) Cs[s * m + r] -= hh;
+  }
+  for (int r = tid; r < m; r += NT) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) s = fma(Gt[j * (m + 1) + r], Gt[j * (m + 1) + m], s);
+    A.Cf[Ke * m + r] = s;
+  }
+  __syncthreads();
+
+  // [R_u | r_u] = L_s^-T [H | h];  write C^K
+  for (int t = tid; t < m + 1; t += NT) {
+    double x[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
+    bwd_subst<n>(Ss, invdS, x);
+#pragma unroll
+    for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+  }
+  double* Cout = A.C + Ke * (int64_t)(m * m);
+  for (int t = tid; t < m * m; t += NT) Cout[t] = Cs[t];
+  __syncthreads();
+
+  // recovery record: R_u|r_u [n][m+1], Y [n][m], MC [3][n][n], normals [4][3]
+  double* R = A.rec + Ke * (int64_t)D::rec;
+  for (int t = tid; t < n * (m + 1); t += NT) R[t] = Gt[t];
+  R += n * (m + 1);
+  for (int t = tid; t < n * m; t += NT) R[t] = V[t];
+  R += n * m;
+  for (int t = tid; t < 3 * n * n; t += NT) R[t] = W[t];
+  R += 3 * n * n;
+  if (tid < 12) R[tid] = s_nrm[tid / 3][tid % 3];
+  if (tid == 0) {
+    if (s_bad) atomicAdd(A.status + 0, 1);
+    if (s_coef) atomicAdd(A.status + 1, 1);
+  }
+}
+
+template <int K>
+static cudaError_t launch_k(hdg_mesh* M, const AsmArgs& a) {
+  constexpr int NT = (K >= 3) ? 256 : 128;
+  const size_t smem = AsmSmem<K>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(assemble_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  assemble_kernel<K, NT><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  M->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(hdg_mesh* M) {
+  AsmArgs a;
+  a.vx = M->d_vx;
+  a.perm = M->d_perm;
+  a.kappa = M->kappa;
+  a.c = M->c;
+  a.f = M->f;
+  a.tau = M->tau;
+  a.P = M->dt.P;
+  a.Chat = M->dt.Chat;
+  a.S = M->dt.S;
+  a.E = M->dt.E;
+  a.w = M->dt.vol_w;
+  a.pairs_n = M->dt.pairs_n;
+  a.pairs_m = M->dt.pairs_m;
+  a.C = M->d_C;
+  a.Cf = M->d_Cf;
+  a.rec = M->d_rec;
+  a.status = M->d_status;
+  a.nelt = M->nelt;
+  switch (M->k) {
+    case 1: return launch_k<1>(M, a);
+    case 2: return launch_k<2>(M, a);
+    case 3: return launch_k<3>(M, a);
+    case 4: return launch_k<4>(M, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int64_t rec_stride_of(int k) {
+  switch (k) {
+    case 1: return Dims<1>::rec;
+    case 2: return Dims<2>::rec;
+    case 3: return Dims<3>::rec;
+    case 4: return Dims<4>::rec;
+  }
+  return 0;
+}
+
+}  // namespace hdg

@@ -1,0 +1,122 @@
+// Internal declarations of libhdg (host tables, mesh handle, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+
+namespace hdg {
+
+// ------------------------------------------------------------------ reference tables
+// Host copies, row-major.  Built once per degree k (tables.cpp).
+struct Tables {
+  int k = 0, n = 0, d2 = 0, m = 0, nq = 0, nf = 0, n1 = 0;
+  std::vector<double> vol_pts;  // [nq][3]   p_hat_q                      (eq. 3.1)
+  std::vector<double> vol_w;    // [nq]      omega_hat_q, sum = 1         (eq. 3.1)
+  std::vector<double> lam;      // [nq][4]   barycentrics Lambda          (eq. 3.4)
+  std::vector<double> P;        // [nq][n]   P_hat_j(p_hat_q)             (eq. 3.5)
+  std::vector<double> Pd;       // [3][nq][n] d_* P_hat_j(p_hat_q)        (eq. 3.66)
+  std::vector<double> Chat;     // [3][n][n] C_hat^*                      (eq. 3.7)
+  std::vector<double> face_pts; // [nf][2]   q_hat_r = (s, t)
+  std::vector<double> face_w;   // [nf]      varpi_r, sum = 1
+  std::vector<double> xi;       // [nf][3]   barycentrics Xi              (eq. 6.2)
+  std::vector<double> Pl;       // [4][nf][n] P_hat_i(q_hat_r^l)          (eq. 4.4)
+  std::vector<double> D;        // [nf][d2]  D_hat_i(q_hat_r)             (eq. 4.7)
+  std::vector<double> Dmu;      // [6][nf][d2] D_hat_i(F_mu(q_hat_r))     (Section 4, type (c))
+  std::vector<double> S;        // [4][n][n] (varpi . P^l)^T P^l          (eq. 4.5)
+  std::vector<double> E;        // [4][6][d2][n] (varpi . D^mu)^T P^l     (eq. 4.10)
+  std::vector<double> P1;       // [nq][n1]  degree-(k+1) basis at the volume nodes
+  std::vector<double> G1;       // [3][nq][n1] its reference gradients
+  std::vector<double> Shat1;    // [6][n1][n1] (1/6) sum_q w d_# P'_i d_% P'_j, (#,%) in
+                                //   xx, xy, xz, yy, yz, zz  (stiffness of eq. 9.11)
+};
+
+bool build_tables(int k, Tables* t, std::string* err);
+int d3_of(int k);
+int d2_of(int k);
+
+// ------------------------------------------------------------------ device table copies
+struct DevTables {
+  double *P = nullptr, *Pd = nullptr, *Chat = nullptr, *S = nullptr, *E = nullptr;
+  double *vol_w = nullptr, *lam = nullptr, *face_w = nullptr, *xi = nullptr, *D = nullptr;
+  double *P1 = nullptr, *G1 = nullptr, *Shat1 = nullptr;
+  int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
+  int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices
+  int16_t* pairs_n1 = nullptr;  // [(n1-1) n1 / 2][2] pairs of 1..n1-1 (postprocess)
+};
+
+}  // namespace hdg
+
+// ------------------------------------------------------------------ mesh handle
+struct hdg_mesh {
+  int k = 0;
+  hdg::Tables tab;
+  hdg::DevTables dt;
+  int64_t nelt = 0, nfc = 0, nver = 0, ndir = 0, nneu = 0;
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+
+  // host expanded mesh
+  std::vector<int32_t> h_faces;      // [nfc][4]
+  std::vector<int32_t> h_facebyele;  // [nelt][4]
+  std::vector<int32_t> h_perm;       // [nelt][4] in 1..6
+
+  // device mesh
+  double* d_vx = nullptr;         // [12][nelt] SoA: x1..x4, y1..y4, z1..z4
+  double* d_fvx = nullptr;        // [9][nfc]   SoA: sorted face vertices x1..x3, y1..y3, z1..z3
+  int32_t* d_facebyele = nullptr; // [nelt][4]
+  int32_t* d_perm = nullptr;      // [nelt][4]
+  int32_t* d_owner = nullptr;     // [nfc][2]   4*K + l of the (up to) two elements, -1 if none
+  int32_t* d_ftype = nullptr;     // [nfc]      0 interior, 1 Dirichlet, 2 Neumann
+
+  // borrowed coefficient / data pointers (device)
+  const double *kappa = nullptr, *c = nullptr, *f = nullptr, *tau = nullptr;
+  const double *uD = nullptr, *gN = nullptr;
+
+  // products of hdg_assemble_condense (library-owned)
+  bool assembled = false;
+  double* d_C = nullptr;    // [nelt][m][m] condensed matrices C^K (eq. 5.5)
+  double* d_Cf = nullptr;   // [nelt][m]    C_f^K (eq. 5.6)
+  double* d_rec = nullptr;  // [nelt][rec_stride] recovery operators (eq. 5.3)
+  int64_t rec_stride = 0;
+  int32_t* d_status = nullptr;  // [4] error counters written by kernels
+
+  // trace-solve workspace (library-owned, allocated on first solve)
+  bool rhs_ready = false;
+  double bnorm = 0.0;  // ||b||_2 of the current right-hand side (host copy)
+  double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr,
+         *d_q = nullptr, *d_uhatD = nullptr, *d_BJ = nullptr, *d_red = nullptr,
+         *d_scal = nullptr;
+  unsigned int* d_counter = nullptr;
+  float *d_C32 = nullptr, *d_BJ32 = nullptr, *d_r32 = nullptr, *d_x32 = nullptr,
+        *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr;
+  int red_blocks = 0;
+  cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  int graph_iters = 0;
+};
+
+namespace hdg {
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+#define HDG_CUDA_TRY(expr)                                                               \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return ::hdg::fail(HDG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// kernel launchers (defined in the .cu files); return cudaGetLastError()
+cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* FX, double* FY,
+                          double* FZ);
+cudaError_t launch_assemble(hdg_mesh* M);
+cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u);
+cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar);
+int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0,
+                double* uhat, int* iters, double* relres);
+int trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm);
+}  // namespace hdg

@@ -1,0 +1,239 @@
+// K2 local recovery (eq. 5.3), K5 superconvergent postprocess (eq. 9.11), and the
+// quadrature-node helper (eq. 3.4, 6.2).  FP64.
+#include "device_common.cuh"
+#include "hdg_internal.h"
+
+namespace hdg {
+
+// ----------------------------------------------------------------------- nodes
+__global__ void qnodes_kernel(const double* __restrict__ vx, const double* __restrict__ lam,
+                              int64_t nelt, int nq, double* X, double* Y, double* Z) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nelt * nq) return;
+  const int64_t K = t / nq;
+  const int q = (int)(t - K * nq);
+  double out[3];
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i) s = fma(lam[q * 4 + i], vx[(d * 4 + i) * nelt + K], s);
+    out[d] = s;
+  }
+  X[t] = out[0];
+  Y[t] = out[1];
+  Z[t] = out[2];
+}
+
+__global__ void fnodes_kernel(const double* __restrict__ fvx, const double* __restrict__ xi,
+                              int64_t nfc, int nf, double* X, double* Y, double* Z) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nfc * nf) return;
+  const int64_t e = t / nf;
+  const int r = (int)(t - e * nf);
+  double out[3];
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i) s = fma(xi[r * 3 + i], fvx[(d * 3 + i) * nfc + e], s);
+    out[d] = s;
+  }
+  X[t] = out[0];
+  Y[t] = out[1];
+  Z[t] = out[2];
+}
+
+cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* FX, double* FY,
+                          double* FZ) {
+  const int nq = M->tab.nq, nf = M->tab.nf;
+  if (X) {
+    int64_t tot = M->nelt * nq;
+    qnodes_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(M->d_vx, M->dt.lam, M->nelt, nq, X, Y, Z);
+    M->launches++;
+  }
+  if (FX) {
+    int64_t tot = M->nfc * nf;
+    fnodes_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(M->d_fvx, M->dt.xi, M->nfc, nf, FX, FY, FZ);
+    M->launches++;
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------- recovery
+// u = R_u u_dK + r_u;  q_* = MC_* u - Y (n_* o u_dK)     (eq. 5.3 through the factors of K1)
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) recover_kernel(const double* __restrict__ rec,
+                                                     const int32_t* __restrict__ fbe,
+                                                     const double* __restrict__ uhat, int64_t nelt,
+                                                     double* __restrict__ q, double* __restrict__ u) {
+  using D = Dims<K>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2;
+  __shared__ double uh[m], us[n], nrm[12];
+  const int64_t Ke = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* R = rec + Ke * (int64_t)D::rec;
+  const double* Y = R + n * (m + 1);
+  const double* MC = Y + n * m;
+  for (int t = tid; t < m; t += NT) {
+    const int f = fbe[Ke * 4 + t / d2];
+    uh[t] = uhat[(int64_t)f * d2 + (t % d2)];
+  }
+  if (tid < 12) nrm[tid] = MC[3 * n * n + tid];
+  __syncthreads();
+  for (int i = warp; i < n; i += NT / 32) {
+    double s = 0.0;
+    for (int r = lane; r < m + 1; r += 32) s = fma(R[i * (m + 1) + r], r < m ? uh[r] : 1.0, s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      us[i] = s;
+      u[Ke * n + i] = s;
+    }
+  }
+  __syncthreads();
+  for (int l = warp; l < n; l += NT / 32) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int r = lane; r < m; r += 32) {
+      const double yu = Y[l * m + r] * uh[r];
+      const int fl = r / d2;
+      s[0] = fma(-yu, nrm[3 * fl + 0], s[0]);
+      s[1] = fma(-yu, nrm[3 * fl + 1], s[1]);
+      s[2] = fma(-yu, nrm[3 * fl + 2], s[2]);
+    }
+    for (int c = lane; c < n; c += 32) {
+      const double uc = us[c];
+      s[0] = fma(MC[(0 * n + l) * n + c], uc, s[0]);
+      s[1] = fma(MC[(1 * n + l) * n + c], uc, s[1]);
+      s[2] = fma(MC[(2 * n + l) * n + c], uc, s[2]);
+    }
+#pragma unroll
+    for (int st = 0; st < 3; ++st)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[st] += __shfl_xor_sync(0xffffffffu, s[st], o);
+    if (lane == 0)
+      for (int st = 0; st < 3; ++st) q[(Ke * 3 + st) * n + l] = s[st];
+  }
+}
+
+cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
+  const unsigned g = (unsigned)M->nelt;
+  switch (M->k) {
+    case 1: recover_kernel<1, 64><<<g, 64, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 2: recover_kernel<2, 64><<<g, 64, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 3: recover_kernel<3, 128><<<g, 128, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 4: recover_kernel<4, 128><<<g, 128, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    default: return cudaErrorInvalidValue;
+  }
+  M->launches++;
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------- postprocess
+// (grad u*, grad w)_K = -(kappa^-1 q_h, grad w)_K for w in P_{k+1}(K), (u*, 1)_K = (u_h, 1)_K.
+// With the orthonormal hierarchical basis P'_1 = 1 and P'_i (i > 1) has zero mean, so
+// u*_1 = u_{h,1} and the coefficients 2..n1 solve the (n1-1) x (n1-1) SPD stiffness system.
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) postprocess_kernel(
+    const double* __restrict__ vx, const double* __restrict__ kappa, const double* __restrict__ P,
+    const double* __restrict__ G1, const double* __restrict__ Shat1, const double* __restrict__ w,
+    const int16_t* __restrict__ pairs1, const double* __restrict__ q, const double* __restrict__ u,
+    int64_t nelt, double* __restrict__ ustar, int32_t* status) {
+  using D = Dims<K>;
+  constexpr int n = D::n, nq = D::nq, n1 = D::n1, nr = n1 - 1;
+  constexpr int NP = nr * (nr + 1) / 2;
+  __shared__ double Ks[nr * nr], rhs[nr], invd[nr];
+  __shared__ double qs[3 * n], Qs[3 * nq];
+  __shared__ double s_a[3][3], s_det, s_g[6];
+  __shared__ int s_bad;
+  const int64_t Ke = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    Geo g;
+    element_geometry(vx, nelt, Ke, g);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) s_a[i][j] = g.a[i][j];
+    s_det = g.det;
+    const int pr[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+      for (int st = 0; st < 3; ++st) s += g.a[st][pr[c][0]] * g.a[st][pr[c][1]];
+      s_g[c] = s / g.det;
+    }
+    s_bad = 0;
+  }
+  for (int t = tid; t < 3 * n; t += NT) qs[t] = q[Ke * 3 * n + t];
+  __syncthreads();
+  // Q_#(p) = omega kappa^-1 sum_* a_{*#} q_*(p) at each node
+  for (int p = tid; p < nq; p += NT) {
+    double qh[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+      const double pv = __ldg(P + p * n + i);
+      qh[0] = fma(qs[i], pv, qh[0]);
+      qh[1] = fma(qs[n + i], pv, qh[1]);
+      qh[2] = fma(qs[2 * n + i], pv, qh[2]);
+    }
+    const double wk = w[p] / kappa[Ke * nq + p];
+    for (int h = 0; h < 3; ++h)
+      Qs[h * nq + p] = wk * (s_a[0][h] * qh[0] + s_a[1][h] * qh[1] + s_a[2][h] * qh[2]);
+  }
+  // reduced stiffness (indices 1..n1-1)
+  for (int t = tid; t < NP; t += NT) {
+    const int i = pairs1[2 * t], j = pairs1[2 * t + 1];  // 0-based into 1..n1-1
+    const int I = i + 1, J = j + 1;
+    double s = 0.0;
+    for (int c = 0; c < 6; ++c) {
+      const double sij = __ldg(Shat1 + (c * n1 + I) * n1 + J);
+      const double sji = __ldg(Shat1 + (c * n1 + J) * n1 + I);
+      const bool diag = (c == 0 || c == 3 || c == 5);
+      s = fma(s_g[c], diag ? sij : sij + sji, s);
+    }
+    Ks[i * nr + j] = s;
+    Ks[j * nr + i] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < nr; i += NT) {
+    double s = 0.0;
+    for (int h = 0; h < 3; ++h)
+      for (int p = 0; p < nq; ++p) s = fma(Qs[h * nq + p], __ldg(G1 + (h * nq + p) * n1 + i + 1), s);
+    rhs[i] = -s / 6.0;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    bool ok = warp_cholesky<nr>(Ks, invd, lane);
+    if (!ok && lane == 0) s_bad = 1;
+    __syncwarp();
+    // L y = rhs, L^T x = y, in shared memory (one lane; nr <= 55)
+    if (lane == 0) {
+      for (int i = 0; i < nr; ++i) {
+        double s = rhs[i];
+        for (int l = 0; l < i; ++l) s = fma(-Ks[i * nr + l], rhs[l], s);
+        rhs[i] = s * invd[i];
+      }
+      for (int i = nr - 1; i >= 0; --i) {
+        double s = rhs[i];
+        for (int l = i + 1; l < nr; ++l) s = fma(-Ks[l * nr + i], rhs[l], s);
+        rhs[i] = s * invd[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < n1; t += NT) ustar[Ke * n1 + t] = (t == 0) ? u[Ke * n] : rhs[t - 1];
+  if (tid == 0 && s_bad) atomicAdd(status + 2, 1);
+}
+
+cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar) {
+  const unsigned g = (unsigned)M->nelt;
+#define HDG_PP(KK, NTT)                                                                             \
+  postprocess_kernel<KK, NTT><<<g, NTT, 0, M->stream>>>(M->d_vx, M->kappa, M->dt.P, M->dt.G1,      \
+                                                       M->dt.Shat1, M->dt.vol_w, M->dt.pairs_n1, q, \
+                                                       u, M->nelt, ustar, M->d_status)
+  switch (M->k) {
+    case 1: HDG_PP(1, 64); break;
+    case 2: HDG_PP(2, 64); break;
+    case 3: HDG_PP(3, 128); break;
+    case 4: HDG_PP(4, 128); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef HDG_PP
+  M->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace hdg

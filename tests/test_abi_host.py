@@ -1,0 +1,112 @@
+"""C-ABI library: loads, exports every declared symbol, and its host logic (quadrature,
+bases, table products, expanded mesh) agrees with the independent oracle.  CPU only: no
+call here touches the GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import basis, hdg as ohdg, quadrature
+from oracle.geometry import ExpandedMesh
+from workloads import boundary_faces, kuhn_cube
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1305_1489_gb300 import _lib, build
+    build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hdg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hdg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1305_1489_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.exported_symbols())
+
+
+def _table(lib, k, name):
+    size = C.c_int64(0)
+    assert lib.hdg_host_table(k, name.encode(), None, 0, C.byref(size)) == 0
+    out = np.zeros(size.value)
+    assert lib.hdg_host_table(k, name.encode(), out.ctypes.data, size.value, C.byref(size)) == 0
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_host_tables_match_oracle(lib, k):
+    tab = ohdg.Tables(k)
+    n, d2 = tab.n, tab.d2
+    assert np.allclose(_table(lib, k, "vol_pts").reshape(-1, 3), tab.p, atol=1e-15, rtol=0)
+    assert np.allclose(_table(lib, k, "vol_w"), tab.w, atol=1e-15, rtol=0)
+    assert np.allclose(_table(lib, k, "face_pts").reshape(-1, 2), tab.qf, atol=1e-15, rtol=0)
+    assert np.allclose(_table(lib, k, "face_w"), tab.varpi, atol=1e-15, rtol=0)
+    tol = 1e-12
+    assert np.abs(_table(lib, k, "P").reshape(-1, n) - tab.P).max() < tol
+    assert np.abs(_table(lib, k, "Pd").reshape(3, -1, n) - tab.Pstar).max() < 1e-11
+    assert np.abs(_table(lib, k, "Chat").reshape(3, n, n) - tab.Chat).max() < tol
+    assert np.abs(_table(lib, k, "Pl").reshape(4, -1, n) - tab.Pl).max() < tol
+    assert np.abs(_table(lib, k, "D").reshape(-1, d2) - tab.D).max() < tol
+    assert np.abs(_table(lib, k, "Dmu").reshape(6, -1, d2) - tab.Dmu).max() < tol
+    S = np.stack([(tab.varpi[:, None] * tab.Pl[l]).T @ tab.Pl[l] for l in range(4)])
+    assert np.abs(_table(lib, k, "S").reshape(4, n, n) - S).max() < tol
+    E = np.stack([[(tab.varpi[:, None] * tab.Dmu[mu]).T @ tab.Pl[l] for mu in range(6)] for l in range(4)])
+    assert np.abs(_table(lib, k, "E").reshape(4, 6, d2, n) - E).max() < tol
+    n1 = basis.d3(k + 1)
+    assert np.abs(_table(lib, k, "P1").reshape(-1, n1) - basis.dubiner3(k + 1, tab.p)).max() < tol
+    assert np.abs(_table(lib, k, "G1").reshape(3, -1, n1) - basis.dubiner3_grad(k + 1, tab.p)).max() < 1e-11
+
+
+def _expand(lib, c, e, d, nn):
+    nelt = len(e)
+    nfc = C.c_int64(0)
+    faces = np.zeros((4 * nelt, 4), np.int32)
+    fbe = np.zeros((nelt, 4), np.int32)
+    perm = np.zeros((nelt, 4), np.int32)
+    c = np.ascontiguousarray(c, np.float64)
+    e = np.ascontiguousarray(e, np.int32)
+    d = np.ascontiguousarray(d, np.int32)
+    nn = np.ascontiguousarray(nn, np.int32)
+    rc = lib.hdg_host_expand_mesh(c.ctypes.data, len(c), e.ctypes.data, nelt,
+                                  d.ctypes.data if len(d) else None, len(d),
+                                  nn.ctypes.data if len(nn) else None, len(nn),
+                                  C.byref(nfc), faces.ctypes.data, fbe.ctypes.data, perm.ctypes.data)
+    return rc, faces[:nfc.value], fbe, perm
+
+
+@pytest.mark.parametrize("s,jit", [(2, 0.0), (3, 0.2)])
+def test_host_expanded_mesh_matches_oracle(lib, s, jit):
+    c, e = kuhn_cube(s, jitter=jit, seed=1)
+    d, n = boundary_faces(c, e, lambda ax, v: "D" if ax == 2 else "N")
+    rc, faces, fbe, perm = _expand(lib, c, e, d, n)
+    assert rc == 0
+    m = ExpandedMesh(c, e, d, n)
+    assert np.array_equal(faces[:, :3], m.faces)
+    assert np.array_equal(faces[:, 3], m.facetype)
+    assert np.array_equal(fbe, m.facebyele)
+    assert np.array_equal(perm, m.perm)
+
+
+def test_host_mesh_errors(lib):
+    c, e = kuhn_cube(1)
+    d, n = boundary_faces(c, e, lambda ax, v: "D")
+    rc, *_ = _expand(lib, c, e, d[:-1], n)
+    assert rc == 3  # HDG_ERR_NONCONFORMING: a boundary face is in neither list
+    e2 = e.copy()
+    e2[0, [2, 3]] = e2[0, [3, 2]]
+    rc, *_ = _expand(lib, c, e2, d, n)
+    assert rc == 2  # HDG_ERR_ORIENTATION
+    size = C.c_int64(0)
+    assert lib.hdg_host_table(7, b"P", None, 0, C.byref(size)) == 9  # HDG_ERR_UNSUPPORTED
