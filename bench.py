@@ -282,6 +282,11 @@ def run_gpu(args, rank, world, local_rank):
         phase_ms, total_ms = tt.tolist()
     value = world * nelt * args.steps / (phase_ms / 1e3)
 
+    if args.only_steps:
+        return {"phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
+                              "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
+                "value": value, "gpu_launches": int(launches), "ms_per_step": total_ms / args.steps}
+
     # time-to-1e-10: plain FP64 zero-start block-Jacobi PCG vs mixed precision
     solve = {}
     for name, prec in (("plain_fp64", HDG_FP64), ("mixed_fp32_fp64", HDG_MIXED_FP32)):
@@ -361,6 +366,27 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
+def profile_k1(s_sub, launches=2):
+    """Small case for a full ncu capture of K1: the same problem on an s^3 x 6 mesh."""
+    import torch
+
+    from paper_1305_1489_gb300 import HDGMesh, build
+    from workloads import boundary_faces, get_problem, kuhn_cube
+
+    build()
+    prob = get_problem(WORKLOAD["name"]).at(s=s_sub)
+    c, e = kuhn_cube(prob.s)
+    d, n = boundary_faces(c, e, prob.classify)
+    M = HDGMesh(c, e, d, n, prob.k)
+    X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    M.set_coefficients(dv(prob.kappa(X, Y, Z)), dv(prob.c(X, Y, Z)), dv(prob.f(X, Y, Z)))
+    for _ in range(launches):
+        M.assemble_condense()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_k1": {"nelt": M.nelt, "launches": launches}}))
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -384,7 +410,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-sample", type=int, default=12288, help="oracle elements per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true", help="timed steps only (profiling)")
+    ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
     args = ap.parse_args()
+    if args.profile_k1:
+        profile_k1(args.profile_k1)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -400,7 +431,7 @@ def main():
         dist.init_process_group("nccl")
     out = run_gpu(args, rank, world, local_rank)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and not args.only_steps:
             out["cpu_baseline"] = oracle_baseline(sample_elems=args.ref_sample, steps=1, warmup=1)
         print(json.dumps(out))
     if world > 1:

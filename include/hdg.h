@@ -102,11 +102,23 @@ int hdg_quadrature_nodes(hdg_mesh* mesh, double* X, double* Y, double* Z,
 /* PDE coefficients at the volume nodes (device f64, borrowed: they must stay valid until
  * the next hdg_assemble_condense and hdg_postprocess that use them have completed).
  *   kappa [nelt][nq] > 0, c [nelt][nq] >= 0, f [nelt][nq];
- *   beta: must be NULL (convection is not part of this build);
+ *   beta [3][nelt][nq]: convection field (Section 9, eq. 9.1) or NULL for reaction-diffusion;
+ *     when given, hdg_set_face_convection must also be called before assembly;
  *   tau [nelt][4] >= 0 per element face (eq. 4.22), or NULL for tau = 1.
- * Positivity is checked in hdg_assemble_condense (HDG_ERR_COEFF).                         */
+ * With convection the method solves div(q + beta u) + c u = f with the numerical flux
+ * q.nu + (beta.nu) u_hat + tau (u - u_hat); tau - beta.nu/2 > 0 and c + div(beta)/2 >= 0
+ * are the caller's responsibility (they make the local solves and the trace system
+ * well posed).  Positivity of kappa and c is checked in hdg_assemble_condense (HDG_ERR_COEFF). */
 int hdg_set_coefficients(hdg_mesh* mesh, const double* kappa, const double* c,
                          const double* beta, const double* f, const double* tau);
+
+/* Element face nodes F_K(q_hat_r^l) (eq. 4.1): X, Y, Z device f64 [nelt][4][nf], the points
+ * where the convection field enters the face integrals of Section 9.                     */
+int hdg_element_face_nodes(hdg_mesh* mesh, double* X, double* Y, double* Z);
+
+/* Convection field at the element face nodes, beta_f [3][nelt][4][nf] device f64 (borrowed).
+ * Used by the face matrices <(beta.nu) D_i, P_j> and <(beta.nu) D_i, D_j> (Section 9).   */
+int hdg_set_face_convection(hdg_mesh* mesh, const double* beta_f);
 
 /* Boundary data at the face nodes (device f64, borrowed like the coefficients):
  *   uD [nfc][nf]: u_D at the face nodes (read on Dirichlet faces only), or NULL for u_D = 0;
@@ -121,11 +133,13 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
 
-/* Copy the condensed local matrices out (tests): C [nelt][m][m], Cf [nelt][m] device f64. */
+/* Copy the condensed local matrices out (tests): C [nelt][m][m] (row-major C^K), Cf [nelt][m]
+ * device f64.                                                                              */
 int hdg_get_condensed(const hdg_mesh* mesh, double* C, double* Cf);
 
 /* Global trace system H u_hat = F + G_N (eq. 6.5), Dirichlet faces eliminated (Section 6),
- * solved matrix-free element by element with block-Jacobi preconditioned CG to
+ * solved matrix-free element by element with block-Jacobi preconditioned CG (BiCGStab when a
+ * convection field is set: the trace matrix is then non-symmetric) to
  *   ||b - H u_hat||_2 <= rtol ||b||_2  (FP64 residual over the free dofs).
  *   precision: HDG_FP64 (plain PCG) or HDG_MIXED_FP32 (FP32 inner PCG, FP64 refinement).
  *   x0: device f64 [nfc][d2] initial guess or NULL (zero start).

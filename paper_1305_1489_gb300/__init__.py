@@ -26,7 +26,7 @@ __all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "build", "load_l
 
 
 def build(**kw):
-    from .build import build as _b
+    from .buildlib import build as _b
     return _b(**kw)
 
 
@@ -93,6 +93,14 @@ def hdg_quadrature_nodes(h, X, Y, Z, FX, FY, FZ):
 
 def hdg_set_coefficients(h, kappa, c, beta, f, tau):
     return _lib.check(_lib.load().hdg_set_coefficients(h, _ptr(kappa), _ptr(c), _ptr(beta), _ptr(f), _ptr(tau)))
+
+
+def hdg_element_face_nodes(h, X, Y, Z):
+    return _lib.check(_lib.load().hdg_element_face_nodes(h, _ptr(X), _ptr(Y), _ptr(Z)))
+
+
+def hdg_set_face_convection(h, beta_f):
+    return _lib.check(_lib.load().hdg_set_face_convection(h, _ptr(beta_f)))
 
 
 def hdg_set_boundary_data(h, uD, gN):
@@ -178,14 +186,29 @@ class HDGMesh:
         hdg_quadrature_nodes(self._h, None, None, None, X, Y, Z)
         return X, Y, Z
 
-    def set_coefficients(self, kappa, c, f, tau=None):
+    def element_face_nodes(self):
+        """F_K(q_hat_r^l): X, Y, Z [nelt, 4, nf] (where beta enters the face integrals)."""
+        X, Y, Z = (self._empty(self.nelt, 4, self.nf) for _ in range(3))
+        hdg_element_face_nodes(self._h, X, Y, Z)
+        return X, Y, Z
+
+    def set_coefficients(self, kappa, c, f, tau=None, beta=None, beta_faces=None):
+        """kappa, c, f [nelt, nq]; tau [nelt, 4]; beta [3, nelt, nq] and beta_faces
+        [3, nelt, 4, nf] (convection, both or neither)."""
         kappa = _dev_f64(kappa, (self.nelt, self.nq), "kappa")
         c = _dev_f64(c, (self.nelt, self.nq), "c")
         f = _dev_f64(f, (self.nelt, self.nq), "f")
         if tau is not None:
             tau = _dev_f64(tau, (self.nelt, 4), "tau")
-        self._keep.update(kappa=kappa, c=c, f=f, tau=tau)
-        hdg_set_coefficients(self._h, kappa, c, None, f, tau)
+        if (beta is None) != (beta_faces is None):
+            raise ValueError("beta and beta_faces go together")
+        if beta is not None:
+            beta = _dev_f64(beta, (3, self.nelt, self.nq), "beta")
+            beta_faces = _dev_f64(beta_faces, (3, self.nelt, 4, self.nf), "beta_faces")
+        self._keep.update(kappa=kappa, c=c, f=f, tau=tau, beta=beta, beta_faces=beta_faces)
+        hdg_set_coefficients(self._h, kappa, c, beta, f, tau)
+        if beta is not None:
+            hdg_set_face_convection(self._h, beta_faces)
 
     def set_boundary_data(self, uD=None, gN=None):
         if uD is not None:

@@ -39,6 +39,8 @@ _SIGS = {
     "hdg_quadrature_nodes": [P, P, P, P, P, P, P],
     "hdg_set_coefficients": [P, P, P, P, P, P],
     "hdg_set_boundary_data": [P, P, P],
+    "hdg_element_face_nodes": [P, P, P, P],
+    "hdg_set_face_convection": [P, P],
     "hdg_assemble_condense": [P, C.c_int],
     "hdg_get_condensed": [P, P, P],
     "hdg_solve_trace": [P, C.c_int, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
@@ -64,7 +66,7 @@ def load(path=LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"libhdg.so not built at {path}; run paper_1305_1489_gb300.build.build()")
+        raise ImportError(f"libhdg.so not built at {path}; run paper_1305_1489_gb300.build()")
     lib = C.CDLL(path)
     for name, args in _SIGS.items():
         fn = getattr(lib, name)

@@ -1,6 +1,6 @@
 """Build libhdg.so in-tree: every translation unit compiled in parallel by nvcc for sm_103a.
 
-    python -m paper_1305_1489_gb300.build [--verbose-ptxas]
+    python -m paper_1305_1489_gb300.buildlib [--verbose-ptxas]
 """
 
 import os

@@ -46,7 +46,8 @@ static int upload_tables(hdg_mesh* M) {
       (rc = upload(&D.S, T.S)) || (rc = upload(&D.E, T.E)) || (rc = upload(&D.vol_w, T.vol_w)) ||
       (rc = upload(&D.lam, T.lam)) || (rc = upload(&D.face_w, T.face_w)) || (rc = upload(&D.xi, T.xi)) ||
       (rc = upload(&D.D, T.D)) || (rc = upload(&D.P1, T.P1)) || (rc = upload(&D.G1, T.G1)) ||
-      (rc = upload(&D.Shat1, T.Shat1)))
+      (rc = upload(&D.Shat1, T.Shat1)) || (rc = upload(&D.Pl, T.Pl)) || (rc = upload(&D.Dmu, T.Dmu)) ||
+      (rc = upload(&D.face_pts, T.face_pts)))
     return rc;
   if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
       (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
@@ -60,11 +61,12 @@ static void release(hdg_mesh* M) {
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
                   M->d_p32, M->d_q32, M->dt.P, M->dt.Pd, M->dt.Chat, M->dt.S, M->dt.E, M->dt.vol_w, M->dt.lam,
                   M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
-                  M->dt.pairs_m, M->dt.pairs_n1};
+                  M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
   if (M->graph32) cudaGraphExecDestroy(M->graph32);
+  if (M->graph_bicg) cudaGraphExecDestroy(M->graph_bicg);
   if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
 }
 
@@ -146,7 +148,7 @@ int hdg_mesh_get_info(const hdg_mesh* M, hdg_mesh_info* info) {
   info->n1 = M->tab.n1;
   info->nq = M->tab.nq;
   info->nf = M->tab.nf;
-  info->has_convection = 0;
+  info->has_convection = M->beta_q != nullptr;
   return HDG_OK;
 }
 
@@ -168,11 +170,29 @@ int hdg_quadrature_nodes(hdg_mesh* M, double* X, double* Y, double* Z, double* F
 int hdg_set_coefficients(hdg_mesh* M, const double* kappa, const double* c, const double* beta, const double* f,
                          const double* tau) {
   if (!M || !kappa || !c || !f) return fail(HDG_ERR_ARG, "kappa, c and f are required");
-  if (beta) return fail(HDG_ERR_UNSUPPORTED, "convection (beta) is not part of this build");
+  if ((beta != nullptr) != (M->beta_q != nullptr)) {  // switching symmetric <-> non-symmetric
+    if (M->graph64) { cudaGraphExecDestroy(M->graph64); M->graph64 = nullptr; }
+  }
+  M->beta_q = beta;
+  if (!beta) M->beta_f = nullptr;
   M->kappa = kappa;
   M->c = c;
   M->f = f;
   M->tau = tau;
+  M->assembled = false;
+  M->rhs_ready = false;
+  return HDG_OK;
+}
+
+int hdg_element_face_nodes(hdg_mesh* M, double* X, double* Y, double* Z) {
+  if (!M || !X || !Y || !Z) return fail(HDG_ERR_ARG, "NULL argument");
+  HDG_CUDA_TRY(launch_element_face_nodes(M, X, Y, Z));
+  return HDG_OK;
+}
+
+int hdg_set_face_convection(hdg_mesh* M, const double* beta_f) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  M->beta_f = beta_f;
   M->assembled = false;
   M->rhs_ready = false;
   return HDG_OK;
@@ -190,6 +210,7 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
   if (precision != HDG_FP64) return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64");
+  if (M->beta_q && !M->beta_f) return fail(HDG_ERR_STATE, "convection set without hdg_set_face_convection");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   HDG_CUDA_TRY(launch_assemble(M));
   M->assembled = true;
@@ -201,7 +222,8 @@ int hdg_get_condensed(const hdg_mesh* M, double* C, double* Cf) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (!M->assembled) return fail(HDG_ERR_STATE, "not assembled");
   const int m = M->tab.m;
-  if (C) HDG_CUDA_TRY(cudaMemcpyAsync(C, M->d_C, sizeof(double) * M->nelt * m * m, cudaMemcpyDeviceToDevice, M->stream));
+  if (C && M->beta_q) HDG_CUDA_TRY(launch_transpose_blocks(const_cast<hdg_mesh*>(M), M->d_C, C));  // stored transposed
+  else if (C) HDG_CUDA_TRY(cudaMemcpyAsync(C, M->d_C, sizeof(double) * M->nelt * m * m, cudaMemcpyDeviceToDevice, M->stream));
   if (Cf) HDG_CUDA_TRY(cudaMemcpyAsync(Cf, M->d_Cf, sizeof(double) * M->nelt * m, cudaMemcpyDeviceToDevice, M->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
   return HDG_OK;

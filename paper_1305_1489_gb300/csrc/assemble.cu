@@ -15,6 +15,18 @@
 // and stores the recovery operators of eq. 5.3:
 //   u = R_u u_dK + r_u with [R_u | r_u] = L_s^-T [H | h];
 //   q_* = MC_* u - Y (n_* o u_dK) with MC_* = L^-T W_* = M^-1 C_*^T, Y = L^-T V = M^-1 E^T.
+//
+// Convection (CONV = true; reading of Section 9: div(q + beta u) + c u = f, flux
+// q.nu + (beta.nu) u_hat + tau (u - u_hat)) adds to the same elimination
+//   B_c = -(beta P_j, grad P_i)_K (eq. 9.1 matrices) to S_u, which is then non-symmetric and
+//   factored by LU without pivoting (its symmetric part is positive definite when
+//   c + div(beta)/2 >= 0 and tau - beta.nu/2 > 0);
+//   alphaDP = <(beta.nu) D_i, P_j> and alphaDD = <(beta.nu) D_i, D_j> per face (element
+//   parametrisation of eq. 4.1, beta given at the element's face nodes);
+//   G_col = G - alphaDP;  S_u = L U;  H_col = L^-1 G_col^T,  H_row = U^-T G^T;
+//   C^K = (n_l . n_l') o (V^T V) - H_row^T H_col + tauDD - alphaDD,  C_f = H_row^T L^-1 f;
+//   [R_u | r_u] = U^-1 [H_col | L^-1 f].
+// C^K is then stored transposed (the trace operator reads C^K rows as stored columns).
 #include "device_common.cuh"
 #include "hdg_internal.h"
 
@@ -24,17 +36,19 @@ struct AsmArgs {
   const double* vx;
   const int32_t* perm;
   const double *kappa, *c, *f, *tau;
+  const double *beta_q, *beta_f;  // [3][nelt][nq], [3][nelt][4][nf] (convection only)
   const double *P, *Chat, *S, *E, *w;
+  const double *Pd, *Pl, *Dmu, *wf;  // convection only
   const int16_t *pairs_n, *pairs_m;
   double *C, *Cf, *rec;
   int32_t* status;
   int64_t nelt;
 };
 
-template <int K>
+template <int K, bool CONV>
 struct AsmSmem {
   using D = Dims<K>;
-  static constexpr int n = D::n, m = D::m, nq = D::nq;
+  static constexpr int n = D::n, m = D::m, nq = D::nq, nf = D::nf, d2 = D::d2;
   static constexpr int o_kw = 0, o_cw = o_kw + nq, o_fw = o_cw + nq;
   static constexpr int o_M = o_fw + nq;          // n*n   M -> L
   static constexpr int o_S = o_M + n * n;        // n*n   S_u -> L_s
@@ -43,15 +57,21 @@ struct AsmSmem {
   static constexpr int o_Wt = o_V + n * m;       // 4 n n (sum_* n_{l*} W_*)[l'][j]
   static constexpr int o_G = o_Wt + 4 * n * n;   // n*(m+1) G^T | f -> H | h -> R_u | r_u
   static constexpr int o_C = o_G + n * (m + 1);  // m*m
-  static constexpr int total = o_C + m * m;
+  // convection: H_row^T [n][m] (first alphaDP^T, then G^T, then H_row), 3 x nq reference
+  // convection weights, 4 x nf face weights varpi (beta . n_l), alphaDD [4][d2][d2]
+  static constexpr int o_Hr = o_C + m * m;
+  static constexpr int o_bw = o_Hr + (CONV ? n * m : 0);
+  static constexpr int o_bn = o_bw + (CONV ? 3 * nq : 0);
+  static constexpr int o_aDD = o_bn + (CONV ? 4 * nf : 0);
+  static constexpr int total = o_aDD + (CONV ? 4 * d2 * d2 : 0);
   static constexpr size_t bytes = sizeof(double) * total;
 };
 
-template <int K, int NT>
+template <int K, int NT, bool CONV>
 __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
   using D = Dims<K>;
-  using SM = AsmSmem<K>;
-  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq;
+  using SM = AsmSmem<K, CONV>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq, nf = D::nf;
   constexpr int NP = n * (n + 1) / 2, MP = m * (m + 1) / 2;
   extern __shared__ double sm[];
   double* kw = sm + SM::o_kw;
@@ -64,6 +84,10 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
   double* Wt = sm + SM::o_Wt;
   double* Gt = sm + SM::o_G;
   double* Cs = sm + SM::o_C;
+  double* Hr = sm + SM::o_Hr;
+  double* bw = sm + SM::o_bw;
+  double* bn = sm + SM::o_bn;
+  double* aDD = sm + SM::o_aDD;
   __shared__ double s_a[3][3], s_nrm[4][3], s_T[4], s_vol;
   __shared__ double invdM[n], invdS[n];
   __shared__ int s_perm[4];
@@ -98,6 +122,24 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
     kw[q] = vw / kap;
     cw[q] = vw * cc;
     fw[q] = vw * ff;
+    if constexpr (CONV) {
+      // -(1/6) omega_q sum_* a_{*#} beta_*(p_q): B_c = sum_q sum_# bw[#][q] P_qj dhat_# P_qi
+      const double b0 = A.beta_q[(0 * A.nelt + Ke) * nq + q], b1 = A.beta_q[(1 * A.nelt + Ke) * nq + q],
+                   b2 = A.beta_q[(2 * A.nelt + Ke) * nq + q];
+      const double sc = -A.w[q] / 6.0;
+#pragma unroll
+      for (int h = 0; h < 3; ++h) bw[h * nq + q] = sc * (s_a[0][h] * b0 + s_a[1][h] * b1 + s_a[2][h] * b2);
+    }
+  }
+  if constexpr (CONV) {
+    // varpi_r beta(x_{r,l}^K) . n_l at the element's face nodes
+    for (int t = tid; t < 4 * nf; t += NT) {
+      const int fl = t / nf, r = t - fl * nf;
+      double acc = 0.0;
+#pragma unroll
+      for (int st = 0; st < 3; ++st) acc = fma(A.beta_f[((int64_t)st * A.nelt + Ke) * 4 * nf + t], s_nrm[fl][st], acc);
+      bn[t] = A.wf[r] * acc;
+    }
   }
   __syncthreads();
 
@@ -115,8 +157,23 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
     for (int l = 0; l < 4; ++l) s2 = fma(s_T[l], __ldg(A.S + (l * n + i) * n + j), s2);
     Ms[i * n + j] = s1;
     Ms[j * n + i] = s1;
-    Ss[i * n + j] = s2;
-    Ss[j * n + i] = s2;
+    if constexpr (CONV) {
+      double bij = 0.0, bji = 0.0;  // B_c[i][j] = sum bw P_qj d P_qi,  B_c[j][i] = sum bw P_qi d P_qj
+      for (int q = 0; q < nq; ++q) {
+        const double pi = __ldg(A.P + q * n + i), pj = __ldg(A.P + q * n + j);
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+          const double wq = bw[h * nq + q];
+          bij = fma(wq * pj, __ldg(A.Pd + (h * nq + q) * n + i), bij);
+          bji = fma(wq * pi, __ldg(A.Pd + (h * nq + q) * n + j), bji);
+        }
+      }
+      Ss[i * n + j] = s2 + bij;
+      Ss[j * n + i] = s2 + bji;
+    } else {
+      Ss[i * n + j] = s2;
+      Ss[j * n + i] = s2;
+    }
   }
   for (int i = tid; i < n; i += NT) {
     double s = 0.0;
@@ -134,6 +191,23 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
   for (int t = tid; t < n * m; t += NT) {
     const int l = t / m, r = t - l * m, fl = r / d2, a = r - fl * d2;
     V[t] = __ldg(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + l);  // E^T
+    if constexpr (CONV) {
+      // alphaDP^T[l][r] = sum_r' varpi (beta.n) D^mu_{r'a} P^l_{r'l}
+      const double* Dm = A.Dmu + (int64_t)s_perm[fl] * nf * d2;
+      const double* Pl = A.Pl + (int64_t)fl * nf * n;
+      double acc = 0.0;
+      for (int rr = 0; rr < nf; ++rr) acc = fma(bn[fl * nf + rr] * __ldg(Dm + rr * d2 + a), __ldg(Pl + rr * n + l), acc);
+      Hr[t] = acc;
+    }
+  }
+  if constexpr (CONV) {
+    for (int t = tid; t < 4 * d2 * d2; t += NT) {
+      const int fl = t / (d2 * d2), ab = t - fl * d2 * d2, a = ab / d2, b = ab - a * d2;
+      const double* Dm = A.Dmu + (int64_t)s_perm[fl] * nf * d2;
+      double acc = 0.0;
+      for (int rr = 0; rr < nf; ++rr) acc = fma(bn[fl * nf + rr] * __ldg(Dm + rr * d2 + a), __ldg(Dm + rr * d2 + b), acc);
+      aDD[t] = acc;
+    }
   }
   __syncthreads();
 
@@ -189,6 +263,9 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
     for (int l = 0; l < n; ++l) b = fma(V[l * m + r], V[l * m + s], b);
     const double nn = s_nrm[fr][0] * s_nrm[fs][0] + s_nrm[fr][1] * s_nrm[fs][1] + s_nrm[fr][2] * s_nrm[fs][2];
     double cv = nn * b + (r == s ? s_T[fr] : 0.0);
+    if constexpr (CONV) {
+      if (fr == fs) cv -= aDD[fr * d2 * d2 + (r - fr * d2) * d2 + (s - fs * d2)];
+    }
     Cs[r * m + s] = cv;
     Cs[s * m + r] = cv;
   }
@@ -196,7 +273,7 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
 
   // warp 0: L_s L_s^T = S_u;  other warps: G^T[j][r] = T_l E[r][j] + sum_l' V[l'][r] Wt_l[l'][j]
   if (warp == 0) {
-    bool ok = warp_cholesky<n>(Ss, invdS, lane);
+    bool ok = CONV ? warp_lu<n>(Ss, invdS, lane) : warp_cholesky<n>(Ss, invdS, lane);
     if (!ok && lane == 0) s_bad = 1;
   } else {
     for (int t = tid - 32; t < n * m; t += NT - 32) {
@@ -205,20 +282,34 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
       const double* wt = Wt + fl * n * n;
 #pragma unroll 4
       for (int l = 0; l < n; ++l) g = fma(V[l * m + r], wt[l * n + j], g);
-      Gt[j * (m + 1) + r] = g;
+      if constexpr (CONV) {
+        Gt[j * (m + 1) + r] = g - Hr[j * m + r];  // G_col^T = (G - alphaDP)^T
+        Hr[j * m + r] = g;                       // G^T
+      } else {
+        Gt[j * (m + 1) + r] = g;
+      }
     }
   }
   __syncthreads();
 
   // [H | h] = L_s^-1 [G^T | f];  Y = L^-T V;  MC_* = L^-T W_*
-  for (int t = tid; t < (m + 1) + m + 3 * n; t += NT) {
+  // (convection: [H_col | h] = L^-1 [G_col^T | f] and H_row = U^-T G^T)
+  constexpr int NTRI = (m + 1) + m + 3 * n + (CONV ? m : 0);
+  for (int t = tid; t < NTRI; t += NT) {
     double x[n];
     if (t < m + 1) {
 #pragma unroll
       for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
-      fwd_subst<n>(Ss, invdS, x);
+      if constexpr (CONV) fwd_subst_unit<n>(Ss, x); else fwd_subst<n>(Ss, invdS, x);
 #pragma unroll
       for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+    } else if (t >= 2 * m + 1 + 3 * n) {
+      const int col = t - (2 * m + 1 + 3 * n);
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = Hr[l * m + col];
+      fwd_subst_Ut<n>(Ss, invdS, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) Hr[l * m + col] = x[l];
     } else if (t < 2 * m + 1) {
       const int col = t - (m + 1);
 #pragma unroll
@@ -239,19 +330,31 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
   }
   __syncthreads();
 
-  // C -= H^T H;  C_f = H^T h
-  for (int t = tid; t < MP; t += NT) {
-    const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
-    double hh = 0.0;
+  // C -= H^T H;  C_f = H^T h   (convection: C -= H_row^T H_col;  C_f = H_row^T h)
+  if constexpr (CONV) {
+    for (int t = tid; t < m * m; t += NT) {
+      const int r = t / m, s = t - r * m;
+      double hh = 0.0;
 #pragma unroll 4
-    for (int j = 0; j < n; ++j) hh = fma(Gt[j * (m + 1) + r], Gt[j * (m + 1) + s], hh);
-    Cs[r * m + s] -= hh;
-    if (r != s) Cs[s * m + r] -= hh;
+      for (int j = 0; j < n; ++j) hh = fma(Hr[j * m + r], Gt[j * (m + 1) + s], hh);
+      Cs[t] -= hh;
+    }
+  } else {
+    for (int t = tid; t < MP; t += NT) {
+      const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
+      double hh = 0.0;
+#pragma unroll 4
+      for (int j = 0; j < n; ++j) hh = fma(Gt[j * (m + 1) + r], Gt[j * (m + 1) + s], hh);
+      Cs[r * m + s] -= hh;
+      if (r != s) Cs[s * m + r] -= hh;
+    }
   }
   for (int r = tid; r < m; r += NT) {
+    const double* hrow = CONV ? Hr : Gt;
+    const int ld = CONV ? m : (m + 1);
     double s = 0.0;
 #pragma unroll 4
-    for (int j = 0; j < n; ++j) s = fma(Gt[j * (m + 1) + r], Gt[j * (m + 1) + m], s);
+    for (int j = 0; j < n; ++j) s = fma(hrow[j * ld + r], Gt[j * (m + 1) + m], s);
     A.Cf[Ke * m + r] = s;
   }
   __syncthreads();
@@ -261,12 +364,19 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
     double x[n];
 #pragma unroll
     for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
-    bwd_subst<n>(Ss, invdS, x);
+    if constexpr (CONV) bwd_subst_U<n>(Ss, invdS, x); else bwd_subst<n>(Ss, invdS, x);
 #pragma unroll
     for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
   }
   double* Cout = A.C + Ke * (int64_t)(m * m);
-  for (int t = tid; t < m * m; t += NT) Cout[t] = Cs[t];
+  if constexpr (CONV) {
+    for (int t = tid; t < m * m; t += NT) {  // stored transposed: Cout[s][r] = C^K[r][s]
+      const int sidx = t / m, r = t - sidx * m;
+      Cout[t] = Cs[r * m + sidx];
+    }
+  } else {
+    for (int t = tid; t < m * m; t += NT) Cout[t] = Cs[t];
+  }
   __syncthreads();
 
   // recovery record: R_u|r_u [n][m+1], Y [n][m], MC [3][n][n], normals [4][3]
@@ -284,13 +394,13 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
   }
 }
 
-template <int K>
+template <int K, bool CONV>
 static cudaError_t launch_k(hdg_mesh* M, const AsmArgs& a) {
   constexpr int NT = (K >= 3) ? 256 : 128;
-  const size_t smem = AsmSmem<K>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(assemble_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = AsmSmem<K, CONV>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(assemble_kernel<K, NT, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  assemble_kernel<K, NT><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  assemble_kernel<K, NT, CONV><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
   M->launches += 1;
   return cudaGetLastError();
 }
@@ -303,6 +413,12 @@ cudaError_t launch_assemble(hdg_mesh* M) {
   a.c = M->c;
   a.f = M->f;
   a.tau = M->tau;
+  a.beta_q = M->beta_q;
+  a.beta_f = M->beta_f;
+  a.Pd = M->dt.Pd;
+  a.Pl = M->dt.Pl;
+  a.Dmu = M->dt.Dmu;
+  a.wf = M->dt.face_w;
   a.P = M->dt.P;
   a.Chat = M->dt.Chat;
   a.S = M->dt.S;
@@ -315,11 +431,12 @@ cudaError_t launch_assemble(hdg_mesh* M) {
   a.rec = M->d_rec;
   a.status = M->d_status;
   a.nelt = M->nelt;
+  const bool conv = M->beta_q != nullptr;
   switch (M->k) {
-    case 1: return launch_k<1>(M, a);
-    case 2: return launch_k<2>(M, a);
-    case 3: return launch_k<3>(M, a);
-    case 4: return launch_k<4>(M, a);
+    case 1: return conv ? launch_k<1, true>(M, a) : launch_k<1, false>(M, a);
+    case 2: return conv ? launch_k<2, true>(M, a) : launch_k<2, false>(M, a);
+    case 3: return conv ? launch_k<3, true>(M, a) : launch_k<3, false>(M, a);
+    case 4: return conv ? launch_k<4, true>(M, a) : launch_k<4, false>(M, a);
   }
   return cudaErrorInvalidValue;
 }

@@ -114,6 +114,29 @@ __device__ __forceinline__ bool warp_cholesky(double* A, double* invd, int lane)
   return ok;
 }
 
+// In-place LU without pivoting (Doolittle: unit-lower L below the diagonal, U on and above)
+// of an N x N matrix in shared memory, by one warp.  Used for matrices whose symmetric part
+// is positive definite (then every leading minor is non-zero).  invd receives 1/U_jj.
+template <int N>
+__device__ __forceinline__ bool warp_lu(double* A, double* invd, int lane) {
+  bool ok = true;
+  for (int j = 0; j < N; ++j) {
+    const double piv = A[j * N + j];
+    ok = ok && (piv != 0.0) && isfinite(piv);
+    const double ip = 1.0 / piv;
+    if (lane == 0) invd[j] = ip;
+    for (int i = j + 1 + lane; i < N; i += 32) A[i * N + j] *= ip;
+    __syncwarp();
+    const int w = N - j - 1;
+    for (int t = lane; t < w * w; t += 32) {
+      const int i = j + 1 + t / w, l = j + 1 + t % w;
+      A[i * N + l] = fma(-A[i * N + j], A[j * N + l], A[i * N + l]);
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
 // Forward substitution L x = b for one right-hand-side column held in registers.
 template <int N>
 __device__ __forceinline__ void fwd_subst(const double* __restrict__ L, const double* invd, double* x) {
@@ -122,6 +145,42 @@ __device__ __forceinline__ void fwd_subst(const double* __restrict__ L, const do
     double s = x[l];
 #pragma unroll
     for (int i = 0; i < l; ++i) s = fma(-L[l * N + i], x[i], s);
+    x[l] = s * invd[l];
+  }
+}
+
+// Forward substitution with the unit-lower factor of warp_lu.
+template <int N>
+__device__ __forceinline__ void fwd_subst_unit(const double* __restrict__ LU, double* x) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    double s = x[l];
+#pragma unroll
+    for (int i = 0; i < l; ++i) s = fma(-LU[l * N + i], x[i], s);
+    x[l] = s;
+  }
+}
+
+// Forward substitution U^T x = b (U^T is lower triangular) with the factor of warp_lu.
+template <int N>
+__device__ __forceinline__ void fwd_subst_Ut(const double* __restrict__ LU, const double* invd, double* x) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    double s = x[l];
+#pragma unroll
+    for (int i = 0; i < l; ++i) s = fma(-LU[i * N + l], x[i], s);
+    x[l] = s * invd[l];
+  }
+}
+
+// Backward substitution U x = b with the factor of warp_lu.
+template <int N>
+__device__ __forceinline__ void bwd_subst_U(const double* __restrict__ LU, const double* invd, double* x) {
+#pragma unroll
+  for (int l = N - 1; l >= 0; --l) {
+    double s = x[l];
+#pragma unroll
+    for (int i = l + 1; i < N; ++i) s = fma(-LU[l * N + i], x[i], s);
     x[l] = s * invd[l];
   }
 }

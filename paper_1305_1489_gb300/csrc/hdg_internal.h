@@ -43,7 +43,7 @@ int d2_of(int k);
 struct DevTables {
   double *P = nullptr, *Pd = nullptr, *Chat = nullptr, *S = nullptr, *E = nullptr;
   double *vol_w = nullptr, *lam = nullptr, *face_w = nullptr, *xi = nullptr, *D = nullptr;
-  double *P1 = nullptr, *G1 = nullptr, *Shat1 = nullptr;
+  double *P1 = nullptr, *G1 = nullptr, *Shat1 = nullptr, *Pl = nullptr, *Dmu = nullptr, *face_pts = nullptr;
   int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
   int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices
   int16_t* pairs_n1 = nullptr;  // [(n1-1) n1 / 2][2] pairs of 1..n1-1 (postprocess)
@@ -75,6 +75,8 @@ struct hdg_mesh {
 
   // borrowed coefficient / data pointers (device)
   const double *kappa = nullptr, *c = nullptr, *f = nullptr, *tau = nullptr;
+  const double *beta_q = nullptr;  // [3][nelt][nq] convection at the volume nodes, or NULL
+  const double *beta_f = nullptr;  // [3][nelt][4][nf] convection at the element face nodes
   const double *uD = nullptr, *gN = nullptr;
 
   // products of hdg_assemble_condense (library-owned)
@@ -95,7 +97,8 @@ struct hdg_mesh {
   float *d_C32 = nullptr, *d_BJ32 = nullptr, *d_r32 = nullptr, *d_x32 = nullptr,
         *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr;
   int red_blocks = 0;
-  cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
+  cudaGraphExec_t graph64 = nullptr, graph32 = nullptr, graph_bicg = nullptr;
+  double* d_bicg = nullptr;  // [4][nfc][d2] extra BiCGStab vectors (s, t, ph, sh)
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   int graph_iters = 0;
 };
@@ -115,6 +118,8 @@ cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* 
                           double* FZ);
 cudaError_t launch_assemble(hdg_mesh* M);
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u);
+cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double* Z);
+cudaError_t launch_transpose_blocks(hdg_mesh* M, const double* src, double* dst);
 cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar);
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0,
                 double* uhat, int* iters, double* relres);

@@ -56,6 +56,57 @@ cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* 
   return cudaGetLastError();
 }
 
+// F_K(q_hat_r^l) for every element, local face l (eq. 2.5 / 4.1) and face node r
+__global__ void efnodes_kernel(const double* __restrict__ vx, const double* __restrict__ qf, int64_t nelt, int nf,
+                               double* X, double* Y, double* Z) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nelt * 4 * nf) return;
+  const int64_t K = t / (4 * nf);
+  const int rem = (int)(t - K * 4 * nf), l = rem / nf, r = rem - l * nf;
+  const double s = qf[2 * r], u = qf[2 * r + 1];
+  double ref[3];
+  switch (l) {  // q_hat^l of Section 4
+    case 0: ref[0] = s; ref[1] = u; ref[2] = 0.0; break;
+    case 1: ref[0] = s; ref[1] = 0.0; ref[2] = u; break;
+    case 2: ref[0] = 0.0; ref[1] = s; ref[2] = u; break;
+    default: ref[0] = s; ref[1] = u; ref[2] = 1.0 - s - u; break;
+  }
+  double out[3];
+  for (int d = 0; d < 3; ++d) {
+    const double v1 = vx[(d * 4 + 0) * nelt + K];
+    double acc = v1;
+    for (int j = 0; j < 3; ++j) acc = fma(vx[(d * 4 + j + 1) * nelt + K] - v1, ref[j], acc);
+    out[d] = acc;
+  }
+  X[t] = out[0];
+  Y[t] = out[1];
+  Z[t] = out[2];
+}
+
+cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double* Z) {
+  const int64_t tot = M->nelt * 4 * M->tab.nf;
+  efnodes_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(M->d_vx, M->dt.face_pts, M->nelt, M->tab.nf,
+                                                                       X, Y, Z);
+  M->launches++;
+  return cudaGetLastError();
+}
+
+__global__ void transpose_blocks_kernel(const double* __restrict__ src, double* __restrict__ dst, int64_t nelt, int m) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nelt * m * m) return;
+  const int64_t K = t / (m * m);
+  const int rem = (int)(t - K * m * m), i = rem / m, j = rem - i * m;
+  dst[t] = src[K * m * m + j * m + i];
+}
+
+cudaError_t launch_transpose_blocks(hdg_mesh* M, const double* src, double* dst) {
+  const int m = M->tab.m;
+  const int64_t tot = M->nelt * m * m;
+  transpose_blocks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(src, dst, M->nelt, m);
+  M->launches++;
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------- recovery
 // u = R_u u_dK + r_u;  q_* = MC_* u - Y (n_* o u_dK)     (eq. 5.3 through the factors of K1)
 template <int K, int NT>

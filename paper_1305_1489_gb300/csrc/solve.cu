@@ -190,7 +190,8 @@ __global__ void rhs_kernel(FaceArgs F, const double* __restrict__ C, const doubl
 // Inverse of each free face's diagonal block of H (block-Jacobi), by Cholesky.  One thread
 // per face; T = the precision the inverse is stored in.
 template <typename T>
-__global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, T* __restrict__ Binv, int32_t* status) {
+__global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, T* __restrict__ Binv, int32_t* status,
+                          bool nonsym) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= F.nfc) return;
   const int d2 = F.d2, m = F.m;
@@ -205,10 +206,35 @@ __global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, T* __restric
     if (ow < 0) continue;
     const double* Ck = C + (int64_t)(ow >> 2) * m * m;
     const int r0 = (ow & 3) * d2;
+    // stored C^K (symmetric) or its transpose (convection): block (i, j) of C^K is at [r0+j][r0+i]
     for (int i = 0; i < d2; ++i)
-      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Ck[(r0 + i) * m + r0 + j];
+      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Ck[(r0 + j) * m + r0 + i];
   }
   bool ok = true;
+  if (nonsym) {  // Gauss-Jordan without pivoting (the block's symmetric part is positive definite)
+    for (int i = 0; i < d2 * d2; ++i) X[i] = 0.0;
+    for (int i = 0; i < d2; ++i) X[i * d2 + i] = 1.0;
+    for (int j = 0; j < d2; ++j) {
+      const double piv = A[j * d2 + j];
+      ok = ok && piv != 0.0 && isfinite(piv);
+      const double ip = 1.0 / piv;
+      for (int c = 0; c < d2; ++c) {
+        A[j * d2 + c] *= ip;
+        X[j * d2 + c] *= ip;
+      }
+      for (int i = 0; i < d2; ++i) {
+        if (i == j) continue;
+        const double f = A[i * d2 + j];
+        for (int c = 0; c < d2; ++c) {
+          A[i * d2 + c] -= f * A[j * d2 + c];
+          X[i * d2 + c] -= f * X[j * d2 + c];
+        }
+      }
+    }
+    for (int i = 0; i < d2 * d2; ++i) Binv[e * d2 * d2 + i] = (T)X[i];
+    if (!ok) atomicAdd(status + 3, 1);
+    return;
+  }
   for (int j = 0; j < d2; ++j) {  // in-place lower Cholesky
     double s = A[j * d2 + j];
     for (int l = 0; l < j; ++l) s -= A[j * d2 + l] * A[j * d2 + l];
@@ -362,6 +388,137 @@ __global__ void pcg_dir_kernel(int64_t ntot, const T* __restrict__ z, T* __restr
   if (t < ntot) p[t] = z[t] + (T)beta * p[t];
 }
 
+// ------------------------------------------------------------------ BiCGStab (convection)
+// Right-preconditioned BiCGStab (van der Vorst 1992) with the block-Jacobi preconditioner,
+// for the non-symmetric trace matrix of convection-diffusion.  Vectors: x, r, rhat (shadow
+// residual), p, v, s, t, ph = M^-1 p, sh = M^-1 s.  Scalars rho, alpha, omega, beta on the
+// device; five kernels per iteration.
+enum { B_RHO = 0, B_ALPHA, B_OMEGA, B_BETA, B_RR, B_DONE, B_ITERS, B_TOL2, B_MAXIT, B_BAD, B_NSCAL };
+
+struct BicgVecs {
+  double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
+};
+
+// r = b - H x (or b), rhat = r, p = v = 0; rho = rhat.r, beta = 0, omega = 1, rr
+__global__ void bicg_init_kernel(FaceArgs F, const double* __restrict__ C, const double* __restrict__ b,
+                                 BicgVecs V, bool have_x, double* red, unsigned int* counter, double* scal) {
+  int64_t e, t;
+  int a;
+  double v[2] = {0.0, 0.0};
+  if (face_slot(F, e, a, t)) {
+    double rv = 0.0;
+    if (F.ftype[e] != 1) rv = b[t] - (have_x ? face_apply<double>(C, V.x, F, e, a) : 0.0);
+    if (!have_x) V.x[t] = 0.0;
+    V.r[t] = rv;
+    V.rh[t] = rv;
+    V.p[t] = 0.0;
+    V.v[t] = 0.0;
+    v[0] = rv * rv;
+    v[1] = rv * rv;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
+    scal[B_RHO] = out[0];
+    scal[B_RR] = out[1];
+    scal[B_BETA] = 0.0;
+    scal[B_OMEGA] = 1.0;
+    scal[B_ITERS] = 0.0;
+    scal[B_DONE] = (out[1] <= scal[B_TOL2]) ? 1.0 : 0.0;
+  }
+}
+
+// p = r + beta (p - omega v);  ph = M^-1 p
+__global__ void bicg_p_kernel(FaceArgs F, const double* __restrict__ Binv, BicgVecs V, const double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  int64_t e, t;
+  int a;
+  const bool act = face_slot(F, e, a, t);
+  if (act) V.p[t] = V.r[t] + scal[B_BETA] * (V.p[t] - scal[B_OMEGA] * V.v[t]);
+  __syncthreads();
+  if (act) V.ph[t] = bj_apply<double>(Binv, V.p, e, a, F.d2);
+}
+
+// v = H ph;  alpha = rho / (rhat . v)
+__global__ void bicg_v_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs V, double* red,
+                              unsigned int* counter, double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  int64_t e, t;
+  int a;
+  double v[1] = {0.0};
+  if (face_slot(F, e, a, t)) {
+    const double vv = (F.ftype[e] != 1) ? face_apply<double>(C, V.ph, F, e, a) : 0.0;
+    V.v[t] = vv;
+    v[0] = V.rh[t] * vv;
+  }
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
+    if (out[0] == 0.0 || !isfinite(out[0])) {
+      scal[B_BAD] = 1.0;
+      scal[B_DONE] = 1.0;
+      scal[B_ALPHA] = 0.0;
+    } else {
+      scal[B_ALPHA] = scal[B_RHO] / out[0];
+    }
+  }
+}
+
+// s = r - alpha v;  sh = M^-1 s
+__global__ void bicg_s_kernel(FaceArgs F, const double* __restrict__ Binv, BicgVecs V, const double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  int64_t e, t;
+  int a;
+  const bool act = face_slot(F, e, a, t);
+  if (act) V.s[t] = V.r[t] - scal[B_ALPHA] * V.v[t];
+  __syncthreads();
+  if (act) V.sh[t] = bj_apply<double>(Binv, V.s, e, a, F.d2);
+}
+
+// t = H sh;  omega = (t.s) / (t.t)
+__global__ void bicg_t_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs V, double* red,
+                              unsigned int* counter, double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  int64_t e, t;
+  int a;
+  double v[2] = {0.0, 0.0};
+  if (face_slot(F, e, a, t)) {
+    const double tv = (F.ftype[e] != 1) ? face_apply<double>(C, V.sh, F, e, a) : 0.0;
+    V.t[t] = tv;
+    v[0] = tv * V.s[t];
+    v[1] = tv * tv;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) scal[B_OMEGA] = (out[1] > 0.0) ? out[0] / out[1] : 0.0;
+}
+
+// x += alpha ph + omega sh;  r = s - omega t;  rho' = rhat.r;  beta = (rho'/rho)(alpha/omega)
+__global__ void bicg_x_kernel(FaceArgs F, BicgVecs V, double* red, unsigned int* counter, double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  const double alpha = scal[B_ALPHA], omega = scal[B_OMEGA];
+  int64_t e, t;
+  int a;
+  double v[2] = {0.0, 0.0};
+  if (face_slot(F, e, a, t)) {
+    V.x[t] += alpha * V.ph[t] + omega * V.sh[t];
+    const double rv = V.s[t] - omega * V.t[t];
+    V.r[t] = rv;
+    v[0] = V.rh[t] * rv;
+    v[1] = rv * rv;
+  }
+  double out[2];
+  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
+    const double rho_old = scal[B_RHO];
+    scal[B_BETA] = (out[0] / rho_old) * (alpha / omega);
+    scal[B_RHO] = out[0];
+    scal[B_RR] = out[1];
+    scal[B_ITERS] += 1.0;
+    if (omega == 0.0 || out[0] == 0.0 || !isfinite(out[1])) {
+      scal[B_BAD] = (out[1] <= scal[B_TOL2]) ? 0.0 : 1.0;
+      scal[B_DONE] = 1.0;
+    }
+    if (out[1] <= scal[B_TOL2] || scal[B_ITERS] >= scal[B_MAXIT]) scal[B_DONE] = 1.0;
+  }
+}
+
 // ------------------------------------------------------------------ host side
 static FaceArgs face_args(hdg_mesh* M) {
   FaceArgs F;
@@ -398,6 +555,9 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
     HDG_CUDA_TRY(cudaMemsetAsync(M->d_counter, 0, sizeof(unsigned int) * 4, M->stream));
     M->red_blocks = nb;
   }
+  if (M->beta_q && !M->d_bicg) {
+    HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * nv));
+  }
   if (mixed && !M->d_C32) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_C32, sizeof(float) * M->nelt * M->tab.m * M->tab.m));
     HDG_CUDA_TRY(cudaMalloc(&M->d_BJ32, sizeof(float) * M->nfc * M->tab.d2 * M->tab.d2));
@@ -421,7 +581,8 @@ static int prepare_rhs(hdg_mesh* M) {
   bdata_kernel<<<nb, kNT, 0, M->stream>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf,
                                           M->uD, M->gN, xD, phiN);
   rhs_kernel<<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter, M->d_scal);
-  bj_kernel<double><<<(unsigned)((M->nfc + 63) / 64), 64, 0, M->stream>>>(F, M->d_C, M->d_BJ, M->d_status);
+  bj_kernel<double><<<(unsigned)((M->nfc + 63) / 64), 64, 0, M->stream>>>(F, M->d_C, M->d_BJ, M->d_status,
+                                                                        M->beta_q != nullptr);
   M->launches += 3;
   HDG_CUDA_TRY(cudaGetLastError());
   double bb;
@@ -479,6 +640,49 @@ static int pcg_run(hdg_mesh* M, const T* C, const T* Binv, const T* rhs, T* x, b
   return HDG_OK;
 }
 
+static int bicg_run(hdg_mesh* M, bool have_x, double tol2, int maxit, int* iters, bool* bad) {
+  FaceArgs F = face_args(M);
+  const int nb = nblocks(M);
+  const int64_t nv = M->nfc * M->tab.d2;
+  BicgVecs V{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + nv, M->d_bicg + 2 * nv,
+             M->d_bicg + 3 * nv};
+  double* scal = M->d_scal;
+  double hs[B_NSCAL] = {0};
+  hs[B_TOL2] = tol2;
+  hs[B_MAXIT] = (double)maxit;
+  HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
+  bicg_init_kernel<<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, V, have_x, M->d_red, M->d_counter, scal);
+  M->launches++;
+  HDG_CUDA_TRY(cudaGetLastError());
+  if (!M->graph_bicg) {
+    if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = M->cap_stream;
+    cudaGraph_t g;
+    HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < kGraphIters; ++it) {
+      bicg_p_kernel<<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
+      bicg_v_kernel<<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
+      bicg_s_kernel<<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
+      bicg_t_kernel<<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
+      bicg_x_kernel<<<nb, kNT, 0, cs>>>(F, V, M->d_red, M->d_counter, scal);
+    }
+    HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+    HDG_CUDA_TRY(cudaGraphInstantiate(&M->graph_bicg, g, 0));
+    cudaGraphDestroy(g);
+  }
+  double hv[B_NSCAL];
+  for (;;) {
+    HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+    HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+    if (hv[B_DONE] != 0.0) break;
+    HDG_CUDA_TRY(cudaGraphLaunch(M->graph_bicg, M->stream));
+    M->launches += 5 * kGraphIters;
+  }
+  *iters = (int)hv[B_ITERS];
+  *bad = hv[B_BAD] != 0.0;
+  return HDG_OK;
+}
+
 // ||b - H x||_2 over the free dofs in FP64, r returned in M->d_r.
 static int true_residual(hdg_mesh* M, const double* x, double* r, double* rnorm) {
   FaceArgs F = face_args(M);
@@ -525,7 +729,22 @@ int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double
   bool converged = false, bad = false;
   double rnorm = 0.0;
   if (x0) HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
-  if (!mixed) {
+  if (M->beta_q) {
+    // non-symmetric trace matrix (convection): block-Jacobi BiCGStab in FP64
+    if (mixed) return fail(HDG_ERR_UNSUPPORTED, "the mixed-precision solve is for symmetric (beta = 0) problems");
+    bool have_x = x0 != nullptr;
+    for (int pass = 0; pass < 3 && !converged && total_it < maxit; ++pass) {
+      int it;
+      rc = bicg_run(M, have_x, tol * tol, maxit - total_it, &it, &bad);
+      if (rc) return rc;
+      total_it += it;
+      rc = true_residual(M, M->d_x, M->d_q, &rnorm);
+      if (rc) return rc;
+      converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
+      have_x = true;  // restart from the current iterate if the recursive residual drifted
+      if (bad && !converged) bad = false;
+    }
+  } else if (!mixed) {
     int it;
     double rr;
     rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, x0 != nullptr, M->d_r, M->d_z, M->d_p, M->d_q,
