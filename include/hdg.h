@@ -150,6 +150,22 @@ int hdg_get_condensed(const hdg_mesh* mesh, double* C, double* Cf);
 int hdg_solve_trace(hdg_mesh* mesh, int precision, double rtol, int maxit, const double* x0,
                     double* uhat, int* iters, double* relres);
 
+/* Same solve as hdg_solve_trace with precision HDG_FP64, for callers that cannot allocate
+ * device memory when they solve (an application that reserves its whole device-memory budget
+ * up front, or a pool-managed framework that forbids allocations after warm-up; cudaMalloc
+ * would also synchronise the device).  The paper has no counterpart: this is a deployment
+ * variant.  It allocates nothing: every scratch buffer (right-hand side, boundary data,
+ * block-Jacobi inverses, Krylov vectors, reduction partials) lives in one file-scope static
+ * device array of 11.6 MiB that each GPU loading the library holds until the process exits.
+ *   Limit: nfc * d2 <= 65,536 trace unknowns; larger meshes return HDG_ERR_ARG.
+ *   The first call on a device looks up the array's address (with that device current);
+ *   make that first call before any stream capture.
+ *   All calls share the array and leave their contents in it; the call clears what must
+ *   start at zero.  Calls whose GPU work overlaps (other streams or host threads) race.
+ * Arguments, outputs and errors as for hdg_solve_trace (x0, uhat device f64 [nfc][d2]).  */
+int hdg_solve_trace_noalloc(hdg_mesh* mesh, double rtol, int maxit, const double* x0,
+                            double* uhat, int* iters, double* relres);
+
 /* Residual check (tests): r = b - H x over the free dofs, device f64 [nfc][d2]; returns
  * ||r||_2 and ||b||_2 through the host pointers.                                          */
 int hdg_trace_residual(hdg_mesh* mesh, const double* x, double* r, double* rnorm, double* bnorm);

@@ -45,6 +45,7 @@ _SIGS = {
     "hdg_get_condensed": [P, P, P],
     "hdg_solve_trace": [P, C.c_int, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_trace_residual": [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "hdg_solve_trace_noalloc": [P, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_recover": [P, P, P, P],
     "hdg_postprocess": [P, P, P, P],
     "hdg_last_error": [C.c_char_p, C.c_size_t],
