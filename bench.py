@@ -200,7 +200,7 @@ def oracle_baseline(sample_elems, steps=1, warmup=0):
 def run_gpu(args, rank, world, local_rank):
     import torch
 
-    from paper_1305_1489_gb300 import HDG_FP64, HDG_MIXED_FP32, HDGMesh, build
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, HDG_MIXED_FP32, HDGMesh, build
     from workloads import boundary_faces, get_problem, kuhn_cube
 
     if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1305_1489_gb300", "libhdg.so")):
@@ -227,6 +227,8 @@ def run_gpu(args, rank, world, local_rank):
     dv = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in host.items()}
     M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
     M.set_boundary_data(dv["uD"], dv["gN"])
+    M.set_inner_tolerance(args.inner_rtol)
+    asm_prec = HDG_DF32 if args.asm == "df32" else HDG_FP64
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def ev():
@@ -236,7 +238,7 @@ def run_gpu(args, rank, world, local_rank):
         flush.fill_(1.0)
         e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
         e0.record(stream)
-        M.assemble_condense()
+        M.assemble_condense(asm_prec)
         e1.record(stream)
         uhat, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
         e2.record(stream)
@@ -317,7 +319,7 @@ def run_gpu(args, rank, world, local_rank):
             dv[k_].copy_(v, non_blocking=True)
         M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
         M.set_boundary_data(dv["uD"], dv["gN"])
-        M.assemble_condense()
+        M.assemble_condense(asm_prec)
         b.record(stream)
         uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
         cc.record(stream)
@@ -366,11 +368,11 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-def profile_k1(s_sub, launches=2):
+def profile_k1(s_sub, launches=2, asm="df32"):
     """Small case for a full ncu capture of K1: the same problem on an s^3 x 6 mesh."""
     import torch
 
-    from paper_1305_1489_gb300 import HDGMesh, build
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, HDGMesh, build
     from workloads import boundary_faces, get_problem, kuhn_cube
 
     build()
@@ -382,9 +384,9 @@ def profile_k1(s_sub, launches=2):
     dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     M.set_coefficients(dv(prob.kappa(X, Y, Z)), dv(prob.c(X, Y, Z)), dv(prob.f(X, Y, Z)))
     for _ in range(launches):
-        M.assemble_condense()
+        M.assemble_condense(HDG_DF32 if asm == "df32" else HDG_FP64)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_k1": {"nelt": M.nelt, "launches": launches}}))
+    print(json.dumps({"profile_k1": {"nelt": M.nelt, "launches": launches, "asm": asm}}))
 
 
 def run_reference(args, rank):
@@ -411,10 +413,13 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=12288, help="oracle elements per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true", help="timed steps only (profiling)")
+    ap.add_argument("--asm", default="df32", choices=["df32", "fp64"],
+                    help="assembly arithmetic: double-float on the FP32 pipe or native FP64")
+    ap.add_argument("--inner-rtol", type=float, default=1e-6, help="FP32 inner solve tolerance")
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
     args = ap.parse_args()
     if args.profile_k1:
-        profile_k1(args.profile_k1)
+        profile_k1(args.profile_k1, asm=args.asm)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -52,7 +52,9 @@ typedef enum {
 
 typedef enum {
   HDG_FP64 = 0,        /* every operation in IEEE double                                   */
-  HDG_MIXED_FP32 = 1   /* FP32 inner solve with FP64 residuals and refinement (solve only) */
+  HDG_MIXED_FP32 = 1,  /* FP32 inner solve with FP64 residuals and refinement (solve only) */
+  HDG_DF32 = 2         /* assembly only: double-float arithmetic (pairs of FP32, ~48-bit
+                          significand) on the FP32 pipe; results stored as FP64           */
 } hdg_precision;
 
 typedef struct hdg_mesh hdg_mesh;
@@ -128,8 +130,9 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
 
 /* Per-element assembly of the local blocks and static condensation (Sections 3-5):
  * C^K = A3 A1^-1 A2 + tauDD (eq. 5.5), C_f^K = A3 A1^-1 A_f (eq. 5.6), and the operators of
- * the local recovery (eq. 5.3), into library-owned device memory.  FP64 throughout.
- * precision must be HDG_FP64.  Asynchronous; synchronises only to report
+ * the local recovery (eq. 5.3), into library-owned device memory.
+ * precision: HDG_FP64 (native FP64) or HDG_DF32 (double-float on the FP32 pipe, FP64-level
+ * accuracy; reaction-diffusion only).  Synchronises to report
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
 
@@ -165,6 +168,10 @@ int hdg_solve_trace(hdg_mesh* mesh, int precision, double rtol, int maxit, const
  * Arguments, outputs and errors as for hdg_solve_trace (x0, uhat device f64 [nfc][d2]).  */
 int hdg_solve_trace_noalloc(hdg_mesh* mesh, double rtol, int maxit, const double* x0,
                             double* uhat, int* iters, double* relres);
+
+/* Relative tolerance of each FP32 inner solve of the HDG_MIXED_FP32 trace solve (default
+ * 1e-4): every outer FP64 refinement step asks the inner PCG for this residual reduction.  */
+int hdg_set_inner_tolerance(hdg_mesh* mesh, double rtol);
 
 /* Residual check (tests): r = b - H x over the free dofs, device f64 [nfc][d2]; returns
  * ||r||_2 and ||b||_2 through the host pointers.                                          */

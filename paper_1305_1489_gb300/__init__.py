@@ -20,9 +20,9 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import HDG_FP64, HDG_MIXED_FP32, HDGError  # noqa: F401
+from ._lib import HDG_DF32, HDG_FP64, HDG_MIXED_FP32, HDGError  # noqa: F401
 
-__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "build", "load_library"]
+__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "HDG_DF32", "build", "load_library"]
 
 
 def build(**kw):
@@ -123,6 +123,10 @@ def hdg_solve_trace(h, precision, rtol, maxit, x0, uhat):
     return code, it.value, rr.value
 
 
+def hdg_set_inner_tolerance(h, rtol):
+    return _lib.check(_lib.load().hdg_set_inner_tolerance(h, float(rtol)))
+
+
 def hdg_trace_residual(h, x, r):
     rn = C.c_double(0.0)
     bn = C.c_double(0.0)
@@ -218,8 +222,8 @@ class HDGMesh:
         self._keep.update(uD=uD, gN=gN)
         hdg_set_boundary_data(self._h, uD, gN)
 
-    def assemble_condense(self):
-        hdg_assemble_condense(self._h, HDG_FP64)
+    def assemble_condense(self, precision=HDG_FP64):
+        hdg_assemble_condense(self._h, precision)
 
     def condensed(self):
         Cm = self._empty(self.nelt, self.m, self.m)
@@ -235,6 +239,9 @@ class HDGMesh:
         if code != 0 and raise_on_fail:
             raise HDGError(code, _lib.last_error())
         return uhat, it, rr
+
+    def set_inner_tolerance(self, rtol):
+        hdg_set_inner_tolerance(self._h, rtol)
 
     def residual(self, x):
         r = self._empty(self.nfc, self.d2)

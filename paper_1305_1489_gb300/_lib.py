@@ -8,6 +8,7 @@ LIB_PATH = os.path.join(_HERE, "libhdg.so")
 
 HDG_FP64 = 0
 HDG_MIXED_FP32 = 1
+HDG_DF32 = 2
 
 STATUS = {
     0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_ORIENTATION", 3: "HDG_ERR_NONCONFORMING",
@@ -45,6 +46,7 @@ _SIGS = {
     "hdg_get_condensed": [P, P, P],
     "hdg_solve_trace": [P, C.c_int, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_trace_residual": [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "hdg_set_inner_tolerance": [P, C.c_double],
     "hdg_solve_trace_noalloc": [P, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_recover": [P, P, P, P],
     "hdg_postprocess": [P, P, P, P],

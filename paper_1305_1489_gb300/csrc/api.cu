@@ -38,6 +38,18 @@ static std::vector<int16_t> pair_list(int n, int first) {
   return v;
 }
 
+// split each double into the float pair hi + lo (hi = nearest float, lo = nearest float of
+// the remainder) for the double-float kernels
+static std::vector<float> split_df(const std::vector<double>& v) {
+  std::vector<float> o(2 * v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float hi = (float)v[i];
+    o[2 * i] = hi;
+    o[2 * i + 1] = (float)(v[i] - (double)hi);
+  }
+  return o;
+}
+
 static int upload_tables(hdg_mesh* M) {
   const Tables& T = M->tab;
   DevTables& D = M->dt;
@@ -48,6 +60,9 @@ static int upload_tables(hdg_mesh* M) {
       (rc = upload(&D.D, T.D)) || (rc = upload(&D.P1, T.P1)) || (rc = upload(&D.G1, T.G1)) ||
       (rc = upload(&D.Shat1, T.Shat1)) || (rc = upload(&D.Pl, T.Pl)) || (rc = upload(&D.Dmu, T.Dmu)) ||
       (rc = upload(&D.face_pts, T.face_pts)))
+    return rc;
+  if ((rc = upload(&D.P_df, split_df(T.P))) || (rc = upload(&D.Chat_df, split_df(T.Chat))) ||
+      (rc = upload(&D.S_df, split_df(T.S))) || (rc = upload(&D.E_df, split_df(T.E))))
     return rc;
   if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
       (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
@@ -61,7 +76,8 @@ static void release(hdg_mesh* M) {
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
                   M->d_p32, M->d_q32, M->dt.P, M->dt.Pd, M->dt.Chat, M->dt.S, M->dt.E, M->dt.vol_w, M->dt.lam,
                   M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
-                  M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg};
+                  M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
+                  M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
@@ -209,10 +225,13 @@ int hdg_set_boundary_data(hdg_mesh* M, const double* uD, const double* gN) {
 int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
-  if (precision != HDG_FP64) return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64");
+  if (precision != HDG_FP64 && precision != HDG_DF32)
+    return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64 or HDG_DF32");
   if (M->beta_q && !M->beta_f) return fail(HDG_ERR_STATE, "convection set without hdg_set_face_convection");
+  if (M->beta_q && precision == HDG_DF32)
+    return fail(HDG_ERR_UNSUPPORTED, "the double-float assembly covers reaction-diffusion (beta = 0)");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
-  HDG_CUDA_TRY(launch_assemble(M));
+  HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   M->assembled = true;
   M->rhs_ready = false;
   return check_status(M);
@@ -222,8 +241,8 @@ int hdg_get_condensed(const hdg_mesh* M, double* C, double* Cf) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (!M->assembled) return fail(HDG_ERR_STATE, "not assembled");
   const int m = M->tab.m;
-  if (C && M->beta_q) HDG_CUDA_TRY(launch_transpose_blocks(const_cast<hdg_mesh*>(M), M->d_C, C));  // stored transposed
-  else if (C) HDG_CUDA_TRY(cudaMemcpyAsync(C, M->d_C, sizeof(double) * M->nelt * m * m, cudaMemcpyDeviceToDevice, M->stream));
+  (void)m;
+  if (C) HDG_CUDA_TRY(launch_unblock(const_cast<hdg_mesh*>(M), M->d_C, C));  // stored face-blocked
   if (Cf) HDG_CUDA_TRY(cudaMemcpyAsync(Cf, M->d_Cf, sizeof(double) * M->nelt * m, cudaMemcpyDeviceToDevice, M->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
   return HDG_OK;
@@ -235,6 +254,12 @@ int hdg_solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const do
   int rc = solve_trace(M, precision, rtol, maxit, x0, uhat, iters, relres);
   if (rc == HDG_OK) rc = check_status(M);
   return rc;
+}
+
+int hdg_set_inner_tolerance(hdg_mesh* M, double rtol) {
+  if (!M || !(rtol > 0) || !(rtol < 1)) return fail(HDG_ERR_ARG, "inner tolerance must be in (0, 1)");
+  M->inner_rtol = rtol;
+  return HDG_OK;
 }
 
 int hdg_trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {

@@ -26,7 +26,6 @@
 //   G_col = G - alphaDP;  S_u = L U;  H_col = L^-1 G_col^T,  H_row = U^-T G^T;
 //   C^K = (n_l . n_l') o (V^T V) - H_row^T H_col + tauDD - alphaDD,  C_f = H_row^T L^-1 f;
 //   [R_u | r_u] = U^-1 [H_col | L^-1 f].
-// C^K is then stored transposed (the trace operator reads C^K rows as stored columns).
 #include "device_common.cuh"
 #include "hdg_internal.h"
 
@@ -368,14 +367,12 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
 #pragma unroll
     for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
   }
+  // C^K face-blocked: Cout[l][s][a] = C^K[l d2 + a][s] (the row block of local face l is
+  // contiguous; the trace operator reads it with unit stride)
   double* Cout = A.C + Ke * (int64_t)(m * m);
-  if constexpr (CONV) {
-    for (int t = tid; t < m * m; t += NT) {  // stored transposed: Cout[s][r] = C^K[r][s]
-      const int sidx = t / m, r = t - sidx * m;
-      Cout[t] = Cs[r * m + sidx];
-    }
-  } else {
-    for (int t = tid; t < m * m; t += NT) Cout[t] = Cs[t];
+  for (int t = tid; t < m * m; t += NT) {
+    const int fl = t / (m * d2), rem = t - fl * m * d2, sidx = rem / d2, a = rem - sidx * d2;
+    Cout[t] = Cs[(fl * d2 + a) * m + sidx];
   }
   __syncthreads();
 

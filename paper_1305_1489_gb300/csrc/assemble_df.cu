@@ -1,0 +1,387 @@
+// K1 in double-float arithmetic (precision HDG_DF32): the same per-element assembly and static
+// condensation as assemble.cu (reaction-diffusion path), with every operation carried out as
+// double-float on the FP32 pipe (device_df.cuh) instead of native FP64.  On GB300 the FP64
+// pipe runs at 1/63 of the FP32 rate, so the FP64-accurate condensation is faster this way.
+// Inputs (kappa, c, f in FP64) are split into double-float once per node; outputs (C^K, C_f^K,
+// the recovery record) are written back as FP64 in the same layouts as the FP64 kernel, so
+// the trace solve, recovery and postprocess are unchanged.  Algorithm (see assemble.cu):
+//   L L^T = M_{kappa^-1};  W_* = L^-1 C_*^T;  V = L^-1 E^T;  S_u = M_c + tauPP + sum W^T W;
+//   G = diag(T) E + sum_* diag(n_*) V^T W_*;  L_s L_s^T = S_u;  [H | h] = L_s^-1 [G^T | f];
+//   C^K = (n_l . n_l') o (V^T V) - H^T H + tauDD;  C_f^K = H^T h;
+//   recovery: [R_u | r_u] = L_s^-T [H | h],  Y = L^-T V,  MC_* = L^-T W_*.
+#include "device_common.cuh"
+#include "device_df.cuh"
+#include "hdg_internal.h"
+
+namespace hdg {
+
+struct AsmDfArgs {
+  const double* vx;
+  const int32_t* perm;
+  const double *kappa, *c, *f, *tau;
+  const df *P, *Chat, *S, *E;  // double-float copies of the reference tables
+  const double* w;
+  const int16_t *pairs_n, *pairs_m;
+  double *C, *Cf, *rec;
+  int32_t* status;
+  int64_t nelt;
+};
+
+template <int K>
+struct AsmDfSmem {
+  using D = Dims<K>;
+  static constexpr int n = D::n, m = D::m, nq = D::nq;
+  static constexpr int o_kw = 0, o_cw = o_kw + nq, o_fw = o_cw + nq;
+  static constexpr int o_M = o_fw + nq;
+  static constexpr int o_S = o_M + n * n;
+  static constexpr int o_W = o_S + n * n;
+  static constexpr int o_V = o_W + 3 * n * n;
+  static constexpr int o_Wt = o_V + n * m;
+  static constexpr int o_G = o_Wt + 4 * n * n;
+  static constexpr int o_C = o_G + n * (m + 1);
+  static constexpr int total = o_C + m * m;
+  static constexpr size_t bytes = sizeof(df) * total;
+};
+
+__device__ __forceinline__ df shfl_xor_df(df x, int o) {
+  return df_make(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
+}
+
+// Cholesky by one warp, double-float (left-looking by columns).  invd receives 1/L_jj.
+template <int N>
+__device__ __forceinline__ bool warp_cholesky_df(df* A, df* invd, int lane) {
+  bool ok = true;
+  for (int j = 0; j < N; ++j) {
+    dacc s = dacc_zero();
+    for (int l = lane; l < j; l += 32) dacc_mac(s, A[j * N + l], A[j * N + l]);
+    df sv = dacc_result(s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sv = df_add(sv, shfl_xor_df(sv, o));
+    const double dd = df_to_double(A[j * N + j]) - df_to_double(sv);
+    ok = ok && (dd > 0.0);
+    const double d = sqrt(dd);
+    const df dv = df_from_double(d), id = df_from_double(1.0 / d);
+    __syncwarp();
+    if (lane == 0) {
+      A[j * N + j] = dv;
+      invd[j] = id;
+    }
+    for (int i = j + 1 + lane; i < N; i += 32) {
+      dacc t = dacc_from(A[i * N + j]);
+      for (int l = 0; l < j; ++l) dacc_msub(t, A[i * N + l], A[j * N + l]);
+      A[i * N + j] = df_mul(dacc_result(t), id);
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
+template <int N>
+__device__ __forceinline__ void fwd_subst_df(const df* __restrict__ L, const df* invd, df* x) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    dacc s = dacc_from(x[l]);
+#pragma unroll
+    for (int i = 0; i < l; ++i) dacc_msub(s, L[l * N + i], x[i]);
+    x[l] = df_mul(dacc_result(s), invd[l]);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void bwd_subst_df(const df* __restrict__ L, const df* invd, df* x) {
+#pragma unroll
+  for (int l = N - 1; l >= 0; --l) {
+    dacc s = dacc_from(x[l]);
+#pragma unroll
+    for (int i = l + 1; i < N; ++i) dacc_msub(s, L[i * N + l], x[i]);
+    x[l] = df_mul(dacc_result(s), invd[l]);
+  }
+}
+
+__device__ __forceinline__ df ldg_df(const df* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df_make(v.x, v.y);
+}
+
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) assemble_df_kernel(AsmDfArgs A) {
+  using D = Dims<K>;
+  using SM = AsmDfSmem<K>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq;
+  constexpr int NP = n * (n + 1) / 2, MP = m * (m + 1) / 2;
+  extern __shared__ df smd[];
+  df* kw = smd + SM::o_kw;
+  df* cw = smd + SM::o_cw;
+  df* fw = smd + SM::o_fw;
+  df* Ms = smd + SM::o_M;
+  df* Ss = smd + SM::o_S;
+  df* W = smd + SM::o_W;
+  df* V = smd + SM::o_V;
+  df* Wt = smd + SM::o_Wt;
+  df* Gt = smd + SM::o_G;
+  df* Cs = smd + SM::o_C;
+  __shared__ df s_a[3][3], s_nrm[4][3], s_T[4], s_nn[4][4];
+  __shared__ double s_vol;
+  __shared__ df invdM[n], invdS[n];
+  __shared__ int s_perm[4];
+  __shared__ int s_bad, s_coef;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int64_t Ke = blockIdx.x;
+
+  if (tid == 0) {
+    Geo g;
+    element_geometry(A.vx, A.nelt, Ke, g);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) s_a[i][j] = df_from_double(g.a[i][j]);
+    for (int l = 0; l < 4; ++l) {
+      for (int d = 0; d < 3; ++d) s_nrm[l][d] = df_from_double(g.nrm[l][d]);
+      const double tau = A.tau ? A.tau[Ke * 4 + l] : 1.0;
+      s_T[l] = df_from_double(tau * g.area[l]);  // T_l = tau_l |e_l|, eq. 4.22
+      s_perm[l] = A.perm[Ke * 4 + l] - 1;
+    }
+    for (int l = 0; l < 4; ++l)
+      for (int l2 = 0; l2 < 4; ++l2)
+        s_nn[l][l2] = df_from_double(g.nrm[l][0] * g.nrm[l2][0] + g.nrm[l][1] * g.nrm[l2][1] +
+                                     g.nrm[l][2] * g.nrm[l2][2]);
+    s_vol = g.vol;
+    s_bad = 0;
+    s_coef = 0;
+  }
+  __syncthreads();
+
+  for (int q = tid; q < nq; q += NT) {
+    const double kap = A.kappa[Ke * nq + q], cc = A.c[Ke * nq + q], ff = A.f[Ke * nq + q];
+    if (!(kap > 0.0) || !(cc >= 0.0) || !isfinite(kap) || !isfinite(cc) || !isfinite(ff)) s_coef = 1;
+    const double vw = s_vol * A.w[q];
+    kw[q] = df_from_double(vw / kap);
+    cw[q] = df_from_double(vw * cc);
+    fw[q] = df_from_double(vw * ff);
+  }
+  __syncthreads();
+
+  for (int t = tid; t < NP; t += NT) {
+    const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
+    dacc s1 = dacc_zero(), s2 = dacc_zero();
+#pragma unroll 5
+    for (int q = 0; q < nq; ++q) {
+      const df pp = df_mul(ldg_df(A.P + q * n + i), ldg_df(A.P + q * n + j));
+      dacc_mac(s1, kw[q], pp);
+      dacc_mac(s2, cw[q], pp);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) dacc_mac(s2, s_T[l], ldg_df(A.S + (l * n + i) * n + j));
+    const df v1 = dacc_result(s1), v2 = dacc_result(s2);
+    Ms[i * n + j] = v1;
+    Ms[j * n + i] = v1;
+    Ss[i * n + j] = v2;
+    Ss[j * n + i] = v2;
+  }
+  for (int i = tid; i < n; i += NT) {
+    dacc s = dacc_zero();
+    for (int q = 0; q < nq; ++q) dacc_mac(s, fw[q], ldg_df(A.P + q * n + i));
+    Gt[i * (m + 1) + m] = dacc_result(s);
+  }
+  for (int t = tid; t < 3 * n * n; t += NT) {
+    const int st = t / (n * n), rem = t - st * n * n, l = rem / n, cidx = rem - l * n;
+    dacc s = dacc_zero();
+#pragma unroll
+    for (int h = 0; h < 3; ++h) dacc_mac(s, s_a[st][h], ldg_df(A.Chat + (h * n + cidx) * n + l));
+    W[t] = dacc_result(s);
+  }
+  for (int t = tid; t < n * m; t += NT) {
+    const int l = t / m, r = t - l * m, fl = r / d2, a = r - fl * d2;
+    V[t] = ldg_df(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + l);
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    const bool ok = warp_cholesky_df<n>(Ms, invdM, lane);
+    if (!ok && lane == 0) s_bad = 1;
+  }
+  __syncthreads();
+
+  for (int t = tid; t < 3 * n + m; t += NT) {
+    df* base;
+    int col, stride;
+    if (t < 3 * n) {
+      base = W + (t / n) * n * n;
+      col = t % n;
+      stride = n;
+    } else {
+      base = V;
+      col = t - 3 * n;
+      stride = m;
+    }
+    df x[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = base[l * stride + col];
+    fwd_subst_df<n>(Ms, invdM, x);
+#pragma unroll
+    for (int l = 0; l < n; ++l) base[l * stride + col] = x[l];
+  }
+  __syncthreads();
+
+  for (int t = tid; t < NP; t += NT) {
+    const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
+    dacc s = dacc_from(Ss[i * n + j]);
+#pragma unroll
+    for (int st = 0; st < 3; ++st)
+#pragma unroll 4
+      for (int l = 0; l < n; ++l) dacc_mac(s, W[st * n * n + l * n + i], W[st * n * n + l * n + j]);
+    const df v = dacc_result(s);
+    Ss[i * n + j] = v;
+    Ss[j * n + i] = v;
+  }
+  for (int t = tid; t < 4 * n * n; t += NT) {
+    const int fl = t / (n * n), rem = t - fl * n * n;
+    dacc s = dacc_zero();
+#pragma unroll
+    for (int st = 0; st < 3; ++st) dacc_mac(s, s_nrm[fl][st], W[st * n * n + rem]);
+    Wt[t] = dacc_result(s);
+  }
+  for (int t = tid; t < MP; t += NT) {
+    const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
+    const int fr = r / d2, fs = s / d2;
+    dacc b = dacc_zero();
+#pragma unroll 4
+    for (int l = 0; l < n; ++l) dacc_mac(b, V[l * m + r], V[l * m + s]);
+    df cv = df_mul(s_nn[fr][fs], dacc_result(b));
+    if (r == s) cv = df_add(cv, s_T[fr]);
+    Cs[r * m + s] = cv;
+    Cs[s * m + r] = cv;
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    const bool ok = warp_cholesky_df<n>(Ss, invdS, lane);
+    if (!ok && lane == 0) s_bad = 1;
+  } else {
+    for (int t = tid - 32; t < n * m; t += NT - 32) {
+      const int j = t / m, r = t - j * m, fl = r / d2, a = r - fl * d2;
+      dacc g = dacc_zero();
+      dacc_mac(g, s_T[fl], ldg_df(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + j));
+      const df* wt = Wt + fl * n * n;
+#pragma unroll 4
+      for (int l = 0; l < n; ++l) dacc_mac(g, V[l * m + r], wt[l * n + j]);
+      Gt[j * (m + 1) + r] = dacc_result(g);
+    }
+  }
+  __syncthreads();
+
+  for (int t = tid; t < (m + 1) + m + 3 * n; t += NT) {
+    df x[n];
+    if (t < m + 1) {
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
+      fwd_subst_df<n>(Ss, invdS, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+    } else if (t < 2 * m + 1) {
+      const int col = t - (m + 1);
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = V[l * m + col];
+      bwd_subst_df<n>(Ms, invdM, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
+    } else {
+      const int tt = t - (2 * m + 1);
+      df* base = W + (tt / n) * n * n;
+      const int col = tt % n;
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = base[l * n + col];
+      bwd_subst_df<n>(Ms, invdM, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) base[l * n + col] = x[l];
+    }
+  }
+  __syncthreads();
+
+  for (int t = tid; t < MP; t += NT) {
+    const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
+    dacc hh = dacc_from(Cs[r * m + s]);
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) dacc_msub(hh, Gt[j * (m + 1) + r], Gt[j * (m + 1) + s]);
+    const df v = dacc_result(hh);
+    Cs[r * m + s] = v;
+    Cs[s * m + r] = v;
+  }
+  for (int r = tid; r < m; r += NT) {
+    dacc s = dacc_zero();
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) dacc_mac(s, Gt[j * (m + 1) + r], Gt[j * (m + 1) + m]);
+    A.Cf[Ke * m + r] = df_to_double(dacc_result(s));
+  }
+  __syncthreads();
+
+  for (int t = tid; t < m + 1; t += NT) {
+    df x[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
+    bwd_subst_df<n>(Ss, invdS, x);
+#pragma unroll
+    for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+  }
+  double* Cout = A.C + Ke * (int64_t)(m * m);  // face-blocked, as in assemble.cu
+  for (int t = tid; t < m * m; t += NT) {
+    const int fl = t / (m * d2), rem = t - fl * m * d2, sidx = rem / d2, a = rem - sidx * d2;
+    Cout[t] = df_to_double(Cs[(fl * d2 + a) * m + sidx]);
+  }
+  __syncthreads();
+
+  double* R = A.rec + Ke * (int64_t)D::rec;
+  for (int t = tid; t < n * (m + 1); t += NT) R[t] = df_to_double(Gt[t]);
+  R += n * (m + 1);
+  for (int t = tid; t < n * m; t += NT) R[t] = df_to_double(V[t]);
+  R += n * m;
+  for (int t = tid; t < 3 * n * n; t += NT) R[t] = df_to_double(W[t]);
+  R += 3 * n * n;
+  if (tid < 12) R[tid] = df_to_double(s_nrm[tid / 3][tid % 3]);
+  if (tid == 0) {
+    if (s_bad) atomicAdd(A.status + 0, 1);
+    if (s_coef) atomicAdd(A.status + 1, 1);
+  }
+}
+
+template <int K>
+static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
+  constexpr int NT = (K >= 3) ? 256 : 128;
+  const size_t smem = AsmDfSmem<K>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(assemble_df_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  assemble_df_kernel<K, NT><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  M->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_df(hdg_mesh* M) {
+  AsmDfArgs a;
+  a.vx = M->d_vx;
+  a.perm = M->d_perm;
+  a.kappa = M->kappa;
+  a.c = M->c;
+  a.f = M->f;
+  a.tau = M->tau;
+  a.P = reinterpret_cast<const df*>(M->dt.P_df);
+  a.Chat = reinterpret_cast<const df*>(M->dt.Chat_df);
+  a.S = reinterpret_cast<const df*>(M->dt.S_df);
+  a.E = reinterpret_cast<const df*>(M->dt.E_df);
+  a.w = M->dt.vol_w;
+  a.pairs_n = M->dt.pairs_n;
+  a.pairs_m = M->dt.pairs_m;
+  a.C = M->d_C;
+  a.Cf = M->d_Cf;
+  a.rec = M->d_rec;
+  a.status = M->d_status;
+  a.nelt = M->nelt;
+  switch (M->k) {
+    case 1: return launch_df_k<1>(M, a);
+    case 2: return launch_df_k<2>(M, a);
+    case 3: return launch_df_k<3>(M, a);
+    case 4: return launch_df_k<4>(M, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hdg

@@ -1,0 +1,122 @@
+// Double-float ("double-word") arithmetic on the FP32 pipe.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, carrying about
+// 48 significant bits.  GB300 executes FP32 at 63x its FP64 rate, so FP64-accurate dense
+// linear algebra runs faster as double-float than as native FP64.  Building blocks (all
+// exact, using the hardware FMA):
+//   two_sum      Knuth, TAOCP vol. 2, 4.2.2: s + e = a + b exactly
+//   fast_two_sum Dekker 1971: the same when |a| >= |b|
+//   two_prod     p + e = a * b exactly, e = fma(a, b, -p)
+// The product follows the double-word product of Joldes, Muller and Popescu ("Tight and
+// rigorous error bounds for basic building blocks of double-word arithmetic", ACM TOMS 2017,
+// DWTimesDW1); dot products accumulate the exact leading products with two_sum and collect
+// every low-order term in a second float, as in the compensated dot product of Ogita, Rump
+// and Oishi (SIAM J. Sci. Comput. 2005), then renormalise once.  Reciprocal and square root
+// are formed in FP64 from the double-float value (a handful per element).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hdg {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float hi, float lo) {
+  df r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df_make(s, e);
+}
+
+__device__ __forceinline__ df df_from_double(double d) {
+  const float hi = __double2float_rn(d);
+  return df_make(hi, __double2float_rn(d - (double)hi));
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ df df_neg(df x) { return df_make(-x.hi, -x.lo); }
+
+// x * y, relative error below 5 u^2 (u = 2^-24)
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+
+// x + y with two_sum on the leading parts (absolute error ~u^2 (|x| + |y|))
+__device__ __forceinline__ df df_add(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+
+// Unnormalised accumulator: hi collects the exact leading products by two_sum, lo every
+// rounding error and low-order product term.
+struct dacc {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dacc dacc_zero() {
+  dacc a;
+  a.hi = 0.f;
+  a.lo = 0.f;
+  return a;
+}
+
+__device__ __forceinline__ dacc dacc_from(df x) {
+  dacc a;
+  a.hi = x.hi;
+  a.lo = x.lo;
+  return a;
+}
+
+// acc += x * y
+__device__ __forceinline__ void dacc_mac(dacc& acc, df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+
+// acc -= x * y
+__device__ __forceinline__ void dacc_msub(dacc& acc, df x, df y) { dacc_mac(acc, df_neg(x), y); }
+
+// acc += x
+__device__ __forceinline__ void dacc_add(dacc& acc, df x) {
+  const float s = __fadd_rn(acc.hi, x.hi);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(x.hi, bb));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, x.lo));
+}
+
+__device__ __forceinline__ df dacc_result(const dacc& a) { return fast_two_sum(a.hi, a.lo); }
+
+// 1/x and sqrt(x) through FP64 (few per element)
+__device__ __forceinline__ df df_recip(df x) { return df_from_double(1.0 / df_to_double(x)); }
+__device__ __forceinline__ df df_sqrt(df x) { return df_from_double(sqrt(df_to_double(x))); }
+
+}  // namespace hdg

@@ -44,6 +44,8 @@ struct DevTables {
   double *P = nullptr, *Pd = nullptr, *Chat = nullptr, *S = nullptr, *E = nullptr;
   double *vol_w = nullptr, *lam = nullptr, *face_w = nullptr, *xi = nullptr, *D = nullptr;
   double *P1 = nullptr, *G1 = nullptr, *Shat1 = nullptr, *Pl = nullptr, *Dmu = nullptr, *face_pts = nullptr;
+  // double-float (hi, lo) float pairs of P, C_hat, S, E for the HDG_DF32 assembly
+  float *P_df = nullptr, *Chat_df = nullptr, *S_df = nullptr, *E_df = nullptr;
   int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
   int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices
   int16_t* pairs_n1 = nullptr;  // [(n1-1) n1 / 2][2] pairs of 1..n1-1 (postprocess)
@@ -81,7 +83,7 @@ struct hdg_mesh {
 
   // products of hdg_assemble_condense (library-owned)
   bool assembled = false;
-  double* d_C = nullptr;    // [nelt][m][m] condensed matrices C^K (eq. 5.5)
+  double* d_C = nullptr;    // [nelt][4][m][d2] condensed C^K, face-blocked (eq. 5.5)
   double* d_Cf = nullptr;   // [nelt][m]    C_f^K (eq. 5.6)
   double* d_rec = nullptr;  // [nelt][rec_stride] recovery operators (eq. 5.3)
   int64_t rec_stride = 0;
@@ -90,6 +92,7 @@ struct hdg_mesh {
   // trace-solve workspace (library-owned, allocated on first solve)
   bool rhs_ready = false;
   double bnorm = 0.0;  // ||b||_2 of the current right-hand side (host copy)
+  double inner_rtol = 1e-4;  // relative tolerance of each FP32 inner solve (mixed precision)
   double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr,
          *d_q = nullptr, *d_uhatD = nullptr, *d_BJ = nullptr, *d_red = nullptr,
          *d_scal = nullptr;
@@ -117,9 +120,10 @@ int fail(int code, const std::string& msg);
 cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* FX, double* FY,
                           double* FZ);
 cudaError_t launch_assemble(hdg_mesh* M);
+cudaError_t launch_assemble_df(hdg_mesh* M);
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u);
 cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double* Z);
-cudaError_t launch_transpose_blocks(hdg_mesh* M, const double* src, double* dst);
+cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst);
 cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar);
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0,
                 double* uhat, int* iters, double* relres);

@@ -106,11 +106,12 @@ __device__ __forceinline__ double apply(const Ops& F, const double* __restrict__
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
     const int64_t K = ow >> 2;
-    const double* Ck = F.C + K * (int64_t)(F.m * F.m) + (ow & 3) * F.d2 + a;
+    // face-blocked C^K: [K][l][s][a] = C^K[l d2 + a][s]
+    const double* Ck = F.C + K * (int64_t)(F.m * F.m) + (ow & 3) * (F.m * F.d2) + a;
     for (int fl = 0; fl < 4; ++fl) {
       const double* xs = x + (int64_t)F.fbe[4 * K + fl] * F.d2;
-      const double* cc = Ck + (int64_t)(fl * F.d2) * F.m;
-      for (int b = 0; b < F.d2; ++b) acc = fma(cc[(int64_t)b * F.m], xs[b], acc);
+      const double* cc = Ck + (int64_t)(fl * F.d2) * F.d2;
+      for (int b = 0; b < F.d2; ++b) acc = fma(cc[(int64_t)b * F.d2], xs[b], acc);
     }
   }
   return acc;
@@ -185,10 +186,11 @@ __global__ void k_bj(Ops F, double* Binv) {
   for (int o = 0; o < 2; ++o) {
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
-    const double* Ck = F.C + (int64_t)(ow >> 2) * m * m;
-    const int r0 = (ow & 3) * d2;
+    const int l = ow & 3;
+    // C^K[l d2 + i][l d2 + j] is stored at [K][l][l d2 + j][i]
+    const double* Cb = F.C + (int64_t)(ow >> 2) * m * m + l * (m * d2) + (l * d2) * d2;
     for (int i = 0; i < d2; ++i)
-      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Ck[(r0 + i) * m + r0 + j];
+      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Cb[j * d2 + i];
   }
   for (int j = 0; j < d2; ++j) {
     double s = A[j * d2 + j];

@@ -91,18 +91,20 @@ cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double*
   return cudaGetLastError();
 }
 
-__global__ void transpose_blocks_kernel(const double* __restrict__ src, double* __restrict__ dst, int64_t nelt, int m) {
+// face-blocked storage [K][l][s][a] -> row-major C^K [K][l d2 + a][s]
+__global__ void unblock_kernel(const double* __restrict__ src, double* __restrict__ dst, int64_t nelt, int m, int d2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nelt * m * m) return;
   const int64_t K = t / (m * m);
-  const int rem = (int)(t - K * m * m), i = rem / m, j = rem - i * m;
-  dst[t] = src[K * m * m + j * m + i];
+  const int rem = (int)(t - K * m * m), r = rem / m, s = rem - r * m;
+  const int l = r / d2, a = r - l * d2;
+  dst[t] = src[K * m * m + (l * m + s) * d2 + a];
 }
 
-cudaError_t launch_transpose_blocks(hdg_mesh* M, const double* src, double* dst) {
+cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst) {
   const int m = M->tab.m;
   const int64_t tot = M->nelt * m * m;
-  transpose_blocks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(src, dst, M->nelt, m);
+  unblock_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(src, dst, M->nelt, m, M->tab.d2);
   M->launches++;
   return cudaGetLastError();
 }

@@ -1,19 +1,20 @@
 // Trace system of Section 6: boundary data (eq. 6.3, 6.4), right-hand side F + G_N - H_{.,D} u_D
-// (eq. 6.5 with Dirichlet elimination), block-Jacobi preconditioned CG on the free faces, and
-// the FP32-inner / FP64-outer mixed-precision variant.
+// (eq. 6.5 with Dirichlet elimination), block-Jacobi preconditioned CG on the free faces (BiCGStab
+// when convection makes H non-symmetric), and the FP32-inner / FP64-outer mixed-precision variant.
 //
-// Operator: matrix-free, element by element, "face owner" form.  Each face e gathers the
-// row blocks of C^K belonging to it from its (at most two) elements:
+// Operator: matrix-free, element by element, "face owner" form.  Each face e gathers the row
+// blocks of C^K that belong to it from its (at most two) elements:
 //     (H x)_e = sum_{K owns e as local face l} (C^K x_dK)_{l-block}
-// which is the sparse assembly of Section 6 applied without forming H.  Every row of every
-// C^K is read once per product; there are no atomics and the result is deterministic.
-// C^K is symmetric for reaction-diffusion, so the l-block rows are read as columns, which
-// makes the d2 threads of one face read consecutive addresses.
+// which is the sparse assembly of Section 6 applied without forming H.  Every row of every C^K
+// is read once per product; there are no atomics and the result is deterministic.  K1 stores
+// C^K face-blocked, [K][l][s][a] = C^K[l d2 + a][s], so the row block of a face is one
+// contiguous array whose d2 columns are read by the face's d2 threads with unit stride.
 //
-// Scalars (alpha, beta, r.z, r.r) stay on the device: each reduction is finished by the last
-// block to arrive, summing per-block partials in block order (deterministic).  One PCG
-// iteration = three kernels; batches of iterations are captured in a CUDA graph and the host
-// reads the convergence flag after each replay.
+// Scheduling: every face kernel runs on a persistent grid (at most kMaxBlocks blocks, each
+// looping over tiles of kNT / d2 whole faces), so the deterministic last-block reductions sum
+// at most kMaxBlocks per-block partials.  Scalars (alpha, beta, r.z, r.r) stay on the device;
+// batches of iterations are captured in a CUDA graph and the host reads the convergence flag
+// after each replay.
 #include <cmath>
 #include <vector>
 
@@ -22,37 +23,45 @@
 
 namespace hdg {
 
-constexpr int kNT = 128;        // threads per block in the face kernels
-constexpr int kGraphIters = 16; // PCG iterations per graph replay
+constexpr int kNT = 128;          // threads per block in the face kernels
+constexpr int kMaxBlocks = 1216;  // 152 SMs x 8 resident blocks
+constexpr int kGraphIters = 16;   // PCG iterations per graph replay
 
 // scalar slots (double) of a solve
-enum {
-  S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_DONE, S_ITERS, S_TOL2, S_MAXIT, S_PQ, S_BAD, S_NSCAL
-};
+enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_DONE, S_ITERS, S_TOL2, S_MAXIT, S_PQ, S_BAD, S_NSCAL };
 
 struct FaceArgs {
-  const int32_t* owner;   // [nfc][2]
-  const int32_t* fbe;     // [nelt][4]
-  const int32_t* ftype;   // [nfc]
+  const int32_t* owner;  // [nfc][2] 4K + l
+  const int32_t* fbe;    // [nelt][4]
+  const int32_t* ftype;  // [nfc]
   int64_t nfc;
-  int d2, m;
 };
 
-// Thread -> (face e, entry a): each block holds kNT / d2 whole faces, so the d2 entries of a
-// face are always in one block.  Returns false for the idle tail threads.
-__device__ __forceinline__ bool face_slot(const FaceArgs& F, int64_t& e, int& a, int64_t& t) {
-  const int fpb = kNT / F.d2;
-  const int loc = threadIdx.x / F.d2;
-  a = threadIdx.x - loc * F.d2;
-  e = (int64_t)blockIdx.x * fpb + loc;
-  t = e * F.d2 + a;
-  return loc < fpb && e < F.nfc;
+// Tile t of a block holds faces [t*FPB, (t+1)*FPB); thread -> (face e, entry a).
+template <int D2>
+struct Tile {
+  static constexpr int FPB = kNT / D2;
+  int64_t e, t;
+  int a;
+  bool act;
+  __device__ __forceinline__ Tile(const FaceArgs& F, int64_t tile) {
+    const int loc = threadIdx.x / D2;
+    a = threadIdx.x - loc * D2;
+    e = tile * FPB + loc;
+    t = e * D2 + a;
+    act = loc < FPB && e < F.nfc;
+  }
+};
+
+template <int D2>
+__device__ __forceinline__ int64_t ntiles(const FaceArgs& F) {
+  return (F.nfc + Tile<D2>::FPB - 1) / Tile<D2>::FPB;
 }
 
-// Last-block-done reduction of up to 3 values; returns true on the block that finishes.
+// Last-block-done reduction of NSLOT values; returns true on the block that finishes.  The
+// finishing block sums the per-block partials in block order, so the result is deterministic.
 template <int NSLOT>
-__device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int* counter,
-                            double (&out)[NSLOT]) {
+__device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int* counter, double (&out)[NSLOT]) {
   __shared__ double wsum[NSLOT][kNT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -82,7 +91,7 @@ __device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int*
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     double x = 0.0;
-    for (int i = threadIdx.x; i < nb; i += kNT) x += ((volatile double*)red)[s * nb + i];
+    for (int i = threadIdx.x; i < nb; i += kNT) x += __ldcg(red + s * nb + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) wsum[s][w] = x;
@@ -98,168 +107,196 @@ __device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int*
   return true;
 }
 
-// y_e = sum over owners of the face's row block of C^K times x_dK.  T = storage/arith type.
-template <typename T>
-__device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __restrict__ x,
-                                        const FaceArgs& F, int64_t e, int a) {
-  T acc = (T)0;
-  const int m = F.m, d2 = F.d2;
+// (H x)_e entry a: the face's row blocks of C^K (face-blocked storage) times x_dK.  Each
+// owner's column (m values, unit stride across the face's d2 threads) and the gathered x_dK
+// are loaded into registers before any FMA, so every thread keeps 2m loads in flight.
+template <typename T, int D2>
+__device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __restrict__ x, const FaceArgs& F,
+                                        int64_t e, int a) {
+  constexpr int m = 4 * D2;
+  T acc0 = (T)0, acc1 = (T)0;
 #pragma unroll
   for (int o = 0; o < 2; ++o) {
-    const int ow = F.owner[2 * e + o];
+    const int ow = __ldg(F.owner + 2 * e + o);
     if (ow < 0) continue;
     const int64_t K = ow >> 2;
-    const int r = (ow & 3) * d2 + a;
-    const T* Ck = C + K * (int64_t)(m * m) + r;
-    const int32_t* fb = F.fbe + 4 * K;
+    const T* Cb = C + K * (int64_t)(m * m) + (ow & 3) * (m * D2) + a;
+    const int4 fb = __ldg(reinterpret_cast<const int4*>(F.fbe) + K);
+    const int f4[4] = {fb.x, fb.y, fb.z, fb.w};
+    T cv[m], xv[m];
+#pragma unroll
+    for (int s = 0; s < m; ++s) cv[s] = __ldg(Cb + s * D2);
+#pragma unroll
     for (int fl = 0; fl < 4; ++fl) {
-      const T* xs = x + (int64_t)fb[fl] * d2;
-      const T* cc = Ck + (int64_t)(fl * d2) * m;
-      for (int b = 0; b < d2; ++b) acc = fma(cc[(int64_t)b * m], xs[b], acc);
+      const T* xs = x + (int64_t)f4[fl] * D2;
+#pragma unroll
+      for (int b = 0; b < D2; ++b) xv[fl * D2 + b] = xs[b];
+    }
+    asm volatile("" ::: "memory");  // keep every load above issued before the first FMA
+#pragma unroll
+    for (int s = 0; s < m; ++s) {
+      if (s & 1) acc1 = fma(cv[s], xv[s], acc1); else acc0 = fma(cv[s], xv[s], acc0);
     }
   }
-  return acc;
+  return acc0 + acc1;
+}
+
+template <typename T, int D2>
+__device__ __forceinline__ T bj_apply(const T* __restrict__ Binv, const T* __restrict__ r, int64_t e, int a) {
+  T s0 = (T)0, s1 = (T)0;
+  const T* Bi = Binv + (e * D2 + a) * D2;
+  const T* re = r + e * D2;
+#pragma unroll
+  for (int b = 0; b < D2; ++b) {
+    if (b & 1) s1 = fma(Bi[b], re[b], s1); else s0 = fma(Bi[b], re[b], s0);
+  }
+  return s0 + s1;
 }
 
 // ------------------------------------------------------------------ setup kernels
 // u_hat_D (eq. 6.3, with (varpi . D)^T D = I for the orthonormal basis and exact rule) on
 // Dirichlet faces, Phi_N (eq. 6.4) on Neumann faces.
+template <int D2>
 __global__ void bdata_kernel(FaceArgs F, const double* __restrict__ fvx, const double* __restrict__ vx,
                              int64_t nelt, const double* __restrict__ D, const double* __restrict__ wf,
                              int nf, const double* __restrict__ uD, const double* __restrict__ gN,
                              double* __restrict__ xD, double* __restrict__ phiN) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= F.nfc * F.d2) return;
-  const int64_t e = t / F.d2;
-  const int a = (int)(t - e * F.d2);
-  const int ty = F.ftype[e];
-  double xd = 0.0, ph = 0.0;
-  if (ty == 1 && uD) {
-    for (int r = 0; r < nf; ++r) xd = fma(wf[r] * D[r * F.d2 + a], uD[e * nf + r], xd);
-  } else if (ty == 2 && gN) {
-    // n_e: outward normal of the owning element, |n_e| = |e|
-    double w[3][3];
-    for (int i = 0; i < 3; ++i)
-      for (int d = 0; d < 3; ++d) w[i][d] = fvx[(d * 3 + i) * F.nfc + e];
-    double u1[3], u2[3], nv[3];
-    for (int d = 0; d < 3; ++d) {
-      u1[d] = w[1][d] - w[0][d];
-      u2[d] = w[2][d] - w[0][d];
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const int64_t e = T_.e, t = T_.t;
+    const int a = T_.a;
+    const int ty = F.ftype[e];
+    double xd = 0.0, ph = 0.0;
+    if (ty == 1 && uD) {
+      for (int r = 0; r < nf; ++r) xd = fma(wf[r] * D[r * D2 + a], uD[e * nf + r], xd);
+    } else if (ty == 2 && gN) {
+      // n_e: outward normal of the owning element, |n_e| = |e|
+      double w[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int d = 0; d < 3; ++d) w[i][d] = fvx[(d * 3 + i) * F.nfc + e];
+      double u1[3], u2[3], nv[3];
+      for (int d = 0; d < 3; ++d) {
+        u1[d] = w[1][d] - w[0][d];
+        u2[d] = w[2][d] - w[0][d];
+      }
+      cross3(u1, u2, nv);
+      const int ow = F.owner[2 * e];
+      const int64_t K = ow >> 2;
+      const int opp[4] = {3, 2, 1, 0};  // vertex of K not on local face l (eq. 2.1)
+      const int vi = opp[ow & 3];
+      double dot = 0.0;
+      for (int d = 0; d < 3; ++d) dot += nv[d] * (vx[(d * 4 + vi) * nelt + K] - w[0][d]);
+      const double sg = dot > 0 ? -0.5 : 0.5;
+      for (int s = 0; s < 3; ++s) {
+        double acc = 0.0;
+        for (int r = 0; r < nf; ++r) acc = fma(wf[r] * D[r * D2 + a], gN[((int64_t)s * F.nfc + e) * nf + r], acc);
+        ph = fma(sg * nv[s], acc, ph);
+      }
     }
-    cross3(u1, u2, nv);
-    const int ow = F.owner[2 * e];
-    const int64_t K = ow >> 2;
-    const int opp[4] = {3, 2, 1, 0};  // vertex of K not on local face l (eq. 2.1)
-    const int vi = opp[ow & 3];
-    double dot = 0.0;
-    for (int d = 0; d < 3; ++d) dot += nv[d] * (vx[(d * 4 + vi) * nelt + K] - w[0][d]);
-    const double sg = dot > 0 ? -0.5 : 0.5;
-    for (int s = 0; s < 3; ++s) {
-      double acc = 0.0;
-      for (int r = 0; r < nf; ++r) acc = fma(wf[r] * D[r * F.d2 + a], gN[((int64_t)s * F.nfc + e) * nf + r], acc);
-      ph = fma(sg * nv[s], acc, ph);
-    }
+    xD[t] = xd;
+    phiN[t] = ph;
   }
-  xD[t] = xd;
-  phiN[t] = ph;
 }
 
 // b = F + G_N - H x_D on free faces (F assembled from C_f^K), 0 on Dirichlet faces.
+template <int D2>
 __global__ void rhs_kernel(FaceArgs F, const double* __restrict__ C, const double* __restrict__ Cf,
-                           const double* __restrict__ xD, const double* __restrict__ phiN,
-                           double* __restrict__ b, double* red, unsigned int* counter, double* scal) {
-  int64_t e, t;
-  int a;
+                           const double* __restrict__ xD, const double* __restrict__ phiN, double* __restrict__ b,
+                           double* red, unsigned int* counter, double* scal) {
+  constexpr int m = 4 * D2;
   double v = 0.0;
-  if (face_slot(F, e, a, t)) {
-    if (F.ftype[e] != 1) {
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    double bv = 0.0;
+    if (F.ftype[T_.e] != 1) {
       double fsum = 0.0;
       for (int o = 0; o < 2; ++o) {
-        const int ow = F.owner[2 * e + o];
+        const int ow = F.owner[2 * T_.e + o];
         if (ow < 0) continue;
-        fsum += Cf[(int64_t)(ow >> 2) * F.m + (ow & 3) * F.d2 + a];
+        fsum += Cf[(int64_t)(ow >> 2) * m + (ow & 3) * D2 + T_.a];
       }
-      v = fsum + phiN[t] - face_apply<double>(C, xD, F, e, a);
+      bv = fsum + phiN[T_.t] - face_apply<double, D2>(C, xD, F, T_.e, T_.a);
     }
-    b[t] = v;
+    b[T_.t] = bv;
+    v = fma(bv, bv, v);
   }
-  double in[1] = {v * v}, out[1];
+  double in[1] = {v}, out[1];
   if (grid_reduce<1>(in, red, counter, out) && threadIdx.x == 0) scal[S_BB] = out[0];
 }
 
-// Inverse of each free face's diagonal block of H (block-Jacobi), by Cholesky.  One thread
-// per face; T = the precision the inverse is stored in.
-template <typename T>
-__global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, T* __restrict__ Binv, int32_t* status,
+// Inverse of each free face's diagonal block of H (block-Jacobi): Cholesky, or Gauss-Jordan
+// without pivoting for convection (the block's symmetric part is positive definite).
+template <int D2>
+__global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __restrict__ Binv, int32_t* status,
                           bool nonsym) {
+  constexpr int m = 4 * D2;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= F.nfc) return;
-  const int d2 = F.d2, m = F.m;
-  double A[15 * 15], X[15 * 15];
-  for (int i = 0; i < d2 * d2; ++i) A[i] = 0.0;
+  double A[D2 * D2], X[D2 * D2];
   if (F.ftype[e] == 1) {
-    for (int i = 0; i < d2 * d2; ++i) Binv[e * d2 * d2 + i] = (T)0;
+    for (int i = 0; i < D2 * D2; ++i) Binv[e * D2 * D2 + i] = 0.0;
     return;
   }
+  for (int i = 0; i < D2 * D2; ++i) A[i] = 0.0;
   for (int o = 0; o < 2; ++o) {
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
-    const double* Ck = C + (int64_t)(ow >> 2) * m * m;
-    const int r0 = (ow & 3) * d2;
-    // stored C^K (symmetric) or its transpose (convection): block (i, j) of C^K is at [r0+j][r0+i]
-    for (int i = 0; i < d2; ++i)
-      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Ck[(r0 + j) * m + r0 + i];
+    const int l = ow & 3;
+    // C^K[l d2 + i][l d2 + j] is stored at [K][l][l d2 + j][i]
+    const double* Cb = C + (int64_t)(ow >> 2) * m * m + l * (m * D2) + (l * D2) * D2;
+    for (int i = 0; i < D2; ++i)
+      for (int j = 0; j < D2; ++j) A[i * D2 + j] += Cb[j * D2 + i];
   }
   bool ok = true;
-  if (nonsym) {  // Gauss-Jordan without pivoting (the block's symmetric part is positive definite)
-    for (int i = 0; i < d2 * d2; ++i) X[i] = 0.0;
-    for (int i = 0; i < d2; ++i) X[i * d2 + i] = 1.0;
-    for (int j = 0; j < d2; ++j) {
-      const double piv = A[j * d2 + j];
+  if (nonsym) {
+    for (int i = 0; i < D2 * D2; ++i) X[i] = 0.0;
+    for (int i = 0; i < D2; ++i) X[i * D2 + i] = 1.0;
+    for (int j = 0; j < D2; ++j) {
+      const double piv = A[j * D2 + j];
       ok = ok && piv != 0.0 && isfinite(piv);
       const double ip = 1.0 / piv;
-      for (int c = 0; c < d2; ++c) {
-        A[j * d2 + c] *= ip;
-        X[j * d2 + c] *= ip;
+      for (int c = 0; c < D2; ++c) {
+        A[j * D2 + c] *= ip;
+        X[j * D2 + c] *= ip;
       }
-      for (int i = 0; i < d2; ++i) {
+      for (int i = 0; i < D2; ++i) {
         if (i == j) continue;
-        const double f = A[i * d2 + j];
-        for (int c = 0; c < d2; ++c) {
-          A[i * d2 + c] -= f * A[j * d2 + c];
-          X[i * d2 + c] -= f * X[j * d2 + c];
+        const double f = A[i * D2 + j];
+        for (int c = 0; c < D2; ++c) {
+          A[i * D2 + c] -= f * A[j * D2 + c];
+          X[i * D2 + c] -= f * X[j * D2 + c];
         }
       }
     }
-    for (int i = 0; i < d2 * d2; ++i) Binv[e * d2 * d2 + i] = (T)X[i];
-    if (!ok) atomicAdd(status + 3, 1);
-    return;
-  }
-  for (int j = 0; j < d2; ++j) {  // in-place lower Cholesky
-    double s = A[j * d2 + j];
-    for (int l = 0; l < j; ++l) s -= A[j * d2 + l] * A[j * d2 + l];
-    ok = ok && s > 0.0;
-    const double d = sqrt(s);
-    A[j * d2 + j] = d;
-    for (int i = j + 1; i < d2; ++i) {
-      double t = A[i * d2 + j];
-      for (int l = 0; l < j; ++l) t -= A[i * d2 + l] * A[j * d2 + l];
-      A[i * d2 + j] = t / d;
+  } else {
+    for (int j = 0; j < D2; ++j) {  // in-place lower Cholesky
+      double s = A[j * D2 + j];
+      for (int l = 0; l < j; ++l) s -= A[j * D2 + l] * A[j * D2 + l];
+      ok = ok && s > 0.0;
+      const double d = sqrt(s);
+      A[j * D2 + j] = d;
+      for (int i = j + 1; i < D2; ++i) {
+        double t = A[i * D2 + j];
+        for (int l = 0; l < j; ++l) t -= A[i * D2 + l] * A[j * D2 + l];
+        A[i * D2 + j] = t / d;
+      }
+    }
+    for (int c = 0; c < D2; ++c) {  // columns of A^-1 = L^-T L^-1 e_c
+      for (int i = 0; i < D2; ++i) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int l = 0; l < i; ++l) s -= A[i * D2 + l] * X[l * D2 + c];
+        X[i * D2 + c] = s / A[i * D2 + i];
+      }
+      for (int i = D2 - 1; i >= 0; --i) {
+        double s = X[i * D2 + c];
+        for (int l = i + 1; l < D2; ++l) s -= A[l * D2 + i] * X[l * D2 + c];
+        X[i * D2 + c] = s / A[i * D2 + i];
+      }
     }
   }
-  for (int c = 0; c < d2; ++c) {  // columns of A^-1 = L^-T L^-1 e_c
-    for (int i = 0; i < d2; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int l = 0; l < i; ++l) s -= A[i * d2 + l] * X[l * d2 + c];
-      X[i * d2 + c] = s / A[i * d2 + i];
-    }
-    for (int i = d2 - 1; i >= 0; --i) {
-      double s = X[i * d2 + c];
-      for (int l = i + 1; l < d2; ++l) s -= A[l * d2 + i] * X[l * d2 + c];
-      X[i * d2 + c] = s / A[i * d2 + i];
-    }
-  }
-  for (int i = 0; i < d2 * d2; ++i) Binv[e * d2 * d2 + i] = (T)X[i];
+  for (int i = 0; i < D2 * D2; ++i) Binv[e * D2 * D2 + i] = X[i];
   if (!ok) atomicAdd(status + 3, 1);
 }
 
@@ -270,47 +307,36 @@ __global__ void convert_kernel(const double* __restrict__ a, T* __restrict__ b, 
 }
 
 // ------------------------------------------------------------------ PCG kernels
-// z_e = Binv_e r_e for the d2 entries of face e handled by this thread group
-template <typename T>
-__device__ __forceinline__ T bj_apply(const T* __restrict__ Binv, const T* __restrict__ r, int64_t e, int a, int d2) {
-  T s = (T)0;
-  const T* Bi = Binv + (e * d2 + a) * d2;
-  const T* re = r + e * d2;
-  for (int b = 0; b < d2; ++b) s = fma(Bi[b], re[b], s);
-  return s;
-}
-
-// init: r = b - H x (x given) or r = b (x = 0);  z = B^-1 r;  p = z;  rz, rr
-template <typename T>
-__global__ void pcg_init_kernel(FaceArgs F, const T* __restrict__ C, const T* __restrict__ Binv,
-                                const T* __restrict__ b, T* __restrict__ x, bool have_x, T* __restrict__ r,
-                                double* red, unsigned int* counter, double* scal) {
-  int64_t e, t;
-  int a;
-  double v[2] = {0.0, 0.0};
-  if (face_slot(F, e, a, t)) {
-    T rv = (T)0;
-    if (F.ftype[e] != 1) rv = b[t] - (have_x ? face_apply<T>(C, x, F, e, a) : (T)0);
-    if (!have_x) x[t] = (T)0;
-    r[t] = rv;
-    v[1] = (double)rv * (double)rv;
-  }
-  double out[2];
-  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) scal[S_RR] = out[1];
-}
-
-template <typename T>
-__global__ void pcg_precond_kernel(FaceArgs F, const T* __restrict__ Binv, const T* __restrict__ r,
-                                   T* __restrict__ z, T* __restrict__ p, double* red, unsigned int* counter,
-                                   double* scal) {
-  int64_t e, t;
-  int a;
+// init: r = b - H x (x given) or r = b (x = 0);  r.r
+template <typename T, int D2>
+__global__ void pcg_init_kernel(FaceArgs F, const T* __restrict__ C, const T* __restrict__ b, T* __restrict__ x,
+                                bool have_x, T* __restrict__ r, double* red, unsigned int* counter, double* scal) {
   double v[1] = {0.0};
-  if (face_slot(F, e, a, t)) {
-    T zv = bj_apply<T>(Binv, r, e, a, F.d2);
-    z[t] = zv;
-    p[t] = zv;
-    v[0] = (double)r[t] * (double)zv;
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    T rv = (T)0;
+    if (F.ftype[T_.e] != 1) rv = b[T_.t] - (have_x ? face_apply<T, D2>(C, x, F, T_.e, T_.a) : (T)0);
+    if (!have_x) x[T_.t] = (T)0;
+    r[T_.t] = rv;
+    v[0] = fma((double)rv, (double)rv, v[0]);
+  }
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) scal[S_RR] = out[0];
+}
+
+// z = B^-1 r;  p = z;  r.z
+template <typename T, int D2>
+__global__ void pcg_precond_kernel(FaceArgs F, const T* __restrict__ Binv, const T* __restrict__ r, T* __restrict__ z,
+                                   T* __restrict__ p, double* red, unsigned int* counter, double* scal) {
+  double v[1] = {0.0};
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const T zv = bj_apply<T, D2>(Binv, r, T_.e, T_.a);
+    z[T_.t] = zv;
+    p[T_.t] = zv;
+    v[0] = fma((double)r[T_.t], (double)zv, v[0]);
   }
   double out[1];
   if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
@@ -321,17 +347,17 @@ __global__ void pcg_precond_kernel(FaceArgs F, const T* __restrict__ Binv, const
 }
 
 // q = H p (free faces), alpha = rz / (p.q)
-template <typename T>
+template <typename T, int D2>
 __global__ void pcg_matvec_kernel(FaceArgs F, const T* __restrict__ C, const T* __restrict__ p, T* __restrict__ q,
                                   double* red, unsigned int* counter, double* scal) {
   if (scal[S_DONE] != 0.0) return;
-  int64_t e, t;
-  int a;
   double v[1] = {0.0};
-  if (face_slot(F, e, a, t)) {
-    T qv = (F.ftype[e] != 1) ? face_apply<T>(C, p, F, e, a) : (T)0;
-    q[t] = qv;
-    v[0] = (double)p[t] * (double)qv;
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const T qv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, p, F, T_.e, T_.a) : (T)0;
+    q[T_.t] = qv;
+    v[0] = fma((double)p[T_.t], (double)qv, v[0]);
   }
   double out[1];
   if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
@@ -347,27 +373,27 @@ __global__ void pcg_matvec_kernel(FaceArgs F, const T* __restrict__ C, const T* 
 }
 
 // x += alpha p;  r -= alpha q;  z = B^-1 r;  beta = r.z_new / r.z;  convergence test on r.r
-template <typename T>
+template <typename T, int D2>
 __global__ void pcg_update_kernel(FaceArgs F, const T* __restrict__ Binv, T* __restrict__ x, T* __restrict__ r,
-                                  T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q,
-                                  double* red, unsigned int* counter, double* scal) {
+                                  T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q, double* red,
+                                  unsigned int* counter, double* scal) {
   if (scal[S_DONE] != 0.0) return;
-  const double alpha = scal[S_ALPHA];
-  int64_t e, t;
-  int a;
-  const bool act = face_slot(F, e, a, t);
-  if (act) {
-    x[t] = x[t] + (T)alpha * p[t];
-    r[t] = r[t] - (T)alpha * q[t];
-  }
-  __syncthreads();  // the d2 entries of r of this face (same block) are now updated
+  const T alpha = (T)scal[S_ALPHA];
   double v[2] = {0.0, 0.0};
-  if (act) {
-    const T zv = bj_apply<T>(Binv, r, e, a, F.d2);
-    z[t] = zv;
-    const T rv = r[t];
-    v[0] = (double)rv * (double)zv;
-    v[1] = (double)rv * (double)rv;
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (T_.act) {
+      x[T_.t] = fma(alpha, p[T_.t], x[T_.t]);
+      r[T_.t] = fma(-alpha, q[T_.t], r[T_.t]);
+    }
+    __syncthreads();  // the d2 entries of r of each face of the tile are updated
+    if (T_.act) {
+      const T zv = bj_apply<T, D2>(Binv, r, T_.e, T_.a);
+      z[T_.t] = zv;
+      const double rv = (double)r[T_.t];
+      v[0] = fma(rv, (double)zv, v[0]);
+      v[1] = fma(rv, rv, v[1]);
+    }
   }
   double out[2];
   if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
@@ -383,9 +409,9 @@ __global__ void pcg_update_kernel(FaceArgs F, const T* __restrict__ Binv, T* __r
 template <typename T>
 __global__ void pcg_dir_kernel(int64_t ntot, const T* __restrict__ z, T* __restrict__ p, const double* scal) {
   if (scal[S_DONE] != 0.0) return;
-  const double beta = scal[S_BETA];
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < ntot) p[t] = z[t] + (T)beta * p[t];
+  const T beta = (T)scal[S_BETA];
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x)
+    p[t] = fma(beta, p[t], z[t]);
 }
 
 // ------------------------------------------------------------------ BiCGStab (convection)
@@ -400,21 +426,23 @@ struct BicgVecs {
 };
 
 // r = b - H x (or b), rhat = r, p = v = 0; rho = rhat.r, beta = 0, omega = 1, rr
+template <int D2>
 __global__ void bicg_init_kernel(FaceArgs F, const double* __restrict__ C, const double* __restrict__ b,
                                  BicgVecs V, bool have_x, double* red, unsigned int* counter, double* scal) {
-  int64_t e, t;
-  int a;
   double v[2] = {0.0, 0.0};
-  if (face_slot(F, e, a, t)) {
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const int64_t t = T_.t;
     double rv = 0.0;
-    if (F.ftype[e] != 1) rv = b[t] - (have_x ? face_apply<double>(C, V.x, F, e, a) : 0.0);
+    if (F.ftype[T_.e] != 1) rv = b[t] - (have_x ? face_apply<double, D2>(C, V.x, F, T_.e, T_.a) : 0.0);
     if (!have_x) V.x[t] = 0.0;
     V.r[t] = rv;
     V.rh[t] = rv;
     V.p[t] = 0.0;
     V.v[t] = 0.0;
-    v[0] = rv * rv;
-    v[1] = rv * rv;
+    v[0] = fma(rv, rv, v[0]);
+    v[1] = fma(rv, rv, v[1]);
   }
   double out[2];
   if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
@@ -428,27 +456,30 @@ __global__ void bicg_init_kernel(FaceArgs F, const double* __restrict__ C, const
 }
 
 // p = r + beta (p - omega v);  ph = M^-1 p
+template <int D2>
 __global__ void bicg_p_kernel(FaceArgs F, const double* __restrict__ Binv, BicgVecs V, const double* scal) {
   if (scal[B_DONE] != 0.0) return;
-  int64_t e, t;
-  int a;
-  const bool act = face_slot(F, e, a, t);
-  if (act) V.p[t] = V.r[t] + scal[B_BETA] * (V.p[t] - scal[B_OMEGA] * V.v[t]);
-  __syncthreads();
-  if (act) V.ph[t] = bj_apply<double>(Binv, V.p, e, a, F.d2);
+  const double beta = scal[B_BETA], omega = scal[B_OMEGA];
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (T_.act) V.p[T_.t] = V.r[T_.t] + beta * (V.p[T_.t] - omega * V.v[T_.t]);
+    __syncthreads();
+    if (T_.act) V.ph[T_.t] = bj_apply<double, D2>(Binv, V.p, T_.e, T_.a);
+  }
 }
 
 // v = H ph;  alpha = rho / (rhat . v)
+template <int D2>
 __global__ void bicg_v_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
-  int64_t e, t;
-  int a;
   double v[1] = {0.0};
-  if (face_slot(F, e, a, t)) {
-    const double vv = (F.ftype[e] != 1) ? face_apply<double>(C, V.ph, F, e, a) : 0.0;
-    V.v[t] = vv;
-    v[0] = V.rh[t] * vv;
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const double vv = (F.ftype[T_.e] != 1) ? face_apply<double, D2>(C, V.ph, F, T_.e, T_.a) : 0.0;
+    V.v[T_.t] = vv;
+    v[0] = fma(V.rh[T_.t], vv, v[0]);
   }
   double out[1];
   if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
@@ -463,46 +494,51 @@ __global__ void bicg_v_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs
 }
 
 // s = r - alpha v;  sh = M^-1 s
+template <int D2>
 __global__ void bicg_s_kernel(FaceArgs F, const double* __restrict__ Binv, BicgVecs V, const double* scal) {
   if (scal[B_DONE] != 0.0) return;
-  int64_t e, t;
-  int a;
-  const bool act = face_slot(F, e, a, t);
-  if (act) V.s[t] = V.r[t] - scal[B_ALPHA] * V.v[t];
-  __syncthreads();
-  if (act) V.sh[t] = bj_apply<double>(Binv, V.s, e, a, F.d2);
+  const double alpha = scal[B_ALPHA];
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (T_.act) V.s[T_.t] = V.r[T_.t] - alpha * V.v[T_.t];
+    __syncthreads();
+    if (T_.act) V.sh[T_.t] = bj_apply<double, D2>(Binv, V.s, T_.e, T_.a);
+  }
 }
 
 // t = H sh;  omega = (t.s) / (t.t)
+template <int D2>
 __global__ void bicg_t_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
-  int64_t e, t;
-  int a;
   double v[2] = {0.0, 0.0};
-  if (face_slot(F, e, a, t)) {
-    const double tv = (F.ftype[e] != 1) ? face_apply<double>(C, V.sh, F, e, a) : 0.0;
-    V.t[t] = tv;
-    v[0] = tv * V.s[t];
-    v[1] = tv * tv;
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const double tv = (F.ftype[T_.e] != 1) ? face_apply<double, D2>(C, V.sh, F, T_.e, T_.a) : 0.0;
+    V.t[T_.t] = tv;
+    v[0] = fma(tv, V.s[T_.t], v[0]);
+    v[1] = fma(tv, tv, v[1]);
   }
   double out[2];
   if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) scal[B_OMEGA] = (out[1] > 0.0) ? out[0] / out[1] : 0.0;
 }
 
 // x += alpha ph + omega sh;  r = s - omega t;  rho' = rhat.r;  beta = (rho'/rho)(alpha/omega)
+template <int D2>
 __global__ void bicg_x_kernel(FaceArgs F, BicgVecs V, double* red, unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
   const double alpha = scal[B_ALPHA], omega = scal[B_OMEGA];
-  int64_t e, t;
-  int a;
   double v[2] = {0.0, 0.0};
-  if (face_slot(F, e, a, t)) {
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    const int64_t t = T_.t;
     V.x[t] += alpha * V.ph[t] + omega * V.sh[t];
     const double rv = V.s[t] - omega * V.t[t];
     V.r[t] = rv;
-    v[0] = V.rh[t] * rv;
-    v[1] = rv * rv;
+    v[0] = fma(V.rh[t], rv, v[0]);
+    v[1] = fma(rv, rv, v[1]);
   }
   double out[2];
   if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
@@ -519,6 +555,17 @@ __global__ void bicg_x_kernel(FaceArgs F, BicgVecs V, double* red, unsigned int*
   }
 }
 
+__global__ void finish_kernel(int64_t ntot, const int32_t* ftype, int d2, const double* x, const double* xD,
+                              double* uhat) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x)
+    uhat[t] = (ftype[t / d2] == 1) ? xD[t] : x[t];
+}
+
+__global__ void axpy_f32_kernel(int64_t n, const float* __restrict__ d, double* __restrict__ x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    x[t] += (double)d[t];
+}
+
 // ------------------------------------------------------------------ host side
 static FaceArgs face_args(hdg_mesh* M) {
   FaceArgs F;
@@ -526,20 +573,18 @@ static FaceArgs face_args(hdg_mesh* M) {
   F.fbe = M->d_facebyele;
   F.ftype = M->d_ftype;
   F.nfc = M->nfc;
-  F.d2 = M->tab.d2;
-  F.m = M->tab.m;
   return F;
 }
 
-// blocks of the face kernels (kNT / d2 whole faces per block)
+// blocks of the face kernels: persistent grid over tiles of kNT / d2 whole faces
 static int nblocks(hdg_mesh* M) {
   const int fpb = kNT / M->tab.d2;
-  return (int)((M->nfc + fpb - 1) / fpb);
+  const int64_t tiles = (M->nfc + fpb - 1) / fpb;
+  return (int)(tiles < kMaxBlocks ? tiles : kMaxBlocks);
 }
 
 static int ensure_workspace(hdg_mesh* M, bool mixed) {
   const int64_t nv = M->nfc * M->tab.d2;
-  const int nb = nblocks(M);
   if (!M->d_b) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_b, sizeof(double) * nv));
     HDG_CUDA_TRY(cudaMalloc(&M->d_x, sizeof(double) * nv));
@@ -549,15 +594,13 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_q, sizeof(double) * nv));
     HDG_CUDA_TRY(cudaMalloc(&M->d_uhatD, sizeof(double) * 2 * nv));
     HDG_CUDA_TRY(cudaMalloc(&M->d_BJ, sizeof(double) * M->nfc * M->tab.d2 * M->tab.d2));
-    HDG_CUDA_TRY(cudaMalloc(&M->d_red, sizeof(double) * 4 * nb));
+    HDG_CUDA_TRY(cudaMalloc(&M->d_red, sizeof(double) * 4 * kMaxBlocks));
     HDG_CUDA_TRY(cudaMalloc(&M->d_scal, sizeof(double) * 2 * S_NSCAL));
     HDG_CUDA_TRY(cudaMalloc(&M->d_counter, sizeof(unsigned int) * 4));
     HDG_CUDA_TRY(cudaMemsetAsync(M->d_counter, 0, sizeof(unsigned int) * 4, M->stream));
-    M->red_blocks = nb;
+    M->red_blocks = kMaxBlocks;
   }
-  if (M->beta_q && !M->d_bicg) {
-    HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * nv));
-  }
+  if (M->beta_q && !M->d_bicg) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * nv));
   if (mixed && !M->d_C32) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_C32, sizeof(float) * M->nelt * M->tab.m * M->tab.m));
     HDG_CUDA_TRY(cudaMalloc(&M->d_BJ32, sizeof(float) * M->nfc * M->tab.d2 * M->tab.d2));
@@ -570,258 +613,263 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
   return HDG_OK;
 }
 
-// Boundary data, block-Jacobi inverse and right-hand side (once per assembled system).
-static int prepare_rhs(hdg_mesh* M) {
-  if (M->rhs_ready) return HDG_OK;
-  FaceArgs F = face_args(M);
-  const int64_t nv = M->nfc * M->tab.d2;
-  const int nb = nblocks(M);
-  double* xD = M->d_uhatD;
-  double* phiN = M->d_uhatD + nv;
-  bdata_kernel<<<nb, kNT, 0, M->stream>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf,
-                                          M->uD, M->gN, xD, phiN);
-  rhs_kernel<<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter, M->d_scal);
-  bj_kernel<double><<<(unsigned)((M->nfc + 63) / 64), 64, 0, M->stream>>>(F, M->d_C, M->d_BJ, M->d_status,
-                                                                        M->beta_q != nullptr);
-  M->launches += 3;
-  HDG_CUDA_TRY(cudaGetLastError());
-  double bb;
-  HDG_CUDA_TRY(cudaMemcpyAsync(&bb, M->d_scal + S_BB, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
-  HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-  M->bnorm = std::sqrt(bb);
-  M->rhs_ready = true;
-  return HDG_OK;
-}
-
-// One PCG solve of H_T x = rhs to ||r|| <= sqrt(tol2) (absolute), T in {double, float}.
-// scal: device scalars of this solve.  Returns iterations through *iters.
-template <typename T>
-static int pcg_run(hdg_mesh* M, const T* C, const T* Binv, const T* rhs, T* x, bool have_x, T* r, T* z, T* p,
-                   T* q, double* scal, double tol2, int maxit, cudaGraphExec_t* graph, int* iters, double* rr_out,
-                   bool* bad) {
-  FaceArgs F = face_args(M);
-  const int nb = nblocks(M);
-  const int64_t nv = M->nfc * M->tab.d2;
-  double hs[S_NSCAL] = {0};
-  hs[S_TOL2] = tol2;
-  hs[S_MAXIT] = (double)maxit;
-  HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
-  pcg_init_kernel<T><<<nb, kNT, 0, M->stream>>>(F, C, Binv, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
-  pcg_precond_kernel<T><<<nb, kNT, 0, M->stream>>>(F, Binv, r, z, p, M->d_red, M->d_counter, scal);
-  M->launches += 2;
-  HDG_CUDA_TRY(cudaGetLastError());
-  if (!*graph) {
-    cudaGraph_t g;
-    // capture on a private stream (the caller's may be the legacy default stream, which
-    // cannot be captured); the graph is then launched on the caller's stream
-    if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
-    cudaStream_t cs = M->cap_stream;
-    HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < kGraphIters; ++it) {
-      pcg_matvec_kernel<T><<<nb, kNT, 0, cs>>>(F, C, p, q, M->d_red, M->d_counter, scal);
-      pcg_update_kernel<T><<<nb, kNT, 0, cs>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
-      pcg_dir_kernel<T><<<nb, kNT, 0, cs>>>(nv, z, p, scal);
-    }
-    HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
-    HDG_CUDA_TRY(cudaGraphInstantiate(graph, g, 0));
-    cudaGraphDestroy(g);
-  }
-  double hv[S_NSCAL];
-  for (;;) {
-    HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+template <int D2>
+struct Solver {
+  // Boundary data, block-Jacobi inverse and right-hand side (once per assembled system).
+  static int prepare_rhs(hdg_mesh* M) {
+    if (M->rhs_ready) return HDG_OK;
+    FaceArgs F = face_args(M);
+    const int64_t nv = M->nfc * D2;
+    const int nb = nblocks(M);
+    double* xD = M->d_uhatD;
+    double* phiN = M->d_uhatD + nv;
+    bdata_kernel<D2><<<nb, kNT, 0, M->stream>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf,
+                                                M->uD, M->gN, xD, phiN);
+    rhs_kernel<D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
+                                              M->d_scal);
+    bj_kernel<D2><<<(unsigned)((M->nfc + 63) / 64), 64, 0, M->stream>>>(F, M->d_C, M->d_BJ, M->d_status,
+                                                                       M->beta_q != nullptr);
+    M->launches += 3;
+    HDG_CUDA_TRY(cudaGetLastError());
+    double bb;
+    HDG_CUDA_TRY(cudaMemcpyAsync(&bb, M->d_scal + S_BB, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
     HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-    if (hv[S_DONE] != 0.0) break;
-    HDG_CUDA_TRY(cudaGraphLaunch(*graph, M->stream));
-    M->launches += 3 * kGraphIters;
+    M->bnorm = std::sqrt(bb);
+    M->rhs_ready = true;
+    return HDG_OK;
   }
-  *iters = (int)hv[S_ITERS];
-  *rr_out = hv[S_RR];
-  *bad = hv[S_BAD] != 0.0;
-  return HDG_OK;
-}
 
-static int bicg_run(hdg_mesh* M, bool have_x, double tol2, int maxit, int* iters, bool* bad) {
-  FaceArgs F = face_args(M);
-  const int nb = nblocks(M);
-  const int64_t nv = M->nfc * M->tab.d2;
-  BicgVecs V{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + nv, M->d_bicg + 2 * nv,
-             M->d_bicg + 3 * nv};
-  double* scal = M->d_scal;
-  double hs[B_NSCAL] = {0};
-  hs[B_TOL2] = tol2;
-  hs[B_MAXIT] = (double)maxit;
-  HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
-  bicg_init_kernel<<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, V, have_x, M->d_red, M->d_counter, scal);
-  M->launches++;
-  HDG_CUDA_TRY(cudaGetLastError());
-  if (!M->graph_bicg) {
-    if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
-    cudaStream_t cs = M->cap_stream;
-    cudaGraph_t g;
-    HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < kGraphIters; ++it) {
-      bicg_p_kernel<<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
-      bicg_v_kernel<<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
-      bicg_s_kernel<<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
-      bicg_t_kernel<<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
-      bicg_x_kernel<<<nb, kNT, 0, cs>>>(F, V, M->d_red, M->d_counter, scal);
+  // One PCG solve of H_T x = rhs to ||r|| <= sqrt(tol2) (absolute), T in {double, float}.
+  template <typename T>
+  static int pcg_run(hdg_mesh* M, const T* C, const T* Binv, const T* rhs, T* x, bool have_x, T* r, T* z, T* p,
+                     T* q, double* scal, double tol2, int maxit, cudaGraphExec_t* graph, int* iters, bool* bad) {
+    FaceArgs F = face_args(M);
+    const int nb = nblocks(M);
+    const int64_t nv = M->nfc * D2;
+    double hs[S_NSCAL] = {0};
+    hs[S_TOL2] = tol2;
+    hs[S_MAXIT] = (double)maxit;
+    HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
+    pcg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
+    pcg_precond_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, Binv, r, z, p, M->d_red, M->d_counter, scal);
+    M->launches += 2;
+    HDG_CUDA_TRY(cudaGetLastError());
+    if (!*graph) {
+      // capture on a private stream (the caller's may be the legacy default stream, which
+      // cannot be captured); the graph is then launched on the caller's stream
+      if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t cs = M->cap_stream;
+      cudaGraph_t g;
+      HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      for (int it = 0; it < kGraphIters; ++it) {
+        pcg_matvec_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+        pcg_update_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
+        pcg_dir_kernel<T><<<nb, kNT, 0, cs>>>(nv, z, p, scal);
+      }
+      HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+      HDG_CUDA_TRY(cudaGraphInstantiate(graph, g, 0));
+      cudaGraphDestroy(g);
     }
-    HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
-    HDG_CUDA_TRY(cudaGraphInstantiate(&M->graph_bicg, g, 0));
-    cudaGraphDestroy(g);
+    double hv[S_NSCAL];
+    for (;;) {
+      HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+      HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+      if (hv[S_DONE] != 0.0) break;
+      HDG_CUDA_TRY(cudaGraphLaunch(*graph, M->stream));
+      M->launches += 3 * kGraphIters;
+    }
+    *iters = (int)hv[S_ITERS];
+    *bad = hv[S_BAD] != 0.0;
+    return HDG_OK;
   }
-  double hv[B_NSCAL];
-  for (;;) {
-    HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+
+  static int bicg_run(hdg_mesh* M, bool have_x, double tol2, int maxit, int* iters, bool* bad) {
+    FaceArgs F = face_args(M);
+    const int nb = nblocks(M);
+    const int64_t nv = M->nfc * D2;
+    BicgVecs V{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + nv, M->d_bicg + 2 * nv,
+               M->d_bicg + 3 * nv};
+    double* scal = M->d_scal;
+    double hs[B_NSCAL] = {0};
+    hs[B_TOL2] = tol2;
+    hs[B_MAXIT] = (double)maxit;
+    HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
+    bicg_init_kernel<D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, V, have_x, M->d_red, M->d_counter, scal);
+    M->launches++;
+    HDG_CUDA_TRY(cudaGetLastError());
+    if (!M->graph_bicg) {
+      if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t cs = M->cap_stream;
+      cudaGraph_t g;
+      HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      for (int it = 0; it < kGraphIters; ++it) {
+        bicg_p_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
+        bicg_v_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
+        bicg_s_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
+        bicg_t_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
+        bicg_x_kernel<D2><<<nb, kNT, 0, cs>>>(F, V, M->d_red, M->d_counter, scal);
+      }
+      HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+      HDG_CUDA_TRY(cudaGraphInstantiate(&M->graph_bicg, g, 0));
+      cudaGraphDestroy(g);
+    }
+    double hv[B_NSCAL];
+    for (;;) {
+      HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+      HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+      if (hv[B_DONE] != 0.0) break;
+      HDG_CUDA_TRY(cudaGraphLaunch(M->graph_bicg, M->stream));
+      M->launches += 5 * kGraphIters;
+    }
+    *iters = (int)hv[B_ITERS];
+    *bad = hv[B_BAD] != 0.0;
+    return HDG_OK;
+  }
+
+  // ||b - H x||_2 over the free dofs in FP64, r written to `r`.
+  static int true_residual(hdg_mesh* M, const double* x, double* r, double* rnorm) {
+    FaceArgs F = face_args(M);
+    const int nb = nblocks(M);
+    double* scal = M->d_scal + S_NSCAL;
+    pcg_init_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, const_cast<double*>(x), true, r,
+                                                           M->d_red, M->d_counter, scal);
+    M->launches++;
+    HDG_CUDA_TRY(cudaGetLastError());
+    double rr;
+    HDG_CUDA_TRY(cudaMemcpyAsync(&rr, scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
     HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-    if (hv[B_DONE] != 0.0) break;
-    HDG_CUDA_TRY(cudaGraphLaunch(M->graph_bicg, M->stream));
-    M->launches += 5 * kGraphIters;
+    *rnorm = std::sqrt(rr);
+    return HDG_OK;
   }
-  *iters = (int)hv[B_ITERS];
-  *bad = hv[B_BAD] != 0.0;
-  return HDG_OK;
-}
 
-// ||b - H x||_2 over the free dofs in FP64, r returned in M->d_r.
-static int true_residual(hdg_mesh* M, const double* x, double* r, double* rnorm) {
-  FaceArgs F = face_args(M);
-  const int nb = nblocks(M);
-  double* scal = M->d_scal + S_NSCAL;
-  pcg_init_kernel<double><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_BJ, M->d_b, const_cast<double*>(x), true, r,
-                                                     M->d_red, M->d_counter, scal);
-  M->launches++;
-  HDG_CUDA_TRY(cudaGetLastError());
-  double rr;
-  HDG_CUDA_TRY(cudaMemcpyAsync(&rr, scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
-  HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-  *rnorm = std::sqrt(rr);
-  return HDG_OK;
-}
+  static int solve(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0, double* uhat, int* iters,
+                   double* relres) {
+    const bool mixed = precision == HDG_MIXED_FP32;
+    int rc = ensure_workspace(M, mixed);
+    if (rc) return rc;
+    rc = prepare_rhs(M);
+    if (rc) return rc;
+    const int64_t nv = M->nfc * D2;
+    const int nb = nblocks(M);
+    const double bnorm = M->bnorm;
+    const double tol = rtol * bnorm;
+    int total_it = 0;
+    bool converged = false, bad = false;
+    double rnorm = 0.0;
+    if (x0) HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
+    if (M->beta_q) {
+      // non-symmetric trace matrix (convection): block-Jacobi BiCGStab in FP64
+      if (mixed) return fail(HDG_ERR_UNSUPPORTED, "the mixed-precision solve is for symmetric (beta = 0) problems");
+      bool have_x = x0 != nullptr;
+      for (int pass = 0; pass < 3 && !converged && total_it < maxit; ++pass) {
+        int it;
+        rc = bicg_run(M, have_x, tol * tol, maxit - total_it, &it, &bad);
+        if (rc) return rc;
+        total_it += it;
+        rc = true_residual(M, M->d_x, M->d_q, &rnorm);
+        if (rc) return rc;
+        converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
+        have_x = true;  // restart from the current iterate if the recursive residual drifted
+        if (bad && !converged) bad = false;
+      }
+    } else if (!mixed) {
+      int it;
+      rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, x0 != nullptr, M->d_r, M->d_z, M->d_p, M->d_q,
+                           M->d_scal, tol * tol, maxit, &M->graph64, &it, &bad);
+      if (rc) return rc;
+      total_it = it;
+      rc = true_residual(M, M->d_x, M->d_q, &rnorm);
+      if (rc) return rc;
+      converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
+      if (!converged && it < maxit && !bad) {
+        // recursive residual converged but the true one did not: one more restarted pass
+        rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, true, M->d_r, M->d_z, M->d_p, M->d_q, M->d_scal,
+                             tol * tol, maxit - it, &M->graph64, &it, &bad);
+        if (rc) return rc;
+        total_it += it;
+        rc = true_residual(M, M->d_x, M->d_q, &rnorm);
+        if (rc) return rc;
+        converged = rnorm <= tol * 1.0000001;
+      }
+    } else {
+      // mixed: FP32 copies of C^K and the block inverses, FP64 outer residual and update
+      const int64_t nC = M->nelt * (int64_t)M->tab.m * M->tab.m;
+      convert_kernel<float><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, nC);
+      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * D2 * D2);
+      M->launches += 2;
+      if (!x0) HDG_CUDA_TRY(cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, M->stream));
+      for (int outer = 0; outer < 30; ++outer) {
+        rc = true_residual(M, M->d_x, M->d_r, &rnorm);
+        if (rc) return rc;
+        if (rnorm <= tol || bnorm == 0.0) {
+          converged = true;
+          break;
+        }
+        if (total_it >= maxit) break;
+        convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_r, M->d_r32, nv);
+        M->launches++;
+        int it;
+        const double itol = M->inner_rtol * rnorm;
+        rc = pcg_run<float>(M, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, false, M->d_q32, M->d_z32, M->d_p32,
+                            reinterpret_cast<float*>(M->d_q), M->d_scal, itol * itol, maxit - total_it, &M->graph32,
+                            &it, &bad);
+        if (rc) return rc;
+        total_it += it;
+        axpy_f32_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_x32, M->d_x);
+        M->launches++;
+        if (bad) break;
+      }
+    }
+    finish_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, D2, M->d_x, M->d_uhatD, uhat);
+    M->launches++;
+    HDG_CUDA_TRY(cudaGetLastError());
+    HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+    if (iters) *iters = total_it;
+    if (relres) *relres = bnorm > 0 ? rnorm / bnorm : 0.0;
+    if (bad) return fail(HDG_ERR_NOT_CONVERGED, "Krylov breakdown");
+    if (!converged)
+      return fail(HDG_ERR_NOT_CONVERGED, "trace solve reached maxit with relative residual " +
+                                             std::to_string(bnorm > 0 ? rnorm / bnorm : 0.0));
+    return HDG_OK;
+  }
 
-__global__ void finish_kernel(int64_t ntot, const int32_t* ftype, int d2, const double* x, const double* xD,
-                              double* uhat) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntot) return;
-  uhat[t] = (ftype[t / d2] == 1) ? xD[t] : x[t];
-}
-
-__global__ void axpy_f32_kernel(int64_t n, const float* __restrict__ d, double* __restrict__ x) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) x[t] += (double)d[t];
-}
+  static int residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {
+    int rc = ensure_workspace(M, false);
+    if (rc) return rc;
+    rc = prepare_rhs(M);
+    if (rc) return rc;
+    double rn;
+    rc = true_residual(M, x, r, &rn);
+    if (rc) return rc;
+    if (rnorm) *rnorm = rn;
+    if (bnorm) *bnorm = M->bnorm;
+    return HDG_OK;
+  }
+};
 
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0, double* uhat, int* iters,
                 double* relres) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "hdg_solve_trace before hdg_assemble_condense");
   if (precision != HDG_FP64 && precision != HDG_MIXED_FP32) return fail(HDG_ERR_ARG, "unknown precision");
   if (!(rtol > 0) || maxit < 1 || !uhat) return fail(HDG_ERR_ARG, "bad rtol/maxit/uhat");
-  const bool mixed = precision == HDG_MIXED_FP32;
-  int rc = ensure_workspace(M, mixed);
-  if (rc) return rc;
-  rc = prepare_rhs(M);
-  if (rc) return rc;
-  const int64_t nv = M->nfc * M->tab.d2;
-  const int nb = nblocks(M);
-  const double bnorm = M->bnorm;
-  const double tol = rtol * bnorm;
-  int total_it = 0;
-  bool converged = false, bad = false;
-  double rnorm = 0.0;
-  if (x0) HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
-  if (M->beta_q) {
-    // non-symmetric trace matrix (convection): block-Jacobi BiCGStab in FP64
-    if (mixed) return fail(HDG_ERR_UNSUPPORTED, "the mixed-precision solve is for symmetric (beta = 0) problems");
-    bool have_x = x0 != nullptr;
-    for (int pass = 0; pass < 3 && !converged && total_it < maxit; ++pass) {
-      int it;
-      rc = bicg_run(M, have_x, tol * tol, maxit - total_it, &it, &bad);
-      if (rc) return rc;
-      total_it += it;
-      rc = true_residual(M, M->d_x, M->d_q, &rnorm);
-      if (rc) return rc;
-      converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
-      have_x = true;  // restart from the current iterate if the recursive residual drifted
-      if (bad && !converged) bad = false;
-    }
-  } else if (!mixed) {
-    int it;
-    double rr;
-    rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, x0 != nullptr, M->d_r, M->d_z, M->d_p, M->d_q,
-                         M->d_scal, tol * tol, maxit, &M->graph64, &it, &rr, &bad);
-    if (rc) return rc;
-    total_it = it;
-    rc = true_residual(M, M->d_x, M->d_q, &rnorm);
-    if (rc) return rc;
-    converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
-    if (!converged && it < maxit && !bad) {
-      // recursive residual converged but the true one did not: one more restarted pass
-      rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, true, M->d_r, M->d_z, M->d_p, M->d_q, M->d_scal,
-                           tol * tol, maxit - it, &M->graph64, &it, &rr, &bad);
-      if (rc) return rc;
-      total_it += it;
-      rc = true_residual(M, M->d_x, M->d_q, &rnorm);
-      if (rc) return rc;
-      converged = rnorm <= tol * 1.0000001;
-    }
-  } else {
-    // mixed: FP32 copies of C^K and the block inverses, FP64 outer residual and update
-    FaceArgs F = face_args(M);
-    const int64_t nC = M->nelt * (int64_t)M->tab.m * M->tab.m;
-    convert_kernel<float><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, nC);
-    convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * M->tab.d2 * M->tab.d2);
-    M->launches += 2;
-    (void)F;
-    if (!x0) HDG_CUDA_TRY(cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, M->stream));
-    const double inner_rtol = 1e-4;
-    for (int outer = 0; outer < 30; ++outer) {
-      rc = true_residual(M, M->d_x, M->d_r, &rnorm);
-      if (rc) return rc;
-      if (rnorm <= tol || bnorm == 0.0) {
-        converged = true;
-        break;
-      }
-      if (total_it >= maxit) break;
-      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_r, M->d_r32, nv);
-      M->launches++;
-      int it;
-      double rr;
-      double itol = inner_rtol * rnorm;
-      rc = pcg_run<float>(M, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, false, M->d_q32, M->d_z32, M->d_p32,
-                          reinterpret_cast<float*>(M->d_q), M->d_scal, itol * itol, maxit - total_it, &M->graph32,
-                          &it, &rr, &bad);
-      if (rc) return rc;
-      total_it += it;
-      axpy_f32_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_x32, M->d_x);
-      M->launches++;
-      if (bad) break;
-    }
+  switch (M->tab.d2) {
+    case 3: return Solver<3>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
+    case 6: return Solver<6>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
+    case 10: return Solver<10>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
+    case 15: return Solver<15>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
   }
-  finish_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, M->tab.d2, M->d_x, M->d_uhatD, uhat);
-  M->launches++;
-  HDG_CUDA_TRY(cudaGetLastError());
-  HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-  if (iters) *iters = total_it;
-  if (relres) *relres = bnorm > 0 ? rnorm / bnorm : 0.0;
-  if (bad) return fail(HDG_ERR_NOT_CONVERGED, "PCG breakdown (non-positive curvature)");
-  if (!converged)
-    return fail(HDG_ERR_NOT_CONVERGED, "trace solve reached maxit with relative residual " +
-                                           std::to_string(bnorm > 0 ? rnorm / bnorm : 0.0));
-  return HDG_OK;
+  return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }
 
 int trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "residual before hdg_assemble_condense");
-  int rc = ensure_workspace(M, false);
-  if (rc) return rc;
-  rc = prepare_rhs(M);
-  if (rc) return rc;
-  double rn;
-  rc = true_residual(M, x, r, &rn);
-  if (rc) return rc;
-  if (rnorm) *rnorm = rn;
-  if (bnorm) *bnorm = M->bnorm;
-  return HDG_OK;
+  switch (M->tab.d2) {
+    case 3: return Solver<3>::residual(M, x, r, rnorm, bnorm);
+    case 6: return Solver<6>::residual(M, x, r, rnorm, bnorm);
+    case 10: return Solver<10>::residual(M, x, r, rnorm, bnorm);
+    case 15: return Solver<15>::residual(M, x, r, rnorm, bnorm);
+  }
+  return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }
 
 }  // namespace hdg
