@@ -83,6 +83,8 @@ static void release(hdg_mesh* M) {
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
   if (M->graph32) cudaGraphExecDestroy(M->graph32);
   if (M->graph_bicg) cudaGraphExecDestroy(M->graph_bicg);
+  if (M->wgraph64) cudaGraphExecDestroy(M->wgraph64);
+  if (M->wgraph32) cudaGraphExecDestroy(M->wgraph32);
   if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
 }
 
@@ -188,6 +190,7 @@ int hdg_set_coefficients(hdg_mesh* M, const double* kappa, const double* c, cons
   if (!M || !kappa || !c || !f) return fail(HDG_ERR_ARG, "kappa, c and f are required");
   if ((beta != nullptr) != (M->beta_q != nullptr)) {  // switching symmetric <-> non-symmetric
     if (M->graph64) { cudaGraphExecDestroy(M->graph64); M->graph64 = nullptr; }
+    if (M->wgraph64) { cudaGraphExecDestroy(M->wgraph64); M->wgraph64 = nullptr; }
   }
   M->beta_q = beta;
   if (!beta) M->beta_f = nullptr;

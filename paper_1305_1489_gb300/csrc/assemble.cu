@@ -67,7 +67,7 @@ struct AsmSmem {
 };
 
 template <int K, int NT, bool CONV>
-__global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
+__global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmArgs A) {
   using D = Dims<K>;
   using SM = AsmSmem<K, CONV>;
   constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq, nf = D::nf;
@@ -393,9 +393,11 @@ __global__ void __launch_bounds__(NT) assemble_kernel(AsmArgs A) {
 
 template <int K, bool CONV>
 static cudaError_t launch_k(hdg_mesh* M, const AsmArgs& a) {
-  constexpr int NT = (K >= 3) ? 256 : 128;
+  constexpr int NT = K1Occupancy<K>::NT;
   const size_t smem = AsmSmem<K, CONV>::bytes;
   cudaError_t e = cudaFuncSetAttribute(assemble_kernel<K, NT, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(assemble_kernel<K, NT, CONV>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   assemble_kernel<K, NT, CONV><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
   M->launches += 1;

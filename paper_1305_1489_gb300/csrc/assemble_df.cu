@@ -104,7 +104,7 @@ __device__ __forceinline__ df ldg_df(const df* p) {
 }
 
 template <int K, int NT>
-__global__ void __launch_bounds__(NT) assemble_df_kernel(AsmDfArgs A) {
+__global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_df_kernel(AsmDfArgs A) {
   using D = Dims<K>;
   using SM = AsmDfSmem<K>;
   constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq;
@@ -346,9 +346,11 @@ __global__ void __launch_bounds__(NT) assemble_df_kernel(AsmDfArgs A) {
 
 template <int K>
 static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
-  constexpr int NT = (K >= 3) ? 256 : 128;
+  constexpr int NT = K1Occupancy<K>::NT;
   const size_t smem = AsmDfSmem<K>::bytes;
   cudaError_t e = cudaFuncSetAttribute(assemble_df_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(assemble_df_kernel<K, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   assemble_df_kernel<K, NT><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
   M->launches += 1;

@@ -19,6 +19,15 @@ struct Dims {
   static constexpr int rec = n * (m + 1) + n * m + 3 * n * n + 12;
 };
 
+// Launch shape of K1 (one element per CTA): threads per CTA and the number of CTAs each SM
+// should hold (register budget 65536 / (NT * MINB) per thread); shared memory per CTA is
+// 3.7 / 17 / 58 / 156 KB for k = 1..4.
+template <int K>
+struct K1Occupancy {
+  static constexpr int NT = (K >= 3) ? 256 : 128;
+  static constexpr int MINB = (K == 1) ? 8 : (K == 2) ? 4 : (K == 3) ? 3 : 1;
+};
+
 // Element geometry from the SoA vertex array vx [12][nelt] (x1..x4, y1..y4, z1..z4).
 //  a[*][#] = (det B_K B_K^-T)_{*#}, the Piola cofactors of eq. 3.8;
 //  nrm[l] = outward normal of local face l (eq. 2.1 order) with |nrm[l]| = |e_l| (Section 2).

@@ -103,6 +103,8 @@ struct hdg_mesh {
   cudaGraphExec_t graph64 = nullptr, graph32 = nullptr, graph_bicg = nullptr;
   double* d_bicg = nullptr;  // [4][nfc][d2] extra BiCGStab vectors (s, t, ph, sh)
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  cudaGraphExec_t wgraph64 = nullptr, wgraph32 = nullptr;  // device-driven (conditional WHILE) PCG loops
+  bool no_cond_graphs = false;  // the driver refused conditional nodes: host-driven loop
   int graph_iters = 0;
 };
 
@@ -128,4 +130,8 @@ cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, do
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0,
                 double* uhat, int* iters, double* relres);
 int trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm);
+int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
+                       double* norms, double rtol, int maxit, double* q, double* u, double* uhat, cudaGraphNode_t* last);
+int batch_group_iterations(hdg_mesh* M, int* iters, int* status);
+int build_mesh(hdg_mesh* M, const double* coords, const int32_t* elems, const int32_t* dir, const int32_t* neu);
 }  // namespace hdg

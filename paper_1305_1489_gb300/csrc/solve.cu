@@ -28,7 +28,7 @@ constexpr int kMaxBlocks = 1216;  // 152 SMs x 8 resident blocks
 constexpr int kGraphIters = 16;   // PCG iterations per graph replay
 
 // scalar slots (double) of a solve
-enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_DONE, S_ITERS, S_TOL2, S_MAXIT, S_PQ, S_BAD, S_NSCAL };
+enum { S_RZ = 0, S_ALPHA, S_BETA, S_RR, S_BB, S_DONE, S_ITERS, S_TOL2, S_MAXIT, S_PQ, S_BAD, S_BODIES, S_MAXBODIES, S_NSCAL };
 
 struct FaceArgs {
   const int32_t* owner;  // [nfc][2] 4K + l
@@ -414,12 +414,26 @@ __global__ void pcg_dir_kernel(int64_t ntot, const T* __restrict__ z, T* __restr
     p[t] = fma(beta, p[t], z[t]);
 }
 
+// End of one body of the device-driven loop: keep looping while the solve is not done and
+// fewer than scal[max_slot] bodies have run (the host sets that bound before every launch).
+// The body counter is independent of the reductions, so the loop ends even if a reduction
+// never completes.
+__global__ void loop_control_kernel(cudaGraphConditionalHandle h, double* scal, int done_slot, int bodies_slot,
+                                    int max_slot) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double nb = scal[bodies_slot] + 1.0;
+    scal[bodies_slot] = nb;
+    const bool more = scal[done_slot] == 0.0 && nb < scal[max_slot];
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
 // ------------------------------------------------------------------ BiCGStab (convection)
 // Right-preconditioned BiCGStab (van der Vorst 1992) with the block-Jacobi preconditioner,
 // for the non-symmetric trace matrix of convection-diffusion.  Vectors: x, r, rhat (shadow
 // residual), p, v, s, t, ph = M^-1 p, sh = M^-1 s.  Scalars rho, alpha, omega, beta on the
 // device; five kernels per iteration.
-enum { B_RHO = 0, B_ALPHA, B_OMEGA, B_BETA, B_RR, B_DONE, B_ITERS, B_TOL2, B_MAXIT, B_BAD, B_NSCAL };
+enum { B_RHO = 0, B_ALPHA, B_OMEGA, B_BETA, B_RR, B_DONE, B_ITERS, B_TOL2, B_MAXIT, B_BAD, B_BODIES, B_NSCAL };
 
 struct BicgVecs {
   double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
@@ -613,6 +627,40 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
   return HDG_OK;
 }
 
+// Build an executable graph that runs `body` (a capture callback on stream cs) inside a
+// conditional WHILE node; the body must end with loop_control_kernel on the same handle.
+// Returns false (and leaves *exec null) if the driver refuses conditional nodes.
+template <typename BodyFn>
+static bool build_while_graph(cudaStream_t cs, cudaGraphExec_t* exec, BodyFn body) {
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle h;
+  bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNode_t node;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  ok = ok && cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  if (ok) {
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      body(cs, h);
+      cudaGraph_t out = nullptr;
+      ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    }
+  }
+  ok = ok && cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
+  cudaGraphDestroy(g);
+  if (!ok) {
+    *exec = nullptr;
+    cudaGetLastError();
+  }
+  return ok;
+}
+
 template <int D2>
 struct Solver {
   // Boundary data, block-Jacobi inverse and right-hand side (once per assembled system).
@@ -649,34 +697,56 @@ struct Solver {
     double hs[S_NSCAL] = {0};
     hs[S_TOL2] = tol2;
     hs[S_MAXIT] = (double)maxit;
+    hs[S_MAXBODIES] = (double)(maxit / kGraphIters + 2);  // bound of the device-driven loop
     HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
     pcg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
     pcg_precond_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, Binv, r, z, p, M->d_red, M->d_counter, scal);
     M->launches += 2;
     HDG_CUDA_TRY(cudaGetLastError());
-    if (!*graph) {
-      // capture on a private stream (the caller's may be the legacy default stream, which
-      // cannot be captured); the graph is then launched on the caller's stream
-      if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
-      cudaStream_t cs = M->cap_stream;
-      cudaGraph_t g;
-      HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = M->cap_stream;
+    auto body = [&](cudaStream_t st, cudaGraphConditionalHandle h) {
       for (int it = 0; it < kGraphIters; ++it) {
-        pcg_matvec_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, C, p, q, M->d_red, M->d_counter, scal);
-        pcg_update_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
-        pcg_dir_kernel<T><<<nb, kNT, 0, cs>>>(nv, z, p, scal);
+        pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+        pcg_update_kernel<T, D2><<<nb, kNT, 0, st>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
+        pcg_dir_kernel<T><<<nb, kNT, 0, st>>>(nv, z, p, scal);
       }
-      HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
-      HDG_CUDA_TRY(cudaGraphInstantiate(graph, g, 0));
-      cudaGraphDestroy(g);
+      loop_control_kernel<<<1, 32, 0, st>>>(h, scal, S_DONE, S_BODIES, S_MAXBODIES);
+    };
+    cudaGraphExec_t* wg = (sizeof(T) == 8) ? &M->wgraph64 : &M->wgraph32;
+    if (!*wg && !M->no_cond_graphs) {
+      if (!build_while_graph(cs, wg, body)) M->no_cond_graphs = true;
     }
     double hv[S_NSCAL];
-    for (;;) {
+    if (*wg) {
+      // device-driven loop: one graph launch runs the iterations until convergence
+      HDG_CUDA_TRY(cudaGraphLaunch(*wg, M->stream));
+      M->launches += 1;
       HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
       HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-      if (hv[S_DONE] != 0.0) break;
-      HDG_CUDA_TRY(cudaGraphLaunch(*graph, M->stream));
-      M->launches += 3 * kGraphIters;
+      M->launches += (int64_t)(3 * kGraphIters + 1) * (int64_t)hv[S_BODIES];
+    } else {
+      if (!*graph) {
+        // capture on a private stream (the caller's may be the legacy default stream, which
+        // cannot be captured); the graph is then launched on the caller's stream
+        cudaGraph_t g;
+        HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < kGraphIters; ++it) {
+          pcg_matvec_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+          pcg_update_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
+          pcg_dir_kernel<T><<<nb, kNT, 0, cs>>>(nv, z, p, scal);
+        }
+        HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+        HDG_CUDA_TRY(cudaGraphInstantiate(graph, g, 0));
+        cudaGraphDestroy(g);
+      }
+      for (;;) {
+        HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+        HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+        if (hv[S_DONE] != 0.0) break;
+        HDG_CUDA_TRY(cudaGraphLaunch(*graph, M->stream));
+        M->launches += 3 * kGraphIters;
+      }
     }
     *iters = (int)hv[S_ITERS];
     *bad = hv[S_BAD] != 0.0;
@@ -846,6 +916,140 @@ struct Solver {
     return HDG_OK;
   }
 };
+
+// ------------------------------------------------------------------ batched graph
+// Per-problem squared norms of a trace vector: out[p] += sum over the problem's free entries.
+__global__ void prob_norms_kernel(const double* __restrict__ v, const int32_t* __restrict__ face_prob, int64_t nfc,
+                                  int d2, double* out) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nfc * d2; t += (int64_t)gridDim.x * blockDim.x) {
+    const int p = face_prob[t / d2];
+    double x = v[t] * v[t];
+    // combine lanes of the same problem (problems occupy contiguous face ranges)
+    const int p0 = __shfl_sync(0xffffffffu, p, 0);
+    const bool uniform = __all_sync(__activemask(), p == p0);
+    if (uniform && __activemask() == 0xffffffffu) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) atomicAdd(out + p, x);
+    } else {
+      atomicAdd(out + p, x);
+    }
+  }
+}
+
+// PCG scalars for the device-driven batch solve: the stopping threshold is
+// (rtol * min_p ||b_p||)^2 so that every problem of the union meets rtol (||r_p|| <= ||r||).
+__global__ void batch_scalars_kernel(double* scal, const double* bn2, int np, double rtol, int maxit, int graph_iters) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double mn = 1e300;
+  for (int p = 0; p < np; ++p) mn = fmin(mn, bn2[p] > 0.0 ? bn2[p] : mn);
+  if (!(mn < 1e300)) mn = 0.0;
+  for (int i = 0; i < S_NSCAL; ++i) scal[i] = 0.0;
+  scal[S_TOL2] = rtol * rtol * mn;
+  scal[S_MAXIT] = (double)maxit;
+  scal[S_MAXBODIES] = (double)(maxit / graph_iters + 2);
+}
+
+template <int D2>
+static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
+                        double* norms, double rtol, int maxit, double* q, double* u, double* uhat,
+                        cudaGraphNode_t* last) {
+  FaceArgs F = face_args(M);
+  const int nb = nblocks(M);
+  const int64_t nv = M->nfc * D2;
+  int rc = ensure_workspace(M, false);
+  if (rc) return rc;
+  if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = M->cap_stream;
+  cudaStream_t saved = M->stream;
+  double* scal = M->d_scal;
+  double* xD = M->d_uhatD;
+  double* phiN = M->d_uhatD + nv;
+  // A: assembly, boundary data, right-hand side, block-Jacobi, per-problem ||b_p||, PCG start
+  cudaGraph_t ga;
+  HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  M->stream = cs;
+  cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, cs);
+  cudaError_t e = (asm_precision == HDG_DF32) ? launch_assemble_df(M) : launch_assemble(M);
+  bdata_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf, M->uD, M->gN,
+                                       xD, phiN);
+  rhs_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
+                                     M->d_scal + S_NSCAL);
+  bj_kernel<D2><<<(unsigned)((M->nfc + 63) / 64), 64, 0, cs>>>(F, M->d_C, M->d_BJ, M->d_status, false);
+  cudaMemsetAsync(norms, 0, sizeof(double) * 2 * np, cs);
+  prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_b, face_prob, M->nfc, D2, norms);
+  batch_scalars_kernel<<<1, 32, 0, cs>>>(scal, norms, np, rtol, maxit, kGraphIters);
+  pcg_init_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_b, M->d_x, false, M->d_r, M->d_red, M->d_counter,
+                                                  scal);
+  pcg_precond_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, M->d_r, M->d_z, M->d_p, M->d_red, M->d_counter,
+                                                     scal);
+  M->stream = saved;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &ga);
+  if (e != cudaSuccess || e2 != cudaSuccess) return fail(HDG_ERR_CUDA, "batch graph capture (assembly/setup) failed");
+  cudaGraphNode_t na, nw, nc;
+  HDG_CUDA_TRY(cudaGraphAddChildGraphNode(&na, graph, nullptr, 0, ga));
+  cudaGraphDestroy(ga);
+  // W: device-driven PCG loop
+  cudaGraphConditionalHandle h;
+  HDG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  HDG_CUDA_TRY(cudaGraphAddNode(&nw, graph, &na, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  for (int it = 0; it < kGraphIters; ++it) {
+    pcg_matvec_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_p, M->d_q, M->d_red, M->d_counter, scal);
+    pcg_update_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_red,
+                                                      M->d_counter, scal);
+    pcg_dir_kernel<double><<<nb, kNT, 0, cs>>>(nv, M->d_z, M->d_p, scal);
+  }
+  loop_control_kernel<<<1, 32, 0, cs>>>(h, scal, S_DONE, S_BODIES, S_MAXBODIES);
+  cudaGraph_t bout;
+  HDG_CUDA_TRY(cudaStreamEndCapture(cs, &bout));
+  // C: true residual, per-problem ||r_p||, trace with Dirichlet data, recovery
+  cudaGraph_t gc;
+  HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  M->stream = cs;
+  pcg_init_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_b, M->d_x, true, M->d_q, M->d_red, M->d_counter,
+                                                  M->d_scal + S_NSCAL);
+  prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_q, face_prob, M->nfc, D2, norms + np);
+  finish_kernel<<<nb, kNT, 0, cs>>>(nv, M->d_ftype, D2, M->d_x, M->d_uhatD, uhat);
+  e = launch_recover(M, uhat, q, u);
+  M->stream = saved;
+  e2 = cudaStreamEndCapture(cs, &gc);
+  if (e != cudaSuccess || e2 != cudaSuccess) return fail(HDG_ERR_CUDA, "batch graph capture (recovery) failed");
+  HDG_CUDA_TRY(cudaGraphAddChildGraphNode(&nc, graph, &nw, 1, gc));
+  cudaGraphDestroy(gc);
+  *last = nc;
+  M->rhs_ready = false;
+  return HDG_OK;
+}
+
+int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
+                       double* norms, double rtol, int maxit, double* q, double* u, double* uhat, cudaGraphNode_t* last) {
+  switch (M->tab.d2) {
+    case 3: return record_group<3>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 6: return record_group<6>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 10: return record_group<10>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 15: return record_group<15>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+  }
+  return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
+}
+
+// iterations run by the last device-driven solve of M
+int batch_group_iterations(hdg_mesh* M, int* iters, int* status) {
+  double hv[S_NSCAL];
+  HDG_CUDA_TRY(cudaMemcpy(hv, M->d_scal, sizeof(hv), cudaMemcpyDeviceToHost));
+  *iters = (int)hv[S_ITERS];
+  int32_t st[4];
+  HDG_CUDA_TRY(cudaMemcpy(st, M->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  *status = (hv[S_BAD] != 0.0 || st[0] || st[1] || st[3]) ? 1 : 0;
+  return HDG_OK;
+}
 
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0, double* uhat, int* iters,
                 double* relres) {
