@@ -389,6 +389,61 @@ def profile_k1(s_sub, launches=2, asm="df32"):
     print(json.dumps({"profile_k1": {"nelt": M.nelt, "launches": launches, "asm": asm}}))
 
 
+def run_batch(args):
+    """64 independent cube problems (s ~ U{8..24}, k ~ U{1..4}, kappa = 10^U(-1,1), c ~ U[0,5],
+    Dirichlet everywhere, seed 4) solved as one batch: one CUDA graph launch (double-float
+    assembly, FP64 PCG to 1e-10 for every problem, recovery).  Returns elements/s."""
+    import torch
+
+    from paper_1305_1489_gb300 import HDG_DF32, HDGBatch, build
+    from workloads import boundary_faces, kuhn_cube
+    from workloads.problems import batch_problems
+
+    build()
+    probs = batch_problems(args.batch_n)
+    meshes = []
+    for p in probs:
+        c, e = kuhn_cube(p.s)
+        d, n = boundary_faces(c, e, p.classify)
+        meshes.append((c, e, d, n, p.k))
+    B = HDGBatch(meshes)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    nelt = 0
+    for G in B.groups:
+        M = G["mesh"]
+        nelt += M.nelt
+        X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+        FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
+        kap, cq, fq = (np.zeros_like(X) for _ in range(3))
+        uD = np.zeros_like(FX)
+        for i, p in enumerate(G["probs"]):
+            pr = probs[p]
+            es = slice(G["elem_off"][i], G["elem_off"][i + 1])
+            fs = slice(G["face_off"][i], G["face_off"][i + 1])
+            kap[es], cq[es], fq[es] = pr.kappa(X[es], Y[es], Z[es]), pr.c(X[es], Y[es], Z[es]), pr.f(X[es], Y[es], Z[es])
+            uD[fs] = pr.uD(FX[fs], FY[fs], FZ[fs])
+        M.set_coefficients(dev(kap), dev(cq), dev(fq))
+        M.set_boundary_data(dev(uD))
+    relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)  # warm-up + graph build
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.batch_reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(B.stream)
+        relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)
+        b.record(B.stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    out = {"problems": len(probs), "elements": int(nelt), "groups": [
+        {"k": G["k"], "problems": int(len(G["probs"])), "elements": int(G["mesh"].nelt), "iterations": int(it)}
+        for G, it in zip(B.groups, iters)],
+        "ms_per_batch": ms, "elements_per_s": nelt / (ms / 1e3), "max_relres": float(relres.max()),
+        "graph_launches_per_batch": 1}
+    B.close()
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -416,10 +471,17 @@ def main():
     ap.add_argument("--asm", default="df32", choices=["df32", "fp64"],
                     help="assembly arithmetic: double-float on the FP32 pipe or native FP64")
     ap.add_argument("--inner-rtol", type=float, default=1e-6, help="FP32 inner solve tolerance")
+    ap.add_argument("--batch", action="store_true", help="also time the 64-problem mixed-degree batch")
+    ap.add_argument("--batch-only", action="store_true", help="time only the batch and exit")
+    ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
     args = ap.parse_args()
     if args.profile_k1:
         profile_k1(args.profile_k1, asm=args.asm)
+        return
+    if args.batch_only:
+        print(json.dumps({"batch": run_batch(args)}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -438,6 +500,8 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and not args.only_steps:
             out["cpu_baseline"] = oracle_baseline(sample_elems=args.ref_sample, steps=1, warmup=1)
+        if args.batch and world == 1:
+            out["batch"] = run_batch(args)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

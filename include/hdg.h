@@ -186,6 +186,37 @@ int hdg_recover(hdg_mesh* mesh, const double* uhat, double* q, double* u);
  * hdg_set_coefficients.                                                                   */
 int hdg_postprocess(hdg_mesh* mesh, const double* q, const double* u, double* ustar);
 
+/* ------------------------------------------------------------------ batched problems
+ * Many independent problems of mixed degree solved together.  Problems of equal degree are
+ * merged into one disjoint-union mesh (a "group"), so each phase is one launch per group, and
+ * the whole batch (assembly + condensation, boundary data, block-Jacobi PCG run on the device
+ * until convergence, recovery) is one CUDA graph launch with one branch per group.
+ * hdg_batch_create: per problem p, host arrays as for hdg_mesh_create (coords[p] [nver[p]][3],
+ *   elems[p] [nelt[p]][4], dir[p] [ndir[p]][3], neu[p] [nneu[p]][3]) and degree k[p] in 1..4.
+ * hdg_batch_group: the union mesh of group g (owned by the batch: set its coefficients and
+ *   boundary data with hdg_set_coefficients / hdg_set_boundary_data, query its nodes with
+ *   hdg_quadrature_nodes), its degree, its problems (prob_ids [np]) and their element and
+ *   face ranges in the union (elem_off, face_off [np+1]); any output pointer may be NULL.
+ * hdg_batch_run: precision HDG_FP64 or HDG_DF32 (assembly arithmetic), FP64 PCG iterated
+ *   until ||r|| <= rtol min_p ||b_p|| (so every problem meets rtol).  relres [nprob] host:
+ *   per-problem ||b_p - H_p u_p|| / ||b_p||; iters [ngroups] host.  HDG_ERR_NOT_CONVERGED if
+ *   some problem misses rtol within maxit.
+ * hdg_batch_solution: device pointers (owned by the batch) to the group's u_hat [nfc][d2],
+ *   q [nelt][3][n], u [nelt][n] in union numbering.                                        */
+typedef struct hdg_batch hdg_batch;
+int hdg_batch_create(int nprob, const double* const* coords, const int64_t* nver,
+                     const int32_t* const* elems, const int64_t* nelt,
+                     const int32_t* const* dir, const int64_t* ndir,
+                     const int32_t* const* neu, const int64_t* nneu, const int* k,
+                     void* stream, hdg_batch** out);
+int hdg_batch_num_groups(const hdg_batch* batch, int* ngroups);
+int hdg_batch_group(const hdg_batch* batch, int g, hdg_mesh** mesh, int* k, int* np,
+                    int32_t* prob_ids, int64_t* elem_off, int64_t* face_off);
+int hdg_batch_run(hdg_batch* batch, int precision, double rtol, int maxit, double* relres,
+                  int* iters);
+int hdg_batch_solution(const hdg_batch* batch, int g, double** uhat, double** q, double** u);
+int hdg_batch_destroy(hdg_batch* batch);
+
 /* Copy the message of the calling thread's last error into buf (NUL-terminated). */
 int hdg_last_error(char* buf, size_t len);
 

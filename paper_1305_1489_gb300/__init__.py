@@ -150,12 +150,14 @@ def hdg_launch_count(h):
 class HDGMesh:
     """Owns one hdg_mesh handle; tensors passed in are kept alive while the library borrows them."""
 
-    def __init__(self, coords, elements, dirichlet, neumann, k, stream=None):
+    def __init__(self, coords, elements, dirichlet, neumann, k, stream=None, _handle=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("HDGMesh needs a CUDA device: libhdg has no CPU path")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self._h = hdg_mesh_create(coords, elements, dirichlet, neumann, k, self.stream.cuda_stream)
+        self._owned = _handle is None
+        self._h = _handle if _handle is not None else hdg_mesh_create(coords, elements, dirichlet, neumann, k,
+                                                                     self.stream.cuda_stream)
         self.info = hdg_mesh_get_info(self._h)
         for key in ("nelt", "nfc", "k", "n", "d2", "m", "n1", "nq", "nf"):
             setattr(self, key, self.info[key])
@@ -163,7 +165,8 @@ class HDGMesh:
 
     def close(self):
         if getattr(self, "_h", None) is not None:
-            hdg_mesh_destroy(self._h)
+            if getattr(self, "_owned", True):
+                hdg_mesh_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -263,3 +266,94 @@ class HDGMesh:
     @property
     def launches(self):
         return hdg_launch_count(self._h)
+
+
+# ---------------------------------------------------------------- batched problems
+class HDGBatch:
+    """Many independent problems solved together (hdg_batch_*): problems of equal degree form
+    one union mesh per group; one CUDA graph launch runs the whole batch."""
+
+    def __init__(self, meshes, stream=None):
+        """meshes: list of (coords, elements, dirichlet, neumann, k)."""
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.nprob = len(meshes)
+        arrs = []
+        for (c, e, d, n, k) in meshes:
+            arrs.append((np.ascontiguousarray(c, np.float64), np.ascontiguousarray(e, np.int32),
+                         np.ascontiguousarray(np.asarray(d).reshape(-1, 3), np.int32),
+                         np.ascontiguousarray(np.asarray(n).reshape(-1, 3), np.int32), int(k)))
+        self._arrs = arrs
+        N = self.nprob
+        P = C.c_void_p
+        cp = (P * N)(*[a[0].ctypes.data for a in arrs])
+        ep = (P * N)(*[a[1].ctypes.data for a in arrs])
+        dp = (P * N)(*[a[2].ctypes.data if len(a[2]) else None for a in arrs])
+        npp = (P * N)(*[a[3].ctypes.data if len(a[3]) else None for a in arrs])
+        nv = (C.c_int64 * N)(*[len(a[0]) for a in arrs])
+        ne = (C.c_int64 * N)(*[len(a[1]) for a in arrs])
+        nd = (C.c_int64 * N)(*[len(a[2]) for a in arrs])
+        nn = (C.c_int64 * N)(*[len(a[3]) for a in arrs])
+        kk = (C.c_int * N)(*[a[4] for a in arrs])
+        h = C.c_void_p()
+        lib = _lib.load()
+        _lib.check(lib.hdg_batch_create(N, cp, nv, ep, ne, dp, nd, npp, nn, kk, C.c_void_p(self.stream.cuda_stream),
+                                        C.byref(h)))
+        self._h = h
+        ng = C.c_int(0)
+        _lib.check(lib.hdg_batch_num_groups(h, C.byref(ng)))
+        self.groups = []
+        for g in range(ng.value):
+            mh = C.c_void_p()
+            k = C.c_int(0)
+            npg = C.c_int(0)
+            _lib.check(lib.hdg_batch_group(h, g, C.byref(mh), C.byref(k), C.byref(npg), None, None, None))
+            ids = np.zeros(npg.value, np.int32)
+            eo = np.zeros(npg.value + 1, np.int64)
+            fo = np.zeros(npg.value + 1, np.int64)
+            _lib.check(lib.hdg_batch_group(h, g, None, None, None, ids.ctypes.data, eo.ctypes.data, fo.ctypes.data))
+            mesh = HDGMesh(None, None, None, None, k.value, stream=self.stream, _handle=mh)
+            self.groups.append(dict(mesh=mesh, k=k.value, probs=ids, elem_off=eo, face_off=fo))
+
+    def run(self, precision=HDG_FP64, rtol=1e-10, maxit=20000, raise_on_fail=True):
+        relres = np.zeros(self.nprob)
+        iters = np.zeros(len(self.groups), np.int32)
+        code = _lib.load().hdg_batch_run(self._h, precision, float(rtol), int(maxit), relres.ctypes.data,
+                                         iters.ctypes.data)
+        if code != 0 and raise_on_fail:
+            raise HDGError(code, _lib.last_error())
+        return relres, iters
+
+    def solution(self, g):
+        """(u_hat, q, u) of group g in union numbering, copied into new CUDA tensors."""
+        G = self.groups[g]
+        M = G["mesh"]
+        uh, q, u = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _lib.check(_lib.load().hdg_batch_solution(self._h, g, C.byref(uh), C.byref(q), C.byref(u)))
+        out = []
+        for ptr, shape in ((uh, (M.nfc, M.d2)), (q, (M.nelt, 3, M.n)), (u, (M.nelt, M.n))):
+            out.append(_device_view(ptr.value, int(np.prod(shape))).view(shape).clone())
+        return tuple(out)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            for G in self.groups:
+                G["mesh"]._h = None
+            _lib.load().hdg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view(ptr, numel):
+    """A float64 CUDA tensor aliasing library-owned device memory (no copy)."""
+    import torch
+
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (numel,), "typestr": "<f8", "data": (ptr, False), "version": 3,
+                                    "strides": None}
+    return torch.as_tensor(_Arr(), device="cuda")

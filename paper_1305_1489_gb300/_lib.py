@@ -53,6 +53,12 @@ _SIGS = {
     "hdg_last_error": [C.c_char_p, C.c_size_t],
     "hdg_launch_count": [P],
     "hdg_host_table": [C.c_int, C.c_char_p, P, I64, C.POINTER(I64)],
+    "hdg_batch_create": [C.c_int, P, P, P, P, P, P, P, P, P, P, C.POINTER(P)],
+    "hdg_batch_num_groups": [P, C.POINTER(C.c_int)],
+    "hdg_batch_group": [P, C.c_int, C.POINTER(P), C.POINTER(C.c_int), C.POINTER(C.c_int), P, P, P],
+    "hdg_batch_run": [P, C.c_int, C.c_double, C.c_int, P, P],
+    "hdg_batch_solution": [P, C.c_int, C.POINTER(P), C.POINTER(P), C.POINTER(P)],
+    "hdg_batch_destroy": [P],
     "hdg_host_expand_mesh": [P, I64, P, I64, P, I64, P, I64, C.POINTER(I64), P, P, P],
 }
 

@@ -376,13 +376,23 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
   }
   __syncthreads();
 
-  // recovery record: R_u|r_u [n][m+1], Y [n][m], MC [3][n][n], normals [4][3]
+  // recovery record, column-major so that the recovery kernel reads it with unit stride:
+  // [R_u | r_u]^T [m+1][n], Y^T [m][n], MC_*^T [3][n][n], normals [4][3]
   double* R = A.rec + Ke * (int64_t)D::rec;
-  for (int t = tid; t < n * (m + 1); t += NT) R[t] = Gt[t];
+  for (int t = tid; t < n * (m + 1); t += NT) {
+    const int r = t / n, i = t - r * n;
+    R[t] = Gt[i * (m + 1) + r];
+  }
   R += n * (m + 1);
-  for (int t = tid; t < n * m; t += NT) R[t] = V[t];
+  for (int t = tid; t < n * m; t += NT) {
+    const int r = t / n, l = t - r * n;
+    R[t] = V[l * m + r];
+  }
   R += n * m;
-  for (int t = tid; t < 3 * n * n; t += NT) R[t] = W[t];
+  for (int t = tid; t < 3 * n * n; t += NT) {
+    const int st = t / (n * n), rem = t - st * n * n, c = rem / n, l = rem - c * n;
+    R[t] = W[st * n * n + l * n + c];
+  }
   R += 3 * n * n;
   if (tid < 12) R[tid] = s_nrm[tid / 3][tid % 3];
   if (tid == 0) {

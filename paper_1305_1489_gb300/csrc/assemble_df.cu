@@ -330,12 +330,22 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_df_kernel(A
   }
   __syncthreads();
 
+  // recovery record, column-major (as in assemble.cu)
   double* R = A.rec + Ke * (int64_t)D::rec;
-  for (int t = tid; t < n * (m + 1); t += NT) R[t] = df_to_double(Gt[t]);
+  for (int t = tid; t < n * (m + 1); t += NT) {
+    const int r = t / n, i = t - r * n;
+    R[t] = df_to_double(Gt[i * (m + 1) + r]);
+  }
   R += n * (m + 1);
-  for (int t = tid; t < n * m; t += NT) R[t] = df_to_double(V[t]);
+  for (int t = tid; t < n * m; t += NT) {
+    const int r = t / n, l = t - r * n;
+    R[t] = df_to_double(V[l * m + r]);
+  }
   R += n * m;
-  for (int t = tid; t < 3 * n * n; t += NT) R[t] = df_to_double(W[t]);
+  for (int t = tid; t < 3 * n * n; t += NT) {
+    const int st = t / (n * n), rem = t - st * n * n, c = rem / n, l = rem - c * n;
+    R[t] = df_to_double(W[st * n * n + l * n + c]);
+  }
   R += 3 * n * n;
   if (tid < 12) R[tid] = df_to_double(s_nrm[tid / 3][tid % 3]);
   if (tid == 0) {

@@ -15,7 +15,7 @@ struct Dims {
   static constexpr int nq = (K + 2) * (K + 2) * (K + 2);     // volume nodes
   static constexpr int nf = (K + 2) * (K + 2);               // face nodes
   static constexpr int n1 = (K + 2) * (K + 3) * (K + 4) / 6; // dim P_{k+1}(K)
-  // per-element recovery record: R_u [n][m+1] | Y [n][m] | MC [3][n][n] | normals [12]
+  // per-element recovery record, column-major: [R_u|r_u]^T [m+1][n] | Y^T [m][n] | MC^T [3][n][n] | normals [12]
   static constexpr int rec = n * (m + 1) + n * m + 3 * n * n + 12;
 };
 

@@ -110,68 +110,73 @@ cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst) {
 }
 
 // ----------------------------------------------------------------------- recovery
-// u = R_u u_dK + r_u;  q_* = MC_* u - Y (n_* o u_dK)     (eq. 5.3 through the factors of K1)
-template <int K, int NT>
-__global__ void __launch_bounds__(NT) recover_kernel(const double* __restrict__ rec,
-                                                     const int32_t* __restrict__ fbe,
-                                                     const double* __restrict__ uhat, int64_t nelt,
-                                                     double* __restrict__ q, double* __restrict__ u) {
+// u = R_u u_dK + r_u;  q_* = MC_* u - Y (n_* o u_dK)   (eq. 5.3 through the factors of K1).
+// One warp per element; the column-major record makes every column read a unit-stride
+// access across the lanes, and all columns are issued before they are consumed.
+constexpr int kRecWarps = 4;
+
+template <int K>
+__global__ void __launch_bounds__(32 * kRecWarps) recover_kernel(const double* __restrict__ rec,
+                                                                const int32_t* __restrict__ fbe,
+                                                                const double* __restrict__ uhat, int64_t nelt,
+                                                                double* __restrict__ q, double* __restrict__ u) {
   using D = Dims<K>;
   constexpr int n = D::n, m = D::m, d2 = D::d2;
-  __shared__ double uh[m], us[n], nrm[12];
-  const int64_t Ke = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double suh[kRecWarps][m], su[kRecWarps][n];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t Ke = (int64_t)blockIdx.x * kRecWarps + warp;
+  if (Ke >= nelt) return;
   const double* R = rec + Ke * (int64_t)D::rec;
-  const double* Y = R + n * (m + 1);
-  const double* MC = Y + n * m;
-  for (int t = tid; t < m; t += NT) {
-    const int f = fbe[Ke * 4 + t / d2];
-    uh[t] = uhat[(int64_t)f * d2 + (t % d2)];
-  }
-  if (tid < 12) nrm[tid] = MC[3 * n * n + tid];
-  __syncthreads();
-  for (int i = warp; i < n; i += NT / 32) {
-    double s = 0.0;
-    for (int r = lane; r < m + 1; r += 32) s = fma(R[i * (m + 1) + r], r < m ? uh[r] : 1.0, s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      us[i] = s;
-      u[Ke * n + i] = s;
+  const double* YT = R + n * (m + 1);
+  const double* MCT = YT + n * m;
+  const double* nrm = MCT + 3 * n * n;
+  for (int t = lane; t < m; t += 32) suh[warp][t] = __ldg(uhat + (int64_t)__ldg(fbe + Ke * 4 + t / d2) * d2 + (t % d2));
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    double s0 = __ldg(R + m * n + i), s1 = 0.0;
+#pragma unroll 8
+    for (int r = 0; r < m; r += 2) {
+      s0 = fma(__ldg(R + r * n + i), suh[warp][r], s0);
+      if (r + 1 < m) s1 = fma(__ldg(R + (r + 1) * n + i), suh[warp][r + 1], s1);
     }
+    su[warp][i] = s0 + s1;
+    u[Ke * n + i] = s0 + s1;
   }
-  __syncthreads();
-  for (int l = warp; l < n; l += NT / 32) {
+  __syncwarp();
+  double nv[12];
+#pragma unroll
+  for (int t = 0; t < 12; ++t) nv[t] = __ldg(nrm + t);
+  for (int l = lane; l < n; l += 32) {
     double s[3] = {0.0, 0.0, 0.0};
-    for (int r = lane; r < m; r += 32) {
-      const double yu = Y[l * m + r] * uh[r];
+#pragma unroll 4
+    for (int c = 0; c < n; ++c) {
+      const double uc = su[warp][c];
+      s[0] = fma(__ldg(MCT + (0 * n + c) * n + l), uc, s[0]);
+      s[1] = fma(__ldg(MCT + (1 * n + c) * n + l), uc, s[1]);
+      s[2] = fma(__ldg(MCT + (2 * n + c) * n + l), uc, s[2]);
+    }
+#pragma unroll 4
+    for (int r = 0; r < m; ++r) {
+      const double yu = __ldg(YT + r * n + l) * suh[warp][r];
       const int fl = r / d2;
-      s[0] = fma(-yu, nrm[3 * fl + 0], s[0]);
-      s[1] = fma(-yu, nrm[3 * fl + 1], s[1]);
-      s[2] = fma(-yu, nrm[3 * fl + 2], s[2]);
+      s[0] = fma(-yu, nv[3 * fl + 0], s[0]);
+      s[1] = fma(-yu, nv[3 * fl + 1], s[1]);
+      s[2] = fma(-yu, nv[3 * fl + 2], s[2]);
     }
-    for (int c = lane; c < n; c += 32) {
-      const double uc = us[c];
-      s[0] = fma(MC[(0 * n + l) * n + c], uc, s[0]);
-      s[1] = fma(MC[(1 * n + l) * n + c], uc, s[1]);
-      s[2] = fma(MC[(2 * n + l) * n + c], uc, s[2]);
-    }
-#pragma unroll
-    for (int st = 0; st < 3; ++st)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s[st] += __shfl_xor_sync(0xffffffffu, s[st], o);
-    if (lane == 0)
-      for (int st = 0; st < 3; ++st) q[(Ke * 3 + st) * n + l] = s[st];
+    q[(Ke * 3 + 0) * n + l] = s[0];
+    q[(Ke * 3 + 1) * n + l] = s[1];
+    q[(Ke * 3 + 2) * n + l] = s[2];
   }
 }
 
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
-  const unsigned g = (unsigned)M->nelt;
+  const unsigned g = (unsigned)((M->nelt + kRecWarps - 1) / kRecWarps);
+  const int nt = 32 * kRecWarps;
   switch (M->k) {
-    case 1: recover_kernel<1, 64><<<g, 64, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
-    case 2: recover_kernel<2, 64><<<g, 64, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
-    case 3: recover_kernel<3, 128><<<g, 128, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
-    case 4: recover_kernel<4, 128><<<g, 128, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 1: recover_kernel<1><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 2: recover_kernel<2><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 3: recover_kernel<3><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 4: recover_kernel<4><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
     default: return cudaErrorInvalidValue;
   }
   M->launches++;

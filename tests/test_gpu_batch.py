@@ -1,0 +1,69 @@
+"""Batched solve of independent problems of mixed degree (one CUDA graph launch) against
+the oracle solving each problem on its own."""
+import numpy as np
+import pytest
+
+from oracle import hdg as ohdg
+from workloads import get_problem
+from workloads.problems import sinsinsin
+
+from hdg_cases import make_mesh, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_1489_gb300 import build
+    build()
+
+
+def _problems():
+    probs = [sinsinsin("b0", 2, 1, kappa0=0.3, c0=2.0), sinsinsin("b1", 3, 2, kappa0=4.0, c0=0.0),
+             sinsinsin("b2", 2, 1, kappa0=1.5, c0=0.5), get_problem("cube16_k3").at(s=2, k=2),
+             sinsinsin("b4", 1, 3, kappa0=0.7, c0=1.0), sinsinsin("b5", 2, 3, kappa0=9.0, c0=3.0)]
+    probs[3].jitter, probs[3].seed = 0.1, 5
+    return probs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df32"])
+def test_batch_matches_individual_solves(prec):
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, HDGBatch
+    probs = _problems()
+    meshes = [make_mesh(p) for p in probs]
+    B = HDGBatch([(c, e, d, n, p.k) for (c, e, d, n), p in zip(meshes, probs)])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    for G in B.groups:
+        M = G["mesh"]
+        X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+        FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
+        kap, cq, fq = (np.zeros_like(X) for _ in range(3))
+        uD = np.zeros_like(FX)
+        gN = np.zeros((3,) + FX.shape)
+        for i, p in enumerate(G["probs"]):
+            pr = probs[p]
+            es = slice(G["elem_off"][i], G["elem_off"][i + 1])
+            fs = slice(G["face_off"][i], G["face_off"][i + 1])
+            kap[es], cq[es], fq[es] = pr.kappa(X[es], Y[es], Z[es]), pr.c(X[es], Y[es], Z[es]), pr.f(X[es], Y[es], Z[es])
+            uD[fs] = pr.uD(FX[fs], FY[fs], FZ[fs])
+            if pr.gN is not None:
+                gN[:, fs] = np.stack(pr.gN(FX[fs], FY[fs], FZ[fs]))
+        M.set_coefficients(dev(kap), dev(cq), dev(fq))
+        M.set_boundary_data(dev(uD), dev(gN))
+    relres, iters = B.run(precision=HDG_DF32 if prec == "df32" else HDG_FP64, rtol=1e-12, maxit=5000)
+    assert np.all(relres <= 1e-12)
+    for g, G in enumerate(B.groups):
+        uhat, q, u = (t.cpu().numpy() for t in B.solution(g))
+        for i, p in enumerate(G["probs"]):
+            c, e, d, n = meshes[p]
+            ref = ohdg.solve_problem(probs[p], c, e, d, n)
+            es = slice(G["elem_off"][i], G["elem_off"][i + 1])
+            fs = slice(G["face_off"][i], G["face_off"][i + 1])
+            assert rel(uhat[fs], ref["uhat"]) < 1e-9, (p, rel(uhat[fs], ref["uhat"]))
+            assert rel(u[es], ref["u"]) < 1e-9
+            assert rel(q[es], ref["q"]) < 1e-9
+    # a second launch of the same graph gives the same answer
+    relres2, _ = B.run(precision=HDG_DF32 if prec == "df32" else HDG_FP64, rtol=1e-12, maxit=5000)
+    assert np.allclose(relres, relres2, rtol=0, atol=1e-15)
+    B.close()
