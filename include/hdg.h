@@ -169,6 +169,60 @@ int hdg_solve_trace(hdg_mesh* mesh, int precision, double rtol, int maxit, const
 int hdg_solve_trace_noalloc(hdg_mesh* mesh, double rtol, int maxit, const double* x0,
                             double* uhat, int* iters, double* relres);
 
+/* y = H x on the free faces (0 on Dirichlet faces), the trace operator of eq. 6.5 applied
+ * matrix-free; x, y device f64 [nfc][d2].                                                 */
+int hdg_trace_apply(hdg_mesh* mesh, const double* x, double* y);
+
+/* ------------------------------------------------------------------ learned initial guess
+ * (not in the paper).  A continuous piecewise-linear coarse field with values c [nc] at
+ * coarse nodes is given through per-vertex interpolation: the value at mesh vertex v is
+ * sum_{j<4} weights[4v+j] c[nodes[4v+j]] (nodes < 0 are skipped); nodes int32 and weights
+ * f64 [nver][4], device.  On meshes nested in the coarse mesh the field is linear on each
+ * element, so its trace on a face is exactly u_hat_e = T [V(w1) V(w2) V(w3)] with
+ * T = (varpi . D)^T Xi (eq. 6.3).
+ * hdg_prolong:  uhat [nfc][d2] = Pi c (0 on Dirichlet faces).
+ * hdg_restrict: c [nc] = Pi^T y (adjoint of hdg_prolong over the free faces).
+ * hdg_coarse_solve: the coarse Galerkin problem (Pi^T H Pi) c = Pi^T b by matrix-free CG in
+ *   FP64 to rtol (relative to Pi^T b); after hdg_assemble_condense and the boundary data.
+ *   It allocates temporary device buffers.                                                */
+int hdg_prolong(hdg_mesh* mesh, const int32_t* nodes, const double* weights, const double* coarse,
+                double* uhat);
+int hdg_restrict(hdg_mesh* mesh, const int32_t* nodes, const double* weights, int64_t nc,
+                 const double* y, double* coarse);
+int hdg_coarse_solve(hdg_mesh* mesh, const int32_t* nodes, const double* weights, int64_t nc,
+                     double* c, double rtol, int maxit, int* iters, double* relres);
+/* hdg_fourier_field: sampled coefficient fields for training and evaluating the network.
+ * out[i] = g(x_i), or exp(g(x_i)) if exponentiate, for the random Fourier field
+ *   g(x) = sigma M^-1/2 sum_m (xi_m cos(omega_m . x) + eta_m sin(omega_m . x)),
+ * omega [M][3], amps [2M] = (xi_1..xi_M, eta_1..eta_M); X, Y, Z, out [n]; all device, FP64.
+ * 1 <= M <= 1024.  (Input generation for the learned guess; no counterpart in the paper.)  */
+int hdg_fourier_field(int64_t n, const double* X, const double* Y, const double* Z, int M,
+                      const double* omega, const double* amps, double sigma, int exponentiate,
+                      double* out, void* stream);
+/* hdg_coarse_guess: x0 [nfc][d2] = alpha Pi c with alpha = (w.b)/(w.Hw), w = Pi c (the
+ * energy-optimal multiple; a one-vector coarse correction).  alpha returned on the host.  */
+int hdg_coarse_guess(hdg_mesh* mesh, const int32_t* nodes, const double* weights,
+                     const double* coarse, double* x0, double* alpha);
+
+/* Kernels of the small network that maps random-field parameters to coarse solutions
+ * (FP32, device pointers, enqueued on `stream`):
+ * hdg_nn_gemm: C[M][N] = act(sum_k A(m,k) B(k,n) + beta C + bias[n]) with
+ *   A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C row stride ldc, bias [N] or
+ *   NULL, act 0 (identity) or 1 (tanh).
+ * hdg_nn_tanh_bwd: dY[i] *= 1 - Y[i]^2.   hdg_nn_colsum: db[n] = sum_m dZ[m][n].
+ * hdg_nn_mse: grad = 2 (pred - target) / n; loss_partial [64] sums to mean((pred - target)^2).
+ * hdg_nn_adam: one Adam step (Kingma and Ba 2015) at step number `step` >= 1.           */
+int hdg_nn_gemm(int M, int N, int K, const float* A, int sam, int sak, const float* B, int sbk,
+                int sbn, float* C, int ldc, float beta, const float* bias, int act, void* stream);
+int hdg_nn_tanh_bwd(int64_t n, const float* Y, float* dY, void* stream);
+/* hdg_nn_to_f64: y[i] = (double) x[i] (network output -> coarse coefficients).             */
+int hdg_nn_to_f64(int64_t n, const float* x, double* y, void* stream);
+int hdg_nn_colsum(int M, int N, const float* dZ, float* db, void* stream);
+int hdg_nn_mse(int64_t n, const float* pred, const float* target, float* grad,
+               float* loss_partial, void* stream);
+int hdg_nn_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1,
+                float b2, float eps, int step, void* stream);
+
 /* Relative tolerance of each FP32 inner solve of the HDG_MIXED_FP32 trace solve (default
  * 1e-4): every outer FP64 refinement step asks the inner PCG for this residual reduction.  */
 int hdg_set_inner_tolerance(hdg_mesh* mesh, double rtol);

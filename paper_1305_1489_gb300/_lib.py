@@ -47,6 +47,19 @@ _SIGS = {
     "hdg_solve_trace": [P, C.c_int, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_trace_residual": [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "hdg_set_inner_tolerance": [P, C.c_double],
+    "hdg_trace_apply": [P, P, P],
+    "hdg_prolong": [P, P, P, P, P],
+    "hdg_restrict": [P, P, P, I64, P, P],
+    "hdg_coarse_solve": [P, P, P, I64, P, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "hdg_coarse_guess": [P, P, P, P, P, C.POINTER(C.c_double)],
+    "hdg_fourier_field": [I64, P, P, P, C.c_int, P, P, C.c_double, C.c_int, P, P],
+    "hdg_nn_gemm": [C.c_int, C.c_int, C.c_int, P, C.c_int, C.c_int, P, C.c_int, C.c_int, P, C.c_int, C.c_float, P,
+                    C.c_int, P],
+    "hdg_nn_tanh_bwd": [I64, P, P, P],
+    "hdg_nn_to_f64": [I64, P, P, P],
+    "hdg_nn_colsum": [C.c_int, C.c_int, P, P, P],
+    "hdg_nn_mse": [I64, P, P, P, P, P],
+    "hdg_nn_adam": [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P],
     "hdg_solve_trace_noalloc": [P, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_recover": [P, P, P, P],
     "hdg_postprocess": [P, P, P, P],

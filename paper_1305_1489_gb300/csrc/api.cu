@@ -77,7 +77,7 @@ static void release(hdg_mesh* M) {
                   M->d_p32, M->d_q32, M->dt.P, M->dt.Pd, M->dt.Chat, M->dt.S, M->dt.E, M->dt.vol_w, M->dt.lam,
                   M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
                   M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
-                  M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df};
+                  M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
@@ -263,6 +263,11 @@ int hdg_set_inner_tolerance(hdg_mesh* M, double rtol) {
   if (!M || !(rtol > 0) || !(rtol < 1)) return fail(HDG_ERR_ARG, "inner tolerance must be in (0, 1)");
   M->inner_rtol = rtol;
   return HDG_OK;
+}
+
+int hdg_trace_apply(hdg_mesh* M, const double* x, double* y) {
+  if (!M || !x || !y) return fail(HDG_ERR_ARG, "NULL argument");
+  return trace_apply(M, x, y);
 }
 
 int hdg_trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {

@@ -70,6 +70,8 @@ struct hdg_mesh {
   // device mesh
   double* d_vx = nullptr;         // [12][nelt] SoA: x1..x4, y1..y4, z1..z4
   double* d_fvx = nullptr;        // [9][nfc]   SoA: sorted face vertices x1..x3, y1..y3, z1..z3
+  int32_t* d_fverts = nullptr;    // [nfc][3]   sorted face vertex numbers (coarse prolongation)
+  double* d_Tproj = nullptr;      // [d2][3]    (varpi . D)^T Xi: linear face data -> face basis
   int32_t* d_facebyele = nullptr; // [nelt][4]
   int32_t* d_perm = nullptr;      // [nelt][4]
   int32_t* d_owner = nullptr;     // [nfc][2]   4*K + l of the (up to) two elements, -1 if none
@@ -130,6 +132,7 @@ cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, do
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0,
                 double* uhat, int* iters, double* relres);
 int trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm);
+int trace_apply(hdg_mesh* M, const double* x, double* y);
 int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
                        double* norms, double rtol, int maxit, double* q, double* u, double* uhat, cudaGraphNode_t* last);
 int batch_group_iterations(hdg_mesh* M, int* iters, int* status);

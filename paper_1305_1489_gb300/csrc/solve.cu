@@ -569,6 +569,22 @@ __global__ void bicg_x_kernel(FaceArgs F, BicgVecs V, double* red, unsigned int*
   }
 }
 
+// y = H x on the free faces, 0 on Dirichlet faces
+template <int D2>
+__global__ void apply_kernel(FaceArgs F, const double* __restrict__ C, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    y[T_.t] = (F.ftype[T_.e] != 1) ? face_apply<double, D2>(C, x, F, T_.e, T_.a) : 0.0;
+  }
+}
+
+// zero the Dirichlet entries of a caller's initial guess (the unknowns are the free faces)
+__global__ void mask_dirichlet_kernel(int64_t ntot, const int32_t* ftype, int d2, double* x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x)
+    if (ftype[t / d2] == 1) x[t] = 0.0;
+}
+
 __global__ void finish_kernel(int64_t ntot, const int32_t* ftype, int d2, const double* x, const double* xD,
                               double* uhat) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x)
@@ -826,7 +842,11 @@ struct Solver {
     int total_it = 0;
     bool converged = false, bad = false;
     double rnorm = 0.0;
-    if (x0) HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
+    if (x0) {
+      HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
+      mask_dirichlet_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, D2, M->d_x);
+      M->launches++;
+    }
     if (M->beta_q) {
       // non-symmetric trace matrix (convection): block-Jacobi BiCGStab in FP64
       if (mixed) return fail(HDG_ERR_UNSUPPORTED, "the mixed-precision solve is for symmetric (beta = 0) problems");
@@ -900,6 +920,13 @@ struct Solver {
     if (!converged)
       return fail(HDG_ERR_NOT_CONVERGED, "trace solve reached maxit with relative residual " +
                                              std::to_string(bnorm > 0 ? rnorm / bnorm : 0.0));
+    return HDG_OK;
+  }
+
+  static int apply(hdg_mesh* M, const double* x, double* y) {
+    apply_kernel<D2><<<nblocks(M), kNT, 0, M->stream>>>(face_args(M), M->d_C, x, y);
+    M->launches++;
+    HDG_CUDA_TRY(cudaGetLastError());
     return HDG_OK;
   }
 
@@ -1061,6 +1088,17 @@ int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double
     case 6: return Solver<6>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
     case 10: return Solver<10>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
     case 15: return Solver<15>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
+  }
+  return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
+}
+
+int trace_apply(hdg_mesh* M, const double* x, double* y) {
+  if (!M->assembled) return fail(HDG_ERR_STATE, "operator before hdg_assemble_condense");
+  switch (M->tab.d2) {
+    case 3: return Solver<3>::apply(M, x, y);
+    case 6: return Solver<6>::apply(M, x, y);
+    case 10: return Solver<10>::apply(M, x, y);
+    case 15: return Solver<15>::apply(M, x, y);
   }
   return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }

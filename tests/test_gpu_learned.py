@@ -1,0 +1,173 @@
+"""The learned initial guess on the GPU: network kernels against the FP64 network oracle,
+the random-field sampler against its definition, the coarse prolongation / Galerkin solve
+against the oracle's trace system, and the gain of the trained network over the zero start.
+"""
+import numpy as np
+import pytest
+
+from oracle import hdg as ohdg
+from oracle import mlp as omlp
+from oracle.geometry import ExpandedMesh
+from workloads import kuhn_coarse_interpolation
+from workloads.problems import cube32_k2_grf, grf_field, grf_frequencies, grf_sample
+
+from hdg_cases import gpu_setup, make_mesh, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_1489_gb300 import build
+    build()
+
+
+def _f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.mark.parametrize("sizes,batch", [([5, 7, 6, 4], 9), ([70, 45, 33], 37)])
+def test_network_forward_backward_match_oracle(sizes, batch):
+    from paper_1305_1489_gb300.learned import MLP
+    rng = np.random.default_rng(1)
+    params = [p + 0.05 * rng.normal(size=p.shape) for p in omlp.init(sizes, seed=4)]
+    params = [p.astype(np.float32).astype(np.float64) for p in params]  # same values on both sides
+    x = rng.normal(size=(batch, sizes[0])).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=(batch, sizes[-1])).astype(np.float32).astype(np.float64)
+    net = MLP(sizes, params=params)
+    y, acts = net.forward(_f32(x))
+    part, g = net.loss_grad(y, _f32(t))
+    grads = net.backward(acts, g)
+    torch.cuda.synchronize()
+    y0, _ = omlp.forward(params, x)
+    loss0, grads0 = omlp.loss_and_grads(params, x, t)
+    assert rel(y.cpu().numpy(), y0) < 2e-6
+    assert abs(float(part.cpu().numpy().astype(np.float64).sum()) - loss0) < 2e-6 * loss0
+    for gg, g0 in zip(grads, grads0):
+        assert rel(gg.cpu().numpy(), g0) < 2e-5
+
+
+def test_adam_step_matches_oracle():
+    from paper_1305_1489_gb300.learned import MLP
+    sizes = [6, 8, 3]
+    params = [p.astype(np.float32).astype(np.float64) for p in omlp.init(sizes, seed=9)]
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(5, 6)).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=(5, 3)).astype(np.float32).astype(np.float64)
+    net = MLP(sizes, params=params)
+    ref = [p.copy() for p in params]
+    m = [np.zeros_like(p) for p in params]
+    v = [np.zeros_like(p) for p in params]
+    for step in (1, 2, 3):
+        net.train_step(_f32(x), _f32(t), lr=1e-2)
+        _, gr = omlp.loss_and_grads(ref, x, t)
+        for i in range(len(ref)):
+            ref[i], m[i], v[i] = omlp.adam_step(ref[i], gr[i], m[i], v[i], step, lr=1e-2)
+    torch.cuda.synchronize()
+    for p, r in zip(net.params, ref):
+        assert np.abs(p.double().cpu().numpy() - r).max() < 1e-5
+
+
+def test_fourier_field_matches_definition():
+    from paper_1305_1489_gb300.learned import fourier_field
+    rng = np.random.default_rng(0)
+    P = rng.uniform(0, 1, size=(3, 1237))
+    omega = grf_frequencies()
+    amps = grf_sample(17)
+    dev = [torch.from_numpy(p.copy()).cuda() for p in P]
+    got = fourier_field(*dev, omega, amps, 1.0, exponentiate=True).cpu().numpy()
+    want = np.exp(grf_field(amps, omega)(*P))
+    assert rel(got, want) < 1e-13
+    got_g = fourier_field(*dev, omega, amps, 0.7, exponentiate=False).cpu().numpy()
+    assert rel(got_g, grf_field(amps, omega, sigma=0.7)(*P)) < 1e-13
+
+
+def _grf_case(s, sample):
+    prob = cube32_k2_grf(sample_id=sample, s=s, k=2)
+    c, e, d, n = make_mesh(prob)
+    return prob, c, e, d, n
+
+
+def _oracle_prolongation(c, e, d, n, k, nodes, weights, nc):
+    """Pi as a dense matrix [nfc*d2, nc]: vertex values -> face-node values -> eq. 6.3 projection."""
+    mesh = ExpandedMesh(c, e, d, n)
+    tab = ohdg.Tables(k)
+    Wv = np.zeros((len(c), nc))
+    for j in range(4):
+        ok = nodes[:, j] >= 0
+        np.add.at(Wv, (np.nonzero(ok)[0], nodes[ok, j]), weights[ok, j])
+    P = np.zeros((mesh.nfc, tab.d2, nc))
+    for col in range(nc):
+        V = Wv[:, col]
+        face_vals = V[mesh.faces] @ tab.Xi.T  # [nfc, Nf]
+        P[:, :, col] = ohdg.dirichlet_data(tab, face_vals)
+    P[mesh.dirfaces] = 0.0
+    return mesh, tab, P.reshape(-1, nc)
+
+
+def test_prolong_restrict_match_oracle():
+    from paper_1305_1489_gb300.learned import CoarseSpace
+    prob, c, e, d, n = _grf_case(4, 3)
+    nodes, weights, nc = kuhn_coarse_interpolation(4, 2, interior_only=False)
+    _, tab, P = _oracle_prolongation(c, e, d, n, 2, nodes, weights, nc)
+    M = gpu_setup(prob, c, e, d, n)
+    cs = CoarseSpace(nodes, weights, nc)
+    rng = np.random.default_rng(6)
+    cv = rng.normal(size=nc)
+    up = cs.prolong(M, torch.from_numpy(cv).cuda()).cpu().numpy().ravel()
+    assert rel(up, P @ cv) < 1e-13
+    y = rng.normal(size=P.shape[0])
+    rs = cs.restrict(M, torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel(rs, P.T @ y) < 1e-13
+
+
+def test_coarse_galerkin_solve_matches_oracle():
+    from paper_1305_1489_gb300.learned import CoarseSpace
+    prob, c, e, d, n = _grf_case(8, 5)
+    nodes, weights, nc = kuhn_coarse_interpolation(8, 4, interior_only=True)
+    assert nc == 27
+    mesh, tab, P = _oracle_prolongation(c, e, d, n, 2, nodes, weights, nc)
+    X, Y, Z = ohdg.volume_nodes(mesh, tab)
+    blk = ohdg.local_blocks(mesh, tab, prob.kappa(X, Y, Z), prob.c(X, Y, Z), prob.f(X, Y, Z), tau=prob.tau)
+    CK, Cf, _, _ = ohdg.local_solvers(blk)
+    H, F = ohdg.assemble(mesh, tab.d2, CK, Cf)
+    c_or = np.linalg.solve(P.T @ (H @ P), P.T @ F)  # u_D = 0: b = F on the free entries
+    M = gpu_setup(prob, c, e, d, n)
+    M.assemble_condense()
+    cs = CoarseSpace(nodes, weights, nc)
+    cg, it, rr = cs.coarse_solve(M, rtol=1e-13, maxit=500)
+    assert rr <= 1e-13 and it > 0
+    assert rel(cg.cpu().numpy(), c_or) < 1e-10
+    # energy-optimal multiple: alpha = 1 for the Galerkin solution itself
+    x0, alpha = cs.guess(M, cg)
+    assert abs(alpha - 1.0) < 1e-10
+    assert rel(x0.cpu().numpy().ravel(), P @ c_or) < 1e-10
+
+
+def test_learned_guess_gains_over_zero_start():
+    """Train on 48 coarse Galerkin targets at s = 8, k = 2; on held-out fields the trained
+    network's x0 must take fewer PCG iterations than the zero start (same 1e-10 residual), and
+    both solutions must agree."""
+    from paper_1305_1489_gb300.learned import CoarseSpace, LearnedGuess
+    s = 8
+    prob, c, e, d, n = _grf_case(s, 0)
+    M = gpu_setup(prob, c, e, d, n)
+    nodes, weights, nc = kuhn_coarse_interpolation(s, s // 2, interior_only=True)
+    cs = CoarseSpace(nodes, weights, nc)
+    ones = torch.ones(M.nelt, M.nq, dtype=torch.float64, device="cuda")
+    lg = LearnedGuess(M, cs, grf_frequencies(), 1.0, ones, ones, hidden=(64, 64), seed=3)
+    A, T, _ = lg.generate([grf_sample(i) for i in range(48)])
+    hist = lg.fit(A, T, epochs=150, batch=16, lr=2e-3)
+    assert hist[-1][1] < 0.5 * hist[0][1]
+    lg.fold_normalisation()
+    it0, it1 = [], []
+    for i in range(1000, 1006):
+        amps = grf_sample(i)
+        u1, n1, r1, used = lg.solve(amps, rtol=1e-10)
+        u0, n0, r0, _ = lg.solve(amps, rtol=1e-10, use_guess=False)
+        assert used and r1 <= 1e-10 and r0 <= 1e-10
+        assert rel(u1.cpu().numpy(), u0.cpu().numpy()) < 1e-7
+        it0.append(n0)
+        it1.append(n1)
+    assert np.mean(it1) < np.mean(it0)

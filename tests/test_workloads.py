@@ -59,3 +59,33 @@ def test_batch_sampler():
     probs = batch_problems()
     assert len(probs) == 64
     assert all(8 <= p.s <= 24 and 1 <= p.k <= 4 for p in probs)
+
+
+def test_coarse_interpolation_is_nested_p1():
+    """The fine-vertex values of a random coarse P1 field, interpolated linearly on each fine
+    element, equal the coarse field (Freudenthal interpolation on the coarse Kuhn simplex)."""
+    from workloads import kuhn_coarse_interpolation
+    s, sc = 6, 3
+    c, e = kuhn_cube(s)
+    nodes, w, nc = kuhn_coarse_interpolation(s, sc, interior_only=False)
+    rng = np.random.default_rng(0)
+    cv = rng.normal(size=nc)
+    V = (np.where(nodes >= 0, cv[np.maximum(nodes, 0)], 0.0) * w).sum(axis=1)
+    bary = rng.dirichlet(np.ones(4), size=len(e))
+    pts = np.einsum("ek,ekd->ed", bary, c[e])
+    fine = np.einsum("ek,ek->e", bary, V[e])
+    m1 = sc + 1
+    loc = pts * sc
+    base = np.minimum(np.floor(loc).astype(int), sc - 1)
+    x = loc - base
+    order = np.argsort(-x, axis=1)
+    xs = np.take_along_axis(x, order, axis=1)
+    vid = lambda b: b[:, 0] + m1 * (b[:, 1] + m1 * b[:, 2])  # noqa: E731
+    v0 = base.copy()
+    unit = np.eye(3, dtype=int)
+    v1 = v0 + unit[order[:, 0]]
+    v2 = v1 + unit[order[:, 1]]
+    v3 = v2 + unit[order[:, 2]]
+    coarse = ((1 - xs[:, 0]) * cv[vid(v0)] + (xs[:, 0] - xs[:, 1]) * cv[vid(v1)]
+              + (xs[:, 1] - xs[:, 2]) * cv[vid(v2)] + xs[:, 2] * cv[vid(v3)])
+    assert np.abs(fine - coarse).max() < 1e-12

@@ -8,5 +8,5 @@ no quadrature, no basis, no local solver.  Both the oracle and the CUDA path eva
 these functions at their own quadrature nodes.
 """
 
-from .mesh import kuhn_cube, boundary_faces  # noqa: F401
+from .mesh import boundary_faces, kuhn_coarse_interpolation, kuhn_cube, kuhn_p1_hierarchy  # noqa: F401
 from .problems import PROBLEMS, Problem, get_problem  # noqa: F401

@@ -85,3 +85,113 @@ def boundary_faces(coords, elems, classify):
     d = np.concatenate(dirs).astype(np.int32).reshape(-1, 3) if dirs else np.zeros((0, 3), np.int32)
     n = np.concatenate(neus).astype(np.int32).reshape(-1, 3) if neus else np.zeros((0, 3), np.int32)
     return d, n
+
+
+def kuhn_coarse_interpolation(s, s_coarse, interior_only=True):
+    """Vertex interpolation from the coarse Kuhn grid (s_coarse^3 cubes) to the fine one.
+
+    The fine grid (s = r s_coarse, r a power of two) refines every coarse Kuhn simplex into
+    Kuhn simplices, so a continuous piecewise-linear field on the coarse mesh is linear on
+    every fine element and is fixed by its values at the fine vertices.  For r = 2 a fine
+    vertex lies at a coarse node or at the midpoint of a coarse Kuhn edge (the cube's main
+    diagonal direction (1,1,1) and its face diagonals in the +,+ directions are edges).
+    Returns nodes int32 [nver, 4] (-1 = unused) and weights f64 [nver, 4] over the coarse
+    nodes numbered i + (s_c+1)(j + (s_c+1) l) -- or, with interior_only, over the interior
+    coarse nodes only (boundary coarse values fixed to zero), plus the number of coarse
+    unknowns.
+    """
+    if s == s_coarse:
+        r = 1
+    elif s == 2 * s_coarse:
+        r = 2
+    else:
+        raise ValueError("only s = s_coarse or s = 2 s_coarse")
+    n1, m1 = s + 1, s_coarse + 1
+    I, J, L = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    I, J, L = (a.transpose(2, 1, 0).ravel() for a in (I, J, L))  # vertex id = i + n1 (j + n1 l)
+    if r == 1:
+        ends = [(I, J, L, 1.0)]
+    else:
+        b0 = np.stack([I // 2, J // 2, L // 2], axis=1)
+        odd = np.stack([I % 2, J % 2, L % 2], axis=1)
+        # the fine vertex is the midpoint of the coarse edge from b0 to b0 + odd
+        ends = [(b0[:, 0], b0[:, 1], b0[:, 2], 0.5), (b0[:, 0] + odd[:, 0], b0[:, 1] + odd[:, 1], b0[:, 2] + odd[:, 2], 0.5)]
+        is_node = odd.sum(axis=1) == 0
+    nodes = -np.ones((len(I), 4), np.int64)
+    weights = np.zeros((len(I), 4))
+    if interior_only:
+        cid = -np.ones(m1 ** 3, np.int64)
+        ii, jj, ll = np.meshgrid(np.arange(m1), np.arange(m1), np.arange(m1), indexing="ij")
+        ii, jj, ll = (a.transpose(2, 1, 0).ravel() for a in (ii, jj, ll))
+        inner = (ii > 0) & (ii < s_coarse) & (jj > 0) & (jj < s_coarse) & (ll > 0) & (ll < s_coarse)
+        cid[inner] = np.arange(inner.sum())
+        nc = int(inner.sum())
+    else:
+        cid = np.arange(m1 ** 3)
+        nc = m1 ** 3
+    for slot, (a, b, c, w) in enumerate(ends):
+        g = cid[a + m1 * (b + m1 * c)]
+        wt = np.full(len(I), w)
+        if r == 2:
+            wt = np.where(is_node, 1.0 if slot == 0 else 0.0, wt)
+        ok = (g >= 0) & (wt != 0.0)
+        nodes[ok, slot] = g[ok]
+        weights[ok, slot] = wt[ok]
+    return nodes.astype(np.int32), weights, nc
+
+
+def _grid_ids(s):
+    n1 = s + 1
+    I, J, L = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    return tuple(a.transpose(2, 1, 0).ravel() for a in (I, J, L))  # id = i + n1 (j + n1 l)
+
+
+def _kept(s, fixed_planes):
+    """Mask of grid vertices not on a fixed (Dirichlet) plane; planes are (axis, 0.0 or 1.0)."""
+    ijk = _grid_ids(s)
+    keep = np.ones((s + 1) ** 3, bool)
+    for ax, val in fixed_planes:
+        keep &= ijk[ax] != (0 if val == 0.0 else s)
+    return keep
+
+
+def kuhn_p1_hierarchy(s, fixed_planes, max_coarsest=64):
+    """Nested continuous P1 spaces for the two-level trace preconditioner of an s^3 Kuhn cube.
+
+    Level 0 is the P1 space of the mesh itself (one node per vertex not on a fixed plane);
+    level l+1 is the P1 space of the Kuhn grid with half the cells per side, down to the first
+    level with at most max_coarsest nodes.  Returns (sizes [nlev], nodes int32 [R, 4],
+    weights f64 [R, 4]) with R = nver + sizes[0] + ... + sizes[nlev-2]: first, for every mesh
+    vertex, its level-0 node (weight 1; -1 on a fixed plane); then, for every node of level l,
+    the level-(l+1) nodes and weights that interpolate it (coarse vertex: itself; midpoint of
+    a coarse Kuhn edge: the two ends with 1/2).  s must be a power of two times the coarsest
+    grid size.
+    """
+    keep = _kept(s, fixed_planes)
+    ids = -np.ones((s + 1) ** 3, np.int64)
+    ids[keep] = np.arange(keep.sum())
+    sizes = [int(keep.sum())]
+    nodes = [np.stack([ids, -np.ones_like(ids), -np.ones_like(ids), -np.ones_like(ids)], axis=1)]
+    weights = [np.stack([np.where(keep, 1.0, 0.0), np.zeros(len(ids)), np.zeros(len(ids)), np.zeros(len(ids))],
+                        axis=1)]
+    cur = s
+    while sizes[-1] > max_coarsest:
+        if cur % 2 or cur < 2:
+            raise ValueError("cannot coarsen further: s must be a power of two times a small grid")
+        nd, wt, _ = kuhn_coarse_interpolation(cur, cur // 2, interior_only=False)
+        keep_c = _kept(cur // 2, fixed_planes)
+        cid = -np.ones((cur // 2 + 1) ** 3, np.int64)
+        cid[keep_c] = np.arange(keep_c.sum())
+        rows_f = np.nonzero(_kept(cur, fixed_planes))[0]  # level-l nodes in id order
+        nd, wt = nd[rows_f].astype(np.int64), wt[rows_f]
+        mapped = np.where(nd >= 0, cid[np.maximum(nd, 0)], -1)
+        wt = np.where(mapped >= 0, wt, 0.0)
+        nodes.append(mapped)
+        weights.append(wt)
+        sizes.append(int(keep_c.sum()))
+        if sizes[-1] == 0:
+            raise ValueError("the coarsest level has no free nodes")
+        cur //= 2
+    if len(sizes) < 2:
+        raise ValueError("the hierarchy needs at least two levels")
+    return sizes, np.concatenate(nodes).astype(np.int32), np.concatenate(weights)
