@@ -223,6 +223,26 @@ int hdg_nn_mse(int64_t n, const float* pred, const float* target, float* grad,
 int hdg_nn_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1,
                 float b2, float eps, int step, void* stream);
 
+/* ------------------------------------------------------------------ two-level preconditioner
+ * (not in the paper, which solves eq. 6.5 directly).  With a coarse space set, the PCG of
+ * hdg_solve_trace (both precisions; not the BiCGStab of convection problems) is preconditioned
+ * by M^-1 r = B^-1 r + Pi V(Pi^T r): B the block-Jacobi part, Pi the trace (eq. 6.3 face
+ * coefficients) of a continuous piecewise-linear field, V one symmetric V-cycle (one l1-Jacobi
+ * sweep before and after each coarse correction, FP32) for A_0 = Pi^T H Pi over nested levels
+ * A_{l+1} = P_l^T A_l P_l, exact dense solve on the coarsest level.  The Galerkin matrices are
+ * rebuilt on the device after every hdg_assemble_condense (at the next solve).
+ * hdg_set_coarse_space: nlev >= 2 levels with sizes[l] nodes (sizes[nlev-1] <= 128); host
+ *   arrays nodes int32 / weights f64 [R][4], R = nver + sizes[0] + ... + sizes[nlev-2]: first,
+ *   per mesh vertex, the level-0 nodes and weights giving its value; then, per node of level
+ *   l < nlev-1, the level-(l+1) nodes and weights interpolating it.  Node -1 = unused entry.
+ *   Copied; nlev = 0 removes the coarse space.  Every element may touch at most 8 level-0
+ *   nodes (HDG_ERR_UNSUPPORTED).  Invalid sizes or nodes: HDG_ERR_ARG.
+ * hdg_coarse_precond_apply: z = M^-1 r for device f64 [nfc][d2] vectors (Dirichlet entries
+ *   of r ignored; tests and inspection).                                                   */
+int hdg_set_coarse_space(hdg_mesh* mesh, int nlev, const int64_t* sizes, const int32_t* nodes,
+                         const double* weights);
+int hdg_coarse_precond_apply(hdg_mesh* mesh, const double* r, double* z);
+
 /* Relative tolerance of each FP32 inner solve of the HDG_MIXED_FP32 trace solve (default
  * 1e-4): every outer FP64 refinement step asks the inner PCG for this residual reduction.  */
 int hdg_set_inner_tolerance(hdg_mesh* mesh, double rtol);

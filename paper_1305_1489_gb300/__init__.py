@@ -243,6 +243,26 @@ class HDGMesh:
             raise HDGError(code, _lib.last_error())
         return uhat, it, rr
 
+    def set_coarse_space(self, sizes, nodes, weights):
+        """Two-level preconditioner from nested P1 levels (hdg_set_coarse_space); sizes=None
+        removes it."""
+        lib = _lib.load()
+        if sizes is None:
+            _lib.check(lib.hdg_set_coarse_space(self._h, 0, None, None, None))
+            return
+        sz = np.ascontiguousarray(sizes, dtype=np.int64)
+        nd = np.ascontiguousarray(nodes, dtype=np.int32)
+        wt = np.ascontiguousarray(weights, dtype=np.float64)
+        if nd.shape != wt.shape or nd.ndim != 2 or nd.shape[1] != 4:
+            raise ValueError("nodes and weights must both be [R, 4]")
+        _lib.check(lib.hdg_set_coarse_space(self._h, len(sz), _ptr(sz), _ptr(nd), _ptr(wt)))
+
+    def precond_apply(self, r):
+        z = self._empty(self.nfc, self.d2)
+        _lib.check(_lib.load().hdg_coarse_precond_apply(self._h, _dev_f64(r, (self.nfc, self.d2), "r").data_ptr(),
+                                                        z.data_ptr()))
+        return z
+
     def set_inner_tolerance(self, rtol):
         hdg_set_inner_tolerance(self._h, rtol)
 

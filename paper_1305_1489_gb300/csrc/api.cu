@@ -71,6 +71,7 @@ static int upload_tables(hdg_mesh* M) {
 }
 
 static void release(hdg_mesh* M) {
+  coarse_free(M);
   void* ptrs[] = {M->d_vx, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
                   M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
@@ -236,6 +237,7 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   M->assembled = true;
+  if (M->coarse) coarse_invalidate(M);
   M->rhs_ready = false;
   return check_status(M);
 }

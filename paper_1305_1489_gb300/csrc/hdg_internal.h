@@ -11,6 +11,8 @@
 
 namespace hdg {
 
+struct Coarse;
+
 // ------------------------------------------------------------------ reference tables
 // Host copies, row-major.  Built once per degree k (tables.cpp).
 struct Tables {
@@ -108,6 +110,8 @@ struct hdg_mesh {
   cudaGraphExec_t wgraph64 = nullptr, wgraph32 = nullptr;  // device-driven (conditional WHILE) PCG loops
   bool no_cond_graphs = false;  // the driver refused conditional nodes: host-driven loop
   int graph_iters = 0;
+  hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL
+  bool graphs_tl = false;         // the cached PCG graphs include the coarse correction
 };
 
 namespace hdg {
@@ -137,4 +141,9 @@ int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const 
                        double* norms, double rtol, int maxit, double* q, double* u, double* uhat, cudaGraphNode_t* last);
 int batch_group_iterations(hdg_mesh* M, int* iters, int* status);
 int build_mesh(hdg_mesh* M, const double* coords, const int32_t* elems, const int32_t* dir, const int32_t* neu);
+int ensure_face_verts(hdg_mesh* M);   // d_fverts and d_Tproj (coarse prolongation)
+int coarse_build(hdg_mesh* M);        // Galerkin hierarchy of the two-level preconditioner
+void coarse_free(hdg_mesh* M);
+void coarse_invalidate(hdg_mesh* M);  // the Galerkin values must be rebuilt (new assembly)
+int coarse_precond_apply(hdg_mesh* M, const double* r, double* z);
 }  // namespace hdg

@@ -211,7 +211,7 @@ __global__ void nn_adam_kernel(int64_t n, float* __restrict__ p, const float* __
 
 using namespace hdg;
 
-static int ensure_face_verts(hdg_mesh* M) {
+int hdg::ensure_face_verts(hdg_mesh* M) {
   if (M->d_fverts) return HDG_OK;
   std::vector<int32_t> fv(3 * M->nfc);
   for (int64_t e = 0; e < M->nfc; ++e)

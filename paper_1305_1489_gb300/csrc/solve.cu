@@ -15,6 +15,7 @@
 // at most kMaxBlocks per-block partials.  Scalars (alpha, beta, r.z, r.r) stay on the device;
 // batches of iterations are captured in a CUDA graph and the host reads the convergence flag
 // after each replay.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -57,6 +58,10 @@ template <int D2>
 __device__ __forceinline__ int64_t ntiles(const FaceArgs& F) {
   return (F.nfc + Tile<D2>::FPB - 1) / Tile<D2>::FPB;
 }
+
+}  // namespace hdg
+#include "coarse.cuh"
+namespace hdg {
 
 // Last-block-done reduction of NSLOT values; returns true on the block that finishes.  The
 // finishing block sums the per-block partials in block order, so the result is deterministic.
@@ -414,6 +419,72 @@ __global__ void pcg_dir_kernel(int64_t ntot, const T* __restrict__ z, T* __restr
     p[t] = fma(beta, p[t], z[t]);
 }
 
+// Two-level variant of the update: x += alpha p;  r -= alpha q;  r.r;  rc += Pi^T r.  The
+// preconditioned residual is formed by pcg_zc_kernel after the V-cycle.
+template <typename T, int D2>
+__global__ void pcg_update_tl_kernel(FaceArgs F, CoarseArgs CA, T* __restrict__ x, T* __restrict__ r,
+                                     const T* __restrict__ p, const T* __restrict__ q, double* red,
+                                     unsigned int* counter, double* scal) {
+  if (scal[S_DONE] != 0.0) return;
+  const T alpha = (T)scal[S_ALPHA];
+  double v[1] = {0.0};
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (T_.act) {
+      x[T_.t] = fma(alpha, p[T_.t], x[T_.t]);
+      const T rv = fma(-alpha, q[T_.t], r[T_.t]);
+      r[T_.t] = rv;
+      v[0] = fma((double)rv, (double)rv, v[0]);
+    }
+    __syncthreads();  // the d2 entries of r of each face of the tile are updated
+    if (T_.act && T_.a == 0 && F.ftype[T_.e] != 1) restrict_face<T, D2>(CA, r, T_.e);
+  }
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
+    scal[S_RR] = out[0];
+    scal[S_ITERS] += 1.0;
+    if (out[0] <= scal[S_TOL2] || scal[S_ITERS] >= scal[S_MAXIT]) scal[S_DONE] = 1.0;
+  }
+}
+
+// rc += Pi^T r (start of a two-level solve; rc zeroed before)
+template <typename T, int D2>
+__global__ void restrict_tl_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ r) {
+  const int64_t fpt = kNT;  // one thread per face
+  for (int64_t e = (int64_t)blockIdx.x * fpt + threadIdx.x; e < F.nfc; e += (int64_t)gridDim.x * fpt)
+    if (F.ftype[e] != 1) restrict_face<T, D2>(CA, r, e);
+}
+
+// z = B^-1 r + Pi e0;  r.z;  INIT: p = z and the convergence flag, else beta.  Clears rc.
+template <typename T, int D2, bool INIT>
+__global__ void pcg_zc_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ Binv, const T* __restrict__ r,
+                              T* __restrict__ z, T* __restrict__ p, double* red, unsigned int* counter, double* scal) {
+  if (!INIT && scal[S_DONE] != 0.0) return;
+  double v[1] = {0.0};
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    T zv = bj_apply<T, D2>(Binv, r, T_.e, T_.a);
+    if (F.ftype[T_.e] != 1) zv += (T)prolong_face<D2>(CA, T_.e, T_.a);
+    z[T_.t] = zv;
+    if (INIT) p[T_.t] = zv;
+    v[0] = fma((double)r[T_.t], (double)zv, v[0]);
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < CA.n0; i += (int64_t)gridDim.x * blockDim.x)
+    CA.rc[i] = 0.0;
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
+    if (INIT) {
+      scal[S_RZ] = out[0];
+      scal[S_DONE] = (scal[S_RR] <= scal[S_TOL2]) ? 1.0 : 0.0;
+      scal[S_ITERS] = 0.0;
+    } else {
+      scal[S_BETA] = out[0] / scal[S_RZ];
+      scal[S_RZ] = out[0];
+    }
+  }
+}
+
 // End of one body of the device-driven loop: keep looping while the solve is not done and
 // fewer than scal[max_slot] bodies have run (the host sets that bound before every launch).
 // The body counter is independent of the reductions, so the loop ends even if a reduction
@@ -613,6 +684,41 @@ static int nblocks(hdg_mesh* M) {
   return (int)(tiles < kMaxBlocks ? tiles : kMaxBlocks);
 }
 
+static CoarseArgs coarse_args(hdg_mesh* M) {
+  const Coarse* c = M->coarse;
+  CoarseArgs a;
+  a.fverts = M->d_fverts;
+  a.T = M->d_Tproj;
+  a.vnodes = c->vnodes;
+  a.vw = c->vw;
+  a.rc = c->rc;
+  a.e0 = c->e0;
+  a.n0 = c->lv[0].n;
+  return a;
+}
+
+// level-0 down, the single-CTA coarse levels and level-0 up of one V-cycle
+static void coarse_cycle(hdg_mesh* M, cudaStream_t st, const double* done) {
+  Coarse* c = M->coarse;
+  const CoarseLevel& L0 = c->lv[0];
+  const int g0 = (int)std::min<int64_t>((L0.n + 255) / 256, kMaxBlocks);
+  l0_down_kernel<<<g0, 256, 0, st>>>(L0, c->rc, done);
+  vcycle_kernel<<<1, kVcThreads, 0, st>>>(c->d_lv, c->nlev, c->Ainv, done);
+  l0_up_kernel<<<g0, 256, 0, st>>>(L0, c->lv[1].x, c->rc, c->e0, done);
+}
+
+// graphs captured with or without the coarse correction are not interchangeable
+static void match_graphs(hdg_mesh* M, bool tl) {
+  if (M->graphs_tl == tl) return;
+  cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32};
+  for (cudaGraphExec_t* g : gs)
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  M->graphs_tl = tl;
+}
+
 static int ensure_workspace(hdg_mesh* M, bool mixed) {
   const int64_t nv = M->nfc * M->tab.d2;
   if (!M->d_b) {
@@ -715,18 +821,37 @@ struct Solver {
     hs[S_MAXIT] = (double)maxit;
     hs[S_MAXBODIES] = (double)(maxit / kGraphIters + 2);  // bound of the device-driven loop
     HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
+    const bool tl = M->coarse != nullptr && M->coarse->ready;
+    match_graphs(M, tl);
+    const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
+    const int per_it = tl ? 7 : 3;  // kernels per iteration
     pcg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
-    pcg_precond_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, Binv, r, z, p, M->d_red, M->d_counter, scal);
-    M->launches += 2;
+    if (tl) {
+      HDG_CUDA_TRY(cudaMemsetAsync(CA.rc, 0, sizeof(double) * CA.n0, M->stream));
+      restrict_tl_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, CA, r);
+      coarse_cycle(M, M->stream, scal + S_DONE);
+      pcg_zc_kernel<T, D2, true><<<nb, kNT, 0, M->stream>>>(F, CA, Binv, r, z, p, M->d_red, M->d_counter, scal);
+      M->launches += 6;
+    } else {
+      pcg_precond_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, Binv, r, z, p, M->d_red, M->d_counter, scal);
+      M->launches += 2;
+    }
     HDG_CUDA_TRY(cudaGetLastError());
     if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = M->cap_stream;
-    auto body = [&](cudaStream_t st, cudaGraphConditionalHandle h) {
-      for (int it = 0; it < kGraphIters; ++it) {
-        pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+    auto iteration = [&](cudaStream_t st) {
+      pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+      if (tl) {
+        pcg_update_tl_kernel<T, D2><<<nb, kNT, 0, st>>>(F, CA, x, r, p, q, M->d_red, M->d_counter, scal);
+        coarse_cycle(M, st, scal + S_DONE);
+        pcg_zc_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, CA, Binv, r, z, p, M->d_red, M->d_counter, scal);
+      } else {
         pcg_update_kernel<T, D2><<<nb, kNT, 0, st>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
-        pcg_dir_kernel<T><<<nb, kNT, 0, st>>>(nv, z, p, scal);
       }
+      pcg_dir_kernel<T><<<nb, kNT, 0, st>>>(nv, z, p, scal);
+    };
+    auto body = [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+      for (int it = 0; it < kGraphIters; ++it) iteration(st);
       loop_control_kernel<<<1, 32, 0, st>>>(h, scal, S_DONE, S_BODIES, S_MAXBODIES);
     };
     cudaGraphExec_t* wg = (sizeof(T) == 8) ? &M->wgraph64 : &M->wgraph32;
@@ -740,18 +865,14 @@ struct Solver {
       M->launches += 1;
       HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
       HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-      M->launches += (int64_t)(3 * kGraphIters + 1) * (int64_t)hv[S_BODIES];
+      M->launches += (int64_t)(per_it * kGraphIters + 1) * (int64_t)hv[S_BODIES];
     } else {
       if (!*graph) {
         // capture on a private stream (the caller's may be the legacy default stream, which
         // cannot be captured); the graph is then launched on the caller's stream
         cudaGraph_t g;
         HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        for (int it = 0; it < kGraphIters; ++it) {
-          pcg_matvec_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, C, p, q, M->d_red, M->d_counter, scal);
-          pcg_update_kernel<T, D2><<<nb, kNT, 0, cs>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
-          pcg_dir_kernel<T><<<nb, kNT, 0, cs>>>(nv, z, p, scal);
-        }
+        for (int it = 0; it < kGraphIters; ++it) iteration(cs);
         HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
         HDG_CUDA_TRY(cudaGraphInstantiate(graph, g, 0));
         cudaGraphDestroy(g);
@@ -761,7 +882,7 @@ struct Solver {
         HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
         if (hv[S_DONE] != 0.0) break;
         HDG_CUDA_TRY(cudaGraphLaunch(*graph, M->stream));
-        M->launches += 3 * kGraphIters;
+        M->launches += per_it * kGraphIters;
       }
     }
     *iters = (int)hv[S_ITERS];
@@ -842,6 +963,10 @@ struct Solver {
     int total_it = 0;
     bool converged = false, bad = false;
     double rnorm = 0.0;
+    if (M->coarse && !M->beta_q && !M->coarse->ready) {
+      rc = coarse_build(M);
+      if (rc) return rc;
+    }
     if (x0) {
       HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
       mask_dirichlet_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, D2, M->d_x);
@@ -920,6 +1045,32 @@ struct Solver {
     if (!converged)
       return fail(HDG_ERR_NOT_CONVERGED, "trace solve reached maxit with relative residual " +
                                              std::to_string(bnorm > 0 ? rnorm / bnorm : 0.0));
+    return HDG_OK;
+  }
+
+  // z = B^-1 r + Pi V(Pi^T r): one application of the two-level preconditioner (FP64 vectors)
+  static int precond_apply(hdg_mesh* M, const double* r, double* z) {
+    int rc = ensure_workspace(M, false);
+    if (rc) return rc;
+    rc = prepare_rhs(M);
+    if (rc) return rc;
+    if (!M->coarse->ready) {
+      rc = coarse_build(M);
+      if (rc) return rc;
+    }
+    FaceArgs F = face_args(M);
+    const int nb = nblocks(M);
+    const CoarseArgs CA = coarse_args(M);
+    double* scal = M->d_scal + S_NSCAL;
+    HDG_CUDA_TRY(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSCAL, M->stream));
+    HDG_CUDA_TRY(cudaMemsetAsync(CA.rc, 0, sizeof(double) * CA.n0, M->stream));
+    restrict_tl_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, CA, r);
+    coarse_cycle(M, M->stream, scal + S_DONE);
+    pcg_zc_kernel<double, D2, true><<<nb, kNT, 0, M->stream>>>(F, CA, M->d_BJ, r, z, M->d_q, M->d_red, M->d_counter,
+                                                               scal);
+    M->launches += 5;
+    HDG_CUDA_TRY(cudaGetLastError());
+    HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
     return HDG_OK;
   }
 
@@ -1099,6 +1250,19 @@ int trace_apply(hdg_mesh* M, const double* x, double* y) {
     case 6: return Solver<6>::apply(M, x, y);
     case 10: return Solver<10>::apply(M, x, y);
     case 15: return Solver<15>::apply(M, x, y);
+  }
+  return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
+}
+
+int coarse_precond_apply(hdg_mesh* M, const double* r, double* z) {
+  if (!M->assembled) return fail(HDG_ERR_STATE, "preconditioner before hdg_assemble_condense");
+  if (!M->coarse) return fail(HDG_ERR_STATE, "no coarse space: call hdg_set_coarse_space first");
+  if (M->beta_q) return fail(HDG_ERR_UNSUPPORTED, "the two-level preconditioner is for beta = 0");
+  switch (M->tab.d2) {
+    case 3: return Solver<3>::precond_apply(M, r, z);
+    case 6: return Solver<6>::precond_apply(M, r, z);
+    case 10: return Solver<10>::precond_apply(M, r, z);
+    case 15: return Solver<15>::precond_apply(M, r, z);
   }
   return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }
