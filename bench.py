@@ -8,11 +8,13 @@ kappa = 1 + 0.5 sin(2 pi x) cos(2 pi y), c = 1 + x^2, manufactured u = (1 + x^2 
 exp(0.5x - y + z), Dirichlet on x = 0 and x = 1, Neumann elsewhere.  Synthetic, seeded.
 
 One step = the whole hot path on one batch of resident inputs:
-  assemble + condense (K1)  ->  trace solve to ||b - H u||/||b|| <= 1e-10 (FP32 inner PCG with
-  FP64 refinement)  ->  recover (K2)  ->  postprocess (K5).
+  assemble + condense (K1, double-float)  ->  trace solve to ||b - H u||/||b|| <= 1e-10 (FP32
+  inner PCG with FP64 refinement, two-level preconditioner)  ->  recover (K2)  ->
+  postprocess (K5).
 value = elements/s over the metric's phases (assemble + condense + recover), timed with CUDA
 events on the launching stream; the trace solve's time-to-1e-10 is reported beside it for the
-plain FP64 block-Jacobi PCG (zero start) and for the mixed-precision solve.
+plain FP64 block-Jacobi PCG (zero start), the mixed-precision solve and the two-level
+preconditioned solves.
 L2 is flushed (256 MiB write) before every step; the inputs (74 MB) are smaller than L2.
 With --impl reference the FP64 CPU oracle is timed on the host cores on the same workload.
 """
@@ -39,9 +41,10 @@ UNIT = "elements/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_MEASURED_TFLOPS = 1.19  # FMA-chain microbenchmark on this machine's GB300 (1 block/SM saturates)
 
-# DRAM traffic of one K1 launch at this workload, from the ncu capture recorded in
-# profiles/assemble_kernel_cube16_k3.md, valid while assemble.cu is unchanged.
-K1_TRAFFIC = {"sha256": None, "bytes": None}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one K1 launch at this workload,
+# from the ncu captures summarised under profiles/, valid while the kernel source is unchanged.
+K1_TRAFFIC = {"assemble_df.cu": {"sha256": "74db6c1e5a2a6d46675d7879426d673c9a9a18f26d04c2319e871196e47fa4ba", "bytes": 82824960 + 858117376},
+              "assemble.cu": {"sha256": None, "bytes": None}}
 
 
 def flops_per_element_k1(k):
@@ -229,6 +232,11 @@ def run_gpu(args, rank, world, local_rank):
     M.set_boundary_data(dv["uD"], dv["gN"])
     M.set_inner_tolerance(args.inner_rtol)
     asm_prec = HDG_DF32 if args.asm == "df32" else HDG_FP64
+    from workloads import kuhn_p1_hierarchy
+    hierarchy = kuhn_p1_hierarchy(prob.s, prob.dirichlet_planes)
+    step_prec = HDG_MIXED_FP32 if args.solve == "mixed" else HDG_FP64
+    if args.coarse:
+        M.set_coarse_space(*hierarchy)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def ev():
@@ -240,7 +248,7 @@ def run_gpu(args, rank, world, local_rank):
         e0.record(stream)
         M.assemble_condense(asm_prec)
         e1.record(stream)
-        uhat, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
+        uhat, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
         e2.record(stream)
         q, u = M.recover(uhat)
         e3.record(stream)
@@ -289,11 +297,20 @@ def run_gpu(args, rank, world, local_rank):
                               "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
                 "value": value, "gpu_launches": int(launches), "ms_per_step": total_ms / args.steps}
 
-    # time-to-1e-10: plain FP64 zero-start block-Jacobi PCG vs mixed precision
+    # time-to-1e-10 (zero start): plain FP64 block-Jacobi PCG, mixed precision, and both with the
+    # two-level preconditioner (its Galerkin set-up after the assembly is inside the time)
     solve = {}
-    for name, prec in (("plain_fp64", HDG_FP64), ("mixed_fp32_fp64", HDG_MIXED_FP32)):
+    cases = (("plain_fp64", HDG_FP64, False), ("mixed_fp32_fp64", HDG_MIXED_FP32, False),
+             ("two_level_fp64", HDG_FP64, True), ("two_level_mixed", HDG_MIXED_FP32, True))
+    for name, prec, tl in cases:
+        if tl:
+            M.set_coarse_space(*hierarchy)
+        else:
+            M.set_coarse_space(None, None, None)
         ts, its = [], []
-        for _ in range(2):
+        for _ in range(3):
+            M.assemble_condense(asm_prec)
+            torch.cuda.synchronize()
             a, b = ev(), ev()
             a.record(stream)
             uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=prec)
@@ -301,8 +318,13 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
             its.append(it)
-        solve[name] = {"ms": min(ts), "iterations": its[-1], "relres": rr}
-    solve["speedup_mixed_vs_plain"] = solve["plain_fp64"]["ms"] / solve["mixed_fp32_fp64"]["ms"]
+        solve[name] = {"ms": float(np.median(ts)), "iterations": its[-1], "relres": rr}
+    for name in ("mixed_fp32_fp64", "two_level_fp64", "two_level_mixed"):
+        solve["speedup_" + name + "_vs_plain"] = solve["plain_fp64"]["ms"] / solve[name]["ms"]
+    if args.coarse:
+        M.set_coarse_space(*hierarchy)
+    else:
+        M.set_coarse_space(None, None, None)
 
     # end to end through the public API with host buffers (pinned) and copies in the region
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
@@ -321,7 +343,7 @@ def run_gpu(args, rank, world, local_rank):
         M.set_boundary_data(dv["uD"], dv["gN"])
         M.assemble_condense(asm_prec)
         b.record(stream)
-        uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
+        uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
         cc.record(stream)
         q, u = M.recover(uh)
         hq.copy_(q, non_blocking=True)
@@ -335,19 +357,25 @@ def run_gpu(args, rank, world, local_rank):
            "phases": "H2D of kappa,c,f,u_D,g_N + assemble_condense + recover + D2H of q,u "
                      "(the trace solve runs between them and is excluded, as in value)"}
 
-    # roofline of the dominant kernel (K1, FP64-ALU bound)
+    # roofline of the dominant kernel of the metric (K1).  Its work is the FP64 flop count of
+    # the algorithm; the double-float variant executes it on the FP32 pipe, so the reference
+    # peak is the FP64 pipe's (the best a native-FP64 K1 could do on this GPU).
     k1_ms = float(np.mean(t_asm))
     flops = flops_per_element_k1(prob.k) * nelt
     achieved = flops / (k1_ms / 1e3) / 1e12
-    sha = _sha(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", "assemble.cu"))
-    traffic = K1_TRAFFIC["bytes"] if K1_TRAFFIC["sha256"] == sha else None
+    k1_src = "assemble_df.cu" if args.asm == "df32" else "assemble.cu"
+    sha = _sha(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", k1_src))
+    trec = K1_TRAFFIC.get(k1_src, {})
+    traffic = trec.get("bytes") if trec.get("sha256") == sha else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "assemble_kernel<3,256> (K1, FP64)",
+                "kernel": ("assemble_df_kernel<3> (K1, double-float on the FP32 pipe)" if args.asm == "df32"
+                           else "assemble_kernel<3,256> (K1, FP64)"),
+                "work": "FP64-equivalent flops of the structured elimination",
                 "flops_per_element": flops_per_element_k1(prob.k),
                 "algorithmic_bytes_per_launch": k1_bytes_per_element(prob.k) * nelt,
-                "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived); measured FMA "
-                             f"microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s",
+                "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts and the "
+                             f"maximum clock); measured FMA microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s",
                 "frac_of_measured": achieved / FP64_MEASURED_TFLOPS}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -358,7 +386,11 @@ def run_gpu(args, rank, world, local_rank):
                    "nelt": nelt, "nfc": M.nfc, "trace_dofs": M.nfc * M.d2, "k": prob.k,
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "solve_in_step": "mixed FP32/FP64 PCG to 1e-10 relative residual"},
+                   "solve_in_step": ("mixed FP32/FP64" if args.solve == "mixed" else "FP64")
+                   + " PCG to 1e-10 relative residual, "
+                   + ("two-level (block-Jacobi + P1 V-cycle) preconditioner" if args.coarse else
+                      "block-Jacobi preconditioner"),
+                   "coarse_levels": hierarchy[0] if args.coarse else None},
         "phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
                       "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
         "solve_time_to_1e-10": solve,
@@ -471,6 +503,9 @@ def main():
     ap.add_argument("--asm", default="df32", choices=["df32", "fp64"],
                     help="assembly arithmetic: double-float on the FP32 pipe or native FP64")
     ap.add_argument("--inner-rtol", type=float, default=1e-6, help="FP32 inner solve tolerance")
+    ap.add_argument("--solve", default="mixed", choices=["mixed", "fp64"], help="trace solve precision in the step")
+    ap.add_argument("--no-coarse", dest="coarse", action="store_false",
+                    help="block-Jacobi only (no two-level preconditioner) in the step")
     ap.add_argument("--batch", action="store_true", help="also time the 64-problem mixed-degree batch")
     ap.add_argument("--batch-only", action="store_true", help="time only the batch and exit")
     ap.add_argument("--batch-n", type=int, default=64)

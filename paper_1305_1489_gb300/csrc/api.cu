@@ -1,5 +1,6 @@
 // C ABI of libhdg (declared in include/hdg.h): argument checking, ownership, dispatch.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -122,6 +123,9 @@ int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, in
   M->ndir = ndir;
   M->nneu = nneu;
   M->stream = (cudaStream_t)stream;
+  // HDG_HOST_LOOP=1: drive the PCG loop from the host (replays of a plain captured graph)
+  // instead of the device-side conditional loop, e.g. for profilers that list graph kernels.
+  if (const char* hl = std::getenv("HDG_HOST_LOOP")) M->no_cond_graphs = hl[0] == '1';
   std::string err;
   int rc = HDG_OK;
   if (!build_tables(k, &M->tab, &err)) rc = fail(HDG_ERR_ARG, err);

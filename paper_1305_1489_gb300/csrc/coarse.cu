@@ -444,6 +444,14 @@ extern "C" {
 int hdg_set_coarse_space(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t* nodes, const double* weights) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (M->stream) cudaStreamSynchronize(M->stream);
+  // the cached PCG graphs hold pointers into the old coarse space: rebuild them at the next solve
+  cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32};
+  for (cudaGraphExec_t* g : gs)
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  M->graphs_tl = false;
   coarse_free(M);
   if (nlev == 0) return HDG_OK;
   return set_coarse(M, nlev, sizes, nodes, weights);

@@ -94,6 +94,12 @@ def test_two_level_solve_matches_direct_and_saves_iterations(precision):
     M.set_coarse_space(None, None, None)
     _, it3, _ = M.solve_trace(1e-10, 5000, precision=prec)
     assert it3 == it_bj
+    # setting the coarse space again (new device arrays) after solves with cached graphs
+    M.set_coarse_space(sizes, nodes, weights)
+    u4, it4, _ = M.solve_trace(1e-10, 5000, precision=prec)
+    M.set_coarse_space(sizes, nodes, weights)
+    u5, it5, _ = M.solve_trace(1e-10, 5000, precision=prec)
+    assert it4 == it5 and abs(it4 - it_tl) <= 2 and rel(u5.cpu().numpy(), uo) < 1e-8
 
 
 def test_two_level_with_neumann_faces_and_k3():
