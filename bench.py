@@ -237,6 +237,8 @@ def run_gpu(args, rank, world, local_rank):
     step_prec = HDG_MIXED_FP32 if args.solve == "mixed" else HDG_FP64
     if args.coarse:
         M.set_coarse_space(*hierarchy)
+    M.assemble_condense(asm_prec)
+    tuned = M.autotune() if args.autotune else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def ev():
@@ -390,7 +392,8 @@ def run_gpu(args, rank, world, local_rank):
                    + " PCG to 1e-10 relative residual, "
                    + ("two-level (block-Jacobi + P1 V-cycle) preconditioner" if args.coarse else
                       "block-Jacobi preconditioner"),
-                   "coarse_levels": hierarchy[0] if args.coarse else None},
+                   "coarse_levels": hierarchy[0] if args.coarse else None,
+                   "autotune": ({"face_blocks": tuned[0], "fp64_iteration_ms": tuned[1]} if tuned else None)},
         "phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
                       "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
         "solve_time_to_1e-10": solve,
@@ -476,6 +479,106 @@ def run_batch(args):
     return out
 
 
+def run_learned(args):
+    """The learned initial guess on the random-field workload: 32^3 x 6 Kuhn cube (196,608
+    elements), k = 2, kappa = exp(g) with g a Gaussian random field (sigma 1, correlation
+    length 0.2, 128 Fourier modes), c = f = 1, u = 0 on the whole boundary.  The network
+    (g at the 3,375 interior nodes of the 16^3 grid -> tanh layer -> the coarse P1 field on that
+    grid) is trained with the library's kernels on the coarse Galerkin projections of the
+    trace solutions of `learned_train` fields and evaluated on `learned_eval` held-out fields:
+    energy error of the initial guess, and PCG iterations and time to 1e-10 from the zero start
+    and from the learned guess (guess time included), for block-Jacobi and two-level PCG in
+    FP64 and mixed precision."""
+    import torch
+
+    from paper_1305_1489_gb300 import HDG_FP64, HDG_MIXED_FP32, HDGMesh, build
+    from paper_1305_1489_gb300.learned import CoarseSpace, LearnedGuess
+    from workloads import boundary_faces, kuhn_coarse_interpolation, kuhn_cube, kuhn_grid_points, kuhn_p1_hierarchy
+    from workloads.problems import cube32_k2_grf, grf_frequencies, grf_sample
+
+    build()
+    prob = cube32_k2_grf(0)
+    c, e = kuhn_cube(prob.s)
+    d, n = boundary_faces(c, e, prob.classify)
+    M = HDGMesh(c, e, d, n, prob.k)
+    M.set_boundary_data(torch.zeros(M.nfc, M.nf, dtype=torch.float64, device="cuda"))
+    M.set_inner_tolerance(args.inner_rtol)
+    ones = torch.ones(M.nelt, M.nq, dtype=torch.float64, device="cuda")
+    sc = prob.s // 2
+    nodes, weights, nc = kuhn_coarse_interpolation(prob.s, sc, interior_only=True)
+    cs = CoarseSpace(nodes, weights, nc)
+    lg = LearnedGuess(M, cs, grf_frequencies(), 1.0, ones, ones, kuhn_grid_points(sc), hidden=(256,), seed=3)
+    hierarchy = kuhn_p1_hierarchy(prob.s, prob.dirichlet_planes)
+    sync = torch.cuda.synchronize
+
+    t0 = time.perf_counter()
+    A, T, its = lg.generate([grf_sample(i) for i in range(args.learned_train)])
+    sync()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = lg.fit(A, T, epochs=args.learned_epochs, batch=64, lr=1e-3)
+    sync()
+    t_fit = time.perf_counter() - t0
+    lg.fold_normalisation()
+    c_mean = torch.from_numpy(T.mean(axis=0)).cuda()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    rows = []
+    M.set_coarse_space(*hierarchy)
+    for j in range(args.learned_eval):
+        amps = grf_sample(100_000 + j)
+        lg.set_field(amps)
+        u, _, _ = M.solve_trace(1e-11, 20000)
+        uHu = float((u * M.apply(u)).sum())
+
+        def energy(x):
+            err = u - x
+            return float((err * M.apply(err)).sum()) / uHu
+        row = {"energy_net": energy(lg.guess(amps)[0]), "energy_mean": energy(cs.guess(M, c_mean)[0])}
+        variants = [("two_level", True)] + ([("block_jacobi", False)] if j < args.learned_bj_eval else [])
+        for pname, tl in variants:
+            if not tl:
+                M.set_coarse_space(None, None, None)
+            for prec_name, prec in (("fp64", HDG_FP64), ("mixed", HDG_MIXED_FP32)):
+                for start in ("zero", "learned"):
+                    lg.set_field(amps)  # fresh assembly: the Galerkin set-up is inside the time
+                    sync()
+                    a, b = ev(), ev()
+                    a.record()
+                    if start == "learned":
+                        uh, it, rr, used = lg.solve(amps, rtol=1e-10, maxit=40000, precision=prec, assemble=False)
+                    else:
+                        uh, it, rr = M.solve_trace(1e-10, 40000, precision=prec)
+                    b.record()
+                    sync()
+                    row[f"{pname}_{prec_name}_{start}"] = (it, a.elapsed_time(b), rr)
+            if not tl:
+                M.set_coarse_space(*hierarchy)
+        rows.append(row)
+
+    def med(key, idx):
+        vals = [r[key][idx] for r in rows if key in r]
+        return float(np.median(vals)) if vals else None
+    out = {"workload": "cube32_k2_grf: 32^3x6 Kuhn tets (196,608 elements), k=2, kappa=exp(GRF), c=f=1, u_D=0",
+           "train_fields": args.learned_train, "eval_fields": args.learned_eval,
+           "block_jacobi_eval_fields": min(args.learned_bj_eval, args.learned_eval),
+           "network": {"sizes": lg.sizes, "epochs": args.learned_epochs, "final_loss": hist[-1][1]},
+           "generate_s": t_gen, "train_s": t_fit, "coarse_solve_iterations_median": float(np.median(its)),
+           "energy_error_median": {"zero_start": 1.0, "mean_field_guess": float(np.median([r["energy_mean"] for r in rows])),
+                                   "learned_guess": float(np.median([r["energy_net"] for r in rows]))},
+           "median_iterations_and_ms": {}}
+    for pname in ("block_jacobi", "two_level"):
+        for prec_name in ("fp64", "mixed"):
+            for start in ("zero", "learned"):
+                k_ = f"{pname}_{prec_name}_{start}"
+                out["median_iterations_and_ms"][k_] = {"iterations": med(k_, 0), "ms": med(k_, 1),
+                                                       "max_relres": max([r[k_][2] for r in rows if k_ in r] or [0.0])}
+    M.close()
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -504,6 +607,8 @@ def main():
                     help="assembly arithmetic: double-float on the FP32 pipe or native FP64")
     ap.add_argument("--inner-rtol", type=float, default=1e-6, help="FP32 inner solve tolerance")
     ap.add_argument("--solve", default="mixed", choices=["mixed", "fp64"], help="trace solve precision in the step")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default persistent grid of the solve kernels")
     ap.add_argument("--no-coarse", dest="coarse", action="store_false",
                     help="block-Jacobi only (no two-level preconditioner) in the step")
     ap.add_argument("--batch", action="store_true", help="also time the 64-problem mixed-degree batch")
@@ -511,12 +616,20 @@ def main():
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
+    ap.add_argument("--learned", action="store_true", help="train and evaluate the learned guess and exit")
+    ap.add_argument("--learned-train", type=int, default=2000)
+    ap.add_argument("--learned-eval", type=int, default=200)
+    ap.add_argument("--learned-bj-eval", type=int, default=20, help="held-out fields also timed with block-Jacobi")
+    ap.add_argument("--learned-epochs", type=int, default=60)
     args = ap.parse_args()
     if args.profile_k1:
         profile_k1(args.profile_k1, asm=args.asm)
         return
     if args.batch_only:
         print(json.dumps({"batch": run_batch(args)}))
+        return
+    if args.learned:
+        print(json.dumps({"learned": run_learned(args)}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -215,8 +215,10 @@ int hdg_coarse_guess(hdg_mesh* mesh, const int32_t* nodes, const double* weights
 int hdg_nn_gemm(int M, int N, int K, const float* A, int sam, int sak, const float* B, int sbk,
                 int sbn, float* C, int ldc, float beta, const float* bias, int act, void* stream);
 int hdg_nn_tanh_bwd(int64_t n, const float* Y, float* dY, void* stream);
-/* hdg_nn_to_f64: y[i] = (double) x[i] (network output -> coarse coefficients).             */
+/* hdg_nn_to_f64: y[i] = (double) x[i] (network output -> coarse coefficients).
+ * hdg_nn_to_f32: y[i] = (float) x[i] (sampled field -> network input).                    */
 int hdg_nn_to_f64(int64_t n, const float* x, double* y, void* stream);
+int hdg_nn_to_f32(int64_t n, const double* x, float* y, void* stream);
 int hdg_nn_colsum(int M, int N, const float* dZ, float* db, void* stream);
 int hdg_nn_mse(int64_t n, const float* pred, const float* target, float* grad,
                float* loss_partial, void* stream);
@@ -242,6 +244,14 @@ int hdg_nn_adam(int64_t n, float* p, const float* g, float* m, float* v, float l
 int hdg_set_coarse_space(hdg_mesh* mesh, int nlev, const int64_t* sizes, const int32_t* nodes,
                          const double* weights);
 int hdg_coarse_precond_apply(hdg_mesh* mesh, const double* r, double* z);
+
+/* hdg_autotune: pick the persistent grid of the trace-solve kernels (4 to 32 blocks per SM)
+ * by timing one FP64 block-Jacobi PCG iteration (operator, update, direction) of the
+ * assembled system on the mesh stream; the choice is kept by the mesh (default 8 blocks per
+ * SM).  Outputs (nullable host pointers): the chosen number of blocks and the best time of
+ * one iteration in ms.  Requires hdg_assemble_condense (HDG_ERR_STATE) and the boundary
+ * data.  Not in the paper.                                                                   */
+int hdg_autotune(hdg_mesh* mesh, int* face_blocks, double* best_ms);
 
 /* Relative tolerance of each FP32 inner solve of the HDG_MIXED_FP32 trace solve (default
  * 1e-4): every outer FP64 refinement step asks the inner PCG for this residual reduction.  */

@@ -257,6 +257,20 @@ class HDGMesh:
             raise ValueError("nodes and weights must both be [R, 4]")
         _lib.check(lib.hdg_set_coarse_space(self._h, len(sz), _ptr(sz), _ptr(nd), _ptr(wt)))
 
+    def autotune(self):
+        """Pick the persistent grid of the trace-solve kernels by timing (hdg_autotune);
+        returns (blocks, ms per FP64 PCG iteration)."""
+        nb, ms = C.c_int(0), C.c_double(0.0)
+        _lib.check(_lib.load().hdg_autotune(self._h, C.byref(nb), C.byref(ms)))
+        return nb.value, ms.value
+
+    def apply(self, x):
+        """y = H x on the free faces (hdg_trace_apply; Dirichlet rows 0)."""
+        y = self._empty(self.nfc, self.d2)
+        _lib.check(_lib.load().hdg_trace_apply(self._h, _dev_f64(x, (self.nfc, self.d2), "x").data_ptr(),
+                                               y.data_ptr()))
+        return y
+
     def precond_apply(self, r):
         z = self._empty(self.nfc, self.d2)
         _lib.check(_lib.load().hdg_coarse_precond_apply(self._h, _dev_f64(r, (self.nfc, self.d2), "r").data_ptr(),

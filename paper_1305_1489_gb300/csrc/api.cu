@@ -276,6 +276,11 @@ int hdg_trace_apply(hdg_mesh* M, const double* x, double* y) {
   return trace_apply(M, x, y);
 }
 
+int hdg_autotune(hdg_mesh* M, int* face_blocks, double* best_ms) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  return autotune_face_grid(M, face_blocks, best_ms);
+}
+
 int hdg_trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {
   if (!M || !x || !r) return fail(HDG_ERR_ARG, "NULL argument");
   return trace_residual(M, x, r, rnorm, bnorm);

@@ -13,6 +13,7 @@
 // inverse of the coarsest level (Gauss-Jordan, one CTA) complete it.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <numeric>
 #include <vector>
 
@@ -194,7 +195,8 @@ void coarse_free(hdg_mesh* M) {
     cudaFree(c->rap_dst[l]);
     cudaFree(c->rap_w[l]);
   }
-  void* ptrs[] = {c->d_lv, c->vnodes, c->vw, c->vwd, c->elist, c->eslot, c->rc, c->e0, c->Adense, c->Ainv};
+  void* ptrs[] = {c->d_lv, c->vnodes, c->vw, c->vwd, c->gptr, c->gfi, c->gw, c->elist, c->eslot, c->rc, c->e0,
+                  c->Adense, c->Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -234,6 +236,12 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
   Coarse* c = new Coarse();
   M->coarse = c;
   c->nlev = nlev;
+  // HDG_COARSE_TAIL_MAX: largest level handled by the single-CTA part of the V-cycle (the
+  // finer levels run as grid-wide kernels); a tuning knob, default kTailMax
+  if (const char* tm = std::getenv("HDG_COARSE_TAIL_MAX")) {
+    const long v = std::strtol(tm, nullptr, 10);
+    if (v >= 1) c->tail_max = v;
+  }
   c->lv.resize(nlev);
   for (int l = 0; l < nlev; ++l) c->lv[l].n = sizes[l];
 
@@ -282,6 +290,38 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
   }
   std::vector<std::vector<int32_t>> rowptr(nlev), col(nlev);
   keys_to_csr(keys, n0, n0, rowptr[0], col[0]);
+  // restriction gather: for every level-0 node, the (free face, vertex slot, weight) entries
+  if (M->nfc >= ((int64_t)1 << 29)) {
+    coarse_free(M);
+    return fail(HDG_ERR_UNSUPPORTED, "too many faces for the restriction gather");
+  }
+  std::vector<int32_t> gptr(n0 + 1, 0), gfi;
+  std::vector<float> gw;
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int32_t> fill;
+    if (pass == 1) {
+      for (int64_t i = 0; i < n0; ++i) gptr[i + 1] += gptr[i];
+      gfi.resize(gptr[n0]);
+      gw.resize(gptr[n0]);
+      fill.assign(gptr.begin(), gptr.end() - 1);
+    }
+    for (int64_t f = 0; f < M->nfc; ++f) {
+      if (M->h_faces[4 * f + 3] == 1) continue;  // Dirichlet
+      for (int i = 0; i < 3; ++i) {
+        const int64_t v = M->h_faces[4 * f + i];
+        for (int j = 0; j < 4; ++j) {
+          const int32_t nd = vn[4 * v + j];
+          if (nd < 0) continue;
+          if (pass == 0) {
+            gptr[nd + 1]++;
+          } else {
+            gfi[fill[nd]] = (int32_t)(4 * f + i);
+            gw[fill[nd]++] = (float)vwd[4 * v + j];
+          }
+        }
+      }
+    }
+  }
   std::vector<int32_t> eslot((size_t)M->nelt * kElemNodes * kElemNodes, 0);
   for (int64_t K = 0; K < M->nelt; ++K)
     for (int u = 0; u < kElemNodes; ++u)
@@ -380,6 +420,9 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
   if (!rc) rc = upload(&c->vnodes, vn);
   if (!rc) rc = upload(&c->vw, vw);
   if (!rc) rc = upload(&c->vwd, vwd);
+  if (!rc) rc = upload(&c->gptr, gptr);
+  if (!rc) rc = upload(&c->gfi, gfi);
+  if (!rc) rc = upload(&c->gw, gw);
   if (!rc) rc = upload(&c->elist, elist);
   if (!rc) rc = upload(&c->eslot, eslot);
   if (!rc) rc = alloc(&c->rc, n0);

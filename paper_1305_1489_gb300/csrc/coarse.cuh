@@ -13,12 +13,16 @@
 // captured batch of iterations).
 //
 // Per PCG iteration (after q = H p and alpha):
-//   update_tl   x += alpha p, r -= alpha q, r.r, and rc = Pi^T r (face -> vertex -> level-0
-//               node, FP64 atomics; one thread per free face)
-//   l0_down     level 0 (grid): x0 = D0^-1 b0, t0 = b0 - A0 x0         (b0 = rc, FP32)
-//   vcycle      one CTA: levels 1 .. L-1 (restrict t0, smooth, exact coarsest, prolong, smooth)
-//   l0_up       level 0 (grid): x0' = x0 + P0 x1, e0 = x0' + D0^-1 (b0 - A0 x0')
-//   zc          z = B^-1 r + Pi e0, r.z, beta; clears rc for the next restriction
+//   update_tl   x += alpha p, r -= alpha q, r.r
+//   restrict    rc = Pi^T r: one warp per level-0 node gathers its (face, vertex slot, weight)
+//               list (built on the host), FP64 sums, no atomics
+//   down        level 0 and every level above kTailMax nodes (grid kernels): x = D^-1 b,
+//               t = b - A x; coarser grid levels first gather b = P^T t
+//   vcycle      one CTA: the remaining small levels (restrict, smooth, exact coarsest,
+//               prolong, smooth)
+//   up          grid levels, coarse to fine: x' = x + P x_coarse, out = x' + D^-1 (b - A x');
+//               level 0 writes e0
+//   zc          z = B^-1 r + Pi e0, r.z, beta
 // The V-cycle runs in FP32 (a preconditioner only has to be fixed, symmetric and positive);
 // every scalar of the Krylov method and the FP64 solve itself are unchanged.
 #pragma once
@@ -30,6 +34,7 @@ namespace hdg {
 
 constexpr int kVcThreads = 1024;  // threads of the single-CTA V-cycle kernel
 constexpr int kMaxCoarsest = 128;  // largest coarsest level (dense inverse)
+constexpr int kTailMax = 1024;     // levels up to this size run inside the single-CTA kernel
 
 // One level of the hierarchy on the device.  Level l holds A_l (CSR), the l1-Jacobi inverse
 // diagonal, its interpolation from level l+1 (ELL [n][4]) and the transpose of that
@@ -53,9 +58,12 @@ struct CoarseArgs {
   const double* T;        // [d2][3]  (varpi . D)^T Xi
   const int32_t* vnodes;  // [nver][4] level-0 nodes of each mesh vertex
   const float* vw;        // [nver][4] weights
-  double* rc;             // [n0] Pi^T r (FP64 accumulation)
+  double* rc;             // [n0] Pi^T r
   const float* e0;        // [n0] V-cycle output on level 0
   int64_t n0;
+  const int32_t* gptr;    // [n0+1] CSR of the restriction gather
+  const int32_t* gfi;     // 4 f + i: free face f whose vertex slot i carries the node
+  const float* gw;        // weight of the node at that vertex
 };
 
 struct Coarse {
@@ -65,6 +73,8 @@ struct Coarse {
   int32_t* vnodes = nullptr;
   float* vw = nullptr;
   double* vwd = nullptr;     // FP64 weights for the Galerkin set-up
+  int32_t *gptr = nullptr, *gfi = nullptr;  // restriction gather (CoarseArgs)
+  float* gw = nullptr;
   int32_t* elist = nullptr;  // [nelt][8] level-0 nodes touched by the element (-1 unused)
   int32_t* eslot = nullptr;  // [nelt][64] CSR positions in A_0 of the pairs of elist
   std::vector<int64_t> rap_n;             // Galerkin triple counts per level
@@ -75,28 +85,31 @@ struct Coarse {
   double* Adense = nullptr;  // [nL][nL] FP64 scratch of the coarsest inverse
   float* Ainv = nullptr;     // [nL][nL]
   int64_t nL = 0;
+  int64_t tail_max = kTailMax;  // levels up to this size run in the single-CTA kernel
   bool ready = false;        // Galerkin hierarchy built for the current assembly
 };
 
 // ------------------------------------------------------------------ per-iteration kernels
-// rc += Pi^T r for the free faces of a tile (called by one thread per face, a == 0)
+// rc = Pi^T r: one warp per level-0 node sums sum_a T[a][i] r[f][a] weighted over its list
 template <typename T, int D2>
-__device__ __forceinline__ void restrict_face(const CoarseArgs& CA, const T* __restrict__ r, int64_t e) {
-  double s[3] = {0.0, 0.0, 0.0};
+__global__ void restrict_gather_kernel(CoarseArgs CA, const T* __restrict__ r, const double* done) {
+  if (*done != 0.0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; n < CA.n0; n += nwarps) {
+    double s = 0.0;
+    for (int k = CA.gptr[n] + lane; k < CA.gptr[n + 1]; k += 32) {
+      const int32_t fi = CA.gfi[k];
+      const int64_t f = fi >> 2;
+      const int i = fi & 3;
+      double t = 0.0;
 #pragma unroll
-  for (int a = 0; a < D2; ++a) {
-    const double ra = (double)r[e * D2 + a];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) s[i] = fma(CA.T[a * 3 + i], ra, s[i]);
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int64_t v = CA.fverts[3 * e + i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int nd = CA.vnodes[4 * v + j];
-      if (nd >= 0) atomicAdd(CA.rc + nd, (double)CA.vw[4 * v + j] * s[i]);
+      for (int a = 0; a < D2; ++a) t = fma(CA.T[a * 3 + i], (double)r[f * D2 + a], t);
+      s = fma((double)CA.gw[k], t, s);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) CA.rc[n] = s;
   }
 }
 
@@ -118,49 +131,66 @@ __device__ __forceinline__ float prolong_face(const CoarseArgs& CA, int64_t e, i
   return s;
 }
 
-// level 0, down: x0 = D^-1 b, t0 = b - A x0 with b = rc (x0 of the neighbours computed on the fly)
-static __global__ void l0_down_kernel(CoarseLevel L0, const double* __restrict__ rc, const double* done) {
+// Grid-wide level kernels (levels with more than kTailMax nodes, and always level 0).  The
+// right-hand side of level 0 is rc (FP64); of a coarser level, its b.
+// down: x = D^-1 b, t = b - A x (the x of the neighbours formed on the fly from b)
+template <bool L0>
+__global__ void level_down_kernel(CoarseLevel L, const double* __restrict__ rc, const double* done) {
   if (*done != 0.0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L0.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float bi = (float)rc[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float bi = L0 ? (float)rc[i] : L.b[i];
     float ax = 0.f;
-    for (int k = L0.rowptr[i]; k < L0.rowptr[i + 1]; ++k) {
-      const int j = L0.col[k];
-      ax = fmaf(L0.valf[k], L0.dinv[j] * (float)rc[j], ax);
+    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; ++k) {
+      const int j = L.col[k];
+      ax = fmaf(L.valf[k], L.dinv[j] * (L0 ? (float)rc[j] : L.b[j]), ax);
     }
-    L0.x[i] = L0.dinv[i] * bi;
-    L0.t[i] = bi - ax;
+    L.x[i] = L.dinv[i] * bi;
+    L.t[i] = bi - ax;
   }
 }
 
-// level 0, up: x0' = x0 + P0 x1, e0 = x0' + D^-1 (b - A x0')
-__device__ __forceinline__ float l0_corrected(const CoarseLevel& L0, const float* __restrict__ x1, int64_t j) {
-  float v = L0.x[j];
+// restriction to a grid level: C.b = P^T t of the finer level P
+static __global__ void level_restrict_kernel(CoarseLevel P, CoarseLevel C, const double* done) {
+  if (*done != 0.0) return;
+  for (int64_t J = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; J < C.n; J += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = P.tptr[J]; k < P.tptr[J + 1]; ++k) s = fmaf(P.tw[k], P.t[P.tidx[k]], s);
+    C.b[J] = s;
+  }
+}
+
+// x' = x + P x_next (the coarse correction interpolated)
+__device__ __forceinline__ float level_corrected(const CoarseLevel& L, const float* __restrict__ xn, int64_t j) {
+  float v = L.x[j];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int nd = L0.pn[4 * j + q];
-    if (nd >= 0) v = fmaf(L0.pw[4 * j + q], x1[nd], v);
+    const int nd = L.pn[4 * j + q];
+    if (nd >= 0) v = fmaf(L.pw[4 * j + q], xn[nd], v);
   }
   return v;
 }
 
-static __global__ void l0_up_kernel(CoarseLevel L0, const float* __restrict__ x1, const double* __restrict__ rc,
-                             float* __restrict__ e0, const double* done) {
+// up: out = x' + D^-1 (b - A x')
+template <bool L0>
+__global__ void level_up_kernel(CoarseLevel L, const float* __restrict__ xn, const double* __restrict__ rc,
+                                float* __restrict__ out, const double* done) {
   if (*done != 0.0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L0.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x) {
     float ax = 0.f;
-    for (int k = L0.rowptr[i]; k < L0.rowptr[i + 1]; ++k) ax = fmaf(L0.valf[k], l0_corrected(L0, x1, L0.col[k]), ax);
-    e0[i] = l0_corrected(L0, x1, i) + L0.dinv[i] * ((float)rc[i] - ax);
+    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; ++k) ax = fmaf(L.valf[k], level_corrected(L, xn, L.col[k]), ax);
+    const float bi = L0 ? (float)rc[i] : L.b[i];
+    out[i] = level_corrected(L, xn, i) + L.dinv[i] * (bi - ax);
   }
 }
 
-// Levels 1 .. nlev-1 of the V-cycle in one CTA (the coarse levels are small: 1/8 of the
-// previous one each).  Input: lv[0].t (level-0 residual); output: lv[1].x.
-static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseLevel* __restrict__ lv, int nlev,
-                                                            const float* __restrict__ Ainv, const double* done) {
+// Levels first .. nlev-1 of the V-cycle in one CTA (the tail of small levels, at most
+// kTailMax nodes each).  Input: lv[first-1].t (residual of the finer level); output: lv[first].x.
+static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseLevel* __restrict__ lv, int first,
+                                                            int nlev, const float* __restrict__ Ainv,
+                                                            const double* done) {
   if (*done != 0.0) return;
   const int tid = threadIdx.x;
-  int l = 1;
+  int l = first;
   for (; l < nlev; ++l) {
     const CoarseLevel& P = lv[l - 1];  // interpolation l -> l-1 is stored on level l-1
     const CoarseLevel& C = lv[l];
@@ -189,7 +219,7 @@ static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseL
     }
     __syncthreads();
   }
-  for (l = nlev - 2; l >= 1; --l) {
+  for (l = nlev - 2; l >= first; --l) {
     const CoarseLevel& C = lv[l];
     const float* xc = lv[l + 1].x;
     for (int64_t i = tid; i < C.n; i += kVcThreads) {

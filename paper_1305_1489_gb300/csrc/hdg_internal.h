@@ -110,6 +110,7 @@ struct hdg_mesh {
   cudaGraphExec_t wgraph64 = nullptr, wgraph32 = nullptr;  // device-driven (conditional WHILE) PCG loops
   bool no_cond_graphs = false;  // the driver refused conditional nodes: host-driven loop
   int graph_iters = 0;
+  int face_blocks = 1216;         // persistent grid of the face kernels (hdg_autotune)
   hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL
   bool graphs_tl = false;         // the cached PCG graphs include the coarse correction
 };
@@ -146,4 +147,5 @@ int coarse_build(hdg_mesh* M);        // Galerkin hierarchy of the two-level pre
 void coarse_free(hdg_mesh* M);
 void coarse_invalidate(hdg_mesh* M);  // the Galerkin values must be rebuilt (new assembly)
 int coarse_precond_apply(hdg_mesh* M, const double* r, double* z);
+int autotune_face_grid(hdg_mesh* M, int* chosen, double* best_ms);
 }  // namespace hdg

@@ -159,6 +159,11 @@ __global__ void nn_to_f64_kernel(int64_t n, const float* __restrict__ x, double*
     y[i] = (double)x[i];
 }
 
+__global__ void nn_to_f32_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 // dZ = dY * (1 - Y^2) (tanh) in place
 __global__ void nn_tanh_bwd_kernel(int64_t n, const float* __restrict__ Y, float* __restrict__ dY) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -396,6 +401,14 @@ int hdg_nn_to_f64(int64_t n, const float* x, double* y, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return fail(HDG_ERR_ARG, "bad argument");
   if (n == 0) return HDG_OK;
   nn_to_f64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1216), 256, 0, (cudaStream_t)stream>>>(n, x, y);
+  HDG_CUDA_TRY(cudaGetLastError());
+  return HDG_OK;
+}
+
+int hdg_nn_to_f32(int64_t n, const double* x, float* y, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(HDG_ERR_ARG, "bad argument");
+  if (n == 0) return HDG_OK;
+  nn_to_f32_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1216), 256, 0, (cudaStream_t)stream>>>(n, x, y);
   HDG_CUDA_TRY(cudaGetLastError());
   return HDG_OK;
 }

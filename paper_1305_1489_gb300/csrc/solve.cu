@@ -10,9 +10,10 @@
 // C^K face-blocked, [K][l][s][a] = C^K[l d2 + a][s], so the row block of a face is one
 // contiguous array whose d2 columns are read by the face's d2 threads with unit stride.
 //
-// Scheduling: every face kernel runs on a persistent grid (at most kMaxBlocks blocks, each
-// looping over tiles of kNT / d2 whole faces), so the deterministic last-block reductions sum
-// at most kMaxBlocks per-block partials.  Scalars (alpha, beta, r.z, r.r) stay on the device;
+// Scheduling: every face kernel runs on a persistent grid (M->face_blocks blocks, at most
+// kMaxBlocks, each looping over tiles of kNT / d2 whole faces), so the deterministic
+// last-block reductions sum at most that many per-block partials.  hdg_autotune picks the
+// grid size per mesh by timing the trace operator.  Scalars (alpha, beta, r.z, r.r) stay on the device;
 // batches of iterations are captured in a CUDA graph and the host reads the convergence flag
 // after each replay.
 #include <algorithm>
@@ -25,7 +26,7 @@
 namespace hdg {
 
 constexpr int kNT = 128;          // threads per block in the face kernels
-constexpr int kMaxBlocks = 1216;  // 152 SMs x 8 resident blocks
+constexpr int kMaxBlocks = 152 * 32;  // largest persistent grid (size of the partials buffer)
 constexpr int kGraphIters = 16;   // PCG iterations per graph replay
 
 // scalar slots (double) of a solve
@@ -419,12 +420,11 @@ __global__ void pcg_dir_kernel(int64_t ntot, const T* __restrict__ z, T* __restr
     p[t] = fma(beta, p[t], z[t]);
 }
 
-// Two-level variant of the update: x += alpha p;  r -= alpha q;  r.r;  rc += Pi^T r.  The
-// preconditioned residual is formed by pcg_zc_kernel after the V-cycle.
+// Two-level variant of the update: x += alpha p;  r -= alpha q;  r.r.  The preconditioned
+// residual is formed by the restriction, the V-cycle and pcg_zc_kernel.
 template <typename T, int D2>
-__global__ void pcg_update_tl_kernel(FaceArgs F, CoarseArgs CA, T* __restrict__ x, T* __restrict__ r,
-                                     const T* __restrict__ p, const T* __restrict__ q, double* red,
-                                     unsigned int* counter, double* scal) {
+__global__ void pcg_update_tl_kernel(FaceArgs F, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                     const T* __restrict__ q, double* red, unsigned int* counter, double* scal) {
   if (scal[S_DONE] != 0.0) return;
   const T alpha = (T)scal[S_ALPHA];
   double v[1] = {0.0};
@@ -436,8 +436,6 @@ __global__ void pcg_update_tl_kernel(FaceArgs F, CoarseArgs CA, T* __restrict__ 
       r[T_.t] = rv;
       v[0] = fma((double)rv, (double)rv, v[0]);
     }
-    __syncthreads();  // the d2 entries of r of each face of the tile are updated
-    if (T_.act && T_.a == 0 && F.ftype[T_.e] != 1) restrict_face<T, D2>(CA, r, T_.e);
   }
   double out[1];
   if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
@@ -447,15 +445,7 @@ __global__ void pcg_update_tl_kernel(FaceArgs F, CoarseArgs CA, T* __restrict__ 
   }
 }
 
-// rc += Pi^T r (start of a two-level solve; rc zeroed before)
-template <typename T, int D2>
-__global__ void restrict_tl_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ r) {
-  const int64_t fpt = kNT;  // one thread per face
-  for (int64_t e = (int64_t)blockIdx.x * fpt + threadIdx.x; e < F.nfc; e += (int64_t)gridDim.x * fpt)
-    if (F.ftype[e] != 1) restrict_face<T, D2>(CA, r, e);
-}
-
-// z = B^-1 r + Pi e0;  r.z;  INIT: p = z and the convergence flag, else beta.  Clears rc.
+// z = B^-1 r + Pi e0;  r.z;  INIT: p = z and the convergence flag, else beta.
 template <typename T, int D2, bool INIT>
 __global__ void pcg_zc_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ Binv, const T* __restrict__ r,
                               T* __restrict__ z, T* __restrict__ p, double* red, unsigned int* counter, double* scal) {
@@ -470,8 +460,6 @@ __global__ void pcg_zc_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ B
     if (INIT) p[T_.t] = zv;
     v[0] = fma((double)r[T_.t], (double)zv, v[0]);
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < CA.n0; i += (int64_t)gridDim.x * blockDim.x)
-    CA.rc[i] = 0.0;
   double out[1];
   if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
     if (INIT) {
@@ -681,7 +669,8 @@ static FaceArgs face_args(hdg_mesh* M) {
 static int nblocks(hdg_mesh* M) {
   const int fpb = kNT / M->tab.d2;
   const int64_t tiles = (M->nfc + fpb - 1) / fpb;
-  return (int)(tiles < kMaxBlocks ? tiles : kMaxBlocks);
+  const int64_t cap = std::min<int64_t>(M->face_blocks, kMaxBlocks);
+  return (int)(tiles < cap ? tiles : cap);
 }
 
 static CoarseArgs coarse_args(hdg_mesh* M) {
@@ -694,17 +683,44 @@ static CoarseArgs coarse_args(hdg_mesh* M) {
   a.rc = c->rc;
   a.e0 = c->e0;
   a.n0 = c->lv[0].n;
+  a.gptr = c->gptr;
+  a.gfi = c->gfi;
+  a.gw = c->gw;
   return a;
 }
 
-// level-0 down, the single-CTA coarse levels and level-0 up of one V-cycle
-static void coarse_cycle(hdg_mesh* M, cudaStream_t st, const double* done) {
+// number of levels run as grid kernels: level 0 and the following levels above tail_max nodes
+static int grid_levels(const Coarse* c) {
+  int G = 1;
+  while (G < c->nlev - 1 && c->lv[G].n > c->tail_max) ++G;
+  return G;
+}
+
+// kernels of one coarse correction (restriction of r, V-cycle): 2 G + 2
+static int coarse_cycle_kernels(const Coarse* c) { return 2 * grid_levels(c) + 2; }
+
+// restriction of r and one V-cycle: grid levels down, the single-CTA tail, grid levels up
+template <typename T, int D2>
+static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStream_t st, const double* done) {
   Coarse* c = M->coarse;
-  const CoarseLevel& L0 = c->lv[0];
-  const int g0 = (int)std::min<int64_t>((L0.n + 255) / 256, kMaxBlocks);
-  l0_down_kernel<<<g0, 256, 0, st>>>(L0, c->rc, done);
-  vcycle_kernel<<<1, kVcThreads, 0, st>>>(c->d_lv, c->nlev, c->Ainv, done);
-  l0_up_kernel<<<g0, 256, 0, st>>>(L0, c->lv[1].x, c->rc, c->e0, done);
+  const int G = grid_levels(c);
+  auto grid = [](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, kMaxBlocks); };
+  const int gr = (int)std::min<int64_t>((c->lv[0].n + 7) / 8, 152 * 16);  // one warp per node
+  restrict_gather_kernel<T, D2><<<gr, 256, 0, st>>>(CA, r, done);
+  level_down_kernel<true><<<grid(c->lv[0].n), 256, 0, st>>>(c->lv[0], c->rc, done);
+  for (int l = 1; l < G; ++l) {
+    level_restrict_kernel<<<grid(c->lv[l].n), 256, 0, st>>>(c->lv[l - 1], c->lv[l], done);
+    level_down_kernel<false><<<grid(c->lv[l].n), 256, 0, st>>>(c->lv[l], nullptr, done);
+  }
+  vcycle_kernel<<<1, kVcThreads, 0, st>>>(c->d_lv, G, c->nlev, c->Ainv, done);
+  for (int l = G - 1; l >= 0; --l) {
+    const float* xn = (l + 1 == G) ? c->lv[G].x : c->lv[l + 1].t;
+    float* out = (l == 0) ? c->e0 : c->lv[l].t;
+    if (l == 0)
+      level_up_kernel<true><<<grid(c->lv[0].n), 256, 0, st>>>(c->lv[0], xn, c->rc, out, done);
+    else
+      level_up_kernel<false><<<grid(c->lv[l].n), 256, 0, st>>>(c->lv[l], xn, nullptr, out, done);
+  }
 }
 
 // graphs captured with or without the coarse correction are not interchangeable
@@ -824,14 +840,12 @@ struct Solver {
     const bool tl = M->coarse != nullptr && M->coarse->ready;
     match_graphs(M, tl);
     const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
-    const int per_it = tl ? 7 : 3;  // kernels per iteration
+    const int per_it = tl ? 4 + coarse_cycle_kernels(M->coarse) : 3;  // kernels per iteration
     pcg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
     if (tl) {
-      HDG_CUDA_TRY(cudaMemsetAsync(CA.rc, 0, sizeof(double) * CA.n0, M->stream));
-      restrict_tl_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, CA, r);
-      coarse_cycle(M, M->stream, scal + S_DONE);
+      coarse_cycle<T, D2>(M, CA, r, M->stream, scal + S_DONE);
       pcg_zc_kernel<T, D2, true><<<nb, kNT, 0, M->stream>>>(F, CA, Binv, r, z, p, M->d_red, M->d_counter, scal);
-      M->launches += 6;
+      M->launches += 2 + coarse_cycle_kernels(M->coarse);
     } else {
       pcg_precond_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, Binv, r, z, p, M->d_red, M->d_counter, scal);
       M->launches += 2;
@@ -842,8 +856,8 @@ struct Solver {
     auto iteration = [&](cudaStream_t st) {
       pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
       if (tl) {
-        pcg_update_tl_kernel<T, D2><<<nb, kNT, 0, st>>>(F, CA, x, r, p, q, M->d_red, M->d_counter, scal);
-        coarse_cycle(M, st, scal + S_DONE);
+        pcg_update_tl_kernel<T, D2><<<nb, kNT, 0, st>>>(F, x, r, p, q, M->d_red, M->d_counter, scal);
+        coarse_cycle<T, D2>(M, CA, r, st, scal + S_DONE);
         pcg_zc_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, CA, Binv, r, z, p, M->d_red, M->d_counter, scal);
       } else {
         pcg_update_kernel<T, D2><<<nb, kNT, 0, st>>>(F, Binv, x, r, z, p, q, M->d_red, M->d_counter, scal);
@@ -1048,6 +1062,71 @@ struct Solver {
     return HDG_OK;
   }
 
+  // Time one block-Jacobi PCG iteration (operator, update with its reductions, direction) in
+  // FP64 for persistent grids of 4, 8, 16 and 32 blocks per SM; keep the fastest.  Cached
+  // graphs are rebuilt when the grid changes.
+  static int autotune(hdg_mesh* M, int* chosen, double* best_ms) {
+    int rc = ensure_workspace(M, false);
+    if (rc) return rc;
+    rc = prepare_rhs(M);
+    if (rc) return rc;
+    const int old = M->face_blocks;
+    const int64_t nv = M->nfc * D2;
+    const int cands[] = {152 * 4, 152 * 8, 152 * 16, 152 * 32};
+    double* scal = M->d_scal + S_NSCAL;  // scratch scalars: never done, so every kernel runs
+    double hs[S_NSCAL] = {0};
+    hs[S_TOL2] = -1.0;
+    hs[S_MAXIT] = 1e30;
+    hs[S_RZ] = 1.0;
+    HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
+    HDG_CUDA_TRY(cudaMemcpyAsync(M->d_p, M->d_b, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
+    HDG_CUDA_TRY(cudaMemcpyAsync(M->d_r, M->d_b, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
+    HDG_CUDA_TRY(cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, M->stream));
+    cudaEvent_t a, b;
+    HDG_CUDA_TRY(cudaEventCreate(&a));
+    HDG_CUDA_TRY(cudaEventCreate(&b));
+    int best = old;
+    float best_t = 1e30f;
+    FaceArgs F = face_args(M);
+    auto iteration = [&](int nb) {
+      pcg_matvec_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_p, M->d_q, M->d_red, M->d_counter,
+                                                               scal);
+      pcg_update_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_BJ, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q,
+                                                               M->d_red, M->d_counter, scal);
+      pcg_dir_kernel<double><<<nb, kNT, 0, M->stream>>>(nv, M->d_z, M->d_p, scal);
+    };
+    for (int cand : cands) {
+      M->face_blocks = cand;
+      const int nb = nblocks(M);
+      iteration(nb);  // warm-up
+      HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
+      for (int rep = 0; rep < 4; ++rep) iteration(nb);
+      HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
+      HDG_CUDA_TRY(cudaEventSynchronize(b));
+      float ms = 0.f;
+      HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+      M->launches += 15;
+      if (ms < best_t) {
+        best_t = ms;
+        best = cand;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    M->face_blocks = best;
+    if (best != old) {
+      cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg};
+      for (cudaGraphExec_t* g : gs)
+        if (*g) {
+          cudaGraphExecDestroy(*g);
+          *g = nullptr;
+        }
+    }
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t / 4.0;
+    return HDG_OK;
+  }
+
   // z = B^-1 r + Pi V(Pi^T r): one application of the two-level preconditioner (FP64 vectors)
   static int precond_apply(hdg_mesh* M, const double* r, double* z) {
     int rc = ensure_workspace(M, false);
@@ -1063,12 +1142,10 @@ struct Solver {
     const CoarseArgs CA = coarse_args(M);
     double* scal = M->d_scal + S_NSCAL;
     HDG_CUDA_TRY(cudaMemsetAsync(scal, 0, sizeof(double) * S_NSCAL, M->stream));
-    HDG_CUDA_TRY(cudaMemsetAsync(CA.rc, 0, sizeof(double) * CA.n0, M->stream));
-    restrict_tl_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, CA, r);
-    coarse_cycle(M, M->stream, scal + S_DONE);
+    coarse_cycle<double, D2>(M, CA, r, M->stream, scal + S_DONE);
     pcg_zc_kernel<double, D2, true><<<nb, kNT, 0, M->stream>>>(F, CA, M->d_BJ, r, z, M->d_q, M->d_red, M->d_counter,
                                                                scal);
-    M->launches += 5;
+    M->launches += 1 + coarse_cycle_kernels(M->coarse);
     HDG_CUDA_TRY(cudaGetLastError());
     HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
     return HDG_OK;
@@ -1250,6 +1327,17 @@ int trace_apply(hdg_mesh* M, const double* x, double* y) {
     case 6: return Solver<6>::apply(M, x, y);
     case 10: return Solver<10>::apply(M, x, y);
     case 15: return Solver<15>::apply(M, x, y);
+  }
+  return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
+}
+
+int autotune_face_grid(hdg_mesh* M, int* chosen, double* best_ms) {
+  if (!M->assembled) return fail(HDG_ERR_STATE, "autotune before hdg_assemble_condense");
+  switch (M->tab.d2) {
+    case 3: return Solver<3>::autotune(M, chosen, best_ms);
+    case 6: return Solver<6>::autotune(M, chosen, best_ms);
+    case 10: return Solver<10>::autotune(M, chosen, best_ms);
+    case 15: return Solver<15>::autotune(M, chosen, best_ms);
   }
   return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }

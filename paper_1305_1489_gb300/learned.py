@@ -1,8 +1,8 @@
 """Learned initial guess for the trace solve (argument marshalling over libhdg's kernels).
 
-A small network phi_theta maps the parameters xi of a coefficient field (here the amplitudes
-of a Gaussian random field, kappa = exp(g)) to the coefficients c of a continuous
-piecewise-linear coarse field.  Its training targets are the coarse Galerkin solutions
+A small network phi_theta maps a coefficient field kappa = exp(g) (here g a Gaussian random
+field with parameters xi), seen through g at the coarse nodes, to the coefficients c of a
+continuous piecewise-linear coarse field.  Its training targets are the coarse Galerkin solutions
 c* = (Pi^T H Pi)^-1 Pi^T b of the trace system (hdg_coarse_solve), i.e. the trace in range(Pi)
 closest to the solution in the energy norm.  At solve time x0 = alpha Pi phi_theta(xi) with the
 energy-optimal alpha (hdg_coarse_guess), and PCG runs from x0 to the same residual tolerance as
@@ -173,9 +173,11 @@ class LearnedGuess:
     mesh:   an HDGMesh whose coefficients are set with the arrays this object owns
     coarse: CoarseSpace on a coarser nested grid
     omega:  [M, 3] frequencies of the field, sigma its standard deviation
+    feature_points: [nfeat, 3] points where g is sampled as the network's input (the coarse
+            nodes)
     """
 
-    def __init__(self, mesh, coarse, omega, sigma, c, f, hidden=(256, 256), seed=7,
+    def __init__(self, mesh, coarse, omega, sigma, c, f, feature_points, hidden=(256, 256), seed=7,
                  assemble_precision=None):
         import torch
         from . import HDG_DF32
@@ -186,10 +188,21 @@ class LearnedGuess:
         self.kappa = torch.empty_like(self.X)
         self.c, self.f = c, f
         self.asm = HDG_DF32 if assemble_precision is None else assemble_precision
-        self.sizes = [2 * self.nmodes, *hidden, coarse.nc]
+        P = torch.from_numpy(np.ascontiguousarray(feature_points, np.float64)).cuda()
+        self.FX, self.FY, self.FZ = (P[:, i].contiguous() for i in range(3))
+        self.sizes = [P.shape[0], *hidden, coarse.nc]
         self.net = MLP(self.sizes, seed=seed)
         self.mean = self.std = None
         self.history = []
+
+    def features(self, amps):
+        """Network input of the field xi: g at the feature points (FP32 device [nfeat])."""
+        import torch
+        g = fourier_field(self.FX, self.FY, self.FZ, self.omega, amps, self.sigma, False)
+        out = torch.empty(g.numel(), dtype=torch.float32, device="cuda")
+        _lib.check(_lib.load().hdg_nn_to_f32(g.numel(), _p(g), _p(out),
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return out
 
     # -- one field on the mesh
     def set_field(self, amps):
@@ -205,14 +218,16 @@ class LearnedGuess:
         return c, it, rr
 
     def generate(self, amps_list, rtol=1e-8):
-        """Training pairs: inputs [N, 2M] and targets [N, nc] (host, float64)."""
+        """Training pairs: inputs [N, nfeat] (host, float32) and targets [N, nc] (host, float64)."""
         T = np.empty((len(amps_list), self.coarse.nc))
+        A = np.empty((len(amps_list), self.sizes[0]), np.float32)
         its = []
         for i, a in enumerate(amps_list):
             c, it, _ = self.target(a, rtol)
             T[i] = c.cpu().numpy()
+            A[i] = self.features(a).cpu().numpy()
             its.append(it)
-        return np.asarray(amps_list, np.float64), T, its
+        return A, T, its
 
     # -- training (all arithmetic in the hdg_nn_* kernels)
     def fit(self, A, T, epochs=200, batch=64, lr=1e-3, seed=0):
@@ -238,7 +253,7 @@ class LearnedGuess:
     def predict(self, amps):
         """c = mean + std * phi(xi) as FP64 device [nc]."""
         import torch
-        x = torch.from_numpy(np.ascontiguousarray(np.asarray(amps, np.float32)[None, :])).cuda()
+        x = self.features(amps)[None, :]
         y, _ = self.net.forward(x)
         yd = torch.empty(self.coarse.nc, dtype=torch.float64, device="cuda")
         _lib.check(_lib.load().hdg_nn_to_f64(yd.numel(), _p(y), _p(yd), C.c_void_p(self.net.stream)))
@@ -259,14 +274,16 @@ class LearnedGuess:
         """x0 = alpha Pi phi(xi) (after set_field).  Returns (x0, alpha)."""
         return self.coarse.guess(self.mesh, self.predict(amps))
 
-    def solve(self, amps, rtol=1e-10, maxit=20000, precision=None, use_guess=True):
+    def solve(self, amps, rtol=1e-10, maxit=20000, precision=None, use_guess=True, assemble=True):
         """Trace solve of the field xi to the relative residual rtol, started from the learned
         x0.  The energy-optimal alpha makes x0 no worse than zero in the energy norm; a guess
         that is not finite or has alpha <= 0, or a solve from x0 that fails, falls back to the
-        zero start.  Returns (uhat, iters, relres, used_guess)."""
+        zero start.  assemble=False: the field is already set and assembled.  Returns
+        (uhat, iters, relres, used_guess)."""
         from . import HDG_FP64
         prec = HDG_FP64 if precision is None else precision
-        self.set_field(amps)
+        if assemble:
+            self.set_field(amps)
         if use_guess:
             x0, alpha = self.guess(amps)
             if np.isfinite(alpha) and alpha > 0.0:

@@ -41,9 +41,13 @@ def _oracle(prob, c, e, d, n, sizes, nodes, weights):
     return mesh, tab, H, tl.setup(mesh, tab, H, sizes, nodes, weights)
 
 
-@pytest.mark.parametrize("name,s,k,maxc", [("grf", 4, 2, 1), ("poly", 4, 1, 30), ("poly", 4, 3, 30),
-                                           ("grf", 8, 2, 64), ("poly", 4, 4, 30)])
-def test_precond_apply_matches_oracle(name, s, k, maxc):
+@pytest.mark.parametrize("name,s,k,maxc,tail", [("grf", 4, 2, 1, None), ("poly", 4, 1, 30, None),
+                                                ("poly", 4, 3, 30, None), ("grf", 8, 2, 64, None),
+                                                ("poly", 4, 4, 30, None), ("grf", 8, 2, 1, "8")])
+def test_precond_apply_matches_oracle(name, s, k, maxc, tail, monkeypatch):
+    # tail = largest level of the single-CTA part; "8" puts the 27-node level on grid kernels
+    if tail is not None:
+        monkeypatch.setenv("HDG_COARSE_TAIL_MAX", tail)
     prob, c, e, d, n = _case(name, s, k)
     sizes, nodes, weights = kuhn_p1_hierarchy(s, prob.dirichlet_planes, max_coarsest=maxc)
     mesh, tab, H, (Binv, Pi, As, Ps) = _oracle(prob, c, e, d, n, sizes, nodes, weights)

@@ -8,5 +8,6 @@ no quadrature, no basis, no local solver.  Both the oracle and the CUDA path eva
 these functions at their own quadrature nodes.
 """
 
-from .mesh import boundary_faces, kuhn_coarse_interpolation, kuhn_cube, kuhn_p1_hierarchy  # noqa: F401
+from .mesh import (boundary_faces, kuhn_coarse_interpolation, kuhn_cube, kuhn_grid_points,  # noqa: F401
+                   kuhn_p1_hierarchy)
 from .problems import PROBLEMS, Problem, get_problem  # noqa: F401

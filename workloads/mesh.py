@@ -195,3 +195,14 @@ def kuhn_p1_hierarchy(s, fixed_planes, max_coarsest=64):
     if len(sizes) < 2:
         raise ValueError("the hierarchy needs at least two levels")
     return sizes, np.concatenate(nodes).astype(np.int32), np.concatenate(weights)
+
+
+def kuhn_grid_points(s, interior_only=True):
+    """Coordinates [n, 3] of the vertices of the s^3 grid in vertex-id order (the numbering of
+    kuhn_coarse_interpolation's coarse nodes), interior vertices only if asked."""
+    i, j, l = _grid_ids(s)
+    pts = np.stack([i, j, l], axis=1) / s
+    if interior_only:
+        keep = (i > 0) & (i < s) & (j > 0) & (j < s) & (l > 0) & (l < s)
+        pts = pts[keep]
+    return pts
