@@ -199,6 +199,24 @@ def oracle_baseline(sample_elems, steps=1, warmup=0):
                       f"{cores} spawn workers with 1 BLAS thread each"}
 
 
+# ------------------------------------------------------------------ multi-rank helpers
+def max_over_ranks(vals, world, device):
+    """Element-wise maximum of per-rank timings (every rank gets the result)."""
+    if world <= 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(vals), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(nelt, steps, world, phase_ms):
+    """Whole-job throughput: every rank processes its own copy of the workload (replicas), so
+    the elements of all ranks over the slowest rank's time."""
+    return world * nelt * steps / (phase_ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -288,11 +306,8 @@ def run_gpu(args, rank, world, local_rank):
     t_rec = [c_.elapsed_time(d_) for _, _, c_, d_, *_ in recs]
     t_pp = [d_.elapsed_time(e_) for _, _, _, d_, e_, *_ in recs]
     phase_ms = sum(t_asm) + sum(t_rec)
-    if world > 1:
-        tt = torch.tensor([phase_ms, total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        phase_ms, total_ms = tt.tolist()
-    value = world * nelt * args.steps / (phase_ms / 1e3)
+    phase_ms, total_ms = max_over_ranks([phase_ms, total_ms], world, dev)
+    value = job_value(nelt, args.steps, world, phase_ms)
 
     if args.only_steps:
         return {"phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
@@ -427,7 +442,8 @@ def profile_k1(s_sub, launches=2, asm="df32"):
 def run_batch(args):
     """64 independent cube problems (s ~ U{8..24}, k ~ U{1..4}, kappa = 10^U(-1,1), c ~ U[0,5],
     Dirichlet everywhere, seed 4) solved as one batch: one CUDA graph launch (double-float
-    assembly, FP64 PCG to 1e-10 for every problem, recovery).  Returns elements/s."""
+    assembly, FP64 PCG to 1e-10 for every problem, recovery), with the block-Jacobi and with
+    the two-level preconditioner.  Returns elements/s of both."""
     import torch
 
     from paper_1305_1489_gb300 import HDG_DF32, HDGBatch, build
@@ -459,22 +475,29 @@ def run_batch(args):
             uD[fs] = pr.uD(FX[fs], FY[fs], FZ[fs])
         M.set_coefficients(dev(kap), dev(cq), dev(fq))
         M.set_boundary_data(dev(uD))
-    relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)  # warm-up + graph build
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(args.batch_reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(B.stream)
-        relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)
-        b.record(B.stream)
+    from workloads import kuhn_p1_hierarchy
+
+    def timed():
+        relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)  # warm-up + graph build
         torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    ms = float(np.median(ts))
-    out = {"problems": len(probs), "elements": int(nelt), "groups": [
-        {"k": G["k"], "problems": int(len(G["probs"])), "elements": int(G["mesh"].nelt), "iterations": int(it)}
-        for G, it in zip(B.groups, iters)],
-        "ms_per_batch": ms, "elements_per_s": nelt / (ms / 1e3), "max_relres": float(relres.max()),
-        "graph_launches_per_batch": 1}
+        ts = []
+        for _ in range(args.batch_reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(B.stream)
+            relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)
+            b.record(B.stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        return {"groups": [{"k": G["k"], "problems": int(len(G["probs"])), "elements": int(G["mesh"].nelt),
+                            "iterations": int(it)} for G, it in zip(B.groups, iters)],
+                "ms_per_batch": ms, "elements_per_s": nelt / (ms / 1e3), "max_relres": float(relres.max())}
+
+    out = {"problems": len(probs), "elements": int(nelt), "graph_launches_per_batch": 1,
+           "block_jacobi": timed()}
+    B.set_coarse_spaces([kuhn_p1_hierarchy(p.s, p.dirichlet_planes, max_coarsest=1, strict=False) for p in probs])
+    out["two_level"] = timed()
+    out["speedup_two_level"] = out["block_jacobi"]["ms_per_batch"] / out["two_level"]["ms_per_batch"]
     B.close()
     return out
 

@@ -349,6 +349,50 @@ class HDGBatch:
             mesh = HDGMesh(None, None, None, None, k.value, stream=self.stream, _handle=mh)
             self.groups.append(dict(mesh=mesh, k=k.value, probs=ids, elem_off=eo, face_off=fo))
 
+    def set_coarse_spaces(self, hierarchies):
+        """Two-level preconditioner for every group: hierarchies[p] = (sizes, nodes, weights) of
+        problem p in its own numbering (as for HDGMesh.set_coarse_space).  Per group the levels
+        of its problems are joined block-diagonally (node and vertex numbers offset in union
+        order); a problem with fewer levels repeats its coarsest level (identity rows) so that
+        all have the group's depth.  hierarchies=None removes the coarse spaces."""
+        for G in self.groups:
+            M = G["mesh"]
+            if hierarchies is None:
+                M.set_coarse_space(None, None, None)
+                continue
+            hs = [hierarchies[p] for p in G["probs"]]
+            depth = max(2, max(len(h[0]) for h in hs))
+            sizes = np.zeros(depth, np.int64)
+            per = []  # per problem: list of per-level row blocks (nodes, weights) and level sizes
+            for (sz, nd, wt), p in zip(hs, G["probs"]):
+                nver = len(self._arrs[p][0])
+                szp = list(sz) + [sz[-1]] * (depth - len(sz))
+                blocks = [(nd[:nver], wt[:nver])]
+                off = nver
+                for l in range(depth - 1):
+                    if l < len(sz) - 1:
+                        blocks.append((nd[off:off + sz[l]], wt[off:off + sz[l]]))
+                        off += sz[l]
+                    else:  # repeat the coarsest level
+                        n_ = szp[l]
+                        ident = np.full((n_, 4), -1, np.int32)
+                        ident[:, 0] = np.arange(n_)
+                        w_ = np.zeros((n_, 4))
+                        w_[:, 0] = 1.0
+                        blocks.append((ident, w_))
+                per.append((szp, blocks))
+                sizes += np.asarray(szp, np.int64)
+            rows_n, rows_w = [], []
+            for b in range(depth):  # block b: mesh vertices (b = 0) or level b-1 nodes
+                tgt_off = 0
+                for szp, blocks in per:
+                    nd, wt = blocks[b]
+                    nd = np.asarray(nd, np.int64)
+                    rows_n.append(np.where(nd >= 0, nd + tgt_off, -1))
+                    rows_w.append(np.asarray(wt, np.float64))
+                    tgt_off += szp[b]
+            M.set_coarse_space(sizes, np.concatenate(rows_n).astype(np.int32), np.concatenate(rows_w))
+
     def run(self, precision=HDG_FP64, rtol=1e-10, maxit=20000, raise_on_fail=True):
         relres = np.zeros(self.nprob)
         iters = np.zeros(len(self.groups), np.int32)

@@ -37,6 +37,7 @@ struct hdg_batch {
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   int built_prec = -1, built_maxit = -1;
+  std::vector<int> built_gens;  // coarse-space generation of every group mesh at graph build
   double built_rtol = -1.0;
 };
 
@@ -171,7 +172,10 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     if (!G.mesh->kappa) return fail(HDG_ERR_STATE, "coefficients not set on every batch group");
     if (G.mesh->beta_q) return fail(HDG_ERR_UNSUPPORTED, "batched solves are for reaction-diffusion (beta = 0)");
   }
-  if (!B->exec || B->built_prec != precision || B->built_rtol != rtol || B->built_maxit != maxit) {
+  std::vector<int> gens;
+  for (auto& G : B->groups) gens.push_back(G.mesh->coarse_gen);
+  if (!B->exec || B->built_prec != precision || B->built_rtol != rtol || B->built_maxit != maxit ||
+      B->built_gens != gens) {
     if (B->exec) {
       cudaGraphExecDestroy(B->exec);
       B->exec = nullptr;
@@ -199,6 +203,7 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     B->built_prec = precision;
     B->built_rtol = rtol;
     B->built_maxit = maxit;
+    B->built_gens = gens;
   }
   HDG_CUDA_TRY(cudaGraphLaunch(B->exec, B->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(B->stream));

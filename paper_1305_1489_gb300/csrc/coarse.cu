@@ -438,13 +438,12 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
   return HDG_OK;
 }
 
-int coarse_build(hdg_mesh* M) {
+// Galerkin values of the whole hierarchy on M->stream, no host synchronisation (also used
+// inside the batch graph); rows with a non-positive diagonal or pivot count in d_status[3].
+int coarse_launch_build(hdg_mesh* M) {
   Coarse* c = M->coarse;
-  if (!c) return fail(HDG_ERR_STATE, "no coarse space");
-  if (!M->assembled) return fail(HDG_ERR_STATE, "coarse space before hdg_assemble_condense");
   cudaStream_t st = M->stream;
   for (const CoarseLevel& L : c->lv) HDG_CUDA_TRY(cudaMemsetAsync(L.val, 0, sizeof(double) * L.nnz, st));
-  HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, st));
   const unsigned gb = (unsigned)std::min<int64_t>((M->nelt + kGalWarps - 1) / kGalWarps, 152 * 16);
 #define HDG_GAL(D)                                                                                              \
   galerkin0_kernel<D><<<gb, 32 * kGalWarps, 0, st>>>(M->nelt, M->d_C, M->d_facebyele, M->d_ftype, M->d_fverts, \
@@ -470,6 +469,17 @@ int coarse_build(hdg_mesh* M) {
   coarsest_inverse_kernel<<<1, 1024, 0, st>>>(c->lv[c->nlev - 1], c->Adense, c->Ainv, M->d_status + 3);
   M->launches += 2 + 2 * c->nlev;
   HDG_CUDA_TRY(cudaGetLastError());
+  return HDG_OK;
+}
+
+int coarse_build(hdg_mesh* M) {
+  Coarse* c = M->coarse;
+  if (!c) return fail(HDG_ERR_STATE, "no coarse space");
+  if (!M->assembled) return fail(HDG_ERR_STATE, "coarse space before hdg_assemble_condense");
+  cudaStream_t st = M->stream;
+  HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 3, 0, sizeof(int32_t), st));
+  int rc = coarse_launch_build(M);
+  if (rc) return rc;
   int32_t st4[4];
   HDG_CUDA_TRY(cudaMemcpyAsync(st4, M->d_status, sizeof(st4), cudaMemcpyDeviceToHost, st));
   HDG_CUDA_TRY(cudaStreamSynchronize(st));
@@ -495,6 +505,7 @@ int hdg_set_coarse_space(hdg_mesh* M, int nlev, const int64_t* sizes, const int3
       *g = nullptr;
     }
   M->graphs_tl = false;
+  M->coarse_gen++;
   coarse_free(M);
   if (nlev == 0) return HDG_OK;
   return set_coarse(M, nlev, sizes, nodes, weights);

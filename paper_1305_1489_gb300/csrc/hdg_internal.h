@@ -113,6 +113,7 @@ struct hdg_mesh {
   int face_blocks = 1216;         // persistent grid of the face kernels (hdg_autotune)
   hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL
   bool graphs_tl = false;         // the cached PCG graphs include the coarse correction
+  int coarse_gen = 0;             // incremented by every hdg_set_coarse_space
 };
 
 namespace hdg {
@@ -144,6 +145,7 @@ int batch_group_iterations(hdg_mesh* M, int* iters, int* status);
 int build_mesh(hdg_mesh* M, const double* coords, const int32_t* elems, const int32_t* dir, const int32_t* neu);
 int ensure_face_verts(hdg_mesh* M);   // d_fverts and d_Tproj (coarse prolongation)
 int coarse_build(hdg_mesh* M);        // Galerkin hierarchy of the two-level preconditioner
+int coarse_launch_build(hdg_mesh* M); // the same, enqueued on M->stream without synchronising
 void coarse_free(hdg_mesh* M);
 void coarse_invalidate(hdg_mesh* M);  // the Galerkin values must be rebuilt (new assembly)
 int coarse_precond_apply(hdg_mesh* M, const double* r, double* z);

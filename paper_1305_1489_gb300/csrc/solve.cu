@@ -1232,14 +1232,29 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const
   rhs_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
                                      M->d_scal + S_NSCAL);
   bj_kernel<D2><<<(unsigned)((M->nfc + 63) / 64), 64, 0, cs>>>(F, M->d_C, M->d_BJ, M->d_status, false);
+  const bool tl = M->coarse != nullptr;
+  const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
+  int rcb = tl ? coarse_launch_build(M) : HDG_OK;  // Galerkin hierarchy of this assembly
   cudaMemsetAsync(norms, 0, sizeof(double) * 2 * np, cs);
   prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_b, face_prob, M->nfc, D2, norms);
   batch_scalars_kernel<<<1, 32, 0, cs>>>(scal, norms, np, rtol, maxit, kGraphIters);
   pcg_init_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_b, M->d_x, false, M->d_r, M->d_red, M->d_counter,
                                                   scal);
-  pcg_precond_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, M->d_r, M->d_z, M->d_p, M->d_red, M->d_counter,
-                                                     scal);
+  if (tl) {
+    coarse_cycle<double, D2>(M, CA, M->d_r, cs, scal + S_DONE);
+    pcg_zc_kernel<double, D2, true><<<nb, kNT, 0, cs>>>(F, CA, M->d_BJ, M->d_r, M->d_z, M->d_p, M->d_red,
+                                                        M->d_counter, scal);
+  } else {
+    pcg_precond_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, M->d_r, M->d_z, M->d_p, M->d_red, M->d_counter,
+                                                       scal);
+  }
   M->stream = saved;
+  if (rcb) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(cs, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    return rcb;
+  }
   cudaError_t e2 = cudaStreamEndCapture(cs, &ga);
   if (e != cudaSuccess || e2 != cudaSuccess) return fail(HDG_ERR_CUDA, "batch graph capture (assembly/setup) failed");
   cudaGraphNode_t na, nw, nc;
@@ -1258,8 +1273,16 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const
   HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   for (int it = 0; it < kGraphIters; ++it) {
     pcg_matvec_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_p, M->d_q, M->d_red, M->d_counter, scal);
-    pcg_update_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_red,
-                                                      M->d_counter, scal);
+    if (tl) {
+      pcg_update_tl_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_x, M->d_r, M->d_p, M->d_q, M->d_red, M->d_counter,
+                                                           scal);
+      coarse_cycle<double, D2>(M, CA, M->d_r, cs, scal + S_DONE);
+      pcg_zc_kernel<double, D2, false><<<nb, kNT, 0, cs>>>(F, CA, M->d_BJ, M->d_r, M->d_z, M->d_p, M->d_red,
+                                                           M->d_counter, scal);
+    } else {
+      pcg_update_kernel<double, D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q,
+                                                        M->d_red, M->d_counter, scal);
+    }
     pcg_dir_kernel<double><<<nb, kNT, 0, cs>>>(nv, M->d_z, M->d_p, scal);
   }
   loop_control_kernel<<<1, 32, 0, cs>>>(h, scal, S_DONE, S_BODIES, S_MAXBODIES);

@@ -89,3 +89,30 @@ def test_coarse_interpolation_is_nested_p1():
     coarse = ((1 - xs[:, 0]) * cv[vid(v0)] + (xs[:, 0] - xs[:, 1]) * cv[vid(v1)]
               + (xs[:, 1] - xs[:, 2]) * cv[vid(v2)] + xs[:, 2] * cv[vid(v3)])
     assert np.abs(fine - coarse).max() < 1e-12
+
+
+def test_kuhn_interpolation_any_sizes():
+    """Linear interpolation between Kuhn grids of any two sizes reproduces linear fields, has
+    weights in [0, 1] summing to one, and for s_fine = 2 s_coarse is the nested midpoint rule."""
+    from workloads import kuhn_coarse_interpolation, kuhn_interpolation
+
+    def grid(s):
+        i = np.arange(s + 1)
+        I, J, L = np.meshgrid(i, i, i, indexing="ij")
+        return np.stack([a.transpose(2, 1, 0).ravel() for a in (I, J, L)], 1) / s
+
+    g = lambda p: 1.0 + p @ np.array([0.3, -2.0, 1.1])  # noqa: E731
+    for sf, sc in [(9, 5), (7, 4), (13, 7), (6, 3), (5, 5)]:
+        nd, w = kuhn_interpolation(sf, sc)
+        cf = g(grid(sc))
+        val = sum(np.where(nd[:, j] >= 0, w[:, j] * cf[np.maximum(nd[:, j], 0)], 0.0) for j in range(4))
+        assert np.abs(val - g(grid(sf))).max() < 1e-13
+        assert w.min() >= 0.0 and np.abs(w.sum(axis=1) - 1.0).max() < 1e-13
+    n1, w1 = kuhn_interpolation(8, 4)
+    n2, w2, _ = kuhn_coarse_interpolation(8, 4, interior_only=False)
+    D1, D2 = np.zeros((729, 125)), np.zeros((729, 125))
+    for j in range(4):
+        ok1, ok2 = n1[:, j] >= 0, n2[:, j] >= 0
+        np.add.at(D1, (np.nonzero(ok1)[0], n1[ok1, j]), w1[ok1, j])
+        np.add.at(D2, (np.nonzero(ok2)[0], n2[ok2, j]), w2[ok2, j])
+    assert np.abs(D1 - D2).max() == 0.0

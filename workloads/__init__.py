@@ -9,5 +9,5 @@ these functions at their own quadrature nodes.
 """
 
 from .mesh import (boundary_faces, kuhn_coarse_interpolation, kuhn_cube, kuhn_grid_points,  # noqa: F401
-                   kuhn_p1_hierarchy)
+                   kuhn_interpolation, kuhn_p1_hierarchy)
 from .problems import PROBLEMS, Problem, get_problem  # noqa: F401

@@ -155,17 +155,45 @@ def _kept(s, fixed_planes):
     return keep
 
 
-def kuhn_p1_hierarchy(s, fixed_planes, max_coarsest=64):
-    """Nested continuous P1 spaces for the two-level trace preconditioner of an s^3 Kuhn cube.
+def kuhn_interpolation(s_fine, s_coarse):
+    """Linear interpolation of the P1 field of the s_coarse^3 Kuhn grid at the vertices of the
+    s_fine^3 grid (any two sizes): a fine vertex at x lies in the coarse cube c = floor(x s_c)
+    and, with xi = x s_c - c sorted so that xi_a >= xi_b >= xi_d, in the Kuhn simplex
+    c, c + e_a, c + e_a + e_b, c + 1 whose barycentric weights are 1 - xi_a, xi_a - xi_b,
+    xi_b - xi_d, xi_d.  Returns nodes int64 [nver_fine, 4] (coarse vertex ids, -1 where the
+    weight is 0) and weights f64 [nver_fine, 4].  For s_fine = 2 s_coarse this is the nested
+    midpoint rule of kuhn_coarse_interpolation."""
+    i, j, l = _grid_ids(s_fine)
+    x = np.stack([i, j, l], axis=1) * (s_coarse / s_fine)
+    cell = np.minimum(np.floor(x + 1e-12), s_coarse - 1).astype(np.int64)
+    xi = np.clip(x - cell, 0.0, 1.0)
+    order = np.argsort(-xi, axis=1, kind="stable")
+    xs = np.take_along_axis(xi, order, axis=1)
+    w = np.stack([1.0 - xs[:, 0], xs[:, 0] - xs[:, 1], xs[:, 1] - xs[:, 2], xs[:, 2]], axis=1)
+    corner = cell.copy()
+    nodes = np.empty((len(i), 4), np.int64)
+    m1 = s_coarse + 1
+    nodes[:, 0] = corner[:, 0] + m1 * (corner[:, 1] + m1 * corner[:, 2])
+    for q in range(3):
+        corner[np.arange(len(i)), order[:, q]] += 1
+        nodes[:, q + 1] = corner[:, 0] + m1 * (corner[:, 1] + m1 * corner[:, 2])
+    w = np.where(np.abs(w) < 1e-13, 0.0, w)
+    nodes = np.where(w != 0.0, nodes, -1)
+    return nodes, w
+
+
+def kuhn_p1_hierarchy(s, fixed_planes, max_coarsest=64, strict=True):
+    """Continuous P1 spaces for the two-level trace preconditioner of an s^3 Kuhn cube.
 
     Level 0 is the P1 space of the mesh itself (one node per vertex not on a fixed plane);
-    level l+1 is the P1 space of the Kuhn grid with half the cells per side, down to the first
-    level with at most max_coarsest nodes.  Returns (sizes [nlev], nodes int32 [R, 4],
+    level l+1 is the P1 space of the Kuhn grid with ceil(s_l / 2) cells per side, down to the
+    first level with at most max_coarsest nodes.  Returns (sizes [nlev], nodes int32 [R, 4],
     weights f64 [R, 4]) with R = nver + sizes[0] + ... + sizes[nlev-2]: first, for every mesh
     vertex, its level-0 node (weight 1; -1 on a fixed plane); then, for every node of level l,
-    the level-(l+1) nodes and weights that interpolate it (coarse vertex: itself; midpoint of
-    a coarse Kuhn edge: the two ends with 1/2).  s must be a power of two times the coarsest
-    grid size.
+    the level-(l+1) nodes and weights that interpolate it (kuhn_interpolation; values on a
+    fixed plane are 0 and drop out).  For even sizes the levels are nested.  With
+    strict=False a grid too small to coarsen returns the levels built so far (possibly one
+    level, possibly empty) instead of raising.
     """
     keep = _kept(s, fixed_planes)
     ids = -np.ones((s + 1) ** 3, np.int64)
@@ -176,23 +204,24 @@ def kuhn_p1_hierarchy(s, fixed_planes, max_coarsest=64):
                         axis=1)]
     cur = s
     while sizes[-1] > max_coarsest:
-        if cur % 2 or cur < 2:
-            raise ValueError("cannot coarsen further: s must be a power of two times a small grid")
-        nd, wt, _ = kuhn_coarse_interpolation(cur, cur // 2, interior_only=False)
-        keep_c = _kept(cur // 2, fixed_planes)
-        cid = -np.ones((cur // 2 + 1) ** 3, np.int64)
+        nxt = (cur + 1) // 2
+        keep_c = _kept(nxt, fixed_planes)
+        if nxt == cur or not keep_c.any():
+            if strict:
+                raise ValueError("cannot coarsen further")
+            break
+        nd, wt = kuhn_interpolation(cur, nxt)
+        cid = -np.ones((nxt + 1) ** 3, np.int64)
         cid[keep_c] = np.arange(keep_c.sum())
         rows_f = np.nonzero(_kept(cur, fixed_planes))[0]  # level-l nodes in id order
-        nd, wt = nd[rows_f].astype(np.int64), wt[rows_f]
+        nd, wt = nd[rows_f], wt[rows_f]
         mapped = np.where(nd >= 0, cid[np.maximum(nd, 0)], -1)
         wt = np.where(mapped >= 0, wt, 0.0)
         nodes.append(mapped)
         weights.append(wt)
         sizes.append(int(keep_c.sum()))
-        if sizes[-1] == 0:
-            raise ValueError("the coarsest level has no free nodes")
-        cur //= 2
-    if len(sizes) < 2:
+        cur = nxt
+    if len(sizes) < 2 and strict:
         raise ValueError("the hierarchy needs at least two levels")
     return sizes, np.concatenate(nodes).astype(np.int32), np.concatenate(weights)
 
