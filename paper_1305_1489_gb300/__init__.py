@@ -258,11 +258,12 @@ class HDGMesh:
         _lib.check(lib.hdg_set_coarse_space(self._h, len(sz), _ptr(sz), _ptr(nd), _ptr(wt)))
 
     def autotune(self):
-        """Pick the persistent grid of the trace-solve kernels by timing (hdg_autotune);
-        returns (blocks, ms per FP64 PCG iteration)."""
-        nb, ms = C.c_int(0), C.c_double(0.0)
-        _lib.check(_lib.load().hdg_autotune(self._h, C.byref(nb), C.byref(ms)))
-        return nb.value, ms.value
+        """Pick the persistent grid of the trace-solve kernels and the launch shape of the
+        double-float assembly by timing (hdg_autotune); returns (blocks, ms per FP64 PCG
+        iteration, assembly threads per element, ms per assembly)."""
+        nb, ms, nt, kms = C.c_int(0), C.c_double(0.0), C.c_int(0), C.c_double(0.0)
+        _lib.check(_lib.load().hdg_autotune(self._h, C.byref(nb), C.byref(ms), C.byref(nt), C.byref(kms)))
+        return nb.value, ms.value, nt.value, kms.value
 
     def apply(self, x):
         """y = H x on the free faces (hdg_trace_apply; Dirichlet rows 0)."""

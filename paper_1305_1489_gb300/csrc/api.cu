@@ -241,6 +241,7 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   M->assembled = true;
+  M->asm_prec = precision;
   if (M->coarse) coarse_invalidate(M);
   M->rhs_ready = false;
   return check_status(M);
@@ -276,9 +277,42 @@ int hdg_trace_apply(hdg_mesh* M, const double* x, double* y) {
   return trace_apply(M, x, y);
 }
 
-int hdg_autotune(hdg_mesh* M, int* face_blocks, double* best_ms) {
+int hdg_autotune(hdg_mesh* M, int* face_blocks, double* iter_ms, int* k1_nthreads, double* k1_ms) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
-  return autotune_face_grid(M, face_blocks, best_ms);
+  int rc = autotune_face_grid(M, face_blocks, iter_ms);
+  if (rc) return rc;
+  // launch shapes of the double-float K1 (reaction-diffusion only): two timed launches each
+  float best_t = 1e30f;
+  int best = 0;
+  if (!M->beta_q) {
+    cudaEvent_t a, b;
+    HDG_CUDA_TRY(cudaEventCreate(&a));
+    HDG_CUDA_TRY(cudaEventCreate(&b));
+    for (int v = 0; v < k1_variants(M->k); ++v) {
+      M->k1_variant = v;
+      HDG_CUDA_TRY(launch_assemble_df(M));  // warm-up (sets the launch attributes)
+      HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
+      HDG_CUDA_TRY(launch_assemble_df(M));
+      HDG_CUDA_TRY(launch_assemble_df(M));
+      HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
+      HDG_CUDA_TRY(cudaEventSynchronize(b));
+      float ms = 0.f;
+      HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_t) {
+        best_t = ms;
+        best = v;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    M->k1_variant = best;
+    // restore the system of the caller's last assembly
+    rc = hdg_assemble_condense(M, M->asm_prec >= 0 ? M->asm_prec : HDG_FP64);
+    if (rc) return rc;
+  }
+  if (k1_nthreads) *k1_nthreads = k1_threads(M->k, M->k1_variant);
+  if (k1_ms) *k1_ms = best_t < 1e29f ? best_t / 2.0 : 0.0;
+  return HDG_OK;
 }
 
 int hdg_trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {

@@ -27,21 +27,35 @@ struct AsmDfArgs {
   int64_t nelt;
 };
 
+// Shared-memory plan.  The weighted coefficients kw, cw, fw are read only by the first phase
+// (masses and the load vector); C is first written three barriers later, so they share its
+// space.
 template <int K>
 struct AsmDfSmem {
   using D = Dims<K>;
   static constexpr int n = D::n, m = D::m, nq = D::nq;
-  static constexpr int o_kw = 0, o_cw = o_kw + nq, o_fw = o_cw + nq;
-  static constexpr int o_M = o_fw + nq;
+  static constexpr int o_M = 0;
   static constexpr int o_S = o_M + n * n;
   static constexpr int o_W = o_S + n * n;
   static constexpr int o_V = o_W + 3 * n * n;
   static constexpr int o_Wt = o_V + n * m;
   static constexpr int o_G = o_Wt + 4 * n * n;
   static constexpr int o_C = o_G + n * (m + 1);
+  static constexpr int o_kw = o_C, o_cw = o_kw + nq, o_fw = o_cw + nq;
+  static_assert(3 * nq <= m * m, "kw, cw, fw must fit in the space of C");
   static constexpr int total = o_C + m * m;
   static constexpr size_t bytes = sizeof(df) * total;
 };
+
+// Launch shapes of K1 per degree: variant 0 is the default; variant 1 trades threads per
+// element for resident elements per SM (hdg_autotune times both).
+template <int K, int V>
+struct K1Shape {
+  static constexpr int NT = K1Occupancy<K>::NT, MINB = K1Occupancy<K>::MINB;
+};
+template <> struct K1Shape<1, 1> { static constexpr int NT = 64, MINB = 16; };
+template <> struct K1Shape<2, 1> { static constexpr int NT = 128, MINB = 6; };
+template <> struct K1Shape<3, 1> { static constexpr int NT = 192, MINB = 4; };
 
 __device__ __forceinline__ df shfl_xor_df(df x, int o) {
   return df_make(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
@@ -103,8 +117,8 @@ __device__ __forceinline__ df ldg_df(const df* p) {
   return df_make(v.x, v.y);
 }
 
-template <int K, int NT>
-__global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_df_kernel(AsmDfArgs A) {
+template <int K, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   using D = Dims<K>;
   using SM = AsmDfSmem<K>;
   constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq;
@@ -354,17 +368,34 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_df_kernel(A
   }
 }
 
-template <int K>
-static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
-  constexpr int NT = K1Occupancy<K>::NT;
+template <int K, int V>
+static cudaError_t launch_df_shape(hdg_mesh* M, const AsmDfArgs& a) {
+  constexpr int NT = K1Shape<K, V>::NT, MINB = K1Shape<K, V>::MINB;
   const size_t smem = AsmDfSmem<K>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(assemble_df_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(assemble_df_kernel<K, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  assemble_df_kernel<K, NT><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  assemble_df_kernel<K, NT, MINB><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
   M->launches += 1;
   return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
+  if (K <= 3 && M->k1_variant == 1) return launch_df_shape<K, (K <= 3 ? 1 : 0)>(M, a);
+  return launch_df_shape<K, 0>(M, a);
+}
+
+int k1_variants(int k) { return k <= 3 ? 2 : 1; }
+int k1_threads(int k, int variant) {
+  switch (k) {
+    case 1: return variant ? K1Shape<1, 1>::NT : K1Shape<1, 0>::NT;
+    case 2: return variant ? K1Shape<2, 1>::NT : K1Shape<2, 0>::NT;
+    case 3: return variant ? K1Shape<3, 1>::NT : K1Shape<3, 0>::NT;
+    default: return K1Shape<4, 0>::NT;
+  }
 }
 
 cudaError_t launch_assemble_df(hdg_mesh* M) {
