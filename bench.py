@@ -43,7 +43,8 @@ FP64_MEASURED_TFLOPS = 1.19  # FMA-chain microbenchmark on this machine's GB300 (1 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one K1 launch at this workload,
 # from the ncu captures summarised under profiles/, valid while the kernel source is unchanged.
-K1_TRAFFIC = {"assemble_df.cu": {"sha256": "74db6c1e5a2a6d46675d7879426d673c9a9a18f26d04c2319e871196e47fa4ba", "bytes": 82824960 + 858117376},
+K1_TRAFFIC = {"assemble_df.cu": {"sha256": "0228074b1fbb564215919af5007c4837b3bb78181dd233923eaa170cf0cee6dc",
+                                 "bytes": 89852160 + 869804544},
               "assemble.cu": {"sha256": None, "bytes": None}}
 
 
