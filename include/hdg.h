@@ -245,16 +245,23 @@ int hdg_set_coarse_space(hdg_mesh* mesh, int nlev, const int64_t* sizes, const i
                          const double* weights);
 int hdg_coarse_precond_apply(hdg_mesh* mesh, const double* r, double* z);
 
-/* hdg_autotune: (1) pick the persistent grid of the trace-solve kernels (4 to 32 blocks per
- * SM) by timing one FP64 block-Jacobi PCG iteration (operator, update, direction) of the
- * assembled system; (2) pick the launch shape of the double-float assembly (threads per
- * element and resident elements per SM; k = 1..3 have two shapes) by timing it.  The choices
- * are kept by the mesh; the system of the caller's last hdg_assemble_condense is restored.
- * Outputs (nullable host pointers): blocks of the grid, ms of one PCG iteration, threads per
- * element of the assembly, ms of one assembly.  Requires hdg_assemble_condense
+/* hdg_autotune: (1) pick the persistent grids of the trace-solve kernels (4 to 32 blocks per
+ * SM), one for the FP64 and one for the FP32 iterations, by timing one block-Jacobi PCG
+ * iteration (operator, update, direction) of the assembled system in each precision;
+ * (2) pick the launch shape of the double-float assembly (threads per element and resident
+ * elements per SM; k = 1..3 have two shapes) by timing it.  The choices are kept by the
+ * mesh; the system of the caller's last hdg_assemble_condense is restored.  out (nullable,
+ * host) receives the choices and the best times.  Requires hdg_assemble_condense
  * (HDG_ERR_STATE) and the boundary data.  Not in the paper.                                */
-int hdg_autotune(hdg_mesh* mesh, int* face_blocks, double* iter_ms, int* k1_threads,
-                 double* k1_ms);
+typedef struct hdg_tuning {
+  int face_blocks;    /* FP64 persistent grid (blocks)                  */
+  int face_blocks32;  /* FP32 persistent grid (blocks)                  */
+  int k1_threads;     /* threads per element of the double-float K1     */
+  double iter_ms;     /* one FP64 block-Jacobi iteration at the choice  */
+  double iter32_ms;   /* one FP32 iteration at the choice               */
+  double k1_ms;       /* one double-float assembly at the choice        */
+} hdg_tuning;
+int hdg_autotune(hdg_mesh* mesh, hdg_tuning* out);
 
 /* Relative tolerance of each FP32 inner solve of the HDG_MIXED_FP32 trace solve (default
  * 1e-4): every outer FP64 refinement step asks the inner PCG for this residual reduction.  */

@@ -258,12 +258,15 @@ class HDGMesh:
         _lib.check(lib.hdg_set_coarse_space(self._h, len(sz), _ptr(sz), _ptr(nd), _ptr(wt)))
 
     def autotune(self):
-        """Pick the persistent grid of the trace-solve kernels and the launch shape of the
-        double-float assembly by timing (hdg_autotune); returns (blocks, ms per FP64 PCG
-        iteration, assembly threads per element, ms per assembly)."""
-        nb, ms, nt, kms = C.c_int(0), C.c_double(0.0), C.c_int(0), C.c_double(0.0)
-        _lib.check(_lib.load().hdg_autotune(self._h, C.byref(nb), C.byref(ms), C.byref(nt), C.byref(kms)))
-        return nb.value, ms.value, nt.value, kms.value
+        """Pick the persistent grids of the trace-solve kernels (FP64 and FP32) and the launch
+        shape of the double-float assembly by timing (hdg_autotune); returns a dict of the
+        choices and the best times."""
+        class Tuning(C.Structure):
+            _fields_ = [("face_blocks", C.c_int), ("face_blocks32", C.c_int), ("k1_threads", C.c_int),
+                        ("iter_ms", C.c_double), ("iter32_ms", C.c_double), ("k1_ms", C.c_double)]
+        t = Tuning()
+        _lib.check(_lib.load().hdg_autotune(self._h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def apply(self, x):
         """y = H x on the free faces (hdg_trace_apply; Dirichlet rows 0)."""
@@ -393,6 +396,15 @@ class HDGBatch:
                     rows_w.append(np.asarray(wt, np.float64))
                     tgt_off += szp[b]
             M.set_coarse_space(sizes, np.concatenate(rows_n).astype(np.int32), np.concatenate(rows_w))
+
+    def autotune(self, precision=HDG_DF32):
+        """hdg_autotune on every group mesh (assembles each group once first); the batch graph
+        is rebuilt with the tuned shapes at the next run.  Returns the choices per group."""
+        out = []
+        for G in self.groups:
+            G["mesh"].assemble_condense(precision)
+            out.append(G["mesh"].autotune())
+        return out
 
     def run(self, precision=HDG_FP64, rtol=1e-10, maxit=20000, raise_on_fail=True):
         relres = np.zeros(self.nprob)

@@ -62,7 +62,7 @@ _SIGS = {
     "hdg_nn_mse": [I64, P, P, P, P, P],
     "hdg_nn_adam": [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P],
     "hdg_set_coarse_space": [P, C.c_int, P, P, P],
-    "hdg_autotune": [P, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "hdg_autotune": [P, P],
     "hdg_coarse_precond_apply": [P, P, P],
     "hdg_solve_trace_noalloc": [P, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_recover": [P, P, P, P],

@@ -277,9 +277,10 @@ int hdg_trace_apply(hdg_mesh* M, const double* x, double* y) {
   return trace_apply(M, x, y);
 }
 
-int hdg_autotune(hdg_mesh* M, int* face_blocks, double* iter_ms, int* k1_nthreads, double* k1_ms) {
+int hdg_autotune(hdg_mesh* M, hdg_tuning* out) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
-  int rc = autotune_face_grid(M, face_blocks, iter_ms);
+  hdg_tuning t = {};
+  int rc = autotune_face_grid(M, &t);
   if (rc) return rc;
   // launch shapes of the double-float K1 (reaction-diffusion only): two timed launches each
   float best_t = 1e30f;
@@ -310,8 +311,9 @@ int hdg_autotune(hdg_mesh* M, int* face_blocks, double* iter_ms, int* k1_nthread
     rc = hdg_assemble_condense(M, M->asm_prec >= 0 ? M->asm_prec : HDG_FP64);
     if (rc) return rc;
   }
-  if (k1_nthreads) *k1_nthreads = k1_threads(M->k, M->k1_variant);
-  if (k1_ms) *k1_ms = best_t < 1e29f ? best_t / 2.0 : 0.0;
+  t.k1_threads = k1_threads(M->k, M->k1_variant);
+  t.k1_ms = best_t < 1e29f ? best_t / 2.0 : 0.0;
+  if (out) *out = t;
   return HDG_OK;
 }
 

@@ -9,6 +9,8 @@
 //   G = diag(T) E + sum_* diag(n_*) V^T W_*;  L_s L_s^T = S_u;  [H | h] = L_s^-1 [G^T | f];
 //   C^K = (n_l . n_l') o (V^T V) - H^T H + tauDD;  C_f^K = H^T h;
 //   recovery: [R_u | r_u] = L_s^-T [H | h],  Y = L^-T V,  MC_* = L^-T W_*.
+#include <cstdlib>
+
 #include "device_common.cuh"
 #include "device_df.cuh"
 #include "hdg_internal.h"
@@ -27,9 +29,10 @@ struct AsmDfArgs {
   int64_t nelt;
 };
 
-// Shared-memory plan.  The weighted coefficients kw, cw, fw are read only by the first phase
-// (masses and the load vector); C is first written three barriers later, so they share its
-// space.
+// Shared-memory plan.  C is formed in one pass near the end (C = (n_l . n_l') o V^T V
+// + tauDD - H^T H), so its space first holds the weighted coefficients kw, cw, fw (read only
+// by the first phase) and then the face-weighted sums Wt_l = sum_* n_{l*} W_* (read only by
+// the phase that forms G): WTF faces at a time, all four when they fit.
 template <int K>
 struct AsmDfSmem {
   using D = Dims<K>;
@@ -38,17 +41,19 @@ struct AsmDfSmem {
   static constexpr int o_S = o_M + n * n;
   static constexpr int o_W = o_S + n * n;
   static constexpr int o_V = o_W + 3 * n * n;
-  static constexpr int o_Wt = o_V + n * m;
-  static constexpr int o_G = o_Wt + 4 * n * n;
+  static constexpr int o_G = o_V + n * m;
   static constexpr int o_C = o_G + n * (m + 1);
   static constexpr int o_kw = o_C, o_cw = o_kw + nq, o_fw = o_cw + nq;
+  static constexpr int o_Wt = o_C;
+  static constexpr int WTF = (4 * n * n <= m * m) ? 4 : 2;  // faces of Wt held at once
   static_assert(3 * nq <= m * m, "kw, cw, fw must fit in the space of C");
+  static_assert(WTF * n * n <= m * m, "Wt must fit in the space of C");
   static constexpr int total = o_C + m * m;
   static constexpr size_t bytes = sizeof(df) * total;
 };
 
-// Launch shapes of K1 per degree: variant 0 is the default; variant 1 trades threads per
-// element for resident elements per SM (hdg_autotune times both).
+// Launch shapes of K1 per degree: variant 0 is the default; the others trade threads per
+// element for resident elements per SM (hdg_autotune times them all).
 template <int K, int V>
 struct K1Shape {
   static constexpr int NT = K1Occupancy<K>::NT, MINB = K1Occupancy<K>::MINB;
@@ -56,6 +61,14 @@ struct K1Shape {
 template <> struct K1Shape<1, 1> { static constexpr int NT = 64, MINB = 16; };
 template <> struct K1Shape<2, 1> { static constexpr int NT = 128, MINB = 6; };
 template <> struct K1Shape<3, 1> { static constexpr int NT = 192, MINB = 4; };
+template <> struct K1Shape<3, 2> { static constexpr int NT = 128, MINB = 5; };
+template <> struct K1Shape<4, 1> { static constexpr int NT = 128, MINB = 2; };
+
+// barrier among the warps 1 .. NT/32 - 1 (warp 0 is busy with a factorisation meanwhile)
+template <int NT>
+__device__ __forceinline__ void sync_workers() {
+  asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");
+}
 
 __device__ __forceinline__ df shfl_xor_df(df x, int o) {
   return df_make(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
@@ -248,23 +261,13 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     Ss[i * n + j] = v;
     Ss[j * n + i] = v;
   }
-  for (int t = tid; t < 4 * n * n; t += NT) {
+  constexpr int WTF = SM::WTF;
+  for (int t = tid; t < WTF * n * n; t += NT) {
     const int fl = t / (n * n), rem = t - fl * n * n;
     dacc s = dacc_zero();
 #pragma unroll
     for (int st = 0; st < 3; ++st) dacc_mac(s, s_nrm[fl][st], W[st * n * n + rem]);
     Wt[t] = dacc_result(s);
-  }
-  for (int t = tid; t < MP; t += NT) {
-    const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
-    const int fr = r / d2, fs = s / d2;
-    dacc b = dacc_zero();
-#pragma unroll 4
-    for (int l = 0; l < n; ++l) dacc_mac(b, V[l * m + r], V[l * m + s]);
-    df cv = df_mul(s_nn[fr][fs], dacc_result(b));
-    if (r == s) cv = df_add(cv, s_T[fr]);
-    Cs[r * m + s] = cv;
-    Cs[s * m + r] = cv;
   }
   __syncthreads();
 
@@ -272,19 +275,34 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     const bool ok = warp_cholesky_df<n>(Ss, invdS, lane);
     if (!ok && lane == 0) s_bad = 1;
   } else {
-    for (int t = tid - 32; t < n * m; t += NT - 32) {
-      const int j = t / m, r = t - j * m, fl = r / d2, a = r - fl * d2;
-      dacc g = dacc_zero();
-      dacc_mac(g, s_T[fl], ldg_df(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + j));
-      const df* wt = Wt + fl * n * n;
+    // G^T[j][r] = T_l E[r][j] + (V^T Wt_l)[r][j] for the columns r of face l, WTF faces per pass
+#pragma unroll 1
+    for (int f0 = 0; f0 < 4; f0 += WTF) {
+      if (f0 > 0) {
+        sync_workers<NT>();  // every column of the previous faces is done with Wt
+        for (int t = tid - 32; t < WTF * n * n; t += NT - 32) {
+          const int fl = f0 + t / (n * n), rem = t % (n * n);
+          dacc s = dacc_zero();
+#pragma unroll
+          for (int st = 0; st < 3; ++st) dacc_mac(s, s_nrm[fl][st], W[st * n * n + rem]);
+          Wt[t] = dacc_result(s);
+        }
+        sync_workers<NT>();
+      }
+      for (int t = tid - 32; t < n * WTF * d2; t += NT - 32) {
+        const int j = t / (WTF * d2), r = f0 * d2 + (t - j * (WTF * d2)), fl = r / d2, a = r - fl * d2;
+        dacc g = dacc_zero();
+        dacc_mac(g, s_T[fl], ldg_df(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + j));
+        const df* wt = Wt + (fl - f0) * n * n;
 #pragma unroll 4
-      for (int l = 0; l < n; ++l) dacc_mac(g, V[l * m + r], wt[l * n + j]);
-      Gt[j * (m + 1) + r] = dacc_result(g);
+        for (int l = 0; l < n; ++l) dacc_mac(g, V[l * m + r], wt[l * n + j]);
+        Gt[j * (m + 1) + r] = dacc_result(g);
+      }
     }
   }
   __syncthreads();
 
-  for (int t = tid; t < (m + 1) + m + 3 * n; t += NT) {
+  for (int t = tid; t < (m + 1) + 3 * n; t += NT) {
     df x[n];
     if (t < m + 1) {
 #pragma unroll
@@ -292,15 +310,8 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
       fwd_subst_df<n>(Ss, invdS, x);
 #pragma unroll
       for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
-    } else if (t < 2 * m + 1) {
-      const int col = t - (m + 1);
-#pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = V[l * m + col];
-      bwd_subst_df<n>(Ms, invdM, x);
-#pragma unroll
-      for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
     } else {
-      const int tt = t - (2 * m + 1);
+      const int tt = t - (m + 1);
       df* base = W + (tt / n) * n * n;
       const int col = tt % n;
 #pragma unroll
@@ -312,9 +323,16 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   __syncthreads();
 
+  // C = (n_l . n_l') o V^T V + tauDD - H^T H  (V = L^-1 E^T still; H = rows of G^T)
   for (int t = tid; t < MP; t += NT) {
     const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
-    dacc hh = dacc_from(Cs[r * m + s]);
+    const int fr = r / d2, fs = s / d2;
+    dacc b = dacc_zero();
+#pragma unroll 4
+    for (int l = 0; l < n; ++l) dacc_mac(b, V[l * m + r], V[l * m + s]);
+    df cv = df_mul(s_nn[fr][fs], dacc_result(b));
+    if (r == s) cv = df_add(cv, s_T[fr]);
+    dacc hh = dacc_from(cv);
 #pragma unroll 4
     for (int j = 0; j < n; ++j) dacc_msub(hh, Gt[j * (m + 1) + r], Gt[j * (m + 1) + s]);
     const df v = dacc_result(hh);
@@ -329,13 +347,22 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   __syncthreads();
 
-  for (int t = tid; t < m + 1; t += NT) {
+  for (int t = tid; t < (m + 1) + m; t += NT) {
     df x[n];
+    if (t < m + 1) {
 #pragma unroll
-    for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
-    bwd_subst_df<n>(Ss, invdS, x);
+      for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
+      bwd_subst_df<n>(Ss, invdS, x);
 #pragma unroll
-    for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+      for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
+    } else {  // Y = M^-1 E^T = L^-T V for the recovery record
+      const int col = t - (m + 1);
+#pragma unroll
+      for (int l = 0; l < n; ++l) x[l] = V[l * m + col];
+      bwd_subst_df<n>(Ms, invdM, x);
+#pragma unroll
+      for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
+    }
   }
   double* Cout = A.C + Ke * (int64_t)(m * m);  // face-blocked, as in assemble.cu
   for (int t = tid; t < m * m; t += NT) {
@@ -384,17 +411,21 @@ static cudaError_t launch_df_shape(hdg_mesh* M, const AsmDfArgs& a) {
 
 template <int K>
 static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
-  if (K <= 3 && M->k1_variant == 1) return launch_df_shape<K, (K <= 3 ? 1 : 0)>(M, a);
+  // HDG_K1_VARIANT overrides the tuned shape (tests of every shape, profiling)
+  int v = M->k1_variant;
+  if (const char* ev = std::getenv("HDG_K1_VARIANT")) v = std::atoi(ev);
+  if (v == 1) return launch_df_shape<K, 1>(M, a);
+  if (K == 3 && v == 2) return launch_df_shape<K, (K == 3 ? 2 : 0)>(M, a);
   return launch_df_shape<K, 0>(M, a);
 }
 
-int k1_variants(int k) { return k <= 3 ? 2 : 1; }
+int k1_variants(int k) { return k == 3 ? 3 : 2; }
 int k1_threads(int k, int variant) {
   switch (k) {
     case 1: return variant ? K1Shape<1, 1>::NT : K1Shape<1, 0>::NT;
     case 2: return variant ? K1Shape<2, 1>::NT : K1Shape<2, 0>::NT;
-    case 3: return variant ? K1Shape<3, 1>::NT : K1Shape<3, 0>::NT;
-    default: return K1Shape<4, 0>::NT;
+    case 3: return variant == 2 ? K1Shape<3, 2>::NT : variant ? K1Shape<3, 1>::NT : K1Shape<3, 0>::NT;
+    default: return variant ? K1Shape<4, 1>::NT : K1Shape<4, 0>::NT;
   }
 }
 

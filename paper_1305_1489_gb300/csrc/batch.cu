@@ -37,7 +37,7 @@ struct hdg_batch {
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   int built_prec = -1, built_maxit = -1;
-  std::vector<int> built_gens;  // coarse-space generation of every group mesh at graph build
+  std::vector<int> built_gens;  // coarse-space generation, grid and K1 shape of every group at graph build
   double built_rtol = -1.0;
 };
 
@@ -172,8 +172,12 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     if (!G.mesh->kappa) return fail(HDG_ERR_STATE, "coefficients not set on every batch group");
     if (G.mesh->beta_q) return fail(HDG_ERR_UNSUPPORTED, "batched solves are for reaction-diffusion (beta = 0)");
   }
-  std::vector<int> gens;
-  for (auto& G : B->groups) gens.push_back(G.mesh->coarse_gen);
+  std::vector<int> gens;  // what the recorded graph depends on besides the arguments
+  for (auto& G : B->groups) {
+    gens.push_back(G.mesh->coarse_gen);
+    gens.push_back(G.mesh->face_blocks);
+    gens.push_back(G.mesh->k1_variant);
+  }
   if (!B->exec || B->built_prec != precision || B->built_rtol != rtol || B->built_maxit != maxit ||
       B->built_gens != gens) {
     if (B->exec) {

@@ -111,6 +111,7 @@ struct hdg_mesh {
   bool no_cond_graphs = false;  // the driver refused conditional nodes: host-driven loop
   int graph_iters = 0;
   int face_blocks = 1216;         // persistent grid of the face kernels (hdg_autotune)
+  int face_blocks32 = 1216;       // the same for the FP32 inner iterations
   int k1_variant = 0;             // launch shape of the double-float K1 (hdg_autotune)
   int asm_prec = -1;              // precision of the last hdg_assemble_condense
   hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL
@@ -151,7 +152,7 @@ int coarse_launch_build(hdg_mesh* M); // the same, enqueued on M->stream without
 void coarse_free(hdg_mesh* M);
 void coarse_invalidate(hdg_mesh* M);  // the Galerkin values must be rebuilt (new assembly)
 int coarse_precond_apply(hdg_mesh* M, const double* r, double* z);
-int autotune_face_grid(hdg_mesh* M, int* chosen, double* best_ms);
+int autotune_face_grid(hdg_mesh* M, hdg_tuning* out);
 int k1_variants(int k);              // launch shapes of the double-float K1 for degree k
 int k1_threads(int k, int variant);  // threads per element of a shape
 }  // namespace hdg

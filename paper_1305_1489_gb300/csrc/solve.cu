@@ -673,6 +673,17 @@ static int nblocks(hdg_mesh* M) {
   return (int)(tiles < cap ? tiles : cap);
 }
 
+// the FP32 inner solve has its own persistent grid (hdg_autotune tunes both)
+template <typename T>
+static int nblocks_t(hdg_mesh* M) {
+  if (sizeof(T) == 8) return nblocks(M);
+  const int save = M->face_blocks;
+  M->face_blocks = M->face_blocks32;
+  const int nb = nblocks(M);
+  M->face_blocks = save;
+  return nb;
+}
+
 static CoarseArgs coarse_args(hdg_mesh* M) {
   const Coarse* c = M->coarse;
   CoarseArgs a;
@@ -830,7 +841,7 @@ struct Solver {
   static int pcg_run(hdg_mesh* M, const T* C, const T* Binv, const T* rhs, T* x, bool have_x, T* r, T* z, T* p,
                      T* q, double* scal, double tol2, int maxit, cudaGraphExec_t* graph, int* iters, bool* bad) {
     FaceArgs F = face_args(M);
-    const int nb = nblocks(M);
+    const int nb = nblocks_t<T>(M);
     const int64_t nv = M->nfc * D2;
     double hs[S_NSCAL] = {0};
     hs[S_TOL2] = tol2;
@@ -1065,7 +1076,7 @@ struct Solver {
   // Time one block-Jacobi PCG iteration (operator, update with its reductions, direction) in
   // FP64 for persistent grids of 4, 8, 16 and 32 blocks per SM; keep the fastest.  Cached
   // graphs are rebuilt when the grid changes.
-  static int autotune(hdg_mesh* M, int* chosen, double* best_ms) {
+  static int autotune(hdg_mesh* M, hdg_tuning* out) {
     int rc = ensure_workspace(M, false);
     if (rc) return rc;
     rc = prepare_rhs(M);
@@ -1111,10 +1122,53 @@ struct Solver {
         best = cand;
       }
     }
+    M->face_blocks = best;
+    // the same for the FP32 inner iteration (mixed precision), on FP32 copies of C^K and B^-1
+    int best32 = M->face_blocks32;
+    float best32_t = 1e30f;
+    if (!M->beta_q) {
+      rc = ensure_workspace(M, true);
+      if (rc) return rc;
+      const int64_t nC = M->nelt * (int64_t)M->tab.m * M->tab.m;
+      convert_kernel<float><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, nC);
+      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * D2 * D2);
+      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_b, M->d_p32, nv);
+      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_b, M->d_r32, nv);
+      HDG_CUDA_TRY(cudaMemsetAsync(M->d_x32, 0, sizeof(float) * nv, M->stream));
+      HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
+      float* q32 = reinterpret_cast<float*>(M->d_q);
+      auto iteration32 = [&](int nb) {
+        pcg_matvec_kernel<float, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C32, M->d_p32, q32, M->d_red, M->d_counter,
+                                                                scal);
+        pcg_update_kernel<float, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_BJ32, M->d_x32, M->d_r32, M->d_z32,
+                                                                M->d_p32, q32, M->d_red, M->d_counter, scal);
+        pcg_dir_kernel<float><<<nb, kNT, 0, M->stream>>>(nv, M->d_z32, M->d_p32, scal);
+      };
+      const int keep = M->face_blocks;
+      for (int cand : cands) {
+        M->face_blocks = cand;
+        const int nb = nblocks(M);
+        iteration32(nb);
+        HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
+        for (int rep = 0; rep < 4; ++rep) iteration32(nb);
+        HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
+        HDG_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        M->launches += 15;
+        if (ms < best32_t) {
+          best32_t = ms;
+          best32 = cand;
+        }
+      }
+      M->face_blocks = keep;
+      M->launches += 4;
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    M->face_blocks = best;
-    if (best != old) {
+    const bool changed = best != old || best32 != M->face_blocks32;
+    M->face_blocks32 = best32;
+    if (changed) {
       cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg};
       for (cudaGraphExec_t* g : gs)
         if (*g) {
@@ -1122,8 +1176,12 @@ struct Solver {
           *g = nullptr;
         }
     }
-    if (chosen) *chosen = best;
-    if (best_ms) *best_ms = best_t / 4.0;
+    if (out) {
+      out->face_blocks = best;
+      out->iter_ms = best_t / 4.0;
+      out->face_blocks32 = best32;
+      out->iter32_ms = best32_t < 1e29f ? best32_t / 4.0 : 0.0;
+    }
     return HDG_OK;
   }
 
@@ -1354,13 +1412,13 @@ int trace_apply(hdg_mesh* M, const double* x, double* y) {
   return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }
 
-int autotune_face_grid(hdg_mesh* M, int* chosen, double* best_ms) {
+int autotune_face_grid(hdg_mesh* M, hdg_tuning* out) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "autotune before hdg_assemble_condense");
   switch (M->tab.d2) {
-    case 3: return Solver<3>::autotune(M, chosen, best_ms);
-    case 6: return Solver<6>::autotune(M, chosen, best_ms);
-    case 10: return Solver<10>::autotune(M, chosen, best_ms);
-    case 15: return Solver<15>::autotune(M, chosen, best_ms);
+    case 3: return Solver<3>::autotune(M, out);
+    case 6: return Solver<6>::autotune(M, out);
+    case 10: return Solver<10>::autotune(M, out);
+    case 15: return Solver<15>::autotune(M, out);
   }
   return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }

@@ -147,10 +147,13 @@ def test_error_paths():
     assert ei.value.code == 2
 
 
-@pytest.mark.parametrize("k,s", [(1, 3), (2, 2), (3, 2), (4, 1)])
-def test_double_float_assembly(k, s):
-    """HDG_DF32: the same condensation in double-float arithmetic on the FP32 pipe."""
+@pytest.mark.parametrize("k,s,shape", [(1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (3, 2, "0"), (3, 2, "1"),
+                                     (3, 2, "2"), (4, 1, "0"), (4, 2, "1")])
+def test_double_float_assembly(k, s, shape, monkeypatch):
+    """HDG_DF32: the same condensation in double-float arithmetic on the FP32 pipe, for every
+    launch shape the autotuner may pick (HDG_K1_VARIANT forces one)."""
     from paper_1305_1489_gb300 import HDG_DF32
+    monkeypatch.setenv("HDG_K1_VARIANT", shape)
     prob = _varprob(k)
     c, e, d, n = make_mesh(prob, s=s)
     rng = np.random.default_rng(k + 10)
