@@ -233,7 +233,7 @@ int hdg_nn_adam(int64_t n, float* p, const float* g, float* m, float* v, float l
  * sweep before and after each coarse correction, FP32) for A_0 = Pi^T H Pi over nested levels
  * A_{l+1} = P_l^T A_l P_l, exact dense solve on the coarsest level.  The Galerkin matrices are
  * rebuilt on the device after every hdg_assemble_condense (at the next solve).
- * hdg_set_coarse_space: nlev >= 2 levels with sizes[l] nodes (sizes[nlev-1] <= 128); host
+ * hdg_set_coarse_space: 2 <= nlev <= 17 levels with sizes[l] nodes (sizes[nlev-1] <= 128); host
  *   arrays nodes int32 / weights f64 [R][4], R = nver + sizes[0] + ... + sizes[nlev-2]: first,
  *   per mesh vertex, the level-0 nodes and weights giving its value; then, per node of level
  *   l < nlev-1, the level-(l+1) nodes and weights interpolating it.  Node -1 = unused entry.

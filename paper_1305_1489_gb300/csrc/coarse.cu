@@ -195,8 +195,8 @@ void coarse_free(hdg_mesh* M) {
     cudaFree(c->rap_dst[l]);
     cudaFree(c->rap_w[l]);
   }
-  void* ptrs[] = {c->d_lv, c->vnodes, c->vw, c->vwd, c->gptr, c->gfi, c->gw, c->elist, c->eslot, c->rc, c->e0,
-                  c->Adense, c->Ainv};
+  void* ptrs[] = {c->d_lv, c->vnodes, c->vw, c->vwd, c->gptr, c->gfi, c->gw, c->elist, c->eslot, c->rc, c->Tf,
+                  c->e0, c->Adense, c->Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -209,6 +209,7 @@ void coarse_invalidate(hdg_mesh* M) {
 
 static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t* nodes, const double* weights) {
   if (nlev < 2 || !sizes || !nodes || !weights) return fail(HDG_ERR_ARG, "need nlev >= 2 levels and their arrays");
+  if (nlev > kMaxTailLevels + 1) return fail(HDG_ERR_UNSUPPORTED, "at most 17 levels");
   for (int l = 0; l < nlev; ++l)
     if (sizes[l] < 1 || sizes[l] > (int64_t)1 << 30) return fail(HDG_ERR_ARG, "every level needs 1 .. 2^30 nodes");
   if (sizes[nlev - 1] > kMaxCoarsest)
@@ -409,6 +410,8 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
     if (!rc) rc = alloc(&L.x, L.n);
     if (!rc) rc = alloc(&L.t, L.n);
     if (!rc && l + 1 < nlev) {
+      L.nnext = sizes[l + 1];
+      L.ntr = (int64_t)tidx[l].size();
       rc = upload(&L.pn, pn[l]);
       if (!rc) rc = upload(&L.pw, pw[l]);
       if (!rc) rc = upload(&L.tptr, tptr[l]);
@@ -426,6 +429,13 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
   if (!rc) rc = upload(&c->elist, elist);
   if (!rc) rc = upload(&c->eslot, eslot);
   if (!rc) rc = alloc(&c->rc, n0);
+  if (!rc) {  // FP32 copy of (varpi . D)^T Xi for the per-iteration kernels
+    std::vector<double> Td(3 * M->tab.d2);
+    rc = cudaMemcpy(Td.data(), M->d_Tproj, sizeof(double) * Td.size(), cudaMemcpyDeviceToHost) == cudaSuccess
+             ? HDG_OK
+             : fail(HDG_ERR_CUDA, "copy of the face projection table");
+    if (!rc) rc = upload(&c->Tf, std::vector<float>(Td.begin(), Td.end()));
+  }
   if (!rc) rc = alloc(&c->e0, n0);
   if (!rc) rc = alloc(&c->Adense, c->nL * c->nL);
   if (!rc) rc = alloc(&c->Ainv, c->nL * c->nL);

@@ -15,16 +15,17 @@
 // Per PCG iteration (after q = H p and alpha):
 //   update_tl   x += alpha p, r -= alpha q, r.r
 //   restrict    rc = Pi^T r: one warp per level-0 node gathers its (face, vertex slot, weight)
-//               list (built on the host), FP64 sums, no atomics
-//   down        level 0 and every level above kTailMax nodes (grid kernels): x = D^-1 b,
-//               t = b - A x; coarser grid levels first gather b = P^T t
+//               list (built on the host), FP32 sums, no atomics
+//   down        level 0 and every level above kTailMax nodes (grid kernels, 16 lanes per
+//               row): x = D^-1 b, t = b - A x; coarser grid levels first gather b = P^T t
 //   vcycle      one CTA: the remaining small levels (restrict, smooth, exact coarsest,
 //               prolong, smooth)
 //   up          grid levels, coarse to fine: x' = x + P x_coarse, out = x' + D^-1 (b - A x');
 //               level 0 writes e0
 //   zc          z = B^-1 r + Pi e0, r.z, beta
-// The V-cycle runs in FP32 (a preconditioner only has to be fixed, symmetric and positive);
-// every scalar of the Krylov method and the FP64 solve itself are unchanged.
+// The coarse correction runs in FP32 (a preconditioner only has to be fixed, symmetric and
+// positive; GB300's FP64 pipe is 1/63 of its FP32 rate); every scalar of the Krylov method and
+// the FP64 solve itself are unchanged.
 #pragma once
 
 #include <cstdint>
@@ -49,16 +50,29 @@ struct CoarseLevel {
   float* pw = nullptr;     // [n][4] their weights
   int32_t *tptr = nullptr, *tidx = nullptr;  // transpose of (pn, pw): rows = level-(l+1) nodes
   float* tw = nullptr;
+  int64_t ntr = 0;         // entries of the transpose
+  int64_t nnext = 0;       // nodes of level l+1 (0 on the coarsest level)
   float *b = nullptr, *x = nullptr, *t = nullptr;
 };
+
+constexpr int kMaxTailLevels = 16;         // tail levels of the single-CTA kernel (nlev <= 17)
+constexpr int64_t kTailSmemMax = 200 << 10;  // largest shared-memory copy of the tail
+
+// bytes of the shared-memory copy of one tail level (16-byte aligned arrays)
+__host__ __device__ inline int64_t tail_align(int64_t b) { return (b + 15) & ~int64_t(15); }
+__host__ __device__ inline int64_t tail_level_bytes(const CoarseLevel& L) {
+  int64_t b = tail_align(4 * (L.n + 1)) + 2 * tail_align(4 * L.nnz) + 4 * tail_align(4 * L.n);
+  if (L.nnext > 0) b += 2 * tail_align(16 * L.n) + tail_align(4 * (L.nnext + 1)) + 2 * tail_align(4 * L.ntr);
+  return b;
+}
 
 // Level-0 arguments of the face kernels.
 struct CoarseArgs {
   const int32_t* fverts;  // [nfc][3] sorted face vertices
-  const double* T;        // [d2][3]  (varpi . D)^T Xi
+  const float* Tf;        // [d2][3]  (varpi . D)^T Xi, FP32
   const int32_t* vnodes;  // [nver][4] level-0 nodes of each mesh vertex
   const float* vw;        // [nver][4] weights
-  double* rc;             // [n0] Pi^T r
+  float* rc;              // [n0] Pi^T r
   const float* e0;        // [n0] V-cycle output on level 0
   int64_t n0;
   const int32_t* gptr;    // [n0+1] CSR of the restriction gather
@@ -80,12 +94,14 @@ struct Coarse {
   std::vector<int64_t> rap_n;             // Galerkin triple counts per level
   std::vector<int32_t*> rap_src, rap_dst; // A_{l+1}[dst] += w A_l[src]
   std::vector<double*> rap_w;
-  double* rc = nullptr;
+  float* rc = nullptr;
+  float* Tf = nullptr;       // FP32 copy of (varpi . D)^T Xi
   float* e0 = nullptr;
   double* Adense = nullptr;  // [nL][nL] FP64 scratch of the coarsest inverse
   float* Ainv = nullptr;     // [nL][nL]
   int64_t nL = 0;
   int64_t tail_max = kTailMax;  // levels up to this size run in the single-CTA kernel
+  int64_t tail_smem = 0;        // bytes of the tail's shared-memory copy (0: the tail reads global)
   bool ready = false;        // Galerkin hierarchy built for the current assembly
 };
 
@@ -97,15 +113,15 @@ __global__ void restrict_gather_kernel(CoarseArgs CA, const T* __restrict__ r, c
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; n < CA.n0; n += nwarps) {
-    double s = 0.0;
+    float s = 0.f;
     for (int k = CA.gptr[n] + lane; k < CA.gptr[n + 1]; k += 32) {
       const int32_t fi = CA.gfi[k];
       const int64_t f = fi >> 2;
       const int i = fi & 3;
-      double t = 0.0;
+      float t = 0.f;
 #pragma unroll
-      for (int a = 0; a < D2; ++a) t = fma(CA.T[a * 3 + i], (double)r[f * D2 + a], t);
-      s = fma((double)CA.gw[k], t, s);
+      for (int a = 0; a < D2; ++a) t = fmaf(CA.Tf[a * 3 + i], (float)r[f * D2 + a], t);
+      s = fmaf(CA.gw[k], t, s);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -126,26 +142,45 @@ __device__ __forceinline__ float prolong_face(const CoarseArgs& CA, int64_t e, i
       const int nd = CA.vnodes[4 * v + j];
       if (nd >= 0) val = fmaf(CA.vw[4 * v + j], CA.e0[nd], val);
     }
-    s = fmaf((float)CA.T[a * 3 + i], val, s);
+    s = fmaf(CA.Tf[a * 3 + i], val, s);
   }
   return s;
 }
 
-// Grid-wide level kernels (levels with more than kTailMax nodes, and always level 0).  The
-// right-hand side of level 0 is rc (FP64); of a coarser level, its b.
+// Grid-wide level kernels (levels with more than the tail size, and always level 0): a group
+// of 16 lanes per row shares the row's entries and sums them with shuffles.  The right-hand
+// side of level 0 is rc; of a coarser level, its b.
+constexpr int kRowLanes = 16;
+
+__device__ __forceinline__ float group_sum16(float v) {
+#pragma unroll
+  for (int o = kRowLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // down: x = D^-1 b, t = b - A x (the x of the neighbours formed on the fly from b)
 template <bool L0>
-__global__ void level_down_kernel(CoarseLevel L, const double* __restrict__ rc, const double* done) {
+__global__ void level_down_kernel(CoarseLevel L, const float* __restrict__ rc, const double* done) {
   if (*done != 0.0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float bi = L0 ? (float)rc[i] : L.b[i];
+  const int g = threadIdx.x & (kRowLanes - 1);
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / kRowLanes;
+  // every lane of a warp runs the same number of trips (the shuffles need full warps)
+  const int64_t trips = (L.n + ngroups - 1) / ngroups;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+  for (int64_t trip = 0; trip < trips; ++trip) {
+    const int64_t i = i0 + trip * ngroups;
     float ax = 0.f;
-    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; ++k) {
-      const int j = L.col[k];
-      ax = fmaf(L.valf[k], L.dinv[j] * (L0 ? (float)rc[j] : L.b[j]), ax);
+    if (i < L.n)
+      for (int k = L.rowptr[i] + g; k < L.rowptr[i + 1]; k += kRowLanes) {
+        const int j = L.col[k];
+        ax = fmaf(L.valf[k], L.dinv[j] * (L0 ? rc[j] : L.b[j]), ax);
+      }
+    ax = group_sum16(ax);
+    if (i < L.n && g == 0) {
+      const float bi = L0 ? rc[i] : L.b[i];
+      L.x[i] = L.dinv[i] * bi;
+      L.t[i] = bi - ax;
     }
-    L.x[i] = L.dinv[i] * bi;
-    L.t[i] = bi - ax;
   }
 }
 
@@ -172,28 +207,100 @@ __device__ __forceinline__ float level_corrected(const CoarseLevel& L, const flo
 
 // up: out = x' + D^-1 (b - A x')
 template <bool L0>
-__global__ void level_up_kernel(CoarseLevel L, const float* __restrict__ xn, const double* __restrict__ rc,
+__global__ void level_up_kernel(CoarseLevel L, const float* __restrict__ xn, const float* __restrict__ rc,
                                 float* __restrict__ out, const double* done) {
   if (*done != 0.0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int g = threadIdx.x & (kRowLanes - 1);
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / kRowLanes;
+  const int64_t trips = (L.n + ngroups - 1) / ngroups;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+  for (int64_t trip = 0; trip < trips; ++trip) {
+    const int64_t i = i0 + trip * ngroups;
     float ax = 0.f;
-    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; ++k) ax = fmaf(L.valf[k], level_corrected(L, xn, L.col[k]), ax);
-    const float bi = L0 ? (float)rc[i] : L.b[i];
-    out[i] = level_corrected(L, xn, i) + L.dinv[i] * (bi - ax);
+    if (i < L.n)
+      for (int k = L.rowptr[i] + g; k < L.rowptr[i + 1]; k += kRowLanes)
+        ax = fmaf(L.valf[k], level_corrected(L, xn, L.col[k]), ax);
+    ax = group_sum16(ax);
+    if (i < L.n && g == 0) {
+      const float bi = L0 ? rc[i] : L.b[i];
+      out[i] = level_corrected(L, xn, i) + L.dinv[i] * (bi - ax);
+    }
   }
 }
 
-// Levels first .. nlev-1 of the V-cycle in one CTA (the tail of small levels, at most
-// kTailMax nodes each).  Input: lv[first-1].t (residual of the finer level); output: lv[first].x.
+// Levels first .. nlev-1 of the V-cycle in one CTA (the tail of small levels, at most the tail
+// size each).  Input: lv[first-1].t (residual of the finer level); output: lv[first].x.  With
+// use_smem the tail's matrices, interpolations and vectors are first copied into dynamic
+// shared memory (tail_level_bytes each), so that the dozen barrier-separated phases below
+// read shared memory instead of L2.
+template <typename V>
+__device__ __forceinline__ V* tail_take(unsigned char*& p, int64_t count) {
+  V* q = reinterpret_cast<V*>(p);
+  p += tail_align(sizeof(V) * count);
+  return q;
+}
+
+template <typename V>
+__device__ __forceinline__ void tail_copy(V* dst, const V* __restrict__ src, int64_t count) {
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+}
+
 static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseLevel* __restrict__ lv, int first,
                                                             int nlev, const float* __restrict__ Ainv,
-                                                            const double* done) {
+                                                            const double* done, int use_smem) {
   if (*done != 0.0) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  __shared__ CoarseLevel sl[kMaxTailLevels];
   const int tid = threadIdx.x;
+  const int nt = nlev - first;
+  if (use_smem) {
+    if (tid == 0) {
+      unsigned char* p = tail_smem;
+      for (int t = 0; t < nt; ++t) {
+        CoarseLevel S = lv[first + t];
+        S.rowptr = tail_take<int32_t>(p, S.n + 1);
+        S.col = tail_take<int32_t>(p, S.nnz);
+        S.valf = tail_take<float>(p, S.nnz);
+        S.dinv = tail_take<float>(p, S.n);
+        S.b = tail_take<float>(p, S.n);
+        S.x = tail_take<float>(p, S.n);
+        S.t = tail_take<float>(p, S.n);
+        if (S.nnext > 0) {
+          S.pn = tail_take<int32_t>(p, 4 * S.n);
+          S.pw = tail_take<float>(p, 4 * S.n);
+          S.tptr = tail_take<int32_t>(p, S.nnext + 1);
+          S.tidx = tail_take<int32_t>(p, S.ntr);
+          S.tw = tail_take<float>(p, S.ntr);
+        }
+        sl[t] = S;
+      }
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      const CoarseLevel& G = lv[first + t];
+      const CoarseLevel& S = sl[t];
+      tail_copy(S.rowptr, G.rowptr, G.n + 1);
+      tail_copy(S.col, G.col, G.nnz);
+      tail_copy(S.valf, G.valf, G.nnz);
+      tail_copy(S.dinv, G.dinv, G.n);
+      if (G.nnext > 0) {
+        tail_copy(S.pn, G.pn, 4 * G.n);
+        tail_copy(S.pw, G.pw, 4 * G.n);
+        tail_copy(S.tptr, G.tptr, G.nnext + 1);
+        tail_copy(S.tidx, G.tidx, G.ntr);
+        tail_copy(S.tw, G.tw, G.ntr);
+      }
+    }
+  } else if (tid < nt) {
+    sl[tid] = lv[first + tid];
+  }
+  __syncthreads();
+  // level l of the cycle: the grid level first-1 stays in global memory
+  auto lev = [&](int l) -> const CoarseLevel& { return l < first ? lv[l] : sl[l - first]; };
   int l = first;
   for (; l < nlev; ++l) {
-    const CoarseLevel& P = lv[l - 1];  // interpolation l -> l-1 is stored on level l-1
-    const CoarseLevel& C = lv[l];
+    const CoarseLevel& P = lev(l - 1);  // interpolation l -> l-1 is stored on level l-1
+    const CoarseLevel& C = lev(l);
     for (int64_t J = tid; J < C.n; J += kVcThreads) {
       float s = 0.f;
       for (int k = P.tptr[J]; k < P.tptr[J + 1]; ++k) s = fmaf(P.tw[k], P.t[P.tidx[k]], s);
@@ -211,7 +318,7 @@ static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseL
     __syncthreads();
   }
   {  // coarsest: x = A^-1 b (dense)
-    const CoarseLevel& C = lv[nlev - 1];
+    const CoarseLevel& C = lev(nlev - 1);
     for (int64_t i = tid; i < C.n; i += kVcThreads) {
       float s = 0.f;
       for (int64_t j = 0; j < C.n; ++j) s = fmaf(Ainv[i * C.n + j], C.b[j], s);
@@ -220,8 +327,8 @@ static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseL
     __syncthreads();
   }
   for (l = nlev - 2; l >= first; --l) {
-    const CoarseLevel& C = lv[l];
-    const float* xc = lv[l + 1].x;
+    const CoarseLevel& C = lev(l);
+    const float* xc = lev(l + 1).x;
     for (int64_t i = tid; i < C.n; i += kVcThreads) {
       float v = C.x[i];
 #pragma unroll
@@ -240,6 +347,11 @@ static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseL
     __syncthreads();
     for (int64_t i = tid; i < C.n; i += kVcThreads) C.x[i] += C.t[i];
     __syncthreads();
+  }
+  if (use_smem) {  // the result of the first tail level goes back to global memory
+    const CoarseLevel& C = sl[0];
+    float* out = lv[first].x;
+    for (int64_t i = tid; i < C.n; i += kVcThreads) out[i] = C.x[i];
   }
 }
 

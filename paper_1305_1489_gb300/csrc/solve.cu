@@ -684,11 +684,26 @@ static int nblocks_t(hdg_mesh* M) {
   return nb;
 }
 
+// shared-memory copy of the V-cycle's tail (set before any capture of the kernel)
+static int grid_levels(const Coarse* c);
+static void prepare_tail(hdg_mesh* M) {
+  Coarse* c = M->coarse;
+  const int G = grid_levels(c);
+  int64_t bytes = 0;
+  for (int l = G; l < c->nlev; ++l) bytes += tail_level_bytes(c->lv[l]);
+  const bool fits = c->nlev - G <= kMaxTailLevels && bytes <= kTailSmemMax &&
+                    cudaFuncSetAttribute(vcycle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                        cudaSuccess;
+  cudaGetLastError();
+  c->tail_smem = fits ? bytes : 0;
+}
+
 static CoarseArgs coarse_args(hdg_mesh* M) {
+  prepare_tail(M);
   const Coarse* c = M->coarse;
   CoarseArgs a;
   a.fverts = M->d_fverts;
-  a.T = M->d_Tproj;
+  a.Tf = c->Tf;
   a.vnodes = c->vnodes;
   a.vw = c->vw;
   a.rc = c->rc;
@@ -716,21 +731,22 @@ static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStre
   Coarse* c = M->coarse;
   const int G = grid_levels(c);
   auto grid = [](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, kMaxBlocks); };
+  auto rows = [](int64_t n) { return (int)std::min<int64_t>((n * kRowLanes + 255) / 256, kMaxBlocks); };
   const int gr = (int)std::min<int64_t>((c->lv[0].n + 7) / 8, 152 * 16);  // one warp per node
   restrict_gather_kernel<T, D2><<<gr, 256, 0, st>>>(CA, r, done);
-  level_down_kernel<true><<<grid(c->lv[0].n), 256, 0, st>>>(c->lv[0], c->rc, done);
+  level_down_kernel<true><<<rows(c->lv[0].n), 256, 0, st>>>(c->lv[0], c->rc, done);
   for (int l = 1; l < G; ++l) {
     level_restrict_kernel<<<grid(c->lv[l].n), 256, 0, st>>>(c->lv[l - 1], c->lv[l], done);
-    level_down_kernel<false><<<grid(c->lv[l].n), 256, 0, st>>>(c->lv[l], nullptr, done);
+    level_down_kernel<false><<<rows(c->lv[l].n), 256, 0, st>>>(c->lv[l], nullptr, done);
   }
-  vcycle_kernel<<<1, kVcThreads, 0, st>>>(c->d_lv, G, c->nlev, c->Ainv, done);
+  vcycle_kernel<<<1, kVcThreads, c->tail_smem, st>>>(c->d_lv, G, c->nlev, c->Ainv, done, c->tail_smem > 0);
   for (int l = G - 1; l >= 0; --l) {
     const float* xn = (l + 1 == G) ? c->lv[G].x : c->lv[l + 1].t;
     float* out = (l == 0) ? c->e0 : c->lv[l].t;
     if (l == 0)
-      level_up_kernel<true><<<grid(c->lv[0].n), 256, 0, st>>>(c->lv[0], xn, c->rc, out, done);
+      level_up_kernel<true><<<rows(c->lv[0].n), 256, 0, st>>>(c->lv[0], xn, c->rc, out, done);
     else
-      level_up_kernel<false><<<grid(c->lv[l].n), 256, 0, st>>>(c->lv[l], xn, nullptr, out, done);
+      level_up_kernel<false><<<rows(c->lv[l].n), 256, 0, st>>>(c->lv[l], xn, nullptr, out, done);
   }
 }
 
@@ -1279,6 +1295,8 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const
   double* scal = M->d_scal;
   double* xD = M->d_uhatD;
   double* phiN = M->d_uhatD + nv;
+  const bool tl = M->coarse != nullptr;
+  const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};  // host set-up, before the capture
   // A: assembly, boundary data, right-hand side, block-Jacobi, per-problem ||b_p||, PCG start
   cudaGraph_t ga;
   HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -1290,8 +1308,6 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const
   rhs_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
                                      M->d_scal + S_NSCAL);
   bj_kernel<D2><<<(unsigned)((M->nfc + 63) / 64), 64, 0, cs>>>(F, M->d_C, M->d_BJ, M->d_status, false);
-  const bool tl = M->coarse != nullptr;
-  const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
   int rcb = tl ? coarse_launch_build(M) : HDG_OK;  // Galerkin hierarchy of this assembly
   cudaMemsetAsync(norms, 0, sizeof(double) * 2 * np, cs);
   prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_b, face_prob, M->nfc, D2, norms);
