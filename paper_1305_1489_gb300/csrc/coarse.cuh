@@ -240,9 +240,57 @@ __device__ __forceinline__ V* tail_take(unsigned char*& p, int64_t count) {
   return q;
 }
 
-template <typename V>
-__device__ __forceinline__ void tail_copy(V* dst, const V* __restrict__ src, int64_t count) {
-  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+// Copy of the tail's arrays into shared memory in one flattened pass, so that every thread
+// issues all its loads before its first store (one memory latency for the whole copy).
+// Segments are 4-byte arrays: whole 16-byte chunks first, then the remaining words.
+constexpr int kMaxTailSegs = kMaxTailLevels * 9;
+
+struct TailSegs {
+  const int32_t* src[kMaxTailSegs];
+  int32_t* dst[kMaxTailSegs];
+  int32_t start16[kMaxTailSegs + 1];  // prefix of 16-byte chunks
+  int32_t startw[kMaxTailSegs + 1];   // prefix of remaining words
+  int nseg;
+};
+
+__device__ __forceinline__ int tail_find(const int32_t* start, int nseg, int c) {
+  int lo = 0, hi = nseg - 1;  // last segment with start[s] <= c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void tail_copy_all(const TailSegs& S) {
+  constexpr int U = 8;
+  const int bs = blockDim.x, tid = threadIdx.x;
+  const int total16 = S.start16[S.nseg];
+  for (int base = tid; base < total16; base += U * bs) {
+    int4 v[U];
+    int4* d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = base + u * bs;
+      d[u] = nullptr;
+      if (c < total16) {
+        const int sg = tail_find(S.start16, S.nseg, c);
+        const int off = c - S.start16[sg];
+        v[u] = __ldg(reinterpret_cast<const int4*>(S.src[sg]) + off);
+        d[u] = reinterpret_cast<int4*>(S.dst[sg]) + off;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (d[u]) *d[u] = v[u];
+  }
+  const int totalw = S.startw[S.nseg];
+  for (int c = tid; c < totalw; c += bs) {
+    const int sg = tail_find(S.startw, S.nseg, c);
+    const int full = (S.start16[sg + 1] - S.start16[sg]) * 4;
+    const int w = full + (c - S.startw[sg]);
+    S.dst[sg][w] = __ldg(S.src[sg] + w);
+  }
 }
 
 static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseLevel* __restrict__ lv, int first,
@@ -254,10 +302,22 @@ static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseL
   const int tid = threadIdx.x;
   const int nt = nlev - first;
   if (use_smem) {
+    __shared__ TailSegs segs;
     if (tid == 0) {
       unsigned char* p = tail_smem;
+      int ns = 0;
+      auto add = [&](const void* src, void* dst, int64_t words) {
+        segs.src[ns] = reinterpret_cast<const int32_t*>(src);
+        segs.dst[ns] = reinterpret_cast<int32_t*>(dst);
+        segs.start16[ns + 1] = segs.start16[ns] + (int32_t)(words / 4);
+        segs.startw[ns + 1] = segs.startw[ns] + (int32_t)(words % 4);
+        ++ns;
+      };
+      segs.start16[0] = 0;
+      segs.startw[0] = 0;
       for (int t = 0; t < nt; ++t) {
-        CoarseLevel S = lv[first + t];
+        const CoarseLevel& G = lv[first + t];
+        CoarseLevel S = G;
         S.rowptr = tail_take<int32_t>(p, S.n + 1);
         S.col = tail_take<int32_t>(p, S.nnz);
         S.valf = tail_take<float>(p, S.nnz);
@@ -265,32 +325,28 @@ static __global__ void __launch_bounds__(kVcThreads) vcycle_kernel(const CoarseL
         S.b = tail_take<float>(p, S.n);
         S.x = tail_take<float>(p, S.n);
         S.t = tail_take<float>(p, S.n);
+        add(G.rowptr, S.rowptr, S.n + 1);
+        add(G.col, S.col, S.nnz);
+        add(G.valf, S.valf, S.nnz);
+        add(G.dinv, S.dinv, S.n);
         if (S.nnext > 0) {
           S.pn = tail_take<int32_t>(p, 4 * S.n);
           S.pw = tail_take<float>(p, 4 * S.n);
           S.tptr = tail_take<int32_t>(p, S.nnext + 1);
           S.tidx = tail_take<int32_t>(p, S.ntr);
           S.tw = tail_take<float>(p, S.ntr);
+          add(G.pn, S.pn, 4 * S.n);
+          add(G.pw, S.pw, 4 * S.n);
+          add(G.tptr, S.tptr, S.nnext + 1);
+          add(G.tidx, S.tidx, S.ntr);
+          add(G.tw, S.tw, S.ntr);
         }
         sl[t] = S;
       }
+      segs.nseg = ns;
     }
     __syncthreads();
-    for (int t = 0; t < nt; ++t) {
-      const CoarseLevel& G = lv[first + t];
-      const CoarseLevel& S = sl[t];
-      tail_copy(S.rowptr, G.rowptr, G.n + 1);
-      tail_copy(S.col, G.col, G.nnz);
-      tail_copy(S.valf, G.valf, G.nnz);
-      tail_copy(S.dinv, G.dinv, G.n);
-      if (G.nnext > 0) {
-        tail_copy(S.pn, G.pn, 4 * G.n);
-        tail_copy(S.pw, G.pw, 4 * G.n);
-        tail_copy(S.tptr, G.tptr, G.nnext + 1);
-        tail_copy(S.tidx, G.tidx, G.ntr);
-        tail_copy(S.tw, G.tw, G.ntr);
-      }
-    }
+    tail_copy_all(segs);
   } else if (tid < nt) {
     sl[tid] = lv[first + tid];
   }
