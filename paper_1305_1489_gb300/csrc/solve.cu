@@ -116,9 +116,47 @@ __device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int*
 // (H x)_e entry a: the face's row blocks of C^K (face-blocked storage) times x_dK.  Each
 // owner's column (m values, unit stride across the face's d2 threads) and the gathered x_dK
 // are loaded into registers before any FMA, so every thread keeps 2m loads in flight.
+// The FP32 copy of C^K used by the inner solve is stored row-major per face block,
+// [K][l][a][s] = C^K[l d2 + a][s], so that thread a reads its row as m/4 16-byte loads.
+template <int D2>
+__device__ __forceinline__ float face_apply_rm(const float* __restrict__ C, const float* __restrict__ x,
+                                               const FaceArgs& F, int64_t e, int a) {
+  constexpr int m = 4 * D2;
+  float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    const int ow = __ldg(F.owner + 2 * e + o);
+    if (ow < 0) continue;
+    const int64_t K = ow >> 2;
+    const float4* row = reinterpret_cast<const float4*>(C + K * (int64_t)(m * m) + (ow & 3) * (m * D2) + a * m);
+    const int4 fb = __ldg(reinterpret_cast<const int4*>(F.fbe) + K);
+    const int f4[4] = {fb.x, fb.y, fb.z, fb.w};
+    float4 cv[m / 4];
+    float xv[m];
+#pragma unroll
+    for (int q = 0; q < m / 4; ++q) cv[q] = __ldg(row + q);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) {
+      const float* xs = x + (int64_t)f4[fl] * D2;
+#pragma unroll
+      for (int b = 0; b < D2; ++b) xv[fl * D2 + b] = xs[b];
+    }
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < m / 4; ++q) {
+      acc0 = fmaf(cv[q].x, xv[4 * q], acc0);
+      acc1 = fmaf(cv[q].y, xv[4 * q + 1], acc1);
+      acc0 = fmaf(cv[q].z, xv[4 * q + 2], acc0);
+      acc1 = fmaf(cv[q].w, xv[4 * q + 3], acc1);
+    }
+  }
+  return acc0 + acc1;
+}
+
 template <typename T, int D2>
 __device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __restrict__ x, const FaceArgs& F,
                                         int64_t e, int a) {
+  if constexpr (sizeof(T) == 4) return face_apply_rm<D2>(C, x, F, e, a);
   constexpr int m = 4 * D2;
   T acc0 = (T)0, acc1 = (T)0;
 #pragma unroll
@@ -304,6 +342,20 @@ __global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __re
   }
   for (int i = 0; i < D2 * D2; ++i) Binv[e * D2 * D2 + i] = X[i];
   if (!ok) atomicAdd(status + 3, 1);
+}
+
+// FP32 copy of C^K in the row-major face-block layout of face_apply_rm
+template <int D2>
+__global__ void convert_c32_kernel(const double* __restrict__ C, float* __restrict__ C32, int64_t nelt) {
+  constexpr int m = 4 * D2;
+  const int64_t n = nelt * m * m;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t K = i / (m * m);
+    const int rem = (int)(i - K * (m * m));
+    const int l = rem / (m * D2), r2 = rem - l * (m * D2);
+    const int a = r2 / m, sidx = r2 - a * m;
+    C32[i] = (float)C[K * (m * m) + l * (m * D2) + sidx * D2 + a];
+  }
 }
 
 template <typename T>
@@ -1049,8 +1101,7 @@ struct Solver {
       }
     } else {
       // mixed: FP32 copies of C^K and the block inverses, FP64 outer residual and update
-      const int64_t nC = M->nelt * (int64_t)M->tab.m * M->tab.m;
-      convert_kernel<float><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, nC);
+      convert_c32_kernel<D2><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, M->nelt);
       convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * D2 * D2);
       M->launches += 2;
       if (!x0) HDG_CUDA_TRY(cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, M->stream));
@@ -1145,8 +1196,7 @@ struct Solver {
     if (!M->beta_q) {
       rc = ensure_workspace(M, true);
       if (rc) return rc;
-      const int64_t nC = M->nelt * (int64_t)M->tab.m * M->tab.m;
-      convert_kernel<float><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, nC);
+      convert_c32_kernel<D2><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, M->nelt);
       convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * D2 * D2);
       convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_b, M->d_p32, nv);
       convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_b, M->d_r32, nv);
