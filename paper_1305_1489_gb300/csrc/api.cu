@@ -252,7 +252,7 @@ int hdg_get_condensed(const hdg_mesh* M, double* C, double* Cf) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "not assembled");
   const int m = M->tab.m;
   (void)m;
-  if (C) HDG_CUDA_TRY(launch_unblock(const_cast<hdg_mesh*>(M), M->d_C, C));  // stored face-blocked
+  if (C) HDG_CUDA_TRY(launch_unblock(const_cast<hdg_mesh*>(M), M->d_C, C));  // stored row-major
   if (Cf) HDG_CUDA_TRY(cudaMemcpyAsync(Cf, M->d_Cf, sizeof(double) * M->nelt * m, cudaMemcpyDeviceToDevice, M->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
   return HDG_OK;

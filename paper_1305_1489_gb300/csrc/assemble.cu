@@ -367,13 +367,10 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
 #pragma unroll
     for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
   }
-  // C^K face-blocked: Cout[l][s][a] = C^K[l d2 + a][s] (the row block of local face l is
-  // contiguous; the trace operator reads it with unit stride)
+  // C^K row-major, [K][r][s] with r = l d2 + a: the row block of local face l is contiguous
+  // and each row is one unit-stride array, read by the trace operator with 16-byte loads
   double* Cout = A.C + Ke * (int64_t)(m * m);
-  for (int t = tid; t < m * m; t += NT) {
-    const int fl = t / (m * d2), rem = t - fl * m * d2, sidx = rem / d2, a = rem - sidx * d2;
-    Cout[t] = Cs[(fl * d2 + a) * m + sidx];
-  }
+  for (int t = tid; t < m * m; t += NT) Cout[t] = Cs[t];
   __syncthreads();
 
   // recovery record, column-major so that the recovery kernel reads it with unit stride:

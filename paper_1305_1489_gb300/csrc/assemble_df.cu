@@ -364,11 +364,8 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
       for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
     }
   }
-  double* Cout = A.C + Ke * (int64_t)(m * m);  // face-blocked, as in assemble.cu
-  for (int t = tid; t < m * m; t += NT) {
-    const int fl = t / (m * d2), rem = t - fl * m * d2, sidx = rem / d2, a = rem - sidx * d2;
-    Cout[t] = df_to_double(Cs[(fl * d2 + a) * m + sidx]);
-  }
+  double* Cout = A.C + Ke * (int64_t)(m * m);  // row-major, as in assemble.cu
+  for (int t = tid; t < m * m; t += NT) Cout[t] = df_to_double(Cs[t]);
   __syncthreads();
 
   // recovery record, column-major (as in assemble.cu)

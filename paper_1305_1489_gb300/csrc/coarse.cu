@@ -68,13 +68,12 @@ __global__ void __launch_bounds__(32 * kGalWarps) galerkin0_kernel(
     __syncwarp();
     const double* CK = C + K * (int64_t)(m * m);
     for (int s = lane; s < m; s += 32) {
-      const int l = s / D2, a = s - l * D2;
-      const double* row = CK + l * (m * D2) + a;  // C^K[l d2 + a][t] at [l][t][a]
+      const double* row = CK + (int64_t)s * m;  // C^K[s][t], row-major
       double y[kElemNodes];
 #pragma unroll
       for (int u = 0; u < kElemNodes; ++u) y[u] = 0.0;
       for (int t = 0; t < m; ++t) {
-        const double c = row[t * D2];
+        const double c = row[t];
 #pragma unroll
         for (int u = 0; u < kElemNodes; ++u)
           if (u < cnt) y[u] = fma(c, Rs[w][t][u], y[u]);

@@ -87,7 +87,7 @@ struct hdg_mesh {
 
   // products of hdg_assemble_condense (library-owned)
   bool assembled = false;
-  double* d_C = nullptr;    // [nelt][4][m][d2] condensed C^K, face-blocked (eq. 5.5)
+  double* d_C = nullptr;    // [nelt][m][m] condensed C^K, row-major (eq. 5.5)
   double* d_Cf = nullptr;   // [nelt][m]    C_f^K (eq. 5.6)
   double* d_rec = nullptr;  // [nelt][rec_stride] recovery operators (eq. 5.3)
   int64_t rec_stride = 0;

@@ -106,12 +106,12 @@ __device__ __forceinline__ double apply(const Ops& F, const double* __restrict__
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
     const int64_t K = ow >> 2;
-    // face-blocked C^K: [K][l][s][a] = C^K[l d2 + a][s]
-    const double* Ck = F.C + K * (int64_t)(F.m * F.m) + (ow & 3) * (F.m * F.d2) + a;
+    // row-major C^K: row (l d2 + a)
+    const double* Ck = F.C + K * (int64_t)(F.m * F.m) + (int64_t)((ow & 3) * F.d2 + a) * F.m;
     for (int fl = 0; fl < 4; ++fl) {
       const double* xs = x + (int64_t)F.fbe[4 * K + fl] * F.d2;
-      const double* cc = Ck + (int64_t)(fl * F.d2) * F.d2;
-      for (int b = 0; b < F.d2; ++b) acc = fma(cc[(int64_t)b * F.d2], xs[b], acc);
+      const double* cc = Ck + fl * F.d2;
+      for (int b = 0; b < F.d2; ++b) acc = fma(cc[b], xs[b], acc);
     }
   }
   return acc;
@@ -187,10 +187,10 @@ __global__ void k_bj(Ops F, double* Binv) {
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
     const int l = ow & 3;
-    // C^K[l d2 + i][l d2 + j] is stored at [K][l][l d2 + j][i]
-    const double* Cb = F.C + (int64_t)(ow >> 2) * m * m + l * (m * d2) + (l * d2) * d2;
+    // C^K[l d2 + i][l d2 + j], row-major
+    const double* Cb = F.C + (int64_t)(ow >> 2) * m * m + (int64_t)(l * d2) * m + l * d2;
     for (int i = 0; i < d2; ++i)
-      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Cb[j * d2 + i];
+      for (int j = 0; j < d2; ++j) A[i * d2 + j] += Cb[i * m + j];
   }
   for (int j = 0; j < d2; ++j) {
     double s = A[j * d2 + j];

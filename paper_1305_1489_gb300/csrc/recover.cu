@@ -91,14 +91,12 @@ cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double*
   return cudaGetLastError();
 }
 
-// face-blocked storage [K][l][s][a] -> row-major C^K [K][l d2 + a][s]
+// copy of the stored C^K (already row-major [K][l d2 + a][s]) for the caller
 __global__ void unblock_kernel(const double* __restrict__ src, double* __restrict__ dst, int64_t nelt, int m, int d2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  (void)d2;
   if (t >= nelt * m * m) return;
-  const int64_t K = t / (m * m);
-  const int rem = (int)(t - K * m * m), r = rem / m, s = rem - r * m;
-  const int l = r / d2, a = r - l * d2;
-  dst[t] = src[K * m * m + (l * m + s) * d2 + a];
+  dst[t] = src[t];
 }
 
 cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst) {

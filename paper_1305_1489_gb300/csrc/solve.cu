@@ -7,8 +7,8 @@
 //     (H x)_e = sum_{K owns e as local face l} (C^K x_dK)_{l-block}
 // which is the sparse assembly of Section 6 applied without forming H.  Every row of every C^K
 // is read once per product; there are no atomics and the result is deterministic.  K1 stores
-// C^K face-blocked, [K][l][s][a] = C^K[l d2 + a][s], so the row block of a face is one
-// contiguous array whose d2 columns are read by the face's d2 threads with unit stride.
+// C^K row-major, so the row block of a face is one contiguous array and each of the face's d2
+// threads reads its own row with 16-byte loads.
 //
 // Scheduling: every face kernel runs on a persistent grid (M->face_blocks blocks, at most
 // kMaxBlocks, each looping over tiles of kNT / d2 whole faces), so the deterministic
@@ -113,11 +113,11 @@ __device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int*
   return true;
 }
 
-// (H x)_e entry a: the face's row blocks of C^K (face-blocked storage) times x_dK.  Each
+// (H x)_e entry a: the face's row blocks of C^K (row-major storage) times x_dK.  Each
 // owner's column (m values, unit stride across the face's d2 threads) and the gathered x_dK
 // are loaded into registers before any FMA, so every thread keeps 2m loads in flight.
-// The FP32 copy of C^K used by the inner solve is stored row-major per face block,
-// [K][l][a][s] = C^K[l d2 + a][s], so that thread a reads its row as m/4 16-byte loads.
+// C^K is stored row-major, [K][r][s] = C^K[r][s] with r = l d2 + a, so that thread a of face
+// l reads its row as 16-byte loads (m/4 for the FP32 copy, m/2 in FP64).
 template <int D2>
 __device__ __forceinline__ float face_apply_rm(const float* __restrict__ C, const float* __restrict__ x,
                                                const FaceArgs& F, int64_t e, int a) {
@@ -156,33 +156,40 @@ __device__ __forceinline__ float face_apply_rm(const float* __restrict__ C, cons
 template <typename T, int D2>
 __device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __restrict__ x, const FaceArgs& F,
                                         int64_t e, int a) {
-  if constexpr (sizeof(T) == 4) return face_apply_rm<D2>(C, x, F, e, a);
-  constexpr int m = 4 * D2;
-  T acc0 = (T)0, acc1 = (T)0;
+  if constexpr (sizeof(T) == 4) {
+    return face_apply_rm<D2>(C, x, F, e, a);
+  } else {
+    // C^K row-major [K][r][s] (r = l d2 + a): thread a reads its row as m/2 16-byte loads
+    constexpr int m = 4 * D2;
+    double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
-  for (int o = 0; o < 2; ++o) {
-    const int ow = __ldg(F.owner + 2 * e + o);
-    if (ow < 0) continue;
-    const int64_t K = ow >> 2;
-    const T* Cb = C + K * (int64_t)(m * m) + (ow & 3) * (m * D2) + a;
-    const int4 fb = __ldg(reinterpret_cast<const int4*>(F.fbe) + K);
-    const int f4[4] = {fb.x, fb.y, fb.z, fb.w};
-    T cv[m], xv[m];
+    for (int o = 0; o < 2; ++o) {
+      const int ow = __ldg(F.owner + 2 * e + o);
+      if (ow < 0) continue;
+      const int64_t K = ow >> 2;
+      const double2* row =
+          reinterpret_cast<const double2*>(C + K * (int64_t)(m * m) + ((ow & 3) * D2 + a) * (int64_t)m);
+      const int4 fb = __ldg(reinterpret_cast<const int4*>(F.fbe) + K);
+      const int f4[4] = {fb.x, fb.y, fb.z, fb.w};
+      double2 cv[m / 2];
+      double xv[m];
 #pragma unroll
-    for (int s = 0; s < m; ++s) cv[s] = __ldg(Cb + s * D2);
+      for (int q = 0; q < m / 2; ++q) cv[q] = __ldg(row + q);
 #pragma unroll
-    for (int fl = 0; fl < 4; ++fl) {
-      const T* xs = x + (int64_t)f4[fl] * D2;
+      for (int fl = 0; fl < 4; ++fl) {
+        const double* xs = x + (int64_t)f4[fl] * D2;
 #pragma unroll
-      for (int b = 0; b < D2; ++b) xv[fl * D2 + b] = xs[b];
+        for (int b = 0; b < D2; ++b) xv[fl * D2 + b] = xs[b];
+      }
+      asm volatile("" ::: "memory");  // keep every load above issued before the first FMA
+#pragma unroll
+      for (int q = 0; q < m / 2; ++q) {
+        acc0 = fma(cv[q].x, xv[2 * q], acc0);
+        acc1 = fma(cv[q].y, xv[2 * q + 1], acc1);
+      }
     }
-    asm volatile("" ::: "memory");  // keep every load above issued before the first FMA
-#pragma unroll
-    for (int s = 0; s < m; ++s) {
-      if (s & 1) acc1 = fma(cv[s], xv[s], acc1); else acc0 = fma(cv[s], xv[s], acc0);
-    }
+    return (T)(acc0 + acc1);
   }
-  return acc0 + acc1;
 }
 
 template <typename T, int D2>
@@ -288,10 +295,10 @@ __global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __re
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
     const int l = ow & 3;
-    // C^K[l d2 + i][l d2 + j] is stored at [K][l][l d2 + j][i]
-    const double* Cb = C + (int64_t)(ow >> 2) * m * m + l * (m * D2) + (l * D2) * D2;
+    // C^K[l d2 + i][l d2 + j], row-major
+    const double* Cb = C + (int64_t)(ow >> 2) * m * m + (int64_t)(l * D2) * m + l * D2;
     for (int i = 0; i < D2; ++i)
-      for (int j = 0; j < D2; ++j) A[i * D2 + j] += Cb[j * D2 + i];
+      for (int j = 0; j < D2; ++j) A[i * D2 + j] += Cb[i * m + j];
   }
   bool ok = true;
   if (nonsym) {
@@ -344,18 +351,13 @@ __global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __re
   if (!ok) atomicAdd(status + 3, 1);
 }
 
-// FP32 copy of C^K in the row-major face-block layout of face_apply_rm
+// FP32 copy of C^K (same row-major layout)
 template <int D2>
 __global__ void convert_c32_kernel(const double* __restrict__ C, float* __restrict__ C32, int64_t nelt) {
   constexpr int m = 4 * D2;
   const int64_t n = nelt * m * m;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t K = i / (m * m);
-    const int rem = (int)(i - K * (m * m));
-    const int l = rem / (m * D2), r2 = rem - l * (m * D2);
-    const int a = r2 / m, sidx = r2 - a * m;
-    C32[i] = (float)C[K * (m * m) + l * (m * D2) + sidx * D2 + a];
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    C32[i] = (float)C[i];
 }
 
 template <typename T>
