@@ -177,3 +177,49 @@ def test_double_float_assembly(k, s, shape, monkeypatch):
     assert rel(q1.cpu().numpy(), ref["q"]) < 1e-11
     uhat, it, rr = M2.solve_trace(rtol=1e-14, maxit=5000)
     assert rel(uhat.cpu().numpy(), ref["uhat"]) < 1e-11
+
+
+@pytest.mark.parametrize("k,s", [(2, 4), (3, 3)])
+def test_mixed_precision_field_errors(k, s):
+    """The mixed-precision path of the bench (double-float condensation, FP32 inner / FP64 outer
+    two-level PCG to 1e-10): every field against the FP64 oracle, and the discretisation
+    errors of eq. 10.1/10.2 unchanged to 3 digits."""
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_MIXED_FP32
+    from workloads import kuhn_p1_hierarchy
+    prob = _varprob(k)
+    c, e, d, n = make_mesh(prob, s=s)
+    ref = ohdg.solve_problem(prob, c, e, d, n)
+    M = gpu_setup(prob, c, e, d, n)
+    M.set_inner_tolerance(1e-6)
+    M.set_coarse_space(*kuhn_p1_hierarchy(s, prob.dirichlet_planes, max_coarsest=8, strict=False))
+    M.assemble_condense(HDG_DF32)
+    uhat, it, rr = M.solve_trace(rtol=1e-10, maxit=5000, precision=HDG_MIXED_FP32)
+    assert rr <= 1e-10
+    q, u = M.recover(uhat)
+    us = M.postprocess(q, u)
+    got = {"uhat": uhat.cpu().numpy(), "q": q.cpu().numpy(), "u": u.cpu().numpy(), "ustar": us.cpu().numpy()}
+    errs = {f: rel(got[f], ref[f]) for f in got}
+    print(f"k={k} s={s} field errors vs the FP64 oracle: " + ", ".join(f"{f} {v:.1e}" for f, v in errs.items()))
+    for f in got:
+        assert errs[f] < 1e-8, (f, errs[f])
+    mesh = ExpandedMesh(c, e, d, n)
+    e_gpu = ohdg.errors(mesh, k, got["q"], got["u"], got["uhat"], got["ustar"], prob)
+    e_ref = ohdg.errors(mesh, k, ref["q"], ref["u"], ref["uhat"], ref["ustar"], prob)
+    for key in e_ref:
+        assert abs(e_gpu[key] - e_ref[key]) <= 1e-3 * e_ref[key], (key, e_gpu[key], e_ref[key])
+
+
+def test_host_loop_matches_device_loop(monkeypatch):
+    """HDG_HOST_LOOP=1 (host replays instead of the conditional WHILE node) runs the same
+    iterations and reaches the same trace."""
+    prob = _varprob(2)
+    c, e, d, n = make_mesh(prob, s=3)
+    M = gpu_setup(prob, c, e, d, n)
+    M.assemble_condense()
+    u1, it1, r1 = M.solve_trace(rtol=1e-12, maxit=5000)
+    monkeypatch.setenv("HDG_HOST_LOOP", "1")
+    M2 = gpu_setup(prob, c, e, d, n)
+    M2.assemble_condense()
+    u2, it2, r2 = M2.solve_trace(rtol=1e-12, maxit=5000)
+    assert it1 == it2 and abs(r1 - r2) <= 1e-15 * max(r1, 1e-300) + 1e-30
+    assert np.array_equal(u1.cpu().numpy(), u2.cpu().numpy())
