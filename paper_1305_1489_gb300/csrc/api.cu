@@ -242,6 +242,8 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   M->assembled = true;
   M->asm_prec = precision;
+  M->c32_ready = false;
+  M->bj64_ready = M->bj32_ready = false;
   if (M->coarse) coarse_invalidate(M);
   M->rhs_ready = false;
   return check_status(M);

@@ -219,6 +219,9 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     if (rc) return rc;
     G.mesh->launches += 1;
     G.mesh->assembled = true;
+    G.mesh->c32_ready = false;
+    G.mesh->bj64_ready = G.mesh->bj32_ready = false;
+    if (G.mesh->coarse) coarse_invalidate(G.mesh);
     if (iters) iters[gi] = it;
     if (st) bad = true;
     std::vector<double> nrm(2 * G.probs.size());

@@ -25,14 +25,16 @@ namespace hdg {
 constexpr int kElemNodes = 8;  // level-0 nodes per element (4 for nested P1 spaces)
 constexpr int kGalWarps = 4;
 
-template <int D2>
+// T: arithmetic of the product and type of C^K (FP32 when the FP32 copy of the mixed solve
+// exists: the coarse operator only serves the preconditioner)
+template <int D2, typename T>
 __global__ void __launch_bounds__(32 * kGalWarps) galerkin0_kernel(
-    int64_t nelt, const double* __restrict__ C, const int32_t* __restrict__ fbe, const int32_t* __restrict__ ftype,
+    int64_t nelt, const T* __restrict__ C, const int32_t* __restrict__ fbe, const int32_t* __restrict__ ftype,
     const int32_t* __restrict__ fverts, const double* __restrict__ Tp, const int32_t* __restrict__ vnodes,
     const double* __restrict__ vwd, const int32_t* __restrict__ elist, const int32_t* __restrict__ eslot,
     double* __restrict__ A0) {
   constexpr int m = 4 * D2;
-  __shared__ double Rs[kGalWarps][m][kElemNodes], Ys[kGalWarps][m][kElemNodes];
+  __shared__ T Rs[kGalWarps][m][kElemNodes], Ys[kGalWarps][m][kElemNodes];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int64_t K = (int64_t)blockIdx.x * kGalWarps + w; K < nelt; K += (int64_t)gridDim.x * kGalWarps) {
     int nd[kElemNodes], cnt = 0;
@@ -45,9 +47,9 @@ __global__ void __launch_bounds__(32 * kGalWarps) galerkin0_kernel(
     for (int s = lane; s < m; s += 32) {
       const int fl = s / D2, b = s - fl * D2;
       const int64_t f = fbe[4 * K + fl];
-      double R[kElemNodes];
+      T R[kElemNodes];
 #pragma unroll
-      for (int u = 0; u < kElemNodes; ++u) R[u] = 0.0;
+      for (int u = 0; u < kElemNodes; ++u) R[u] = (T)0;
       if (ftype[f] != 1) {
         for (int i = 0; i < 3; ++i) {
           const int64_t v = fverts[3 * f + i];
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(32 * kGalWarps) galerkin0_kernel(
           for (int j = 0; j < 4; ++j) {
             const int node = vnodes[4 * v + j];
             if (node < 0) continue;
-            const double wt = tb * vwd[4 * v + j];
+            const T wt = (T)(tb * vwd[4 * v + j]);
 #pragma unroll
             for (int u = 0; u < kElemNodes; ++u)
               if (nd[u] == node) R[u] += wt;
@@ -66,14 +68,14 @@ __global__ void __launch_bounds__(32 * kGalWarps) galerkin0_kernel(
       for (int u = 0; u < kElemNodes; ++u) Rs[w][s][u] = R[u];
     }
     __syncwarp();
-    const double* CK = C + K * (int64_t)(m * m);
+    const T* CK = C + K * (int64_t)(m * m);
     for (int s = lane; s < m; s += 32) {
-      const double* row = CK + (int64_t)s * m;  // C^K[s][t], row-major
-      double y[kElemNodes];
+      const T* row = CK + (int64_t)s * m;  // C^K[s][t], row-major
+      T y[kElemNodes];
 #pragma unroll
-      for (int u = 0; u < kElemNodes; ++u) y[u] = 0.0;
+      for (int u = 0; u < kElemNodes; ++u) y[u] = (T)0;
       for (int t = 0; t < m; ++t) {
-        const double c = row[t];
+        const T c = row[t];
 #pragma unroll
         for (int u = 0; u < kElemNodes; ++u)
           if (u < cnt) y[u] = fma(c, Rs[w][t][u], y[u]);
@@ -85,10 +87,10 @@ __global__ void __launch_bounds__(32 * kGalWarps) galerkin0_kernel(
     for (int p = lane; p < kElemNodes * kElemNodes; p += 32) {
       const int u = p / kElemNodes, v = p - u * kElemNodes;
       if (u < cnt && v < cnt) {
-        double acc = 0.0;
+        T acc = (T)0;
         for (int s = 0; s < m; ++s) acc = fma(Rs[w][s][u], Ys[w][s][v], acc);
         const int32_t slot = eslot[K * kElemNodes * kElemNodes + p];
-        if (slot >= 0) atomicAdd(A0 + slot, acc);
+        if (slot >= 0) atomicAdd(A0 + slot, (double)acc);
       }
     }
     __syncwarp();
@@ -454,10 +456,15 @@ int coarse_launch_build(hdg_mesh* M) {
   cudaStream_t st = M->stream;
   for (const CoarseLevel& L : c->lv) HDG_CUDA_TRY(cudaMemsetAsync(L.val, 0, sizeof(double) * L.nnz, st));
   const unsigned gb = (unsigned)std::min<int64_t>((M->nelt + kGalWarps - 1) / kGalWarps, 152 * 16);
-#define HDG_GAL(D)                                                                                              \
-  galerkin0_kernel<D><<<gb, 32 * kGalWarps, 0, st>>>(M->nelt, M->d_C, M->d_facebyele, M->d_ftype, M->d_fverts, \
-                                                     M->d_Tproj, c->vnodes, c->vwd, c->elist, c->eslot,        \
-                                                     c->lv[0].val)
+#define HDG_GAL(D)                                                                                             \
+  if (M->c32_ready && M->d_C32)                                                                               \
+    galerkin0_kernel<D, float><<<gb, 32 * kGalWarps, 0, st>>>(M->nelt, M->d_C32, M->d_facebyele, M->d_ftype,   \
+                                                              M->d_fverts, M->d_Tproj, c->vnodes, c->vwd,      \
+                                                              c->elist, c->eslot, c->lv[0].val);               \
+  else                                                                                                        \
+    galerkin0_kernel<D, double><<<gb, 32 * kGalWarps, 0, st>>>(M->nelt, M->d_C, M->d_facebyele, M->d_ftype,   \
+                                                               M->d_fverts, M->d_Tproj, c->vnodes, c->vwd,     \
+                                                               c->elist, c->eslot, c->lv[0].val)
   switch (M->tab.d2) {
     case 3: HDG_GAL(3); break;
     case 6: HDG_GAL(6); break;

@@ -95,6 +95,8 @@ struct hdg_mesh {
 
   // trace-solve workspace (library-owned, allocated on first solve)
   bool rhs_ready = false;
+  bool bj64_ready = false, bj32_ready = false;  // block-Jacobi inverses of the current system
+  bool c32_ready = false;                       // FP32 copy of C^K of the current assembly
   double bnorm = 0.0;  // ||b||_2 of the current right-hand side (host copy)
   double inner_rtol = 1e-4;  // relative tolerance of each FP32 inner solve (mixed precision)
   double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr,

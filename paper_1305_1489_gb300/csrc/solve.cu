@@ -278,19 +278,20 @@ __global__ void rhs_kernel(FaceArgs F, const double* __restrict__ C, const doubl
 }
 
 // Inverse of each free face's diagonal block of H (block-Jacobi): Cholesky, or Gauss-Jordan
-// without pivoting for convection (the block's symmetric part is positive definite).
-template <int D2>
-__global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __restrict__ Binv, int32_t* status,
+// without pivoting for convection (the block's symmetric part is positive definite).  TB is
+// the arithmetic and output type: FP64 for the FP64 solves, FP32 for the inner FP32 solve.
+template <int D2, typename TB>
+__global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, TB* __restrict__ Binv, int32_t* status,
                           bool nonsym) {
   constexpr int m = 4 * D2;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= F.nfc) return;
-  double A[D2 * D2], X[D2 * D2];
+  TB A[D2 * D2], X[D2 * D2];
   if (F.ftype[e] == 1) {
-    for (int i = 0; i < D2 * D2; ++i) Binv[e * D2 * D2 + i] = 0.0;
+    for (int i = 0; i < D2 * D2; ++i) Binv[e * D2 * D2 + i] = (TB)0;
     return;
   }
-  for (int i = 0; i < D2 * D2; ++i) A[i] = 0.0;
+  for (int i = 0; i < D2 * D2; ++i) A[i] = (TB)0;
   for (int o = 0; o < 2; ++o) {
     const int ow = F.owner[2 * e + o];
     if (ow < 0) continue;
@@ -298,23 +299,23 @@ __global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __re
     // C^K[l d2 + i][l d2 + j], row-major
     const double* Cb = C + (int64_t)(ow >> 2) * m * m + (int64_t)(l * D2) * m + l * D2;
     for (int i = 0; i < D2; ++i)
-      for (int j = 0; j < D2; ++j) A[i * D2 + j] += Cb[i * m + j];
+      for (int j = 0; j < D2; ++j) A[i * D2 + j] += (TB)Cb[i * m + j];
   }
   bool ok = true;
   if (nonsym) {
-    for (int i = 0; i < D2 * D2; ++i) X[i] = 0.0;
-    for (int i = 0; i < D2; ++i) X[i * D2 + i] = 1.0;
+    for (int i = 0; i < D2 * D2; ++i) X[i] = (TB)0;
+    for (int i = 0; i < D2; ++i) X[i * D2 + i] = (TB)1;
     for (int j = 0; j < D2; ++j) {
-      const double piv = A[j * D2 + j];
-      ok = ok && piv != 0.0 && isfinite(piv);
-      const double ip = 1.0 / piv;
+      const TB piv = A[j * D2 + j];
+      ok = ok && piv != (TB)0 && isfinite(piv);
+      const TB ip = (TB)1 / piv;
       for (int c = 0; c < D2; ++c) {
         A[j * D2 + c] *= ip;
         X[j * D2 + c] *= ip;
       }
       for (int i = 0; i < D2; ++i) {
         if (i == j) continue;
-        const double f = A[i * D2 + j];
+        const TB f = A[i * D2 + j];
         for (int c = 0; c < D2; ++c) {
           A[i * D2 + c] -= f * A[j * D2 + c];
           X[i * D2 + c] -= f * X[j * D2 + c];
@@ -323,25 +324,25 @@ __global__ void bj_kernel(FaceArgs F, const double* __restrict__ C, double* __re
     }
   } else {
     for (int j = 0; j < D2; ++j) {  // in-place lower Cholesky
-      double s = A[j * D2 + j];
+      TB s = A[j * D2 + j];
       for (int l = 0; l < j; ++l) s -= A[j * D2 + l] * A[j * D2 + l];
-      ok = ok && s > 0.0;
-      const double d = sqrt(s);
+      ok = ok && s > (TB)0;
+      const TB d = sqrt(s);
       A[j * D2 + j] = d;
       for (int i = j + 1; i < D2; ++i) {
-        double t = A[i * D2 + j];
+        TB t = A[i * D2 + j];
         for (int l = 0; l < j; ++l) t -= A[i * D2 + l] * A[j * D2 + l];
         A[i * D2 + j] = t / d;
       }
     }
     for (int c = 0; c < D2; ++c) {  // columns of A^-1 = L^-T L^-1 e_c
       for (int i = 0; i < D2; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
+        TB s = (i == c) ? (TB)1 : (TB)0;
         for (int l = 0; l < i; ++l) s -= A[i * D2 + l] * X[l * D2 + c];
         X[i * D2 + c] = s / A[i * D2 + i];
       }
       for (int i = D2 - 1; i >= 0; --i) {
-        double s = X[i * D2 + c];
+        TB s = X[i * D2 + c];
         for (int l = i + 1; l < D2; ++l) s -= A[l * D2 + i] * X[l * D2 + c];
         X[i * D2 + c] = s / A[i * D2 + i];
       }
@@ -894,15 +895,31 @@ struct Solver {
                                                 M->uD, M->gN, xD, phiN);
     rhs_kernel<D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
                                               M->d_scal);
-    bj_kernel<D2><<<(unsigned)((M->nfc + 63) / 64), 64, 0, M->stream>>>(F, M->d_C, M->d_BJ, M->d_status,
-                                                                       M->beta_q != nullptr);
-    M->launches += 3;
+    M->launches += 2;
     HDG_CUDA_TRY(cudaGetLastError());
     double bb;
     HDG_CUDA_TRY(cudaMemcpyAsync(&bb, M->d_scal + S_BB, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
     HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
     M->bnorm = std::sqrt(bb);
     M->rhs_ready = true;
+    M->bj64_ready = M->bj32_ready = false;
+    return HDG_OK;
+  }
+
+  // Block-Jacobi inverses of the current assembly, in the precision of the solve that uses
+  // them (the FP32 inner solve computes its own in FP32); a non-SPD block counts in status[3].
+  template <typename TB>
+  static int ensure_bj(hdg_mesh* M) {
+    const bool f32 = sizeof(TB) == 4;
+    if (f32 ? M->bj32_ready : M->bj64_ready) return HDG_OK;
+    int rc = ensure_workspace(M, f32);
+    if (rc) return rc;
+    TB* out = f32 ? reinterpret_cast<TB*>(M->d_BJ32) : reinterpret_cast<TB*>(M->d_BJ);
+    bj_kernel<D2, TB><<<(unsigned)((M->nfc + 63) / 64), 64, 0, M->stream>>>(face_args(M), M->d_C, out, M->d_status,
+                                                                           M->beta_q != nullptr);
+    M->launches++;
+    HDG_CUDA_TRY(cudaGetLastError());
+    (f32 ? M->bj32_ready : M->bj64_ready) = true;
     return HDG_OK;
   }
 
@@ -1058,10 +1075,17 @@ struct Solver {
     int total_it = 0;
     bool converged = false, bad = false;
     double rnorm = 0.0;
+    if (mixed && !M->c32_ready) {  // FP32 copy of C^K (also read by the coarse set-up below)
+      convert_c32_kernel<D2><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, M->nelt);
+      M->launches++;
+      M->c32_ready = true;
+    }
     if (M->coarse && !M->beta_q && !M->coarse->ready) {
       rc = coarse_build(M);
       if (rc) return rc;
     }
+    rc = mixed ? ensure_bj<float>(M) : ensure_bj<double>(M);
+    if (rc) return rc;
     if (x0) {
       HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
       mask_dirichlet_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, D2, M->d_x);
@@ -1103,9 +1127,6 @@ struct Solver {
       }
     } else {
       // mixed: FP32 copies of C^K and the block inverses, FP64 outer residual and update
-      convert_c32_kernel<D2><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, M->nelt);
-      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * D2 * D2);
-      M->launches += 2;
       if (!x0) HDG_CUDA_TRY(cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, M->stream));
       for (int outer = 0; outer < 30; ++outer) {
         rc = true_residual(M, M->d_x, M->d_r, &rnorm);
@@ -1149,6 +1170,8 @@ struct Solver {
     int rc = ensure_workspace(M, false);
     if (rc) return rc;
     rc = prepare_rhs(M);
+    if (rc) return rc;
+    rc = ensure_bj<double>(M);
     if (rc) return rc;
     const int old = M->face_blocks;
     const int64_t nv = M->nfc * D2;
@@ -1198,8 +1221,12 @@ struct Solver {
     if (!M->beta_q) {
       rc = ensure_workspace(M, true);
       if (rc) return rc;
-      convert_c32_kernel<D2><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, M->nelt);
-      convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_BJ, M->d_BJ32, M->nfc * D2 * D2);
+      if (!M->c32_ready) {
+        convert_c32_kernel<D2><<<1216, 256, 0, M->stream>>>(M->d_C, M->d_C32, M->nelt);
+        M->c32_ready = true;
+      }
+      rc = ensure_bj<float>(M);
+      if (rc) return rc;
       convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_b, M->d_p32, nv);
       convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_b, M->d_r32, nv);
       HDG_CUDA_TRY(cudaMemsetAsync(M->d_x32, 0, sizeof(float) * nv, M->stream));
@@ -1263,6 +1290,8 @@ struct Solver {
       rc = coarse_build(M);
       if (rc) return rc;
     }
+    rc = ensure_bj<double>(M);
+    if (rc) return rc;
     FaceArgs F = face_args(M);
     const int nb = nblocks(M);
     const CoarseArgs CA = coarse_args(M);
@@ -1359,7 +1388,7 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const
                                        xD, phiN);
   rhs_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
                                      M->d_scal + S_NSCAL);
-  bj_kernel<D2><<<(unsigned)((M->nfc + 63) / 64), 64, 0, cs>>>(F, M->d_C, M->d_BJ, M->d_status, false);
+  bj_kernel<D2, double><<<(unsigned)((M->nfc + 63) / 64), 64, 0, cs>>>(F, M->d_C, M->d_BJ, M->d_status, false);
   int rcb = tl ? coarse_launch_build(M) : HDG_OK;  // Galerkin hierarchy of this assembly
   cudaMemsetAsync(norms, 0, sizeof(double) * 2 * np, cs);
   prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_b, face_prob, M->nfc, D2, norms);
