@@ -196,8 +196,8 @@ void coarse_free(hdg_mesh* M) {
     cudaFree(c->rap_dst[l]);
     cudaFree(c->rap_w[l]);
   }
-  void* ptrs[] = {c->d_lv, c->vnodes, c->vw, c->vwd, c->gptr, c->gfi, c->gw, c->elist, c->eslot, c->rc, c->Tf,
-                  c->e0, c->Adense, c->Ainv};
+  void* ptrs[] = {c->d_lv, c->vnodes, c->vw, c->vwd, c->gptr, c->gfi, c->gw, c->fnode, c->fwt, c->elist, c->eslot,
+                  c->rc, c->Tf, c->e0, c->Adense, c->Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -324,6 +324,24 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
       }
     }
   }
+  // per-face vertex nodes, when every vertex carries at most one level-0 node
+  bool single = true;
+  for (int64_t v = 0; v < nver && single; ++v)
+    for (int j = 1; j < 4; ++j) single = single && vn[4 * v + j] < 0;
+  std::vector<int32_t> fnode;
+  std::vector<float> fwt;
+  if (single) {
+    fnode.assign(3 * M->nfc, -1);
+    fwt.assign(3 * M->nfc, 0.f);
+    for (int64_t f = 0; f < M->nfc; ++f) {
+      if (M->h_faces[4 * f + 3] == 1) continue;  // Dirichlet: no prolongation
+      for (int i = 0; i < 3; ++i) {
+        const int64_t v = M->h_faces[4 * f + i];
+        fnode[3 * f + i] = vn[4 * v];
+        fwt[3 * f + i] = (float)vwd[4 * v];
+      }
+    }
+  }
   std::vector<int32_t> eslot((size_t)M->nelt * kElemNodes * kElemNodes, 0);
   for (int64_t K = 0; K < M->nelt; ++K)
     for (int u = 0; u < kElemNodes; ++u)
@@ -427,6 +445,8 @@ static int set_coarse(hdg_mesh* M, int nlev, const int64_t* sizes, const int32_t
   if (!rc) rc = upload(&c->gptr, gptr);
   if (!rc) rc = upload(&c->gfi, gfi);
   if (!rc) rc = upload(&c->gw, gw);
+  if (!rc && !fnode.empty()) rc = upload(&c->fnode, fnode);
+  if (!rc && !fwt.empty()) rc = upload(&c->fwt, fwt);
   if (!rc) rc = upload(&c->elist, elist);
   if (!rc) rc = upload(&c->eslot, eslot);
   if (!rc) rc = alloc(&c->rc, n0);

@@ -78,6 +78,8 @@ struct CoarseArgs {
   const int32_t* gptr;    // [n0+1] CSR of the restriction gather
   const int32_t* gfi;     // 4 f + i: free face f whose vertex slot i carries the node
   const float* gw;        // weight of the node at that vertex
+  const int32_t* fnode;   // [nfc][3] level-0 node of each face vertex (-1: none), or NULL when
+  const float* fwt;       //   a vertex may carry several nodes; [nfc][3] their weights
 };
 
 struct Coarse {
@@ -89,6 +91,8 @@ struct Coarse {
   double* vwd = nullptr;     // FP64 weights for the Galerkin set-up
   int32_t *gptr = nullptr, *gfi = nullptr;  // restriction gather (CoarseArgs)
   float* gw = nullptr;
+  int32_t* fnode = nullptr;  // per-face vertex nodes when every vertex carries at most one node
+  float* fwt = nullptr;
   int32_t* elist = nullptr;  // [nelt][8] level-0 nodes touched by the element (-1 unused)
   int32_t* eslot = nullptr;  // [nelt][64] CSR positions in A_0 of the pairs of elist
   std::vector<int64_t> rap_n;             // Galerkin triple counts per level
@@ -133,6 +137,14 @@ __global__ void restrict_gather_kernel(CoarseArgs CA, const T* __restrict__ r, c
 template <int D2>
 __device__ __forceinline__ float prolong_face(const CoarseArgs& CA, int64_t e, int a) {
   float s = 0.f;
+  if (CA.fnode) {  // one node per vertex (the P1 space of the mesh itself)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int nd = CA.fnode[3 * e + i];
+      if (nd >= 0) s = fmaf(CA.Tf[a * 3 + i] * CA.fwt[3 * e + i], CA.e0[nd], s);
+    }
+    return s;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const int64_t v = CA.fverts[3 * e + i];

@@ -96,8 +96,16 @@ __device__ bool grid_reduce(const double (&v)[NSLOT], double* red, unsigned int*
   __threadfence();
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
+    // eight independent loads per trip, so that the partials arrive in one memory latency
     double x = 0.0;
-    for (int i = threadIdx.x; i < nb; i += kNT) x += __ldcg(red + s * nb + i);
+    const double* rs = red + s * nb;
+    for (int i0 = threadIdx.x; i0 < nb; i0 += 8 * kNT) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (i0 + u * kNT < nb) ? __ldcg(rs + i0 + u * kNT) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x += v[u];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) wsum[s][w] = x;
@@ -767,6 +775,8 @@ static CoarseArgs coarse_args(hdg_mesh* M) {
   a.gptr = c->gptr;
   a.gfi = c->gfi;
   a.gw = c->gw;
+  a.fnode = c->fnode;
+  a.fwt = c->fwt;
   return a;
 }
 
