@@ -63,6 +63,7 @@ template <> struct K1Shape<2, 1> { static constexpr int NT = 128, MINB = 6; };
 template <> struct K1Shape<3, 1> { static constexpr int NT = 192, MINB = 4; };
 template <> struct K1Shape<3, 2> { static constexpr int NT = 128, MINB = 5; };
 template <> struct K1Shape<4, 1> { static constexpr int NT = 128, MINB = 2; };
+template <> struct K1Shape<4, 2> { static constexpr int NT = 192, MINB = 2; };
 
 // barrier among the warps 1 .. NT/32 - 1 (warp 0 is busy with a factorisation meanwhile)
 template <int NT>
@@ -412,17 +413,17 @@ static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
   int v = M->k1_variant;
   if (const char* ev = std::getenv("HDG_K1_VARIANT")) v = std::atoi(ev);
   if (v == 1) return launch_df_shape<K, 1>(M, a);
-  if (K == 3 && v == 2) return launch_df_shape<K, (K == 3 ? 2 : 0)>(M, a);
+  if (K >= 3 && v == 2) return launch_df_shape<K, (K >= 3 ? 2 : 0)>(M, a);
   return launch_df_shape<K, 0>(M, a);
 }
 
-int k1_variants(int k) { return k == 3 ? 3 : 2; }
+int k1_variants(int k) { return k >= 3 ? 3 : 2; }
 int k1_threads(int k, int variant) {
   switch (k) {
     case 1: return variant ? K1Shape<1, 1>::NT : K1Shape<1, 0>::NT;
     case 2: return variant ? K1Shape<2, 1>::NT : K1Shape<2, 0>::NT;
     case 3: return variant == 2 ? K1Shape<3, 2>::NT : variant ? K1Shape<3, 1>::NT : K1Shape<3, 0>::NT;
-    default: return variant ? K1Shape<4, 1>::NT : K1Shape<4, 0>::NT;
+    default: return variant == 2 ? K1Shape<4, 2>::NT : variant ? K1Shape<4, 1>::NT : K1Shape<4, 0>::NT;
   }
 }
 

@@ -148,7 +148,7 @@ def test_error_paths():
 
 
 @pytest.mark.parametrize("k,s,shape", [(1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (3, 2, "0"), (3, 2, "1"),
-                                     (3, 2, "2"), (4, 1, "0"), (4, 2, "1")])
+                                     (3, 2, "2"), (4, 1, "0"), (4, 2, "1"), (4, 1, "2")])
 def test_double_float_assembly(k, s, shape, monkeypatch):
     """HDG_DF32: the same condensation in double-float arithmetic on the FP32 pipe, for every
     launch shape the autotuner may pick (HDG_K1_VARIANT forces one)."""

@@ -144,3 +144,30 @@ def test_coarse_space_argument_errors():
     M.set_coarse_space(sizes, nodes, weights)
     z = M.precond_apply(torch.ones(M.nfc, M.d2, dtype=torch.float64, device="cuda"))
     assert torch.isfinite(z).all()
+
+
+def test_precond_apply_coarse_level0_matches_oracle():
+    """Level 0 on the 2h grid (each mesh vertex interpolates from up to two level-0 nodes):
+    the general prolongation and restriction paths against the oracle."""
+    from workloads import kuhn_coarse_interpolation
+    prob, c, e, d, n = _case("grf", 8, 2)
+    nodes0, weights0, n0 = kuhn_coarse_interpolation(8, 4, interior_only=True)
+    sz, nd, wt = kuhn_p1_hierarchy(4, prob.dirichlet_planes, max_coarsest=1)
+    assert sz[0] == n0
+    skip = 5 ** 3  # the vertex rows of the 4^3 grid's own hierarchy
+    sizes = sz
+    nodes = np.concatenate([nodes0, nd[skip:]]).astype(np.int32)
+    weights = np.concatenate([weights0, wt[skip:]])
+    mesh, tab, H, (Binv, Pi, As, Ps) = _oracle(prob, c, e, d, n, sizes, nodes, weights)
+    M = gpu_setup(prob, c, e, d, n)
+    M.assemble_condense()
+    M.set_coarse_space(sizes, nodes, weights)
+    rng = np.random.default_rng(3)
+    r = rng.normal(size=(M.nfc, M.d2))
+    r[mesh.dirfaces] = 0.0
+    z = M.precond_apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    zo = tl.apply(Binv, Pi, As, Ps, r.ravel()).reshape(-1, tab.d2)
+    zo[mesh.dirfaces] = 0.0
+    assert rel(z.ravel(), zo.ravel()) < 1e-5
+    u, it, rr = M.solve_trace(1e-10, 5000)
+    assert rr <= 1e-10
