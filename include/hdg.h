@@ -283,18 +283,22 @@ int hdg_postprocess(hdg_mesh* mesh, const double* q, const double* u, double* us
 /* ------------------------------------------------------------------ batched problems
  * Many independent problems of mixed degree solved together.  Problems of equal degree are
  * merged into one disjoint-union mesh (a "group"), so each phase is one launch per group, and
- * the whole batch (assembly + condensation, boundary data, block-Jacobi PCG run on the device
- * until convergence, recovery) is one CUDA graph launch with one branch per group.
+ * the whole batch (assembly + condensation, boundary data, PCG run on the device until
+ * convergence, recovery) is one CUDA graph launch with one branch per group.
  * hdg_batch_create: per problem p, host arrays as for hdg_mesh_create (coords[p] [nver[p]][3],
  *   elems[p] [nelt[p]][4], dir[p] [ndir[p]][3], neu[p] [nneu[p]][3]) and degree k[p] in 1..4.
  * hdg_batch_group: the union mesh of group g (owned by the batch: set its coefficients and
  *   boundary data with hdg_set_coefficients / hdg_set_boundary_data, query its nodes with
  *   hdg_quadrature_nodes), its degree, its problems (prob_ids [np]) and their element and
  *   face ranges in the union (elem_off, face_off [np+1]); any output pointer may be NULL.
- * hdg_batch_run: precision HDG_FP64 or HDG_DF32 (assembly arithmetic), FP64 PCG iterated
- *   until ||r|| <= rtol min_p ||b_p|| (so every problem meets rtol).  relres [nprob] host:
- *   per-problem ||b_p - H_p u_p|| / ||b_p||; iters [ngroups] host.  HDG_ERR_NOT_CONVERGED if
- *   some problem misses rtol within maxit.
+ * hdg_batch_run: precision HDG_FP64 or HDG_DF32 (assembly arithmetic), PCG iterated until
+ *   ||r|| <= rtol min_p ||b_p|| (so every problem meets rtol).  relres [nprob] host:
+ *   per-problem ||b_p - H_p u_p|| / ||b_p||; iters [ngroups] host (inner iterations for the
+ *   mixed solve).  HDG_ERR_NOT_CONVERGED if some problem misses rtol within maxit.  A group
+ *   mesh with a coarse space (hdg_set_coarse_space) uses the two-level preconditioner.
+ * hdg_batch_set_solve_precision: HDG_FP64 (default) or HDG_MIXED_FP32: FP64 residuals and
+ *   updates around FP32 inner PCG solves (each to the group mesh's inner tolerance), both
+ *   loops driven on the device inside the batch graph (nested conditional WHILE nodes).
  * hdg_batch_solution: device pointers (owned by the batch) to the group's u_hat [nfc][d2],
  *   q [nelt][3][n], u [nelt][n] in union numbering.                                        */
 typedef struct hdg_batch hdg_batch;
@@ -308,6 +312,7 @@ int hdg_batch_group(const hdg_batch* batch, int g, hdg_mesh** mesh, int* k, int*
                     int32_t* prob_ids, int64_t* elem_off, int64_t* face_off);
 int hdg_batch_run(hdg_batch* batch, int precision, double rtol, int maxit, double* relres,
                   int* iters);
+int hdg_batch_set_solve_precision(hdg_batch* batch, int precision);
 int hdg_batch_solution(const hdg_batch* batch, int g, double** uhat, double** q, double** u);
 int hdg_batch_destroy(hdg_batch* batch);
 

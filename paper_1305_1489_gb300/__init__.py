@@ -406,6 +406,14 @@ class HDGBatch:
             out.append(G["mesh"].autotune())
         return out
 
+    def set_solve_precision(self, precision):
+        """HDG_FP64 (default) or HDG_MIXED_FP32 for the batch's trace solves."""
+        _lib.check(_lib.load().hdg_batch_set_solve_precision(self._h, int(precision)))
+
+    def set_inner_tolerance(self, rtol):
+        for G in self.groups:
+            G["mesh"].set_inner_tolerance(rtol)
+
     def run(self, precision=HDG_FP64, rtol=1e-10, maxit=20000, raise_on_fail=True):
         relres = np.zeros(self.nprob)
         iters = np.zeros(len(self.groups), np.int32)

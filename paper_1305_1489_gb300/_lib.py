@@ -74,6 +74,7 @@ _SIGS = {
     "hdg_batch_num_groups": [P, C.POINTER(C.c_int)],
     "hdg_batch_group": [P, C.c_int, C.POINTER(P), C.POINTER(C.c_int), C.POINTER(C.c_int), P, P, P],
     "hdg_batch_run": [P, C.c_int, C.c_double, C.c_int, P, P],
+    "hdg_batch_set_solve_precision": [P, C.c_int],
     "hdg_batch_solution": [P, C.c_int, C.POINTER(P), C.POINTER(P), C.POINTER(P)],
     "hdg_batch_destroy": [P],
     "hdg_host_expand_mesh": [P, I64, P, I64, P, I64, P, I64, C.POINTER(I64), P, P, P],

@@ -37,6 +37,7 @@ struct hdg_batch {
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   int built_prec = -1, built_maxit = -1;
+  int solve_prec = HDG_FP64, built_solve_prec = -1;
   std::vector<int> built_gens;  // coarse-space generation, grid and K1 shape of every group at graph build
   double built_rtol = -1.0;
 };
@@ -179,7 +180,7 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     gens.push_back(G.mesh->k1_variant);
   }
   if (!B->exec || B->built_prec != precision || B->built_rtol != rtol || B->built_maxit != maxit ||
-      B->built_gens != gens) {
+      B->built_gens != gens || B->built_solve_prec != B->solve_prec) {
     if (B->exec) {
       cudaGraphExecDestroy(B->exec);
       B->exec = nullptr;
@@ -194,7 +195,8 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     HDG_CUDA_TRY(cudaGraphCreate(&graph, 0));
     for (auto& G : B->groups) {
       cudaGraphNode_t last;
-      int rc = batch_record_group(G.mesh, graph, precision, G.d_face_prob, (int)G.probs.size(), G.d_norms, rtol,
+      int rc = batch_record_group(G.mesh, graph, precision, B->solve_prec, G.d_face_prob, (int)G.probs.size(),
+                                  G.d_norms, rtol,
                                   maxit, G.d_q, G.d_u, G.d_uhat, &last);
       if (rc) {
         cudaGraphDestroy(graph);
@@ -208,6 +210,7 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
     B->built_rtol = rtol;
     B->built_maxit = maxit;
     B->built_gens = gens;
+    B->built_solve_prec = B->solve_prec;
   }
   HDG_CUDA_TRY(cudaGraphLaunch(B->exec, B->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(B->stream));
@@ -235,6 +238,14 @@ int hdg_batch_run(hdg_batch* B, int precision, double rtol, int maxit, double* r
   }
   if (bad) return fail(HDG_ERR_LOCAL_SINGULAR, "batch: a local factorisation or the PCG broke down");
   if (notconv) return fail(HDG_ERR_NOT_CONVERGED, "batch: some problem did not reach the tolerance within maxit");
+  return HDG_OK;
+}
+
+int hdg_batch_set_solve_precision(hdg_batch* B, int precision) {
+  if (!B) return fail(HDG_ERR_ARG, "NULL batch");
+  if (precision != HDG_FP64 && precision != HDG_MIXED_FP32)
+    return fail(HDG_ERR_ARG, "batch solve precision must be HDG_FP64 or HDG_MIXED_FP32");
+  B->solve_prec = precision;
   return HDG_OK;
 }
 

@@ -144,7 +144,7 @@ int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double
                 double* uhat, int* iters, double* relres);
 int trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm);
 int trace_apply(hdg_mesh* M, const double* x, double* y);
-int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
+int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, int solve_precision, const int32_t* face_prob, int np,
                        double* norms, double rtol, int maxit, double* q, double* u, double* uhat, cudaGraphNode_t* last);
 int batch_group_iterations(hdg_mesh* M, int* iters, int* status);
 int build_mesh(hdg_mesh* M, const double* coords, const int32_t* elems, const int32_t* dir, const int32_t* neu);

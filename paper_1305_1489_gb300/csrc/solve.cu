@@ -1371,10 +1371,41 @@ __global__ void batch_scalars_kernel(double* scal, const double* bn2, int np, do
   scal[S_MAXBODIES] = (double)(maxit / graph_iters + 2);
 }
 
+// Mixed-precision batch: control of the device-driven refinement loop.  After the FP64 residual
+// r = b - H x (rr in so[S_RR]): stop when rr <= so[S_TOL2], after max_outer refinements or when
+// the inner iterations reach so[S_MAXIT]; otherwise start an inner FP32 solve to inner_rtol.
+__global__ void outer_check_kernel(cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner, double* so,
+                                   double* si, double inner_rtol, int max_outer, int graph_iters) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double rr = so[S_RR];
+  const double nb = so[S_BODIES] + 1.0;
+  so[S_BODIES] = nb;
+  const bool done = !(rr > so[S_TOL2]) || nb > (double)max_outer || so[S_ITERS] >= so[S_MAXIT];
+  for (int i = 0; i < S_NSCAL; ++i) si[i] = 0.0;
+  si[S_TOL2] = done ? 1e300 : inner_rtol * inner_rtol * rr;
+  const double left = fmax(so[S_MAXIT] - so[S_ITERS], 1.0);
+  si[S_MAXIT] = left;
+  si[S_MAXBODIES] = floor(left / graph_iters) + 2.0;
+  cudaGraphSetConditional(h_outer, done ? 0u : 1u);
+  cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+}
+
+// total inner iterations of the refinement
+__global__ void outer_accum_kernel(double* so, const double* si) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) so[S_ITERS] += si[S_ITERS];
+}
+
 template <int D2>
-static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
-                        double* norms, double rtol, int maxit, double* q, double* u, double* uhat,
-                        cudaGraphNode_t* last) {
+static int record_group_mixed(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
+                              double* norms, double rtol, int maxit, double* q, double* u, double* uhat,
+                              cudaGraphNode_t* last);
+
+template <int D2>
+static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, int solve_precision,
+                        const int32_t* face_prob, int np, double* norms, double rtol, int maxit, double* q, double* u,
+                        double* uhat, cudaGraphNode_t* last) {
+  if (solve_precision == HDG_MIXED_FP32)
+    return record_group_mixed<D2>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
   FaceArgs F = face_args(M);
   const int nb = nblocks(M);
   const int64_t nv = M->nfc * D2;
@@ -1472,13 +1503,152 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const
   return HDG_OK;
 }
 
-int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
-                       double* norms, double rtol, int maxit, double* q, double* u, double* uhat, cudaGraphNode_t* last) {
+// Part A, the refinement WHILE loop (FP64 residual, FP32 inner PCG in a nested WHILE loop,
+// update) and part C of a mixed-precision group.
+template <int D2>
+static int record_group_mixed(hdg_mesh* M, cudaGraph_t graph, int asm_precision, const int32_t* face_prob, int np,
+                              double* norms, double rtol, int maxit, double* q, double* u, double* uhat,
+                              cudaGraphNode_t* last) {
+  constexpr int kMaxOuter = 30;
+  FaceArgs F = face_args(M);
+  const int nb64 = nblocks(M);
+  const int nb32 = nblocks_t<float>(M);
+  const int64_t nv = M->nfc * D2;
+  int rc = ensure_workspace(M, true);
+  if (rc) return rc;
+  if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = M->cap_stream;
+  cudaStream_t saved = M->stream;
+  double* so = M->d_scal;             // refinement scalars
+  double* si = M->d_scal + S_NSCAL;   // inner FP32 PCG scalars
+  double* xD = M->d_uhatD;
+  double* phiN = M->d_uhatD + nv;
+  float* q32 = reinterpret_cast<float*>(M->d_q);
+  const bool tl = M->coarse != nullptr;
+  M->c32_ready = true;  // the graph converts C^K before the coarse set-up reads it
+  const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
+  // A: assembly, boundary data, right-hand side, FP32 operator and block inverses, coarse
+  // hierarchy, per-problem ||b_p||, x = 0
+  cudaGraph_t ga;
+  HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  M->stream = cs;
+  cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, cs);
+  cudaError_t e = (asm_precision == HDG_DF32) ? launch_assemble_df(M) : launch_assemble(M);
+  bdata_kernel<D2><<<nb64, kNT, 0, cs>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf, M->uD,
+                                         M->gN, xD, phiN);
+  rhs_kernel<D2><<<nb64, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter, si);
+  convert_c32_kernel<D2><<<1216, 256, 0, cs>>>(M->d_C, M->d_C32, M->nelt);
+  bj_kernel<D2, float><<<(unsigned)((M->nfc + 63) / 64), 64, 0, cs>>>(F, M->d_C, M->d_BJ32, M->d_status, false);
+  int rcb = tl ? coarse_launch_build(M) : HDG_OK;
+  cudaMemsetAsync(norms, 0, sizeof(double) * 2 * np, cs);
+  prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_b, face_prob, M->nfc, D2, norms);
+  batch_scalars_kernel<<<1, 32, 0, cs>>>(so, norms, np, rtol, maxit, kGraphIters);
+  cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, cs);
+  M->stream = saved;
+  M->c32_ready = false;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &ga);
+  if (rcb) {
+    if (e2 == cudaSuccess) cudaGraphDestroy(ga);
+    return rcb;
+  }
+  if (e != cudaSuccess || e2 != cudaSuccess) return fail(HDG_ERR_CUDA, "batch graph capture (assembly/setup) failed");
+  cudaGraphNode_t na, nw, nc;
+  HDG_CUDA_TRY(cudaGraphAddChildGraphNode(&na, graph, nullptr, 0, ga));
+  cudaGraphDestroy(ga);
+  // W: refinement loop
+  cudaGraphConditionalHandle h_outer;
+  HDG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_outer, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h_outer;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  HDG_CUDA_TRY(cudaGraphAddNode(&nw, graph, &na, nullptr, 1, &cp));
+  cudaGraph_t obody = cp.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle h_inner;
+  HDG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_inner, obody, 1, cudaGraphCondAssignDefault));
+  // outer body, first part: FP64 residual, control, FP32 start of the inner solve
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pcg_init_kernel<double, D2><<<nb64, kNT, 0, cs>>>(F, M->d_C, M->d_b, M->d_x, true, M->d_r, M->d_red, M->d_counter,
+                                                    so);
+  outer_check_kernel<<<1, 32, 0, cs>>>(h_outer, h_inner, so, si, M->inner_rtol, kMaxOuter, kGraphIters);
+  convert_kernel<float><<<304, 256, 0, cs>>>(M->d_r, M->d_r32, nv);
+  pcg_init_kernel<float, D2><<<nb32, kNT, 0, cs>>>(F, M->d_C32, M->d_r32, M->d_x32, false, M->d_q32, M->d_red,
+                                                   M->d_counter, si);
+  if (tl) {
+    coarse_cycle<float, D2>(M, CA, M->d_q32, cs, si + S_DONE);
+    pcg_zc_kernel<float, D2, true><<<nb32, kNT, 0, cs>>>(F, CA, M->d_BJ32, M->d_q32, M->d_z32, M->d_p32, M->d_red,
+                                                         M->d_counter, si);
+  } else {
+    pcg_precond_kernel<float, D2><<<nb32, kNT, 0, cs>>>(F, M->d_BJ32, M->d_q32, M->d_z32, M->d_p32, M->d_red,
+                                                        M->d_counter, si);
+  }
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  HDG_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+  cudaGraph_t junk = nullptr;
+  HDG_CUDA_TRY(cudaStreamEndCapture(cs, &junk));
+  // the inner FP32 PCG loop, nested
+  cudaGraphNode_t ni;
+  cudaGraphNodeParams ci = {};
+  ci.type = cudaGraphNodeTypeConditional;
+  ci.conditional.handle = h_inner;
+  ci.conditional.type = cudaGraphCondTypeWhile;
+  ci.conditional.size = 1;
+  HDG_CUDA_TRY(cudaGraphAddNode(&ni, obody, tail.data(), nullptr, tail.size(), &ci));
+  cudaGraph_t ibody = ci.conditional.phGraph_out[0];
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  for (int it = 0; it < kGraphIters; ++it) {
+    pcg_matvec_kernel<float, D2><<<nb32, kNT, 0, cs>>>(F, M->d_C32, M->d_p32, q32, M->d_red, M->d_counter, si);
+    if (tl) {
+      pcg_update_tl_kernel<float, D2><<<nb32, kNT, 0, cs>>>(F, M->d_x32, M->d_q32, M->d_p32, q32, M->d_red,
+                                                            M->d_counter, si);
+      coarse_cycle<float, D2>(M, CA, M->d_q32, cs, si + S_DONE);
+      pcg_zc_kernel<float, D2, false><<<nb32, kNT, 0, cs>>>(F, CA, M->d_BJ32, M->d_q32, M->d_z32, M->d_p32, M->d_red,
+                                                            M->d_counter, si);
+    } else {
+      pcg_update_kernel<float, D2><<<nb32, kNT, 0, cs>>>(F, M->d_BJ32, M->d_x32, M->d_q32, M->d_z32, M->d_p32, q32,
+                                                         M->d_red, M->d_counter, si);
+    }
+    pcg_dir_kernel<float><<<nb32, kNT, 0, cs>>>(nv, M->d_z32, M->d_p32, si);
+  }
+  loop_control_kernel<<<1, 32, 0, cs>>>(h_inner, si, S_DONE, S_BODIES, S_MAXBODIES);
+  HDG_CUDA_TRY(cudaStreamEndCapture(cs, &junk));
+  // outer body, last part: x += x32, iteration count
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, obody, &ni, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  axpy_f32_kernel<<<nb64, kNT, 0, cs>>>(nv, M->d_x32, M->d_x);
+  outer_accum_kernel<<<1, 32, 0, cs>>>(so, si);
+  HDG_CUDA_TRY(cudaStreamEndCapture(cs, &junk));
+  // C: true residual, per-problem ||r_p||, trace with Dirichlet data, recovery
+  cudaGraph_t gc;
+  HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  M->stream = cs;
+  pcg_init_kernel<double, D2><<<nb64, kNT, 0, cs>>>(F, M->d_C, M->d_b, M->d_x, true, M->d_q, M->d_red, M->d_counter,
+                                                    si);
+  prob_norms_kernel<<<304, 256, 0, cs>>>(M->d_q, face_prob, M->nfc, D2, norms + np);
+  finish_kernel<<<nb64, kNT, 0, cs>>>(nv, M->d_ftype, D2, M->d_x, M->d_uhatD, uhat);
+  e = launch_recover(M, uhat, q, u);
+  M->stream = saved;
+  e2 = cudaStreamEndCapture(cs, &gc);
+  if (e != cudaSuccess || e2 != cudaSuccess) return fail(HDG_ERR_CUDA, "batch graph capture (recovery) failed");
+  HDG_CUDA_TRY(cudaGraphAddChildGraphNode(&nc, graph, &nw, 1, gc));
+  cudaGraphDestroy(gc);
+  *last = nc;
+  M->rhs_ready = false;
+  return HDG_OK;
+}
+
+int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, int solve_precision,
+                       const int32_t* face_prob, int np, double* norms, double rtol, int maxit, double* q, double* u,
+                       double* uhat, cudaGraphNode_t* last) {
+  const int sp = solve_precision;
   switch (M->tab.d2) {
-    case 3: return record_group<3>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
-    case 6: return record_group<6>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
-    case 10: return record_group<10>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
-    case 15: return record_group<15>(M, graph, asm_precision, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 3: return record_group<3>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 6: return record_group<6>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 10: return record_group<10>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
+    case 15: return record_group<15>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
   }
   return fail(HDG_ERR_UNSUPPORTED, "unsupported degree");
 }

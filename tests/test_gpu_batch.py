@@ -116,3 +116,52 @@ def test_batch_two_level_matches_individual_solves():
     _, it_again = B.run(precision=HDG_FP64, rtol=1e-11, maxit=20000)
     assert np.all(it_again == it_bj)
     B.close()
+
+
+@pytest.mark.parametrize("coarse", [False, True])
+def test_batch_mixed_precision_matches_individual_solves(coarse):
+    """FP32 inner / FP64 outer refinement inside the batch graph (nested device-driven loops),
+    with block-Jacobi or two-level preconditioning: every problem reaches rtol and the oracle's
+    solution."""
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_MIXED_FP32, HDGBatch
+    from workloads import kuhn_p1_hierarchy
+    probs = _problems() + [sinsinsin("b6", 6, 2, kappa0=2.0, c0=1.0)]
+    meshes = [make_mesh(p) for p in probs]
+    B = HDGBatch([(c, e, d, n, p.k) for (c, e, d, n), p in zip(meshes, probs)])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    for G in B.groups:
+        M = G["mesh"]
+        X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+        FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
+        kap, cq, fq = (np.zeros_like(X) for _ in range(3))
+        uD = np.zeros_like(FX)
+        gN = np.zeros((3,) + FX.shape)
+        for i, p in enumerate(G["probs"]):
+            pr = probs[p]
+            es = slice(G["elem_off"][i], G["elem_off"][i + 1])
+            fs = slice(G["face_off"][i], G["face_off"][i + 1])
+            kap[es], cq[es], fq[es] = pr.kappa(X[es], Y[es], Z[es]), pr.c(X[es], Y[es], Z[es]), pr.f(X[es], Y[es], Z[es])
+            uD[fs] = pr.uD(FX[fs], FY[fs], FZ[fs])
+            if pr.gN is not None:
+                gN[:, fs] = np.stack(pr.gN(FX[fs], FY[fs], FZ[fs]))
+        M.set_coefficients(dev(kap), dev(cq), dev(fq))
+        M.set_boundary_data(dev(uD), dev(gN))
+    if coarse:
+        B.set_coarse_spaces([kuhn_p1_hierarchy(p.s, p.dirichlet_planes, max_coarsest=1, strict=False) for p in probs])
+    B.set_inner_tolerance(1e-6)
+    B.set_solve_precision(HDG_MIXED_FP32)
+    relres, iters = B.run(precision=HDG_DF32, rtol=1e-11, maxit=20000)
+    assert np.all(relres <= 1e-11) and np.all(iters > 0)
+    for g, G in enumerate(B.groups):
+        uhat, q, u = (t.cpu().numpy() for t in B.solution(g))
+        for i, p in enumerate(G["probs"]):
+            c, e, d, n = meshes[p]
+            ref = ohdg.solve_problem(probs[p], c, e, d, n)
+            fs = slice(G["face_off"][i], G["face_off"][i + 1])
+            es = slice(G["elem_off"][i], G["elem_off"][i + 1])
+            assert rel(uhat[fs], ref["uhat"]) < 1e-9, (p, rel(uhat[fs], ref["uhat"]))
+            assert rel(u[es], ref["u"]) < 1e-9
+    # a second launch reaches the same result
+    relres2, iters2 = B.run(precision=HDG_DF32, rtol=1e-11, maxit=20000)
+    assert np.array_equal(iters, iters2) and np.allclose(relres, relres2, rtol=0, atol=1e-15)
+    B.close()
