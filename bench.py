@@ -43,8 +43,8 @@ FP64_MEASURED_TFLOPS = 1.19  # FMA-chain microbenchmark on this machine's GB300 (1 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one K1 launch at this workload,
 # from the ncu captures summarised under profiles/, valid while the kernel source is unchanged.
-K1_TRAFFIC = {"assemble_df.cu": {"sha256": "9604f55a5a9b32ff1647ec10ad31e643415b3e00a41e9ca4df994475f546afff",
-                                 "bytes": 77148672 + 820019968},
+K1_TRAFFIC = {"assemble_df.cu": {"sha256": "917f948dda95ffd0e8441e0eb8b6b02897fe02ccf48be5cfc6a36520bcbbb2fe",
+                                 "bytes": 77768448 + 819557376},
               "assemble.cu": {"sha256": None, "bytes": None}}
 
 

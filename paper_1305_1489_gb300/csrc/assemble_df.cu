@@ -75,31 +75,70 @@ __device__ __forceinline__ df shfl_xor_df(df x, int o) {
   return df_make(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
 }
 
-// Cholesky by one warp, double-float (left-looking by columns).  invd receives 1/L_jj.
-template <int N>
-__device__ __forceinline__ bool warp_cholesky_df(df* A, df* invd, int lane) {
+// Cholesky (lower) of the N x N double-float matrix A by G threads (g = this thread's index
+// among them): G = 32 is one warp (synchronised by __syncwarp), any other G is the whole
+// block (__syncthreads).  Right-looking: at step j the pivot A_jj is final; every thread takes
+// y = 1/sqrt(A_jj) by df_rsqrt (no FP64) and the trailing triangle is updated,
+// A_ik -= A_ij A_kj y^2 for i >= k > j, its entries dealt round-robin to the G threads in
+// chunks of CH whose loads are issued before any store (so they overlap).  The trailing
+// entries of step j are the last (N-j-1)(N-j)/2 pairs (r <= c) of the row-major upper-triangle
+// list `pairs`, read as one 32-bit word each.  Column j is scaled to L_ij = A_ij y at step
+// j + 1, after the barrier that ends its readers, so each step takes one barrier.  Only the
+// lower triangle is read or written; L_jj goes on the diagonal and 1/L_jj into invd.
+// Returns, on every thread, whether all pivots were positive.
+template <int N, int G>
+__device__ __forceinline__ bool group_cholesky_df(df* A, df* invd, const int16_t* __restrict__ pairs, int g) {
+  constexpr int NP = N * (N + 1) / 2, CH = 4;
+  const int* __restrict__ pw = reinterpret_cast<const int*>(pairs);
   bool ok = true;
+  df yp = df_make(1.f, 0.f), pp = df_make(1.f, 0.f);
   for (int j = 0; j < N; ++j) {
-    dacc s = dacc_zero();
-    for (int l = lane; l < j; l += 32) dacc_mac(s, A[j * N + l], A[j * N + l]);
-    df sv = dacc_result(s);
+    if (j > 0) {
+      for (int i = j + g; i < N; i += G) A[i * N + j - 1] = df_mul(A[i * N + j - 1], yp);
+      if (g == 0) {
+        A[(j - 1) * N + j - 1] = df_mul(pp, yp);
+        invd[j - 1] = yp;
+      }
+    }
+    const df piv = A[j * N + j];
+    ok = ok && (piv.hi > 0.f);
+    const df y = df_rsqrt(piv.hi > 0.f ? piv : df_make(1.f, 0.f));
+    const df y2 = df_mul(y, y);
+    for (int t0 = NP - (N - j - 1) * (N - j) / 2 + g; t0 < NP; t0 += CH * G) {
+      int at[CH];
+      df a[CH], lc[CH], lr[CH];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sv = df_add(sv, shfl_xor_df(sv, o));
-    const double dd = df_to_double(A[j * N + j]) - df_to_double(sv);
-    ok = ok && (dd > 0.0);
-    const double d = sqrt(dd);
-    const df dv = df_from_double(d), id = df_from_double(1.0 / d);
-    __syncwarp();
-    if (lane == 0) {
-      A[j * N + j] = dv;
-      invd[j] = id;
+      for (int u = 0; u < CH; ++u) {
+        const int t = t0 + u * G;
+        if (t < NP) {
+          const int w = __ldg(pw + t);
+          const int r = w & 0xffff, c = w >> 16;  // r <= c: the lower-triangle entry (c, r)
+          at[u] = c * N + r;
+          a[u] = A[c * N + r];
+          lc[u] = A[c * N + j];
+          lr[u] = A[r * N + j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (t0 + u * G < NP) {
+          dacc s = dacc_from(a[u]);
+          dacc_msub(s, lc[u], df_mul(lr[u], y2));
+          a[u] = dacc_result(s);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (t0 + u * G < NP) A[at[u]] = a[u];
     }
-    for (int i = j + 1 + lane; i < N; i += 32) {
-      dacc t = dacc_from(A[i * N + j]);
-      for (int l = 0; l < j; ++l) dacc_msub(t, A[i * N + l], A[j * N + l]);
-      A[i * N + j] = df_mul(dacc_result(t), id);
-    }
-    __syncwarp();
+    if (G == 32) __syncwarp();
+    else __syncthreads();
+    yp = y;
+    pp = piv;
+  }
+  if (g == 0) {
+    A[(N - 1) * N + N - 1] = df_mul(pp, yp);
+    invd[N - 1] = yp;
   }
   return ok;
 }
@@ -149,7 +188,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   df* Gt = smd + SM::o_G;
   df* Cs = smd + SM::o_C;
   __shared__ df s_a[3][3], s_nrm[4][3], s_T[4], s_nn[4][4];
-  __shared__ double s_vol;
+  __shared__ double s_geo[25], s_vol;  // a (9), nrm (12), area (4) in FP64
   __shared__ df invdM[n], invdS[n];
   __shared__ int s_perm[4];
   __shared__ int s_bad, s_coef;
@@ -162,22 +201,32 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     Geo g;
     element_geometry(A.vx, A.nelt, Ke, g);
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) s_a[i][j] = df_from_double(g.a[i][j]);
+      for (int j = 0; j < 3; ++j) s_geo[3 * i + j] = g.a[i][j];
     for (int l = 0; l < 4; ++l) {
-      for (int d = 0; d < 3; ++d) s_nrm[l][d] = df_from_double(g.nrm[l][d]);
-      const double tau = A.tau ? A.tau[Ke * 4 + l] : 1.0;
-      s_T[l] = df_from_double(tau * g.area[l]);  // T_l = tau_l |e_l|, eq. 4.22
-      s_perm[l] = A.perm[Ke * 4 + l] - 1;
+      for (int d = 0; d < 3; ++d) s_geo[9 + 3 * l + d] = g.nrm[l][d];
+      s_geo[21 + l] = g.area[l];
     }
-    for (int l = 0; l < 4; ++l)
-      for (int l2 = 0; l2 < 4; ++l2)
-        s_nn[l][l2] = df_from_double(g.nrm[l][0] * g.nrm[l2][0] + g.nrm[l][1] * g.nrm[l2][1] +
-                                     g.nrm[l][2] * g.nrm[l2][2]);
     s_vol = g.vol;
     s_bad = 0;
     s_coef = 0;
   }
+  if (tid < 4) s_perm[tid] = A.perm[Ke * 4 + tid] - 1;
   __syncthreads();
+
+  // the geometry in double-float, one value per thread (FP64 work off the single-thread path)
+  if (tid < 21) {
+    const df v = df_from_double(s_geo[tid]);
+    if (tid < 9) s_a[tid / 3][tid % 3] = v;
+    else s_nrm[(tid - 9) / 3][(tid - 9) % 3] = v;
+  } else if (tid < 25) {
+    const int l = tid - 21;
+    const double tau = A.tau ? A.tau[Ke * 4 + l] : 1.0;
+    s_T[l] = df_from_double(tau * s_geo[21 + l]);  // T_l = tau_l |e_l|, eq. 4.22
+  } else if (tid < 41) {
+    const double* x = s_geo + 9 + 3 * ((tid - 25) / 4);
+    const double* y = s_geo + 9 + 3 * ((tid - 25) % 4);
+    s_nn[(tid - 25) / 4][(tid - 25) % 4] = df_from_double(x[0] * y[0] + x[1] * y[1] + x[2] * y[2]);
+  }
 
   for (int q = tid; q < nq; q += NT) {
     const double kap = A.kappa[Ke * nq + q], cc = A.c[Ke * nq + q], ff = A.f[Ke * nq + q];
@@ -224,9 +273,9 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   __syncthreads();
 
-  if (warp == 0) {
-    const bool ok = warp_cholesky_df<n>(Ms, invdM, lane);
-    if (!ok && lane == 0) s_bad = 1;
+  {  // every thread of the block factors M (nothing else can proceed meanwhile)
+    const bool ok = group_cholesky_df<n, NT>(Ms, invdM, A.pairs_n, tid);
+    if (!ok && tid == 0) s_bad = 1;
   }
   __syncthreads();
 
@@ -273,7 +322,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   __syncthreads();
 
   if (warp == 0) {
-    const bool ok = warp_cholesky_df<n>(Ss, invdS, lane);
+    const bool ok = group_cholesky_df<n, 32>(Ss, invdS, A.pairs_n, lane);
     if (!ok && lane == 0) s_bad = 1;
   } else {
     // G^T[j][r] = T_l E[r][j] + (V^T Wt_l)[r][j] for the columns r of face l, WTF faces per pass

@@ -11,8 +11,9 @@
 // rigorous error bounds for basic building blocks of double-word arithmetic", ACM TOMS 2017,
 // DWTimesDW1); dot products accumulate the exact leading products with two_sum and collect
 // every low-order term in a second float, as in the compensated dot product of Ogita, Rump
-// and Oishi (SIAM J. Sci. Comput. 2005), then renormalise once.  Reciprocal and square root
-// are formed in FP64 from the double-float value (a handful per element).
+// and Oishi (SIAM J. Sci. Comput. 2005), then renormalise once.  The reciprocal square root
+// of a pivot takes a float seed and two Newton–Raphson steps; the few other reciprocals and
+// roots are formed in FP64 from the double-float value.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -114,6 +115,22 @@ __device__ __forceinline__ void dacc_add(dacc& acc, df x) {
 }
 
 __device__ __forceinline__ df dacc_result(const dacc& a) { return fast_two_sum(a.hi, a.lo); }
+
+// 1/sqrt(a) for a > 0 in the normal float range, on the FP32 pipe: a float seed y0 (rsqrtf,
+// a few ulp) refined by two Newton–Raphson steps for the inverse square root,
+// y <- y + y (1 - a y^2) / 2, which square the relative error (~2^-22 -> ~2^-44 -> the
+// ~2^-45 floor set by the double-float product a y^2).  1 - a y^2 is small, so after the exact
+// leading subtraction (Sterbenz) it needs only float precision.
+__device__ __forceinline__ df df_rsqrt(df a) {
+  const float y0 = rsqrtf(a.hi);
+  const float p = __fmul_rn(y0, y0);
+  df t = df_mul(a, df_make(p, __fmaf_rn(y0, y0, -p)));  // a y0^2 (y0^2 exact as p + e)
+  float r = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+  const df y = fast_two_sum(y0, __fmul_rn(__fmul_rn(y0, r), 0.5f));
+  t = df_mul(a, df_mul(y, y));
+  r = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+  return fast_two_sum(y.hi, __fadd_rn(y.lo, __fmul_rn(__fmul_rn(y.hi, r), 0.5f)));
+}
 
 // 1/x and sqrt(x) through FP64 (few per element)
 __device__ __forceinline__ df df_recip(df x) { return df_from_double(1.0 / df_to_double(x)); }

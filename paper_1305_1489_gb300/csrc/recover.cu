@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(NT) postprocess_kernel(
   using D = Dims<K>;
   constexpr int n = D::n, nq = D::nq, n1 = D::n1, nr = n1 - 1;
   constexpr int NP = nr * (nr + 1) / 2;
-  __shared__ double Ks[nr * nr], rhs[nr], invd[nr];
+  __shared__ double Ks[nr * nr], rhs[nr], invd[nr], rpart[6 * nr];
   __shared__ double qs[3 * n], Qs[3 * nq];
   __shared__ double s_a[3][3], s_det, s_g[6];
   __shared__ int s_bad;
@@ -207,10 +207,11 @@ __global__ void __launch_bounds__(NT) postprocess_kernel(
       for (int j = 0; j < 3; ++j) s_a[i][j] = g.a[i][j];
     s_det = g.det;
     const int pr[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    const double idet = 1.0 / g.det;
     for (int c = 0; c < 6; ++c) {
       double s = 0.0;
       for (int st = 0; st < 3; ++st) s += g.a[st][pr[c][0]] * g.a[st][pr[c][1]];
-      s_g[c] = s / g.det;
+      s_g[c] = s * idet;
     }
     s_bad = 0;
   }
@@ -244,29 +245,61 @@ __global__ void __launch_bounds__(NT) postprocess_kernel(
     Ks[j * nr + i] = s;
   }
   __syncthreads();
-  for (int i = tid; i < nr; i += NT) {
+  // right-hand side: the (h, i) sums split in two halves of the nodes so that whole warps
+  // share the work (GB300's FP64 pipe charges a warp instruction whatever its active lanes)
+  constexpr int NPART = 6 * nr;
+  constexpr int half = (nq + 1) / 2;
+  for (int t = tid; t < NPART; t += NT) {
+    const int hh = t / (2 * nr), rem = t - hh * 2 * nr, part = rem / nr, i = rem - part * nr;
+    const int p0 = part * half, p1 = part ? nq : half;
     double s = 0.0;
-    for (int h = 0; h < 3; ++h)
-      for (int p = 0; p < nq; ++p) s = fma(Qs[h * nq + p], __ldg(G1 + (h * nq + p) * n1 + i + 1), s);
-    rhs[i] = -s / 6.0;
+    for (int p = p0; p < p1; ++p) s = fma(Qs[hh * nq + p], __ldg(G1 + (hh * nq + p) * n1 + i + 1), s);
+    rpart[t] = s;
   }
   __syncthreads();
+  for (int i = tid; i < nr; i += NT) {
+    double s = 0.0;
+    for (int hh = 0; hh < 3; ++hh) s += rpart[hh * 2 * nr + i] + rpart[hh * 2 * nr + nr + i];
+    rhs[i] = s * (-1.0 / 6.0);
+  }
+  // Cholesky of the reduced stiffness, right-looking, the trailing updates spread over the CTA
+  for (int j = 0; j < nr; ++j) {
+    if (tid == 0) {
+      // only 1 / L_jj is used below: one reciprocal square root instead of a root and a divide
+      // (both run on the FP64 pipe, serially, once per column)
+      const double dj = Ks[j * nr + j];
+      if (!(dj > 0.0)) s_bad = 1;
+      invd[j] = rsqrt(dj > 0.0 ? dj : 1.0);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nr; i += NT) Ks[i * nr + j] *= invd[j];
+    __syncthreads();
+    const int mt = nr - j - 1;  // trailing block (lower triangle incl. diagonal): mt (mt + 1) / 2
+    for (int t = tid; t < mt * (mt + 1) / 2; t += NT) {
+      int a = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while (a * (a + 1) / 2 > t) --a;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int b = t - a * (a + 1) / 2;  // b <= a
+      const int i = j + 1 + a, k = j + 1 + b;
+      Ks[i * nr + k] = fma(-Ks[i * nr + j], Ks[k * nr + j], Ks[i * nr + k]);
+    }
+    __syncthreads();
+  }
+  // L y = rhs and L^T x = y by one warp, column-oriented so that every lane has work
   if (warp == 0) {
-    bool ok = warp_cholesky<nr>(Ks, invd, lane);
-    if (!ok && lane == 0) s_bad = 1;
-    __syncwarp();
-    // L y = rhs, L^T x = y, in shared memory (one lane; nr <= 55)
-    if (lane == 0) {
-      for (int i = 0; i < nr; ++i) {
-        double s = rhs[i];
-        for (int l = 0; l < i; ++l) s = fma(-Ks[i * nr + l], rhs[l], s);
-        rhs[i] = s * invd[i];
-      }
-      for (int i = nr - 1; i >= 0; --i) {
-        double s = rhs[i];
-        for (int l = i + 1; l < nr; ++l) s = fma(-Ks[l * nr + i], rhs[l], s);
-        rhs[i] = s * invd[i];
-      }
+    for (int i = 0; i < nr; ++i) {
+      const double yi = rhs[i] * invd[i];
+      __syncwarp();
+      if (lane == 0) rhs[i] = yi;
+      for (int l = i + 1 + lane; l < nr; l += 32) rhs[l] = fma(-Ks[l * nr + i], yi, rhs[l]);
+      __syncwarp();
+    }
+    for (int i = nr - 1; i >= 0; --i) {
+      const double xi = rhs[i] * invd[i];
+      __syncwarp();
+      if (lane == 0) rhs[i] = xi;
+      for (int l = lane; l < i; l += 32) rhs[l] = fma(-Ks[i * nr + l], xi, rhs[l]);
+      __syncwarp();
     }
   }
   __syncthreads();
