@@ -67,9 +67,8 @@ def flops_per_element_k1(k):
     f += MP * (2 * n + 7)           # (n.n) V^T V + tauDD
     f += chol                       # L_s L_s^T = S_u
     f += n * m * (2 * n + 1)        # G
-    f += (m + 1) * n * n + m * n * n + 3 * n * n * n  # H|h, Y, MC
+    f += (m + 1) * n * n            # H|h = L_s^-1 [G^T|f]
     f += MP * (2 * n + 1) + 2 * m * n  # C -= H^T H, C_f
-    f += (m + 1) * n * n            # R_u | r_u
     return f
 
 
@@ -79,7 +78,7 @@ def k1_bytes_per_element(k):
     n = (k + 1) * (k + 2) * (k + 3) // 6
     m = 2 * (k + 1) * (k + 2)
     nq = (k + 2) ** 3
-    rec = n * (m + 1) + n * m + 3 * n * n + 12
+    rec = n * (m + 1) + n * m + 3 * n * n + n * (n + 1) + 12  # [H|h], V, W_*, U_s, U_M, normals
     return 8 * (3 * nq + 12) + 4 * 4 + 8 * (m * m + m + rec)
 
 

@@ -12,9 +12,10 @@
 //   L_s L_s^T = S_u;  H = L_s^-1 G^T;  h = L_s^-1 f
 //   C^K = (n_l . n_l') o (V^T V) - H^T H + tauDD   (eq. 5.5)
 //   C_f^K = H^T h                                 (eq. 5.6)
-// and stores the recovery operators of eq. 5.3:
-//   u = R_u u_dK + r_u with [R_u | r_u] = L_s^-T [H | h];
-//   q_* = MC_* u - Y (n_* o u_dK) with MC_* = L^-T W_* = M^-1 C_*^T, Y = L^-T V = M^-1 E^T.
+// and stores the factored recovery operators of eq. 5.3, which K2 applies with two
+// triangular solves per element (one right-hand side each instead of m + 1 + m + 3n here):
+//   u = L_s^-T (H u_dK + h);  q_* = L^-T (W_* u - V (n_* o u_dK))
+//   (= M^-1 (C_*^T u - E^T (n_* o u_dK))).
 //
 // Convection (CONV = true; reading of Section 9: div(q + beta u) + c u = f, flux
 // q.nu + (beta.nu) u_hat + tau (u - u_hat)) adds to the same elimination
@@ -25,7 +26,7 @@
 //   parametrisation of eq. 4.1, beta given at the element's face nodes);
 //   G_col = G - alphaDP;  S_u = L U;  H_col = L^-1 G_col^T,  H_row = U^-T G^T;
 //   C^K = (n_l . n_l') o (V^T V) - H_row^T H_col + tauDD - alphaDD,  C_f = H_row^T L^-1 f;
-//   [R_u | r_u] = U^-1 [H_col | L^-1 f].
+//   u = U^-1 (H_col u_dK + L^-1 f).
 #include "device_common.cuh"
 #include "hdg_internal.h"
 
@@ -51,10 +52,10 @@ struct AsmSmem {
   static constexpr int o_kw = 0, o_cw = o_kw + nq, o_fw = o_cw + nq;
   static constexpr int o_M = o_fw + nq;          // n*n   M -> L
   static constexpr int o_S = o_M + n * n;        // n*n   S_u -> L_s
-  static constexpr int o_W = o_S + n * n;        // 3 n n W_*[l][c] -> MC_*
-  static constexpr int o_V = o_W + 3 * n * n;    // n*m   V[l][r] -> Y
+  static constexpr int o_W = o_S + n * n;        // 3 n n W_*[l][c]
+  static constexpr int o_V = o_W + 3 * n * n;    // n*m   V[l][r]
   static constexpr int o_Wt = o_V + n * m;       // 4 n n (sum_* n_{l*} W_*)[l'][j]
-  static constexpr int o_G = o_Wt + 4 * n * n;   // n*(m+1) G^T | f -> H | h -> R_u | r_u
+  static constexpr int o_G = o_Wt + 4 * n * n;   // n*(m+1) G^T | f -> H | h
   static constexpr int o_C = o_G + n * (m + 1);  // m*m
   // convection: H_row^T [n][m] (first alphaDP^T, then G^T, then H_row), 3 x nq reference
   // convection weights, 4 x nf face weights varpi (beta . n_l), alphaDD [4][d2][d2]
@@ -291,9 +292,9 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
   }
   __syncthreads();
 
-  // [H | h] = L_s^-1 [G^T | f];  Y = L^-T V;  MC_* = L^-T W_*
-  // (convection: [H_col | h] = L^-1 [G_col^T | f] and H_row = U^-T G^T)
-  constexpr int NTRI = (m + 1) + m + 3 * n + (CONV ? m : 0);
+  // [H | h] = L_s^-1 [G^T | f]  (convection: [H_col | h] = L^-1 [G_col^T | f] and H_row = U^-T G^T);
+  // the back substitutions of the recovery are left to K2
+  constexpr int NTRI = (m + 1) + (CONV ? m : 0);
   for (int t = tid; t < NTRI; t += NT) {
     double x[n];
     if (t < m + 1) {
@@ -302,29 +303,13 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
       if constexpr (CONV) fwd_subst_unit<n>(Ss, x); else fwd_subst<n>(Ss, invdS, x);
 #pragma unroll
       for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
-    } else if (t >= 2 * m + 1 + 3 * n) {
-      const int col = t - (2 * m + 1 + 3 * n);
+    } else {
+      const int col = t - (m + 1);
 #pragma unroll
       for (int l = 0; l < n; ++l) x[l] = Hr[l * m + col];
       fwd_subst_Ut<n>(Ss, invdS, x);
 #pragma unroll
       for (int l = 0; l < n; ++l) Hr[l * m + col] = x[l];
-    } else if (t < 2 * m + 1) {
-      const int col = t - (m + 1);
-#pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = V[l * m + col];
-      bwd_subst<n>(Ms, invdM, x);
-#pragma unroll
-      for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
-    } else {
-      const int tt = t - (2 * m + 1);
-      double* base = W + (tt / n) * n * n;
-      const int col = tt % n;
-#pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = base[l * n + col];
-      bwd_subst<n>(Ms, invdM, x);
-#pragma unroll
-      for (int l = 0; l < n; ++l) base[l * n + col] = x[l];
     }
   }
   __syncthreads();
@@ -358,15 +343,6 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
   }
   __syncthreads();
 
-  // [R_u | r_u] = L_s^-T [H | h];  write C^K
-  for (int t = tid; t < m + 1; t += NT) {
-    double x[n];
-#pragma unroll
-    for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
-    if constexpr (CONV) bwd_subst_U<n>(Ss, invdS, x); else bwd_subst<n>(Ss, invdS, x);
-#pragma unroll
-    for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
-  }
   // C^K row-major, [K][r][s] with r = l d2 + a: the row block of local face l is contiguous
   // and each row is one unit-stride array, read by the trace operator with 16-byte loads
   double* Cout = A.C + Ke * (int64_t)(m * m);
@@ -374,7 +350,9 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
   __syncthreads();
 
   // recovery record, column-major so that the recovery kernel reads it with unit stride:
-  // [R_u | r_u]^T [m+1][n], Y^T [m][n], MC_*^T [3][n][n], normals [4][3]
+  // [H | h]^T [m+1][n], V^T [m][n], W_*^T [3][n][n], U_s and U_M packed by columns (column i:
+  // U_0i .. U_(i-1)i, then 1/U_ii; U_s = L_s^T, or the U of the LU with convection; U_M = L^T),
+  // normals [4][3]
   double* R = A.rec + Ke * (int64_t)D::rec;
   for (int t = tid; t < n * (m + 1); t += NT) {
     const int r = t / n, i = t - r * n;
@@ -391,6 +369,15 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
     R[t] = W[st * n * n + l * n + c];
   }
   R += 3 * n * n;
+  for (int t = tid; t < n * n; t += NT) {
+    const int i = t / n, l = t - i * n;  // U_li, l <= i
+    if (l <= i) {
+      const double us = (l == i) ? invdS[i] : (CONV ? Ss[l * n + i] : Ss[i * n + l]);
+      R[i * (i + 1) / 2 + l] = us;
+      R[D::tri + i * (i + 1) / 2 + l] = (l == i) ? invdM[i] : Ms[i * n + l];
+    }
+  }
+  R += 2 * D::tri;
   if (tid < 12) R[tid] = s_nrm[tid / 3][tid % 3];
   if (tid == 0) {
     if (s_bad) atomicAdd(A.status + 0, 1);

@@ -8,7 +8,7 @@
 //   L L^T = M_{kappa^-1};  W_* = L^-1 C_*^T;  V = L^-1 E^T;  S_u = M_c + tauPP + sum W^T W;
 //   G = diag(T) E + sum_* diag(n_*) V^T W_*;  L_s L_s^T = S_u;  [H | h] = L_s^-1 [G^T | f];
 //   C^K = (n_l . n_l') o (V^T V) - H^T H + tauDD;  C_f^K = H^T h;
-//   recovery: [R_u | r_u] = L_s^-T [H | h],  Y = L^-T V,  MC_* = L^-T W_*.
+//   recovery record: [H | h], V, W_* and the factors L_s, L (K2 does the back substitutions).
 #include <cstdlib>
 
 #include "device_common.cuh"
@@ -150,17 +150,6 @@ __device__ __forceinline__ void fwd_subst_df(const df* __restrict__ L, const df*
     dacc s = dacc_from(x[l]);
 #pragma unroll
     for (int i = 0; i < l; ++i) dacc_msub(s, L[l * N + i], x[i]);
-    x[l] = df_mul(dacc_result(s), invd[l]);
-  }
-}
-
-template <int N>
-__device__ __forceinline__ void bwd_subst_df(const df* __restrict__ L, const df* invd, df* x) {
-#pragma unroll
-  for (int l = N - 1; l >= 0; --l) {
-    dacc s = dacc_from(x[l]);
-#pragma unroll
-    for (int i = l + 1; i < N; ++i) dacc_msub(s, L[i * N + l], x[i]);
     x[l] = df_mul(dacc_result(s), invd[l]);
   }
 }
@@ -352,28 +341,42 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   __syncthreads();
 
-  for (int t = tid; t < (m + 1) + 3 * n; t += NT) {
+  // [H | h] = L_s^-1 [G^T | f] by the first m + 1 threads (the back substitutions of the
+  // recovery are left to K2); meanwhile the others write the parts of the recovery record
+  // that are already final: V^T, W_*^T, U_s and U_M packed by columns (column i: U_0i ..
+  // U_(i-1)i, then 1/U_ii, with U = L^T), the normals.  Column-major blocks, so that the
+  // recovery kernel reads them with unit stride.
+  double* R = A.rec + Ke * (int64_t)D::rec;
+  if (tid < m + 1) {
     df x[n];
-    if (t < m + 1) {
 #pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
-      fwd_subst_df<n>(Ss, invdS, x);
+    for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + tid];
+    fwd_subst_df<n>(Ss, invdS, x);
 #pragma unroll
-      for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
-    } else {
-      const int tt = t - (m + 1);
-      df* base = W + (tt / n) * n * n;
-      const int col = tt % n;
-#pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = base[l * n + col];
-      bwd_subst_df<n>(Ms, invdM, x);
-#pragma unroll
-      for (int l = 0; l < n; ++l) base[l * n + col] = x[l];
+    for (int l = 0; l < n; ++l) Gt[l * (m + 1) + tid] = x[l];
+  } else {
+    constexpr int o_V = n * (m + 1), o_W = o_V + n * m, o_U = o_W + 3 * n * n;
+    for (int t = tid - (m + 1); t < n * m; t += NT - (m + 1)) {
+      const int r = t / n, l = t - r * n;
+      R[o_V + t] = df_to_double(V[l * m + r]);
     }
+    for (int t = tid - (m + 1); t < 3 * n * n; t += NT - (m + 1)) {
+      const int st = t / (n * n), rem = t - st * n * n, c = rem / n, l = rem - c * n;
+      R[o_W + t] = df_to_double(W[st * n * n + l * n + c]);
+    }
+    for (int t = tid - (m + 1); t < n * n; t += NT - (m + 1)) {
+      const int i = t / n, l = t - i * n;
+      if (l <= i) {
+        R[o_U + i * (i + 1) / 2 + l] = df_to_double(l == i ? invdS[i] : Ss[t]);
+        R[o_U + D::tri + i * (i + 1) / 2 + l] = df_to_double(l == i ? invdM[i] : Ms[t]);
+      }
+    }
+    for (int t = tid - (m + 1); t < 12; t += NT - (m + 1))
+      R[o_U + 2 * D::tri + t] = df_to_double(s_nrm[t / 3][t % 3]);
   }
   __syncthreads();
 
-  // C = (n_l . n_l') o V^T V + tauDD - H^T H  (V = L^-1 E^T still; H = rows of G^T)
+  // C = (n_l . n_l') o V^T V + tauDD - H^T H  (V = L^-1 E^T; H = rows of G^T)
   for (int t = tid; t < MP; t += NT) {
     const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
     const int fr = r / d2, fs = s / d2;
@@ -395,47 +398,14 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     for (int j = 0; j < n; ++j) dacc_mac(s, Gt[j * (m + 1) + r], Gt[j * (m + 1) + m]);
     A.Cf[Ke * m + r] = df_to_double(dacc_result(s));
   }
-  __syncthreads();
-
-  for (int t = tid; t < (m + 1) + m; t += NT) {
-    df x[n];
-    if (t < m + 1) {
-#pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + t];
-      bwd_subst_df<n>(Ss, invdS, x);
-#pragma unroll
-      for (int l = 0; l < n; ++l) Gt[l * (m + 1) + t] = x[l];
-    } else {  // Y = M^-1 E^T = L^-T V for the recovery record
-      const int col = t - (m + 1);
-#pragma unroll
-      for (int l = 0; l < n; ++l) x[l] = V[l * m + col];
-      bwd_subst_df<n>(Ms, invdM, x);
-#pragma unroll
-      for (int l = 0; l < n; ++l) V[l * m + col] = x[l];
-    }
-  }
-  double* Cout = A.C + Ke * (int64_t)(m * m);  // row-major, as in assemble.cu
-  for (int t = tid; t < m * m; t += NT) Cout[t] = df_to_double(Cs[t]);
-  __syncthreads();
-
-  // recovery record, column-major (as in assemble.cu)
-  double* R = A.rec + Ke * (int64_t)D::rec;
-  for (int t = tid; t < n * (m + 1); t += NT) {
+  for (int t = tid; t < n * (m + 1); t += NT) {  // [H | h]^T
     const int r = t / n, i = t - r * n;
     R[t] = df_to_double(Gt[i * (m + 1) + r]);
   }
-  R += n * (m + 1);
-  for (int t = tid; t < n * m; t += NT) {
-    const int r = t / n, l = t - r * n;
-    R[t] = df_to_double(V[l * m + r]);
-  }
-  R += n * m;
-  for (int t = tid; t < 3 * n * n; t += NT) {
-    const int st = t / (n * n), rem = t - st * n * n, c = rem / n, l = rem - c * n;
-    R[t] = df_to_double(W[st * n * n + l * n + c]);
-  }
-  R += 3 * n * n;
-  if (tid < 12) R[tid] = df_to_double(s_nrm[tid / 3][tid % 3]);
+  __syncthreads();
+
+  double* Cout = A.C + Ke * (int64_t)(m * m);  // row-major, as in assemble.cu
+  for (int t = tid; t < m * m; t += NT) Cout[t] = df_to_double(Cs[t]);
   if (tid == 0) {
     if (s_bad) atomicAdd(A.status + 0, 1);
     if (s_coef) atomicAdd(A.status + 1, 1);

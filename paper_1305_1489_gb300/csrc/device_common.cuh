@@ -15,8 +15,11 @@ struct Dims {
   static constexpr int nq = (K + 2) * (K + 2) * (K + 2);     // volume nodes
   static constexpr int nf = (K + 2) * (K + 2);               // face nodes
   static constexpr int n1 = (K + 2) * (K + 3) * (K + 4) / 6; // dim P_{k+1}(K)
-  // per-element recovery record, column-major: [R_u|r_u]^T [m+1][n] | Y^T [m][n] | MC^T [3][n][n] | normals [12]
-  static constexpr int rec = n * (m + 1) + n * m + 3 * n * n + 12;
+  // per-element recovery record (eq. 5.3 through the factors of K1), column-major blocks:
+  // [H|h]^T [m+1][n] | V^T [m][n] | W_*^T [3][n][n] | U_s [n(n+1)/2] | U_M [n(n+1)/2] | normals [12]
+  // (U packed by columns, column i holding U_0i .. U_(i-1)i and then 1/U_ii)
+  static constexpr int tri = n * (n + 1) / 2;
+  static constexpr int rec = n * (m + 1) + n * m + 3 * n * n + 2 * tri + 12;
 };
 
 // Launch shape of K1 (one element per CTA): threads per CTA and the number of CTAs each SM
@@ -182,29 +185,7 @@ __device__ __forceinline__ void fwd_subst_Ut(const double* __restrict__ LU, cons
   }
 }
 
-// Backward substitution U x = b with the factor of warp_lu.
-template <int N>
-__device__ __forceinline__ void bwd_subst_U(const double* __restrict__ LU, const double* invd, double* x) {
-#pragma unroll
-  for (int l = N - 1; l >= 0; --l) {
-    double s = x[l];
-#pragma unroll
-    for (int i = l + 1; i < N; ++i) s = fma(-LU[l * N + i], x[i], s);
-    x[l] = s * invd[l];
-  }
-}
 
-// Backward substitution L^T x = b for one column in registers.
-template <int N>
-__device__ __forceinline__ void bwd_subst(const double* __restrict__ L, const double* invd, double* x) {
-#pragma unroll
-  for (int l = N - 1; l >= 0; --l) {
-    double s = x[l];
-#pragma unroll
-    for (int i = l + 1; i < N; ++i) s = fma(-L[i * N + l], x[i], s);
-    x[l] = s * invd[l];
-  }
-}
 
 // Deterministic grid reduction: every block contributes one value per slot (nslots <= 4);
 // the last block to arrive sums the per-block partials in block order and calls fin(sums).

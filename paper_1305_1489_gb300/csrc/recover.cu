@@ -108,10 +108,39 @@ cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst) {
 }
 
 // ----------------------------------------------------------------------- recovery
-// u = R_u u_dK + r_u;  q_* = MC_* u - Y (n_* o u_dK)   (eq. 5.3 through the factors of K1).
-// One warp per element; the column-major record makes every column read a unit-stride
-// access across the lanes, and all columns are issued before they are consumed.
+// u = U_s^-1 (H u_dK + h);  q_* = U_M^-1 (W_* u - V (n_* o u_dK))   (eq. 5.3 through the
+// factors of K1: S_u = U_s^T U_s, or L U_s with convection, and M_{kappa^-1} = U_M^T U_M; H, h,
+// V, W_* are the forward-substituted blocks).  One warp per element; the record is
+// column-major so that every column read is unit-stride across the lanes, and the two
+// upper-triangular solves run by columns from the last unknown (lane l owns rows l, l + 32).
 constexpr int kRecWarps = 4;
+
+// U x = b in place for NV right-hand sides; x[a][v] is row lane + 32 a of right-hand side v.
+// U packed by columns with the inverse diagonal last in each column.
+template <int N, int NV>
+__device__ __forceinline__ void upper_solve(const double* __restrict__ U, double (&x)[(N + 31) / 32][NV], int lane) {
+  constexpr int NA = (N + 31) / 32;
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    const double* col = U + i * (i + 1) / 2;
+    const double inv = __ldg(col + i);
+    double xi[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xi[v] = __shfl_sync(0xffffffffu, x[i >> 5][v], i & 31) * inv;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int l = lane + 32 * a;
+      if (l < i) {
+        const double uli = __ldg(col + l);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) x[a][v] = fma(-uli, xi[v], x[a][v]);
+      } else if (l == i) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) x[a][v] = xi[v];
+      }
+    }
+  }
+}
 
 template <int K>
 __global__ void __launch_bounds__(32 * kRecWarps) recover_kernel(const double* __restrict__ rec,
@@ -119,51 +148,89 @@ __global__ void __launch_bounds__(32 * kRecWarps) recover_kernel(const double* _
                                                                 const double* __restrict__ uhat, int64_t nelt,
                                                                 double* __restrict__ q, double* __restrict__ u) {
   using D = Dims<K>;
-  constexpr int n = D::n, m = D::m, d2 = D::d2;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, NA = (n + 31) / 32;
   __shared__ double suh[kRecWarps][m], su[kRecWarps][n];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t Ke = (int64_t)blockIdx.x * kRecWarps + warp;
-  if (Ke >= nelt) return;
-  const double* R = rec + Ke * (int64_t)D::rec;
-  const double* YT = R + n * (m + 1);
-  const double* MCT = YT + n * m;
-  const double* nrm = MCT + 3 * n * n;
+  if (Ke >= nelt) return;  // a whole warp leaves together
+  const double* HT = rec + Ke * (int64_t)D::rec;
+  const double* VT = HT + n * (m + 1);
+  const double* WT = VT + n * m;
+  const double* Us = WT + 3 * n * n;
+  const double* UM = Us + D::tri;
+  const double* nrm = UM + D::tri;
   for (int t = lane; t < m; t += 32) suh[warp][t] = __ldg(uhat + (int64_t)__ldg(fbe + Ke * 4 + t / d2) * d2 + (t % d2));
   __syncwarp();
-  for (int i = lane; i < n; i += 32) {
-    double s0 = __ldg(R + m * n + i), s1 = 0.0;
+  double x[NA][1];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int i = lane + 32 * a;
+    double s0 = 0.0, s1 = 0.0;
+    if (i < n) {
+      s0 = __ldg(HT + m * n + i);
 #pragma unroll 8
-    for (int r = 0; r < m; r += 2) {
-      s0 = fma(__ldg(R + r * n + i), suh[warp][r], s0);
-      if (r + 1 < m) s1 = fma(__ldg(R + (r + 1) * n + i), suh[warp][r + 1], s1);
+      for (int r = 0; r < m; r += 2) {
+        s0 = fma(__ldg(HT + r * n + i), suh[warp][r], s0);
+        if (r + 1 < m) s1 = fma(__ldg(HT + (r + 1) * n + i), suh[warp][r + 1], s1);
+      }
     }
-    su[warp][i] = s0 + s1;
-    u[Ke * n + i] = s0 + s1;
+    x[a][0] = s0 + s1;
+  }
+  upper_solve<n, 1>(Us, x, lane);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int i = lane + 32 * a;
+    if (i < n) {
+      su[warp][i] = x[a][0];
+      u[Ke * n + i] = x[a][0];
+    }
   }
   __syncwarp();
   double nv[12];
 #pragma unroll
   for (int t = 0; t < 12; ++t) nv[t] = __ldg(nrm + t);
-  for (int l = lane; l < n; l += 32) {
+  double z[NA][3];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int l = lane + 32 * a;
     double s[3] = {0.0, 0.0, 0.0};
+    if (l < n) {
 #pragma unroll 4
-    for (int c = 0; c < n; ++c) {
-      const double uc = su[warp][c];
-      s[0] = fma(__ldg(MCT + (0 * n + c) * n + l), uc, s[0]);
-      s[1] = fma(__ldg(MCT + (1 * n + c) * n + l), uc, s[1]);
-      s[2] = fma(__ldg(MCT + (2 * n + c) * n + l), uc, s[2]);
+      for (int c = 0; c < n; ++c) {
+        const double uc = su[warp][c];
+        s[0] = fma(__ldg(WT + (0 * n + c) * n + l), uc, s[0]);
+        s[1] = fma(__ldg(WT + (1 * n + c) * n + l), uc, s[1]);
+        s[2] = fma(__ldg(WT + (2 * n + c) * n + l), uc, s[2]);
+      }
+      // V (n_* o u_dK) = sum_l n_{l*} V_l u_dK,l: one product per face, then the normals
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        double w0 = 0.0, w1 = 0.0;
+#pragma unroll
+        for (int a2 = 0; a2 < d2; a2 += 2) {
+          const int r = fl * d2 + a2;
+          w0 = fma(__ldg(VT + r * n + l), suh[warp][r], w0);
+          if (a2 + 1 < d2) w1 = fma(__ldg(VT + (r + 1) * n + l), suh[warp][r + 1], w1);
+        }
+        const double w = w0 + w1;
+        s[0] = fma(-w, nv[3 * fl + 0], s[0]);
+        s[1] = fma(-w, nv[3 * fl + 1], s[1]);
+        s[2] = fma(-w, nv[3 * fl + 2], s[2]);
+      }
     }
-#pragma unroll 4
-    for (int r = 0; r < m; ++r) {
-      const double yu = __ldg(YT + r * n + l) * suh[warp][r];
-      const int fl = r / d2;
-      s[0] = fma(-yu, nv[3 * fl + 0], s[0]);
-      s[1] = fma(-yu, nv[3 * fl + 1], s[1]);
-      s[2] = fma(-yu, nv[3 * fl + 2], s[2]);
+    z[a][0] = s[0];
+    z[a][1] = s[1];
+    z[a][2] = s[2];
+  }
+  upper_solve<n, 3>(UM, z, lane);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int l = lane + 32 * a;
+    if (l < n) {
+      q[(Ke * 3 + 0) * n + l] = z[a][0];
+      q[(Ke * 3 + 1) * n + l] = z[a][1];
+      q[(Ke * 3 + 2) * n + l] = z[a][2];
     }
-    q[(Ke * 3 + 0) * n + l] = s[0];
-    q[(Ke * 3 + 1) * n + l] = s[1];
-    q[(Ke * 3 + 2) * n + l] = s[2];
   }
 }
 
