@@ -399,6 +399,7 @@ static cudaError_t launch_k(hdg_mesh* M, const AsmArgs& a) {
 }
 
 cudaError_t launch_assemble(hdg_mesh* M) {
+  M->rec_df = false;
   AsmArgs a;
   a.vx = M->d_vx;
   a.perm = M->d_perm;

@@ -345,8 +345,9 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   // recovery are left to K2); meanwhile the others write the parts of the recovery record
   // that are already final: V^T, W_*^T, U_s and U_M packed by columns (column i: U_0i ..
   // U_(i-1)i, then 1/U_ii, with U = L^T), the normals.  Column-major blocks, so that the
-  // recovery kernel reads them with unit stride.
-  double* R = A.rec + Ke * (int64_t)D::rec;
+  // recovery kernel reads them with unit stride; every entry a double-float pair (8 bytes,
+  // the layout of the FP64 record), read by the double-float recovery kernel.
+  df* R = reinterpret_cast<df*>(A.rec) + Ke * (int64_t)D::rec;
   if (tid < m + 1) {
     df x[n];
 #pragma unroll
@@ -358,21 +359,21 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     constexpr int o_V = n * (m + 1), o_W = o_V + n * m, o_U = o_W + 3 * n * n;
     for (int t = tid - (m + 1); t < n * m; t += NT - (m + 1)) {
       const int r = t / n, l = t - r * n;
-      R[o_V + t] = df_to_double(V[l * m + r]);
+      R[o_V + t] = V[l * m + r];
     }
     for (int t = tid - (m + 1); t < 3 * n * n; t += NT - (m + 1)) {
       const int st = t / (n * n), rem = t - st * n * n, c = rem / n, l = rem - c * n;
-      R[o_W + t] = df_to_double(W[st * n * n + l * n + c]);
+      R[o_W + t] = W[st * n * n + l * n + c];
     }
     for (int t = tid - (m + 1); t < n * n; t += NT - (m + 1)) {
       const int i = t / n, l = t - i * n;
       if (l <= i) {
-        R[o_U + i * (i + 1) / 2 + l] = df_to_double(l == i ? invdS[i] : Ss[t]);
-        R[o_U + D::tri + i * (i + 1) / 2 + l] = df_to_double(l == i ? invdM[i] : Ms[t]);
+        R[o_U + i * (i + 1) / 2 + l] = (l == i) ? invdS[i] : Ss[t];
+        R[o_U + D::tri + i * (i + 1) / 2 + l] = (l == i) ? invdM[i] : Ms[t];
       }
     }
     for (int t = tid - (m + 1); t < 12; t += NT - (m + 1))
-      R[o_U + 2 * D::tri + t] = df_to_double(s_nrm[t / 3][t % 3]);
+      R[o_U + 2 * D::tri + t] = s_nrm[t / 3][t % 3];
   }
   __syncthreads();
 
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   for (int t = tid; t < n * (m + 1); t += NT) {  // [H | h]^T
     const int r = t / n, i = t - r * n;
-    R[t] = df_to_double(Gt[i * (m + 1) + r]);
+    R[t] = Gt[i * (m + 1) + r];
   }
   __syncthreads();
 
@@ -447,6 +448,7 @@ int k1_threads(int k, int variant) {
 }
 
 cudaError_t launch_assemble_df(hdg_mesh* M) {
+  M->rec_df = true;
   AsmDfArgs a;
   a.vx = M->d_vx;
   a.perm = M->d_perm;

@@ -91,6 +91,7 @@ struct hdg_mesh {
   double* d_Cf = nullptr;   // [nelt][m]    C_f^K (eq. 5.6)
   double* d_rec = nullptr;  // [nelt][rec_stride] recovery operators (eq. 5.3)
   int64_t rec_stride = 0;
+  bool rec_df = false;      // the record holds double-float pairs (written by the double-float K1)
   int32_t* d_status = nullptr;  // [4] error counters written by kernels
 
   // trace-solve workspace (library-owned, allocated on first solve)

@@ -1,6 +1,7 @@
 // K2 local recovery (eq. 5.3), K5 superconvergent postprocess (eq. 9.11), and the
 // quadrature-node helper (eq. 3.4, 6.2).  FP64.
 #include "device_common.cuh"
+#include "device_df.cuh"
 #include "hdg_internal.h"
 
 namespace hdg {
@@ -234,16 +235,142 @@ __global__ void __launch_bounds__(32 * kRecWarps) recover_kernel(const double* _
   }
 }
 
+// The same recovery in double-float on the FP32 pipe, for the record of the double-float
+// K1 (entries stored as (hi, lo) float pairs): the accumulations are compensated (dacc), the
+// triangular solves keep every pending right-hand side as an unnormalised accumulator, and
+// u_dK and the results cross to and from FP64 once.
+__device__ __forceinline__ df ldg_df2(const df* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df_make(v.x, v.y);
+}
+
+__device__ __forceinline__ df shfl_df(df x, int src) {
+  return df_make(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
+}
+
+template <int N, int NV>
+__device__ __forceinline__ void upper_solve_df(const df* __restrict__ U, dacc (&x)[(N + 31) / 32][NV], int lane) {
+  constexpr int NA = (N + 31) / 32;
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    const df* col = U + i * (i + 1) / 2;
+    const df inv = ldg_df2(col + i);
+    df xi[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xi[v] = df_mul(shfl_df(dacc_result(x[i >> 5][v]), i & 31), inv);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int l = lane + 32 * a;
+      if (l < i) {
+        const df uli = ldg_df2(col + l);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dacc_msub(x[a][v], uli, xi[v]);
+      } else if (l == i) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) x[a][v] = dacc_from(xi[v]);
+      }
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(32 * kRecWarps) recover_df_kernel(const double* __restrict__ rec,
+                                                                   const int32_t* __restrict__ fbe,
+                                                                   const double* __restrict__ uhat, int64_t nelt,
+                                                                   double* __restrict__ q, double* __restrict__ u) {
+  using D = Dims<K>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, NA = (n + 31) / 32;
+  __shared__ df suh[kRecWarps][m], su[kRecWarps][n];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t Ke = (int64_t)blockIdx.x * kRecWarps + warp;
+  if (Ke >= nelt) return;  // a whole warp leaves together
+  const df* HT = reinterpret_cast<const df*>(rec) + Ke * (int64_t)D::rec;
+  const df* VT = HT + n * (m + 1);
+  const df* WT = VT + n * m;
+  const df* Us = WT + 3 * n * n;
+  const df* UM = Us + D::tri;
+  const df* nrm = UM + D::tri;
+  for (int t = lane; t < m; t += 32)
+    suh[warp][t] = df_from_double(__ldg(uhat + (int64_t)__ldg(fbe + Ke * 4 + t / d2) * d2 + (t % d2)));
+  __syncwarp();
+  dacc x[NA][1];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int i = lane + 32 * a;
+    dacc s = dacc_zero();
+    if (i < n) {
+      s = dacc_from(ldg_df2(HT + m * n + i));
+#pragma unroll 8
+      for (int r = 0; r < m; ++r) dacc_mac(s, ldg_df2(HT + r * n + i), suh[warp][r]);
+    }
+    x[a][0] = s;
+  }
+  upper_solve_df<n, 1>(Us, x, lane);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int i = lane + 32 * a;
+    if (i < n) {
+      const df ui = dacc_result(x[a][0]);
+      su[warp][i] = ui;
+      u[Ke * n + i] = df_to_double(ui);
+    }
+  }
+  __syncwarp();
+  df nv[12];
+#pragma unroll
+  for (int t = 0; t < 12; ++t) nv[t] = ldg_df2(nrm + t);
+  dacc z[NA][3];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int l = lane + 32 * a;
+    z[a][0] = z[a][1] = z[a][2] = dacc_zero();
+    if (l < n) {
+#pragma unroll 4
+      for (int c = 0; c < n; ++c) {
+        const df uc = su[warp][c];
+        dacc_mac(z[a][0], ldg_df2(WT + (0 * n + c) * n + l), uc);
+        dacc_mac(z[a][1], ldg_df2(WT + (1 * n + c) * n + l), uc);
+        dacc_mac(z[a][2], ldg_df2(WT + (2 * n + c) * n + l), uc);
+      }
+      // V (n_* o u_dK) = sum_l n_{l*} V_l u_dK,l: one product per face, then the normals
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        dacc w = dacc_zero();
+#pragma unroll
+        for (int a2 = 0; a2 < d2; ++a2) dacc_mac(w, ldg_df2(VT + (fl * d2 + a2) * n + l), suh[warp][fl * d2 + a2]);
+        const df wv = dacc_result(w);
+        dacc_msub(z[a][0], nv[3 * fl + 0], wv);
+        dacc_msub(z[a][1], nv[3 * fl + 1], wv);
+        dacc_msub(z[a][2], nv[3 * fl + 2], wv);
+      }
+    }
+  }
+  upper_solve_df<n, 3>(UM, z, lane);
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const int l = lane + 32 * a;
+    if (l < n) {
+      q[(Ke * 3 + 0) * n + l] = df_to_double(dacc_result(z[a][0]));
+      q[(Ke * 3 + 1) * n + l] = df_to_double(dacc_result(z[a][1]));
+      q[(Ke * 3 + 2) * n + l] = df_to_double(dacc_result(z[a][2]));
+    }
+  }
+}
+
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
   const unsigned g = (unsigned)((M->nelt + kRecWarps - 1) / kRecWarps);
   const int nt = 32 * kRecWarps;
+#define HDG_REC(KK)                                                                                    \
+  if (M->rec_df) recover_df_kernel<KK><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); \
+  else recover_kernel<KK><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u)
   switch (M->k) {
-    case 1: recover_kernel<1><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
-    case 2: recover_kernel<2><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
-    case 3: recover_kernel<3><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
-    case 4: recover_kernel<4><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); break;
+    case 1: HDG_REC(1); break;
+    case 2: HDG_REC(2); break;
+    case 3: HDG_REC(3); break;
+    case 4: HDG_REC(4); break;
     default: return cudaErrorInvalidValue;
   }
+#undef HDG_REC
   M->launches++;
   return cudaGetLastError();
 }
