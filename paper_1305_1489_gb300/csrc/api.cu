@@ -63,7 +63,10 @@ static int upload_tables(hdg_mesh* M) {
       (rc = upload(&D.face_pts, T.face_pts)))
     return rc;
   if ((rc = upload(&D.P_df, split_df(T.P))) || (rc = upload(&D.Chat_df, split_df(T.Chat))) ||
-      (rc = upload(&D.S_df, split_df(T.S))) || (rc = upload(&D.E_df, split_df(T.E))))
+      (rc = upload(&D.S_df, split_df(T.S))) || (rc = upload(&D.E_df, split_df(T.E))) ||
+      (rc = upload(&D.sfAA_df, split_df(T.sfAA))) || (rc = upload(&D.sfBB_df, split_df(T.sfBB))) ||
+      (rc = upload(&D.sfCC_df, split_df(T.sfCC))) || (rc = upload(&D.sfp2to1, T.sfp2to1)) ||
+      (rc = upload(&D.sfp3to2, T.sfp3to2)))
     return rc;
   if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
       (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
@@ -73,13 +76,14 @@ static int upload_tables(hdg_mesh* M) {
 
 static void release(hdg_mesh* M) {
   coarse_free(M);
-  void* ptrs[] = {M->d_vx, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
+  void* ptrs[] = {M->d_vx, M->d_geo, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
                   M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
                   M->d_p32, M->d_q32, M->dt.P, M->dt.Pd, M->dt.Chat, M->dt.S, M->dt.E, M->dt.vol_w, M->dt.lam,
                   M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
                   M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
-                  M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj};
+                  M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj,
+                  M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
@@ -138,6 +142,8 @@ int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, in
     if (e == cudaSuccess) e = cudaMalloc(&M->d_Cf, sizeof(double) * nelt * m);
     if (e == cudaSuccess) e = cudaMalloc(&M->d_rec, sizeof(double) * nelt * M->rec_stride);
     if (e == cudaSuccess) e = cudaMalloc(&M->d_status, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_geo, sizeof(double) * nelt * kGeoStride);
+    if (e == cudaSuccess) e = launch_geometry(M);  // the mesh's element geometry, once
     if (e != cudaSuccess) rc = fail(HDG_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e));
   }
   if (rc) {

@@ -18,10 +18,12 @@
 namespace hdg {
 
 struct AsmDfArgs {
-  const double* vx;
+  const double* geo;
   const int32_t* perm;
   const double *kappa, *c, *f, *tau;
   const df *P, *Chat, *S, *E;  // double-float copies of the reference tables
+  const df *AA, *BB, *CC;      // sum-factorisation tables of the volume masses
+  const int16_t *p2to1, *p3to2;
   const double* w;
   const int16_t *pairs_n, *pairs_m;
   double *C, *Cf, *rec;
@@ -47,6 +49,12 @@ struct AsmDfSmem {
   static constexpr int o_Wt = o_C;
   static constexpr int WTF = (4 * n * n <= m * m) ? 4 : 2;  // faces of Wt held at once
   static_assert(3 * nq <= m * m, "kw, cw, fw must fit in the space of C");
+  // sum factorisation of the masses: T1 [(kw, cw) np1 + fw (k+1)][nn^2] over W and V, T2
+  // [(kw, cw) np2 + fw d2][nn] in C after kw, cw, fw
+  static constexpr int nn = K + 2, np1 = (K + 1) * (K + 2) / 2, np2 = D::d2 * (D::d2 + 1) / 2;
+  static constexpr int o_T1 = o_W, o_T2 = o_C + 3 * nq;
+  static_assert((2 * np1 + K + 1) * nn * nn <= 3 * n * n + n * m, "T1 must fit in the space of W and V");
+  static_assert(3 * nq + (2 * np2 + D::d2) * nn <= m * m, "T2 must fit in the space of C");
   static_assert(WTF * n * n <= m * m, "Wt must fit in the space of C");
   static constexpr int total = o_C + m * m;
   static constexpr size_t bytes = sizeof(df) * total;
@@ -186,20 +194,14 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   const int lane = tid & 31, warp = tid >> 5;
   const int64_t Ke = blockIdx.x;
 
+  // the element's geometry (formed once per mesh by geometry_kernel), one value per thread
+  if (tid < 25) s_geo[tid] = __ldg(A.geo + Ke * kGeoStride + tid);
+  if (tid == 25) s_vol = __ldg(A.geo + Ke * kGeoStride + 25);
+  if (tid < 4) s_perm[tid] = A.perm[Ke * 4 + tid] - 1;
   if (tid == 0) {
-    Geo g;
-    element_geometry(A.vx, A.nelt, Ke, g);
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) s_geo[3 * i + j] = g.a[i][j];
-    for (int l = 0; l < 4; ++l) {
-      for (int d = 0; d < 3; ++d) s_geo[9 + 3 * l + d] = g.nrm[l][d];
-      s_geo[21 + l] = g.area[l];
-    }
-    s_vol = g.vol;
     s_bad = 0;
     s_coef = 0;
   }
-  if (tid < 4) s_perm[tid] = A.perm[Ke * 4 + tid] - 1;
   __syncthreads();
 
   // the geometry in double-float, one value per thread (FP64 work off the single-thread path)
@@ -227,14 +229,57 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   __syncthreads();
 
-  for (int t = tid; t < NP; t += NT) {
+  // M_{kappa^-1}, M_c and the f^K column by sum factorisation over the conical nodes
+  // (i, j, l): sum_q g_q P_a P_b = sum_i CC_ab(i) sum_j BB(j) sum_l g AA(l).  f_a is the
+  // (0, a) entry of the same sum with g = fw, since P_0 = 1: its pairs are the first k + 1
+  // 1-D pairs, the first d2 2-D pairs and the first n 3-D pairs.
+  constexpr int nn = SM::nn, nn2 = nn * nn, np1 = SM::np1, np2 = SM::np2;
+  df* T1 = smd + SM::o_T1;  // [kw: np1 | cw: np1 | fw: k+1][nn2]
+  df* T2 = smd + SM::o_T2;  // [kw: np2 | cw: np2 | fw: d2][nn]
+  for (int t = tid; t < np1 * nn2; t += NT) {  // T1 = sum_l g A_pa A_pb
+    const int p1 = t / nn2, ij = t - p1 * nn2;
+    const bool wf = p1 <= K;
+    dacc s1 = dacc_zero(), s2 = dacc_zero(), s3 = dacc_zero();
+#pragma unroll
+    for (int l = 0; l < nn; ++l) {
+      const df a = ldg_df(A.AA + p1 * nn + l);
+      dacc_mac(s1, kw[ij * nn + l], a);
+      dacc_mac(s2, cw[ij * nn + l], a);
+      if (wf) dacc_mac(s3, fw[ij * nn + l], a);
+    }
+    T1[t] = dacc_result(s1);
+    T1[np1 * nn2 + t] = dacc_result(s2);
+    if (wf) T1[2 * np1 * nn2 + t] = dacc_result(s3);
+  }
+  __syncthreads();
+  for (int t = tid; t < np2 * nn; t += NT) {  // T2 = sum_j B_a2 B_b2 T1
+    const int p2 = t / nn, i = t - p2 * nn;
+    const bool wf = p2 < d2;
+    const df* t1 = T1 + A.p2to1[p2] * nn2 + i * nn;
+    dacc s1 = dacc_zero(), s2 = dacc_zero(), s3 = dacc_zero();
+#pragma unroll
+    for (int j = 0; j < nn; ++j) {
+      const df b = ldg_df(A.BB + p2 * nn + j);
+      dacc_mac(s1, t1[j], b);
+      dacc_mac(s2, t1[np1 * nn2 + j], b);
+      if (wf) dacc_mac(s3, t1[2 * np1 * nn2 + j], b);
+    }
+    T2[t] = dacc_result(s1);
+    T2[np2 * nn + t] = dacc_result(s2);
+    if (wf) T2[2 * np2 * nn + t] = dacc_result(s3);
+  }
+  __syncthreads();
+  for (int t = tid; t < NP; t += NT) {  // M_ab, S_ab = sum_i C_a C_b T2 (+ tauPP), f_b
     const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
-    dacc s1 = dacc_zero(), s2 = dacc_zero();
-#pragma unroll 5
-    for (int q = 0; q < nq; ++q) {
-      const df pp = df_mul(ldg_df(A.P + q * n + i), ldg_df(A.P + q * n + j));
-      dacc_mac(s1, kw[q], pp);
-      dacc_mac(s2, cw[q], pp);
+    const df* t2 = T2 + A.p3to2[t] * nn;
+    const bool wf = t < n;
+    dacc s1 = dacc_zero(), s2 = dacc_zero(), s3 = dacc_zero();
+#pragma unroll
+    for (int ii = 0; ii < nn; ++ii) {
+      const df c = ldg_df(A.CC + t * nn + ii);
+      dacc_mac(s1, t2[ii], c);
+      dacc_mac(s2, t2[np2 * nn + ii], c);
+      if (wf) dacc_mac(s3, t2[2 * np2 * nn + ii], c);
     }
 #pragma unroll
     for (int l = 0; l < 4; ++l) dacc_mac(s2, s_T[l], ldg_df(A.S + (l * n + i) * n + j));
@@ -243,12 +288,9 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     Ms[j * n + i] = v1;
     Ss[i * n + j] = v2;
     Ss[j * n + i] = v2;
+    if (wf) Gt[j * (m + 1) + m] = dacc_result(s3);  // pair (0, j)
   }
-  for (int i = tid; i < n; i += NT) {
-    dacc s = dacc_zero();
-    for (int q = 0; q < nq; ++q) dacc_mac(s, fw[q], ldg_df(A.P + q * n + i));
-    Gt[i * (m + 1) + m] = dacc_result(s);
-  }
+  // C_*^T from C_hat and the cofactors, V = E^T (both where T1 was)
   for (int t = tid; t < 3 * n * n; t += NT) {
     const int st = t / (n * n), rem = t - st * n * n, l = rem / n, cidx = rem - l * n;
     dacc s = dacc_zero();
@@ -447,10 +489,36 @@ int k1_threads(int k, int variant) {
   }
 }
 
+// Element geometry of the mesh, once (it depends on the vertices only): per element
+// [a (9, row-major) | normals (4 x 3) | areas (4) | vol], FP64.
+__global__ void geometry_kernel(const double* __restrict__ vx, int64_t nelt, double* __restrict__ geo) {
+  const int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nelt) return;
+  Geo g;
+  element_geometry(vx, nelt, K, g);
+  double* o = geo + K * kGeoStride;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) o[3 * i + j] = g.a[i][j];
+  for (int l = 0; l < 4; ++l) {
+    for (int d = 0; d < 3; ++d) o[9 + 3 * l + d] = g.nrm[l][d];
+    o[21 + l] = g.area[l];
+  }
+  o[25] = g.vol;
+  o[26] = g.det;
+  o[27] = 0.0;
+}
+
+cudaError_t launch_geometry(hdg_mesh* M) {
+  const unsigned nb = (unsigned)((M->nelt + 127) / 128);
+  geometry_kernel<<<nb, 128, 0, M->stream>>>(M->d_vx, M->nelt, M->d_geo);
+  M->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble_df(hdg_mesh* M) {
   M->rec_df = true;
   AsmDfArgs a;
-  a.vx = M->d_vx;
+  a.geo = M->d_geo;
   a.perm = M->d_perm;
   a.kappa = M->kappa;
   a.c = M->c;
@@ -460,6 +528,11 @@ cudaError_t launch_assemble_df(hdg_mesh* M) {
   a.Chat = reinterpret_cast<const df*>(M->dt.Chat_df);
   a.S = reinterpret_cast<const df*>(M->dt.S_df);
   a.E = reinterpret_cast<const df*>(M->dt.E_df);
+  a.AA = reinterpret_cast<const df*>(M->dt.sfAA_df);
+  a.BB = reinterpret_cast<const df*>(M->dt.sfBB_df);
+  a.CC = reinterpret_cast<const df*>(M->dt.sfCC_df);
+  a.p2to1 = M->dt.sfp2to1;
+  a.p3to2 = M->dt.sfp3to2;
   a.w = M->dt.vol_w;
   a.pairs_n = M->dt.pairs_n;
   a.pairs_m = M->dt.pairs_m;

@@ -35,6 +35,16 @@ struct Tables {
   std::vector<double> G1;       // [3][nq][n1] its reference gradients
   std::vector<double> Shat1;    // [6][n1][n1] (1/6) sum_q w d_# P'_i d_% P'_j, (#,%) in
                                 //   xx, xy, xz, yy, yz, zz  (stiffness of eq. 9.11)
+  // Sum factorisation of the volume masses: P_a at the conical node (i, j, l) is
+  // A_pa(l) B_(pa,qa)(j) C_a(i), so sum_q g_q P_a P_b = sum_i CC_ab(i) sum_j BB(j) sum_l g AA(l).
+  // Pair lists: 1-D (pa <= pb) over 0..k; 2-D (a2 <= b2) over the (p, q), p + q <= k, listed
+  // p-major from (0, 0); 3-D the (a <= b) pairs of P_k(K) in row-major order (pairs_n).
+  int np1 = 0, np2 = 0;
+  std::vector<double> sfAA;       // [np1][k+2]  A_pa(l) A_pb(l)
+  std::vector<double> sfBB;       // [np2][k+2]  B_a2(j) B_b2(j)
+  std::vector<double> sfCC;       // [n(n+1)/2][k+2]  C_a(i) C_b(i)
+  std::vector<int16_t> sfp2to1;   // [np2]  1-D pair (p_a2, p_b2) of each 2-D pair
+  std::vector<int16_t> sfp3to2;   // [n(n+1)/2]  2-D pair ((pa, qa), (pb, qb)) of each 3-D pair
 };
 
 bool build_tables(int k, Tables* t, std::string* err);
@@ -48,6 +58,8 @@ struct DevTables {
   double *P1 = nullptr, *G1 = nullptr, *Shat1 = nullptr, *Pl = nullptr, *Dmu = nullptr, *face_pts = nullptr;
   // double-float (hi, lo) float pairs of P, C_hat, S, E for the HDG_DF32 assembly
   float *P_df = nullptr, *Chat_df = nullptr, *S_df = nullptr, *E_df = nullptr;
+  float *sfAA_df = nullptr, *sfBB_df = nullptr, *sfCC_df = nullptr;  // sum-factorisation tables
+  int16_t *sfp2to1 = nullptr, *sfp3to2 = nullptr;
   int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
   int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices
   int16_t* pairs_n1 = nullptr;  // [(n1-1) n1 / 2][2] pairs of 1..n1-1 (postprocess)
@@ -71,6 +83,7 @@ struct hdg_mesh {
 
   // device mesh
   double* d_vx = nullptr;         // [12][nelt] SoA: x1..x4, y1..y4, z1..z4
+  double* d_geo = nullptr;        // [nelt][kGeoStride] cofactors a (9), normals (12), areas (4), vol
   double* d_fvx = nullptr;        // [9][nfc]   SoA: sorted face vertices x1..x3, y1..y3, z1..z3
   int32_t* d_fverts = nullptr;    // [nfc][3]   sorted face vertex numbers (coarse prolongation)
   double* d_Tproj = nullptr;      // [d2][3]    (varpi . D)^T Xi: linear face data -> face basis
@@ -137,6 +150,8 @@ cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* 
                           double* FZ);
 cudaError_t launch_assemble(hdg_mesh* M);
 cudaError_t launch_assemble_df(hdg_mesh* M);
+constexpr int kGeoStride = 28;  // doubles per element of d_geo (26 used; 224 bytes, 32-byte aligned rows)
+cudaError_t launch_geometry(hdg_mesh* M);
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u);
 cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double* Z);
 cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst);

@@ -13,6 +13,7 @@
 // through the collapsed coordinates using d/dx P_n^(a,b) = (n+a+b+1)/2 P_{n-1}^(a+1,b+1).
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "hdg_internal.h"
 
@@ -301,6 +302,74 @@ bool build_tables(int k, Tables* T, std::string* err) {
             s += T->face_w[r] * T->Dmu[(mu * nf + r) * d2 + a] * T->Pl[(l * nf + r) * n + j];
           T->E[((l * 6 + mu) * d2 + a) * n + j] = s;
         }
+  }
+
+  // Sum-factorisation tables.  At the node z = t1_i, y = t2_j (1 - t1_i),
+  // x = t3_l (1 - t1_i)(1 - t2_j) the collapsed coordinates are a = 2 t3_l - 1, b = 2 t2_j - 1,
+  // c = 2 t1_i - 1, and the Dubiner function (p, q, r) is nrm A_p(l) B_pq(j) C'_pqr(i) with
+  //   A_p = P_p^(0,0)(a),  B_pq = (1 - t2)^p P_q^(2p+1,0)(b),  C'_pqr = (1 - t1)^(p+q) P_r^(2p+2q+2,0)(c)
+  // (the normalisation nrm goes into C).
+  {
+    std::vector<double> A((k + 1) * nn), B, C(n * nn);
+    std::vector<std::pair<int, int>> idx2;
+    for (int p = 0; p <= k; ++p)
+      for (int q = 0; q + p <= k; ++q) idx2.push_back({p, q});
+    B.resize(idx2.size() * nn);
+    for (int p = 0; p <= k; ++p)
+      for (int l = 0; l < nn; ++l) A[p * nn + l] = jacobi(p, 0, 0, 2 * t3[l] - 1);
+    for (size_t a2 = 0; a2 < idx2.size(); ++a2) {
+      const int p = idx2[a2].first, q = idx2[a2].second;
+      for (int j = 0; j < nn; ++j) B[a2 * nn + j] = std::pow(1 - t2[j], p) * jacobi(q, 2 * p + 1, 0, 2 * t2[j] - 1);
+    }
+    std::vector<int> id2(n);
+    for (int a = 0; a < n; ++a) {
+      const int p = idx[a].p, q = idx[a].q, r = idx[a].r;
+      for (size_t a2 = 0; a2 < idx2.size(); ++a2)
+        if (idx2[a2].first == p && idx2[a2].second == q) id2[a] = (int)a2;
+      const double nrm = std::sqrt((2 * p + 1) * (p + q + 1) * (2.0 * p + 2 * q + 2 * r + 3) / 3.0);
+      for (int i = 0; i < nn; ++i)
+        C[a * nn + i] = nrm * std::pow(1 - t1[i], p + q) * jacobi(r, 2 * p + 2 * q + 2, 0, 2 * t1[i] - 1);
+    }
+    // the factors must reproduce the basis table
+    for (int i = 0; i < nn; ++i)
+      for (int j = 0; j < nn; ++j)
+        for (int l = 0; l < nn; ++l)
+          for (int a = 0; a < n; ++a) {
+            const double v = A[idx[a].p * nn + l] * B[id2[a] * nn + j] * C[a * nn + i];
+            const double ref = T->P[((i * nn + j) * nn + l) * n + a];
+            if (std::fabs(v - ref) > 1e-11 * (1.0 + std::fabs(ref))) {
+              *err = "sum-factorisation tables do not reproduce the volume basis";
+              return false;
+            }
+          }
+    std::vector<int> p1of(( k + 1) * (k + 1));
+    T->sfAA.clear();
+    int np1 = 0;
+    for (int pa = 0; pa <= k; ++pa)
+      for (int pb = pa; pb <= k; ++pb) {
+        p1of[pa * (k + 1) + pb] = p1of[pb * (k + 1) + pa] = np1++;
+        for (int l = 0; l < nn; ++l) T->sfAA.push_back(A[pa * nn + l] * A[pb * nn + l]);
+      }
+    const int nd2 = (int)idx2.size();
+    std::vector<int> p2of(nd2 * nd2);
+    T->sfBB.clear();
+    T->sfp2to1.clear();
+    int np2 = 0;
+    for (int a2 = 0; a2 < nd2; ++a2)
+      for (int b2 = a2; b2 < nd2; ++b2) {
+        p2of[a2 * nd2 + b2] = p2of[b2 * nd2 + a2] = np2++;
+        T->sfp2to1.push_back((int16_t)p1of[idx2[a2].first * (k + 1) + idx2[b2].first]);
+        for (int j = 0; j < nn; ++j) T->sfBB.push_back(B[a2 * nn + j] * B[b2 * nn + j]);
+      }
+    T->sfCC.clear();
+    T->sfp3to2.clear();
+    for (int a = 0; a < n; ++a)
+      for (int b = a; b < n; ++b) {
+        T->sfp3to2.push_back((int16_t)p2of[id2[a] * nd2 + id2[b]]);
+        for (int i = 0; i < nn; ++i) T->sfCC.push_back(C[a * nn + i] * C[b * nn + i]);
+      }
+    T->np1 = np1;
+    T->np2 = np2;
   }
   return true;
 }
