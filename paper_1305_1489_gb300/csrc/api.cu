@@ -95,9 +95,13 @@ static void release(hdg_mesh* M) {
 }
 
 static int check_status(hdg_mesh* M) {
-  int32_t st[4];
+  int32_t st[5];
   HDG_CUDA_TRY(cudaMemcpyAsync(st, M->d_status, sizeof(st), cudaMemcpyDeviceToHost, M->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  if (st[4]) {  // counted by the double-float recovery kernel; reported once
+    HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 4, 0, sizeof(int32_t), M->stream));
+    return fail(HDG_ERR_CUDA, std::to_string(st[4]) + " element(s) whose recovery record copy did not complete (q, u set to NaN)");
+  }
   if (st[1]) return fail(HDG_ERR_COEFF, std::to_string(st[1]) + " element(s) with kappa <= 0, c < 0 or non-finite data");
   if (st[0]) return fail(HDG_ERR_LOCAL_SINGULAR, std::to_string(st[0]) + " element(s) with a non-positive local pivot");
   if (st[2]) return fail(HDG_ERR_LOCAL_SINGULAR, std::to_string(st[2]) + " element(s) with a singular postprocess system");
@@ -141,7 +145,8 @@ int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, in
     cudaError_t e = cudaMalloc(&M->d_C, sizeof(double) * nelt * m * m);
     if (e == cudaSuccess) e = cudaMalloc(&M->d_Cf, sizeof(double) * nelt * m);
     if (e == cudaSuccess) e = cudaMalloc(&M->d_rec, sizeof(double) * nelt * M->rec_stride);
-    if (e == cudaSuccess) e = cudaMalloc(&M->d_status, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_status, sizeof(int32_t) * 8);
+    if (e == cudaSuccess) e = cudaMemset(M->d_status, 0, sizeof(int32_t) * 8);
     if (e == cudaSuccess) e = cudaMalloc(&M->d_geo, sizeof(double) * nelt * kGeoStride);
     if (e == cudaSuccess) e = launch_geometry(M);  // the mesh's element geometry, once
     if (e != cudaSuccess) rc = fail(HDG_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e));

@@ -1,5 +1,6 @@
 // K2 local recovery (eq. 5.3), K5 superconvergent postprocess (eq. 9.11), and the
 // quadrature-node helper (eq. 3.4, 6.2).  FP64.
+#include "device_async.cuh"
 #include "device_common.cuh"
 #include "device_df.cuh"
 #include "hdg_internal.h"
@@ -236,25 +237,26 @@ __global__ void __launch_bounds__(32 * kRecWarps) recover_kernel(const double* _
 }
 
 // The same recovery in double-float on the FP32 pipe, for the record of the double-float
-// K1 (entries stored as (hi, lo) float pairs): the accumulations are compensated (dacc), the
-// triangular solves keep every pending right-hand side as an unnormalised accumulator, and
-// u_dK and the results cross to and from FP64 once.
-__device__ __forceinline__ df ldg_df2(const df* p) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-  return df_make(v.x, v.y);
-}
+// K1 (entries stored as (hi, lo) float pairs).  One warp (one CTA) per element: the element's
+// record, one contiguous block, is brought into shared memory by a single bulk asynchronous
+// copy while the lanes gather u_dK, so the kernel streams the records at the copy engine's
+// rate.  The accumulations are compensated (dacc), the triangular solves keep every pending
+// right-hand side as an unnormalised accumulator, and u_dK and the results cross to and
+// from FP64 once.  A copy that does not complete within the wait limit (it cannot, short of
+// a hardware fault) leaves NaN in the element's q and u and counts in status[4].
+constexpr int kRecWaitPolls = 1 << 16;
 
 __device__ __forceinline__ df shfl_df(df x, int src) {
   return df_make(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
 }
 
 template <int N, int NV>
-__device__ __forceinline__ void upper_solve_df(const df* __restrict__ U, dacc (&x)[(N + 31) / 32][NV], int lane) {
+__device__ __forceinline__ void upper_solve_df(const df* U, dacc (&x)[(N + 31) / 32][NV], int lane) {
   constexpr int NA = (N + 31) / 32;
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
     const df* col = U + i * (i + 1) / 2;
-    const df inv = ldg_df2(col + i);
+    const df inv = col[i];
     df xi[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) xi[v] = df_mul(shfl_df(dacc_result(x[i >> 5][v]), i & 31), inv);
@@ -262,7 +264,7 @@ __device__ __forceinline__ void upper_solve_df(const df* __restrict__ U, dacc (&
     for (int a = 0; a < NA; ++a) {
       const int l = lane + 32 * a;
       if (l < i) {
-        const df uli = ldg_df2(col + l);
+        const df uli = col[l];
 #pragma unroll
         for (int v = 0; v < NV; ++v) dacc_msub(x[a][v], uli, xi[v]);
       } else if (l == i) {
@@ -274,34 +276,52 @@ __device__ __forceinline__ void upper_solve_df(const df* __restrict__ U, dacc (&
 }
 
 template <int K>
-__global__ void __launch_bounds__(32 * kRecWarps) recover_df_kernel(const double* __restrict__ rec,
-                                                                   const int32_t* __restrict__ fbe,
-                                                                   const double* __restrict__ uhat, int64_t nelt,
-                                                                   double* __restrict__ q, double* __restrict__ u) {
+__global__ void __launch_bounds__(32) recover_df_kernel(const double* __restrict__ rec, const int32_t* __restrict__ fbe,
+                                                       const double* __restrict__ uhat, int64_t nelt,
+                                                       double* __restrict__ q, double* __restrict__ u,
+                                                       int32_t* status) {
   using D = Dims<K>;
   constexpr int n = D::n, m = D::m, d2 = D::d2, NA = (n + 31) / 32;
-  __shared__ df suh[kRecWarps][m], su[kRecWarps][n];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t Ke = (int64_t)blockIdx.x * kRecWarps + warp;
-  if (Ke >= nelt) return;  // a whole warp leaves together
-  const df* HT = reinterpret_cast<const df*>(rec) + Ke * (int64_t)D::rec;
+  constexpr uint32_t kBytes = sizeof(df) * D::rec;
+  static_assert(kBytes % 16 == 0, "the record must be a whole number of 16-byte units");
+  extern __shared__ __align__(128) unsigned char rec_smem[];
+  __shared__ df suh[m], su[n];
+  __shared__ __align__(8) uint64_t bar;
+  const int lane = threadIdx.x;
+  const int64_t Ke = blockIdx.x;
+  const df* HT = reinterpret_cast<const df*>(rec_smem);
+  if (lane == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, kBytes);
+    bulk_g2s(rec_smem, reinterpret_cast<const df*>(rec) + Ke * (int64_t)D::rec, kBytes, &bar);
+  }
+  for (int t = lane; t < m; t += 32)
+    suh[t] = df_from_double(__ldg(uhat + (int64_t)__ldg(fbe + Ke * 4 + t / d2) * d2 + (t % d2)));
+  __syncwarp();
+  if (!mbar_wait(&bar, 0, kRecWaitPolls)) {
+    mbar_wait(&bar, 0, kRecWaitPolls);  // give the copy in flight a second chance to land
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int l = lane; l < n; l += 32) {
+      u[Ke * n + l] = nan;
+      for (int st = 0; st < 3; ++st) q[(Ke * 3 + st) * n + l] = nan;
+    }
+    if (lane == 0) atomicAdd(status + 4, 1);
+    return;
+  }
   const df* VT = HT + n * (m + 1);
   const df* WT = VT + n * m;
   const df* Us = WT + 3 * n * n;
   const df* UM = Us + D::tri;
   const df* nrm = UM + D::tri;
-  for (int t = lane; t < m; t += 32)
-    suh[warp][t] = df_from_double(__ldg(uhat + (int64_t)__ldg(fbe + Ke * 4 + t / d2) * d2 + (t % d2)));
-  __syncwarp();
   dacc x[NA][1];
 #pragma unroll
   for (int a = 0; a < NA; ++a) {
     const int i = lane + 32 * a;
     dacc s = dacc_zero();
     if (i < n) {
-      s = dacc_from(ldg_df2(HT + m * n + i));
+      s = dacc_from(HT[m * n + i]);
 #pragma unroll 8
-      for (int r = 0; r < m; ++r) dacc_mac(s, ldg_df2(HT + r * n + i), suh[warp][r]);
+      for (int r = 0; r < m; ++r) dacc_mac(s, HT[r * n + i], suh[r]);
     }
     x[a][0] = s;
   }
@@ -311,14 +331,14 @@ __global__ void __launch_bounds__(32 * kRecWarps) recover_df_kernel(const double
     const int i = lane + 32 * a;
     if (i < n) {
       const df ui = dacc_result(x[a][0]);
-      su[warp][i] = ui;
+      su[i] = ui;
       u[Ke * n + i] = df_to_double(ui);
     }
   }
   __syncwarp();
   df nv[12];
 #pragma unroll
-  for (int t = 0; t < 12; ++t) nv[t] = ldg_df2(nrm + t);
+  for (int t = 0; t < 12; ++t) nv[t] = nrm[t];
   dacc z[NA][3];
 #pragma unroll
   for (int a = 0; a < NA; ++a) {
@@ -327,17 +347,17 @@ __global__ void __launch_bounds__(32 * kRecWarps) recover_df_kernel(const double
     if (l < n) {
 #pragma unroll 4
       for (int c = 0; c < n; ++c) {
-        const df uc = su[warp][c];
-        dacc_mac(z[a][0], ldg_df2(WT + (0 * n + c) * n + l), uc);
-        dacc_mac(z[a][1], ldg_df2(WT + (1 * n + c) * n + l), uc);
-        dacc_mac(z[a][2], ldg_df2(WT + (2 * n + c) * n + l), uc);
+        const df uc = su[c];
+        dacc_mac(z[a][0], WT[(0 * n + c) * n + l], uc);
+        dacc_mac(z[a][1], WT[(1 * n + c) * n + l], uc);
+        dacc_mac(z[a][2], WT[(2 * n + c) * n + l], uc);
       }
       // V (n_* o u_dK) = sum_l n_{l*} V_l u_dK,l: one product per face, then the normals
 #pragma unroll
       for (int fl = 0; fl < 4; ++fl) {
         dacc w = dacc_zero();
 #pragma unroll
-        for (int a2 = 0; a2 < d2; ++a2) dacc_mac(w, ldg_df2(VT + (fl * d2 + a2) * n + l), suh[warp][fl * d2 + a2]);
+        for (int a2 = 0; a2 < d2; ++a2) dacc_mac(w, VT[(fl * d2 + a2) * n + l], suh[fl * d2 + a2]);
         const df wv = dacc_result(w);
         dacc_msub(z[a][0], nv[3 * fl + 0], wv);
         dacc_msub(z[a][1], nv[3 * fl + 1], wv);
@@ -357,11 +377,22 @@ __global__ void __launch_bounds__(32 * kRecWarps) recover_df_kernel(const double
   }
 }
 
+template <int K>
+static cudaError_t launch_recover_df(hdg_mesh* M, const double* uhat, double* q, double* u) {
+  const int smem = (int)(sizeof(df) * Dims<K>::rec);
+  cudaError_t e = cudaFuncSetAttribute(recover_df_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  recover_df_kernel<K><<<(unsigned)M->nelt, 32, smem, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u,
+                                                                     M->d_status);
+  return cudaSuccess;
+}
+
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
   const unsigned g = (unsigned)((M->nelt + kRecWarps - 1) / kRecWarps);
   const int nt = 32 * kRecWarps;
-#define HDG_REC(KK)                                                                                    \
-  if (M->rec_df) recover_df_kernel<KK><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u); \
+  cudaError_t e = cudaSuccess;
+#define HDG_REC(KK)                                 \
+  if (M->rec_df) e = launch_recover_df<KK>(M, uhat, q, u); \
   else recover_kernel<KK><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u)
   switch (M->k) {
     case 1: HDG_REC(1); break;
@@ -371,6 +402,7 @@ cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u
     default: return cudaErrorInvalidValue;
   }
 #undef HDG_REC
+  if (e != cudaSuccess) return e;
   M->launches++;
   return cudaGetLastError();
 }
