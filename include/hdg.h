@@ -280,6 +280,36 @@ int hdg_recover(hdg_mesh* mesh, const double* uhat, double* q, double* u);
  * hdg_set_coefficients.                                                                   */
 int hdg_postprocess(hdg_mesh* mesh, const double* q, const double* u, double* ustar);
 
+/* ------------------------------------------------------------------ projections and error norms
+ * Diagnostics of Section 9 ("Error functions", "HDG projection") and eq. 10.1-10.2.  FP64.
+ *
+ * hdg_projection: the HDG projection of eq. 9.13, (Pi q, Pi u) in P_k(K)^3 x P_k(K) with
+ *   (Pi q, r)_K = (q, r)_K for r in P_{k-1}(K)^3, (Pi u, w)_K = (u, w)_K for w in P_{k-1}(K),
+ *   <Pi q.nu + tau Pi u, v>_dK = <q.nu + tau u, v>_dK for v in R_k(dK), tau as set by
+ *   hdg_set_coefficients (1 when none was given).  Inputs (device f64): q_vol [3][nelt][nq]
+ *   and u_vol [nelt][nq] at the volume nodes (hdg_quadrature_nodes); q_face [3][nelt][4][nf]
+ *   and u_face [nelt][4][nf] at the element-local face nodes (hdg_element_face_nodes).
+ *   Outputs (device f64): Pq [nelt][3][n], Pu [nelt][n] (Dubiner coefficients, as hdg_recover).
+ *   Synchronises the mesh's stream.  HDG_ERR_LOCAL_SINGULAR if an element's m x m face
+ *   system has a zero pivot (its outputs are NaN); HDG_ERR_ARG for NULL pointers.
+ * hdg_face_projection: the L2 projection onto P_k(e) of eq. 9.12 on every face, from the
+ *   values vals [nfc][nf] at the face nodes (hdg_quadrature_nodes); Pu [nfc][d2] device f64.
+ * hdg_volume_norm2: out[0] = sum_K |K| sum_q omega_q (vals - sum_j coef_j P_j)^2 and
+ *   out[1] = sum_K |K| sum_q omega_q vals^2 on the volume rule (host double[2]); coef
+ *   [nelt][dim] in the degree-`degree` basis (degree k: dim = n, as u_h; degree k + 1:
+ *   dim = n1, as u_h*) or NULL (zero), vals [nelt][nq] or NULL (zero).  Synchronises.
+ * hdg_face_norm2: out[0] = ||vals - sum_a coef_a D_a||_h^2 and out[1] = ||vals||_h^2 with
+ *   ||v||_h^2 = sum_e |e| ||v||_e^2 (eq. 10.2) on the face rule; coef [nfc][d2] or NULL,
+ *   vals [nfc][nf] or NULL.  Synchronises.
+ * The ratios of eq. 10.1-10.2 follow: e_h^u = sqrt(out[0] / out[1]) with coef = u_h and vals =
+ * u; eps_h^u with coef = Pi u - u_h and vals = u for the reference; eps_h^uhat with the face
+ * norms of P u - uhat_h and of u.  Sums are deterministic (fixed two-level order).        */
+int hdg_projection(hdg_mesh* mesh, const double* q_vol, const double* u_vol, const double* q_face,
+                   const double* u_face, double* Pq, double* Pu);
+int hdg_face_projection(hdg_mesh* mesh, const double* vals, double* Pu);
+int hdg_volume_norm2(hdg_mesh* mesh, int degree, const double* coef, const double* vals, double* out);
+int hdg_face_norm2(hdg_mesh* mesh, const double* coef, const double* vals, double* out);
+
 /* ------------------------------------------------------------------ batched problems
  * Many independent problems of mixed degree solved together.  Problems of equal degree are
  * merged into one disjoint-union mesh (a "group"), so each phase is one launch per group, and

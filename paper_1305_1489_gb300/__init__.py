@@ -142,6 +142,29 @@ def hdg_postprocess(h, q, u, ustar):
     return _lib.check(_lib.load().hdg_postprocess(h, _ptr(q), _ptr(u), _ptr(ustar)))
 
 
+def hdg_projection(h, q_vol, u_vol, q_face, u_face, Pq, Pu):
+    return _lib.check(_lib.load().hdg_projection(h, _ptr(q_vol), _ptr(u_vol), _ptr(q_face), _ptr(u_face),
+                                                 _ptr(Pq), _ptr(Pu)))
+
+
+def hdg_face_projection(h, vals, Pu):
+    return _lib.check(_lib.load().hdg_face_projection(h, _ptr(vals), _ptr(Pu)))
+
+
+def hdg_volume_norm2(h, degree, coef, vals):
+    out = (C.c_double * 2)()
+    _lib.check(_lib.load().hdg_volume_norm2(h, int(degree), _ptr(coef) if coef is not None else None,
+                                            _ptr(vals) if vals is not None else None, out))
+    return out[0], out[1]
+
+
+def hdg_face_norm2(h, coef, vals):
+    out = (C.c_double * 2)()
+    _lib.check(_lib.load().hdg_face_norm2(h, _ptr(coef) if coef is not None else None,
+                                          _ptr(vals) if vals is not None else None, out))
+    return out[0], out[1]
+
+
 def hdg_launch_count(h):
     return int(_lib.load().hdg_launch_count(h))
 
@@ -300,6 +323,39 @@ class HDGMesh:
         hdg_postprocess(self._h, _dev_f64(q, (self.nelt, 3, self.n), "q"),
                         _dev_f64(u, (self.nelt, self.n), "u"), ustar)
         return ustar
+
+    def projection(self, q_vol, u_vol, q_face, u_face):
+        """HDG projection of eq. 9.13: q_vol [3, nelt, nq], u_vol [nelt, nq] at the volume
+        nodes; q_face [3, nelt, 4, nf], u_face [nelt, 4, nf] at the element face nodes.
+        Returns (Pi q [nelt, 3, n], Pi u [nelt, n])."""
+        Pq = self._empty(self.nelt, 3, self.n)
+        Pu = self._empty(self.nelt, self.n)
+        hdg_projection(self._h, _dev_f64(q_vol, (3, self.nelt, self.nq), "q_vol"),
+                       _dev_f64(u_vol, (self.nelt, self.nq), "u_vol"),
+                       _dev_f64(q_face, (3, self.nelt, 4, self.nf), "q_face"),
+                       _dev_f64(u_face, (self.nelt, 4, self.nf), "u_face"), Pq, Pu)
+        return Pq, Pu
+
+    def face_projection(self, vals):
+        """eq. 9.12 on every face from the values [nfc, nf] at the face nodes: [nfc, d2]."""
+        Pu = self._empty(self.nfc, self.d2)
+        hdg_face_projection(self._h, _dev_f64(vals, (self.nfc, self.nf), "vals"), Pu)
+        return Pu
+
+    def volume_norm2(self, coef=None, vals=None, degree=None):
+        """(sum_K |K| sum_q omega_q (vals - coef . P)^2, sum ... vals^2); coef in the degree-k
+        (default) or degree-(k+1) basis."""
+        degree = self.k if degree is None else degree
+        dim = self.n if degree == self.k else self.n1
+        c = None if coef is None else _dev_f64(coef, (self.nelt, dim), "coef")
+        v = None if vals is None else _dev_f64(vals, (self.nelt, self.nq), "vals")
+        return hdg_volume_norm2(self._h, degree, c, v)
+
+    def face_norm2(self, coef=None, vals=None):
+        """(||vals - coef . D||_h^2, ||vals||_h^2) of eq. 10.2."""
+        c = None if coef is None else _dev_f64(coef, (self.nfc, self.d2), "coef")
+        v = None if vals is None else _dev_f64(vals, (self.nfc, self.nf), "vals")
+        return hdg_face_norm2(self._h, c, v)
 
     @property
     def launches(self):

@@ -83,7 +83,7 @@ static void release(hdg_mesh* M) {
                   M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
                   M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
                   M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj,
-                  M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2};
+                  M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2, M->d_norm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
@@ -347,6 +347,37 @@ int hdg_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar
   if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 2, 0, sizeof(int32_t), M->stream));
   HDG_CUDA_TRY(launch_postprocess(M, q, u, ustar));
+  return HDG_OK;
+}
+
+int hdg_projection(hdg_mesh* M, const double* q_vol, const double* u_vol, const double* q_face,
+                   const double* u_face, double* Pq, double* Pu) {
+  if (!M || !q_vol || !u_vol || !q_face || !u_face || !Pq || !Pu) return fail(HDG_ERR_ARG, "NULL argument");
+  HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 5, 0, sizeof(int32_t), M->stream));
+  HDG_CUDA_TRY(launch_projection(M, q_vol, u_vol, q_face, u_face, Pq, Pu));
+  int32_t bad = 0;
+  HDG_CUDA_TRY(cudaMemcpyAsync(&bad, M->d_status + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, M->stream));
+  HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  if (bad) return fail(HDG_ERR_LOCAL_SINGULAR, std::to_string(bad) + " element(s) with a singular projection system");
+  return HDG_OK;
+}
+
+int hdg_face_projection(hdg_mesh* M, const double* vals, double* Pu) {
+  if (!M || !vals || !Pu) return fail(HDG_ERR_ARG, "NULL argument");
+  HDG_CUDA_TRY(launch_face_projection(M, vals, Pu));
+  return HDG_OK;
+}
+
+int hdg_volume_norm2(hdg_mesh* M, int degree, const double* coef, const double* vals, double* out) {
+  if (!M || !out) return fail(HDG_ERR_ARG, "NULL argument");
+  if (degree != M->k && degree != M->k + 1) return fail(HDG_ERR_ARG, "degree must be k or k + 1");
+  HDG_CUDA_TRY(launch_volume_norm2(M, degree, coef, vals, out));
+  return HDG_OK;
+}
+
+int hdg_face_norm2(hdg_mesh* M, const double* coef, const double* vals, double* out) {
+  if (!M || !out) return fail(HDG_ERR_ARG, "NULL argument");
+  HDG_CUDA_TRY(launch_face_norm2(M, coef, vals, out));
   return HDG_OK;
 }
 

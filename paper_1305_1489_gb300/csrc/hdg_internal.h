@@ -105,7 +105,8 @@ struct hdg_mesh {
   double* d_rec = nullptr;  // [nelt][rec_stride] recovery operators (eq. 5.3)
   int64_t rec_stride = 0;
   bool rec_df = false;      // the record holds double-float pairs (written by the double-float K1)
-  int32_t* d_status = nullptr;  // [4] error counters written by kernels
+  int32_t* d_status = nullptr;  // [8] error counters written by kernels
+  double* d_norm = nullptr;     // partial sums of the error norms (allocated on first use)
 
   // trace-solve workspace (library-owned, allocated on first solve)
   bool rhs_ready = false;
@@ -150,6 +151,11 @@ cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* 
                           double* FZ);
 cudaError_t launch_assemble(hdg_mesh* M);
 cudaError_t launch_assemble_df(hdg_mesh* M);
+cudaError_t launch_projection(hdg_mesh* M, const double* q_vol, const double* u_vol, const double* q_face,
+                              const double* u_face, double* Pq, double* Pu);
+cudaError_t launch_face_projection(hdg_mesh* M, const double* vals, double* Pu);
+cudaError_t launch_volume_norm2(hdg_mesh* M, int degree, const double* coef, const double* vals, double* out_host);
+cudaError_t launch_face_norm2(hdg_mesh* M, const double* coef, const double* vals, double* out_host);
 constexpr int kGeoStride = 28;  // doubles per element of d_geo (26 used; 224 bytes, 32-byte aligned rows)
 cudaError_t launch_geometry(hdg_mesh* M);
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u);
