@@ -136,6 +136,17 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
 
+/* Local method of the next hdg_assemble_condense (Section 9, "BDM"):
+ *   HDG_METHOD_HDG (default): the HDG method of eq. 1.2;
+ *   HDG_METHOD_BDM: the hybridised Brezzi-Douglas-Marini element, tau = 0 (the tau given to
+ *   hdg_set_coefficients is ignored) and u_h in P_{k-1}(K): the degree-k members of the
+ *   hierarchical u basis are erased from the local problem (hdg_recover returns them as 0),
+ *   q_h stays in P_k(K)^3, everything else (trace solve, recovery, postprocess) unchanged.
+ * HDG_ERR_ARG for another value; hdg_assemble_condense returns HDG_ERR_UNSUPPORTED for BDM
+ * with convection.                                                                        */
+typedef enum { HDG_METHOD_HDG = 0, HDG_METHOD_BDM = 1 } hdg_method;
+int hdg_set_method(hdg_mesh* mesh, int method);
+
 /* Copy the condensed local matrices out (tests): C [nelt][m][m] (row-major C^K), Cf [nelt][m]
  * device f64.                                                                              */
 int hdg_get_condensed(const hdg_mesh* mesh, double* C, double* Cf);

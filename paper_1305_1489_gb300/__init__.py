@@ -20,9 +20,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import HDG_DF32, HDG_FP64, HDG_MIXED_FP32, HDGError  # noqa: F401
+from ._lib import HDG_DF32, HDG_FP64, HDG_METHOD_BDM, HDG_METHOD_HDG, HDG_MIXED_FP32, HDGError  # noqa: F401
 
-__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "HDG_DF32", "build", "load_library"]
+__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "HDG_DF32", "HDG_METHOD_HDG", "HDG_METHOD_BDM",
+           "build", "load_library"]
 
 
 def build(**kw):
@@ -323,6 +324,11 @@ class HDGMesh:
         hdg_postprocess(self._h, _dev_f64(q, (self.nelt, 3, self.n), "q"),
                         _dev_f64(u, (self.nelt, self.n), "u"), ustar)
         return ustar
+
+    def set_method(self, method):
+        """HDG_METHOD_HDG (default) or HDG_METHOD_BDM (hybridised BDM: tau = 0, u_h in
+        P_{k-1}) for the next assembly."""
+        _lib.check(_lib.load().hdg_set_method(self._h, int(method)))
 
     def projection(self, q_vol, u_vol, q_face, u_face):
         """HDG projection of eq. 9.13: q_vol [3, nelt, nq], u_vol [nelt, nq] at the volume

@@ -9,6 +9,8 @@ LIB_PATH = os.path.join(_HERE, "libhdg.so")
 HDG_FP64 = 0
 HDG_MIXED_FP32 = 1
 HDG_DF32 = 2
+HDG_METHOD_HDG = 0
+HDG_METHOD_BDM = 1
 
 STATUS = {
     0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_ORIENTATION", 3: "HDG_ERR_NONCONFORMING",
@@ -68,6 +70,7 @@ _SIGS = {
     "hdg_recover": [P, P, P, P],
     "hdg_postprocess": [P, P, P, P],
     "hdg_projection": [P, P, P, P, P, P, P],
+    "hdg_set_method": [P, C.c_int],
     "hdg_face_projection": [P, P, P],
     "hdg_volume_norm2": [P, C.c_int, P, P, P],
     "hdg_face_norm2": [P, P, P, P],

@@ -249,6 +249,8 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (M->beta_q && !M->beta_f) return fail(HDG_ERR_STATE, "convection set without hdg_set_face_convection");
   if (M->beta_q && precision == HDG_DF32)
     return fail(HDG_ERR_UNSUPPORTED, "the double-float assembly covers reaction-diffusion (beta = 0)");
+  if (M->beta_q && M->method == HDG_METHOD_BDM)
+    return fail(HDG_ERR_UNSUPPORTED, "the BDM element is built for reaction-diffusion (beta = 0)");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   M->assembled = true;
@@ -258,6 +260,13 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (M->coarse) coarse_invalidate(M);
   M->rhs_ready = false;
   return check_status(M);
+}
+
+int hdg_set_method(hdg_mesh* M, int method) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  if (method != HDG_METHOD_HDG && method != HDG_METHOD_BDM) return fail(HDG_ERR_ARG, "unknown method");
+  M->method = method;
+  return HDG_OK;
 }
 
 int hdg_get_condensed(const hdg_mesh* M, double* C, double* Cf) {

@@ -43,6 +43,7 @@ struct AsmArgs {
   double *C, *Cf, *rec;
   int32_t* status;
   int64_t nelt;
+  int nu;  // u unknowns kept: n (HDG), n - d2 (hybridised BDM: u in P_{k-1}, tau = 0)
 };
 
 template <int K, bool CONV>
@@ -104,8 +105,8 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
       for (int j = 0; j < 3; ++j) s_a[i][j] = g.a[i][j];
     for (int l = 0; l < 4; ++l) {
       for (int d = 0; d < 3; ++d) s_nrm[l][d] = g.nrm[l][d];
-      double tau = A.tau ? A.tau[Ke * 4 + l] : 1.0;
-      s_T[l] = tau * g.area[l];  // T_l = tau_l |e_l|, eq. 4.22
+      double tau = A.nu < n ? 0.0 : A.tau ? A.tau[Ke * 4 + l] : 1.0;
+      s_T[l] = tau * g.area[l];  // T_l = tau_l |e_l|, eq. 4.22 (0 for BDM)
       s_perm[l] = A.perm[Ke * 4 + l] - 1;
     }
     s_vol = g.vol;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
   for (int i = tid; i < n; i += NT) {
     double s = 0.0;
     for (int q = 0; q < nq; ++q) s = fma(fw[q], __ldg(A.P + q * n + i), s);
-    Gt[i * (m + 1) + m] = s;
+    Gt[i * (m + 1) + m] = i < A.nu ? s : 0.0;  // BDM: no degree-k u test functions
   }
   for (int t = tid; t < 3 * n * n; t += NT) {
     const int st = t / (n * n), rem = t - st * n * n, l = rem / n, cidx = rem - l * n;
@@ -248,8 +249,14 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
     for (int st = 0; st < 3; ++st)
 #pragma unroll 4
       for (int l = 0; l < n; ++l) s = fma(W[st * n * n + l * n + i], W[st * n * n + l * n + j], s);
-    Ss[i * n + j] += s;
-    if (i != j) Ss[j * n + i] += s;
+    if (i < A.nu && j < A.nu) {  // (S_u is not symmetric with convection: update both entries)
+      Ss[i * n + j] += s;
+      if (i != j) Ss[j * n + i] += s;
+    } else {  // BDM: the degree-k u unknowns are decoupled (identity rows and columns), which
+              // erases them from the elimination as the paper erases their rows and columns of A_1
+      Ss[i * n + j] = (i == j) ? 1.0 : 0.0;
+      if (i != j) Ss[j * n + i] = 0.0;
+    }
   }
   for (int t = tid; t < 4 * n * n; t += NT) {
     const int fl = t / (n * n), rem = t - fl * n * n;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
         Gt[j * (m + 1) + r] = g - Hr[j * m + r];  // G_col^T = (G - alphaDP)^T
         Hr[j * m + r] = g;                       // G^T
       } else {
-        Gt[j * (m + 1) + r] = g;
+        Gt[j * (m + 1) + r] = j < A.nu ? g : 0.0;
       }
     }
   }
@@ -423,6 +430,7 @@ cudaError_t launch_assemble(hdg_mesh* M) {
   a.C = M->d_C;
   a.Cf = M->d_Cf;
   a.rec = M->d_rec;
+  a.nu = M->method == HDG_METHOD_BDM ? M->tab.n - M->tab.d2 : M->tab.n;
   a.status = M->d_status;
   a.nelt = M->nelt;
   const bool conv = M->beta_q != nullptr;

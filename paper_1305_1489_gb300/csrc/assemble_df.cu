@@ -29,6 +29,7 @@ struct AsmDfArgs {
   double *C, *Cf, *rec;
   int32_t* status;
   int64_t nelt;
+  int nu;  // u unknowns kept: n (HDG), n - d2 (hybridised BDM: u in P_{k-1}, tau = 0)
 };
 
 // Shared-memory plan.  C is formed in one pass near the end (C = (n_l . n_l') o V^T V
@@ -211,8 +212,8 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     else s_nrm[(tid - 9) / 3][(tid - 9) % 3] = v;
   } else if (tid < 25) {
     const int l = tid - 21;
-    const double tau = A.tau ? A.tau[Ke * 4 + l] : 1.0;
-    s_T[l] = df_from_double(tau * s_geo[21 + l]);  // T_l = tau_l |e_l|, eq. 4.22
+    const double tau = A.nu < n ? 0.0 : A.tau ? A.tau[Ke * 4 + l] : 1.0;
+    s_T[l] = df_from_double(tau * s_geo[21 + l]);  // T_l = tau_l |e_l|, eq. 4.22 (0 for BDM)
   } else if (tid < 41) {
     const double* x = s_geo + 9 + 3 * ((tid - 25) / 4);
     const double* y = s_geo + 9 + 3 * ((tid - 25) % 4);
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     Ms[j * n + i] = v1;
     Ss[i * n + j] = v2;
     Ss[j * n + i] = v2;
-    if (wf) Gt[j * (m + 1) + m] = dacc_result(s3);  // pair (0, j)
+    if (wf) Gt[j * (m + 1) + m] = j < A.nu ? dacc_result(s3) : df_make(0.f, 0.f);  // pair (0, j)
   }
   // C_*^T from C_hat and the cofactors, V = E^T (both where T1 was)
   for (int t = tid; t < 3 * n * n; t += NT) {
@@ -338,7 +339,9 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     for (int st = 0; st < 3; ++st)
 #pragma unroll 4
       for (int l = 0; l < n; ++l) dacc_mac(s, W[st * n * n + l * n + i], W[st * n * n + l * n + j]);
-    const df v = dacc_result(s);
+    // BDM: the degree-k u unknowns are decoupled (identity rows and columns), which erases
+    // them from the elimination exactly as the paper erases their rows and columns of A_1
+    const df v = (i < A.nu && j < A.nu) ? dacc_result(s) : df_make(i == j ? 1.f : 0.f, 0.f);
     Ss[i * n + j] = v;
     Ss[j * n + i] = v;
   }
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
         const df* wt = Wt + (fl - f0) * n * n;
 #pragma unroll 4
         for (int l = 0; l < n; ++l) dacc_mac(g, V[l * m + r], wt[l * n + j]);
-        Gt[j * (m + 1) + r] = dacc_result(g);
+        Gt[j * (m + 1) + r] = j < A.nu ? dacc_result(g) : df_make(0.f, 0.f);
       }
     }
   }
@@ -539,6 +542,7 @@ cudaError_t launch_assemble_df(hdg_mesh* M) {
   a.C = M->d_C;
   a.Cf = M->d_Cf;
   a.rec = M->d_rec;
+  a.nu = M->method == HDG_METHOD_BDM ? M->tab.n - M->tab.d2 : M->tab.n;
   a.status = M->d_status;
   a.nelt = M->nelt;
   switch (M->k) {

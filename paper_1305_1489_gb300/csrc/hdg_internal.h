@@ -105,6 +105,7 @@ struct hdg_mesh {
   double* d_rec = nullptr;  // [nelt][rec_stride] recovery operators (eq. 5.3)
   int64_t rec_stride = 0;
   bool rec_df = false;      // the record holds double-float pairs (written by the double-float K1)
+  int method = 0;           // HDG_METHOD_HDG or HDG_METHOD_BDM (hdg_set_method)
   int32_t* d_status = nullptr;  // [8] error counters written by kernels
   double* d_norm = nullptr;     // partial sums of the error norms (allocated on first use)
 
