@@ -46,8 +46,8 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one K1 launch at this workload,
 # from the ncu captures summarised under profiles/, valid while the kernel source is unchanged.
-K1_TRAFFIC = {"assemble_df.cu": {"sha256": "c5c8fa0251f7ddd551ca4f5e881fc230f9fced2fb368914b1182aba5caf9c399",
-                                 "bytes": 79878400 + 901348864},
+K1_TRAFFIC = {"assemble_df.cu": {"sha256": "60991e4087b1825badc370f5ffa26633b461f005ab25a93cdc44c5d82d083bbd",
+                                 "bytes": 79856896 + 901217280},
               "assemble.cu": {"sha256": None, "bytes": None}}
 
 
