@@ -66,7 +66,8 @@ static int upload_tables(hdg_mesh* M) {
       (rc = upload(&D.S_df, split_df(T.S))) || (rc = upload(&D.E_df, split_df(T.E))) ||
       (rc = upload(&D.sfAA_df, split_df(T.sfAA))) || (rc = upload(&D.sfBB_df, split_df(T.sfBB))) ||
       (rc = upload(&D.sfCC_df, split_df(T.sfCC))) || (rc = upload(&D.sfp2to1, T.sfp2to1)) ||
-      (rc = upload(&D.sfp3to2, T.sfp3to2)))
+      (rc = upload(&D.sfp3to2, T.sfp3to2)) || (rc = upload(&D.G1_df, split_df(T.G1))) ||
+      (rc = upload(&D.Shat1_df, split_df(T.Shat1))))
     return rc;
   if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
       (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
@@ -83,7 +84,8 @@ static void release(hdg_mesh* M) {
                   M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
                   M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
                   M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj,
-                  M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2, M->d_norm};
+                  M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2, M->d_norm,
+                  M->dt.G1_df, M->dt.Shat1_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);

@@ -18,6 +18,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 namespace hdg {
 
 struct df {
@@ -130,6 +132,74 @@ __device__ __forceinline__ df df_rsqrt(df a) {
   t = df_mul(a, df_mul(y, y));
   r = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
   return fast_two_sum(y.hi, __fadd_rn(y.lo, __fmul_rn(__fmul_rn(y.hi, r), 0.5f)));
+}
+
+// Cholesky (lower) of the N x N double-float matrix A by G threads (g = this thread's index
+// among them): G = 32 is one warp (synchronised by __syncwarp), any other G is the whole
+// block (__syncthreads).  Right-looking: at step j the pivot A_jj is final; every thread takes
+// y = 1/sqrt(A_jj) by df_rsqrt (no FP64) and the trailing triangle is updated,
+// A_ik -= A_ij A_kj y^2 for i >= k > j, its entries dealt round-robin to the G threads in
+// chunks of CH whose loads are issued before any store (so they overlap).  The trailing
+// entries of step j are the last (N-j-1)(N-j)/2 pairs (r <= c) of the row-major upper-triangle
+// list `pairs`, read as one 32-bit word each.  Column j is scaled to L_ij = A_ij y at step
+// j + 1, after the barrier that ends its readers, so each step takes one barrier.  Only the
+// lower triangle is read or written; L_jj goes on the diagonal and 1/L_jj into invd.
+// Returns, on every thread, whether all pivots were positive.
+template <int N, int G>
+__device__ __forceinline__ bool group_cholesky_df(df* A, df* invd, const int16_t* __restrict__ pairs, int g) {
+  constexpr int NP = N * (N + 1) / 2, CH = 4;
+  const int* __restrict__ pw = reinterpret_cast<const int*>(pairs);
+  bool ok = true;
+  df yp = df_make(1.f, 0.f), pp = df_make(1.f, 0.f);
+  for (int j = 0; j < N; ++j) {
+    if (j > 0) {
+      for (int i = j + g; i < N; i += G) A[i * N + j - 1] = df_mul(A[i * N + j - 1], yp);
+      if (g == 0) {
+        A[(j - 1) * N + j - 1] = df_mul(pp, yp);
+        invd[j - 1] = yp;
+      }
+    }
+    const df piv = A[j * N + j];
+    ok = ok && (piv.hi > 0.f);
+    const df y = df_rsqrt(piv.hi > 0.f ? piv : df_make(1.f, 0.f));
+    const df y2 = df_mul(y, y);
+    for (int t0 = NP - (N - j - 1) * (N - j) / 2 + g; t0 < NP; t0 += CH * G) {
+      int at[CH];
+      df a[CH], lc[CH], lr[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int t = t0 + u * G;
+        if (t < NP) {
+          const int w = __ldg(pw + t);
+          const int r = w & 0xffff, c = w >> 16;  // r <= c: the lower-triangle entry (c, r)
+          at[u] = c * N + r;
+          a[u] = A[c * N + r];
+          lc[u] = A[c * N + j];
+          lr[u] = A[r * N + j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (t0 + u * G < NP) {
+          dacc s = dacc_from(a[u]);
+          dacc_msub(s, lc[u], df_mul(lr[u], y2));
+          a[u] = dacc_result(s);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (t0 + u * G < NP) A[at[u]] = a[u];
+    }
+    if (G == 32) __syncwarp();
+    else __syncthreads();
+    yp = y;
+    pp = piv;
+  }
+  if (g == 0) {
+    A[(N - 1) * N + N - 1] = df_mul(pp, yp);
+    invd[N - 1] = yp;
+  }
+  return ok;
 }
 
 // 1/x and sqrt(x) through FP64 (few per element)

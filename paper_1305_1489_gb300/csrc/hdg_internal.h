@@ -59,6 +59,7 @@ struct DevTables {
   // double-float (hi, lo) float pairs of P, C_hat, S, E for the HDG_DF32 assembly
   float *P_df = nullptr, *Chat_df = nullptr, *S_df = nullptr, *E_df = nullptr;
   float *sfAA_df = nullptr, *sfBB_df = nullptr, *sfCC_df = nullptr;  // sum-factorisation tables
+  float *G1_df = nullptr, *Shat1_df = nullptr;  // double-float postprocess tables
   int16_t *sfp2to1 = nullptr, *sfp3to2 = nullptr;
   int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
   int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices

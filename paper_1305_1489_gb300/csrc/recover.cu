@@ -533,19 +533,165 @@ __global__ void __launch_bounds__(NT) postprocess_kernel(
   if (tid == 0 && s_bad) atomicAdd(status + 2, 1);
 }
 
+// The same postprocess in double-float on the FP32 pipe (after a double-float assembly):
+// geometry from the per-mesh table, the stiffness and right-hand side by compensated sums,
+// the Cholesky factorisation block-wide (group_cholesky_df: reciprocal square roots by
+// Newton-Raphson, no FP64), the two triangular solves by one warp with every pending entry an
+// unnormalised accumulator; inputs and results cross to and from FP64 once.
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) postprocess_df_kernel(
+    const double* __restrict__ geo, const double* __restrict__ kappa, const df* __restrict__ P,
+    const df* __restrict__ G1, const df* __restrict__ Shat1, const double* __restrict__ w,
+    const int16_t* __restrict__ pairs1, const double* __restrict__ q, const double* __restrict__ u,
+    int64_t nelt, double* __restrict__ ustar, int32_t* status) {
+  using D = Dims<K>;
+  constexpr int n = D::n, nq = D::nq, n1 = D::n1, nr = n1 - 1, NA = (nr + 31) / 32;
+  constexpr int NP = nr * (nr + 1) / 2;
+  __shared__ df Ks[nr * nr], rhs[nr], invd[nr], rpart[6 * nr];
+  __shared__ df qs[3 * n], Qs[3 * nq];
+  __shared__ df s_a[3][3], s_g[6];
+  __shared__ int s_bad;
+  const int64_t Ke = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* ge = geo + Ke * kGeoStride;
+  if (tid < 9) s_a[tid / 3][tid % 3] = df_from_double(ge[tid]);
+  if (tid >= 32 && tid < 38) {  // g_c = sum_* a_{*#} a_{*%} / det for (#, %) = xx, xy, xz, yy, yz, zz
+    const int c = tid - 32;
+    const int p0 = c < 3 ? 0 : c < 5 ? 1 : 2, p1 = c < 3 ? c : c < 5 ? c - 2 : 2;
+    double s = 0.0;
+    for (int st = 0; st < 3; ++st) s += ge[3 * st + p0] * ge[3 * st + p1];
+    s_g[c] = df_from_double(s / ge[26]);
+  }
+  if (tid == 0) s_bad = 0;
+  for (int t = tid; t < 3 * n; t += NT) qs[t] = df_from_double(q[Ke * 3 * n + t]);
+  __syncthreads();
+  // Q_#(p) = omega kappa^-1 sum_* a_{*#} q_*(p) at each node
+  for (int p = tid; p < nq; p += NT) {
+    dacc qh[3] = {dacc_zero(), dacc_zero(), dacc_zero()};
+    for (int i = 0; i < n; ++i) {
+      const df pv = P[p * n + i];
+      dacc_mac(qh[0], qs[i], pv);
+      dacc_mac(qh[1], qs[n + i], pv);
+      dacc_mac(qh[2], qs[2 * n + i], pv);
+    }
+    const df q0 = dacc_result(qh[0]), q1 = dacc_result(qh[1]), q2 = dacc_result(qh[2]);
+    const df wk = df_from_double(w[p] / kappa[Ke * nq + p]);
+    for (int h = 0; h < 3; ++h) {
+      dacc s = dacc_zero();
+      dacc_mac(s, s_a[0][h], q0);
+      dacc_mac(s, s_a[1][h], q1);
+      dacc_mac(s, s_a[2][h], q2);
+      Qs[h * nq + p] = df_mul(wk, dacc_result(s));
+    }
+  }
+  // reduced stiffness (indices 1..n1-1)
+  for (int t = tid; t < NP; t += NT) {
+    const int i = pairs1[2 * t], j = pairs1[2 * t + 1];  // 0-based into 1..n1-1
+    const int I = i + 1, J = j + 1;
+    dacc s = dacc_zero();
+    for (int c = 0; c < 6; ++c) {
+      const df sij = Shat1[(c * n1 + I) * n1 + J];
+      const bool diag = (c == 0 || c == 3 || c == 5);
+      dacc_mac(s, s_g[c], diag ? sij : df_add(sij, Shat1[(c * n1 + J) * n1 + I]));
+    }
+    const df v = dacc_result(s);
+    Ks[i * nr + j] = v;
+    Ks[j * nr + i] = v;
+  }
+  __syncthreads();
+  constexpr int half = (nq + 1) / 2;
+  for (int t = tid; t < 6 * nr; t += NT) {
+    const int hh = t / (2 * nr), rem = t - hh * 2 * nr, part = rem / nr, i = rem - part * nr;
+    const int p0 = part * half, p1 = part ? nq : half;
+    dacc s = dacc_zero();
+    for (int p = p0; p < p1; ++p) dacc_mac(s, Qs[hh * nq + p], G1[(hh * nq + p) * n1 + i + 1]);
+    rpart[t] = dacc_result(s);
+  }
+  __syncthreads();
+  for (int i = tid; i < nr; i += NT) {
+    dacc s = dacc_zero();
+    for (int hh = 0; hh < 3; ++hh) {
+      dacc_add(s, rpart[hh * 2 * nr + i]);
+      dacc_add(s, rpart[hh * 2 * nr + nr + i]);
+    }
+    rhs[i] = df_mul(dacc_result(s), df_from_double(-1.0 / 6.0));
+  }
+  __syncthreads();
+  const bool ok = group_cholesky_df<nr, NT>(Ks, invd, pairs1, tid);
+  if (!ok && tid == 0) s_bad = 1;
+  __syncthreads();
+  // L y = rhs, L^T x = y by one warp, column-oriented; lane l owns rows l and l + 32
+  if (warp == 0) {
+    dacc x[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int l = lane + 32 * a;
+      x[a] = l < nr ? dacc_from(rhs[l]) : dacc_zero();
+    }
+    for (int i = 0; i < nr; ++i) {
+      df xi = df_make(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < NA; ++a)
+        if ((i >> 5) == a) xi = shfl_df(dacc_result(x[a]), i & 31);
+      xi = df_mul(xi, invd[i]);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        const int l = lane + 32 * a;
+        if (l > i && l < nr) dacc_msub(x[a], Ks[l * nr + i], xi);
+        else if (l == i) x[a] = dacc_from(xi);
+      }
+    }
+    for (int i = nr - 1; i >= 0; --i) {
+      df xi = df_make(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < NA; ++a)
+        if ((i >> 5) == a) xi = shfl_df(dacc_result(x[a]), i & 31);
+      xi = df_mul(xi, invd[i]);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        const int l = lane + 32 * a;
+        if (l < i) dacc_msub(x[a], Ks[i * nr + l], xi);
+        else if (l == i) x[a] = dacc_from(xi);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const int l = lane + 32 * a;
+      if (l < nr) ustar[Ke * n1 + 1 + l] = df_to_double(dacc_result(x[a]));
+    }
+    if (lane == 0) ustar[Ke * n1] = u[Ke * n];
+  }
+  if (tid == 0 && s_bad) atomicAdd(status + 2, 1);
+}
+
 cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar) {
   const unsigned g = (unsigned)M->nelt;
 #define HDG_PP(KK, NTT)                                                                             \
   postprocess_kernel<KK, NTT><<<g, NTT, 0, M->stream>>>(M->d_vx, M->kappa, M->dt.P, M->dt.G1,      \
                                                        M->dt.Shat1, M->dt.vol_w, M->dt.pairs_n1, q, \
                                                        u, M->nelt, ustar, M->d_status)
-  switch (M->k) {
-    case 1: HDG_PP(1, 64); break;
-    case 2: HDG_PP(2, 64); break;
-    case 3: HDG_PP(3, 128); break;
-    case 4: HDG_PP(4, 128); break;
-    default: return cudaErrorInvalidValue;
+#define HDG_PPDF(KK, NTT)                                                                              \
+  postprocess_df_kernel<KK, NTT><<<g, NTT, 0, M->stream>>>(                                             \
+      M->d_geo, M->kappa, reinterpret_cast<const df*>(M->dt.P_df), reinterpret_cast<const df*>(M->dt.G1_df), \
+      reinterpret_cast<const df*>(M->dt.Shat1_df), M->dt.vol_w, M->dt.pairs_n1, q, u, M->nelt, ustar, M->d_status)
+  if (M->rec_df) {  // after a double-float assembly: the double-float postprocess
+    switch (M->k) {
+      case 1: HDG_PPDF(1, 64); break;
+      case 2: HDG_PPDF(2, 64); break;
+      case 3: HDG_PPDF(3, 128); break;
+      case 4: HDG_PPDF(4, 128); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (M->k) {
+      case 1: HDG_PP(1, 64); break;
+      case 2: HDG_PP(2, 64); break;
+      case 3: HDG_PP(3, 128); break;
+      case 4: HDG_PP(4, 128); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
+#undef HDG_PPDF
 #undef HDG_PP
   M->launches++;
   return cudaGetLastError();

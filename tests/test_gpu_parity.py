@@ -175,6 +175,9 @@ def test_double_float_assembly(k, s, shape, monkeypatch):
     q1, u1 = M2.recover(torch.from_numpy(ref["uhat"]).cuda())
     assert rel(u1.cpu().numpy(), ref["u"]) < 1e-11
     assert rel(q1.cpu().numpy(), ref["q"]) < 1e-11
+    # the double-float postprocess (it follows a double-float assembly) from the oracle's q, u
+    us = M2.postprocess(torch.from_numpy(ref["q"]).cuda(), torch.from_numpy(ref["u"]).cuda())
+    assert rel(us.cpu().numpy(), ref["ustar"]) < 1e-11
     uhat, it, rr = M2.solve_trace(rtol=1e-14, maxit=5000)
     assert rel(uhat.cpu().numpy(), ref["uhat"]) < 1e-11
 
