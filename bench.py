@@ -45,9 +45,10 @@ FP64_MEASURED_TFLOPS = 1.19  # FMA-chain microbenchmark on this machine's GB300 (1 
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one K1 launch at this workload,
-# from the ncu captures summarised under profiles/, valid while the kernel source is unchanged.
-K1_TRAFFIC = {"assemble_df.cu": {"sha256": "60991e4087b1825badc370f5ffa26633b461f005ab25a93cdc44c5d82d083bbd",
-                                 "bytes": 79856896 + 901217280},
+# from the ncu captures summarised under profiles/, valid while the kernel's sources (K1_SOURCES,
+# hashed together) are unchanged.
+K1_TRAFFIC = {"assemble_df.cu": {"sha256": "957b7963cd4e158eb2ffb756698557867a8bbfada4a45fca4abe240405bc4db3",
+                                 "bytes": 79899392 + 901170944},
               "assemble.cu": {"sha256": None, "bytes": None}}
 
 
@@ -87,9 +88,17 @@ def k1_bytes_per_element(k):
     return 8 * (3 * nq + 12) + 4 * 4 + 8 * (m * m + m + rec)
 
 
-def _sha(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+def _sha(*paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+# the sources of each K1 translation unit (the kernel and the device headers it includes)
+K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "device_df.cuh", "device_common.cuh"),
+              "assemble.cu": ("assemble.cu", "device_common.cuh")}
 
 
 # ------------------------------------------------------------------ clocks
@@ -419,7 +428,7 @@ def run_gpu(args, rank, world, local_rank):
     flops = flops_per_element_k1(prob.k) * nelt
     achieved = flops / (k1_ms / 1e3) / 1e12
     k1_src = "assemble_df.cu" if args.asm == "df32" else "assemble.cu"
-    sha = _sha(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", k1_src))
+    sha = _sha(*(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", f) for f in K1_SOURCES[k1_src]))
     trec = K1_TRAFFIC.get(k1_src, {})
     traffic = trec.get("bytes") if trec.get("sha256") == sha else None
     df = args.asm == "df32"
