@@ -369,7 +369,10 @@ int64_t hdg_launch_count(const hdg_mesh* mesh);
  *   vol_pts [nq][3], vol_w [nq], P [nq][n], Pd [3][nq][n], Chat [3][n][n] (eq. 3.5-3.7),
  *   face_pts [nf][2], face_w [nf], Pl [4][nf][n], D [nf][d2], Dmu [6][nf][d2] (eq. 4.4, 4.7),
  *   S [4][n][n] (eq. 4.5 pieces), E [4][6][d2][n] (eq. 4.10 pieces),
- *   P1 [nq][n1], G1 [3][nq][n1], Shat1 [6][n1][n1] (degree k+1, eq. 9.11).
+ *   P1 [nq][n1], G1 [3][nq][n1], Shat1 [6][n1][n1] (degree k+1, eq. 9.11); the sum-
+ *   factorisation tables of the volume masses: sfAA [np1][k+2], sfBB [np2][k+2],
+ *   sfCC [n(n+1)/2][k+2] (pair products of the collapsed-coordinate factors of the basis),
+ *   sfp2to1 [np2] and sfp3to2 [n(n+1)/2] (pair maps, as doubles).
  * hdg_host_expand_mesh: the expanded mesh of Section 2 on the host.  faces needs room for
  *   4 nelt rows of 4 (nfc <= 4 nelt), facebyele and perm [nelt][4]; *nfc receives the count. */
 int hdg_host_table(int k, const char* name, double* out, int64_t capacity, int64_t* size);

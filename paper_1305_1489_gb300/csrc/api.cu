@@ -422,7 +422,16 @@ int hdg_host_table(int k, const char* name, double* out, int64_t capacity, int64
   else if (s == "P1") v = &T.P1;
   else if (s == "G1") v = &T.G1;
   else if (s == "Shat1") v = &T.Shat1;
-  else return fail(HDG_ERR_ARG, "unknown table " + s);
+  else if (s == "sfAA") v = &T.sfAA;
+  else if (s == "sfBB") v = &T.sfBB;
+  else if (s == "sfCC") v = &T.sfCC;
+  std::vector<double> conv;  // the int16 pair maps, returned as doubles
+  if (s == "sfp2to1" || s == "sfp3to2") {
+    const std::vector<int16_t>& src = (s == "sfp2to1") ? T.sfp2to1 : T.sfp3to2;
+    conv.assign(src.begin(), src.end());
+    v = &conv;
+  }
+  if (!v) return fail(HDG_ERR_ARG, "unknown table " + s);
   *size = (int64_t)v->size();
   if (out) {
     if (capacity < *size) return fail(HDG_ERR_ARG, "capacity too small");

@@ -69,6 +69,28 @@ def test_host_tables_match_oracle(lib, k):
     assert np.abs(_table(lib, k, "G1").reshape(3, -1, n1) - basis.dubiner3_grad(k + 1, tab.p)).max() < 1e-11
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_host_sum_factorisation_reproduces_oracle_masses(lib, k):
+    """The library's sum-factorisation tables, summed in three passes as the double-float K1
+    does, give the oracle's direct quadrature sum_q g_q P_a P_b for an arbitrary weight g."""
+    tab = ohdg.Tables(k)
+    n, d2, nn = tab.n, tab.d2, k + 2
+    AA = _table(lib, k, "sfAA").reshape(-1, nn)
+    BB = _table(lib, k, "sfBB").reshape(-1, nn)
+    CC = _table(lib, k, "sfCC").reshape(-1, nn)
+    p2to1 = _table(lib, k, "sfp2to1").astype(int)
+    p3to2 = _table(lib, k, "sfp3to2").astype(int)
+    assert AA.shape[0] == (k + 1) * (k + 2) // 2 and BB.shape[0] == d2 * (d2 + 1) // 2
+    assert CC.shape[0] == n * (n + 1) // 2
+    g = np.random.default_rng(k).uniform(0.5, 2.0, size=tab.nq).reshape(nn, nn, nn)  # [i, j, l]
+    T1 = np.einsum("ijl,pl->pij", g, AA)
+    T2 = np.einsum("pj,pij->pi", BB, T1[p2to1])
+    lib_mass = np.einsum("ti,ti->t", CC, T2[p3to2])
+    ia, ib = np.triu_indices(n)  # the row-major (a <= b) order of the 3-D pairs
+    ref = np.einsum("q,qt,qt->t", g.ravel(), tab.P[:, ia], tab.P[:, ib])
+    assert np.abs(lib_mass - ref).max() < 1e-12 * np.abs(ref).max()
+
+
 def _expand(lib, c, e, d, nn):
     nelt = len(e)
     nfc = C.c_int64(0)
