@@ -275,8 +275,8 @@ int hdg_get_condensed(const hdg_mesh* M, double* C, double* Cf) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (!M->assembled) return fail(HDG_ERR_STATE, "not assembled");
   const int m = M->tab.m;
-  (void)m;
-  if (C) HDG_CUDA_TRY(launch_unblock(const_cast<hdg_mesh*>(M), M->d_C, C));  // stored row-major
+  if (C)  // stored row-major [K][r][s], the layout of the output
+    HDG_CUDA_TRY(cudaMemcpyAsync(C, M->d_C, sizeof(double) * M->nelt * m * m, cudaMemcpyDeviceToDevice, M->stream));
   if (Cf) HDG_CUDA_TRY(cudaMemcpyAsync(Cf, M->d_Cf, sizeof(double) * M->nelt * m, cudaMemcpyDeviceToDevice, M->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
   return HDG_OK;

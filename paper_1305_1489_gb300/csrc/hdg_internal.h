@@ -162,7 +162,6 @@ constexpr int kGeoStride = 28;  // doubles per element of d_geo (26 used; 224 by
 cudaError_t launch_geometry(hdg_mesh* M);
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u);
 cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double* Z);
-cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst);
 cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar);
 int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double* x0,
                 double* uhat, int* iters, double* relres);

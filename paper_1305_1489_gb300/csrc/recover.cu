@@ -93,22 +93,6 @@ cudaError_t launch_element_face_nodes(hdg_mesh* M, double* X, double* Y, double*
   return cudaGetLastError();
 }
 
-// copy of the stored C^K (already row-major [K][l d2 + a][s]) for the caller
-__global__ void unblock_kernel(const double* __restrict__ src, double* __restrict__ dst, int64_t nelt, int m, int d2) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  (void)d2;
-  if (t >= nelt * m * m) return;
-  dst[t] = src[t];
-}
-
-cudaError_t launch_unblock(hdg_mesh* M, const double* src, double* dst) {
-  const int m = M->tab.m;
-  const int64_t tot = M->nelt * m * m;
-  unblock_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, M->stream>>>(src, dst, M->nelt, m, M->tab.d2);
-  M->launches++;
-  return cudaGetLastError();
-}
-
 // ----------------------------------------------------------------------- recovery
 // u = U_s^-1 (H u_dK + h);  q_* = U_M^-1 (W_* u - V (n_* o u_dK))   (eq. 5.3 through the
 // factors of K1: S_u = U_s^T U_s, or L U_s with convection, and M_{kappa^-1} = U_M^T U_M; H, h,
