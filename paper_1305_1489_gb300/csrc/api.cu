@@ -123,7 +123,7 @@ int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, in
   *out = nullptr;
   if (!coords || !elems || nver < 4 || nelt < 1 || ndir < 0 || nneu < 0 || (ndir && !dir) || (nneu && !neu))
     return fail(HDG_ERR_ARG, "invalid mesh arrays or sizes");
-  if (k < 1 || k > 4) return fail(HDG_ERR_UNSUPPORTED, "degree k must be in 1..4");
+  if (k < 0 || k > 4) return fail(HDG_ERR_UNSUPPORTED, "degree k must be in 0..4");
   if (nelt > (int64_t)1 << 30) return fail(HDG_ERR_ARG, "too many elements");
   hdg_mesh* M = new (std::nothrow) hdg_mesh();
   if (!M) return fail(HDG_ERR_ARG, "out of host memory");
@@ -253,6 +253,8 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
     return fail(HDG_ERR_UNSUPPORTED, "the double-float assembly covers reaction-diffusion (beta = 0)");
   if (M->beta_q && M->method == HDG_METHOD_BDM)
     return fail(HDG_ERR_UNSUPPORTED, "the BDM element is built for reaction-diffusion (beta = 0)");
+  if (M->k == 0 && (M->beta_q || M->method == HDG_METHOD_BDM))
+    return fail(HDG_ERR_UNSUPPORTED, "k = 0 is built for the HDG method without convection");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   M->assembled = true;

@@ -435,6 +435,7 @@ cudaError_t launch_assemble(hdg_mesh* M) {
   a.nelt = M->nelt;
   const bool conv = M->beta_q != nullptr;
   switch (M->k) {
+    case 0: return conv ? cudaErrorInvalidValue : launch_k<0, false>(M, a);
     case 1: return conv ? launch_k<1, true>(M, a) : launch_k<1, false>(M, a);
     case 2: return conv ? launch_k<2, true>(M, a) : launch_k<2, false>(M, a);
     case 3: return conv ? launch_k<3, true>(M, a) : launch_k<3, false>(M, a);
@@ -445,6 +446,7 @@ cudaError_t launch_assemble(hdg_mesh* M) {
 
 int64_t rec_stride_of(int k) {
   switch (k) {
+    case 0: return Dims<0>::rec;
     case 1: return Dims<1>::rec;
     case 2: return Dims<2>::rec;
     case 3: return Dims<3>::rec;

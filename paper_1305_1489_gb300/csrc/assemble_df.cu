@@ -414,9 +414,10 @@ static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
   return launch_df_shape<K, 0>(M, a);
 }
 
-int k1_variants(int k) { return k >= 3 ? 3 : 2; }
+int k1_variants(int k) { return k == 0 ? 1 : k >= 3 ? 3 : 2; }
 int k1_threads(int k, int variant) {
   switch (k) {
+    case 0: return K1Occupancy<0>::NT;  // k = 0 runs the FP64 kernel
     case 1: return variant ? K1Shape<1, 1>::NT : K1Shape<1, 0>::NT;
     case 2: return variant ? K1Shape<2, 1>::NT : K1Shape<2, 0>::NT;
     case 3: return variant == 2 ? K1Shape<3, 2>::NT : variant ? K1Shape<3, 1>::NT : K1Shape<3, 0>::NT;
@@ -451,6 +452,7 @@ cudaError_t launch_geometry(hdg_mesh* M) {
 }
 
 cudaError_t launch_assemble_df(hdg_mesh* M) {
+  if (M->k == 0) return launch_assemble(M);  // k = 0: the FP64 kernel (d3 = 1, nothing to gain)
   M->rec_df = true;
   AsmDfArgs a;
   a.geo = M->d_geo;

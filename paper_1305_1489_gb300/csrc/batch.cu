@@ -73,7 +73,7 @@ int hdg_batch_create(int nprob, const double* const* coords, const int64_t* nver
     std::vector<int> ids;
     for (int p = 0; p < nprob; ++p) {
       if (k[p] < 1 || k[p] > 4) {
-        rc = fail(HDG_ERR_UNSUPPORTED, "degree k must be in 1..4");
+        rc = fail(HDG_ERR_UNSUPPORTED, "batched degrees must be in 1..4");
         break;
       }
       if (k[p] == kk) ids.push_back(p);

@@ -486,6 +486,7 @@ int coarse_launch_build(hdg_mesh* M) {
                                                                M->d_fverts, M->d_Tproj, c->vnodes, c->vwd,     \
                                                                c->elist, c->eslot, c->lv[0].val)
   switch (M->tab.d2) {
+    case 1: HDG_GAL(1); break;
     case 3: HDG_GAL(3); break;
     case 6: HDG_GAL(6); break;
     case 10: HDG_GAL(10); break;

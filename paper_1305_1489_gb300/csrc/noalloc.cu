@@ -443,5 +443,6 @@ int solve(hdg_mesh* M, double rtol, int maxit, const double* x0, double* uhat, i
 extern "C" int hdg_solve_trace_noalloc(hdg_mesh* mesh, double rtol, int maxit, const double* x0, double* uhat,
                                        int* iters, double* relres) {
   if (!mesh) return hdg::fail(HDG_ERR_ARG, "NULL mesh");
+  if (mesh->tab.d2 < 3) return hdg::fail(HDG_ERR_UNSUPPORTED, "the allocation-free solve is built for k >= 1");
   return hdg::noalloc::solve(mesh, rtol, maxit, x0, uhat, iters, relres);
 }

@@ -43,16 +43,17 @@ __global__ void __launch_bounds__(NT) projection_kernel(const double* __restrict
     mu[tid] = perm[Ke * 4 + tid] - 1;
   }
   if (tid == 0) s_bad = 0;
-  // low coefficients: (v, P_i)_K / |K| for i < n - d2
-  for (int t = tid; t < 4 * nlow; t += NT) {
-    const int c = t / nlow, i = t - c * nlow;
-    const double* v = (c < 3 ? q_vol + ((int64_t)c * nelt + Ke) * nq : u_vol + Ke * nq);
-    double s = 0.0;
-    for (int qn = 0; qn < nq; ++qn) s = fma(w[qn] * v[qn], P[qn * n + i], s);
-    low[c][i] = s;
-    if (c < 3) Pq[(Ke * 3 + c) * n + i] = s;
-    else Pu[Ke * n + i] = s;
-  }
+  // low coefficients: (v, P_i)_K / |K| for i < n - d2 (none at k = 0: those rows are void)
+  if constexpr (nlow > 0)
+    for (int t = tid; t < 4 * nlow; t += NT) {
+      const int c = t / nlow, i = t - c * nlow;
+      const double* v = (c < 3 ? q_vol + ((int64_t)c * nelt + Ke) * nq : u_vol + Ke * nq);
+      double s = 0.0;
+      for (int qn = 0; qn < nq; ++qn) s = fma(w[qn] * v[qn], P[qn * n + i], s);
+      low[c][i] = s;
+      if (c < 3) Pq[(Ke * 3 + c) * n + i] = s;
+      else Pu[Ke * n + i] = s;
+    }
   __syncthreads();
   // (q.N_l + T_l u) at the element-local face nodes
   for (int t = tid; t < 4 * nf; t += NT) {
@@ -151,6 +152,7 @@ cudaError_t launch_projection(hdg_mesh* M, const double* q_vol, const double* u_
                                                        M->dt.E, M->dt.Dmu, M->dt.face_w, q_vol, u_vol, q_face, \
                                                        u_face, M->nelt, Pq, Pu, M->d_status)
   switch (M->k) {
+    case 0: HDG_PJ(0, 64); break;
     case 1: HDG_PJ(1, 64); break;
     case 2: HDG_PJ(2, 64); break;
     case 3: HDG_PJ(3, 128); break;

@@ -379,6 +379,7 @@ cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u
   if (M->rec_df) e = launch_recover_df<KK>(M, uhat, q, u); \
   else recover_kernel<KK><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u)
   switch (M->k) {
+    case 0: HDG_REC(0); break;
     case 1: HDG_REC(1); break;
     case 2: HDG_REC(2); break;
     case 3: HDG_REC(3); break;
@@ -668,6 +669,7 @@ cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, do
     }
   } else {
     switch (M->k) {
+      case 0: HDG_PP(0, 64); break;
       case 1: HDG_PP(1, 64); break;
       case 2: HDG_PP(2, 64); break;
       case 3: HDG_PP(3, 128); break;

@@ -1645,6 +1645,7 @@ int batch_record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, int so
                        double* uhat, cudaGraphNode_t* last) {
   const int sp = solve_precision;
   switch (M->tab.d2) {
+    case 1: return record_group<1>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
     case 3: return record_group<3>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
     case 6: return record_group<6>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
     case 10: return record_group<10>(M, graph, asm_precision, sp, face_prob, np, norms, rtol, maxit, q, u, uhat, last);
@@ -1670,6 +1671,7 @@ int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double
   if (precision != HDG_FP64 && precision != HDG_MIXED_FP32) return fail(HDG_ERR_ARG, "unknown precision");
   if (!(rtol > 0) || maxit < 1 || !uhat) return fail(HDG_ERR_ARG, "bad rtol/maxit/uhat");
   switch (M->tab.d2) {
+    case 1: return Solver<1>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
     case 3: return Solver<3>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
     case 6: return Solver<6>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
     case 10: return Solver<10>::solve(M, precision, rtol, maxit, x0, uhat, iters, relres);
@@ -1681,6 +1683,7 @@ int solve_trace(hdg_mesh* M, int precision, double rtol, int maxit, const double
 int trace_apply(hdg_mesh* M, const double* x, double* y) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "operator before hdg_assemble_condense");
   switch (M->tab.d2) {
+    case 1: return Solver<1>::apply(M, x, y);
     case 3: return Solver<3>::apply(M, x, y);
     case 6: return Solver<6>::apply(M, x, y);
     case 10: return Solver<10>::apply(M, x, y);
@@ -1692,6 +1695,7 @@ int trace_apply(hdg_mesh* M, const double* x, double* y) {
 int autotune_face_grid(hdg_mesh* M, hdg_tuning* out) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "autotune before hdg_assemble_condense");
   switch (M->tab.d2) {
+    case 1: return Solver<1>::autotune(M, out);
     case 3: return Solver<3>::autotune(M, out);
     case 6: return Solver<6>::autotune(M, out);
     case 10: return Solver<10>::autotune(M, out);
@@ -1705,6 +1709,7 @@ int coarse_precond_apply(hdg_mesh* M, const double* r, double* z) {
   if (!M->coarse) return fail(HDG_ERR_STATE, "no coarse space: call hdg_set_coarse_space first");
   if (M->beta_q) return fail(HDG_ERR_UNSUPPORTED, "the two-level preconditioner is for beta = 0");
   switch (M->tab.d2) {
+    case 1: return Solver<1>::precond_apply(M, r, z);
     case 3: return Solver<3>::precond_apply(M, r, z);
     case 6: return Solver<6>::precond_apply(M, r, z);
     case 10: return Solver<10>::precond_apply(M, r, z);
@@ -1716,6 +1721,7 @@ int coarse_precond_apply(hdg_mesh* M, const double* r, double* z) {
 int trace_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, double* bnorm) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "residual before hdg_assemble_condense");
   switch (M->tab.d2) {
+    case 1: return Solver<1>::residual(M, x, r, rnorm, bnorm);
     case 3: return Solver<3>::residual(M, x, r, rnorm, bnorm);
     case 6: return Solver<6>::residual(M, x, r, rnorm, bnorm);
     case 10: return Solver<10>::residual(M, x, r, rnorm, bnorm);

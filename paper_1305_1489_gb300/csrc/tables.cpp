@@ -155,8 +155,8 @@ void F_mu(int mu, double s, double t, double* so, double* to) {
 }  // namespace
 
 bool build_tables(int k, Tables* T, std::string* err) {
-  if (k < 1 || k > 4) {
-    *err = "degree k must be in 1..4";
+  if (k < 0 || k > 4) {
+    *err = "degree k must be in 0..4";
     return false;
   }
   const int nn = k + 2;

@@ -67,7 +67,7 @@ def test_quadrature_nodes(k):
     assert np.array_equal(perm, mesh.perm)
 
 
-@pytest.mark.parametrize("k,s", [(1, 4), (2, 2), (3, 2), (4, 1)])
+@pytest.mark.parametrize("k,s", [(0, 3), (1, 4), (2, 2), (3, 2), (4, 1)])
 def test_end_to_end(k, s):
     prob = _varprob(k)
     c, e, d, n = make_mesh(prob, s=s)
@@ -147,7 +147,7 @@ def test_error_paths():
     assert ei.value.code == 2
 
 
-@pytest.mark.parametrize("k,s,shape", [(1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (3, 2, "0"), (3, 2, "1"),
+@pytest.mark.parametrize("k,s,shape", [(0, 3, "0"), (1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (3, 2, "0"), (3, 2, "1"),
                                      (3, 2, "2"), (4, 1, "0"), (4, 2, "1"), (4, 1, "2")])
 def test_double_float_assembly(k, s, shape, monkeypatch):
     """HDG_DF32: the same condensation in double-float arithmetic on the FP32 pipe, for every

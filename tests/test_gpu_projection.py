@@ -33,7 +33,7 @@ def _oracle_inputs(mesh, tab, prob):
     return np.stack(prob.q(X, Y, Z)), prob.u(X, Y, Z), np.stack(prob.q(FX, FY, FZ)), prob.u(FX, FY, FZ)
 
 
-@pytest.mark.parametrize("k,s", [(1, 3), (2, 2), (3, 2), (4, 1)])
+@pytest.mark.parametrize("k,s", [(0, 3), (1, 3), (2, 2), (3, 2), (4, 1)])
 def test_projection_parity(k, s):
     prob = get_problem("cube16_k3").at(k=k)
     c, e, d, n = make_mesh(prob, s=s, jitter=0.15, seed=3)

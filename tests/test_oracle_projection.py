@@ -42,7 +42,7 @@ def _inputs(mesh, tab, qf, uf):
     return q_vol, uf(X, Y, Z), q_face, uf(FX, FY, FZ)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
 def test_projection_reproduces_polynomials_of_degree_k(k):
     rng = np.random.default_rng(10 + k)
     mesh = _mesh(2)

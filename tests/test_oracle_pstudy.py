@@ -1,7 +1,7 @@
 """The p-study of the paper's last experiment (eq. 10.3, Table 4) on the oracle: on a fixed
 mesh, the relative errors of eq. 10.1 decay geometrically in k for a smooth solution, so
 log(e_k / e_{k+1}) / log(e_{k+1} / e_{k+2}) is close to 1 (Table 4: 0.78 to 1.13).  Degrees
-1..4 (k = 0 is not built)."""
+0..4."""
 import numpy as np
 import pytest
 
@@ -17,12 +17,12 @@ def p_ratios(errs, key):
 @pytest.mark.parametrize("s", [2, 3])
 def test_p_convergence_ratios(s):
     errs = []
-    for k in (1, 2, 3, 4):
+    for k in (0, 1, 2, 3, 4):
         prob = get_problem("cube4_k1").at(s=s, k=k)
         r = hdg.solve_problem(prob)
         errs.append(hdg.errors(r["mesh"], k, r["q"], r["u"], r["uhat"], r["ustar"], prob))
     for key in ("e_q", "e_u", "e_uhat"):
         e = [x[key] for x in errs]
-        assert all(e[i + 1] < 0.35 * e[i] for i in range(3)), (key, e)
+        assert all(e[i + 1] < 0.45 * e[i] for i in range(4)), (key, e)
         for ratio in p_ratios(errs, key):
             assert 0.7 < ratio < 1.3, (key, ratio)
