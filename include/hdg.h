@@ -47,7 +47,7 @@ typedef enum {
   HDG_ERR_LOCAL_SINGULAR = 6,  /* a local factorisation met a non-positive pivot           */
   HDG_ERR_NOT_CONVERGED = 7,   /* the trace solve hit maxit before the tolerance            */
   HDG_ERR_COEFF = 8,           /* kappa <= 0 or c < 0 or a non-finite coefficient value     */
-  HDG_ERR_UNSUPPORTED = 9      /* option not built (e.g. degree outside 1..4)               */
+  HDG_ERR_UNSUPPORTED = 9      /* option not built (e.g. degree outside 0..4)               */
 } hdg_status;
 
 typedef enum {
@@ -74,7 +74,9 @@ typedef struct {
 /* Build the expanded mesh (Section 2: faces, facebyele, perm, normals) from the basic one.
  *   coords [nver][3] host f64; elems [nelt][4] host int32, positively oriented;
  *   dir [ndir][3], neu [nneu][3] host int32 vertex triples (any order within a triple).
- *   k in 1..4.  stream: cudaStream_t to use (NULL = legacy default stream).
+ *   k in 0..4 (k = 0: the HDG method without convection; batches, the BDM element and
+ *   hdg_solve_trace_noalloc need k >= 1).  stream: cudaStream_t to use (NULL = legacy
+ *   default stream).
  * The library copies what it needs; the caller's arrays may be freed on return.
  * Every boundary face must be listed exactly once in dir or neu (Gamma = Gamma_D U Gamma_N).
  * Errors: HDG_ERR_ARG, HDG_ERR_ORIENTATION, HDG_ERR_NONCONFORMING, HDG_ERR_CUDA.          */
