@@ -26,3 +26,15 @@ def test_p_convergence_ratios(s):
         assert all(e[i + 1] < 0.45 * e[i] for i in range(4)), (key, e)
         for ratio in p_ratios(errs, key):
             assert 0.7 < ratio < 1.3, (key, ratio)
+
+
+def test_k0_converges_like_h():
+    """k = 0: the errors of eq. 10.1 decay like h (the paper's remark on k = 0)."""
+    errs = []
+    for s in (4, 8):
+        prob = get_problem("cube4_k1").at(s=s, k=0)
+        r = hdg.solve_problem(prob)
+        errs.append(hdg.errors(r["mesh"], 0, r["q"], r["u"], r["uhat"], r["ustar"], prob))
+    for key in ("e_q", "e_u", "e_uhat"):
+        rate = np.log2(errs[0][key] / errs[1][key])
+        assert abs(rate - 1.0) < 0.25, (key, rate)
