@@ -103,9 +103,10 @@ K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "device_df.cuh", "device_comm
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+    """nvidia-smi sampling (every 100 ms, started before the warm-up so that it is running when
+    the timed region starts); only the samples stamped inside the timed region are kept."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -121,27 +122,46 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    def stop(self, t_begin=None, t_end=None):
+        """Summary of the samples stamped within [t_begin, t_end] (epoch seconds, 0.1 s slack);
+        all samples if none falls inside."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
-        sm, mx, reasons = [], [], set()
+        return self.summarise(out, t_begin, t_end)
+
+    @staticmethod
+    def summarise(out, t_begin=None, t_end=None):
+        import datetime
+
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
+            if len(p) < 10:
                 continue
             try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
+                sm, mx = float(p[2]), float(p[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, p[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+            try:  # nvidia-smi stamps local time, e.g. 2026/12/04 04:05:15.159
+                ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, sm, mx, {nm for nm, v in zip(names, p[6:10]) if v.lower() == "active"}))
+        inside = rows
+        window = "all samples"
+        if t_begin is not None and t_end is not None:
+            sel = [r for r in rows if r[0] is not None and t_begin - 0.1 <= r[0] <= t_end + 0.1]
+            if sel:
+                inside, window = sel, "timed region"
+            else:
+                window = "all samples (none stamped inside the timed region)"
+        reasons = set().union(*(r[3] for r in inside)) if inside else set()
+        return {"sm_mhz": float(np.median([r[1] for r in inside])) if inside else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "samples": len(inside), "window": window, "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------------ oracle timing (CPU)
@@ -291,17 +311,19 @@ def run_gpu(args, rank, world, local_rank):
         if rec is not None:
             rec.append((e0, e1, e2, e3, e4, it, rr))
 
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.5)  # nvidia-smi is up and sampling before the timed region
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     recs = []
     launches0 = M.launches
-    clk = ClockSampler(local_rank)
-    clk.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    tw0 = time.time()
     tstart = ev()
     tstart.record(stream)
     for _ in range(args.steps):
@@ -312,7 +334,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t0
-    clocks = clk.stop()
+    clocks = clk.stop(tw0, time.time())
     launches = M.launches - launches0
     total_ms = tstart.elapsed_time(tend)
     t_asm = [a.elapsed_time(b) for a, b, *_ in recs]
@@ -684,7 +706,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-sample", type=int, default=12288, help="oracle elements per step")
