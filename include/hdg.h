@@ -134,7 +134,8 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * C^K = A3 A1^-1 A2 + tauDD (eq. 5.5), C_f^K = A3 A1^-1 A_f (eq. 5.6), and the operators of
  * the local recovery (eq. 5.3), into library-owned device memory.
  * precision: HDG_FP64 (native FP64) or HDG_DF32 (double-float on the FP32 pipe, FP64-level
- * accuracy; reaction-diffusion only).  Synchronises to report
+ * accuracy; reaction-diffusion only; at k = 0 it runs the FP64 kernel).  The precision also
+ * selects that of hdg_recover and hdg_postprocess until the next assembly.  Synchronises to report
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
 
@@ -285,12 +286,14 @@ int hdg_set_inner_tolerance(hdg_mesh* mesh, double rtol);
 int hdg_trace_residual(hdg_mesh* mesh, const double* x, double* r, double* rnorm, double* bnorm);
 
 /* Local recovery (eq. 5.3): q [nelt][3][n], u [nelt][n] device f64 outputs from the trace
- * uhat [nfc][d2] (device f64).                                                            */
+ * uhat [nfc][d2] (device f64); in double-float arithmetic after an HDG_DF32 assembly (a
+ * record copy that never lands, which only a hardware fault could cause, leaves NaN and is
+ * reported by the next assembly as HDG_ERR_CUDA).                                         */
 int hdg_recover(hdg_mesh* mesh, const double* uhat, double* q, double* u);
 
 /* Superconvergent postprocess (eq. 9.11): ustar [nelt][n1] device f64 (coefficients in the
  * degree-(k+1) Dubiner basis) from q, u of hdg_recover; kappa as set by
- * hdg_set_coefficients.                                                                   */
+ * hdg_set_coefficients; in double-float arithmetic after an HDG_DF32 assembly.           */
 int hdg_postprocess(hdg_mesh* mesh, const double* q, const double* u, double* ustar);
 
 /* ------------------------------------------------------------------ projections and error norms
