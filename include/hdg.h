@@ -159,7 +159,8 @@ int hdg_get_condensed(const hdg_mesh* mesh, double* C, double* Cf);
  * convection field is set: the trace matrix is then non-symmetric) to
  *   ||b - H u_hat||_2 <= rtol ||b||_2  (FP64 residual over the free dofs).
  *   precision: HDG_FP64 (plain PCG) or HDG_MIXED_FP32 (FP32 inner PCG, FP64 refinement).
- *   x0: device f64 [nfc][d2] initial guess or NULL (zero start).
+ *   x0: device f64 [nfc][d2] initial guess or NULL (zero start); its entries on Dirichlet faces
+ *   are ignored (u_hat_D enters through the right-hand side), so a previous uhat is a valid guess.
  *   uhat: device f64 [nfc][d2] output; Dirichlet faces receive u_hat_D of eq. 6.3.
  *   iters, relres: host outputs (may be NULL): iterations (inner iterations for the mixed
  *   path) and the final FP64 relative residual.
@@ -179,7 +180,10 @@ int hdg_solve_trace(hdg_mesh* mesh, int precision, double rtol, int maxit, const
  *   make that first call before any stream capture.
  *   All calls share the array and leave their contents in it; the call clears what must
  *   start at zero.  Calls whose GPU work overlaps (other streams or host threads) race.
- * Arguments, outputs and errors as for hdg_solve_trace (x0, uhat device f64 [nfc][d2]).  */
+ * Arguments, outputs and errors as for hdg_solve_trace (x0, uhat device f64 [nfc][d2]; the
+ * Dirichlet entries of x0 are ignored; one restarted pass when the recursive residual has
+ * converged but the true one has not).  It is the symmetric (CG) solve: a mesh with a
+ * convection field returns HDG_ERR_UNSUPPORTED.                                          */
 int hdg_solve_trace_noalloc(hdg_mesh* mesh, double rtol, int maxit, const double* x0,
                             double* uhat, int* iters, double* relres);
 

@@ -327,6 +327,14 @@ __global__ void k_set_scalars(double* scal, double tol2, double maxit) {
   }
 }
 
+// x = x0 on the free faces and 0 on the Dirichlet faces: the Dirichlet values enter through the
+// right-hand side (b = F + G_N - H_{.,D} u_hat_D), so a guess that carries u_hat_D there (a
+// previous solution) must not be applied a second time by the operator.
+__global__ void k_load_x0(int64_t nv, const int32_t* ftype, int d2, const double* __restrict__ x0, double* x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nv) x[t] = (ftype[t / d2] == 1) ? 0.0 : x0[t];
+}
+
 __global__ void k_finish(int64_t nv, const int32_t* ftype, int d2, const double* x, const double* xD, double* uhat) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nv) uhat[t] = (ftype[t / d2] == 1) ? xD[t] : x[t];
@@ -402,35 +410,61 @@ int solve(hdg_mesh* M, double rtol, int maxit, const double* x0, double* uhat, i
   HDG_CUDA_TRY(cudaMemcpyAsync(&bb, scal + S_BB, sizeof(double), cudaMemcpyDeviceToHost, st));
   HDG_CUDA_TRY(cudaStreamSynchronize(st));
   const double bnorm = std::sqrt(bb), tol = rtol * bnorm;
-  if (x0) HDG_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
-  k_set_scalars<<<1, 32, 0, st>>>(scal, tol * tol, (double)maxit);
-  k_init<<<nb, kNT, 0, st>>>(F, b, x, x0 != nullptr, r, red, counter, scal);
-  k_precond<<<nb, kNT, 0, st>>>(F, Binv, r, z, p, red, counter, scal);
-  HDG_CUDA_TRY(cudaGetLastError());
+  if (x0) k_load_x0<<<nb, kNT, 0, st>>>(nv, M->d_ftype, d2, x0, x);
   double hv[S_NSCAL];
-  for (;;) {
-    HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, st));
-    HDG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hv[S_DONE] != 0.0) break;
-    for (int i = 0; i < kIterChunk; ++i) {
-      k_matvec<<<nb, kNT, 0, st>>>(F, p, q, red, counter, scal);
-      k_update<<<nb, kNT, 0, st>>>(F, Binv, x, r, z, p, q, red, counter, scal);
-      k_dir<<<nb, kNT, 0, st>>>(nv, z, p, scal);
-    }
-    HDG_CUDA_TRY(cudaGetLastError());
-  }
-  // true FP64 residual of the final iterate
   double* scal2 = scal + S_NSCAL;
-  k_init<<<nb, kNT, 0, st>>>(F, b, x, true, q, red, counter, scal2);
+  // one PCG pass from x (zero start unless have_x) for at most `budget` iterations
+  auto pass = [&](bool have_x, int budget) -> int {
+    k_set_scalars<<<1, 32, 0, st>>>(scal, tol * tol, (double)budget);
+    k_init<<<nb, kNT, 0, st>>>(F, b, x, have_x, r, red, counter, scal);
+    k_precond<<<nb, kNT, 0, st>>>(F, Binv, r, z, p, red, counter, scal);
+    HDG_CUDA_TRY(cudaGetLastError());
+    for (;;) {
+      HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, st));
+      HDG_CUDA_TRY(cudaStreamSynchronize(st));
+      if (hv[S_DONE] != 0.0) break;
+      for (int i = 0; i < kIterChunk; ++i) {
+        k_matvec<<<nb, kNT, 0, st>>>(F, p, q, red, counter, scal);
+        k_update<<<nb, kNT, 0, st>>>(F, Binv, x, r, z, p, q, red, counter, scal);
+        k_dir<<<nb, kNT, 0, st>>>(nv, z, p, scal);
+      }
+      HDG_CUDA_TRY(cudaGetLastError());
+    }
+    return HDG_OK;
+  };
+  // true FP64 residual ||b - H x|| of the current iterate
+  auto true_res = [&](double* rn) -> int {
+    k_init<<<nb, kNT, 0, st>>>(F, b, x, true, q, red, counter, scal2);
+    HDG_CUDA_TRY(cudaGetLastError());
+    double rr;
+    HDG_CUDA_TRY(cudaMemcpyAsync(&rr, scal2 + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDG_CUDA_TRY(cudaStreamSynchronize(st));
+    *rn = std::sqrt(rr);
+    return HDG_OK;
+  };
+  rc = pass(x0 != nullptr, maxit);
+  if (rc) return rc;
+  int total_it = (int)hv[S_ITERS];
+  bool bad = hv[S_BAD] != 0.0;
+  double rn = 0.0;
+  rc = true_res(&rn);
+  if (rc) return rc;
+  if (!(rn <= tol * 1.0000001 || bnorm == 0.0) && total_it < maxit && !bad) {
+    // the recursive residual converged but the true one did not: one more pass from x, as the
+    // FP64 solve of hdg_solve_trace does
+    rc = pass(true, maxit - total_it);
+    if (rc) return rc;
+    total_it += (int)hv[S_ITERS];
+    bad = hv[S_BAD] != 0.0;
+    rc = true_res(&rn);
+    if (rc) return rc;
+  }
   k_finish<<<nb, kNT, 0, st>>>(nv, M->d_ftype, d2, x, xD, uhat);
   HDG_CUDA_TRY(cudaGetLastError());
-  double rr;
-  HDG_CUDA_TRY(cudaMemcpyAsync(&rr, scal2 + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st));
   HDG_CUDA_TRY(cudaStreamSynchronize(st));
-  const double rn = std::sqrt(rr);
-  if (iters) *iters = (int)hv[S_ITERS];
+  if (iters) *iters = total_it;
   if (relres) *relres = bnorm > 0 ? rn / bnorm : 0.0;
-  if (hv[S_BAD] != 0.0) return fail(HDG_ERR_NOT_CONVERGED, "PCG breakdown (non-positive curvature)");
+  if (bad) return fail(HDG_ERR_NOT_CONVERGED, "PCG breakdown (non-positive curvature)");
   if (!(rn <= tol * 1.0000001 || bnorm == 0.0))
     return fail(HDG_ERR_NOT_CONVERGED, "no-alloc trace solve reached maxit with relative residual " +
                                            std::to_string(bnorm > 0 ? rn / bnorm : 0.0));
@@ -444,5 +478,8 @@ extern "C" int hdg_solve_trace_noalloc(hdg_mesh* mesh, double rtol, int maxit, c
                                        int* iters, double* relres) {
   if (!mesh) return hdg::fail(HDG_ERR_ARG, "NULL mesh");
   if (mesh->tab.d2 < 3) return hdg::fail(HDG_ERR_UNSUPPORTED, "the allocation-free solve is built for k >= 1");
+  if (mesh->beta_q)
+    return hdg::fail(HDG_ERR_UNSUPPORTED,
+                     "the allocation-free solve is the symmetric (CG) solve; it needs beta = 0 (no convection)");
   return hdg::noalloc::solve(mesh, rtol, maxit, x0, uhat, iters, relres);
 }
