@@ -136,6 +136,13 @@ int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, in
   // HDG_HOST_LOOP=1: drive the PCG loop from the host (replays of a plain captured graph)
   // instead of the device-side conditional loop, e.g. for profilers that list graph kernels.
   if (const char* hl = std::getenv("HDG_HOST_LOOP")) M->no_cond_graphs = hl[0] == '1';
+  // HDG_FACE_BLOCKS=n: persistent grid of n blocks for the trace-solve kernels (both
+  // precisions) and a grid cap of n blocks for the coarse-level kernels, so that small meshes
+  // take the multi-tile loops and multi-block reductions that large meshes take.
+  if (const char* fb = std::getenv("HDG_FACE_BLOCKS")) {
+    const int v = std::atoi(fb);
+    if (v > 0) M->face_blocks = M->face_blocks32 = M->grid_cap = v;
+  }
   std::string err;
   int rc = HDG_OK;
   if (!build_tables(k, &M->tab, &err)) rc = fail(HDG_ERR_ARG, err);

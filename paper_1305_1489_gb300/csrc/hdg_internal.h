@@ -131,6 +131,7 @@ struct hdg_mesh {
   int graph_iters = 0;
   int face_blocks = 1216;         // persistent grid of the face kernels (hdg_autotune)
   int face_blocks32 = 1216;       // the same for the FP32 inner iterations
+  int grid_cap = 0;               // > 0: cap on the grids of the coarse-level kernels (HDG_FACE_BLOCKS)
   int k1_variant = 0;             // launch shape of the double-float K1 (hdg_autotune)
   int asm_prec = -1;              // precision of the last hdg_assemble_condense
   hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL

@@ -795,9 +795,10 @@ template <typename T, int D2>
 static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStream_t st, const double* done) {
   Coarse* c = M->coarse;
   const int G = grid_levels(c);
-  auto grid = [](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, kMaxBlocks); };
-  auto rows = [](int64_t n) { return (int)std::min<int64_t>((n * kRowLanes + 255) / 256, kMaxBlocks); };
-  const int gr = (int)std::min<int64_t>((c->lv[0].n + 7) / 8, 152 * 16);  // one warp per node
+  const int64_t cap = M->grid_cap > 0 ? std::min<int64_t>(M->grid_cap, kMaxBlocks) : kMaxBlocks;
+  auto grid = [cap](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, cap); };
+  auto rows = [cap](int64_t n) { return (int)std::min<int64_t>((n * kRowLanes + 255) / 256, cap); };
+  const int gr = (int)std::min<int64_t>({(c->lv[0].n + 7) / 8, (int64_t)152 * 16, cap});  // one warp per node
   restrict_gather_kernel<T, D2><<<gr, 256, 0, st>>>(CA, r, done);
   level_down_kernel<true><<<rows(c->lv[0].n), 256, 0, st>>>(c->lv[0], c->rc, done);
   for (int l = 1; l < G; ++l) {

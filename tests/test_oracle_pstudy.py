@@ -23,7 +23,10 @@ def test_p_convergence_ratios(s):
         errs.append(hdg.errors(r["mesh"], k, r["q"], r["u"], r["uhat"], r["ustar"], prob))
     for key in ("e_q", "e_u", "e_uhat"):
         e = [x[key] for x in errs]
-        assert all(e[i + 1] < 0.45 * e[i] for i in range(4)), (key, e)
+        # geometric decay: the k = 0 -> 1 step (k = 0 converges only like h) with 0.45, the
+        # steps between k >= 1 with 0.35
+        assert e[1] < 0.45 * e[0], (key, e)
+        assert all(e[i + 1] < 0.35 * e[i] for i in range(1, 4)), (key, e)
         for ratio in p_ratios(errs, key):
             assert 0.7 < ratio < 1.3, (key, ratio)
 
