@@ -134,7 +134,8 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * C^K = A3 A1^-1 A2 + tauDD (eq. 5.5), C_f^K = A3 A1^-1 A_f (eq. 5.6), and the operators of
  * the local recovery (eq. 5.3), into library-owned device memory.
  * precision: HDG_FP64 (native FP64) or HDG_DF32 (double-float on the FP32 pipe, FP64-level
- * accuracy; reaction-diffusion only; at k = 0 it runs the FP64 kernel).  The precision also
+ * accuracy; with convection the non-symmetric Schur complement is factored by a double-float
+ * LU without pivoting; at k = 0 it runs the FP64 kernel).  The precision also
  * selects that of hdg_recover and hdg_postprocess until the next assembly.  Synchronises to report
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
@@ -158,7 +159,9 @@ int hdg_get_condensed(const hdg_mesh* mesh, double* C, double* Cf);
  * solved matrix-free element by element with block-Jacobi preconditioned CG (BiCGStab when a
  * convection field is set: the trace matrix is then non-symmetric) to
  *   ||b - H u_hat||_2 <= rtol ||b||_2  (FP64 residual over the free dofs).
- *   precision: HDG_FP64 (plain PCG) or HDG_MIXED_FP32 (FP32 inner PCG, FP64 refinement).
+ *   precision: HDG_FP64 (plain PCG or BiCGStab) or HDG_MIXED_FP32 (FP32 inner PCG or BiCGStab
+ *   iterations, FP64 residuals and refinement; an inner breakdown restarts from the refined
+ *   iterate).
  *   x0: device f64 [nfc][d2] initial guess or NULL (zero start); its entries on Dirichlet faces
  *   are ignored (u_hat_D enters through the right-hand side), so a previous uhat is a valid guess.
  *   uhat: device f64 [nfc][d2] output; Dirichlet faces receive u_hat_D of eq. 6.3.
@@ -245,7 +248,7 @@ int hdg_nn_adam(int64_t n, float* p, const float* g, float* m, float* v, float l
 
 /* ------------------------------------------------------------------ two-level preconditioner
  * (not in the paper, which solves eq. 6.5 directly).  With a coarse space set, the PCG of
- * hdg_solve_trace (both precisions; not the BiCGStab of convection problems) is preconditioned
+ * hdg_solve_trace (both precisions; with convection, right preconditioning of BiCGStab) is preconditioned
  * by M^-1 r = B^-1 r + Pi V(Pi^T r): B the block-Jacobi part, Pi the trace (eq. 6.3 face
  * coefficients) of a continuous piecewise-linear field, V one symmetric V-cycle (one l1-Jacobi
  * sweep before and after each coarse correction, FP32) for A_0 = Pi^T H Pi over nested levels
@@ -282,7 +285,9 @@ typedef struct hdg_tuning {
 int hdg_autotune(hdg_mesh* mesh, hdg_tuning* out);
 
 /* Relative tolerance of each FP32 inner solve of the HDG_MIXED_FP32 trace solve (default
- * 1e-4): every outer FP64 refinement step asks the inner PCG for this residual reduction.  */
+ * 1e-4): every outer FP64 refinement step asks the inner PCG (BiCGStab with convection) for
+ * this residual reduction, or only for half the remaining distance to rtol ||b|| when that is
+ * less (the last step stops as soon as it suffices).                                       */
 int hdg_set_inner_tolerance(hdg_mesh* mesh, double rtol);
 
 /* Residual check (tests): r = b - H x over the free dofs, device f64 [nfc][d2]; returns

@@ -67,7 +67,8 @@ static int upload_tables(hdg_mesh* M) {
       (rc = upload(&D.sfAA_df, split_df(T.sfAA))) || (rc = upload(&D.sfBB_df, split_df(T.sfBB))) ||
       (rc = upload(&D.sfCC_df, split_df(T.sfCC))) || (rc = upload(&D.sfp2to1, T.sfp2to1)) ||
       (rc = upload(&D.sfp3to2, T.sfp3to2)) || (rc = upload(&D.G1_df, split_df(T.G1))) ||
-      (rc = upload(&D.Shat1_df, split_df(T.Shat1))))
+      (rc = upload(&D.Shat1_df, split_df(T.Shat1))) || (rc = upload(&D.Pd_df, split_df(T.Pd))) ||
+      (rc = upload(&D.Pl_df, split_df(T.Pl))) || (rc = upload(&D.Dmu_df, split_df(T.Dmu))))
     return rc;
   if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
       (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
@@ -85,12 +86,15 @@ static void release(hdg_mesh* M) {
                   M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
                   M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj,
                   M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2, M->d_norm,
-                  M->dt.G1_df, M->dt.Shat1_df};
+                  M->dt.G1_df, M->dt.Shat1_df, M->dt.Pd_df, M->dt.Pl_df, M->dt.Dmu_df, M->d_bicg32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
   if (M->graph32) cudaGraphExecDestroy(M->graph32);
   if (M->graph_bicg) cudaGraphExecDestroy(M->graph_bicg);
+  if (M->graph_bicg32) cudaGraphExecDestroy(M->graph_bicg32);
+  if (M->wgraph_bicg) cudaGraphExecDestroy(M->wgraph_bicg);
+  if (M->wgraph_bicg32) cudaGraphExecDestroy(M->wgraph_bicg32);
   if (M->wgraph64) cudaGraphExecDestroy(M->wgraph64);
   if (M->wgraph32) cudaGraphExecDestroy(M->wgraph32);
   if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
@@ -256,8 +260,6 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (precision != HDG_FP64 && precision != HDG_DF32)
     return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64 or HDG_DF32");
   if (M->beta_q && !M->beta_f) return fail(HDG_ERR_STATE, "convection set without hdg_set_face_convection");
-  if (M->beta_q && precision == HDG_DF32)
-    return fail(HDG_ERR_UNSUPPORTED, "the double-float assembly covers reaction-diffusion (beta = 0)");
   if (M->beta_q && M->method == HDG_METHOD_BDM)
     return fail(HDG_ERR_UNSUPPORTED, "the BDM element is built for reaction-diffusion (beta = 0)");
   if (M->k == 0 && (M->beta_q || M->method == HDG_METHOD_BDM))
@@ -315,10 +317,10 @@ int hdg_autotune(hdg_mesh* M, hdg_tuning* out) {
   hdg_tuning t = {};
   int rc = autotune_face_grid(M, &t);
   if (rc) return rc;
-  // launch shapes of the double-float K1 (reaction-diffusion only): two timed launches each
+  // launch shapes of the double-float K1: two timed launches each
   float best_t = 1e30f;
   int best = 0;
-  if (!M->beta_q) {
+  {
     cudaEvent_t a, b;
     HDG_CUDA_TRY(cudaEventCreate(&a));
     HDG_CUDA_TRY(cudaEventCreate(&b));

@@ -9,6 +9,13 @@
 //   G = diag(T) E + sum_* diag(n_*) V^T W_*;  L_s L_s^T = S_u;  [H | h] = L_s^-1 [G^T | f];
 //   C^K = (n_l . n_l') o (V^T V) - H^T H + tauDD;  C_f^K = H^T h;
 //   recovery record: [H | h], V, W_* and the factors L_s, L (K2 does the back substitutions).
+// Convection (CONV = true, the reading of Section 9 in assemble.cu): B_c = -(beta P_j, grad P_i)
+// joins S_u, which is then factored by LU without pivoting; alphaDP = <(beta.nu) D_i, P_j> and
+// alphaDD = <(beta.nu) D_i, D_j> per face; G_col = G - alphaDP;  H_col = L^-1 G_col^T,
+// H_row = U^-T G^T, h = L^-1 f;  C^K = (n_l . n_l') o V^T V - H_row^T H_col + tauDD - alphaDD,
+// C_f = H_row^T h.  B_c is formed as P^T Gq with Gq[q][i] = sum_# bw_#(q) dhat_# P_i(q) and
+// bw_#(q) = -(omega_q / 6) sum_* a_{*#} beta_*(p_q), so its n^2 entries cost nq n products
+// each instead of 3 nq n.
 #include <cstdlib>
 
 #include "device_common.cuh"
@@ -23,6 +30,9 @@ struct AsmDfArgs {
   const double *kappa, *c, *f, *tau;
   const df *P, *Chat, *S, *E;  // double-float copies of the reference tables
   const df *AA, *BB, *CC;      // sum-factorisation tables of the volume masses
+  const double *beta_q, *beta_f;  // convection: [3][nelt][nq], [3][nelt][4][nf] (FP64)
+  const df *Pd, *Pl, *Dmu;        // convection: reference gradients, face traces, face bases
+  const double* wf;               // face weights varpi_r
   const int16_t *p2to1, *p3to2;
   const double* w;
   const int16_t *pairs_n, *pairs_m;
@@ -36,10 +46,10 @@ struct AsmDfArgs {
 // + tauDD - H^T H), so its space first holds the weighted coefficients kw, cw, fw (read only
 // by the first phase) and then the face-weighted sums Wt_l = sum_* n_{l*} W_* (read only by
 // the phase that forms G): WTF faces at a time, all four when they fit.
-template <int K>
+template <int K, bool CONV = false>
 struct AsmDfSmem {
   using D = Dims<K>;
-  static constexpr int n = D::n, m = D::m, nq = D::nq;
+  static constexpr int n = D::n, m = D::m, nq = D::nq, nf = D::nf, d2 = D::d2;
   static constexpr int o_M = 0;
   static constexpr int o_S = o_M + n * n;
   static constexpr int o_W = o_S + n * n;
@@ -57,7 +67,14 @@ struct AsmDfSmem {
   static_assert((2 * np1 + K + 1) * nn * nn <= 3 * n * n + n * m, "T1 must fit in the space of W and V");
   static_assert(3 * nq + (2 * np2 + D::d2) * nn <= m * m, "T2 must fit in the space of C");
   static_assert(WTF * n * n <= m * m, "Wt must fit in the space of C");
-  static constexpr int total = o_C + m * m;
+  // convection: H_row^T [n][m] (alphaDP^T, then G^T, then H_row), the volume weights bw
+  // [3][nq], Gq [nq][n], the face weights varpi_r beta.n_l [4][nf] and alphaDD [4][d2][d2]
+  static constexpr int o_Hr = o_C + m * m;
+  static constexpr int o_bw = o_Hr + (CONV ? n * m : 0);
+  static constexpr int o_Gq = o_bw + (CONV ? 3 * nq : 0);
+  static constexpr int o_bn = o_Gq + (CONV ? nq * n : 0);
+  static constexpr int o_aDD = o_bn + (CONV ? 4 * nf : 0);
+  static constexpr int total = o_aDD + (CONV ? 4 * d2 * d2 : 0);
   static constexpr size_t bytes = sizeof(df) * total;
 };
 
@@ -100,11 +117,62 @@ __device__ __forceinline__ df ldg_df(const df* p) {
   return df_make(v.x, v.y);
 }
 
-template <int K, int NT, int MINB>
+// L x = b with the unit-lower factor of warp_lu_df
+template <int N>
+__device__ __forceinline__ void fwd_subst_unit_df(const df* __restrict__ LU, df* x) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    dacc s = dacc_from(x[l]);
+#pragma unroll
+    for (int i = 0; i < l; ++i) dacc_msub(s, LU[l * N + i], x[i]);
+    x[l] = dacc_result(s);
+  }
+}
+
+// U^T x = b (U^T lower triangular) with the factor of warp_lu_df
+template <int N>
+__device__ __forceinline__ void fwd_subst_Ut_df(const df* __restrict__ LU, const df* invd, df* x) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    dacc s = dacc_from(x[l]);
+#pragma unroll
+    for (int i = 0; i < l; ++i) dacc_msub(s, LU[i * N + l], x[i]);
+    x[l] = df_mul(dacc_result(s), invd[l]);
+  }
+}
+
+// LU without pivoting (unit-lower L below the diagonal, U on and above) of the N x N
+// double-float matrix A by one warp, right-looking: at step j column j is scaled by 1/U_jj
+// and the trailing block updated, A_il -= L_ij U_jl.  invd receives 1/U_jj (formed in FP64,
+// N per element).  For S_u with convection, whose symmetric part is positive definite, every
+// leading minor is non-zero.  Returns, on every lane, whether all pivots were non-zero.
+template <int N>
+__device__ __forceinline__ bool warp_lu_df(df* A, df* invd, int lane) {
+  bool ok = true;
+  for (int j = 0; j < N; ++j) {
+    const df piv = A[j * N + j];
+    ok = ok && (piv.hi != 0.f) && isfinite(piv.hi);
+    const df ip = df_recip(piv.hi != 0.f ? piv : df_make(1.f, 0.f));
+    if (lane == 0) invd[j] = ip;
+    for (int i = j + 1 + lane; i < N; i += 32) A[i * N + j] = df_mul(A[i * N + j], ip);
+    __syncwarp();
+    const int w = N - j - 1;
+    for (int t = lane; t < w * w; t += 32) {
+      const int i = j + 1 + t / w, l = j + 1 + t % w;
+      dacc s = dacc_from(A[i * N + l]);
+      dacc_msub(s, A[i * N + j], A[j * N + l]);
+      A[i * N + l] = dacc_result(s);
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
+template <int K, int NT, int MINB, bool CONV>
 __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   using D = Dims<K>;
-  using SM = AsmDfSmem<K>;
-  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq;
+  using SM = AsmDfSmem<K, CONV>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq, nf = D::nf;
   constexpr int NP = n * (n + 1) / 2, MP = m * (m + 1) / 2;
   extern __shared__ df smd[];
   df* kw = smd + SM::o_kw;
@@ -117,6 +185,11 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   df* Wt = smd + SM::o_Wt;
   df* Gt = smd + SM::o_G;
   df* Cs = smd + SM::o_C;
+  df* Hr = smd + SM::o_Hr;    // convection only
+  df* bw = smd + SM::o_bw;
+  df* Gq = smd + SM::o_Gq;
+  df* bn = smd + SM::o_bn;
+  df* aDD = smd + SM::o_aDD;
   __shared__ df s_a[3][3], s_nrm[4][3], s_T[4], s_nn[4][4];
   __shared__ double s_geo[25], s_vol;  // a (9), nrm (12), area (4) in FP64
   __shared__ df invdM[n], invdS[n];
@@ -159,6 +232,26 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     kw[q] = df_from_double(vw / kap);
     cw[q] = df_from_double(vw * cc);
     fw[q] = df_from_double(vw * ff);
+    if constexpr (CONV) {
+      // bw_#(q) = -(omega_q / 6) sum_* a_{*#} beta_*(p_q)  (B_c = sum_q sum_# bw P_qj dhat_# P_qi)
+      const double b0 = A.beta_q[(0 * A.nelt + Ke) * nq + q], b1 = A.beta_q[(1 * A.nelt + Ke) * nq + q],
+                   b2 = A.beta_q[(2 * A.nelt + Ke) * nq + q];
+      const double sc = -A.w[q] / 6.0;
+#pragma unroll
+      for (int h = 0; h < 3; ++h)
+        bw[h * nq + q] = df_from_double(sc * (s_geo[h] * b0 + s_geo[3 + h] * b1 + s_geo[6 + h] * b2));
+    }
+  }
+  if constexpr (CONV) {
+    // varpi_r beta(x_{r,l}^K) . n_l at the element's face nodes
+    for (int t = tid; t < 4 * nf; t += NT) {
+      const int fl = t / nf, r = t - fl * nf;
+      const double* nl = s_geo + 9 + 3 * fl;
+      double acc = 0.0;
+#pragma unroll
+      for (int st = 0; st < 3; ++st) acc = fma(A.beta_f[((int64_t)st * A.nelt + Ke) * 4 * nf + t], nl[st], acc);
+      bn[t] = df_from_double(A.wf[r] * acc);
+    }
   }
   __syncthreads();
 
@@ -183,6 +276,15 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     T1[t] = dacc_result(s1);
     T1[np1 * nn2 + t] = dacc_result(s2);
     if (wf) T1[2 * np1 * nn2 + t] = dacc_result(s3);
+  }
+  if constexpr (CONV) {  // Gq[q][i] = sum_# bw_#(q) dhat_# P_i(p_hat_q)
+    for (int t = tid; t < nq * n; t += NT) {
+      const int q = t / n, i = t - q * n;
+      dacc g = dacc_zero();
+#pragma unroll
+      for (int h = 0; h < 3; ++h) dacc_mac(g, bw[h * nq + q], ldg_df(A.Pd + (h * nq + q) * n + i));
+      Gq[t] = dacc_result(g);
+    }
   }
   __syncthreads();
   for (int t = tid; t < np2 * nn; t += NT) {  // T2 = sum_j B_a2 B_b2 T1
@@ -219,8 +321,20 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     const df v1 = dacc_result(s1), v2 = dacc_result(s2);
     Ms[i * n + j] = v1;
     Ms[j * n + i] = v1;
-    Ss[i * n + j] = v2;
-    Ss[j * n + i] = v2;
+    if constexpr (CONV) {
+      // B_c[i][j] = sum_q P_qj Gq[q][i],  B_c[j][i] = sum_q P_qi Gq[q][j]
+      dacc bij = dacc_from(v2), bji = dacc_from(v2);
+#pragma unroll 4
+      for (int q = 0; q < nq; ++q) {
+        dacc_mac(bij, ldg_df(A.P + q * n + j), Gq[q * n + i]);
+        dacc_mac(bji, ldg_df(A.P + q * n + i), Gq[q * n + j]);
+      }
+      Ss[i * n + j] = dacc_result(bij);
+      Ss[j * n + i] = dacc_result(bji);
+    } else {
+      Ss[i * n + j] = v2;
+      Ss[j * n + i] = v2;
+    }
     if (wf) Gt[j * (m + 1) + m] = j < A.nu ? dacc_result(s3) : df_make(0.f, 0.f);  // pair (0, j)
   }
   // C_*^T from C_hat and the cofactors, V = E^T (both where T1 was)
@@ -234,6 +348,23 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   for (int t = tid; t < n * m; t += NT) {
     const int l = t / m, r = t - l * m, fl = r / d2, a = r - fl * d2;
     V[t] = ldg_df(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + l);
+    if constexpr (CONV) {
+      // alphaDP^T[l][r] = sum_r' varpi (beta.n) D^mu_{r'a} P^l_{r'l}
+      const df* Dm = A.Dmu + s_perm[fl] * nf * d2;
+      const df* Pl = A.Pl + fl * nf * n;
+      dacc acc = dacc_zero();
+      for (int rr = 0; rr < nf; ++rr) dacc_mac(acc, df_mul(bn[fl * nf + rr], ldg_df(Dm + rr * d2 + a)), ldg_df(Pl + rr * n + l));
+      Hr[t] = dacc_result(acc);
+    }
+  }
+  if constexpr (CONV) {  // alphaDD[l][a][b] = sum_r' varpi (beta.n) D^mu_{r'a} D^mu_{r'b}
+    for (int t = tid; t < 4 * d2 * d2; t += NT) {
+      const int fl = t / (d2 * d2), ab = t - fl * d2 * d2, a = ab / d2, b = ab - a * d2;
+      const df* Dm = A.Dmu + s_perm[fl] * nf * d2;
+      dacc acc = dacc_zero();
+      for (int rr = 0; rr < nf; ++rr) dacc_mac(acc, df_mul(bn[fl * nf + rr], ldg_df(Dm + rr * d2 + a)), ldg_df(Dm + rr * d2 + b));
+      aDD[t] = dacc_result(acc);
+    }
   }
   __syncthreads();
 
@@ -266,16 +397,27 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
 
   for (int t = tid; t < NP; t += NT) {
     const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
-    dacc s = dacc_from(Ss[i * n + j]);
+    if constexpr (CONV) {  // S_u is not symmetric: the same W^T W term joins both entries
+      dacc s = dacc_zero();
 #pragma unroll
-    for (int st = 0; st < 3; ++st)
+      for (int st = 0; st < 3; ++st)
 #pragma unroll 4
-      for (int l = 0; l < n; ++l) dacc_mac(s, W[st * n * n + l * n + i], W[st * n * n + l * n + j]);
-    // BDM: the degree-k u unknowns are decoupled (identity rows and columns), which erases
-    // them from the elimination exactly as the paper erases their rows and columns of A_1
-    const df v = (i < A.nu && j < A.nu) ? dacc_result(s) : df_make(i == j ? 1.f : 0.f, 0.f);
-    Ss[i * n + j] = v;
-    Ss[j * n + i] = v;
+        for (int l = 0; l < n; ++l) dacc_mac(s, W[st * n * n + l * n + i], W[st * n * n + l * n + j]);
+      const df w = dacc_result(s);
+      Ss[i * n + j] = df_add(Ss[i * n + j], w);
+      if (i != j) Ss[j * n + i] = df_add(Ss[j * n + i], w);
+    } else {
+      dacc s = dacc_from(Ss[i * n + j]);
+#pragma unroll
+      for (int st = 0; st < 3; ++st)
+#pragma unroll 4
+        for (int l = 0; l < n; ++l) dacc_mac(s, W[st * n * n + l * n + i], W[st * n * n + l * n + j]);
+      // BDM: the degree-k u unknowns are decoupled (identity rows and columns), which erases
+      // them from the elimination exactly as the paper erases their rows and columns of A_1
+      const df v = (i < A.nu && j < A.nu) ? dacc_result(s) : df_make(i == j ? 1.f : 0.f, 0.f);
+      Ss[i * n + j] = v;
+      Ss[j * n + i] = v;
+    }
   }
   constexpr int WTF = SM::WTF;
   for (int t = tid; t < WTF * n * n; t += NT) {
@@ -288,7 +430,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   __syncthreads();
 
   if (warp == 0) {
-    const bool ok = group_cholesky_df<n, 32>(Ss, invdS, A.pairs_n, lane);
+    const bool ok = CONV ? warp_lu_df<n>(Ss, invdS, lane) : group_cholesky_df<n, 32>(Ss, invdS, A.pairs_n, lane);
     if (!ok && lane == 0) s_bad = 1;
   } else {
     // G^T[j][r] = T_l E[r][j] + (V^T Wt_l)[r][j] for the columns r of face l, WTF faces per pass
@@ -312,7 +454,13 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
         const df* wt = Wt + (fl - f0) * n * n;
 #pragma unroll 4
         for (int l = 0; l < n; ++l) dacc_mac(g, V[l * m + r], wt[l * n + j]);
-        Gt[j * (m + 1) + r] = j < A.nu ? dacc_result(g) : df_make(0.f, 0.f);
+        if constexpr (CONV) {
+          const df gv = dacc_result(g);
+          Gt[j * (m + 1) + r] = df_sub(gv, Hr[j * m + r]);  // G_col^T = (G - alphaDP)^T
+          Hr[j * m + r] = gv;                              // G^T
+        } else {
+          Gt[j * (m + 1) + r] = j < A.nu ? dacc_result(g) : df_make(0.f, 0.f);
+        }
       }
     }
   }
@@ -324,38 +472,67 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   // U_(i-1)i, then 1/U_ii, with U = L^T), the normals.  Column-major blocks, so that the
   // recovery kernel reads them with unit stride; every entry a double-float pair (8 bytes,
   // the layout of the FP64 record), read by the double-float recovery kernel.
+  // (convection: [H_col | h] = L^-1 [G_col^T | f] by the first m + 1 threads and H_row =
+  // U^-T G^T by the next m; U_s is the U of the LU)
   df* R = reinterpret_cast<df*>(A.rec) + Ke * (int64_t)D::rec;
+  constexpr int NTRI = (m + 1) + (CONV ? m : 0);
+  static_assert(NT > NTRI, "K1 needs more threads than triangular solves");
   if (tid < m + 1) {
     df x[n];
 #pragma unroll
     for (int l = 0; l < n; ++l) x[l] = Gt[l * (m + 1) + tid];
-    fwd_subst_df<n>(Ss, invdS, x);
+    if constexpr (CONV) fwd_subst_unit_df<n>(Ss, x); else fwd_subst_df<n>(Ss, invdS, x);
 #pragma unroll
     for (int l = 0; l < n; ++l) Gt[l * (m + 1) + tid] = x[l];
+  } else if (tid < NTRI) {
+    const int col = tid - (m + 1);
+    df x[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) x[l] = Hr[l * m + col];
+    fwd_subst_Ut_df<n>(Ss, invdS, x);
+#pragma unroll
+    for (int l = 0; l < n; ++l) Hr[l * m + col] = x[l];
   } else {
     constexpr int o_V = n * (m + 1), o_W = o_V + n * m, o_U = o_W + 3 * n * n;
-    for (int t = tid - (m + 1); t < n * m; t += NT - (m + 1)) {
+    for (int t = tid - NTRI; t < n * m; t += NT - NTRI) {
       const int r = t / n, l = t - r * n;
       R[o_V + t] = V[l * m + r];
     }
-    for (int t = tid - (m + 1); t < 3 * n * n; t += NT - (m + 1)) {
+    for (int t = tid - NTRI; t < 3 * n * n; t += NT - NTRI) {
       const int st = t / (n * n), rem = t - st * n * n, c = rem / n, l = rem - c * n;
       R[o_W + t] = W[st * n * n + l * n + c];
     }
-    for (int t = tid - (m + 1); t < n * n; t += NT - (m + 1)) {
+    for (int t = tid - NTRI; t < n * n; t += NT - NTRI) {
       const int i = t / n, l = t - i * n;
       if (l <= i) {
-        R[o_U + i * (i + 1) / 2 + l] = (l == i) ? invdS[i] : Ss[t];
+        R[o_U + i * (i + 1) / 2 + l] = (l == i) ? invdS[i] : (CONV ? Ss[l * n + i] : Ss[t]);
         R[o_U + D::tri + i * (i + 1) / 2 + l] = (l == i) ? invdM[i] : Ms[t];
       }
     }
-    for (int t = tid - (m + 1); t < 12; t += NT - (m + 1))
+    for (int t = tid - NTRI; t < 12; t += NT - NTRI)
       R[o_U + 2 * D::tri + t] = s_nrm[t / 3][t % 3];
   }
   __syncthreads();
 
-  // C = (n_l . n_l') o V^T V + tauDD - H^T H  (V = L^-1 E^T; H = rows of G^T)
-  for (int t = tid; t < MP; t += NT) {
+  // C = (n_l . n_l') o V^T V + tauDD - H^T H  (V = L^-1 E^T; H = rows of G^T);
+  // convection: C = (n_l . n_l') o V^T V + tauDD - alphaDD - H_row^T H_col, C_f = H_row^T h
+  if constexpr (CONV) {
+    for (int t = tid; t < m * m; t += NT) {
+      const int r = t / m, s = t - r * m;
+      const int fr = r / d2, fs = s / d2;
+      dacc b = dacc_zero();
+#pragma unroll 4
+      for (int l = 0; l < n; ++l) dacc_mac(b, V[l * m + r], V[l * m + s]);
+      df cv = df_mul(s_nn[fr][fs], dacc_result(b));
+      if (r == s) cv = df_add(cv, s_T[fr]);
+      if (fr == fs) cv = df_sub(cv, aDD[fr * d2 * d2 + (r - fr * d2) * d2 + (s - fs * d2)]);
+      dacc hh = dacc_from(cv);
+#pragma unroll 4
+      for (int j = 0; j < n; ++j) dacc_msub(hh, Hr[j * m + r], Gt[j * (m + 1) + s]);
+      Cs[t] = dacc_result(hh);
+    }
+  }
+  for (int t = tid; t < (CONV ? 0 : MP); t += NT) {
     const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
     const int fr = r / d2, fs = s / d2;
     dacc b = dacc_zero();
@@ -372,8 +549,10 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
   for (int r = tid; r < m; r += NT) {
     dacc s = dacc_zero();
+    const df* hrow = CONV ? Hr : Gt;
+    const int ld = CONV ? m : (m + 1);
 #pragma unroll 4
-    for (int j = 0; j < n; ++j) dacc_mac(s, Gt[j * (m + 1) + r], Gt[j * (m + 1) + m]);
+    for (int j = 0; j < n; ++j) dacc_mac(s, hrow[j * ld + r], Gt[j * (m + 1) + m]);
     A.Cf[Ke * m + r] = df_to_double(dacc_result(s));
   }
   for (int t = tid; t < n * (m + 1); t += NT) {  // [H | h]^T
@@ -390,28 +569,33 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   }
 }
 
-template <int K, int V>
+template <int K, int V, bool CONV>
 static cudaError_t launch_df_shape(hdg_mesh* M, const AsmDfArgs& a) {
   constexpr int NT = K1Shape<K, V>::NT, MINB = K1Shape<K, V>::MINB;
-  const size_t smem = AsmDfSmem<K>::bytes;
-  cudaError_t e =
-      cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = AsmDfSmem<K, CONV>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  assemble_df_kernel<K, NT, MINB><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  assemble_df_kernel<K, NT, MINB, CONV><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
   M->launches += 1;
   return cudaGetLastError();
 }
 
-template <int K>
-static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
+template <int K, bool CONV>
+static cudaError_t launch_df_kc(hdg_mesh* M, const AsmDfArgs& a) {
   // HDG_K1_VARIANT overrides the tuned shape (tests of every shape, profiling)
   int v = M->k1_variant;
   if (const char* ev = std::getenv("HDG_K1_VARIANT")) v = std::atoi(ev);
-  if (v == 1) return launch_df_shape<K, 1>(M, a);
-  if (K >= 3 && v == 2) return launch_df_shape<K, (K >= 3 ? 2 : 0)>(M, a);
-  return launch_df_shape<K, 0>(M, a);
+  if (v == 1) return launch_df_shape<K, 1, CONV>(M, a);
+  if (K >= 3 && v == 2) return launch_df_shape<K, (K >= 3 ? 2 : 0), CONV>(M, a);
+  return launch_df_shape<K, 0, CONV>(M, a);
+}
+
+template <int K>
+static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
+  return a.beta_q ? launch_df_kc<K, true>(M, a) : launch_df_kc<K, false>(M, a);
 }
 
 int k1_variants(int k) { return k == 0 ? 1 : k >= 3 ? 3 : 2; }
@@ -470,6 +654,12 @@ cudaError_t launch_assemble_df(hdg_mesh* M) {
   a.CC = reinterpret_cast<const df*>(M->dt.sfCC_df);
   a.p2to1 = M->dt.sfp2to1;
   a.p3to2 = M->dt.sfp3to2;
+  a.beta_q = M->beta_q;
+  a.beta_f = M->beta_f;
+  a.Pd = reinterpret_cast<const df*>(M->dt.Pd_df);
+  a.Pl = reinterpret_cast<const df*>(M->dt.Pl_df);
+  a.Dmu = reinterpret_cast<const df*>(M->dt.Dmu_df);
+  a.wf = M->dt.face_w;
   a.w = M->dt.vol_w;
   a.pairs_n = M->dt.pairs_n;
   a.pairs_m = M->dt.pairs_m;

@@ -535,7 +535,8 @@ int hdg_set_coarse_space(hdg_mesh* M, int nlev, const int64_t* sizes, const int3
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (M->stream) cudaStreamSynchronize(M->stream);
   // the cached PCG graphs hold pointers into the old coarse space: rebuild them at the next solve
-  cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32};
+  cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg, &M->graph_bicg32,
+                           &M->wgraph_bicg, &M->wgraph_bicg32};
   for (cudaGraphExec_t* g : gs)
     if (*g) {
       cudaGraphExecDestroy(*g);

@@ -60,6 +60,7 @@ struct DevTables {
   float *P_df = nullptr, *Chat_df = nullptr, *S_df = nullptr, *E_df = nullptr;
   float *sfAA_df = nullptr, *sfBB_df = nullptr, *sfCC_df = nullptr;  // sum-factorisation tables
   float *G1_df = nullptr, *Shat1_df = nullptr;  // double-float postprocess tables
+  float *Pd_df = nullptr, *Pl_df = nullptr, *Dmu_df = nullptr;  // double-float convection tables
   int16_t *sfp2to1 = nullptr, *sfp3to2 = nullptr;
   int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
   int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices
@@ -125,6 +126,8 @@ struct hdg_mesh {
   int red_blocks = 0;
   cudaGraphExec_t graph64 = nullptr, graph32 = nullptr, graph_bicg = nullptr;
   double* d_bicg = nullptr;  // [4][nfc][d2] extra BiCGStab vectors (s, t, ph, sh)
+  float* d_bicg32 = nullptr; // the same for the FP32 inner BiCGStab of the mixed solve
+  cudaGraphExec_t graph_bicg32 = nullptr, wgraph_bicg = nullptr, wgraph_bicg32 = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
   cudaGraphExec_t wgraph64 = nullptr, wgraph32 = nullptr;  // device-driven (conditional WHILE) PCG loops
   bool no_cond_graphs = false;  // the driver refused conditional nodes: host-driven loop

@@ -551,71 +551,93 @@ __global__ void loop_control_kernel(cudaGraphConditionalHandle h, double* scal, 
 }
 
 // ------------------------------------------------------------------ BiCGStab (convection)
-// Right-preconditioned BiCGStab (van der Vorst 1992) with the block-Jacobi preconditioner,
-// for the non-symmetric trace matrix of convection-diffusion.  Vectors: x, r, rhat (shadow
-// residual), p, v, s, t, ph = M^-1 p, sh = M^-1 s.  Scalars rho, alpha, omega, beta on the
-// device; five kernels per iteration.
-enum { B_RHO = 0, B_ALPHA, B_OMEGA, B_BETA, B_RR, B_DONE, B_ITERS, B_TOL2, B_MAXIT, B_BAD, B_BODIES, B_NSCAL };
+// Right-preconditioned BiCGStab (van der Vorst 1992) for the non-symmetric trace matrix of
+// convection-diffusion, in FP64 or (inner solve of the mixed-precision path) FP32 vectors,
+// with the block-Jacobi or the two-level preconditioner M^-1 = B^-1 + Pi V(Pi^T .).  Vectors:
+// x, r, rhat (shadow residual), p, v, s, t, ph = M^-1 p, sh = M^-1 s.  Scalars rho, alpha,
+// omega, beta (FP64) on the device.  Per iteration: p, [coarse cycle of p, ph], v = H ph, s,
+// [coarse cycle of s, sh], t = H sh, x and r: five kernels with block-Jacobi, seven plus two
+// coarse cycles with the two-level preconditioner.
+enum { B_RHO = 0, B_ALPHA, B_OMEGA, B_BETA, B_RR, B_DONE, B_ITERS, B_TOL2, B_MAXIT, B_BAD, B_BODIES, B_MAXBODIES,
+       B_NSCAL };
+static_assert((int)B_NSCAL <= (int)S_NSCAL, "BiCGStab scalars share the PCG scalar block");
 
+template <typename T>
 struct BicgVecs {
-  double *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
+  T *x, *r, *rh, *p, *v, *s, *t, *ph, *sh;
 };
 
 // r = b - H x (or b), rhat = r, p = v = 0; rho = rhat.r, beta = 0, omega = 1, rr
-template <int D2>
-__global__ void bicg_init_kernel(FaceArgs F, const double* __restrict__ C, const double* __restrict__ b,
-                                 BicgVecs V, bool have_x, double* red, unsigned int* counter, double* scal) {
-  double v[2] = {0.0, 0.0};
+template <typename T, int D2>
+__global__ void bicg_init_kernel(FaceArgs F, const T* __restrict__ C, const T* __restrict__ b, BicgVecs<T> V,
+                                 bool have_x, double* red, unsigned int* counter, double* scal) {
+  double v[1] = {0.0};
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
     const int64_t t = T_.t;
-    double rv = 0.0;
-    if (F.ftype[T_.e] != 1) rv = b[t] - (have_x ? face_apply<double, D2>(C, V.x, F, T_.e, T_.a) : 0.0);
-    if (!have_x) V.x[t] = 0.0;
+    T rv = (T)0;
+    if (F.ftype[T_.e] != 1) rv = b[t] - (have_x ? face_apply<T, D2>(C, V.x, F, T_.e, T_.a) : (T)0);
+    if (!have_x) V.x[t] = (T)0;
     V.r[t] = rv;
     V.rh[t] = rv;
-    V.p[t] = 0.0;
-    V.v[t] = 0.0;
-    v[0] = fma(rv, rv, v[0]);
-    v[1] = fma(rv, rv, v[1]);
+    V.p[t] = (T)0;
+    V.v[t] = (T)0;
+    v[0] = fma((double)rv, (double)rv, v[0]);
   }
-  double out[2];
-  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
     scal[B_RHO] = out[0];
-    scal[B_RR] = out[1];
+    scal[B_RR] = out[0];
     scal[B_BETA] = 0.0;
     scal[B_OMEGA] = 1.0;
     scal[B_ITERS] = 0.0;
-    scal[B_DONE] = (out[1] <= scal[B_TOL2]) ? 1.0 : 0.0;
+    scal[B_DONE] = (out[0] <= scal[B_TOL2]) ? 1.0 : 0.0;
   }
 }
 
-// p = r + beta (p - omega v);  ph = M^-1 p
-template <int D2>
-__global__ void bicg_p_kernel(FaceArgs F, const double* __restrict__ Binv, BicgVecs V, const double* scal) {
+// p = r + beta (p - omega v);  ph = B^-1 p (block-Jacobi only: with the two-level
+// preconditioner ph is formed after the coarse cycle of p)
+template <typename T, int D2, bool TL>
+__global__ void bicg_p_kernel(FaceArgs F, const T* __restrict__ Binv, BicgVecs<T> V, const double* scal) {
   if (scal[B_DONE] != 0.0) return;
-  const double beta = scal[B_BETA], omega = scal[B_OMEGA];
+  const T beta = (T)scal[B_BETA], omega = (T)scal[B_OMEGA];
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
-    if (T_.act) V.p[T_.t] = V.r[T_.t] + beta * (V.p[T_.t] - omega * V.v[T_.t]);
-    __syncthreads();
-    if (T_.act) V.ph[T_.t] = bj_apply<double, D2>(Binv, V.p, T_.e, T_.a);
+    if (T_.act) V.p[T_.t] = fma(beta, fma(-omega, V.v[T_.t], V.p[T_.t]), V.r[T_.t]);
+    if constexpr (!TL) {
+      __syncthreads();
+      if (T_.act) V.ph[T_.t] = bj_apply<T, D2>(Binv, V.p, T_.e, T_.a);
+    }
+  }
+}
+
+// out = B^-1 in + Pi e0 (the two-level preconditioner, after the coarse cycle of `in`)
+template <typename T, int D2, int DONE>
+__global__ void bicg_tl_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ Binv, const T* __restrict__ in,
+                               T* __restrict__ out, const double* scal) {
+  if (scal[DONE] != 0.0) return;
+  for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
+    Tile<D2> T_(F, tile);
+    if (!T_.act) continue;
+    T zv = bj_apply<T, D2>(Binv, in, T_.e, T_.a);
+    if (F.ftype[T_.e] != 1) zv += (T)prolong_face<D2>(CA, T_.e, T_.a);
+    out[T_.t] = zv;
   }
 }
 
 // v = H ph;  alpha = rho / (rhat . v)
-template <int D2>
-__global__ void bicg_v_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs V, double* red,
+template <typename T, int D2>
+__global__ void bicg_v_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
   double v[1] = {0.0};
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const double vv = (F.ftype[T_.e] != 1) ? face_apply<double, D2>(C, V.ph, F, T_.e, T_.a) : 0.0;
+    const T vv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, V.ph, F, T_.e, T_.a) : (T)0;
     V.v[T_.t] = vv;
-    v[0] = fma(V.rh[T_.t], vv, v[0]);
+    v[0] = fma((double)V.rh[T_.t], (double)vv, v[0]);
   }
   double out[1];
   if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
@@ -629,40 +651,42 @@ __global__ void bicg_v_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs
   }
 }
 
-// s = r - alpha v;  sh = M^-1 s
-template <int D2>
-__global__ void bicg_s_kernel(FaceArgs F, const double* __restrict__ Binv, BicgVecs V, const double* scal) {
+// s = r - alpha v;  sh = B^-1 s (block-Jacobi only)
+template <typename T, int D2, bool TL>
+__global__ void bicg_s_kernel(FaceArgs F, const T* __restrict__ Binv, BicgVecs<T> V, const double* scal) {
   if (scal[B_DONE] != 0.0) return;
-  const double alpha = scal[B_ALPHA];
+  const T alpha = (T)scal[B_ALPHA];
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
-    if (T_.act) V.s[T_.t] = V.r[T_.t] - alpha * V.v[T_.t];
-    __syncthreads();
-    if (T_.act) V.sh[T_.t] = bj_apply<double, D2>(Binv, V.s, T_.e, T_.a);
+    if (T_.act) V.s[T_.t] = fma(-alpha, V.v[T_.t], V.r[T_.t]);
+    if constexpr (!TL) {
+      __syncthreads();
+      if (T_.act) V.sh[T_.t] = bj_apply<T, D2>(Binv, V.s, T_.e, T_.a);
+    }
   }
 }
 
 // t = H sh;  omega = (t.s) / (t.t)
-template <int D2>
-__global__ void bicg_t_kernel(FaceArgs F, const double* __restrict__ C, BicgVecs V, double* red,
+template <typename T, int D2>
+__global__ void bicg_t_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
   double v[2] = {0.0, 0.0};
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const double tv = (F.ftype[T_.e] != 1) ? face_apply<double, D2>(C, V.sh, F, T_.e, T_.a) : 0.0;
+    const T tv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, V.sh, F, T_.e, T_.a) : (T)0;
     V.t[T_.t] = tv;
-    v[0] = fma(tv, V.s[T_.t], v[0]);
-    v[1] = fma(tv, tv, v[1]);
+    v[0] = fma((double)tv, (double)V.s[T_.t], v[0]);
+    v[1] = fma((double)tv, (double)tv, v[1]);
   }
   double out[2];
   if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) scal[B_OMEGA] = (out[1] > 0.0) ? out[0] / out[1] : 0.0;
 }
 
 // x += alpha ph + omega sh;  r = s - omega t;  rho' = rhat.r;  beta = (rho'/rho)(alpha/omega)
-template <int D2>
-__global__ void bicg_x_kernel(FaceArgs F, BicgVecs V, double* red, unsigned int* counter, double* scal) {
+template <typename T, int D2>
+__global__ void bicg_x_kernel(FaceArgs F, BicgVecs<T> V, double* red, unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
   const double alpha = scal[B_ALPHA], omega = scal[B_OMEGA];
   double v[2] = {0.0, 0.0};
@@ -670,11 +694,11 @@ __global__ void bicg_x_kernel(FaceArgs F, BicgVecs V, double* red, unsigned int*
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
     const int64_t t = T_.t;
-    V.x[t] += alpha * V.ph[t] + omega * V.sh[t];
-    const double rv = V.s[t] - omega * V.t[t];
+    V.x[t] = fma((T)alpha, V.ph[t], fma((T)omega, V.sh[t], V.x[t]));
+    const T rv = fma((T)(-omega), V.t[t], V.s[t]);
     V.r[t] = rv;
-    v[0] = fma(V.rh[t], rv, v[0]);
-    v[1] = fma(rv, rv, v[1]);
+    v[0] = fma((double)V.rh[t], (double)rv, v[0]);
+    v[1] = fma((double)rv, (double)rv, v[1]);
   }
   double out[2];
   if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
@@ -819,7 +843,8 @@ static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStre
 // graphs captured with or without the coarse correction are not interchangeable
 static void match_graphs(hdg_mesh* M, bool tl) {
   if (M->graphs_tl == tl) return;
-  cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32};
+  cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg, &M->graph_bicg32,
+                           &M->wgraph_bicg, &M->wgraph_bicg32};
   for (cudaGraphExec_t* g : gs)
     if (*g) {
       cudaGraphExecDestroy(*g);
@@ -846,6 +871,7 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
     M->red_blocks = kMaxBlocks;
   }
   if (M->beta_q && !M->d_bicg) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * nv));
+  if (M->beta_q && mixed && !M->d_bicg32) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg32, sizeof(float) * 4 * nv));
   if (mixed && !M->d_C32) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_C32, sizeof(float) * M->nelt * M->tab.m * M->tab.m));
     HDG_CUDA_TRY(cudaMalloc(&M->d_BJ32, sizeof(float) * M->nfc * M->tab.d2 * M->tab.d2));
@@ -1013,47 +1039,93 @@ struct Solver {
     return HDG_OK;
   }
 
-  static int bicg_run(hdg_mesh* M, bool have_x, double tol2, int maxit, int* iters, bool* bad) {
+  // One BiCGStab solve of H_T x = rhs to ||r|| <= sqrt(tol2) (absolute), T in {double, float},
+  // block-Jacobi or two-level right preconditioning; the iterations run in a device-driven
+  // conditional WHILE loop (host-driven replays when the driver refuses conditional nodes).
+  template <typename T>
+  static int bicg_run(hdg_mesh* M, const T* C, const T* Binv, const T* rhs, BicgVecs<T> V, bool have_x,
+                      double* scal, double tol2, int maxit, cudaGraphExec_t* graph, cudaGraphExec_t* wg,
+                      int* iters, bool* bad) {
     FaceArgs F = face_args(M);
-    const int nb = nblocks(M);
-    const int64_t nv = M->nfc * D2;
-    BicgVecs V{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + nv, M->d_bicg + 2 * nv,
-               M->d_bicg + 3 * nv};
-    double* scal = M->d_scal;
+    const int nb = nblocks_t<T>(M);
     double hs[B_NSCAL] = {0};
     hs[B_TOL2] = tol2;
     hs[B_MAXIT] = (double)maxit;
+    hs[B_MAXBODIES] = (double)(maxit / kGraphIters + 2);  // bound of the device-driven loop
     HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
-    bicg_init_kernel<D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, V, have_x, M->d_red, M->d_counter, scal);
+    const bool tl = M->coarse != nullptr && M->coarse->ready;
+    match_graphs(M, tl);
+    const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
+    const int per_it = tl ? 7 + 2 * coarse_cycle_kernels(M->coarse) : 5;  // kernels per iteration
+    bicg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, V, have_x, M->d_red, M->d_counter, scal);
     M->launches++;
     HDG_CUDA_TRY(cudaGetLastError());
-    if (!M->graph_bicg) {
-      if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
-      cudaStream_t cs = M->cap_stream;
-      cudaGraph_t g;
-      HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      for (int it = 0; it < kGraphIters; ++it) {
-        bicg_p_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
-        bicg_v_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
-        bicg_s_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_BJ, V, scal);
-        bicg_t_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, V, M->d_red, M->d_counter, scal);
-        bicg_x_kernel<D2><<<nb, kNT, 0, cs>>>(F, V, M->d_red, M->d_counter, scal);
+    if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = M->cap_stream;
+    auto iteration = [&](cudaStream_t st) {
+      if (tl) {
+        bicg_p_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
+        coarse_cycle<T, D2>(M, CA, V.p, st, scal + B_DONE);
+        bicg_tl_kernel<T, D2, B_DONE><<<nb, kNT, 0, st>>>(F, CA, Binv, V.p, V.ph, scal);
+      } else {
+        bicg_p_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
       }
-      HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
-      HDG_CUDA_TRY(cudaGraphInstantiate(&M->graph_bicg, g, 0));
-      cudaGraphDestroy(g);
+      bicg_v_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
+      if (tl) {
+        bicg_s_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
+        coarse_cycle<T, D2>(M, CA, V.s, st, scal + B_DONE);
+        bicg_tl_kernel<T, D2, B_DONE><<<nb, kNT, 0, st>>>(F, CA, Binv, V.s, V.sh, scal);
+      } else {
+        bicg_s_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
+      }
+      bicg_t_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
+      bicg_x_kernel<T, D2><<<nb, kNT, 0, st>>>(F, V, M->d_red, M->d_counter, scal);
+    };
+    auto body = [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+      for (int it = 0; it < kGraphIters; ++it) iteration(st);
+      loop_control_kernel<<<1, 32, 0, st>>>(h, scal, B_DONE, B_BODIES, B_MAXBODIES);
+    };
+    if (!*wg && !M->no_cond_graphs) {
+      if (!build_while_graph(cs, wg, body)) M->no_cond_graphs = true;
     }
     double hv[B_NSCAL];
-    for (;;) {
+    if (*wg) {
+      HDG_CUDA_TRY(cudaGraphLaunch(*wg, M->stream));
+      M->launches += 1;
       HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
       HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
-      if (hv[B_DONE] != 0.0) break;
-      HDG_CUDA_TRY(cudaGraphLaunch(M->graph_bicg, M->stream));
-      M->launches += 5 * kGraphIters;
+      M->launches += (int64_t)(per_it * kGraphIters + 1) * (int64_t)hv[B_BODIES];
+    } else {
+      if (!*graph) {
+        cudaGraph_t g;
+        HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < kGraphIters; ++it) iteration(cs);
+        HDG_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+        HDG_CUDA_TRY(cudaGraphInstantiate(graph, g, 0));
+        cudaGraphDestroy(g);
+      }
+      for (;;) {
+        HDG_CUDA_TRY(cudaMemcpyAsync(hv, scal, sizeof(hv), cudaMemcpyDeviceToHost, M->stream));
+        HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+        if (hv[B_DONE] != 0.0) break;
+        HDG_CUDA_TRY(cudaGraphLaunch(*graph, M->stream));
+        M->launches += per_it * kGraphIters;
+      }
     }
     *iters = (int)hv[B_ITERS];
     *bad = hv[B_BAD] != 0.0;
     return HDG_OK;
+  }
+
+  BicgVecs<double> static bicg_vecs64(hdg_mesh* M) {
+    const int64_t nv = M->nfc * D2;
+    return BicgVecs<double>{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + nv, M->d_bicg + 2 * nv,
+                            M->d_bicg + 3 * nv};
+  }
+  BicgVecs<float> static bicg_vecs32(hdg_mesh* M) {
+    const int64_t nv = M->nfc * D2;
+    return BicgVecs<float>{M->d_x32, M->d_q32, M->d_z32, M->d_p32, reinterpret_cast<float*>(M->d_q), M->d_bicg32,
+                           M->d_bicg32 + nv, M->d_bicg32 + 2 * nv, M->d_bicg32 + 3 * nv};
   }
 
   // ||b - H x||_2 over the free dofs in FP64, r written to `r`.
@@ -1069,6 +1141,51 @@ struct Solver {
     HDG_CUDA_TRY(cudaMemcpyAsync(&rr, scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
     HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
     *rnorm = std::sqrt(rr);
+    return HDG_OK;
+  }
+
+  // The FP64 solve from x (zero start unless have_x): BiCGStab with up to three restarted
+  // passes when convection makes H non-symmetric, else PCG with one restarted pass when the
+  // recursive residual converged but the true one did not.
+  static int fp64_solve(hdg_mesh* M, bool have_x, double tol, int maxit, int* total_it, bool* converged, bool* bad,
+                        double* rnorm) {
+    const double bnorm = M->bnorm;
+    int rc;
+    *total_it = 0;
+    *converged = false;
+    *bad = false;
+    if (M->beta_q) {
+      for (int pass = 0; pass < 3 && !*converged && *total_it < maxit; ++pass) {
+        int it;
+        rc = bicg_run<double>(M, M->d_C, M->d_BJ, M->d_b, bicg_vecs64(M), have_x, M->d_scal, tol * tol,
+                              maxit - *total_it, &M->graph_bicg, &M->wgraph_bicg, &it, bad);
+        if (rc) return rc;
+        *total_it += it;
+        rc = true_residual(M, M->d_x, M->d_q, rnorm);
+        if (rc) return rc;
+        *converged = *rnorm <= tol * 1.0000001 || bnorm == 0.0;
+        have_x = true;  // restart from the current iterate if the recursive residual drifted
+        if (*bad && !*converged) *bad = false;
+      }
+      return HDG_OK;
+    }
+    int it;
+    rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, have_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_scal,
+                         tol * tol, maxit, &M->graph64, &it, bad);
+    if (rc) return rc;
+    *total_it = it;
+    rc = true_residual(M, M->d_x, M->d_q, rnorm);
+    if (rc) return rc;
+    *converged = *rnorm <= tol * 1.0000001 || bnorm == 0.0;
+    if (!*converged && it < maxit && !*bad) {
+      rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, true, M->d_r, M->d_z, M->d_p, M->d_q, M->d_scal,
+                           tol * tol, maxit - it, &M->graph64, &it, bad);
+      if (rc) return rc;
+      *total_it += it;
+      rc = true_residual(M, M->d_x, M->d_q, rnorm);
+      if (rc) return rc;
+      *converged = *rnorm <= tol * 1.0000001;
+    }
     return HDG_OK;
   }
 
@@ -1091,7 +1208,7 @@ struct Solver {
       M->launches++;
       M->c32_ready = true;
     }
-    if (M->coarse && !M->beta_q && !M->coarse->ready) {
+    if (M->coarse && !M->coarse->ready) {
       rc = coarse_build(M);
       if (rc) return rc;
     }
@@ -1102,63 +1219,61 @@ struct Solver {
       mask_dirichlet_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, D2, M->d_x);
       M->launches++;
     }
-    if (M->beta_q) {
-      // non-symmetric trace matrix (convection): block-Jacobi BiCGStab in FP64
-      if (mixed) return fail(HDG_ERR_UNSUPPORTED, "the mixed-precision solve is for symmetric (beta = 0) problems");
-      bool have_x = x0 != nullptr;
-      for (int pass = 0; pass < 3 && !converged && total_it < maxit; ++pass) {
-        int it;
-        rc = bicg_run(M, have_x, tol * tol, maxit - total_it, &it, &bad);
-        if (rc) return rc;
-        total_it += it;
-        rc = true_residual(M, M->d_x, M->d_q, &rnorm);
-        if (rc) return rc;
-        converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
-        have_x = true;  // restart from the current iterate if the recursive residual drifted
-        if (bad && !converged) bad = false;
-      }
-    } else if (!mixed) {
-      int it;
-      rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, x0 != nullptr, M->d_r, M->d_z, M->d_p, M->d_q,
-                           M->d_scal, tol * tol, maxit, &M->graph64, &it, &bad);
+    if (!mixed) {
+      rc = fp64_solve(M, x0 != nullptr, tol, maxit, &total_it, &converged, &bad, &rnorm);
       if (rc) return rc;
-      total_it = it;
-      rc = true_residual(M, M->d_x, M->d_q, &rnorm);
-      if (rc) return rc;
-      converged = rnorm <= tol * 1.0000001 || bnorm == 0.0;
-      if (!converged && it < maxit && !bad) {
-        // recursive residual converged but the true one did not: one more restarted pass
-        rc = pcg_run<double>(M, M->d_C, M->d_BJ, M->d_b, M->d_x, true, M->d_r, M->d_z, M->d_p, M->d_q, M->d_scal,
-                             tol * tol, maxit - it, &M->graph64, &it, &bad);
-        if (rc) return rc;
-        total_it += it;
-        rc = true_residual(M, M->d_x, M->d_q, &rnorm);
-        if (rc) return rc;
-        converged = rnorm <= tol * 1.0000001;
-      }
     } else {
       // mixed: FP32 copies of C^K and the block inverses, FP64 outer residual and update
       if (!x0) HDG_CUDA_TRY(cudaMemsetAsync(M->d_x, 0, sizeof(double) * nv, M->stream));
+      double prev = INFINITY;
+      bool fallback = false;
       for (int outer = 0; outer < 30; ++outer) {
         rc = true_residual(M, M->d_x, M->d_r, &rnorm);
         if (rc) return rc;
         if (rnorm <= tol || bnorm == 0.0) {
           converged = true;
+          bad = false;
+          break;
+        }
+        if (outer > 0 && !(rnorm < prev)) {
+          // the last FP32 correction did not reduce the FP64 residual (the FP32 iteration
+          // stagnated or diverged): undo it and finish in FP64 from the previous iterate
+          HDG_CUDA_TRY(cudaMemcpyAsync(M->d_x, M->d_z, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
+          rnorm = prev;
+          fallback = true;
           break;
         }
         if (total_it >= maxit) break;
+        // an inner breakdown still leaves a usable iterate: the outer step keeps it and restarts
+        // the inner solve from the new FP64 residual
+        bad = false;
+        prev = rnorm;
+        HDG_CUDA_TRY(cudaMemcpyAsync(M->d_z, M->d_x, sizeof(double) * nv, cudaMemcpyDeviceToDevice, M->stream));
         convert_kernel<float><<<304, 256, 0, M->stream>>>(M->d_r, M->d_r32, nv);
         M->launches++;
         int it;
-        const double itol = M->inner_rtol * rnorm;
-        rc = pcg_run<float>(M, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, false, M->d_q32, M->d_z32, M->d_p32,
-                            reinterpret_cast<float*>(M->d_q), M->d_scal, itol * itol, maxit - total_it, &M->graph32,
-                            &it, &bad);
+        // each inner solve reduces its residual by inner_rtol, but no further than half the
+        // remaining distance to the outer target (the last step stops as soon as it suffices)
+        const double itol = std::max(M->inner_rtol * rnorm, 0.5 * tol);
+        if (M->beta_q)  // convection: FP32 inner BiCGStab
+          rc = bicg_run<float>(M, M->d_C32, M->d_BJ32, M->d_r32, bicg_vecs32(M), false, M->d_scal, itol * itol,
+                               maxit - total_it, &M->graph_bicg32, &M->wgraph_bicg32, &it, &bad);
+        else
+          rc = pcg_run<float>(M, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, false, M->d_q32, M->d_z32, M->d_p32,
+                              reinterpret_cast<float*>(M->d_q), M->d_scal, itol * itol, maxit - total_it,
+                              &M->graph32, &it, &bad);
         if (rc) return rc;
         total_it += it;
         axpy_f32_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_x32, M->d_x);
         M->launches++;
-        if (bad) break;
+      }
+      if (fallback && total_it < maxit) {
+        rc = ensure_bj<double>(M);
+        if (rc) return rc;
+        int it64 = 0;
+        rc = fp64_solve(M, true, tol, maxit - total_it, &it64, &converged, &bad, &rnorm);
+        if (rc) return rc;
+        total_it += it64;
       }
     }
     finish_kernel<<<nb, kNT, 0, M->stream>>>(nv, M->d_ftype, D2, M->d_x, M->d_uhatD, uhat);
@@ -1229,7 +1344,7 @@ struct Solver {
     // the same for the FP32 inner iteration (mixed precision), on FP32 copies of C^K and B^-1
     int best32 = M->face_blocks32;
     float best32_t = 1e30f;
-    if (!M->beta_q) {
+    {
       rc = ensure_workspace(M, true);
       if (rc) return rc;
       if (!M->c32_ready) {
@@ -1275,7 +1390,8 @@ struct Solver {
     const bool changed = best != old || best32 != M->face_blocks32;
     M->face_blocks32 = best32;
     if (changed) {
-      cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg};
+      cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg,
+                               &M->graph_bicg32, &M->wgraph_bicg, &M->wgraph_bicg32};
       for (cudaGraphExec_t* g : gs)
         if (*g) {
           cudaGraphExecDestroy(*g);
@@ -1708,7 +1824,6 @@ int autotune_face_grid(hdg_mesh* M, hdg_tuning* out) {
 int coarse_precond_apply(hdg_mesh* M, const double* r, double* z) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "preconditioner before hdg_assemble_condense");
   if (!M->coarse) return fail(HDG_ERR_STATE, "no coarse space: call hdg_set_coarse_space first");
-  if (M->beta_q) return fail(HDG_ERR_UNSUPPORTED, "the two-level preconditioner is for beta = 0");
   switch (M->tab.d2) {
     case 1: return Solver<1>::precond_apply(M, r, z);
     case 3: return Solver<3>::precond_apply(M, r, z);
