@@ -1,28 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the HDG hot path on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
 
-Workload (N=1): unit cube, 16^3 subcubes x 6 Kuhn tetrahedra (24,576 elements), k = 3,
-kappa = 1 + 0.5 sin(2 pi x) cos(2 pi y), c = 1 + x^2, manufactured u = (1 + x^2 + yz)
-exp(0.5x - y + z), Dirichlet on x = 0 and x = 1, Neumann elsewhere.  Synthetic, seeded.
+Workload (N=1): the largest single-GPU configuration, cube48_k2_conv -- unit cube, 48^3
+subcubes x 6 Kuhn tetrahedra (663,552 elements, 1,340,928 faces, 8,045,568 trace unknowns),
+interior vertices jittered by U(-0.2h, 0.2h)^3 (seed 0), k = 2, convection beta = (y, -x, 0.5 z),
+kappa = 1 + 0.5 sin(2 pi z), c = 1, tau = 2.5, manufactured u = sin(pi x) sin(pi y) sin(pi z),
+Dirichlet on every face.  Synthetic, seeded.
 
 One step = the whole hot path on one batch of resident inputs:
-  assemble + condense (K1, double-float)  ->  trace solve to ||b - H u||/||b|| <= 1e-10 (FP32
-  inner PCG with FP64 refinement, two-level preconditioner)  ->  recover (K2)  ->
-  postprocess (K5).
+  assemble + condense (K1, double-float on the FP32 pipe, LU of the non-symmetric Schur
+  complement)  ->  trace solve to ||b - H u||/||b|| <= 1e-10 (FP32 inner BiCGStab with FP64
+  residuals and refinement, two-level preconditioner)  ->  recover (K2)  ->  postprocess (K5).
 value = elements/s over the metric's phases (assemble + condense + recover), timed with CUDA
 events on the launching stream; the trace solve's time-to-1e-10 is reported beside it for the
-plain FP64 block-Jacobi PCG (zero start), the mixed-precision solve and the two-level
-preconditioned solves.
-L2 is flushed (256 MiB write) before every step; the inputs (74 MB) are smaller than L2.
+plain FP64 block-Jacobi BiCGStab (zero start), the mixed-precision solve and the two-level
+preconditioned solves.  The inputs (3.4 GB) are larger than L2; L2 is also flushed (256 MiB
+write) before every step.
+Extras (N=1, rank 0, unless --no-extras): the reaction-diffusion workload cube16_k3 (24,576
+elements, k = 3) through the same step; the 64-problem mixed-degree batch; the random-field
+workload cube32_k2_grf's solve times with and without a learned initial guess.
 With --impl reference the FP64 CPU oracle is timed on the host cores on the same workload.
 """
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -34,32 +38,46 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="cube16_k3", s=16, k=3)
+HEADLINE = "cube48_k2_conv"
+EXTRA_RD = "cube16_k3"
 METRIC = "elements/sec (assemble+condense+recover) & time-to-1e-10 solve vs plain FP64 GPU"
 UNIT = "elements/s"
 # FP64 peak of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_MEASURED_TFLOPS = 1.19  # FMA-chain microbenchmark on this machine's GB300 (1 block/SM saturates)
+# FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; measured 74.8 TFLOP/s (FMA chain)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP32_MEASURED_TFLOPS = 74.8
 # FP64-equivalent peak of double-float arithmetic on the FP32 pipe: 152 SMs x 128 FP32 lanes x
 # 2.07 GHz / 12 FP32 instructions per compensated multiply-add (dacc_mac) x 2 flop
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
+HBM_FALLBACK_GBS = 6800.0
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one K1 launch at this workload,
-# from the ncu captures summarised under profiles/, valid while the kernel's sources (K1_SOURCES,
-# hashed together) are unchanged.
-K1_TRAFFIC = {"assemble_df.cu": {"sha256": "957b7963cd4e158eb2ffb756698557867a8bbfada4a45fca4abe240405bc4db3",
-                                 "bytes": 79899392 + 901170944},
-              "assemble.cu": {"sha256": None, "bytes": None}}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per element of one K1 launch, from
+# the ncu captures summarised under profiles/ (captured on a smaller mesh of the same workload
+# and scaled by the element count: K1 streams per-element data only, so traffic is proportional
+# to it), valid while the kernel's sources (K1_SOURCES, hashed together) are unchanged.
+K1_TRAFFIC = {
+    ("cube48_k2_conv", "assemble_df.cu"): {"sha256": None, "bytes_per_element": None, "captured": None},
+    ("cube16_k3", "assemble_df.cu"): {"sha256": None, "bytes_per_element": None, "captured": None},
+}
+# the sources of each K1 translation unit (the kernel and the device headers it includes)
+K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "device_df.cuh", "device_common.cuh"),
+              "assemble.cu": ("assemble.cu", "device_common.cuh")}
 
 
-def flops_per_element_k1(k):
-    """FP64 flops per element of the K1 algorithm (structured elimination), FMA = 2."""
+def _dims(k):
     n = (k + 1) * (k + 2) * (k + 3) // 6
     d2 = (k + 1) * (k + 2) // 2
-    m = 4 * d2
-    nq = (k + 2) ** 3
+    return n, d2, 4 * d2, (k + 2) ** 3, (k + 2) ** 2
+
+
+def flops_per_element_k1(k, conv=False):
+    """FP64 flops per element of the K1 algorithm (structured elimination), FMA = 2."""
+    n, d2, m, nq, nf = _dims(k)
     NP, MP = n * (n + 1) // 2, m * (m + 1) // 2
     chol = sum(2 * j + 3 + (n - j - 1) * (2 * j + 1) for j in range(n))
+    lu = sum(1 + (n - j - 1) + 2 * (n - j - 1) ** 2 for j in range(n))
     nn, np1, np2 = k + 2, (k + 1) * (k + 2) // 2, d2 * (d2 + 1) // 2
     f = 4 * nq                      # |K| w / kappa, |K| w c, |K| w f
     # M_{kappa^-1}, M_c and f^K by sum factorisation (1-D, 2-D, 3-D pair passes), tauPP
@@ -70,22 +88,48 @@ def flops_per_element_k1(k):
     f += (3 * n + m) * n * n        # W_* = L^-1 C_*^T, V = L^-1 E^T
     f += NP * (6 * n + 1)           # S_u += sum W^T W
     f += 20 * n * n                 # sum_* n_{l*} W_*
-    f += MP * (2 * n + 7)           # (n.n) V^T V + tauDD
-    f += chol                       # L_s L_s^T = S_u
     f += n * m * (2 * n + 1)        # G
-    f += (m + 1) * n * n            # H|h = L_s^-1 [G^T|f]
-    f += MP * (2 * n + 1) + 2 * m * n  # C -= H^T H, C_f
+    if not conv:
+        f += MP * (2 * n + 7)       # (n.n) V^T V + tauDD
+        f += chol                   # L_s L_s^T = S_u
+        f += (m + 1) * n * n        # H|h = L_s^-1 [G^T|f]
+        f += MP * (2 * n + 1) + 2 * m * n  # C -= H^T H, C_f
+        return f
+    # convection: weights, Gq, B_c, alphaDP, alphaDD, LU, two sets of forward substitutions,
+    # and the full (non-symmetric) C
+    f += 3 * nq * 8 + 4 * nf * 7    # bw, varpi beta.n
+    f += 6 * nq * n                 # Gq
+    f += 2 * n * (n + 1) * nq       # B_c (both triangles)
+    f += 3 * n * m * nf + 3 * 4 * d2 * d2 * nf  # alphaDP, alphaDD
+    f += lu                         # L U = S_u
+    f += (m + 1) * n * (n - 1) + m * n * (n + 1)  # [H_col|h] = L^-1 [.], H_row = U^-T G^T
+    f += m * m * (4 * n + 4) + 2 * m * n  # C = (n.n) V^T V + tauDD - alphaDD - H_row^T H_col, C_f
     return f
 
 
-def k1_bytes_per_element(k):
-    """Algorithmic HBM bytes of K1 per element: kappa, c, f, geometry, perms, tau in;
-    C^K (full), C_f^K and the recovery record out."""
-    n = (k + 1) * (k + 2) * (k + 3) // 6
-    m = 2 * (k + 1) * (k + 2)
-    nq = (k + 2) ** 3
+def k1_bytes_per_element(k, conv=False):
+    """Algorithmic HBM bytes of K1 per element: kappa, c, f (and beta at the volume and face
+    nodes), geometry, perms, tau in; C^K (full), C_f^K and the recovery record out."""
+    n, d2, m, nq, nf = _dims(k)
     rec = n * (m + 1) + n * m + 3 * n * n + n * (n + 1) + 12  # [H|h], V, W_*, U_s, U_M, normals
-    return 8 * (3 * nq + 12) + 4 * 4 + 8 * (m * m + m + rec)
+    inp = 8 * (3 * nq + 28) + 4 * 4 + 8 * 4
+    if conv:
+        inp += 8 * (3 * nq + 3 * 4 * nf)
+    return inp + 8 * (m * m + m + rec)
+
+
+def krylov_bytes_per_iteration(nelt, nfc, k, conv, fp32=True):
+    """Algorithmic HBM bytes of one inner Krylov iteration (block-Jacobi part; the coarse
+    cycles are not counted, so the fraction below is conservative): every C^K row read once
+    per operator application (2 per BiCGStab iteration, 1 per CG iteration), the block
+    inverses once per preconditioner application, and the vector passes of the method
+    (BiCGStab: 25 vectors read or written per iteration; CG: 12)."""
+    n, d2, m, nq, nf = _dims(k)
+    w = 4 if fp32 else 8
+    nv = nfc * d2
+    apps = 2 if conv else 1
+    vec = 25 if conv else 12
+    return apps * (nelt * m * m * w + nfc * d2 * d2 * w) + vec * nv * w
 
 
 def _sha(*paths):
@@ -96,9 +140,12 @@ def _sha(*paths):
     return h.hexdigest()
 
 
-# the sources of each K1 translation unit (the kernel and the device headers it includes)
-K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "device_df.cuh", "device_common.cuh"),
-              "assemble.cu": ("assemble.cu", "device_common.cuh")}
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 # ------------------------------------------------------------------ clocks
@@ -168,68 +215,108 @@ class ClockSampler:
 _ORACLE = {}
 
 
-def _oracle_init(name):
-    """Worker set-up: the workload's mesh, tables and coefficients, built once per process."""
+def _sub_mesh(coords, elems_sub):
+    """The expanded mesh of a set of elements on their own, in the global vertex numbering (so
+    each element's geometry, face orientation and perm are those of the full mesh), with the
+    faces that the set does not share listed as boundary faces."""
+    from oracle.geometry import LOCAL_FACES, ExpandedMesh
+
+    tri = np.sort(elems_sub[:, LOCAL_FACES].reshape(-1, 3), axis=1)
+    faces, counts = np.unique(tri, axis=0, return_counts=True)
+    return ExpandedMesh(coords, elems_sub, faces[counts == 1], np.zeros((0, 3), np.int64))
+
+
+def _oracle_init(name, samples):
+    """Worker set-up (outside the timed region): for every step, this worker's share of the
+    sampled elements as a mesh of their own, with its coefficients at the oracle's nodes."""
+    from oracle import convection as cv
     from oracle import hdg as ohdg
-    from oracle.geometry import ExpandedMesh
-    from workloads import boundary_faces, get_problem, kuhn_cube
+    from workloads import get_problem, kuhn_cube
 
     prob = get_problem(name)
-    c, e = kuhn_cube(prob.s)
-    d, n = boundary_faces(c, e, prob.classify)
-    mesh = ExpandedMesh(c, e, d, n)
+    c, e = kuhn_cube(prob.s, prob.jitter, prob.seed)
     tab = ohdg.Tables(prob.k)
-    X, Y, Z = ohdg.volume_nodes(mesh, tab)
-    _ORACLE.update(mesh=mesh, tab=tab, kap=prob.kappa(X, Y, Z), c=prob.c(X, Y, Z), f=prob.f(X, Y, Z),
-                   uhat=np.zeros((mesh.nfc, tab.d2)))
+    work = []
+    for idx in samples:
+        mesh = _sub_mesh(c, np.asarray(e)[np.sort(idx)])
+        X, Y, Z = ohdg.volume_nodes(mesh, tab)
+        w = dict(mesh=mesh, kap=prob.kappa(X, Y, Z), c=prob.c(X, Y, Z), f=prob.f(X, Y, Z),
+                 uhat=np.zeros((mesh.nfc, tab.d2)))
+        if prob.beta is not None:
+            FX, FY, FZ = cv.element_face_nodes(mesh, tab)
+            w.update(bq=prob.beta(X, Y, Z), bf=prob.beta(FX, FY, FZ))
+        work.append(w)
+    _ORACLE.update(prob=prob, tab=tab, work=work)
 
 
-def _oracle_chunk(idx):
-    """Oracle assemble + condense + recover on a chunk of elements (one worker process)."""
+def _oracle_chunk(step):
+    """Oracle assemble + condense + recover of this worker's elements of one step."""
+    from oracle import convection as cv
     from oracle import hdg as ohdg
     o = _ORACLE
-    blk = ohdg.local_blocks(o["mesh"], o["tab"], o["kap"], o["c"], o["f"], tau=1.0, elems=idx)
-    CK, Cf, X2, xf = ohdg.local_solvers(blk)
-    ohdg.recover(o["mesh"], X2, xf, o["uhat"], elems=idx)
-    return len(idx)
+    w = o["work"][step]
+    blk = ohdg.local_blocks(w["mesh"], o["tab"], w["kap"], w["c"], w["f"], tau=o["prob"].tau)
+    if "bq" in w:
+        Bc, aDP, aDD = cv.convection_blocks(w["mesh"], o["tab"], w["bq"], w["bf"])
+        CK, Cf, X2, xf, _ = cv.local_solvers_conv(blk, Bc, aDP, aDD)
+    else:
+        CK, Cf, X2, xf = ohdg.local_solvers(blk)
+    ohdg.recover(w["mesh"], X2, xf, w["uhat"])
+    return w["mesh"].nelt
 
 
-def oracle_baseline(sample_elems, steps=1, warmup=0):
-    """Time the oracle as it stands on the host cores: elements/s (assemble+condense+recover)."""
+def oracle_baseline(name, sample_elems, steps=1, warmup=0):
+    """Time the oracle as it stands on the host cores: elements/s (assemble+condense+recover)
+    on `steps` random samples of `sample_elems` elements of the workload's mesh."""
     import multiprocessing as mp
 
-    nelt = 6 * WORKLOAD["s"] ** 3
+    from workloads import get_problem
+
+    prob = get_problem(name)
+    nelt = 6 * prob.s ** 3
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(0)
+    nst = steps + warmup
+    picks = [np.sort(rng.choice(nelt, size=sample_elems, replace=False)) for _ in range(nst)]
+    per_worker = [[np.array_split(p, cores)[wk] for p in picks] for wk in range(cores)]
     ctx = mp.get_context("spawn")
     env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env_backup:
         os.environ[k] = "1"
     try:
-        with ctx.Pool(cores, initializer=_oracle_init, initargs=(WORKLOAD["name"],)) as pool:
-            pool.map(_oracle_chunk, [np.arange(2)] * cores)  # wait for every worker's set-up
+        pools = []
+        # one single-process pool per worker, so each worker holds exactly its own share
+        for wk in range(cores):
+            pools.append(ctx.Pool(1, initializer=_oracle_init, initargs=(name, per_worker[wk])))
+        for p in pools:  # wait for every worker's set-up
+            p.apply(len, ([],))
 
-            def one():
-                idx = np.sort(rng.choice(nelt, size=sample_elems, replace=False))
-                t0 = time.perf_counter()
-                done = sum(pool.map(_oracle_chunk, np.array_split(idx, cores)))
-                return done, time.perf_counter() - t0
-            for _ in range(warmup):
-                one()
-            tot_e, tot_t = 0, 0.0
-            for _ in range(steps):
-                ne, dt = one()
-                tot_e += ne
-                tot_t += dt
+        def one(step):
+            t0 = time.perf_counter()
+            res = [p.apply_async(_oracle_chunk, (step,)) for p in pools]
+            done = sum(r.get() for r in res)
+            return done, time.perf_counter() - t0
+        for s in range(warmup):
+            one(s)
+        tot_e, tot_t = 0, 0.0
+        for s in range(warmup, nst):
+            ne, dt = one(s)
+            tot_e += ne
+            tot_t += dt
     finally:
+        for p in pools:
+            p.close()
+            p.join()
         for k, v in env_backup.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
+    kind = ("numpy FP64 literal blocks + convection blocks (eq. 9.1) + LU of A_1 + recovery" if prob.beta is not None
+            else "numpy FP64 literal blocks + LU of A_1 + recovery")
     return {"value": tot_e / tot_t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{sample_elems} random elements of the {nelt}-element mesh per step "
-                      f"x {steps} step(s); numpy FP64 literal blocks + LU of A_1 + recovery, "
+            "sample": f"{sample_elems} random elements of the {nelt}-element {name} mesh per step x {steps} step(s) "
+                      f"(each step's elements as a mesh of their own, set up outside the timed region); {kind}, "
                       f"{cores} spawn workers with 1 BLAS thread each"}
 
 
@@ -252,40 +339,63 @@ def job_value(nelt, steps, world, phase_ms):
 
 
 # ------------------------------------------------------------------ GPU arm
-def run_gpu(args, rank, world, local_rank):
+class Workload:
+    """A workload's mesh on the GPU and its PDE data at the library's nodes (host copies kept
+    for the end-to-end leg)."""
+
+    def __init__(self, name, dev, stream, s=None):
+        import torch
+
+        from paper_1305_1489_gb300 import HDGMesh
+        from workloads import boundary_faces, get_problem, kuhn_cube
+
+        self.name = name
+        self.prob = prob = get_problem(name) if s is None else get_problem(name).at(s=s)
+        c, e = kuhn_cube(prob.s, prob.jitter, prob.seed)
+        d, n = boundary_faces(c, e, prob.classify)
+        self.M = M = HDGMesh(c, e, d, n, prob.k, stream=stream)
+        self.conv = prob.beta is not None
+        X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+        FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
+        self.X, self.Y, self.Z, self.FX, self.FY, self.FZ = X, Y, Z, FX, FY, FZ
+        host = {"kappa": prob.kappa(X, Y, Z), "c": prob.c(X, Y, Z), "f": prob.f(X, Y, Z),
+                "uD": prob.uD(FX, FY, FZ)}
+        if prob.gN is not None:
+            host["gN"] = np.stack(prob.gN(FX, FY, FZ))
+        if self.conv:
+            EX, EY, EZ = (t.cpu().numpy() for t in M.element_face_nodes())
+            host["beta"] = np.stack(prob.beta(X, Y, Z))
+            host["beta_f"] = np.stack(prob.beta(EX, EY, EZ))
+            host["tau"] = np.full((M.nelt, 4), prob.tau)
+        self.host = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in host.items()}
+        self.dv = {k: torch.from_numpy(v).to(dev) for k, v in self.host.items()}
+        self.set_inputs()
+
+    def set_inputs(self):
+        dv = self.dv
+        if self.conv:
+            self.M.set_coefficients(dv["kappa"], dv["c"], dv["f"], dv["tau"], beta=dv["beta"], beta_faces=dv["beta_f"])
+        else:
+            self.M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
+        self.M.set_boundary_data(dv["uD"], dv.get("gN"))
+
+    def hierarchy(self):
+        from workloads import kuhn_p1_hierarchy
+        return kuhn_p1_hierarchy(self.prob.s, self.prob.dirichlet_planes)
+
+
+def run_workload(W, args, stream, dev, world=1, full=True):
+    """The step of workload W timed over args.steps (after args.warmup), and, with full, the
+    time-to-1e-10 comparison, the diagnostics, the end-to-end leg and the rooflines."""
     import torch
 
-    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, HDG_MIXED_FP32, HDGMesh, build
-    from workloads import boundary_faces, get_problem, kuhn_cube
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, HDG_MIXED_FP32
 
-    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1305_1489_gb300", "libhdg.so")):
-        build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    prob = get_problem(WORKLOAD["name"])
-    c, e = kuhn_cube(prob.s)
-    d, n = boundary_faces(c, e, prob.classify)
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.set_stream(stream)
-    M = HDGMesh(c, e, d, n, prob.k, stream=stream)
+    M, prob = W.M, W.prob
     nelt = M.nelt
-    X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
-    FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
-    host = {
-        "kappa": prob.kappa(X, Y, Z), "c": prob.c(X, Y, Z), "f": prob.f(X, Y, Z),
-        "uD": prob.uD(FX, FY, FZ), "gN": np.stack(prob.gN(FX, FY, FZ)),
-    }
-    dv = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in host.items()}
-    M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
-    M.set_boundary_data(dv["uD"], dv["gN"])
     M.set_inner_tolerance(args.inner_rtol)
     asm_prec = HDG_DF32 if args.asm == "df32" else HDG_FP64
-    from workloads import kuhn_p1_hierarchy
-    hierarchy = kuhn_p1_hierarchy(prob.s, prob.dirichlet_planes)
+    hierarchy = W.hierarchy()
     step_prec = HDG_MIXED_FP32 if args.solve == "mixed" else HDG_FP64
     if args.coarse:
         M.set_coarse_space(*hierarchy)
@@ -311,9 +421,10 @@ def run_gpu(args, rank, world, local_rank):
         if rec is not None:
             rec.append((e0, e1, e2, e3, e4, it, rr))
 
-    clk = ClockSampler(local_rank)
-    clk.start()
-    time.sleep(0.5)  # nvidia-smi is up and sampling before the timed region
+    clk = ClockSampler(dev.index if dev.index is not None else 0)
+    if full:
+        clk.start()
+        time.sleep(0.5)  # nvidia-smi is up and sampling before the timed region
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -334,23 +445,44 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t0
-    clocks = clk.stop(tw0, time.time())
+    clocks = clk.stop(tw0, time.time()) if full else None
     launches = M.launches - launches0
     total_ms = tstart.elapsed_time(tend)
     t_asm = [a.elapsed_time(b) for a, b, *_ in recs]
     t_sol = [b.elapsed_time(c_) for _, b, c_, *_ in recs]
     t_rec = [c_.elapsed_time(d_) for _, _, c_, d_, *_ in recs]
     t_pp = [d_.elapsed_time(e_) for _, _, _, d_, e_, *_ in recs]
+    its = [r[5] for r in recs]
     phase_ms = sum(t_asm) + sum(t_rec)
     phase_ms, total_ms = max_over_ranks([phase_ms, total_ms], world, dev)
     value = job_value(nelt, args.steps, world, phase_ms)
+    phases = {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
+              "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))}
+    peaks = _measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    hbm_note = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback"
+    # roofline of the step's solve: algorithmic bytes of the inner Krylov iterations over their time
+    inner_fp32 = step_prec == HDG_MIXED_FP32
+    kb = krylov_bytes_per_iteration(nelt, M.nfc, prob.k, W.conv, fp32=inner_fp32)
+    it_mean = float(np.mean(its))
+    sol_ach = kb / (phases["trace_solve"] / 1e3 / max(it_mean, 1.0)) / 1e9
+    solve_roofline = {"bound": "hbm", "achieved": sol_ach, "peak": hbm, "unit": "GB/s", "frac": sol_ach / hbm,
+                      "peak_note": hbm_note, "iterations": it_mean,
+                      "ms_per_iteration": phases["trace_solve"] / max(it_mean, 1.0),
+                      "bytes_per_iteration": kb,
+                      "work": ("per inner iteration: " + ("2" if W.conv else "1") + " reads of the "
+                               + ("FP32" if inner_fp32 else "FP64") + " C^K and the block inverses, "
+                               + ("25" if W.conv else "12") + " vector passes; the coarse cycles, the FP64 "
+                               "refinement and the set-up (Galerkin hierarchy, block inverses) are inside the "
+                               "time but not in the bytes, so the fraction is a lower bound")}
+    out = {"value": value, "nelt": nelt, "nfc": M.nfc, "trace_dofs": M.nfc * M.d2, "k": prob.k,
+           "phases_ms": phases, "iterations_per_step": it_mean, "gpu_launches": int(launches),
+           "ms_per_step": total_ms / args.steps, "wall_s_timed": wall, "clocks": clocks, "autotune": tuned,
+           "solve_roofline": solve_roofline, "coarse_levels": [int(x) for x in hierarchy[0]] if args.coarse else None}
+    if not full:
+        return out
 
-    if args.only_steps:
-        return {"phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
-                              "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
-                "value": value, "gpu_launches": int(launches), "ms_per_step": total_ms / args.steps}
-
-    # time-to-1e-10 (zero start): plain FP64 block-Jacobi PCG, mixed precision, and both with the
+    # time-to-1e-10 (zero start): plain FP64 block-Jacobi, mixed precision, and both with the
     # two-level preconditioner (its Galerkin set-up after the assembly is inside the time)
     solve = {}
     cases = (("plain_fp64", HDG_FP64, False), ("mixed_fp32_fp64", HDG_MIXED_FP32, False),
@@ -360,31 +492,33 @@ def run_gpu(args, rank, world, local_rank):
             M.set_coarse_space(*hierarchy)
         else:
             M.set_coarse_space(None, None, None)
-        ts, its = [], []
-        for _ in range(3):
+        ts, its_ = [], []
+        for _ in range(args.solve_reps):
             M.assemble_condense(asm_prec)
             torch.cuda.synchronize()
             a, b = ev(), ev()
             a.record(stream)
-            uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=prec)
+            uh, it, rr = M.solve_trace(rtol=1e-10, maxit=40000, precision=prec, raise_on_fail=False)
             b.record(stream)
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
-            its.append(it)
-        solve[name] = {"ms": float(np.median(ts)), "iterations": its[-1], "relres": rr}
+            its_.append(it)
+        solve[name] = {"ms": float(np.median(ts)), "iterations": its_[-1], "relres": rr, "converged": bool(rr <= 1e-10)}
     for name in ("mixed_fp32_fp64", "two_level_fp64", "two_level_mixed"):
         solve["speedup_" + name + "_vs_plain"] = solve["plain_fp64"]["ms"] / solve[name]["ms"]
+    solve["method"] = "BiCGStab (non-symmetric trace matrix)" if W.conv else "CG"
     if args.coarse:
         M.set_coarse_space(*hierarchy)
     else:
         M.set_coarse_space(None, None, None)
+    out["solve_time_to_1e-10"] = solve
 
-    # superconvergence diagnostics (Section 9, eq. 10.2) of the step's solution: the HDG
-    # projection of the exact (q, u), the face projection of u and the error norms, timed
-    # with CUDA events (outside the metric)
+    # discretisation errors (eq. 10.1-10.2) of the step's solution and the HDG projection
+    # diagnostics (Section 9, eq. 10.2), timed with CUDA events (outside the metric)
     M.assemble_condense(asm_prec)
     uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
     q, u = M.recover(uh)
+    X, Y, Z, FX, FY, FZ = W.X, W.Y, W.Z, W.FX, W.FY, W.FZ
     XF, YF, ZF = (t.cpu().numpy() for t in M.element_face_nodes())
     q_vol = torch.from_numpy(np.ascontiguousarray(np.stack(prob.q(X, Y, Z)))).to(dev)
     q_face = torch.from_numpy(np.ascontiguousarray(np.stack(prob.q(XF, YF, ZF)))).to(dev)
@@ -392,7 +526,7 @@ def run_gpu(args, rank, world, local_rank):
     u_face = torch.from_numpy(np.ascontiguousarray(prob.u(XF, YF, ZF))).to(dev)
     u_fn = torch.from_numpy(np.ascontiguousarray(prob.u(FX, FY, FZ))).to(dev)
     tp = []
-    for _ in range(4):
+    for _ in range(3):
         torch.cuda.synchronize()
         a, b = ev(), ev()
         a.record(stream)
@@ -405,14 +539,16 @@ def run_gpu(args, rank, world, local_rank):
     e_pf, ref_f = M.face_norm2(Pf - uh, None)[0], M.face_norm2(None, u_fn)[1]
     e_u = M.volume_norm2(u, u_vol)[0]
     e_uhat = M.face_norm2(uh, u_fn)[0]
-    diagnostics = {"hdg_projection_ms": float(np.median(tp[1:])),
-                   "eps_u": float(np.sqrt(e_pu / ref_u)), "eps_uhat": float(np.sqrt(e_pf / ref_f)),
-                   "e_u": float(np.sqrt(e_u / ref_u)), "e_uhat": float(np.sqrt(e_uhat / ref_f)),
-                   "note": "eq. 10.1-10.2 ratios of the step's solution (trace solve to 1e-10); the HDG "
-                           "projection (eq. 9.13) time is per launch over all elements"}
+    out["superconvergence"] = {
+        "hdg_projection_ms": float(np.median(tp[1:])),
+        "eps_u": float(np.sqrt(e_pu / ref_u)), "eps_uhat": float(np.sqrt(e_pf / ref_f)),
+        "e_u": float(np.sqrt(e_u / ref_u)), "e_uhat": float(np.sqrt(e_uhat / ref_f)),
+        "note": "eq. 10.1-10.2 ratios of the step's solution (trace solve to 1e-10); the HDG projection "
+                "(eq. 9.13) time is per launch over all elements"}
+    del q_vol, q_face, u_vol, u_face, Pq, Pu
 
     # end to end through the public API with host buffers (pinned) and copies in the region
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    pin = {k: torch.from_numpy(v).pin_memory() for k, v in W.host.items()}
     hq = torch.empty((nelt, 3, M.n), dtype=torch.float64).pin_memory()
     hu = torch.empty((nelt, M.n), dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * 8 for v in pin.values())
@@ -423,9 +559,8 @@ def run_gpu(args, rank, world, local_rank):
         a, b, cc, dd = ev(), ev(), ev(), ev()
         a.record(stream)
         for k_, v in pin.items():
-            dv[k_].copy_(v, non_blocking=True)
-        M.set_coefficients(dv["kappa"], dv["c"], dv["f"])
-        M.set_boundary_data(dv["uD"], dv["gN"])
+            W.dv[k_].copy_(v, non_blocking=True)
+        W.set_inputs()
         M.assemble_condense(asm_prec)
         b.record(stream)
         uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
@@ -437,87 +572,43 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms += a.elapsed_time(b) + cc.elapsed_time(dd)
-    e2e = {"value": world * nelt * args.steps / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "phases": "H2D of kappa,c,f,u_D,g_N + assemble_condense + recover + D2H of q,u "
-                     "(the trace solve runs between them and is excluded, as in value)"}
+    out["e2e"] = {"value": world * nelt * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                  "phases": "H2D of " + ",".join(W.host) + " + assemble_condense + recover + D2H of q,u "
+                            "(the trace solve runs between them and is excluded, as in value)"}
+    del pin, hq, hu
 
     # roofline of the dominant kernel of the metric (K1).  Its work is the FP64 flop count of
     # the algorithm.  The double-float K1 executes it on the FP32 pipe as compensated
     # multiply-adds (12 FP32 instructions each), so its peak is the FP32 pipe's rate / 12; the
     # FP64 K1 is held to the FP64 pipe.
-    k1_ms = float(np.mean(t_asm))
-    flops = flops_per_element_k1(prob.k) * nelt
-    achieved = flops / (k1_ms / 1e3) / 1e12
+    k1_ms = phases["assemble_condense"]
+    fpe = flops_per_element_k1(prob.k, W.conv)
+    achieved = fpe * nelt / (k1_ms / 1e3) / 1e12
     k1_src = "assemble_df.cu" if args.asm == "df32" else "assemble.cu"
     sha = _sha(*(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", f) for f in K1_SOURCES[k1_src]))
-    trec = K1_TRAFFIC.get(k1_src, {})
-    traffic = trec.get("bytes") if trec.get("sha256") == sha else None
+    trec = K1_TRAFFIC.get((W.name, k1_src), {})
+    bpe = trec.get("bytes_per_element") if trec.get("sha256") == sha else None
     df = args.asm == "df32"
     peak = DF_PEAK_TFLOPS if df else FP64_PEAK_TFLOPS
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": ("assemble_df_kernel<3> (K1, double-float on the FP32 pipe)" if df
-                           else "assemble_kernel<3,256> (K1, FP64)"),
-                "work": "FP64-equivalent flops of the structured elimination (sum-factorised masses)",
-                "flops_per_element": flops_per_element_k1(prob.k),
-                "algorithmic_bytes_per_launch": k1_bytes_per_element(prob.k) * nelt,
-                "peak_note": ("double-float on the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz / 12 FP32 "
-                              "instructions per compensated multiply-add x 2 flop (derived from unit counts and "
-                              "the maximum clock)" if df else
-                              "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts and the "
-                              f"maximum clock); measured FMA microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s"),
-                "frac_of_fp64_pipe": achieved / FP64_PEAK_TFLOPS}
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD['name']}: unit cube 16^3x6 Kuhn tets ({nelt} elements), k=3, "
-                               "variable kappa and c, Dirichlet x=0,1 + Neumann elsewhere",
-                   "nelt": nelt, "nfc": M.nfc, "trace_dofs": M.nfc * M.d2, "k": prob.k,
-                   "l2": "flushed before every step (256 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "solve_in_step": ("mixed FP32/FP64" if args.solve == "mixed" else "FP64")
-                   + " PCG to 1e-10 relative residual, "
-                   + ("two-level (block-Jacobi + P1 V-cycle) preconditioner" if args.coarse else
-                      "block-Jacobi preconditioner"),
-                   "coarse_levels": hierarchy[0] if args.coarse else None,
-                   "autotune": tuned},
-        "phases_ms": {"assemble_condense": float(np.mean(t_asm)), "trace_solve": float(np.mean(t_sol)),
-                      "recover": float(np.mean(t_rec)), "postprocess": float(np.mean(t_pp))},
-        "solve_time_to_1e-10": solve,
-        "superconvergence": diagnostics,
-        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
-        "wall_s_timed": wall,
-    }
+    out["roofline"] = {
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        "traffic": bpe * nelt if bpe else None,
+        "traffic_note": (f"ncu dram bytes per element x {nelt} elements ({trec.get('captured')})" if bpe else
+                         "no ncu capture of the current K1 sources"),
+        "kernel": (f"assemble_df_kernel<{prob.k}, .., CONV={str(W.conv).lower()}> (K1, double-float on the FP32 pipe)"
+                   if df else f"assemble_kernel<{prob.k}> (K1, FP64)"),
+        "work": "FP64-equivalent flops of the structured elimination (sum-factorised masses)",
+        "flops_per_element": fpe, "algorithmic_bytes_per_launch": k1_bytes_per_element(prob.k, W.conv) * nelt,
+        "peak_note": ("double-float on the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz / 12 FP32 instructions per "
+                      "compensated multiply-add x 2 flop (derived from unit counts and the maximum clock)" if df else
+                      "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts and the maximum clock); "
+                      f"measured FMA microbenchmark {FP64_MEASURED_TFLOPS} TFLOP/s"),
+        "frac_of_fp64_pipe": achieved / FP64_PEAK_TFLOPS,
+        "fp32_pipe_note": (f"the FP32 FMA pipe's own peak is {FP32_PEAK_TFLOPS:.1f} TFLOP/s derived "
+                           f"({FP32_MEASURED_TFLOPS} measured); ncu's FMA-pipe utilisation of this kernel is in "
+                           "profiles/")}
     return out
-
-
-def profile_k1(s_sub, launches=2, asm="df32", autotune=True):
-    """Small case for ncu captures of K1: the same problem on an s^3 x 6 mesh, autotuned as in
-    the bench (the tuned launch shape appears in the kernel's template arguments)."""
-    import torch
-
-    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, HDGMesh, build
-    from workloads import boundary_faces, get_problem, kuhn_cube
-
-    build()
-    prob = get_problem(WORKLOAD["name"]).at(s=s_sub)
-    c, e = kuhn_cube(prob.s)
-    d, n = boundary_faces(c, e, prob.classify)
-    M = HDGMesh(c, e, d, n, prob.k)
-    X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
-    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    M.set_coefficients(dv(prob.kappa(X, Y, Z)), dv(prob.c(X, Y, Z)), dv(prob.f(X, Y, Z)))
-    M.set_boundary_data(torch.zeros(M.nfc, M.nf, dtype=torch.float64, device="cuda"),
-                        torch.zeros(3, M.nfc, M.nf, dtype=torch.float64, device="cuda"))
-    prec = HDG_DF32 if asm == "df32" else HDG_FP64
-    M.assemble_condense(prec)
-    tuned = M.autotune() if autotune else None
-    for _ in range(launches):
-        M.assemble_condense(prec)
-    torch.cuda.synchronize()
-    print(json.dumps({"profile_k1": {"nelt": M.nelt, "launches": launches, "asm": asm, "autotune": tuned}}))
 
 
 def run_batch(args):
@@ -528,7 +619,7 @@ def run_batch(args):
     import torch
 
     from paper_1305_1489_gb300 import HDG_DF32, HDG_MIXED_FP32, HDGBatch, build
-    from workloads import boundary_faces, kuhn_cube
+    from workloads import boundary_faces, kuhn_cube, kuhn_p1_hierarchy
     from workloads.problems import batch_problems
 
     build()
@@ -556,7 +647,6 @@ def run_batch(args):
             uD[fs] = pr.uD(FX[fs], FY[fs], FZ[fs])
         M.set_coefficients(dev(kap), dev(cq), dev(fq))
         M.set_boundary_data(dev(uD))
-    from workloads import kuhn_p1_hierarchy
 
     def timed():
         relres, iters = B.run(precision=HDG_DF32, rtol=1e-10, maxit=40000)  # warm-up + graph build
@@ -575,7 +665,8 @@ def run_batch(args):
                 "ms_per_batch": ms, "elements_per_s": nelt / (ms / 1e3), "max_relres": float(relres.max())}
 
     tuned = B.autotune(HDG_DF32)
-    out = {"problems": len(probs), "elements": int(nelt), "graph_launches_per_batch": 1,
+    out = {"workload": "64 cube problems, s ~ U{8..24}, k ~ U{1..4}, kappa = 10^U(-1,1), c ~ U[0,5], seed 4",
+           "problems": len(probs), "elements": int(nelt), "graph_launches_per_batch": 1,
            "autotune": tuned, "block_jacobi": timed()}
     B.set_coarse_spaces([kuhn_p1_hierarchy(p.s, p.dirichlet_planes, max_coarsest=1, strict=False) for p in probs])
     out["two_level"] = timed()
@@ -588,16 +679,16 @@ def run_batch(args):
     return out
 
 
-def run_learned(args):
+def run_learned(args, train=None, evaluate=None, bj_eval=None, epochs=None):
     """The learned initial guess on the random-field workload: 32^3 x 6 Kuhn cube (196,608
     elements), k = 2, kappa = exp(g) with g a Gaussian random field (sigma 1, correlation
     length 0.2, 128 Fourier modes), c = f = 1, u = 0 on the whole boundary.  The network
     (g at the 3,375 interior nodes of the 16^3 grid -> tanh layer -> the coarse P1 field on that
     grid) is trained with the library's kernels on the coarse Galerkin projections of the
-    trace solutions of `learned_train` fields and evaluated on `learned_eval` held-out fields:
-    energy error of the initial guess, and PCG iterations and time to 1e-10 from the zero start
-    and from the learned guess (guess time included), for block-Jacobi and two-level PCG in
-    FP64 and mixed precision."""
+    trace solutions of `train` fields and evaluated on `evaluate` held-out fields: energy
+    error of the initial guess, and PCG iterations and time to 1e-10 from the zero start and
+    from the learned guess (guess time included), for block-Jacobi and two-level PCG in FP64
+    and mixed precision."""
     import torch
 
     from paper_1305_1489_gb300 import HDG_FP64, HDG_MIXED_FP32, HDGMesh, build
@@ -605,6 +696,10 @@ def run_learned(args):
     from workloads import boundary_faces, kuhn_coarse_interpolation, kuhn_cube, kuhn_grid_points, kuhn_p1_hierarchy
     from workloads.problems import cube32_k2_grf, grf_frequencies, grf_sample
 
+    train = args.learned_train if train is None else train
+    evaluate = args.learned_eval if evaluate is None else evaluate
+    bj_eval = args.learned_bj_eval if bj_eval is None else bj_eval
+    epochs = args.learned_epochs if epochs is None else epochs
     build()
     prob = cube32_k2_grf(0)
     c, e = kuhn_cube(prob.s)
@@ -621,11 +716,11 @@ def run_learned(args):
     sync = torch.cuda.synchronize
 
     t0 = time.perf_counter()
-    A, T, its = lg.generate([grf_sample(i) for i in range(args.learned_train)])
+    A, T, its = lg.generate([grf_sample(i) for i in range(train)])
     sync()
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = lg.fit(A, T, epochs=args.learned_epochs, batch=64, lr=1e-3)
+    hist = lg.fit(A, T, epochs=epochs, batch=64, lr=1e-3)
     sync()
     t_fit = time.perf_counter() - t0
     lg.fold_normalisation()
@@ -636,7 +731,7 @@ def run_learned(args):
 
     rows = []
     M.set_coarse_space(*hierarchy)
-    for j in range(args.learned_eval):
+    for j in range(evaluate):
         amps = grf_sample(100_000 + j)
         lg.set_field(amps)
         u, _, _ = M.solve_trace(1e-11, 20000)
@@ -646,7 +741,7 @@ def run_learned(args):
             err = u - x
             return float((err * M.apply(err)).sum()) / uHu
         row = {"energy_net": energy(lg.guess(amps)[0]), "energy_mean": energy(cs.guess(M, c_mean)[0])}
-        variants = [("two_level", True)] + ([("block_jacobi", False)] if j < args.learned_bj_eval else [])
+        variants = [("two_level", True)] + ([("block_jacobi", False)] if j < bj_eval else [])
         for pname, tl in variants:
             if not tl:
                 M.set_coarse_space(None, None, None)
@@ -671,9 +766,8 @@ def run_learned(args):
         vals = [r[key][idx] for r in rows if key in r]
         return float(np.median(vals)) if vals else None
     out = {"workload": "cube32_k2_grf: 32^3x6 Kuhn tets (196,608 elements), k=2, kappa=exp(GRF), c=f=1, u_D=0",
-           "train_fields": args.learned_train, "eval_fields": args.learned_eval,
-           "block_jacobi_eval_fields": min(args.learned_bj_eval, args.learned_eval),
-           "network": {"sizes": lg.sizes, "epochs": args.learned_epochs, "final_loss": hist[-1][1]},
+           "train_fields": train, "eval_fields": evaluate, "block_jacobi_eval_fields": min(bj_eval, evaluate),
+           "network": {"sizes": lg.sizes, "epochs": epochs, "final_loss": hist[-1][1]},
            "generate_s": t_gen, "train_s": t_fit, "coarse_solve_iterations_median": float(np.median(its)),
            "energy_error_median": {"zero_start": 1.0, "mean_field_guess": float(np.median([r["energy_mean"] for r in rows])),
                                    "learned_guess": float(np.median([r["energy_net"] for r in rows]))},
@@ -688,15 +782,108 @@ def run_learned(args):
     return out
 
 
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1305_1489_gb300 import build
+
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1305_1489_gb300", "libhdg.so")):
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    W = Workload(HEADLINE, dev, stream)
+    r = run_workload(W, args, stream, dev, world, full=True)
+    W.M.close()
+    del W
+    torch.cuda.empty_cache()
+    prec = "df32" if args.asm == "df32" else "f64"
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": prec,
+        "dtype_note": ("assembly and condensation in double-float (pairs of FP32 on the FP32 pipe, about 48-bit "
+                       "significand; C^K, C_f and the records match the FP64 oracle to 1e-11 relative); trace "
+                       "solve in FP32 inner BiCGStab iterations with FP64 residuals and refinement to 1e-10; "
+                       "recovery and postprocess in double-float" if prec == "df32" else "FP64 throughout"),
+        "data": "synthetic",
+        "config": {"workload": f"{HEADLINE}: unit cube 48^3x6 Kuhn tets ({r['nelt']} elements), interior vertices "
+                               "jittered +-0.2h (seed 0), k=2, beta=(y,-x,0.5z), kappa=1+0.5 sin(2 pi z), c=1, tau=2.5, "
+                               "Dirichlet on every face",
+                   "nelt": r["nelt"], "nfc": r["nfc"], "trace_dofs": r["trace_dofs"], "k": r["k"],
+                   "l2": "inputs (3.4 GB) larger than L2, and L2 flushed before every step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "solve_in_step": ("mixed FP32/FP64" if args.solve == "mixed" else "FP64")
+                   + " BiCGStab to 1e-10 relative residual, "
+                   + ("two-level (block-Jacobi + P1 V-cycle) preconditioner" if args.coarse else
+                      "block-Jacobi preconditioner"),
+                   "coarse_levels": r["coarse_levels"], "autotune": r["autotune"]},
+        "phases_ms": r["phases_ms"], "iterations_per_step": r["iterations_per_step"],
+        "solve_time_to_1e-10": r["solve_time_to_1e-10"], "superconvergence": r["superconvergence"],
+        "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "roofline": r["roofline"],
+        "solve_roofline": r["solve_roofline"], "wall_s_timed": r["wall_s_timed"],
+    }
+    if world == 1 and rank == 0 and args.extras:
+        extras = {}
+        W2 = Workload(EXTRA_RD, dev, stream)
+        r2 = run_workload(W2, args, stream, dev, 1, full=True)
+        extras[EXTRA_RD] = {
+            "workload": f"{EXTRA_RD}: unit cube 16^3x6 Kuhn tets ({r2['nelt']} elements), k=3, variable kappa and c, "
+                        "Dirichlet x=0,1 + Neumann elsewhere (reaction-diffusion, CG)",
+            **{k: r2[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step", "solve_time_to_1e-10",
+                                  "superconvergence", "e2e", "roofline", "solve_roofline", "gpu_launches")}}
+        W2.M.close()
+        del W2
+        torch.cuda.empty_cache()
+        try:
+            extras["batch_64"] = run_batch(args)
+        except Exception as exc:  # noqa: BLE001 -- an extra must not lose the headline line
+            extras["batch_64"] = {"error": repr(exc)}
+        torch.cuda.empty_cache()
+        try:
+            extras["cube32_k2_grf_learned"] = run_learned(args, train=args.extra_learned_train,
+                                                          evaluate=args.extra_learned_eval, bj_eval=1,
+                                                          epochs=args.learned_epochs)
+        except Exception as exc:  # noqa: BLE001
+            extras["cube32_k2_grf_learned"] = {"error": repr(exc)}
+        out["extras"] = extras
+    return out
+
+
+def profile_k1(name, s_sub, launches=2, asm="df32", autotune=True):
+    """Small case for ncu captures of K1: the workload's problem on an s^3 x 6 mesh, autotuned as
+    in the bench (the tuned launch shape appears in the kernel's template arguments)."""
+    import torch
+
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_FP64, build
+
+    build()
+    W = Workload(name, torch.device("cuda", 0), torch.cuda.current_stream(), s=s_sub)
+    M = W.M
+    prec = HDG_DF32 if asm == "df32" else HDG_FP64
+    M.assemble_condense(prec)
+    tuned = M.autotune() if autotune else None
+    for _ in range(launches):
+        M.assemble_condense(prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_k1": {"workload": name, "s": s_sub, "nelt": M.nelt, "launches": launches, "asm": asm,
+                                     "autotune": tuned}}))
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
-    base = oracle_baseline(sample_elems=args.ref_sample, steps=args.steps, warmup=min(args.warmup, 1))
+    base = oracle_baseline(HEADLINE, sample_elems=args.ref_sample, steps=args.steps, warmup=min(args.warmup, 1))
     return {
         "impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD['name']}: unit cube 16^3x6 Kuhn tets (24576 elements), k=3",
+        "config": {"workload": f"{HEADLINE}: unit cube 48^3x6 Kuhn tets (663552 elements), jittered, k=2, convection",
                    "impl": "FP64 CPU oracle (numpy), host cores"},
         "cpu_baseline": base,
         "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -709,30 +896,49 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-sample", type=int, default=12288, help="oracle elements per step")
+    ap.add_argument("--ref-sample", type=int, default=8192, help="oracle elements per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only-steps", action="store_true", help="timed steps only (profiling)")
+    ap.add_argument("--only-steps", action="store_true", help="timed steps only, no comparisons or extras (profiling)")
+    ap.add_argument("--workload", default=HEADLINE, help="workload of --only-steps")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the reaction-diffusion, batch and random-field extras")
     ap.add_argument("--asm", default="df32", choices=["df32", "fp64"],
                     help="assembly arithmetic: double-float on the FP32 pipe or native FP64")
     ap.add_argument("--inner-rtol", type=float, default=1e-6, help="FP32 inner solve tolerance")
     ap.add_argument("--solve", default="mixed", choices=["mixed", "fp64"], help="trace solve precision in the step")
+    ap.add_argument("--solve-reps", type=int, default=2, help="repetitions of each time-to-1e-10 solve")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default persistent grid of the solve kernels")
     ap.add_argument("--no-coarse", dest="coarse", action="store_false",
                     help="block-Jacobi only (no two-level preconditioner) in the step")
-    ap.add_argument("--batch", action="store_true", help="also time the 64-problem mixed-degree batch")
     ap.add_argument("--batch-only", action="store_true", help="time only the batch and exit")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
+    ap.add_argument("--profile-workload", default=HEADLINE)
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned guess and exit")
     ap.add_argument("--learned-train", type=int, default=2000)
     ap.add_argument("--learned-eval", type=int, default=200)
     ap.add_argument("--learned-bj-eval", type=int, default=20, help="held-out fields also timed with block-Jacobi")
     ap.add_argument("--learned-epochs", type=int, default=60)
+    ap.add_argument("--extra-learned-train", type=int, default=200, help="training fields of the learned extra")
+    ap.add_argument("--extra-learned-eval", type=int, default=8, help="held-out fields of the learned extra")
     args = ap.parse_args()
     if args.profile_k1:
-        profile_k1(args.profile_k1, asm=args.asm)
+        profile_k1(args.profile_workload, args.profile_k1, asm=args.asm)
+        return
+    if args.only_steps:
+        import torch
+
+        from paper_1305_1489_gb300 import build
+        build()
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(device=dev)
+        torch.cuda.set_stream(stream)
+        W = Workload(args.workload, dev, stream)
+        r = run_workload(W, args, stream, dev, 1, full=False)
+        print(json.dumps({"only_steps": {k: r[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step",
+                                                            "gpu_launches", "solve_roofline", "autotune")}}))
         return
     if args.batch_only:
         print(json.dumps({"batch": run_batch(args)}))
@@ -755,10 +961,8 @@ def main():
         dist.init_process_group("nccl")
     out = run_gpu(args, rank, world, local_rank)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and not args.only_steps:
-            out["cpu_baseline"] = oracle_baseline(sample_elems=args.ref_sample, steps=1, warmup=1)
-        if args.batch and world == 1:
-            out["batch"] = run_batch(args)
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_baseline(HEADLINE, sample_elems=args.ref_sample, steps=1, warmup=1)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
