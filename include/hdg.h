@@ -335,6 +335,23 @@ int hdg_face_projection(hdg_mesh* mesh, const double* vals, double* Pu);
 int hdg_volume_norm2(hdg_mesh* mesh, int degree, const double* coef, const double* vals, double* out);
 int hdg_face_norm2(hdg_mesh* mesh, const double* coef, const double* vals, double* out);
 
+/* ------------------------------------------------------------------ dense contraction on tensor cores
+ * The volume masses of eq. 3.55 as one dense contraction for all elements,
+ *   out[e][p] = sum_q |K_e| omega_q g[e][q] P_i(p_hat_q) P_j(p_hat_q),  p = (i <= j) in the
+ *   row-major order of the upper triangle (n(n+1)/2 pairs),
+ * i.e. the GEMM [nelt x nq] . [nq x n(n+1)/2].  A measurement of that contraction on its own,
+ * not a step of the solver: hdg_assemble_condense forms the masses by sum factorisation and
+ * keeps FP64-level accuracy, which BF16 operands cannot.
+ *   mode 0: 5th-generation tensor cores (tcgen05.mma, BF16 operands, FP32 accumulation);
+ *   mode 1: CUDA cores, FP32 arithmetic on the same BF16-rounded operands (the reference of
+ *           mode 0: the two differ only by the order of the FP32 additions);
+ *   mode 2: CUDA cores, FP32 operands and arithmetic.
+ *   g: device f64 [nelt][nq] (the coefficient at the volume nodes, e.g. 1/kappa);
+ *   out: device f32 [nelt][n(n+1)/2].
+ * Synchronises the mesh's stream in mode 0 and returns HDG_ERR_CUDA if a tensor-core wait ran
+ * out (bounded waits; the kernel frees its tensor memory in that case).  k >= 1.          */
+int hdg_mass_contraction(hdg_mesh* mesh, const double* g, int mode, float* out);
+
 /* ------------------------------------------------------------------ batched problems
  * Many independent problems of mixed degree solved together.  Problems of equal degree are
  * merged into one disjoint-union mesh (a "group"), so each phase is one launch per group, and

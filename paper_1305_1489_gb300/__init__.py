@@ -363,6 +363,16 @@ class HDGMesh:
         v = None if vals is None else _dev_f64(vals, (self.nfc, self.nf), "vals")
         return hdg_face_norm2(self._h, c, v)
 
+    def mass_contraction(self, g, mode=0):
+        """hdg_mass_contraction: sum_q |K| omega_q g P_i P_j for the n(n+1)/2 pairs (i <= j),
+        [nelt, n(n+1)/2] FP32; mode 0 tensor cores (BF16 operands), 1 CUDA cores on the same
+        BF16 operands, 2 CUDA cores in FP32."""
+        import torch
+        g = _dev_f64(g, (self.nelt, self.nq), "g")
+        out = torch.empty((self.nelt, self.n * (self.n + 1) // 2), dtype=torch.float32, device=g.device)
+        _lib.check(_lib.load().hdg_mass_contraction(self._h, g.data_ptr(), int(mode), out.data_ptr()))
+        return out
+
     @property
     def launches(self):
         return hdg_launch_count(self._h)

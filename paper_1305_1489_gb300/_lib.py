@@ -74,6 +74,7 @@ _SIGS = {
     "hdg_face_projection": [P, P, P],
     "hdg_volume_norm2": [P, C.c_int, P, P, P],
     "hdg_face_norm2": [P, P, P, P],
+    "hdg_mass_contraction": [P, P, C.c_int, P],
     "hdg_last_error": [C.c_char_p, C.c_size_t],
     "hdg_launch_count": [P],
     "hdg_host_table": [C.c_int, C.c_char_p, P, I64, C.POINTER(I64)],

@@ -225,32 +225,36 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     s_nn[(tid - 25) / 4][(tid - 25) % 4] = df_from_double(x[0] * y[0] + x[1] * y[1] + x[2] * y[2]);
   }
 
-  for (int q = tid; q < nq; q += NT) {
-    const double kap = A.kappa[Ke * nq + q], cc = A.c[Ke * nq + q], ff = A.f[Ke * nq + q];
-    if (!(kap > 0.0) || !(cc >= 0.0) || !isfinite(kap) || !isfinite(cc) || !isfinite(ff)) s_coef = 1;
-    const double vw = s_vol * A.w[q];
-    kw[q] = df_from_double(vw / kap);
-    cw[q] = df_from_double(vw * cc);
-    fw[q] = df_from_double(vw * ff);
-    if constexpr (CONV) {
+  // coefficients weighted by |K| omega_q; with convection also the volume weights bw and the
+  // face weights bn, each task on its own thread.  The reciprocal of kappa is a double-float
+  // Newton step on the FP32 pipe (no FP64 division).
+  constexpr int NTASK = CONV ? 2 * nq + 4 * nf : nq;
+  for (int t = tid; t < NTASK; t += NT) {
+    if (t < nq) {
+      const int q = t;
+      const double kap = A.kappa[Ke * nq + q], cc = A.c[Ke * nq + q], ff = A.f[Ke * nq + q];
+      if (!(kap > 0.0) || !(cc >= 0.0) || !isfinite(kap) || !isfinite(cc) || !isfinite(ff)) s_coef = 1;
+      const df vw = df_from_double(s_vol * A.w[q]);
+      kw[q] = df_mul(vw, df_recip(kap > 0.0 ? df_from_double(kap) : df_make(1.f, 0.f)));
+      cw[q] = df_mul(vw, df_from_double(cc));
+      fw[q] = df_mul(vw, df_from_double(ff));
+    } else if (t < 2 * nq) {
       // bw_#(q) = -(omega_q / 6) sum_* a_{*#} beta_*(p_q)  (B_c = sum_q sum_# bw P_qj dhat_# P_qi)
+      const int q = t - nq;
       const double b0 = A.beta_q[(0 * A.nelt + Ke) * nq + q], b1 = A.beta_q[(1 * A.nelt + Ke) * nq + q],
                    b2 = A.beta_q[(2 * A.nelt + Ke) * nq + q];
       const double sc = -A.w[q] / 6.0;
 #pragma unroll
       for (int h = 0; h < 3; ++h)
         bw[h * nq + q] = df_from_double(sc * (s_geo[h] * b0 + s_geo[3 + h] * b1 + s_geo[6 + h] * b2));
-    }
-  }
-  if constexpr (CONV) {
-    // varpi_r beta(x_{r,l}^K) . n_l at the element's face nodes
-    for (int t = tid; t < 4 * nf; t += NT) {
-      const int fl = t / nf, r = t - fl * nf;
+    } else {
+      // varpi_r beta(x_{r,l}^K) . n_l at the element's face nodes
+      const int u = t - 2 * nq, fl = u / nf, r = u - fl * nf;
       const double* nl = s_geo + 9 + 3 * fl;
       double acc = 0.0;
 #pragma unroll
-      for (int st = 0; st < 3; ++st) acc = fma(A.beta_f[((int64_t)st * A.nelt + Ke) * 4 * nf + t], nl[st], acc);
-      bn[t] = df_from_double(A.wf[r] * acc);
+      for (int st = 0; st < 3; ++st) acc = fma(A.beta_f[((int64_t)st * A.nelt + Ke) * 4 * nf + u], nl[st], acc);
+      bn[u] = df_from_double(A.wf[r] * acc);
     }
   }
   __syncthreads();
@@ -321,20 +325,8 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
     const df v1 = dacc_result(s1), v2 = dacc_result(s2);
     Ms[i * n + j] = v1;
     Ms[j * n + i] = v1;
-    if constexpr (CONV) {
-      // B_c[i][j] = sum_q P_qj Gq[q][i],  B_c[j][i] = sum_q P_qi Gq[q][j]
-      dacc bij = dacc_from(v2), bji = dacc_from(v2);
-#pragma unroll 4
-      for (int q = 0; q < nq; ++q) {
-        dacc_mac(bij, ldg_df(A.P + q * n + j), Gq[q * n + i]);
-        dacc_mac(bji, ldg_df(A.P + q * n + i), Gq[q * n + j]);
-      }
-      Ss[i * n + j] = dacc_result(bij);
-      Ss[j * n + i] = dacc_result(bji);
-    } else {
-      Ss[i * n + j] = v2;
-      Ss[j * n + i] = v2;
-    }
+    Ss[i * n + j] = v2;
+    Ss[j * n + i] = v2;
     if (wf) Gt[j * (m + 1) + m] = j < A.nu ? dacc_result(s3) : df_make(0.f, 0.f);  // pair (0, j)
   }
   // C_*^T from C_hat and the cofactors, V = E^T (both where T1 was)
@@ -348,29 +340,57 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   for (int t = tid; t < n * m; t += NT) {
     const int l = t / m, r = t - l * m, fl = r / d2, a = r - fl * d2;
     V[t] = ldg_df(A.E + ((fl * 6 + s_perm[fl]) * d2 + a) * n + l);
-    if constexpr (CONV) {
-      // alphaDP^T[l][r] = sum_r' varpi (beta.n) D^mu_{r'a} P^l_{r'l}
-      const df* Dm = A.Dmu + s_perm[fl] * nf * d2;
-      const df* Pl = A.Pl + fl * nf * n;
-      dacc acc = dacc_zero();
-      for (int rr = 0; rr < nf; ++rr) dacc_mac(acc, df_mul(bn[fl * nf + rr], ldg_df(Dm + rr * d2 + a)), ldg_df(Pl + rr * n + l));
-      Hr[t] = dacc_result(acc);
-    }
-  }
-  if constexpr (CONV) {  // alphaDD[l][a][b] = sum_r' varpi (beta.n) D^mu_{r'a} D^mu_{r'b}
-    for (int t = tid; t < 4 * d2 * d2; t += NT) {
-      const int fl = t / (d2 * d2), ab = t - fl * d2 * d2, a = ab / d2, b = ab - a * d2;
-      const df* Dm = A.Dmu + s_perm[fl] * nf * d2;
-      dacc acc = dacc_zero();
-      for (int rr = 0; rr < nf; ++rr) dacc_mac(acc, df_mul(bn[fl * nf + rr], ldg_df(Dm + rr * d2 + a)), ldg_df(Dm + rr * d2 + b));
-      aDD[t] = dacc_result(acc);
-    }
   }
   __syncthreads();
 
-  {  // every thread of the block factors M (nothing else can proceed meanwhile)
+  if constexpr (!CONV) {  // every thread of the block factors M (nothing else can proceed meanwhile)
     const bool ok = group_cholesky_df<n, NT>(Ms, invdM, A.pairs_n, tid);
     if (!ok && tid == 0) s_bad = 1;
+  } else if (warp == 0) {  // convection: warp 0 factors M while the other warps form the
+    const bool ok = group_cholesky_df<n, 32>(Ms, invdM, A.pairs_n, lane);  // convection blocks
+    if (!ok && lane == 0) s_bad = 1;
+  } else {
+    // B_c[i][j] = sum_q P_qj Gq[q][i] and B_c[j][i] = sum_q P_qi Gq[q][j], into S_u
+    for (int t = tid - 32; t < NP; t += NT - 32) {
+      const int i = A.pairs_n[2 * t], j = A.pairs_n[2 * t + 1];
+      dacc bij = dacc_from(Ss[i * n + j]), bji = dacc_from(Ss[j * n + i]);
+#pragma unroll 4
+      for (int q = 0; q < nq; ++q) {
+        dacc_mac(bij, ldg_df(A.P + q * n + j), Gq[q * n + i]);
+        dacc_mac(bji, ldg_df(A.P + q * n + i), Gq[q * n + j]);
+      }
+      Ss[i * n + j] = dacc_result(bij);
+      if (i != j) Ss[j * n + i] = dacc_result(bji);
+    }
+    // bD[l][r'][a] = varpi (beta.n) D^mu_{r'a} into Gq's space (Gq is read by B_c above, so
+    // the workers meet at a barrier first), then alphaDP^T[l][r] = sum_r' bD P^l_{r'l} and
+    // alphaDD[l][a][b] = sum_r' bD[l][r'][a] D^mu_{r'b}
+    sync_workers<NT>();
+    df* bD = Gq;
+    static_assert(4 * nf * d2 <= nq * n, "bD must fit in the space of Gq");
+    for (int t = tid - 32; t < 4 * nf * d2; t += NT - 32) {
+      const int fl = t / (nf * d2), ra = t - fl * nf * d2, rr = ra / d2, a = ra - rr * d2;
+      bD[t] = df_mul(bn[fl * nf + rr], ldg_df(A.Dmu + (s_perm[fl] * nf + rr) * d2 + a));
+    }
+    sync_workers<NT>();
+    for (int t = tid - 32; t < n * m; t += NT - 32) {
+      const int l = t / m, r = t - l * m, fl = r / d2, a = r - fl * d2;
+      const df* Pl = A.Pl + fl * nf * n;
+      const df* bd = bD + fl * nf * d2;
+      dacc acc = dacc_zero();
+#pragma unroll 4
+      for (int rr = 0; rr < nf; ++rr) dacc_mac(acc, bd[rr * d2 + a], ldg_df(Pl + rr * n + l));
+      Hr[t] = dacc_result(acc);
+    }
+    for (int t = tid - 32; t < 4 * d2 * d2; t += NT - 32) {
+      const int fl = t / (d2 * d2), ab = t - fl * d2 * d2, a = ab / d2, b = ab - a * d2;
+      const df* Dm = A.Dmu + s_perm[fl] * nf * d2;
+      const df* bd = bD + fl * nf * d2;
+      dacc acc = dacc_zero();
+#pragma unroll 4
+      for (int rr = 0; rr < nf; ++rr) dacc_mac(acc, bd[rr * d2 + a], ldg_df(Dm + rr * d2 + b));
+      aDD[t] = dacc_result(acc);
+    }
   }
   __syncthreads();
 
@@ -516,20 +536,28 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
 
   // C = (n_l . n_l') o V^T V + tauDD - H^T H  (V = L^-1 E^T; H = rows of G^T);
   // convection: C = (n_l . n_l') o V^T V + tauDD - alphaDD - H_row^T H_col, C_f = H_row^T h
-  if constexpr (CONV) {
-    for (int t = tid; t < m * m; t += NT) {
-      const int r = t / m, s = t - r * m;
+  if constexpr (CONV) {  // the symmetric V^T V part once per pair (r <= s), both entries after
+    for (int t = tid; t < MP; t += NT) {
+      const int r = A.pairs_m[2 * t], s = A.pairs_m[2 * t + 1];
       const int fr = r / d2, fs = s / d2;
       dacc b = dacc_zero();
 #pragma unroll 4
       for (int l = 0; l < n; ++l) dacc_mac(b, V[l * m + r], V[l * m + s]);
       df cv = df_mul(s_nn[fr][fs], dacc_result(b));
       if (r == s) cv = df_add(cv, s_T[fr]);
-      if (fr == fs) cv = df_sub(cv, aDD[fr * d2 * d2 + (r - fr * d2) * d2 + (s - fs * d2)]);
-      dacc hh = dacc_from(cv);
+      df crs = cv, csr = cv;
+      if (fr == fs) {
+        crs = df_sub(cv, aDD[fr * d2 * d2 + (r - fr * d2) * d2 + (s - fs * d2)]);
+        csr = df_sub(cv, aDD[fr * d2 * d2 + (s - fs * d2) * d2 + (r - fr * d2)]);
+      }
+      dacc h1 = dacc_from(crs), h2 = dacc_from(csr);
 #pragma unroll 4
-      for (int j = 0; j < n; ++j) dacc_msub(hh, Hr[j * m + r], Gt[j * (m + 1) + s]);
-      Cs[t] = dacc_result(hh);
+      for (int j = 0; j < n; ++j) {
+        dacc_msub(h1, Hr[j * m + r], Gt[j * (m + 1) + s]);
+        dacc_msub(h2, Hr[j * m + s], Gt[j * (m + 1) + r]);
+      }
+      Cs[r * m + s] = dacc_result(h1);
+      if (r != s) Cs[s * m + r] = dacc_result(h2);
     }
   }
   for (int t = tid; t < (CONV ? 0 : MP); t += NT) {

@@ -202,8 +202,15 @@ __device__ __forceinline__ bool group_cholesky_df(df* A, df* invd, const int16_t
   return ok;
 }
 
-// 1/x and sqrt(x) through FP64 (few per element)
-__device__ __forceinline__ df df_recip(df x) { return df_from_double(1.0 / df_to_double(x)); }
-__device__ __forceinline__ df df_sqrt(df x) { return df_from_double(sqrt(df_to_double(x))); }
+// 1/a for a non-zero a in the normal float range, on the FP32 pipe: the correctly rounded
+// float reciprocal of a.hi as the seed y0, refined by one Newton-Raphson step
+// y = y0 + y0 (1 - a y0), which squares its relative error (2^-24 -> the ~2^-45 floor of the
+// double-float product).  1 - a y0 is tiny, so its leading subtraction is exact (Sterbenz).
+__device__ __forceinline__ df df_recip(df a) {
+  const float y0 = __frcp_rn(a.hi);
+  const df t = df_mul(a, df_make(y0, 0.f));
+  const float r = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+  return fast_two_sum(y0, __fmul_rn(y0, r));
+}
 
 }  // namespace hdg

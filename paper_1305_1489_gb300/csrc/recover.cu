@@ -361,14 +361,134 @@ __global__ void __launch_bounds__(32) recover_df_kernel(const double* __restrict
   }
 }
 
+// The same recovery for small elements (k <= 2, n <= 10): E = 32 / n elements per warp, lane
+// group g (lanes g n .. g n + n - 1) working on element g exactly as one warp does above (row l
+// of its element on lane g n + l, shuffles within the group), so that the lanes are not left
+// idle by the short columns.  The E records arrive by E bulk copies on one mbarrier.
+template <int K>
+__global__ void __launch_bounds__(32) recover_df_multi_kernel(const double* __restrict__ rec,
+                                                             const int32_t* __restrict__ fbe,
+                                                             const double* __restrict__ uhat, int64_t nelt,
+                                                             double* __restrict__ q, double* __restrict__ u,
+                                                             int32_t* status) {
+  using D = Dims<K>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, E = 32 / n;
+  static_assert(n <= 16, "one lane group of n lanes per element");
+  constexpr uint32_t kBytes = sizeof(df) * D::rec;
+  static_assert(kBytes % 16 == 0, "the record must be a whole number of 16-byte units");
+  extern __shared__ __align__(128) unsigned char rec_smem[];
+  __shared__ df suh[E][m], su[E][n];
+  __shared__ __align__(8) uint64_t bar;
+  const int lane = threadIdx.x;
+  const int g = lane / n < E ? lane / n : E - 1;  // the lanes past E n shadow the last group
+  const int l = lane - (lane / n) * n;
+  const int64_t K0 = (int64_t)blockIdx.x * E;
+  const int ne = (int)((nelt - K0) < E ? (nelt - K0) : E);  // elements of this block
+  const bool act = lane / n < ne;
+  const int64_t Ke = K0 + g;
+  const int base = g * n;  // first lane of the group
+  if (lane == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, kBytes * (uint32_t)ne);
+    for (int e = 0; e < ne; ++e)
+      bulk_g2s(rec_smem + e * kBytes, reinterpret_cast<const df*>(rec) + (K0 + e) * (int64_t)D::rec, kBytes, &bar);
+  }
+  for (int t = lane; t < ne * m; t += 32) {
+    const int e = t / m, r = t - e * m;
+    suh[e][r] = df_from_double(__ldg(uhat + (int64_t)__ldg(fbe + (K0 + e) * 4 + r / d2) * d2 + (r % d2)));
+  }
+  __syncwarp();
+  if (!mbar_wait(&bar, 0, kRecWaitPolls)) {
+    mbar_wait(&bar, 0, kRecWaitPolls);  // give the copies in flight a second chance to land
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (act) {
+      u[Ke * n + l] = nan;
+      for (int st = 0; st < 3; ++st) q[(Ke * 3 + st) * n + l] = nan;
+    }
+    if (lane == 0) atomicAdd(status + 4, 1);
+    return;
+  }
+  const df* HT = reinterpret_cast<const df*>(rec_smem + g * kBytes);
+  const df* VT = HT + n * (m + 1);
+  const df* WT = VT + n * m;
+  const df* Us = WT + 3 * n * n;
+  const df* UM = Us + D::tri;
+  const df* nrm = UM + D::tri;
+  // u = U_s^-1 (H u_dK + h)
+  dacc x = dacc_from(HT[m * n + l]);
+#pragma unroll 8
+  for (int r = 0; r < m; ++r) dacc_mac(x, HT[r * n + l], suh[g][r]);
+#pragma unroll
+  for (int i = n - 1; i >= 0; --i) {
+    const df* col = Us + i * (i + 1) / 2;
+    const df xi = df_mul(shfl_df(dacc_result(x), base + i), col[i]);
+    if (l < i) dacc_msub(x, col[l], xi);
+    else if (l == i) x = dacc_from(xi);
+  }
+  const df ui = dacc_result(x);
+  su[g][l] = ui;
+  if (act) u[Ke * n + l] = df_to_double(ui);
+  __syncwarp();
+  // q_* = U_M^-1 (W_* u - V (n_* o u_dK))
+  dacc z[3] = {dacc_zero(), dacc_zero(), dacc_zero()};
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    const df uc = su[g][c];
+    dacc_mac(z[0], WT[(0 * n + c) * n + l], uc);
+    dacc_mac(z[1], WT[(1 * n + c) * n + l], uc);
+    dacc_mac(z[2], WT[(2 * n + c) * n + l], uc);
+  }
+#pragma unroll
+  for (int fl = 0; fl < 4; ++fl) {
+    dacc w = dacc_zero();
+#pragma unroll
+    for (int a2 = 0; a2 < d2; ++a2) dacc_mac(w, VT[(fl * d2 + a2) * n + l], suh[g][fl * d2 + a2]);
+    const df wv = dacc_result(w);
+    dacc_msub(z[0], nrm[3 * fl + 0], wv);
+    dacc_msub(z[1], nrm[3 * fl + 1], wv);
+    dacc_msub(z[2], nrm[3 * fl + 2], wv);
+  }
+#pragma unroll
+  for (int i = n - 1; i >= 0; --i) {
+    const df* col = UM + i * (i + 1) / 2;
+    const df inv = col[i];
+    df xi[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) xi[v] = df_mul(shfl_df(dacc_result(z[v]), base + i), inv);
+    if (l < i) {
+      const df uli = col[l];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) dacc_msub(z[v], uli, xi[v]);
+    } else if (l == i) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) z[v] = dacc_from(xi[v]);
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) q[(Ke * 3 + v) * n + l] = df_to_double(dacc_result(z[v]));
+  }
+}
+
 template <int K>
 static cudaError_t launch_recover_df(hdg_mesh* M, const double* uhat, double* q, double* u) {
-  const int smem = (int)(sizeof(df) * Dims<K>::rec);
-  cudaError_t e = cudaFuncSetAttribute(recover_df_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  recover_df_kernel<K><<<(unsigned)M->nelt, 32, smem, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u,
-                                                                     M->d_status);
-  return cudaSuccess;
+  if constexpr (Dims<K>::n <= 10) {
+    constexpr int E = 32 / Dims<K>::n;
+    const int smem = (int)(sizeof(df) * Dims<K>::rec * E);
+    cudaError_t e =
+        cudaFuncSetAttribute(recover_df_multi_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    recover_df_multi_kernel<K><<<(unsigned)((M->nelt + E - 1) / E), 32, smem, M->stream>>>(
+        M->d_rec, M->d_facebyele, uhat, M->nelt, q, u, M->d_status);
+    return cudaSuccess;
+  } else {
+    const int smem = (int)(sizeof(df) * Dims<K>::rec);
+    cudaError_t e = cudaFuncSetAttribute(recover_df_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    recover_df_kernel<K><<<(unsigned)M->nelt, 32, smem, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u,
+                                                                       M->d_status);
+    return cudaSuccess;
+  }
 }
 
 cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {

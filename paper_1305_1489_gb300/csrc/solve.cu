@@ -715,6 +715,132 @@ __global__ void bicg_x_kernel(FaceArgs F, BicgVecs<T> V, double* red, unsigned i
   }
 }
 
+// Flat vector forms of the elementwise BiCGStab steps: the vectors as plain arrays of nv
+// entries, W = 16 / sizeof(T) entries per 16-byte load (the extra vectors are laid out with a
+// stride rounded up to W, so every vector starts 16-byte aligned), the remainder entries one
+// by one.  Dirichlet entries need no mask: r, v, t, ph, sh all vanish there.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int W = 2;
+};
+
+template <typename T, typename F>
+__device__ __forceinline__ void flat_loop(int64_t nv, F&& f) {
+  constexpr int W = Vec16<T>::W;
+  const int64_t nvec = nv / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += stride) f(i, true);
+  for (int64_t i = nvec * W + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) f(i, false);
+}
+
+#define HDG_LD(ptr) (reinterpret_cast<const VT*>(ptr)[i])
+#define HDG_ST(ptr, val) (reinterpret_cast<VT*>(ptr)[i] = (val))
+
+// p = r + beta (p - omega v)  (two-level path: ph follows the coarse cycle of p)
+template <typename T>
+__global__ void bicg_p_flat_kernel(int64_t nv, BicgVecs<T> V, const double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  using VT = typename Vec16<T>::V;
+  const T beta = (T)scal[B_BETA], omega = (T)scal[B_OMEGA];
+  flat_loop<T>(nv, [&](int64_t i, bool vec) {
+    if (vec) {
+      const VT rr = HDG_LD(V.r), pp = HDG_LD(V.p), vq = HDG_LD(V.v);
+      const T* r = reinterpret_cast<const T*>(&rr);
+      const T* pv = reinterpret_cast<const T*>(&pp);
+      const T* vv = reinterpret_cast<const T*>(&vq);
+      VT o;
+      T* ov = reinterpret_cast<T*>(&o);
+#pragma unroll
+      for (int w = 0; w < Vec16<T>::W; ++w) ov[w] = fma(beta, fma(-omega, vv[w], pv[w]), r[w]);
+      HDG_ST(V.p, o);
+    } else {
+      V.p[i] = fma(beta, fma(-omega, V.v[i], V.p[i]), V.r[i]);
+    }
+  });
+}
+
+// s = r - alpha v  (two-level path)
+template <typename T>
+__global__ void bicg_s_flat_kernel(int64_t nv, BicgVecs<T> V, const double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  using VT = typename Vec16<T>::V;
+  const T alpha = (T)scal[B_ALPHA];
+  flat_loop<T>(nv, [&](int64_t i, bool vec) {
+    if (vec) {
+      const VT rv = HDG_LD(V.r), vv = HDG_LD(V.v);
+      const T* r = reinterpret_cast<const T*>(&rv);
+      const T* v = reinterpret_cast<const T*>(&vv);
+      VT o;
+      T* ov = reinterpret_cast<T*>(&o);
+#pragma unroll
+      for (int w = 0; w < Vec16<T>::W; ++w) ov[w] = fma(-alpha, v[w], r[w]);
+      HDG_ST(V.s, o);
+    } else {
+      V.s[i] = fma(-alpha, V.v[i], V.r[i]);
+    }
+  });
+}
+
+// x += alpha ph + omega sh;  r = s - omega t;  rho' = rhat.r;  beta = (rho'/rho)(alpha/omega)
+template <typename T>
+__global__ void bicg_x_flat_kernel(int64_t nv, BicgVecs<T> V, double* red, unsigned int* counter, double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  using VT = typename Vec16<T>::V;
+  const double alpha = scal[B_ALPHA], omega = scal[B_OMEGA];
+  const T a = (T)alpha, o = (T)omega;
+  double v[2] = {0.0, 0.0};
+  flat_loop<T>(nv, [&](int64_t i, bool vec) {
+    if (vec) {
+      const VT xv = HDG_LD(V.x), phv = HDG_LD(V.ph), shv = HDG_LD(V.sh), sv = HDG_LD(V.s), tv = HDG_LD(V.t),
+               rhv = HDG_LD(V.rh);
+      const T *x = reinterpret_cast<const T*>(&xv), *ph = reinterpret_cast<const T*>(&phv),
+              *sh = reinterpret_cast<const T*>(&shv), *sp = reinterpret_cast<const T*>(&sv),
+              *tp = reinterpret_cast<const T*>(&tv), *rh = reinterpret_cast<const T*>(&rhv);
+      VT xo, ro;
+      T* xw = reinterpret_cast<T*>(&xo);
+      T* rw = reinterpret_cast<T*>(&ro);
+#pragma unroll
+      for (int w = 0; w < Vec16<T>::W; ++w) {
+        xw[w] = fma(a, ph[w], fma(o, sh[w], x[w]));
+        rw[w] = fma(-o, tp[w], sp[w]);
+        v[0] = fma((double)rh[w], (double)rw[w], v[0]);
+        v[1] = fma((double)rw[w], (double)rw[w], v[1]);
+      }
+      HDG_ST(V.x, xo);
+      HDG_ST(V.r, ro);
+    } else {
+      V.x[i] = fma(a, V.ph[i], fma(o, V.sh[i], V.x[i]));
+      const T rv = fma(-o, V.t[i], V.s[i]);
+      V.r[i] = rv;
+      v[0] = fma((double)V.rh[i], (double)rv, v[0]);
+      v[1] = fma((double)rv, (double)rv, v[1]);
+    }
+  });
+  double out[2];
+  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) {
+    const double rho_old = scal[B_RHO];
+    scal[B_BETA] = (out[0] / rho_old) * (alpha / omega);
+    scal[B_RHO] = out[0];
+    scal[B_RR] = out[1];
+    scal[B_ITERS] += 1.0;
+    if (omega == 0.0 || out[0] == 0.0 || !isfinite(out[1])) {
+      scal[B_BAD] = (out[1] <= scal[B_TOL2]) ? 0.0 : 1.0;
+      scal[B_DONE] = 1.0;
+    }
+    if (out[1] <= scal[B_TOL2] || scal[B_ITERS] >= scal[B_MAXIT]) scal[B_DONE] = 1.0;
+  }
+}
+#undef HDG_LD
+#undef HDG_ST
+
 // y = H x on the free faces, 0 on Dirichlet faces
 template <int D2>
 __global__ void apply_kernel(FaceArgs F, const double* __restrict__ C, const double* __restrict__ x, double* __restrict__ y) {
@@ -853,6 +979,8 @@ static void match_graphs(hdg_mesh* M, bool tl) {
   M->graphs_tl = tl;
 }
 
+static int64_t bicg_stride(int64_t nv, int w) { return (nv + w - 1) / w * w; }
+
 static int ensure_workspace(hdg_mesh* M, bool mixed) {
   const int64_t nv = M->nfc * M->tab.d2;
   if (!M->d_b) {
@@ -870,8 +998,9 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
     HDG_CUDA_TRY(cudaMemsetAsync(M->d_counter, 0, sizeof(unsigned int) * 4, M->stream));
     M->red_blocks = kMaxBlocks;
   }
-  if (M->beta_q && !M->d_bicg) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * nv));
-  if (M->beta_q && mixed && !M->d_bicg32) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg32, sizeof(float) * 4 * nv));
+  if (M->beta_q && !M->d_bicg) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * bicg_stride(nv, 2)));
+  if (M->beta_q && mixed && !M->d_bicg32)
+    HDG_CUDA_TRY(cudaMalloc(&M->d_bicg32, sizeof(float) * 4 * bicg_stride(nv, 4)));
   if (mixed && !M->d_C32) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_C32, sizeof(float) * M->nelt * M->tab.m * M->tab.m));
     HDG_CUDA_TRY(cudaMalloc(&M->d_BJ32, sizeof(float) * M->nfc * M->tab.d2 * M->tab.d2));
@@ -1062,9 +1191,10 @@ struct Solver {
     HDG_CUDA_TRY(cudaGetLastError());
     if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = M->cap_stream;
+    const int64_t nv = M->nfc * D2;
     auto iteration = [&](cudaStream_t st) {
       if (tl) {
-        bicg_p_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
+        bicg_p_flat_kernel<T><<<nb, kNT, 0, st>>>(nv, V, scal);
         coarse_cycle<T, D2>(M, CA, V.p, st, scal + B_DONE);
         bicg_tl_kernel<T, D2, B_DONE><<<nb, kNT, 0, st>>>(F, CA, Binv, V.p, V.ph, scal);
       } else {
@@ -1072,14 +1202,14 @@ struct Solver {
       }
       bicg_v_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
       if (tl) {
-        bicg_s_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
+        bicg_s_flat_kernel<T><<<nb, kNT, 0, st>>>(nv, V, scal);
         coarse_cycle<T, D2>(M, CA, V.s, st, scal + B_DONE);
         bicg_tl_kernel<T, D2, B_DONE><<<nb, kNT, 0, st>>>(F, CA, Binv, V.s, V.sh, scal);
       } else {
         bicg_s_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
       }
       bicg_t_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
-      bicg_x_kernel<T, D2><<<nb, kNT, 0, st>>>(F, V, M->d_red, M->d_counter, scal);
+      bicg_x_flat_kernel<T><<<nb, kNT, 0, st>>>(nv, V, M->d_red, M->d_counter, scal);
     };
     auto body = [&](cudaStream_t st, cudaGraphConditionalHandle h) {
       for (int it = 0; it < kGraphIters; ++it) iteration(st);
@@ -1117,15 +1247,16 @@ struct Solver {
     return HDG_OK;
   }
 
+  // the extra vectors s, t, ph, sh at strides rounded up to whole 16-byte units
   BicgVecs<double> static bicg_vecs64(hdg_mesh* M) {
-    const int64_t nv = M->nfc * D2;
-    return BicgVecs<double>{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + nv, M->d_bicg + 2 * nv,
-                            M->d_bicg + 3 * nv};
+    const int64_t sv = bicg_stride(M->nfc * D2, 2);
+    return BicgVecs<double>{M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_bicg, M->d_bicg + sv, M->d_bicg + 2 * sv,
+                            M->d_bicg + 3 * sv};
   }
   BicgVecs<float> static bicg_vecs32(hdg_mesh* M) {
-    const int64_t nv = M->nfc * D2;
+    const int64_t sv = bicg_stride(M->nfc * D2, 4);
     return BicgVecs<float>{M->d_x32, M->d_q32, M->d_z32, M->d_p32, reinterpret_cast<float*>(M->d_q), M->d_bicg32,
-                           M->d_bicg32 + nv, M->d_bicg32 + 2 * nv, M->d_bicg32 + 3 * nv};
+                           M->d_bicg32 + sv, M->d_bicg32 + 2 * sv, M->d_bicg32 + 3 * sv};
   }
 
   // ||b - H x||_2 over the free dofs in FP64, r written to `r`.
