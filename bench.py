@@ -61,7 +61,11 @@ HBM_FALLBACK_GBS = 6800.0
 # and scaled by the element count: K1 streams per-element data only, so traffic is proportional
 # to it), valid while the kernel's sources (K1_SOURCES, hashed together) are unchanged.
 K1_TRAFFIC = {
-    ("cube48_k2_conv", "assemble_df.cu"): {"sha256": None, "bytes_per_element": None, "captured": None},
+    ("cube48_k2_conv", "assemble_df.cu"): {
+        "sha256": "05e66ac6bb50600708b77d26bb70b8a5d36cfbf90bfe0733a897bb511faeb27e",
+        "bytes_per_element": (120068096 + 237978880) / 24576,
+        "captured": "ncu --set full of the same kernel on the 16^3 x 6 mesh of the workload (24,576 elements), "
+                    "profiles/assemble_df_kernel_conv_k2_cube16.md"},
     ("cube16_k3", "assemble_df.cu"): {"sha256": None, "bytes_per_element": None, "captured": None},
 }
 # the sources of each K1 translation unit (the kernel and the device headers it includes)
@@ -346,7 +350,7 @@ class Workload:
     """A workload's mesh on the GPU and its PDE data at the library's nodes (host copies kept
     for the end-to-end leg)."""
 
-    def __init__(self, name, dev, stream, s=None):
+    def __init__(self, name, dev, stream, s=None, rule=0):
         import torch
 
         from paper_1305_1489_gb300 import HDGMesh
@@ -357,6 +361,8 @@ class Workload:
         c, e = kuhn_cube(prob.s, prob.jitter, prob.seed)
         d, n = boundary_faces(c, e, prob.classify)
         self.M = M = HDGMesh(c, e, d, n, prob.k, stream=stream)
+        if rule:
+            M.set_volume_rule(rule)
         self.conv = prob.beta is not None
         X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
         FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
@@ -616,6 +622,46 @@ def run_workload(W, args, stream, dev, world=1, full=True):
     return out
 
 
+def run_rule_comparison(dev, stream, reps=5):
+    """The FP64 assembly (direct quadrature sums) of the reaction-diffusion workload on the
+    conical rule ((k+2)^3 = 125 nodes at k = 3) and on the smaller symmetric rule (70 nodes):
+    time per launch, and the discretisation errors of the step's solution on each rule."""
+    import torch
+
+    from paper_1305_1489_gb300 import HDG_FP64, HDG_MIXED_FP32, HDG_RULE_CONICAL, HDG_RULE_SYMMETRIC
+
+    out = {"workload": f"{EXTRA_RD} (24,576 elements, k = 3), FP64 assembly"}
+    for name, rule in (("conical", HDG_RULE_CONICAL), ("symmetric", HDG_RULE_SYMMETRIC)):
+        W = Workload(EXTRA_RD, dev, stream, rule=rule)
+        M = W.M
+        M.assemble_condense(HDG_FP64)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.assemble_condense(HDG_FP64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        M.set_inner_tolerance(1e-5)
+        uh, it, rr = M.solve_trace(rtol=1e-12, maxit=20000, precision=HDG_MIXED_FP32)
+        q, u = M.recover(uh)
+        prob = W.prob
+        u_vol = torch.from_numpy(np.ascontiguousarray(prob.u(W.X, W.Y, W.Z))).to(dev)
+        u_fn = torch.from_numpy(np.ascontiguousarray(prob.u(W.FX, W.FY, W.FZ))).to(dev)
+        e_u, ref_u = M.volume_norm2(u, u_vol)
+        e_f, ref_f = M.face_norm2(uh, u_fn)
+        out[name] = {"nq": M.nq, "k1_fp64_ms": float(np.median(ts)),
+                     "coefficient_bytes_per_element": 3 * 8 * M.nq,
+                     "e_u": float(np.sqrt(e_u / ref_u)), "e_uhat": float(np.sqrt(e_f / ref_f))}
+        M.close()
+        del W
+        torch.cuda.empty_cache()
+    out["speedup"] = out["conical"]["k1_fp64_ms"] / out["symmetric"]["k1_fp64_ms"]
+    return out
+
+
 def run_batch(args):
     """64 independent cube problems (s ~ U{8..24}, k ~ U{1..4}, kappa = 10^U(-1,1), c ~ U[0,5],
     Dirichlet everywhere, seed 4) solved as one batch: one CUDA graph launch (double-float
@@ -835,6 +881,18 @@ def run_gpu(args, rank, world, local_rank):
     }
     if world == 1 and rank == 0 and args.extras:
         extras = {}
+        # the small FP64 workload: plain method (FP64 assembly, FP64 block-Jacobi PCG, no coarse space)
+        import copy
+        a1 = copy.copy(args)
+        a1.asm, a1.solve, a1.coarse = "fp64", "fp64", False
+        W1 = Workload("cube4_k1", dev, stream)
+        r1 = run_workload(W1, a1, stream, dev, 1, full=False)
+        extras["cube4_k1"] = {
+            "workload": f"cube4_k1: unit cube 4^3x6 Kuhn tets ({r1['nelt']} elements), k=1, kappa=c=tau=1, Dirichlet "
+                        "everywhere, u = sin sin sin; FP64 assembly and FP64 block-Jacobi PCG to 1e-10 (plain method)",
+            **{k: r1[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step", "gpu_launches")}}
+        W1.M.close()
+        del W1
         W2 = Workload(EXTRA_RD, dev, stream)
         r2 = run_workload(W2, args, stream, dev, 1, full=True)
         extras[EXTRA_RD] = {
@@ -845,6 +903,10 @@ def run_gpu(args, rank, world, local_rank):
         W2.M.close()
         del W2
         torch.cuda.empty_cache()
+        try:
+            extras["symmetric_rule"] = run_rule_comparison(dev, stream)
+        except Exception as exc:  # noqa: BLE001
+            extras["symmetric_rule"] = {"error": repr(exc)}
         try:
             extras["batch_64"] = run_batch(args)
         except Exception as exc:  # noqa: BLE001 -- an extra must not lose the headline line

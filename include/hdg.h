@@ -140,6 +140,22 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
 
+/* Volume quadrature rule (eq. 3.1; the paper leaves the rule open and remarks that suitable
+ * rules are easy to find):
+ *   HDG_RULE_CONICAL (default): conical-product Gauss-Jacobi, (k+2)^3 nodes;
+ *   HDG_RULE_SYMMETRIC: the fully symmetric Grundmann-Moller rule of the same degree 2k+3 with
+ *   C(k+5, 4) nodes (k = 1..4: 15, 35, 70, 126 instead of 27, 64, 125, 216; some weights
+ *   negative), which cuts the coefficient data and the direct quadrature sums of the FP64
+ *   assembly.  The rule changes the discrete solution by the quadrature error, so it is the
+ *   caller's choice, not the autotuner's.
+ * Call right after hdg_mesh_create: every array at the volume nodes changes size, so the
+ * coefficients are unset (set them again from hdg_quadrature_nodes) and the assembly is
+ * invalidated.  The double-float assembly needs the conical rule (its masses are summed by
+ * sum factorisation over the conical product): hdg_assemble_condense(HDG_DF32) returns
+ * HDG_ERR_UNSUPPORTED with the symmetric rule.  HDG_ERR_ARG for another value.            */
+typedef enum { HDG_RULE_CONICAL = 0, HDG_RULE_SYMMETRIC = 1 } hdg_volume_rule;
+int hdg_set_volume_rule(hdg_mesh* mesh, int rule);
+
 /* Local method of the next hdg_assemble_condense (Section 9, "BDM"):
  *   HDG_METHOD_HDG (default): the HDG method of eq. 1.2;
  *   HDG_METHOD_BDM: the hybridised Brezzi-Douglas-Marini element, tau = 0 (the tau given to
@@ -396,7 +412,8 @@ int64_t hdg_launch_count(const hdg_mesh* mesh);
 
 /* Host-only helpers (no GPU needed), used to check the library's host logic.
  * hdg_host_table: copy the reference table `name` of degree k into out (host f64, at least
- *   *size entries; out may be NULL to query *size).  Names and layouts (row-major):
+ *   *size entries; out may be NULL to query *size; "<name>:sym" gives the table of the
+ *   symmetric volume rule of hdg_set_volume_rule).  Names and layouts (row-major):
  *   vol_pts [nq][3], vol_w [nq], P [nq][n], Pd [3][nq][n], Chat [3][n][n] (eq. 3.5-3.7),
  *   face_pts [nf][2], face_w [nf], Pl [4][nf][n], D [nf][d2], Dmu [6][nf][d2] (eq. 4.4, 4.7),
  *   S [4][n][n] (eq. 4.5 pieces), E [4][6][d2][n] (eq. 4.10 pieces),

@@ -81,12 +81,13 @@ def local_solvers_conv(blk, Bc, aDP, aDD):
     return CK, Cf, X2, xf, (A1, A2, Af, A3)
 
 
-def solve_problem_conv(prob, coords, elems, dirichlet, neumann):
-    """Whole pipeline for a convection problem with Dirichlet data on every face."""
+def solve_problem_conv(prob, coords, elems, dirichlet, neumann, rule="conical"):
+    """Whole pipeline for a convection problem with Dirichlet data on every face, on the
+    volume rule `rule`."""
     from .geometry import ExpandedMesh
 
     mesh = ExpandedMesh(coords, elems, dirichlet, neumann)
-    tab = hdg.Tables(prob.k)
+    tab = hdg.Tables(prob.k, rule)
     X, Y, Z = hdg.volume_nodes(mesh, tab)
     kap, cq, fq = prob.kappa(X, Y, Z), prob.c(X, Y, Z), prob.f(X, Y, Z)
     blk = hdg.local_blocks(mesh, tab, kap, cq, fq, tau=prob.tau)

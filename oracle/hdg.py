@@ -34,14 +34,25 @@ from . import basis, quadrature
 from .geometry import ExpandedMesh, piola_cofactors
 
 
-class Tables:
-    """Reference-element tables for degree k (Sections 3 and 4)."""
+def volume_rule(k, rule="conical"):
+    """The volume rule of eq. 3.1: the conical product (default) or the smaller symmetric rule
+    of the same degree (quadrature.symmetric_volume_rule)."""
+    if rule == "conical":
+        return quadrature.volume_rule(k)
+    if rule == "symmetric":
+        return quadrature.symmetric_volume_rule(k)
+    raise ValueError(rule)
 
-    def __init__(self, k):
+
+class Tables:
+    """Reference-element tables for degree k (Sections 3 and 4) on the volume rule `rule`."""
+
+    def __init__(self, k, rule="conical"):
         self.k = k
+        self.rule = rule
         self.n = basis.d3(k)
         self.d2 = basis.d2(k)
-        self.p, self.w, self.Lambda = quadrature.volume_rule(k)  # eq. 3.1
+        self.p, self.w, self.Lambda = volume_rule(k, rule)  # eq. 3.1
         self.P = basis.dubiner3(k, self.p)  # eq. 3.5
         self.Pstar = basis.dubiner3_grad(k, self.p)  # eq. 3.66, [3, Nq, n]
         # eq. 3.7: C_hat^* = (1/6) (omega_hat . P)^T P^*
@@ -225,12 +236,13 @@ def recover(mesh, X2, xf, uhat, elems=None):
     return sol[:, :3 * n].reshape(-1, 3, n), sol[:, 3 * n:]
 
 
-def postprocess(mesh, k, kappa_q, q, u, elems=None):
+def postprocess(mesh, k, kappa_q, q, u, elems=None, rule="conical"):
     """eq. 9.11: u* in P_{k+1}(K) with (grad u*, grad w)_K = -(kappa^-1 q_h, grad w)_K and
-    (u*, 1)_K = (u_h, 1)_K, on the degree-k volume rule; bordered (Lagrange) system per element.
-    Returns u* coefficients in the degree-(k+1) basis, [Nelt, d3(k+1)]."""
+    (u*, 1)_K = (u_h, 1)_K, on the degree-k volume rule `rule` (the one kappa_q is given on);
+    bordered (Lagrange) system per element.  Returns u* coefficients in the degree-(k+1)
+    basis, [Nelt, d3(k+1)]."""
     idx = np.arange(mesh.nelt) if elems is None else np.asarray(elems)
-    p, w, _ = quadrature.volume_rule(k)
+    p, w, _ = volume_rule(k, rule)
     P = basis.dubiner3(k, p)
     P1 = basis.dubiner3(k + 1, p)
     G1 = basis.dubiner3_grad(k + 1, p)  # [3, Nq, n']
@@ -317,16 +329,17 @@ def monolithic_solve(mesh, tab, blk, uhatD, PhiN=None):
     return loc[:, :3 * n].reshape(ne, 3, n), loc[:, 3 * n:], x[nloc:].reshape(mesh.nfc, d2)
 
 
-def solve_problem(prob, coords=None, elems=None, dirichlet=None, neumann=None):
+def solve_problem(prob, coords=None, elems=None, dirichlet=None, neumann=None, rule="conical"):
     """The whole pipeline of Section 3 (i)-(8): mesh, tables, blocks, local solvers, assembly,
-    boundary data, trace solve, recovery, postprocess.  Returns a dict of everything."""
+    boundary data, trace solve, recovery, postprocess, on the volume rule `rule`.  Returns a
+    dict of everything."""
     from workloads import boundary_faces, kuhn_cube
 
     if coords is None:
         coords, elems = kuhn_cube(prob.s, prob.jitter, prob.seed)
         dirichlet, neumann = boundary_faces(coords, elems, prob.classify)
     mesh = ExpandedMesh(coords, elems, dirichlet, neumann)
-    tab = Tables(prob.k)
+    tab = Tables(prob.k, rule)
     X, Y, Z = volume_nodes(mesh, tab)
     kap, cq, fq = prob.kappa(X, Y, Z), prob.c(X, Y, Z), prob.f(X, Y, Z)
     blk = local_blocks(mesh, tab, kap, cq, fq, tau=prob.tau)
@@ -340,6 +353,6 @@ def solve_problem(prob, coords=None, elems=None, dirichlet=None, neumann=None):
         PhiN = neumann_data(mesh, tab, prob.gN(NX, NY, NZ))
     uhat, H, b, free = solve_trace(mesh, tab.d2, H, F, uhatD, PhiN)
     q, u = recover(mesh, X2, xf, uhat)
-    ustar = postprocess(mesh, prob.k, kap, q, u)
+    ustar = postprocess(mesh, prob.k, kap, q, u, rule=rule)
     return dict(mesh=mesh, tab=tab, blk=blk, CK=CK, Cf=Cf, X2=X2, xf=xf, H=H, F=F, b=b, free=free,
                 uhatD=uhatD, PhiN=PhiN, uhat=uhat, q=q, u=u, ustar=ustar, kappa_q=kap)

@@ -91,3 +91,34 @@ def F_mu(mu, qhat):
     }
     a, b = table[mu]
     return np.stack([a, b], axis=-1)
+
+
+def symmetric_volume_rule(k):
+    """Grundmann-Moller rule of index s = k + 1 on the reference tetrahedron (Grundmann and
+    Moller, SIAM J. Numer. Anal. 15, 1978): exact to degree 2s + 1 = 2k + 3 like volume_rule(k)
+    but with C(s + 4, 4) nodes instead of (k + 2)^3 (k = 2: 35 against 64; k = 3: 70 against
+    125) -- the smaller symmetric rule of the paper's remark on quadrature.  With d = 2s + 1 and
+    dimension 3, level i = 0..s contributes the nodes with barycentric coordinates
+    (2 beta_j + 1) / (d + 3 - 2i) for every beta in N^4 with |beta| = s - i, all with the weight
+    (-1)^i 2^-2s (d + 3 - 2i)^d / (i! (d + 3 - i)!) (a rule for the simplex of volume 1/3!; the
+    weights here are scaled by 3! to sum to one, the paper's convention).  Some weights are
+    negative.  Returns the same triple as volume_rule: nodes [Nq,3], weights [Nq], barycentrics."""
+    from itertools import product
+    from math import factorial
+
+    s = k + 1
+    d = 2 * s + 1
+    pts, wts = [], []
+    for i in range(s + 1):
+        wt = (-1) ** i * 2.0 ** (-2 * s) * float(d + 3 - 2 * i) ** d / (factorial(i) * factorial(d + 3 - i))
+        m = s - i
+        for beta in product(range(m + 1), repeat=4):
+            if sum(beta) != m:
+                continue
+            lam = [(2 * b + 1) / (d + 3 - 2 * i) for b in beta]
+            pts.append((lam[1], lam[2], lam[3]))
+            wts.append(wt)
+    p = np.array(pts)
+    w = 6.0 * np.array(wts)
+    lam = np.column_stack([1 - p.sum(axis=1), p[:, 0], p[:, 1], p[:, 2]])
+    return p, w, lam

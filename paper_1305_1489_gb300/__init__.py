@@ -20,9 +20,11 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import HDG_DF32, HDG_FP64, HDG_METHOD_BDM, HDG_METHOD_HDG, HDG_MIXED_FP32, HDGError  # noqa: F401
+from ._lib import (HDG_DF32, HDG_FP64, HDG_METHOD_BDM, HDG_METHOD_HDG, HDG_MIXED_FP32, HDG_RULE_CONICAL,  # noqa: F401
+                   HDG_RULE_SYMMETRIC, HDGError)
 
 __all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "HDG_DF32", "HDG_METHOD_HDG", "HDG_METHOD_BDM",
+           "HDG_RULE_CONICAL", "HDG_RULE_SYMMETRIC",
            "build", "load_library"]
 
 
@@ -185,6 +187,14 @@ class HDGMesh:
         self.info = hdg_mesh_get_info(self._h)
         for key in ("nelt", "nfc", "k", "n", "d2", "m", "n1", "nq", "nf"):
             setattr(self, key, self.info[key])
+        self._keep = {}
+
+    def set_volume_rule(self, rule):
+        """hdg_set_volume_rule: HDG_RULE_CONICAL or HDG_RULE_SYMMETRIC (call before setting the
+        coefficients; self.nq follows)."""
+        _lib.check(_lib.load().hdg_set_volume_rule(self._h, int(rule)))
+        self.info = hdg_mesh_get_info(self._h)
+        self.nq = self.info["nq"]
         self._keep = {}
 
     def close(self):
@@ -505,6 +515,14 @@ class HDGBatch:
         for ptr, shape in ((uh, (M.nfc, M.d2)), (q, (M.nelt, 3, M.n)), (u, (M.nelt, M.n))):
             out.append(_device_view(ptr.value, int(np.prod(shape))).view(shape).clone())
         return tuple(out)
+
+    def set_volume_rule(self, rule):
+        """hdg_set_volume_rule: HDG_RULE_CONICAL or HDG_RULE_SYMMETRIC (call before setting the
+        coefficients; self.nq follows)."""
+        _lib.check(_lib.load().hdg_set_volume_rule(self._h, int(rule)))
+        self.info = hdg_mesh_get_info(self._h)
+        self.nq = self.info["nq"]
+        self._keep = {}
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -11,6 +11,8 @@ HDG_MIXED_FP32 = 1
 HDG_DF32 = 2
 HDG_METHOD_HDG = 0
 HDG_METHOD_BDM = 1
+HDG_RULE_CONICAL = 0
+HDG_RULE_SYMMETRIC = 1
 
 STATUS = {
     0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_ORIENTATION", 3: "HDG_ERR_NONCONFORMING",
@@ -75,6 +77,7 @@ _SIGS = {
     "hdg_volume_norm2": [P, C.c_int, P, P, P],
     "hdg_face_norm2": [P, P, P, P],
     "hdg_mass_contraction": [P, P, C.c_int, P],
+    "hdg_set_volume_rule": [P, C.c_int],
     "hdg_last_error": [C.c_char_p, C.c_size_t],
     "hdg_launch_count": [P],
     "hdg_host_table": [C.c_int, C.c_char_p, P, I64, C.POINTER(I64)],

@@ -76,6 +76,17 @@ static int upload_tables(hdg_mesh* M) {
   return HDG_OK;
 }
 
+// the device copies of the reference tables
+static void free_tables(hdg_mesh* M) {
+  DevTables& D = M->dt;
+  void* ptrs[] = {D.P, D.Pd, D.Chat, D.S, D.E, D.vol_w, D.lam, D.face_w, D.xi, D.D, D.P1, D.G1, D.Shat1, D.pairs_n,
+                  D.pairs_m, D.pairs_n1, D.Pl, D.Dmu, D.face_pts, D.P_df, D.Chat_df, D.S_df, D.E_df, D.sfAA_df,
+                  D.sfBB_df, D.sfCC_df, D.sfp2to1, D.sfp3to2, D.G1_df, D.Shat1_df, D.Pd_df, D.Pl_df, D.Dmu_df};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  D = DevTables();
+}
+
 static void release(hdg_mesh* M) {
   coarse_free(M);
   void* ptrs[] = {M->d_vx, M->d_geo, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
@@ -262,6 +273,9 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (M->beta_q && !M->beta_f) return fail(HDG_ERR_STATE, "convection set without hdg_set_face_convection");
   if (M->beta_q && M->method == HDG_METHOD_BDM)
     return fail(HDG_ERR_UNSUPPORTED, "the BDM element is built for reaction-diffusion (beta = 0)");
+  if (precision == HDG_DF32 && M->tab.rule != HDG_RULE_CONICAL)
+    return fail(HDG_ERR_UNSUPPORTED, "the double-float assembly sums the masses by sum factorisation, which needs "
+                                     "the conical volume rule");
   if (M->k == 0 && (M->beta_q || M->method == HDG_METHOD_BDM))
     return fail(HDG_ERR_UNSUPPORTED, "k = 0 is built for the HDG method without convection");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
@@ -273,6 +287,28 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (M->coarse) coarse_invalidate(M);
   M->rhs_ready = false;
   return check_status(M);
+}
+
+int hdg_set_volume_rule(hdg_mesh* M, int rule) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  if (rule != HDG_RULE_CONICAL && rule != HDG_RULE_SYMMETRIC) return fail(HDG_ERR_ARG, "unknown volume rule");
+  if (M->tab.rule == rule) return HDG_OK;
+  Tables T;
+  std::string err;
+  if (!build_tables(M->k, &T, &err, rule)) return fail(HDG_ERR_UNSUPPORTED, err);
+  if (M->stream) HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  free_tables(M);
+  M->tab = std::move(T);
+  int rc = upload_tables(M);
+  if (rc) return rc;
+  // every array at the volume nodes changes size: the caller sets the coefficients again
+  M->kappa = M->c = M->f = nullptr;
+  M->beta_q = M->beta_f = nullptr;
+  M->assembled = false;
+  M->rhs_ready = false;
+  M->c32_ready = false;
+  M->bj64_ready = M->bj32_ready = false;
+  return HDG_OK;
 }
 
 int hdg_set_method(hdg_mesh* M, int method) {
@@ -415,8 +451,13 @@ int hdg_host_table(int k, const char* name, double* out, int64_t capacity, int64
   if (!name || !size) return fail(HDG_ERR_ARG, "NULL argument");
   Tables T;
   std::string err;
-  if (!build_tables(k, &T, &err)) return fail(HDG_ERR_UNSUPPORTED, err);
-  const std::string s(name);
+  std::string s(name);
+  int rule = 0;  // "<name>:sym": the table of the symmetric volume rule
+  if (s.size() > 4 && s.compare(s.size() - 4, 4, ":sym") == 0) {
+    rule = 1;
+    s.resize(s.size() - 4);
+  }
+  if (!build_tables(k, &T, &err, rule)) return fail(HDG_ERR_UNSUPPORTED, err);
   const std::vector<double>* v = nullptr;
   if (s == "vol_pts") v = &T.vol_pts;
   else if (s == "vol_w") v = &T.vol_w;

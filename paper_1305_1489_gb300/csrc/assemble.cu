@@ -46,10 +46,11 @@ struct AsmArgs {
   int nu;  // u unknowns kept: n (HDG), n - d2 (hybridised BDM: u in P_{k-1}, tau = 0)
 };
 
-template <int K, bool CONV>
+// NQ: volume nodes of the rule in use ((k+2)^3 conical, or the symmetric rule's count)
+template <int K, bool CONV, int NQ>
 struct AsmSmem {
   using D = Dims<K>;
-  static constexpr int n = D::n, m = D::m, nq = D::nq, nf = D::nf, d2 = D::d2;
+  static constexpr int n = D::n, m = D::m, nq = NQ, nf = D::nf, d2 = D::d2;
   static constexpr int o_kw = 0, o_cw = o_kw + nq, o_fw = o_cw + nq;
   static constexpr int o_M = o_fw + nq;          // n*n   M -> L
   static constexpr int o_S = o_M + n * n;        // n*n   S_u -> L_s
@@ -68,11 +69,11 @@ struct AsmSmem {
   static constexpr size_t bytes = sizeof(double) * total;
 };
 
-template <int K, int NT, bool CONV>
+template <int K, int NT, bool CONV, int NQ>
 __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmArgs A) {
   using D = Dims<K>;
-  using SM = AsmSmem<K, CONV>;
-  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = D::nq, nf = D::nf;
+  using SM = AsmSmem<K, CONV, NQ>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, nq = NQ, nf = D::nf;
   constexpr int NP = n * (n + 1) / 2, MP = m * (m + 1) / 2;
   extern __shared__ double sm[];
   double* kw = sm + SM::o_kw;
@@ -392,17 +393,27 @@ __global__ void __launch_bounds__(NT, K1Occupancy<K>::MINB) assemble_kernel(AsmA
   }
 }
 
-template <int K, bool CONV>
-static cudaError_t launch_k(hdg_mesh* M, const AsmArgs& a) {
+template <int K, bool CONV, int NQ>
+static cudaError_t launch_kq(hdg_mesh* M, const AsmArgs& a) {
   constexpr int NT = K1Occupancy<K>::NT;
-  const size_t smem = AsmSmem<K, CONV>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(assemble_kernel<K, NT, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = AsmSmem<K, CONV, NQ>::bytes;
+  cudaError_t e =
+      cudaFuncSetAttribute(assemble_kernel<K, NT, CONV, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(assemble_kernel<K, NT, CONV>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(assemble_kernel<K, NT, CONV, NQ>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  assemble_kernel<K, NT, CONV><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  assemble_kernel<K, NT, CONV, NQ><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
   M->launches += 1;
   return cudaGetLastError();
+}
+
+// the conical rule's (k+2)^3 nodes, or the symmetric rule's C(k+5, 4)
+template <int K, bool CONV>
+static cudaError_t launch_k(hdg_mesh* M, const AsmArgs& a) {
+  constexpr int NQS = (K + 2) * (K + 3) * (K + 4) * (K + 5) / 24;
+  if (M->tab.nq == NQS) return launch_kq<K, CONV, NQS>(M, a);
+  if (M->tab.nq == Dims<K>::nq) return launch_kq<K, CONV, Dims<K>::nq>(M, a);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_assemble(hdg_mesh* M) {

@@ -17,6 +17,7 @@ struct Coarse;
 // Host copies, row-major.  Built once per degree k (tables.cpp).
 struct Tables {
   int k = 0, n = 0, d2 = 0, m = 0, nq = 0, nf = 0, n1 = 0;
+  int rule = 0;  // volume rule: 0 conical product ((k+2)^3 nodes), 1 symmetric (Grundmann-Moller)
   std::vector<double> vol_pts;  // [nq][3]   p_hat_q                      (eq. 3.1)
   std::vector<double> vol_w;    // [nq]      omega_hat_q, sum = 1         (eq. 3.1)
   std::vector<double> lam;      // [nq][4]   barycentrics Lambda          (eq. 3.4)
@@ -47,7 +48,8 @@ struct Tables {
   std::vector<int16_t> sfp3to2;   // [n(n+1)/2]  2-D pair ((pa, qa), (pb, qb)) of each 3-D pair
 };
 
-bool build_tables(int k, Tables* t, std::string* err);
+bool build_tables(int k, Tables* t, std::string* err, int rule = 0);
+int symmetric_rule_nodes(int k);  // nodes of the symmetric volume rule of degree k
 int d3_of(int k);
 int d2_of(int k);
 

@@ -23,11 +23,11 @@ __global__ void __launch_bounds__(NT) projection_kernel(const double* __restrict
                                                         const double* __restrict__ Dmu, const double* __restrict__ wf,
                                                         const double* __restrict__ q_vol, const double* __restrict__ u_vol,
                                                         const double* __restrict__ q_face,
-                                                        const double* __restrict__ u_face, int64_t nelt,
+                                                        const double* __restrict__ u_face, int64_t nelt, int nq,
                                                         double* __restrict__ Pq, double* __restrict__ Pu,
                                                         int32_t* status) {
-  using D = Dims<K>;
-  constexpr int n = D::n, d2 = D::d2, m = D::m, nq = D::nq, nf = D::nf, nlow = n - d2;
+  using D = Dims<K>;  // nq: nodes of the volume rule in use
+  constexpr int n = D::n, d2 = D::d2, m = D::m, nf = D::nf, nlow = n - d2;
   constexpr int LD = m + 1;  // augmented row: [B | rhs]
   __shared__ double B[m * LD];
   __shared__ double low[4][nlow > 0 ? nlow : 1];
@@ -150,7 +150,7 @@ cudaError_t launch_projection(hdg_mesh* M, const double* q_vol, const double* u_
 #define HDG_PJ(KK, NTT)                                                                                     \
   projection_kernel<KK, NTT><<<g, NTT, 0, M->stream>>>(M->d_geo, M->d_perm, M->tau, M->dt.P, M->dt.vol_w,  \
                                                        M->dt.E, M->dt.Dmu, M->dt.face_w, q_vol, u_vol, q_face, \
-                                                       u_face, M->nelt, Pq, Pu, M->d_status)
+                                                       u_face, M->nelt, M->tab.nq, Pq, Pu, M->d_status)
   switch (M->k) {
     case 0: HDG_PJ(0, 64); break;
     case 1: HDG_PJ(1, 64); break;

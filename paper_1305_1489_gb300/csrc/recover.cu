@@ -516,14 +516,14 @@ cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u
 // (grad u*, grad w)_K = -(kappa^-1 q_h, grad w)_K for w in P_{k+1}(K), (u*, 1)_K = (u_h, 1)_K.
 // With the orthonormal hierarchical basis P'_1 = 1 and P'_i (i > 1) has zero mean, so
 // u*_1 = u_{h,1} and the coefficients 2..n1 solve the (n1-1) x (n1-1) SPD stiffness system.
-template <int K, int NT>
+template <int K, int NT, int NQ>
 __global__ void __launch_bounds__(NT) postprocess_kernel(
     const double* __restrict__ vx, const double* __restrict__ kappa, const double* __restrict__ P,
     const double* __restrict__ G1, const double* __restrict__ Shat1, const double* __restrict__ w,
     const int16_t* __restrict__ pairs1, const double* __restrict__ q, const double* __restrict__ u,
     int64_t nelt, double* __restrict__ ustar, int32_t* status) {
   using D = Dims<K>;
-  constexpr int n = D::n, nq = D::nq, n1 = D::n1, nr = n1 - 1;
+  constexpr int n = D::n, nq = NQ, n1 = D::n1, nr = n1 - 1;  // NQ: nodes of the volume rule in use
   constexpr int NP = nr * (nr + 1) / 2;
   __shared__ double Ks[nr * nr], rhs[nr], invd[nr], rpart[6 * nr];
   __shared__ double qs[3 * n], Qs[3 * nq];
@@ -771,10 +771,16 @@ __global__ void __launch_bounds__(NT) postprocess_df_kernel(
 
 cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, double* ustar) {
   const unsigned g = (unsigned)M->nelt;
-#define HDG_PP(KK, NTT)                                                                             \
-  postprocess_kernel<KK, NTT><<<g, NTT, 0, M->stream>>>(M->d_vx, M->kappa, M->dt.P, M->dt.G1,      \
-                                                       M->dt.Shat1, M->dt.vol_w, M->dt.pairs_n1, q, \
-                                                       u, M->nelt, ustar, M->d_status)
+#define HDG_PPQ(KK, NTT, NQQ)                                                                          \
+  postprocess_kernel<KK, NTT, NQQ><<<g, NTT, 0, M->stream>>>(M->d_vx, M->kappa, M->dt.P, M->dt.G1,      \
+                                                            M->dt.Shat1, M->dt.vol_w, M->dt.pairs_n1, q, \
+                                                            u, M->nelt, ustar, M->d_status)
+  // the conical rule's (k+2)^3 nodes, or the symmetric rule's C(k+5, 4)
+#define HDG_PP(KK, NTT)                                                           \
+  if (M->tab.nq == (KK + 2) * (KK + 3) * (KK + 4) * (KK + 5) / 24)               \
+    HDG_PPQ(KK, NTT, (KK + 2) * (KK + 3) * (KK + 4) * (KK + 5) / 24);            \
+  else                                                                            \
+    HDG_PPQ(KK, NTT, Dims<KK>::nq)
 #define HDG_PPDF(KK, NTT)                                                                              \
   postprocess_df_kernel<KK, NTT><<<g, NTT, 0, M->stream>>>(                                             \
       M->d_geo, M->kappa, reinterpret_cast<const df*>(M->dt.P_df), reinterpret_cast<const df*>(M->dt.G1_df), \
@@ -799,6 +805,7 @@ cudaError_t launch_postprocess(hdg_mesh* M, const double* q, const double* u, do
   }
 #undef HDG_PPDF
 #undef HDG_PP
+#undef HDG_PPQ
   M->launches++;
   return cudaGetLastError();
 }

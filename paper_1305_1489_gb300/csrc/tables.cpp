@@ -7,6 +7,13 @@
 // bisection in long double, are the nodes; the weights are mu_0 / sum_j p_j(x)^2 with p_j
 // the orthonormal polynomials (Christoffel numbers).
 //
+// The smaller symmetric volume rule (rule 1, the paper's remark that such rules can be found in
+// the literature): Grundmann-Moller of index s = k + 1 (SIAM J. Numer. Anal. 15, 1978), exact to
+// the same degree 2s + 1 = 2k + 3 with C(s + 4, 4) nodes: level i = 0..s has the nodes with
+// barycentric coordinates (2 b_j + 1) / (d + 3 - 2i), b in N^4, |b| = s - i, d = 2s + 1, all of
+// weight (-1)^i 2^-2s (d + 3 - 2i)^d / (i! (d + 3 - i)!) on the simplex of volume 1/6 (times 6
+// here, so that the weights sum to one).  Some weights are negative.  Formed in long double.
+//
 // Bases (eq. 3.3 and Section 4 "Bases, faces, and boundaries"): Dubiner bases in collapsed
 // coordinates, orthonormal (int_{K_hat} P_i P_j = delta_ij / 6, int_{K_hat_2} D_i D_j =
 // delta_ij / 2), ordered by degree then (p, q[, r]).  Gradients are taken analytically
@@ -154,17 +161,54 @@ void F_mu(int mu, double s, double t, double* so, double* to) {
 
 }  // namespace
 
-bool build_tables(int k, Tables* T, std::string* err) {
+int symmetric_rule_nodes(int k) {
+  const int s = k + 1;
+  return (s + 1) * (s + 2) * (s + 3) * (s + 4) / 24;  // C(s + 4, 4)
+}
+
+namespace {
+// Grundmann-Moller nodes (x, y, z) = barycentrics 1..3 and weights (sum one), see the header
+void symmetric_volume_rule(int k, std::vector<double>* pts, std::vector<double>* w) {
+  const int s = k + 1, d = 2 * s + 1;
+  pts->clear();
+  w->clear();
+  for (int i = 0; i <= s; ++i) {
+    LD fi = 1, fdi = 1;
+    for (int j = 2; j <= i; ++j) fi *= j;
+    for (int j = 2; j <= d + 3 - i; ++j) fdi *= j;
+    const LD den = (LD)(d + 3 - 2 * i);
+    LD wt = std::pow(den, (LD)d) / (fi * fdi) / std::pow((LD)2, (LD)(2 * s));
+    if (i & 1) wt = -wt;
+    const int mlev = s - i;
+    for (int b0 = 0; b0 <= mlev; ++b0)
+      for (int b1 = 0; b1 <= mlev - b0; ++b1)
+        for (int b2 = 0; b2 <= mlev - b0 - b1; ++b2) {
+          const int b3 = mlev - b0 - b1 - b2;
+          pts->push_back((double)((2 * b1 + 1) / den));
+          pts->push_back((double)((2 * b2 + 1) / den));
+          pts->push_back((double)((2 * b3 + 1) / den));
+          w->push_back((double)(6 * wt));
+        }
+  }
+}
+}  // namespace
+
+bool build_tables(int k, Tables* T, std::string* err, int rule) {
   if (k < 0 || k > 4) {
     *err = "degree k must be in 0..4";
     return false;
   }
+  if (rule != 0 && rule != 1) {
+    *err = "unknown volume rule";
+    return false;
+  }
   const int nn = k + 2;
   T->k = k;
+  T->rule = rule;
   T->n = d3_of(k);
   T->d2 = d2_of(k);
   T->m = 4 * T->d2;
-  T->nq = nn * nn * nn;
+  T->nq = rule == 1 ? symmetric_rule_nodes(k) : nn * nn * nn;
   T->nf = nn * nn;
   T->n1 = d3_of(k + 1);
   const int n = T->n, d2 = T->d2, nq = T->nq, nf = T->nf, n1 = T->n1;
@@ -178,7 +222,23 @@ bool build_tables(int k, Tables* T, std::string* err) {
   T->vol_w.resize(nq);
   T->lam.resize(nq * 4);
   double wsum = 0;
-  for (int i = 0; i < nn; ++i)
+  if (rule == 1) {
+    std::vector<double> sp, sw;
+    symmetric_volume_rule(k, &sp, &sw);
+    for (int q = 0; q < nq; ++q) {
+      const double x = sp[3 * q], y = sp[3 * q + 1], z = sp[3 * q + 2];
+      T->vol_pts[3 * q] = x;
+      T->vol_pts[3 * q + 1] = y;
+      T->vol_pts[3 * q + 2] = z;
+      T->vol_w[q] = sw[q];
+      wsum += sw[q];
+      T->lam[4 * q] = 1 - x - y - z;
+      T->lam[4 * q + 1] = x;
+      T->lam[4 * q + 2] = y;
+      T->lam[4 * q + 3] = z;
+    }
+  }
+  for (int i = 0; i < (rule == 1 ? 0 : nn); ++i)
     for (int j = 0; j < nn; ++j)
       for (int l = 0; l < nn; ++l) {
         int q = (i * nn + j) * nn + l;
@@ -308,8 +368,9 @@ bool build_tables(int k, Tables* T, std::string* err) {
   // x = t3_l (1 - t1_i)(1 - t2_j) the collapsed coordinates are a = 2 t3_l - 1, b = 2 t2_j - 1,
   // c = 2 t1_i - 1, and the Dubiner function (p, q, r) is nrm A_p(l) B_pq(j) C'_pqr(i) with
   //   A_p = P_p^(0,0)(a),  B_pq = (1 - t2)^p P_q^(2p+1,0)(b),  C'_pqr = (1 - t1)^(p+q) P_r^(2p+2q+2,0)(c)
-  // (the normalisation nrm goes into C).
-  {
+  // (the normalisation nrm goes into C).  The conical rule only: the symmetric rule has no
+  // tensor structure (the assembly that needs these tables refuses it).
+  if (rule == 0) {
     std::vector<double> A((k + 1) * nn), B, C(n * nn);
     std::vector<std::pair<int, int>> idx2;
     for (int p = 0; p <= k; ++p)

@@ -70,6 +70,21 @@ def test_host_tables_match_oracle(lib, k):
 
 
 @pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_host_symmetric_rule_tables_match_oracle(lib, k):
+    """The library's own Grundmann-Moller rule (tables.cpp) against the oracle's
+    (quadrature.symmetric_volume_rule): same nodes in the same order, same weights, and the
+    volume basis tables built on them."""
+    tab = ohdg.Tables(k, "symmetric")
+    n = tab.n
+    assert np.allclose(_table(lib, k, "vol_pts:sym").reshape(-1, 3), tab.p, atol=1e-15, rtol=0)
+    assert np.allclose(_table(lib, k, "vol_w:sym"), tab.w, atol=1e-14, rtol=0)
+    assert np.abs(_table(lib, k, "P:sym").reshape(-1, n) - tab.P).max() < 1e-12
+    assert np.abs(_table(lib, k, "Pd:sym").reshape(3, -1, n) - tab.Pstar).max() < 1e-11
+    # C_hat is a volume integral of degree 2k - 1: the same on either rule
+    assert np.abs(_table(lib, k, "Chat:sym") - _table(lib, k, "Chat")).max() < 1e-12
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
 def test_host_sum_factorisation_reproduces_oracle_masses(lib, k):
     """The library's sum-factorisation tables, summed in three passes as the double-float K1
     does, give the oracle's direct quadrature sum_q g_q P_a P_b for an arbitrary weight g."""
