@@ -389,8 +389,13 @@ class Workload:
         self.M.set_boundary_data(dv["uD"], dv.get("gN"))
 
     def hierarchy(self):
+        """The nested P1 levels of the two-level preconditioner, coarsened down to at most 64
+        nodes (to a single node on meshes too small for that)."""
         from workloads import kuhn_p1_hierarchy
-        return kuhn_p1_hierarchy(self.prob.s, self.prob.dirichlet_planes)
+        h = kuhn_p1_hierarchy(self.prob.s, self.prob.dirichlet_planes, strict=False)
+        if len(h[0]) < 2:
+            h = kuhn_p1_hierarchy(self.prob.s, self.prob.dirichlet_planes, max_coarsest=1, strict=False)
+        return h
 
 
 def run_workload(W, args, stream, dev, world=1, full=True):
@@ -558,6 +563,10 @@ def run_workload(W, args, stream, dev, world=1, full=True):
                 "(eq. 9.13) time is per launch over all elements"}
     del q_vol, q_face, u_vol, u_face, Pq, Pu
 
+    # the dense mass contraction (eq. 3.55, M_{kappa^-1}) as one GEMM on the tensor cores
+    # (BF16 operands, FP32 accumulation) against the CUDA-core FP32 contraction
+    out["h2_contraction"] = h2_contraction(W, dev, stream)
+
     # end to end through the public API with host buffers (pinned) and copies in the region
     pin = {k: torch.from_numpy(v).pin_memory() for k, v in W.host.items()}
     hq = torch.empty((nelt, 3, M.n), dtype=torch.float64).pin_memory()
@@ -620,6 +629,40 @@ def run_workload(W, args, stream, dev, world=1, full=True):
                            f"({FP32_MEASURED_TFLOPS} measured); ncu's FMA-pipe utilisation of this kernel is in "
                            "profiles/")}
     return out
+
+
+def h2_contraction(W, dev, stream, reps=5):
+    """hdg_mass_contraction of 1/kappa on the workload's mesh: tensor cores (mode 0) and CUDA
+    cores in FP32 (mode 2), times per launch, throughput and the BF16 result's normwise error
+    against the FP32 one."""
+    import torch
+
+    M = W.M
+    g = torch.from_numpy(np.ascontiguousarray(1.0 / W.host["kappa"])).to(dev)
+    n, nq = M.n, M.nq
+    npair = n * (n + 1) // 2
+    res = {}
+    outs = {}
+    for name, mode in (("tensor_core_bf16", 0), ("cuda_core_fp32", 2)):
+        outs[name] = M.mass_contraction(g, mode)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            M.mass_contraction(g, mode)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        flops = 2.0 * M.nelt * nq * npair
+        byts = M.nelt * (8 * nq + 4 * npair + 8)
+        res[name] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "gbs": byts / (ms / 1e3) / 1e9}
+    a, b = outs["tensor_core_bf16"], outs["cuda_core_fp32"]
+    res["bf16_normwise_error_vs_fp32"] = float((a - b).abs().max() / b.abs().max())
+    res["note"] = (f"[{M.nelt} x {nq}] . [{nq} x {npair}] per launch; bytes = the FP64 coefficient in, the FP32 "
+                   "masses out; HBM-bound at this contraction length")
+    return res
 
 
 def run_rule_comparison(dev, stream, reps=5):
@@ -880,46 +923,57 @@ def run_gpu(args, rank, world, local_rank):
         "solve_roofline": r["solve_roofline"], "wall_s_timed": r["wall_s_timed"],
     }
     if world == 1 and rank == 0 and args.extras:
-        extras = {}
+        out["extras"] = run_extras(args, dev, stream)
+    return out
+
+
+def run_extras(args, dev, stream):
+    """The other configurations, each on its own (an extra that fails is recorded as such and
+    cannot lose the headline line)."""
+    import copy
+
+    import torch
+
+    extras = {}
+
+    def guarded(name, fn):
+        try:
+            extras[name] = fn()
+        except Exception as exc:  # noqa: BLE001
+            extras[name] = {"error": repr(exc)}
+        torch.cuda.empty_cache()
+
+    def cube4():
         # the small FP64 workload: plain method (FP64 assembly, FP64 block-Jacobi PCG, no coarse space)
-        import copy
         a1 = copy.copy(args)
         a1.asm, a1.solve, a1.coarse = "fp64", "fp64", False
         W1 = Workload("cube4_k1", dev, stream)
         r1 = run_workload(W1, a1, stream, dev, 1, full=False)
-        extras["cube4_k1"] = {
-            "workload": f"cube4_k1: unit cube 4^3x6 Kuhn tets ({r1['nelt']} elements), k=1, kappa=c=tau=1, Dirichlet "
-                        "everywhere, u = sin sin sin; FP64 assembly and FP64 block-Jacobi PCG to 1e-10 (plain method)",
-            **{k: r1[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step", "gpu_launches")}}
         W1.M.close()
-        del W1
+        return {"workload": f"cube4_k1: unit cube 4^3x6 Kuhn tets ({r1['nelt']} elements), k=1, kappa=c=tau=1, "
+                            "Dirichlet everywhere, u = sin sin sin; FP64 assembly and FP64 block-Jacobi PCG to 1e-10 "
+                            "(plain method)",
+                **{k: r1[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step", "gpu_launches")}}
+
+    def cube16():
         W2 = Workload(EXTRA_RD, dev, stream)
         r2 = run_workload(W2, args, stream, dev, 1, full=True)
-        extras[EXTRA_RD] = {
-            "workload": f"{EXTRA_RD}: unit cube 16^3x6 Kuhn tets ({r2['nelt']} elements), k=3, variable kappa and c, "
-                        "Dirichlet x=0,1 + Neumann elsewhere (reaction-diffusion, CG)",
-            **{k: r2[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step", "solve_time_to_1e-10",
-                                  "superconvergence", "e2e", "roofline", "solve_roofline", "gpu_launches")}}
         W2.M.close()
-        del W2
-        torch.cuda.empty_cache()
-        try:
-            extras["symmetric_rule"] = run_rule_comparison(dev, stream)
-        except Exception as exc:  # noqa: BLE001
-            extras["symmetric_rule"] = {"error": repr(exc)}
-        try:
-            extras["batch_64"] = run_batch(args)
-        except Exception as exc:  # noqa: BLE001 -- an extra must not lose the headline line
-            extras["batch_64"] = {"error": repr(exc)}
-        torch.cuda.empty_cache()
-        try:
-            extras["cube32_k2_grf_learned"] = run_learned(args, train=args.extra_learned_train,
-                                                          evaluate=args.extra_learned_eval, bj_eval=1,
-                                                          epochs=args.learned_epochs)
-        except Exception as exc:  # noqa: BLE001
-            extras["cube32_k2_grf_learned"] = {"error": repr(exc)}
-        out["extras"] = extras
-    return out
+        return {"workload": f"{EXTRA_RD}: unit cube 16^3x6 Kuhn tets ({r2['nelt']} elements), k=3, variable kappa and "
+                            "c, Dirichlet x=0,1 + Neumann elsewhere (reaction-diffusion, CG)",
+                **{k: r2[k] for k in ("value", "phases_ms", "iterations_per_step", "ms_per_step", "solve_time_to_1e-10",
+                                      "superconvergence", "e2e", "roofline", "solve_roofline", "gpu_launches",
+                                      "inner_rtol")}}
+
+    guarded("cube4_k1", cube4)
+    guarded(EXTRA_RD, cube16)
+    guarded("symmetric_rule", lambda: run_rule_comparison(dev, stream))
+    guarded("batch_64", lambda: run_batch(args))
+    guarded("cube32_k2_grf_learned", lambda: run_learned(args, train=args.extra_learned_train,
+                                                         evaluate=args.extra_learned_eval, bj_eval=1,
+                                                         epochs=args.learned_epochs))
+    return extras
+
 
 
 def profile_k1(name, s_sub, launches=2, asm="df32", autotune=True):
@@ -984,6 +1038,8 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
     ap.add_argument("--profile-workload", default=HEADLINE)
+    ap.add_argument("--profile-tc", type=int, default=0,
+                    help="run the tensor-core mass contraction twice on an s^3 x 6 mesh and exit")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned guess and exit")
     ap.add_argument("--learned-train", type=int, default=2000)
     ap.add_argument("--learned-eval", type=int, default=200)
@@ -994,6 +1050,15 @@ def main():
     args = ap.parse_args()
     if args.profile_k1:
         profile_k1(args.profile_workload, args.profile_k1, asm=args.asm)
+        return
+    if args.profile_tc:
+        import torch
+
+        from paper_1305_1489_gb300 import build
+        build()
+        W = Workload(args.profile_workload, torch.device("cuda", 0), torch.cuda.current_stream(), s=args.profile_tc)
+        print(json.dumps({"profile_tc": {"nelt": W.M.nelt, **h2_contraction(W, torch.device("cuda", 0),
+                                                                           torch.cuda.current_stream(), reps=1)}}))
         return
     if args.only_steps:
         import torch

@@ -261,6 +261,18 @@ int hdg_nn_mse(int64_t n, const float* pred, const float* target, float* grad,
                float* loss_partial, void* stream);
 int hdg_nn_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1,
                 float b2, float eps, int step, void* stream);
+/* Normalisation of the training targets T [M][N] (device f64, row-major):
+ * hdg_nn_colstats: mean[j] = (1/M) sum_i T[i][j], scale[j] = the population standard deviation
+ *   of column j, or 1 where it is 0 (device f64 [N] outputs);
+ * hdg_nn_standardize: out[i][j] = (T[i][j] - mean[j]) / scale[j] (device f32 [M][N]);
+ * hdg_nn_fold_affine: the last layer y = W x + b (W [Nout][Nin], b [Nout], device f32) trained on
+ *   standardised targets becomes W <- diag(scale) W, b <- scale o b + mean, so that it returns
+ *   the targets themselves.                                                                 */
+int hdg_nn_colstats(int64_t M, int N, const double* T, double* mean, double* scale, void* stream);
+int hdg_nn_standardize(int64_t M, int N, const double* T, const double* mean, const double* scale, float* out,
+                       void* stream);
+int hdg_nn_fold_affine(int Nout, int Nin, float* W, float* b, const double* mean, const double* scale,
+                       void* stream);
 
 /* ------------------------------------------------------------------ two-level preconditioner
  * (not in the paper, which solves eq. 6.5 directly).  With a coarse space set, the PCG of

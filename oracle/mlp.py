@@ -60,3 +60,18 @@ def adam_step(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mhat = m / (1.0 - b1 ** step)
     vhat = v / (1.0 - b2 ** step)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def standardize(T):
+    """Column statistics of the training targets T [M, N]: mean, scale (population standard
+    deviation, 1 for a column with zero spread) and the standardised targets (T - mean) / scale."""
+    mean = T.mean(axis=0)
+    sd = np.sqrt(((T - mean) ** 2).mean(axis=0))
+    scale = np.where(sd > 0, sd, 1.0)
+    return mean, scale, (T - mean) / scale
+
+
+def fold_affine(W, b, mean, scale):
+    """The last layer y = W x + b trained on standardised targets, rewritten to return the
+    targets: W' = diag(scale) W, b' = scale * b + mean."""
+    return W * scale[:, None], b * scale + mean

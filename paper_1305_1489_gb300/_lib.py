@@ -65,6 +65,9 @@ _SIGS = {
     "hdg_nn_colsum": [C.c_int, C.c_int, P, P, P],
     "hdg_nn_mse": [I64, P, P, P, P, P],
     "hdg_nn_adam": [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P],
+    "hdg_nn_colstats": [I64, C.c_int, P, P, P, P],
+    "hdg_nn_standardize": [I64, C.c_int, P, P, P, P, P],
+    "hdg_nn_fold_affine": [C.c_int, C.c_int, P, P, P, P, P],
     "hdg_set_coarse_space": [P, C.c_int, P, P, P],
     "hdg_autotune": [P, P],
     "hdg_coarse_precond_apply": [P, P, P],

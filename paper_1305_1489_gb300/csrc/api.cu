@@ -68,7 +68,8 @@ static int upload_tables(hdg_mesh* M) {
       (rc = upload(&D.sfCC_df, split_df(T.sfCC))) || (rc = upload(&D.sfp2to1, T.sfp2to1)) ||
       (rc = upload(&D.sfp3to2, T.sfp3to2)) || (rc = upload(&D.G1_df, split_df(T.G1))) ||
       (rc = upload(&D.Shat1_df, split_df(T.Shat1))) || (rc = upload(&D.Pd_df, split_df(T.Pd))) ||
-      (rc = upload(&D.Pl_df, split_df(T.Pl))) || (rc = upload(&D.Dmu_df, split_df(T.Dmu))))
+      (rc = upload(&D.Pl_df, split_df(T.Pl))) || (rc = upload(&D.Dmu_df, split_df(T.Dmu))) ||
+      (rc = upload(&D.vol_w_df, split_df(T.vol_w))) || (rc = upload(&D.face_w_df, split_df(T.face_w))))
     return rc;
   if ((rc = upload(&D.pairs_n, pair_list(T.n, 0))) || (rc = upload(&D.pairs_m, pair_list(T.m, 0))) ||
       (rc = upload(&D.pairs_n1, pair_list(T.n1, 1))))
@@ -81,7 +82,8 @@ static void free_tables(hdg_mesh* M) {
   DevTables& D = M->dt;
   void* ptrs[] = {D.P, D.Pd, D.Chat, D.S, D.E, D.vol_w, D.lam, D.face_w, D.xi, D.D, D.P1, D.G1, D.Shat1, D.pairs_n,
                   D.pairs_m, D.pairs_n1, D.Pl, D.Dmu, D.face_pts, D.P_df, D.Chat_df, D.S_df, D.E_df, D.sfAA_df,
-                  D.sfBB_df, D.sfCC_df, D.sfp2to1, D.sfp3to2, D.G1_df, D.Shat1_df, D.Pd_df, D.Pl_df, D.Dmu_df};
+                  D.sfBB_df, D.sfCC_df, D.sfp2to1, D.sfp3to2, D.G1_df, D.Shat1_df, D.Pd_df, D.Pl_df, D.Dmu_df,
+                  D.vol_w_df, D.face_w_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   D = DevTables();
@@ -89,15 +91,11 @@ static void free_tables(hdg_mesh* M) {
 
 static void release(hdg_mesh* M) {
   coarse_free(M);
+  free_tables(M);
   void* ptrs[] = {M->d_vx, M->d_geo, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
                   M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
-                  M->d_p32, M->d_q32, M->dt.P, M->dt.Pd, M->dt.Chat, M->dt.S, M->dt.E, M->dt.vol_w, M->dt.lam,
-                  M->dt.face_w, M->dt.xi, M->dt.D, M->dt.P1, M->dt.G1, M->dt.Shat1, M->dt.pairs_n,
-                  M->dt.pairs_m, M->dt.pairs_n1, M->dt.Pl, M->dt.Dmu, M->dt.face_pts, M->d_bicg,
-                  M->dt.P_df, M->dt.Chat_df, M->dt.S_df, M->dt.E_df, M->d_fverts, M->d_Tproj,
-                  M->dt.sfAA_df, M->dt.sfBB_df, M->dt.sfCC_df, M->dt.sfp2to1, M->dt.sfp3to2, M->d_norm,
-                  M->dt.G1_df, M->dt.Shat1_df, M->dt.Pd_df, M->dt.Pl_df, M->dt.Dmu_df, M->d_bicg32};
+                  M->d_p32, M->d_q32, M->d_bicg, M->d_fverts, M->d_Tproj, M->d_norm, M->d_bicg32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);

@@ -33,6 +33,7 @@ struct AsmDfArgs {
   const double *beta_q, *beta_f;  // convection: [3][nelt][nq], [3][nelt][4][nf] (FP64)
   const df *Pd, *Pl, *Dmu;        // convection: reference gradients, face traces, face bases
   const double* wf;               // face weights varpi_r
+  const df *w_df, *wf_df;         // volume and face weights as double-float pairs
   const int16_t *p2to1, *p3to2;
   const double* w;
   const int16_t *pairs_n, *pairs_m;
@@ -190,8 +191,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   df* Gq = smd + SM::o_Gq;
   df* bn = smd + SM::o_bn;
   df* aDD = smd + SM::o_aDD;
-  __shared__ df s_a[3][3], s_nrm[4][3], s_T[4], s_nn[4][4];
-  __shared__ double s_geo[25], s_vol;  // a (9), nrm (12), area (4) in FP64
+  __shared__ df s_a[3][3], s_nrm[4][3], s_T[4], s_nn[4][4], s_vol;
   __shared__ df invdM[n], invdS[n];
   __shared__ int s_perm[4];
   __shared__ int s_bad, s_coef;
@@ -200,61 +200,91 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
   const int lane = tid & 31, warp = tid >> 5;
   const int64_t Ke = blockIdx.x;
 
-  // the element's geometry (formed once per mesh by geometry_kernel), one value per thread
-  if (tid < 25) s_geo[tid] = __ldg(A.geo + Ke * kGeoStride + tid);
-  if (tid == 25) s_vol = __ldg(A.geo + Ke * kGeoStride + 25);
-  if (tid < 4) s_perm[tid] = A.perm[Ke * 4 + tid] - 1;
-  if (tid == 0) {
-    s_bad = 0;
-    s_coef = 0;
+  // this thread's coefficient loads of the next phase, issued before the first barrier so that
+  // they overlap the geometry loads (tasks t = tid, tid + NT: kappa, c, f at node t; with
+  // convection beta at volume node t - nq, then beta at face node t - 2 nq)
+  constexpr int NTASK = CONV ? 2 * nq + 4 * nf : nq;
+  constexpr int NPRE = (NTASK + NT - 1) / NT;
+  double pre[NPRE][3];
+#pragma unroll
+  for (int i = 0; i < NPRE; ++i) {
+    const int t = tid + i * NT;
+    pre[i][0] = pre[i][1] = pre[i][2] = 0.0;
+    if (t < nq) {
+      pre[i][0] = __ldg(A.kappa + Ke * nq + t);
+      pre[i][1] = __ldg(A.c + Ke * nq + t);
+      pre[i][2] = __ldg(A.f + Ke * nq + t);
+    } else if (CONV && t < 2 * nq) {
+#pragma unroll
+      for (int st = 0; st < 3; ++st) pre[i][st] = __ldg(A.beta_q + ((int64_t)st * A.nelt + Ke) * nq + (t - nq));
+    } else if (CONV && t < NTASK) {
+#pragma unroll
+      for (int st = 0; st < 3; ++st) pre[i][st] = __ldg(A.beta_f + ((int64_t)st * A.nelt + Ke) * 4 * nf + (t - 2 * nq));
+    }
   }
-  __syncthreads();
 
-  // the geometry in double-float, one value per thread (FP64 work off the single-thread path)
+  // the element's geometry (formed once per mesh by geometry_kernel) in double-float, one
+  // value per thread: cofactors a (9), normals (12), T_l = tau_l |e_l| (4), the volume
   if (tid < 21) {
-    const df v = df_from_double(s_geo[tid]);
+    const df v = df_from_double(__ldg(A.geo + Ke * kGeoStride + tid));
     if (tid < 9) s_a[tid / 3][tid % 3] = v;
     else s_nrm[(tid - 9) / 3][(tid - 9) % 3] = v;
   } else if (tid < 25) {
     const int l = tid - 21;
     const double tau = A.nu < n ? 0.0 : A.tau ? A.tau[Ke * 4 + l] : 1.0;
-    s_T[l] = df_from_double(tau * s_geo[21 + l]);  // T_l = tau_l |e_l|, eq. 4.22 (0 for BDM)
-  } else if (tid < 41) {
-    const double* x = s_geo + 9 + 3 * ((tid - 25) / 4);
-    const double* y = s_geo + 9 + 3 * ((tid - 25) % 4);
-    s_nn[(tid - 25) / 4][(tid - 25) % 4] = df_from_double(x[0] * y[0] + x[1] * y[1] + x[2] * y[2]);
+    s_T[l] = df_from_double(tau * __ldg(A.geo + Ke * kGeoStride + tid));  // eq. 4.22 (0 for BDM)
+  } else if (tid == 25) {
+    s_vol = df_from_double(__ldg(A.geo + Ke * kGeoStride + 25));
+  } else if (tid < 30) {
+    s_perm[tid - 26] = A.perm[Ke * 4 + tid - 26] - 1;
+  } else if (tid == 30) {
+    s_bad = 0;
+    s_coef = 0;
+  }
+  __syncthreads();
+  if (tid < 16) {  // n_l . n_l'
+    const int a = tid / 4, b = tid % 4;
+    dacc s = dacc_zero();
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dacc_mac(s, s_nrm[a][d], s_nrm[b][d]);
+    s_nn[a][b] = dacc_result(s);
   }
 
   // coefficients weighted by |K| omega_q; with convection also the volume weights bw and the
-  // face weights bn, each task on its own thread.  The reciprocal of kappa is a double-float
-  // Newton step on the FP32 pipe (no FP64 division).
-  constexpr int NTASK = CONV ? 2 * nq + 4 * nf : nq;
-  for (int t = tid; t < NTASK; t += NT) {
+  // face weights bn, each task on its own thread, in double-float arithmetic (the FP64 values
+  // are only converted; the reciprocal of kappa is a Newton step on the FP32 pipe).
+#pragma unroll
+  for (int ip = 0; ip < NPRE; ++ip) {
+    const int t = tid + ip * NT;
+    if (t >= NTASK) break;
     if (t < nq) {
       const int q = t;
-      const double kap = A.kappa[Ke * nq + q], cc = A.c[Ke * nq + q], ff = A.f[Ke * nq + q];
+      const double kap = pre[ip][0], cc = pre[ip][1], ff = pre[ip][2];
       if (!(kap > 0.0) || !(cc >= 0.0) || !isfinite(kap) || !isfinite(cc) || !isfinite(ff)) s_coef = 1;
-      const df vw = df_from_double(s_vol * A.w[q]);
+      const df vw = df_mul(s_vol, ldg_df(A.w_df + q));
       kw[q] = df_mul(vw, df_recip(kap > 0.0 ? df_from_double(kap) : df_make(1.f, 0.f)));
       cw[q] = df_mul(vw, df_from_double(cc));
       fw[q] = df_mul(vw, df_from_double(ff));
     } else if (t < 2 * nq) {
       // bw_#(q) = -(omega_q / 6) sum_* a_{*#} beta_*(p_q)  (B_c = sum_q sum_# bw P_qj dhat_# P_qi)
       const int q = t - nq;
-      const double b0 = A.beta_q[(0 * A.nelt + Ke) * nq + q], b1 = A.beta_q[(1 * A.nelt + Ke) * nq + q],
-                   b2 = A.beta_q[(2 * A.nelt + Ke) * nq + q];
-      const double sc = -A.w[q] / 6.0;
+      const df b0 = df_from_double(pre[ip][0]), b1 = df_from_double(pre[ip][1]), b2 = df_from_double(pre[ip][2]);
+      const df sc = df_mul(ldg_df(A.w_df + q), df_from_double(-1.0 / 6.0));
 #pragma unroll
-      for (int h = 0; h < 3; ++h)
-        bw[h * nq + q] = df_from_double(sc * (s_geo[h] * b0 + s_geo[3 + h] * b1 + s_geo[6 + h] * b2));
+      for (int h = 0; h < 3; ++h) {
+        dacc a = dacc_zero();
+        dacc_mac(a, s_a[0][h], b0);
+        dacc_mac(a, s_a[1][h], b1);
+        dacc_mac(a, s_a[2][h], b2);
+        bw[h * nq + q] = df_mul(sc, dacc_result(a));
+      }
     } else {
       // varpi_r beta(x_{r,l}^K) . n_l at the element's face nodes
       const int u = t - 2 * nq, fl = u / nf, r = u - fl * nf;
-      const double* nl = s_geo + 9 + 3 * fl;
-      double acc = 0.0;
+      dacc acc = dacc_zero();
 #pragma unroll
-      for (int st = 0; st < 3; ++st) acc = fma(A.beta_f[((int64_t)st * A.nelt + Ke) * 4 * nf + u], nl[st], acc);
-      bn[u] = df_from_double(A.wf[r] * acc);
+      for (int st = 0; st < 3; ++st) dacc_mac(acc, s_nrm[fl][st], df_from_double(pre[ip][st]));
+      bn[u] = df_mul(ldg_df(A.wf_df + r), dacc_result(acc));
     }
   }
   __syncthreads();
@@ -688,6 +718,8 @@ cudaError_t launch_assemble_df(hdg_mesh* M) {
   a.Pl = reinterpret_cast<const df*>(M->dt.Pl_df);
   a.Dmu = reinterpret_cast<const df*>(M->dt.Dmu_df);
   a.wf = M->dt.face_w;
+  a.w_df = reinterpret_cast<const df*>(M->dt.vol_w_df);
+  a.wf_df = reinterpret_cast<const df*>(M->dt.face_w_df);
   a.w = M->dt.vol_w;
   a.pairs_n = M->dt.pairs_n;
   a.pairs_m = M->dt.pairs_m;

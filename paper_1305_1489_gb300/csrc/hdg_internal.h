@@ -63,6 +63,7 @@ struct DevTables {
   float *sfAA_df = nullptr, *sfBB_df = nullptr, *sfCC_df = nullptr;  // sum-factorisation tables
   float *G1_df = nullptr, *Shat1_df = nullptr;  // double-float postprocess tables
   float *Pd_df = nullptr, *Pl_df = nullptr, *Dmu_df = nullptr;  // double-float convection tables
+  float *vol_w_df = nullptr, *face_w_df = nullptr;  // double-float quadrature weights
   int16_t *sfp2to1 = nullptr, *sfp3to2 = nullptr;
   int16_t* pairs_n = nullptr;   // [n(n+1)/2][2]  (i <= j) pairs of P_k(K) indices
   int16_t* pairs_m = nullptr;   // [m(m+1)/2][2]  (r <= s) pairs of R_k(dK) indices

@@ -266,7 +266,70 @@ static double host_dot(hdg_mesh* M, const double* x, const double* y, int64_t n,
   return s;
 }
 
+// Target normalisation of the network's training (column statistics of the target matrix),
+// and its fold into the last layer after training.  A column with zero spread keeps the scale
+// 1, so its standardised values are 0 and the fold returns its mean.
+__global__ void nn_colstats_kernel(int64_t M, int N, const double* __restrict__ T, double* mean, double* scale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double s = 0.0;
+  for (int64_t i = 0; i < M; ++i) s += T[i * N + j];
+  const double mu = s / (double)M;
+  double v = 0.0;
+  for (int64_t i = 0; i < M; ++i) {
+    const double d = T[i * N + j] - mu;
+    v = fma(d, d, v);
+  }
+  const double sd = sqrt(v / (double)M);
+  mean[j] = mu;
+  scale[j] = sd > 0.0 ? sd : 1.0;
+}
+
+__global__ void nn_standardize_kernel(int64_t M, int N, const double* __restrict__ T, const double* __restrict__ mean,
+                                      const double* __restrict__ scale, float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * N) return;
+  const int j = (int)(t % N);
+  out[t] = (float)((T[t] - mean[j]) / scale[j]);
+}
+
+// last layer y = W x + b on standardised targets -> y' = diag(scale) y + mean
+__global__ void nn_fold_affine_kernel(int Nout, int Nin, float* W, float* b, const double* __restrict__ mean,
+                                      const double* __restrict__ scale) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)Nout * Nin) {
+    const int i = (int)(t / Nin);
+    W[t] = (float)((double)W[t] * scale[i]);
+  }
+  if (t < Nout) b[t] = (float)fma((double)b[t], scale[t], mean[t]);
+}
+
 extern "C" {
+
+int hdg_nn_colstats(int64_t M, int N, const double* T, double* mean, double* scale, void* stream) {
+  if (M < 1 || N < 1 || !T || !mean || !scale) return fail(HDG_ERR_ARG, "bad nn_colstats arguments");
+  nn_colstats_kernel<<<(N + 127) / 128, 128, 0, (cudaStream_t)stream>>>(M, N, T, mean, scale);
+  HDG_CUDA_TRY(cudaGetLastError());
+  return HDG_OK;
+}
+
+int hdg_nn_standardize(int64_t M, int N, const double* T, const double* mean, const double* scale, float* out,
+                       void* stream) {
+  if (M < 1 || N < 1 || !T || !mean || !scale || !out) return fail(HDG_ERR_ARG, "bad nn_standardize arguments");
+  const int64_t tot = M * N;
+  nn_standardize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(M, N, T, mean, scale, out);
+  HDG_CUDA_TRY(cudaGetLastError());
+  return HDG_OK;
+}
+
+int hdg_nn_fold_affine(int Nout, int Nin, float* W, float* b, const double* mean, const double* scale,
+                       void* stream) {
+  if (Nout < 1 || Nin < 1 || !W || !b || !mean || !scale) return fail(HDG_ERR_ARG, "bad nn_fold_affine arguments");
+  const int64_t tot = (int64_t)Nout * Nin;
+  nn_fold_affine_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(Nout, Nin, W, b, mean, scale);
+  HDG_CUDA_TRY(cudaGetLastError());
+  return HDG_OK;
+}
 
 int hdg_prolong(hdg_mesh* M, const int32_t* nodes, const double* weights, const double* coarse, double* uhat) {
   if (!M || !nodes || !weights || !coarse || !uhat) return fail(HDG_ERR_ARG, "NULL argument");

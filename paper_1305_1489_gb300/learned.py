@@ -232,9 +232,16 @@ class LearnedGuess:
     # -- training (all arithmetic in the hdg_nn_* kernels)
     def fit(self, A, T, epochs=200, batch=64, lr=1e-3, seed=0):
         import torch
-        self.mean = T.mean(axis=0)
-        self.std = T.std(axis=0) + 1e-12 * (np.abs(self.mean).max() + 1e-300)
-        Tn = (T - self.mean) / self.std
+        lib = _lib.load()
+        st = C.c_void_p(self.net.stream)
+        M, N = T.shape
+        Td64 = torch.from_numpy(np.ascontiguousarray(T, np.float64)).cuda()
+        self.mean = torch.empty(N, dtype=torch.float64, device="cuda")
+        self.std = torch.empty(N, dtype=torch.float64, device="cuda")
+        _lib.check(lib.hdg_nn_colstats(M, N, _p(Td64), _p(self.mean), _p(self.std), st))
+        Tn32 = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        _lib.check(lib.hdg_nn_standardize(M, N, _p(Td64), _p(self.mean), _p(self.std), _p(Tn32), st))
+        Tn = Tn32.cpu().numpy()
         rng = np.random.default_rng(seed)
         n = len(A)
         nb = max(1, n // batch)
@@ -251,7 +258,8 @@ class LearnedGuess:
         return self.history
 
     def predict(self, amps):
-        """c = mean + std * phi(xi) as FP64 device [nc]."""
+        """c = phi(xi) as FP64 device [nc] (the target normalisation folded into the last
+        layer by fold_normalisation)."""
         import torch
         x = self.features(amps)[None, :]
         y, _ = self.net.forward(x)
@@ -260,15 +268,14 @@ class LearnedGuess:
         return yd
 
     def fold_normalisation(self):
-        """Fold the target normalisation into the last layer so phi(xi) is c itself."""
+        """Fold the target normalisation into the last layer (hdg_nn_fold_affine) so phi(xi)
+        is c itself."""
         import torch
         W, b = self.net.params[-2], self.net.params[-1]
-        Wn = W.double().cpu().numpy() * self.std[:, None]
-        bn = b.double().cpu().numpy() * self.std + self.mean
-        W.copy_(torch.from_numpy(Wn.astype(np.float32)))
-        b.copy_(torch.from_numpy(bn.astype(np.float32)))
-        self.mean = np.zeros_like(self.mean)
-        self.std = np.ones_like(self.std)
+        _lib.check(_lib.load().hdg_nn_fold_affine(W.shape[0], W.shape[1], _p(W), _p(b), _p(self.mean), _p(self.std),
+                                                  C.c_void_p(self.net.stream)))
+        self.mean = torch.zeros_like(self.mean)
+        self.std = torch.ones_like(self.std)
 
     def guess(self, amps):
         """x0 = alpha Pi phi(xi) (after set_field).  Returns (x0, alpha)."""

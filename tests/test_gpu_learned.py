@@ -69,6 +69,34 @@ def test_adam_step_matches_oracle():
         assert np.abs(p.double().cpu().numpy() - r).max() < 1e-5
 
 
+def test_target_normalisation_kernels_match_oracle():
+    """hdg_nn_colstats / hdg_nn_standardize / hdg_nn_fold_affine against oracle/mlp.py: FP64
+    statistics to 1e-13, the FP32 standardised targets and folded layer to FP32 rounding."""
+    import ctypes as C
+    from paper_1305_1489_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(11)
+    M, N, Nin = 37, 129, 20
+    T = rng.normal(0.5, 3.0, size=(M, N))
+    T[:, 5] = -2.25  # a column with zero spread
+    mean, scale, Tn = omlp.standardize(T)
+    Td = torch.from_numpy(T).cuda()
+    mg = torch.empty(N, dtype=torch.float64, device="cuda")
+    sg = torch.empty(N, dtype=torch.float64, device="cuda")
+    out = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.hdg_nn_colstats(M, N, Td.data_ptr(), mg.data_ptr(), sg.data_ptr(), st) == 0
+    assert lib.hdg_nn_standardize(M, N, Td.data_ptr(), mg.data_ptr(), sg.data_ptr(), out.data_ptr(), st) == 0
+    assert rel(mg.cpu().numpy(), mean) < 1e-13 and rel(sg.cpu().numpy(), scale) < 1e-13
+    assert np.abs(out.cpu().numpy() - Tn).max() < 4e-7 * np.abs(Tn).max()
+    W = rng.normal(size=(N, Nin)).astype(np.float32)
+    b = rng.normal(size=N).astype(np.float32)
+    Wf, bf = omlp.fold_affine(W.astype(np.float64), b.astype(np.float64), mean, scale)
+    Wg, bg = _f32(W), _f32(b)
+    assert lib.hdg_nn_fold_affine(N, Nin, Wg.data_ptr(), bg.data_ptr(), mg.data_ptr(), sg.data_ptr(), st) == 0
+    assert rel(Wg.cpu().numpy(), Wf) < 1e-7 and rel(bg.cpu().numpy(), bf) < 1e-7
+
+
 def test_fourier_field_matches_definition():
     from paper_1305_1489_gb300.learned import fourier_field
     rng = np.random.default_rng(0)

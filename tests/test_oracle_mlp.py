@@ -70,3 +70,20 @@ def test_adam_first_step_is_signed_lr():
     p, m, v = mlp.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.1)
     assert np.allclose(p, -0.1 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_standardize_and_fold_closed_forms():
+    """Standardised columns have mean 0 and population standard deviation 1 (a constant column
+    becomes 0), and the folded layer returns scale * (W x + b) + mean for any x."""
+    rng = np.random.default_rng(5)
+    T = rng.normal(3.0, 2.0, size=(40, 6))
+    T[:, 2] = 7.5
+    mean, scale, Tn = mlp.standardize(T)
+    assert np.allclose(Tn.mean(axis=0), 0.0, atol=1e-14)
+    sd = Tn.std(axis=0)
+    assert np.allclose(np.delete(sd, 2), 1.0, atol=1e-14) and np.all(Tn[:, 2] == 0.0)
+    assert scale[2] == 1.0 and mean[2] == 7.5
+    W, b = rng.normal(size=(6, 4)), rng.normal(size=6)
+    Wf, bf = mlp.fold_affine(W, b, mean, scale)
+    x = rng.normal(size=4)
+    assert np.allclose(Wf @ x + bf, scale * (W @ x + b) + mean, rtol=1e-14, atol=1e-14)
