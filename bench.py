@@ -62,8 +62,8 @@ HBM_FALLBACK_GBS = 6800.0
 # to it), valid while the kernel's sources (K1_SOURCES, hashed together) are unchanged.
 K1_TRAFFIC = {
     ("cube48_k2_conv", "assemble_df.cu"): {
-        "sha256": "05e66ac6bb50600708b77d26bb70b8a5d36cfbf90bfe0733a897bb511faeb27e",
-        "bytes_per_element": (120068096 + 237978880) / 24576,
+        "sha256": "f5d739493d422070eb4338af9d0d172d2c73913e696e39886c68d36ed7b7d1c7",
+        "bytes_per_element": (120094464 + 237344000) / 24576,
         "captured": "ncu --set full of the same kernel on the 16^3 x 6 mesh of the workload (24,576 elements), "
                     "profiles/assemble_df_kernel_conv_k2_cube16.md"},
     ("cube16_k3", "assemble_df.cu"): {"sha256": None, "bytes_per_element": None, "captured": None},
@@ -920,7 +920,7 @@ def run_gpu(args, rank, world, local_rank):
         "phases_ms": r["phases_ms"], "iterations_per_step": r["iterations_per_step"],
         "solve_time_to_1e-10": r["solve_time_to_1e-10"], "superconvergence": r["superconvergence"],
         "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "roofline": r["roofline"],
-        "solve_roofline": r["solve_roofline"], "wall_s_timed": r["wall_s_timed"],
+        "solve_roofline": r["solve_roofline"], "h2_contraction": r["h2_contraction"], "wall_s_timed": r["wall_s_timed"],
     }
     if world == 1 and rank == 0 and args.extras:
         out["extras"] = run_extras(args, dev, stream)

@@ -288,8 +288,8 @@ int hdg_nn_fold_affine(int Nout, int Nin, float* W, float* b, const double* mean
  *   l < nlev-1, the level-(l+1) nodes and weights interpolating it.  Node -1 = unused entry.
  *   Copied; nlev = 0 removes the coarse space.  Every element may touch at most 8 level-0
  *   nodes (HDG_ERR_UNSUPPORTED).  Invalid sizes or nodes: HDG_ERR_ARG.
- * hdg_coarse_precond_apply: z = M^-1 r for device f64 [nfc][d2] vectors (Dirichlet entries
- *   of r ignored; tests and inspection).                                                   */
+ * hdg_coarse_precond_apply: z = M^-1 r for device f64 [nfc][d2] vectors starting on 16-byte
+ *   boundaries (HDG_ERR_ARG otherwise; Dirichlet entries of r ignored; tests and inspection). */
 int hdg_set_coarse_space(hdg_mesh* mesh, int nlev, const int64_t* sizes, const int32_t* nodes,
                          const double* weights);
 int hdg_coarse_precond_apply(hdg_mesh* mesh, const double* r, double* z);

@@ -17,6 +17,7 @@
 // batches of iterations are captured in a CUDA graph and the host reads the convergence flag
 // after each replay.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <vector>
 
@@ -200,14 +201,28 @@ __device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __rest
   }
 }
 
+// row a of face e's block inverse times the face's d2 residual entries; for even d2 the rows
+// and the face's entries start on 2-element boundaries, so they are read as pairs
 template <typename T, int D2>
 __device__ __forceinline__ T bj_apply(const T* __restrict__ Binv, const T* __restrict__ r, int64_t e, int a) {
   T s0 = (T)0, s1 = (T)0;
   const T* Bi = Binv + (e * D2 + a) * D2;
   const T* re = r + e * D2;
+  if constexpr (D2 % 2 == 0) {
+    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const V2* Bv = reinterpret_cast<const V2*>(Bi);
+    const V2* rv = reinterpret_cast<const V2*>(re);
 #pragma unroll
-  for (int b = 0; b < D2; ++b) {
-    if (b & 1) s1 = fma(Bi[b], re[b], s1); else s0 = fma(Bi[b], re[b], s0);
+    for (int b = 0; b < D2 / 2; ++b) {
+      const V2 bb = Bv[b], xx = rv[b];
+      s0 = fma((T)bb.x, (T)xx.x, s0);
+      s1 = fma((T)bb.y, (T)xx.y, s1);
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < D2; ++b) {
+      if (b & 1) s1 = fma(Bi[b], re[b], s1); else s0 = fma(Bi[b], re[b], s0);
+    }
   }
   return s0 + s1;
 }
@@ -945,10 +960,12 @@ template <typename T, int D2>
 static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStream_t st, const double* done) {
   Coarse* c = M->coarse;
   const int G = grid_levels(c);
-  const int64_t cap = M->grid_cap > 0 ? std::min<int64_t>(M->grid_cap, kMaxBlocks) : kMaxBlocks;
+  // one pass over every node or row (the level kernels loop when the grid is capped, as the
+  // tests do with HDG_FACE_BLOCKS to exercise those loops)
+  const int64_t cap = M->grid_cap > 0 ? std::min<int64_t>(M->grid_cap, kMaxBlocks) : (int64_t)65535;
   auto grid = [cap](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, cap); };
   auto rows = [cap](int64_t n) { return (int)std::min<int64_t>((n * kRowLanes + 255) / 256, cap); };
-  const int gr = (int)std::min<int64_t>({(c->lv[0].n + 7) / 8, (int64_t)152 * 16, cap});  // one warp per node
+  const int gr = (int)std::min<int64_t>((c->lv[0].n + 7) / 8, cap);  // one warp per node
   restrict_gather_kernel<T, D2><<<gr, 256, 0, st>>>(CA, r, done);
   level_down_kernel<true><<<rows(c->lv[0].n), 256, 0, st>>>(c->lv[0], c->rc, done);
   for (int l = 1; l < G; ++l) {
@@ -1954,6 +1971,8 @@ int autotune_face_grid(hdg_mesh* M, hdg_tuning* out) {
 
 int coarse_precond_apply(hdg_mesh* M, const double* r, double* z) {
   if (!M->assembled) return fail(HDG_ERR_STATE, "preconditioner before hdg_assemble_condense");
+  if ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(z)) % 16 != 0)
+    return fail(HDG_ERR_ARG, "r and z must start on 16-byte boundaries");
   if (!M->coarse) return fail(HDG_ERR_STATE, "no coarse space: call hdg_set_coarse_space first");
   switch (M->tab.d2) {
     case 1: return Solver<1>::precond_apply(M, r, z);
