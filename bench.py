@@ -62,14 +62,18 @@ HBM_FALLBACK_GBS = 6800.0
 # to it), valid while the kernel's sources (K1_SOURCES, hashed together) are unchanged.
 K1_TRAFFIC = {
     ("cube48_k2_conv", "assemble_df.cu"): {
-        "sha256": "f5d739493d422070eb4338af9d0d172d2c73913e696e39886c68d36ed7b7d1c7",
-        "bytes_per_element": (120094464 + 237344000) / 24576,
-        "captured": "ncu --set full of the same kernel on the 16^3 x 6 mesh of the workload (24,576 elements), "
-                    "profiles/assemble_df_kernel_conv_k2_cube16.md"},
-    ("cube16_k3", "assemble_df.cu"): {"sha256": None, "bytes_per_element": None, "captured": None},
+        "sha256": "e5dc7d42c71f777b0a1992e1c310ab466626b7a5d70b19614a2a0c29702ff7e9",
+        "bytes_per_element": (120072704 + 237390592) / 24576,
+        "captured": "ncu dram__bytes_read/write of the same kernel on the 16^3 x 6 mesh of the workload (24,576 "
+                    "elements), profiles/assemble_df_kernel_conv_k2_cube16.md"},
+    ("cube16_k3", "assemble_df.cu"): {
+        "sha256": "e5dc7d42c71f777b0a1992e1c310ab466626b7a5d70b19614a2a0c29702ff7e9",
+        "bytes_per_element": (79970304 + 901217280) / 24576,
+        "captured": "ncu dram__bytes_read/write of the same kernel on the workload's own mesh (24,576 elements), "
+                    "profiles/assemble_df_kernel_cube16_k3.md"},
 }
 # the sources of each K1 translation unit (the kernel and the device headers it includes)
-K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "device_df.cuh", "device_common.cuh"),
+K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "assemble_df.cuh", "device_df.cuh", "device_common.cuh"),
               "assemble.cu": ("assemble.cu", "device_common.cuh")}
 
 
@@ -566,6 +570,11 @@ def run_workload(W, args, stream, dev, world=1, full=True):
     # the dense mass contraction (eq. 3.55, M_{kappa^-1}) as one GEMM on the tensor cores
     # (BF16 operands, FP32 accumulation) against the CUDA-core FP32 contraction
     out["h2_contraction"] = h2_contraction(W, dev, stream)
+    # the HDG_MIXED_BF16 assembly (split-BF16 tensor-core masses, double-float condensation)
+    # beside the step's double-float one: time per assembly and the solution's deviation
+    if args.asm == "df32" and prob.k >= 1:
+        out["mixed_bf16_assembly"] = mixed_bf16_assembly(W, dev, stream, uh, u, step_prec, phases["assemble_condense"])
+        M.assemble_condense(asm_prec)
 
     # end to end through the public API with host buffers (pinned) and copies in the region
     pin = {k: torch.from_numpy(v).pin_memory() for k, v in W.host.items()}
@@ -663,6 +672,54 @@ def h2_contraction(W, dev, stream, reps=5):
     res["note"] = (f"[{M.nelt} x {nq}] . [{nq} x {npair}] per launch; bytes = the FP64 coefficient in, the FP32 "
                    "masses out; HBM-bound at this contraction length")
     return res
+
+
+def mixed_bf16_assembly(W, dev, stream, uh_ref, u_ref, step_prec, df32_ms, reps=5):
+    """hdg_assemble_condense(HDG_MIXED_BF16) on the workload: time per assembly (the tensor-core
+    contraction of the masses and the condensation from them), the contraction alone, and the
+    relative difference of the step's solution (trace and u, solved to 1e-10 the same way)
+    from the double-float assembly's."""
+    import torch
+
+    from paper_1305_1489_gb300 import HDG_MIXED_BF16
+
+    M = W.M
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    masses = [None]
+
+    def contraction():
+        masses[0] = M.mixed_masses()
+
+    ms_tc = timed(contraction)
+    stride = masses[0].shape[1]
+    masses[0] = None
+    ms_asm = timed(lambda: M.assemble_condense(HDG_MIXED_BF16))
+    uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
+    q, u = M.recover(uh)
+    n, nq = M.n, M.nq
+    npair = n * (n + 1) // 2
+    return {"ms": ms_asm, "df32_ms": df32_ms, "speedup_vs_df32": df32_ms / ms_asm,
+            "tc_contraction_ms": ms_tc,
+            "tc_contraction_gbs": M.nelt * (3 * 8 * nq + 4 * stride) / (ms_tc / 1e3) / 1e9,
+            "tc_contraction_tflops": 2.0 * 6 * M.nelt * nq * (2 * npair + n) / (ms_tc / 1e3) / 1e12,
+            "solve_iterations": it, "relres": rr,
+            "uhat_rel_diff_vs_df32": float((uh - uh_ref).abs().max() / uh_ref.abs().max()),
+            "u_rel_diff_vs_df32": float((u - u_ref).abs().max() / u_ref.abs().max()),
+            "note": "masses M_{kappa^-1}, M_c and f^K from three-way BF16 splits (six tcgen05 products, FP32 "
+                    "accumulation), then the double-float condensation; tflops counts the six split products"}
 
 
 def run_rule_comparison(dev, stream, reps=5):
@@ -922,6 +979,8 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "roofline": r["roofline"],
         "solve_roofline": r["solve_roofline"], "h2_contraction": r["h2_contraction"], "wall_s_timed": r["wall_s_timed"],
     }
+    if "mixed_bf16_assembly" in r:
+        out["mixed_bf16_assembly"] = r["mixed_bf16_assembly"]
     if world == 1 and rank == 0 and args.extras:
         out["extras"] = run_extras(args, dev, stream)
     return out
@@ -1038,6 +1097,8 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
     ap.add_argument("--profile-workload", default=HEADLINE)
+    ap.add_argument("--profile-solve", type=int, default=0,
+                    help="two-level mixed trace solves on an s^3 x 6 mesh of --profile-workload, then exit")
     ap.add_argument("--profile-tc", type=int, default=0,
                     help="run the tensor-core mass contraction twice on an s^3 x 6 mesh and exit")
     ap.add_argument("--learned", action="store_true", help="train and evaluate the learned guess and exit")
@@ -1050,6 +1111,23 @@ def main():
     args = ap.parse_args()
     if args.profile_k1:
         profile_k1(args.profile_workload, args.profile_k1, asm=args.asm)
+        return
+    if args.profile_solve:
+        import torch
+
+        from paper_1305_1489_gb300 import HDG_DF32, HDG_MIXED_FP32, build
+        build()
+        W = Workload(args.profile_workload, torch.device("cuda", 0), torch.cuda.current_stream(), s=args.profile_solve)
+        M = W.M
+        M.set_inner_tolerance(INNER_RTOL.get(args.profile_workload, 1e-4))
+        M.set_coarse_space(*W.hierarchy())
+        M.assemble_condense(HDG_DF32)
+        runs = []
+        for _ in range(2):
+            uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=HDG_MIXED_FP32)
+            runs.append({"iterations": it, "relres": rr})
+        print(json.dumps({"profile_solve": {"workload": args.profile_workload, "s": args.profile_solve,
+                                            "nelt": M.nelt, "runs": runs}}))
         return
     if args.profile_tc:
         import torch

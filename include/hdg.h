@@ -53,8 +53,10 @@ typedef enum {
 typedef enum {
   HDG_FP64 = 0,        /* every operation in IEEE double                                   */
   HDG_MIXED_FP32 = 1,  /* FP32 inner solve with FP64 residuals and refinement (solve only) */
-  HDG_DF32 = 2         /* assembly only: double-float arithmetic (pairs of FP32, ~48-bit
+  HDG_DF32 = 2,        /* assembly only: double-float arithmetic (pairs of FP32, ~48-bit
                           significand) on the FP32 pipe; results stored as FP64           */
+  HDG_MIXED_BF16 = 3   /* assembly only: the volume masses on the tensor cores from split
+                          BF16 operands (FP32-level), the condensation as HDG_DF32       */
 } hdg_precision;
 
 typedef struct hdg_mesh hdg_mesh;
@@ -135,7 +137,12 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * the local recovery (eq. 5.3), into library-owned device memory.
  * precision: HDG_FP64 (native FP64) or HDG_DF32 (double-float on the FP32 pipe, FP64-level
  * accuracy; with convection the non-symmetric Schur complement is factored by a double-float
- * LU without pivoting; at k = 0 it runs the FP64 kernel).  The precision also
+ * LU without pivoting; at k = 0 it runs the FP64 kernel), or HDG_MIXED_BF16: the volume masses
+ * M_{kappa^-1}, M_c and f^K (eq. 3.55-3.56, 4.3) as one tensor-core contraction over all
+ * elements (tcgen05, each FP64 operand split into three BF16 parts, the six products above
+ * 2^-24 accumulated in FP32; masses and f^K to FP32-level rounding), then the HDG_DF32
+ * condensation from them; k >= 1 and the conical rule (HDG_ERR_UNSUPPORTED otherwise); it
+ * holds nelt x 4 ceil((n(n+1) + n) / 4) bytes of FP32 masses.  The precision also
  * selects that of hdg_recover and hdg_postprocess until the next assembly.  Synchronises to report
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
@@ -295,8 +302,12 @@ int hdg_set_coarse_space(hdg_mesh* mesh, int nlev, const int64_t* sizes, const i
 int hdg_coarse_precond_apply(hdg_mesh* mesh, const double* r, double* z);
 
 /* hdg_autotune: (1) pick the persistent grids of the trace-solve kernels (4 to 32 blocks per
- * SM), one for the FP64 and one for the FP32 iterations, by timing one block-Jacobi PCG
- * iteration (operator, update, direction) of the assembled system in each precision;
+ * SM) and the form of the operator product (one face-major pass over the faces' rows of C^K,
+ * or an element pass over contiguous C^K blocks followed by a per-face sum of the owners'
+ * contributions), one choice for the FP64 and one for the FP32 iterations, by timing one
+ * block-Jacobi PCG iteration (operator, update, direction) of the assembled system in each
+ * precision (the environment variable HDG_MATVEC=face|element, read at mesh creation, fixes
+ * the form);
  * (2) pick the launch shape of the double-float assembly (threads per element and resident
  * elements per SM; k = 1..3 have two shapes) by timing it.  The choices are kept by the
  * mesh; the system of the caller's last hdg_assemble_condense is restored.  out (nullable,
@@ -309,6 +320,8 @@ typedef struct hdg_tuning {
   double iter_ms;     /* one FP64 block-Jacobi iteration at the choice  */
   double iter32_ms;   /* one FP32 iteration at the choice               */
   double k1_ms;       /* one double-float assembly at the choice        */
+  int matvec_em64;    /* FP64 solve loops: 1 = element pass + face sum,  */
+  int matvec_em32;    /*   0 = one face-major pass; the same for FP32    */
 } hdg_tuning;
 int hdg_autotune(hdg_mesh* mesh, hdg_tuning* out);
 
@@ -379,6 +392,16 @@ int hdg_face_norm2(hdg_mesh* mesh, const double* coef, const double* vals, doubl
  * Synchronises the mesh's stream in mode 0 and returns HDG_ERR_CUDA if a tensor-core wait ran
  * out (bounded waits; the kernel frees its tensor memory in that case).  k >= 1.          */
 int hdg_mass_contraction(hdg_mesh* mesh, const double* g, int mode, float* out);
+
+/* The masses of the HDG_MIXED_BF16 assembly for the current coefficients, on their own (tests,
+ * measurement): out device f32 [nelt][*stride] = [M_{kappa^-1} pairs | M_c pairs | f^K | pad],
+ * pairs (i <= j) in row-major order (i = 0: j = 0..n-1, then i = 1, ...), so the f^K entries
+ * follow the 2 n(n+1)/2 pair entries; *stride (host, nullable) = n(n+1) + n rounded up to a
+ * multiple of 4.  With out NULL only *stride is set.  One tensor-core contraction over all
+ * elements (each FP64 operand split into three BF16 parts, six products, FP32 accumulation).
+ * HDG_ERR_UNSUPPORTED for k = 0 or the symmetric rule, HDG_ERR_COEFF for kappa <= 0, c < 0 or
+ * non-finite data, HDG_ERR_CUDA if an MMA does not complete within the bounded wait.       */
+int hdg_mixed_masses(hdg_mesh* mesh, float* out, int* stride);
 
 /* ------------------------------------------------------------------ batched problems
  * Many independent problems of mixed degree solved together.  Problems of equal degree are

@@ -20,10 +20,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (HDG_DF32, HDG_FP64, HDG_METHOD_BDM, HDG_METHOD_HDG, HDG_MIXED_FP32, HDG_RULE_CONICAL,  # noqa: F401
-                   HDG_RULE_SYMMETRIC, HDGError)
+from ._lib import (HDG_DF32, HDG_FP64, HDG_METHOD_BDM, HDG_METHOD_HDG, HDG_MIXED_BF16, HDG_MIXED_FP32,  # noqa: F401
+                   HDG_RULE_CONICAL, HDG_RULE_SYMMETRIC, HDGError)
 
-__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "HDG_DF32", "HDG_METHOD_HDG", "HDG_METHOD_BDM",
+__all__ = ["HDGMesh", "HDGError", "HDG_FP64", "HDG_MIXED_FP32", "HDG_DF32", "HDG_MIXED_BF16", "HDG_METHOD_HDG", "HDG_METHOD_BDM",
            "HDG_RULE_CONICAL", "HDG_RULE_SYMMETRIC",
            "build", "load_library"]
 
@@ -292,12 +292,14 @@ class HDGMesh:
         _lib.check(lib.hdg_set_coarse_space(self._h, len(sz), _ptr(sz), _ptr(nd), _ptr(wt)))
 
     def autotune(self):
-        """Pick the persistent grids of the trace-solve kernels (FP64 and FP32) and the launch
-        shape of the double-float assembly by timing (hdg_autotune); returns a dict of the
-        choices and the best times."""
+        """Pick the persistent grids and the operator form (element pass + face sum, or one
+        face-major pass) of the trace-solve kernels (FP64 and FP32) and the launch shape of the
+        double-float assembly by timing (hdg_autotune); returns a dict of the choices and the
+        best times."""
         class Tuning(C.Structure):
             _fields_ = [("face_blocks", C.c_int), ("face_blocks32", C.c_int), ("k1_threads", C.c_int),
-                        ("iter_ms", C.c_double), ("iter32_ms", C.c_double), ("k1_ms", C.c_double)]
+                        ("iter_ms", C.c_double), ("iter32_ms", C.c_double), ("k1_ms", C.c_double),
+                        ("matvec_em64", C.c_int), ("matvec_em32", C.c_int)]
         t = Tuning()
         _lib.check(_lib.load().hdg_autotune(self._h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Tuning._fields_}
@@ -381,6 +383,17 @@ class HDGMesh:
         g = _dev_f64(g, (self.nelt, self.nq), "g")
         out = torch.empty((self.nelt, self.n * (self.n + 1) // 2), dtype=torch.float32, device=g.device)
         _lib.check(_lib.load().hdg_mass_contraction(self._h, g.data_ptr(), int(mode), out.data_ptr()))
+        return out
+
+    def mixed_masses(self):
+        """hdg_mixed_masses: the FP32 masses of the HDG_MIXED_BF16 assembly for the current
+        coefficients, [nelt, stride] = [M_{kappa^-1} pairs | M_c pairs | f^K | padding]."""
+        import torch
+        st = C.c_int(0)
+        lib = _lib.load()
+        _lib.check(lib.hdg_mixed_masses(self._h, None, C.byref(st)))
+        out = torch.empty((self.nelt, st.value), dtype=torch.float32, device="cuda")
+        _lib.check(lib.hdg_mixed_masses(self._h, out.data_ptr(), C.byref(st)))
         return out
 
     @property

@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(_HERE, "libhdg.so")
 HDG_FP64 = 0
 HDG_MIXED_FP32 = 1
 HDG_DF32 = 2
+HDG_MIXED_BF16 = 3
 HDG_METHOD_HDG = 0
 HDG_METHOD_BDM = 1
 HDG_RULE_CONICAL = 0
@@ -70,6 +71,7 @@ _SIGS = {
     "hdg_nn_fold_affine": [C.c_int, C.c_int, P, P, P, P, P],
     "hdg_set_coarse_space": [P, C.c_int, P, P, P],
     "hdg_autotune": [P, P],
+    "hdg_mixed_masses": [P, P, P],
     "hdg_coarse_precond_apply": [P, P, P],
     "hdg_solve_trace_noalloc": [P, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "hdg_recover": [P, P, P, P],

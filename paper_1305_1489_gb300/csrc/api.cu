@@ -95,7 +95,8 @@ static void release(hdg_mesh* M) {
   void* ptrs[] = {M->d_vx, M->d_geo, M->d_fvx, M->d_facebyele, M->d_perm, M->d_owner, M->d_ftype, M->d_C, M->d_Cf,
                   M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
-                  M->d_p32, M->d_q32, M->d_bicg, M->d_fverts, M->d_Tproj, M->d_norm, M->d_bicg32};
+                  M->d_p32, M->d_q32, M->d_bicg, M->d_fverts, M->d_Tproj, M->d_norm, M->d_bicg32, M->d_Y,
+                  M->d_mass3B, M->d_mass3, M->d_fslot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
@@ -110,9 +111,14 @@ static void release(hdg_mesh* M) {
 }
 
 static int check_status(hdg_mesh* M) {
-  int32_t st[5];
+  int32_t st[8];
   HDG_CUDA_TRY(cudaMemcpyAsync(st, M->d_status, sizeof(st), cudaMemcpyDeviceToHost, M->stream));
   HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  if (st[7]) {  // counted by the element pass of the trace operator; reported once
+    HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 7, 0, sizeof(int32_t), M->stream));
+    return fail(HDG_ERR_CUDA, std::to_string(st[7]) + " element-pass block(s) whose C^K copies did not complete "
+                                                      "within the wait limit (the solution is not valid)");
+  }
   if (st[4]) {  // counted by the double-float recovery kernel; reported once
     HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 4, 0, sizeof(int32_t), M->stream));
     return fail(HDG_ERR_CUDA, std::to_string(st[4]) + " element(s) whose recovery record copy did not complete (q, u set to NaN)");
@@ -155,6 +161,14 @@ int hdg_mesh_create(const double* coords, int64_t nver, const int32_t* elems, in
   if (const char* fb = std::getenv("HDG_FACE_BLOCKS")) {
     const int v = std::atoi(fb);
     if (v > 0) M->face_blocks = M->face_blocks32 = M->grid_cap = v;
+  }
+  // HDG_MATVEC=face|element: the form of the solve loops' operator products, fixed (the
+  // autotuner then leaves it alone)
+  if (const char* mv = std::getenv("HDG_MATVEC")) {
+    if (std::strcmp(mv, "face") == 0 || std::strcmp(mv, "element") == 0) {
+      M->em64 = M->em32 = mv[0] == 'e';
+      M->em_forced = true;
+    }
   }
   std::string err;
   int rc = HDG_OK;
@@ -266,18 +280,32 @@ int hdg_set_boundary_data(hdg_mesh* M, const double* uD, const double* gN) {
 int hdg_assemble_condense(hdg_mesh* M, int precision) {
   if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
   if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
-  if (precision != HDG_FP64 && precision != HDG_DF32)
-    return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64 or HDG_DF32");
+  if (precision != HDG_FP64 && precision != HDG_DF32 && precision != HDG_MIXED_BF16)
+    return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64, HDG_DF32 or HDG_MIXED_BF16");
   if (M->beta_q && !M->beta_f) return fail(HDG_ERR_STATE, "convection set without hdg_set_face_convection");
   if (M->beta_q && M->method == HDG_METHOD_BDM)
     return fail(HDG_ERR_UNSUPPORTED, "the BDM element is built for reaction-diffusion (beta = 0)");
   if (precision == HDG_DF32 && M->tab.rule != HDG_RULE_CONICAL)
     return fail(HDG_ERR_UNSUPPORTED, "the double-float assembly sums the masses by sum factorisation, which needs "
                                      "the conical volume rule");
+  if (precision == HDG_MIXED_BF16 && (M->tab.rule != HDG_RULE_CONICAL || M->k < 1))
+    return fail(HDG_ERR_UNSUPPORTED, "the split-BF16 assembly is built for k >= 1 on the conical volume rule");
   if (M->k == 0 && (M->beta_q || M->method == HDG_METHOD_BDM))
     return fail(HDG_ERR_UNSUPPORTED, "k = 0 is built for the HDG method without convection");
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
-  HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
+  if (precision == HDG_MIXED_BF16) {
+    const int stride = mass3_stride(M->k);
+    if (!M->d_mass3) HDG_CUDA_TRY(cudaMalloc(&M->d_mass3, sizeof(float) * M->nelt * stride));
+    int rc = mass3_contraction(M, M->d_mass3);
+    if (rc) return rc;
+    int32_t st6 = 0;
+    HDG_CUDA_TRY(cudaMemcpyAsync(&st6, M->d_status + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, M->stream));
+    HDG_CUDA_TRY(cudaStreamSynchronize(M->stream));
+    if (st6) return fail(HDG_ERR_CUDA, "tensor-core contraction: an MMA did not complete within the wait limit");
+    HDG_CUDA_TRY(launch_assemble_df_mass(M, M->d_mass3, stride));
+  } else {
+    HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
+  }
   M->assembled = true;
   M->asm_prec = precision;
   M->c32_ready = false;

@@ -95,6 +95,7 @@ struct hdg_mesh {
   int32_t* d_facebyele = nullptr; // [nelt][4]
   int32_t* d_perm = nullptr;      // [nelt][4]
   int32_t* d_owner = nullptr;     // [nfc][2]   4*K + l of the (up to) two elements, -1 if none
+  int32_t* d_fslot = nullptr;     // [nelt][4]  2 f + side (which owner of face f the element is)
   int32_t* d_ftype = nullptr;     // [nfc]      0 interior, 1 Dirichlet, 2 Neumann
 
   // borrowed coefficient / data pointers (device)
@@ -138,6 +139,17 @@ struct hdg_mesh {
   int face_blocks = 1216;         // persistent grid of the face kernels (hdg_autotune)
   int face_blocks32 = 1216;       // the same for the FP32 inner iterations
   int grid_cap = 0;               // > 0: cap on the grids of the coarse-level kernels (HDG_FACE_BLOCKS)
+  // form of the operator H x in the solve loops: element-major pass + face sum (true) or one
+  // face-major pass (false), per precision; hdg_autotune measures both unless HDG_MATVEC fixed it
+  bool em64 = true, em32 = true;
+  bool em_forced = false;
+  int graphs_em = -1;             // (em64, em32) of the cached graphs
+  double* d_Y = nullptr;          // [nfc][2][d2] element-pass output per face side (FP64 or FP32 view)
+  // HDG_MIXED_BF16 assembly: the split pair-product table of the tensor-core contraction (for
+  // the volume rule mass3_rule) and the per-element FP32 masses [nelt][mass3_stride(k)]
+  void* d_mass3B = nullptr;
+  int mass3_rule = -1;
+  float* d_mass3 = nullptr;
   int k1_variant = 0;             // launch shape of the double-float K1 (hdg_autotune)
   int asm_prec = -1;              // precision of the last hdg_assemble_condense
   hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL
@@ -160,6 +172,9 @@ cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* 
                           double* FZ);
 cudaError_t launch_assemble(hdg_mesh* M);
 cudaError_t launch_assemble_df(hdg_mesh* M);
+cudaError_t launch_assemble_df_mass(hdg_mesh* M, const float* mass3, int stride);
+int mass3_contraction(hdg_mesh* M, float* out);  // tc_mass.cu
+int mass3_stride(int k);
 cudaError_t launch_projection(hdg_mesh* M, const double* q_vol, const double* u_vol, const double* q_face,
                               const double* u_face, double* Pq, double* Pu);
 cudaError_t launch_face_projection(hdg_mesh* M, const double* vals, double* Pu);

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <vector>
 
+#include "device_async.cuh"
 #include "device_common.cuh"
 #include "hdg_internal.h"
 
@@ -147,8 +148,17 @@ __device__ __forceinline__ float face_apply_rm(const float* __restrict__ C, cons
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl) {
       const float* xs = x + (int64_t)f4[fl] * D2;
+      if constexpr (D2 % 2 == 0) {  // a face's entries start on an 8-byte boundary: read in pairs
 #pragma unroll
-      for (int b = 0; b < D2; ++b) xv[fl * D2 + b] = xs[b];
+        for (int b = 0; b < D2; b += 2) {
+          const float2 v = *reinterpret_cast<const float2*>(xs + b);
+          xv[fl * D2 + b] = v.x;
+          xv[fl * D2 + b + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < D2; ++b) xv[fl * D2 + b] = xs[b];
+      }
     }
     asm volatile("" ::: "memory");
 #pragma unroll
@@ -201,28 +211,184 @@ __device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __rest
   }
 }
 
-// row a of face e's block inverse times the face's d2 residual entries; for even d2 the rows
-// and the face's entries start on 2-element boundaries, so they are read as pairs
+// ------------------------------------------------------------------ element-major operator
+// The same product H x in two passes (eq. 6.5 summed element by element):
+//   element pass  for every element K and row r = l d2 + a of C^K, the sum_s C^K[r][s] x_dK[s]
+//                 goes to Y[f][side][a], f the element's face l and side which of the face's
+//                 two owners K is (the per-mesh table fslot = 2 f + side);
+//   face sum      (H x)_e[a] = Y[e][0][a] + Y[e][1][a], fused into the kernel that consumes
+//                 H x: a coalesced stream, no gather (a boundary face reads side 0 only).
+// The element pass is a persistent streaming kernel: the C^K of a group of EB consecutive
+// elements is one contiguous block, which one producer thread copies into a ring of NST
+// shared-memory stages with 1-D bulk copies (the tensor memory accelerator) completed on the
+// stage's "full" mbarrier; one consumer thread per row of the group waits for the stage, takes
+// the dot product of its row with the group's x_dK (gathered through the element's four face
+// numbers one group ahead, staged in shared memory) and arrives on the stage's "empty" mbarrier,
+// which the producer waits on before it reuses the stage.  Every wait is bounded: one that runs
+// out counts in status[7] and the kernel runs on (its output is then garbage, which the solve
+// reports as HDG_ERR_CUDA), waiting at the end, again bounded, for its own copies in flight.
+template <typename T, int D2>
+struct EmPass {
+  static constexpr int m = 4 * D2;
+  static constexpr int EB = (192 / m) > 0 ? 192 / m : 1;  // elements per group
+  static constexpr int ROWS = EB * m;                      // rows of a group (consumer threads)
+  static constexpr int CW = (ROWS + 31) / 32;              // consumer warps
+  static constexpr int NTHR = 32 * CW + 32;                // + the producer warp
+  static constexpr int GBYTES = EB * m * m * (int)sizeof(T);
+  static constexpr int NSTR = (200 * 1024) / GBYTES;
+  static constexpr int NST = NSTR > 4 ? 4 : (NSTR < 2 ? 2 : NSTR);  // stages of the ring
+  static constexpr int XBYTES = 2 * 32 * CW * (int)sizeof(T);       // x_dK, double-buffered
+  static constexpr int SMEM = NST * GBYTES + XBYTES;
+  static_assert(GBYTES % 16 == 0 && (m * (int)sizeof(T)) % 16 == 0, "16-byte bulk copies and rows");
+  static_assert(SMEM <= 227 * 1024, "element pass ring");
+};
+constexpr int kEmWaitPolls = 1 << 22;  // bounded mbarrier waits (far above a copy's latency)
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename T, int D2>
+__global__ void __launch_bounds__(EmPass<T, D2>::NTHR) em_apply_kernel(const T* __restrict__ C, const T* __restrict__ x,
+                                                                       const int32_t* __restrict__ fslot, int64_t nelt,
+                                                                       T* __restrict__ Y, const double* done,
+                                                                       int32_t* status) {
+  using P = EmPass<T, D2>;
+  constexpr int m = P::m, EB = P::EB, NST = P::NST;
+  constexpr int VW = 16 / sizeof(T);
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  if (*done != 0.0) return;
+  extern __shared__ __align__(128) unsigned char em_smem[];
+  T* ring = reinterpret_cast<T*>(em_smem);                     // [NST][EB m m]
+  T* xs = reinterpret_cast<T*>(em_smem + NST * P::GBYTES);     // [2][32 CW]
+  __shared__ __align__(8) uint64_t full[NST], empty[NST];
+  const int tid = threadIdx.x;
+  const int64_t ngroups = (nelt + EB - 1) / EB;
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 32 * P::CW);
+    }
+  }
+  __syncthreads();
+  int fails = 0;
+  if (tid >= 32 * P::CW) {
+    // producer: one thread streams the groups' C^K blocks into the ring
+    if (tid == 32 * P::CW) {
+      int it = 0;
+      for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, ++it) {
+        const int s = it % NST;
+        if (it >= NST && !mbar_wait(&empty[s], (uint32_t)((it / NST) - 1) & 1u, kEmWaitPolls)) ++fails;
+        const int64_t ne = min((int64_t)EB, nelt - g * EB);
+        const uint32_t bytes = (uint32_t)(ne * m * m * (int64_t)sizeof(T));
+        mbar_expect_tx(&full[s], bytes);
+        bulk_g2s(ring + (size_t)s * EB * m * m, C + g * EB * (int64_t)(m * m), bytes, &full[s]);
+      }
+      // the copies still in flight land before the block exits: the last use of each stage
+      for (int u = 0; u < NST && u < it; ++u) {
+        const int last = it - 1 - u, s = last % NST;
+        if (!mbar_wait(&full[s], (uint32_t)(last / NST) & 1u, kEmWaitPolls)) ++fails;
+      }
+    }
+  } else {
+    // consumers: thread (el, r) owns row r of the group's element el
+    const int el = tid / m, r = tid - el * m;
+    const bool lane_act = el < EB;
+    // the gather of x_dK is pipelined over the groups: the face number two groups ahead and
+    // the value one group ahead are in flight while a group is computed, so that no iteration
+    // waits on more than one memory latency
+    auto face_of = [&](int64_t g) -> int {  // 2 f + side of this thread's row of group g
+      const int64_t K = g * EB + el;
+      return (lane_act && g < ngroups && K < nelt) ? __ldg(fslot + 4 * K + r / D2) : -1;
+    };
+    auto x_of = [&](int fs) -> T { return fs >= 0 ? x[(int64_t)(fs >> 1) * D2 + (r % D2)] : (T)0; };
+    const int64_t G = gridDim.x;
+    int fcur = face_of(blockIdx.x);
+    T xn = x_of(fcur);
+    int f1 = face_of(blockIdx.x + G);
+    int it = 0;
+    for (int64_t g = blockIdx.x; g < ngroups; g += G, ++it) {
+      const int s = it % NST;
+      T* xb = xs + (it & 1) * 32 * P::CW;
+      xb[tid] = xn;
+      const int fs = fcur;      // this group's output slot
+      fcur = f1;
+      xn = x_of(f1);            // the next group's x_dK
+      f1 = face_of(g + 2 * G);  // the face numbers of the group after it
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * P::CW) : "memory");  // xb complete
+      if (!mbar_wait(&full[s], (uint32_t)(it / NST) & 1u, kEmWaitPolls)) ++fails;
+      const int64_t K = g * EB + el;
+      if (lane_act && K < nelt) {
+        const V* row = reinterpret_cast<const V*>(ring + (size_t)s * EB * m * m + (size_t)(el * m + r) * m);
+        const V* xr = reinterpret_cast<const V*>(xb + el * m);
+        T acc0 = (T)0, acc1 = (T)0;
+#pragma unroll
+        for (int q = 0; q < m / VW; ++q) {
+          const V cq = row[q], xq = xr[q];
+          if constexpr (sizeof(T) == 4) {
+            acc0 = fmaf(cq.x, xq.x, acc0);
+            acc1 = fmaf(cq.y, xq.y, acc1);
+            acc0 = fmaf(cq.z, xq.z, acc0);
+            acc1 = fmaf(cq.w, xq.w, acc1);
+          } else {
+            acc0 = fma(cq.x, xq.x, acc0);
+            acc1 = fma(cq.y, xq.y, acc1);
+          }
+        }
+        Y[(int64_t)fs * D2 + (r % D2)] = acc0 + acc1;
+      }
+      mbar_arrive(&empty[s]);
+    }
+  }
+  if (fails) atomicAdd(status + 7, 1);
+}
+
+// blocks of the element pass: every SM's resident blocks, or fewer when there are fewer groups
+// (HDG_FACE_BLOCKS caps the grid in the tests, so that each block takes many groups)
+template <typename T, int D2>
+static int em_grid(hdg_mesh* M) {
+  using P = EmPass<T, D2>;
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    cudaFuncSetAttribute(em_apply_kernel<T, D2>, cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, em_apply_kernel<T, D2>, P::NTHR, P::SMEM);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t ngroups = (M->nelt + P::EB - 1) / P::EB;
+  int64_t g = std::min<int64_t>(ngroups, (int64_t)per_sm * sms);
+  if (M->grid_cap > 0) g = std::min<int64_t>(g, M->grid_cap);
+  return (int)std::max<int64_t>(g, 1);
+}
+
+
+// (H x)_e entry a from the element pass: the face's two sides of Y (a boundary face, type != 0,
+// has one owner, so its side 1 holds nothing of this product)
+template <typename T, int D2>
+__device__ __forceinline__ T face_sum(const T* __restrict__ Y, const FaceArgs& F, int64_t e, int a) {
+  const T s0 = Y[(2 * e) * D2 + a];
+  return F.ftype[e] == 0 ? s0 + Y[(2 * e + 1) * D2 + a] : s0;
+}
+
+// (H x)_e entry a in one pass (face-major) or from Y of the element pass (EM)
+template <typename T, int D2, bool EM>
+__device__ __forceinline__ T face_op(const T* __restrict__ CY, const T* __restrict__ x, const FaceArgs& F,
+                                     int64_t e, int a) {
+  if constexpr (EM) return face_sum<T, D2>(CY, F, e, a);
+  else return face_apply<T, D2>(CY, x, F, e, a);
+}
+
+// row a of face e's block inverse times the face's d2 residual entries
 template <typename T, int D2>
 __device__ __forceinline__ T bj_apply(const T* __restrict__ Binv, const T* __restrict__ r, int64_t e, int a) {
   T s0 = (T)0, s1 = (T)0;
   const T* Bi = Binv + (e * D2 + a) * D2;
   const T* re = r + e * D2;
-  if constexpr (D2 % 2 == 0) {
-    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-    const V2* Bv = reinterpret_cast<const V2*>(Bi);
-    const V2* rv = reinterpret_cast<const V2*>(re);
 #pragma unroll
-    for (int b = 0; b < D2 / 2; ++b) {
-      const V2 bb = Bv[b], xx = rv[b];
-      s0 = fma((T)bb.x, (T)xx.x, s0);
-      s1 = fma((T)bb.y, (T)xx.y, s1);
-    }
-  } else {
-#pragma unroll
-    for (int b = 0; b < D2; ++b) {
-      if (b & 1) s1 = fma(Bi[b], re[b], s1); else s0 = fma(Bi[b], re[b], s0);
-    }
+  for (int b = 0; b < D2; ++b) {
+    if (b & 1) s1 = fma(Bi[b], re[b], s1); else s0 = fma(Bi[b], re[b], s0);
   }
   return s0 + s1;
 }
@@ -430,8 +596,8 @@ __global__ void pcg_precond_kernel(FaceArgs F, const T* __restrict__ Binv, const
   }
 }
 
-// q = H p (free faces), alpha = rz / (p.q)
-template <typename T, int D2>
+// q = H p (free faces), alpha = rz / (p.q); with EM, C is Y of the element pass over p
+template <typename T, int D2, bool EM = false>
 __global__ void pcg_matvec_kernel(FaceArgs F, const T* __restrict__ C, const T* __restrict__ p, T* __restrict__ q,
                                   double* red, unsigned int* counter, double* scal) {
   if (scal[S_DONE] != 0.0) return;
@@ -439,7 +605,7 @@ __global__ void pcg_matvec_kernel(FaceArgs F, const T* __restrict__ C, const T* 
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const T qv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, p, F, T_.e, T_.a) : (T)0;
+    const T qv = (F.ftype[T_.e] != 1) ? face_op<T, D2, EM>(C, p, F, T_.e, T_.a) : (T)0;
     q[T_.t] = qv;
     v[0] = fma((double)p[T_.t], (double)qv, v[0]);
   }
@@ -641,8 +807,8 @@ __global__ void bicg_tl_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ 
   }
 }
 
-// v = H ph;  alpha = rho / (rhat . v)
-template <typename T, int D2>
+// v = H ph;  alpha = rho / (rhat . v); with EM, C is Y of the element pass over ph
+template <typename T, int D2, bool EM = false>
 __global__ void bicg_v_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
@@ -650,7 +816,7 @@ __global__ void bicg_v_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const T vv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, V.ph, F, T_.e, T_.a) : (T)0;
+    const T vv = (F.ftype[T_.e] != 1) ? face_op<T, D2, EM>(C, V.ph, F, T_.e, T_.a) : (T)0;
     V.v[T_.t] = vv;
     v[0] = fma((double)V.rh[T_.t], (double)vv, v[0]);
   }
@@ -681,8 +847,8 @@ __global__ void bicg_s_kernel(FaceArgs F, const T* __restrict__ Binv, BicgVecs<T
   }
 }
 
-// t = H sh;  omega = (t.s) / (t.t)
-template <typename T, int D2>
+// t = H sh;  omega = (t.s) / (t.t); with EM, C is Y of the element pass over sh
+template <typename T, int D2, bool EM = false>
 __global__ void bicg_t_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
@@ -690,7 +856,7 @@ __global__ void bicg_t_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const T tv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, V.sh, F, T_.e, T_.a) : (T)0;
+    const T tv = (F.ftype[T_.e] != 1) ? face_op<T, D2, EM>(C, V.sh, F, T_.e, T_.a) : (T)0;
     V.t[T_.t] = tv;
     v[0] = fma((double)tv, (double)V.s[T_.t], v[0]);
     v[1] = fma((double)tv, (double)tv, v[1]);
@@ -960,12 +1126,12 @@ template <typename T, int D2>
 static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStream_t st, const double* done) {
   Coarse* c = M->coarse;
   const int G = grid_levels(c);
-  // one pass over every node or row (the level kernels loop when the grid is capped, as the
-  // tests do with HDG_FACE_BLOCKS to exercise those loops)
-  const int64_t cap = M->grid_cap > 0 ? std::min<int64_t>(M->grid_cap, kMaxBlocks) : (int64_t)65535;
+  // the level kernels loop over their rows when the grid is capped (HDG_FACE_BLOCKS caps it
+  // further in the tests, to exercise those loops on small meshes)
+  const int64_t cap = M->grid_cap > 0 ? std::min<int64_t>(M->grid_cap, kMaxBlocks) : kMaxBlocks;
   auto grid = [cap](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, cap); };
   auto rows = [cap](int64_t n) { return (int)std::min<int64_t>((n * kRowLanes + 255) / 256, cap); };
-  const int gr = (int)std::min<int64_t>((c->lv[0].n + 7) / 8, cap);  // one warp per node
+  const int gr = (int)std::min<int64_t>({(c->lv[0].n + 7) / 8, (int64_t)152 * 16, cap});  // one warp per node
   restrict_gather_kernel<T, D2><<<gr, 256, 0, st>>>(CA, r, done);
   level_down_kernel<true><<<rows(c->lv[0].n), 256, 0, st>>>(c->lv[0], c->rc, done);
   for (int l = 1; l < G; ++l) {
@@ -985,7 +1151,8 @@ static void coarse_cycle(hdg_mesh* M, const CoarseArgs& CA, const T* r, cudaStre
 
 // graphs captured with or without the coarse correction are not interchangeable
 static void match_graphs(hdg_mesh* M, bool tl) {
-  if (M->graphs_tl == tl) return;
+  const int em = (M->em64 ? 2 : 0) | (M->em32 ? 1 : 0);  // nor are those of the two operator forms
+  if (M->graphs_tl == tl && M->graphs_em == em) return;
   cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg, &M->graph_bicg32,
                            &M->wgraph_bicg, &M->wgraph_bicg32};
   for (cudaGraphExec_t* g : gs)
@@ -994,7 +1161,9 @@ static void match_graphs(hdg_mesh* M, bool tl) {
       *g = nullptr;
     }
   M->graphs_tl = tl;
+  M->graphs_em = em;
 }
+
 
 static int64_t bicg_stride(int64_t nv, int w) { return (nv + w - 1) / w * w; }
 
@@ -1013,6 +1182,7 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_scal, sizeof(double) * 2 * S_NSCAL));
     HDG_CUDA_TRY(cudaMalloc(&M->d_counter, sizeof(unsigned int) * 4));
     HDG_CUDA_TRY(cudaMemsetAsync(M->d_counter, 0, sizeof(unsigned int) * 4, M->stream));
+    HDG_CUDA_TRY(cudaMalloc(&M->d_Y, sizeof(double) * 2 * M->nfc * M->tab.d2));
     M->red_blocks = kMaxBlocks;
   }
   if (M->beta_q && !M->d_bicg) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * bicg_stride(nv, 2)));
@@ -1121,7 +1291,10 @@ struct Solver {
     const bool tl = M->coarse != nullptr && M->coarse->ready;
     match_graphs(M, tl);
     const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
-    const int per_it = tl ? 4 + coarse_cycle_kernels(M->coarse) : 3;  // kernels per iteration
+    const bool em = sizeof(T) == 8 ? M->em64 : M->em32;
+    T* Y = reinterpret_cast<T*>(M->d_Y);
+    const int eg = em ? em_grid<T, D2>(M) : 0;
+    const int per_it = (tl ? 4 + coarse_cycle_kernels(M->coarse) : 3) + (em ? 1 : 0);  // kernels per iteration
     pcg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
     if (tl) {
       coarse_cycle<T, D2>(M, CA, r, M->stream, scal + S_DONE);
@@ -1135,7 +1308,13 @@ struct Solver {
     if (!M->cap_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = M->cap_stream;
     auto iteration = [&](cudaStream_t st) {
-      pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+      if (em) {
+        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, p, M->d_fslot, M->nelt, Y,
+                                                                                   scal + S_DONE, M->d_status);
+        pcg_matvec_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Y, p, q, M->d_red, M->d_counter, scal);
+      } else {
+        pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
+      }
       if (tl) {
         pcg_update_tl_kernel<T, D2><<<nb, kNT, 0, st>>>(F, x, r, p, q, M->d_red, M->d_counter, scal);
         coarse_cycle<T, D2>(M, CA, r, st, scal + S_DONE);
@@ -1202,7 +1381,10 @@ struct Solver {
     const bool tl = M->coarse != nullptr && M->coarse->ready;
     match_graphs(M, tl);
     const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
-    const int per_it = tl ? 7 + 2 * coarse_cycle_kernels(M->coarse) : 5;  // kernels per iteration
+    const bool em = sizeof(T) == 8 ? M->em64 : M->em32;
+    T* Y = reinterpret_cast<T*>(M->d_Y);
+    const int eg = em ? em_grid<T, D2>(M) : 0;
+    const int per_it = (tl ? 7 + 2 * coarse_cycle_kernels(M->coarse) : 5) + (em ? 2 : 0);  // kernels per iteration
     bicg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, V, have_x, M->d_red, M->d_counter, scal);
     M->launches++;
     HDG_CUDA_TRY(cudaGetLastError());
@@ -1217,7 +1399,13 @@ struct Solver {
       } else {
         bicg_p_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
       }
-      bicg_v_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
+      if (em) {
+        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, V.ph, M->d_fslot, M->nelt, Y,
+                                                                                   scal + B_DONE, M->d_status);
+        bicg_v_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Y, V, M->d_red, M->d_counter, scal);
+      } else {
+        bicg_v_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
+      }
       if (tl) {
         bicg_s_flat_kernel<T><<<nb, kNT, 0, st>>>(nv, V, scal);
         coarse_cycle<T, D2>(M, CA, V.s, st, scal + B_DONE);
@@ -1225,7 +1413,13 @@ struct Solver {
       } else {
         bicg_s_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
       }
-      bicg_t_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
+      if (em) {
+        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, V.sh, M->d_fslot, M->nelt, Y,
+                                                                                   scal + B_DONE, M->d_status);
+        bicg_t_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Y, V, M->d_red, M->d_counter, scal);
+      } else {
+        bicg_t_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
+      }
       bicg_x_flat_kernel<T><<<nb, kNT, 0, st>>>(nv, V, M->d_red, M->d_counter, scal);
     };
     auto body = [&](cudaStream_t st, cudaGraphConditionalHandle h) {
@@ -1465,33 +1659,49 @@ struct Solver {
     int best = old;
     float best_t = 1e30f;
     FaceArgs F = face_args(M);
-    auto iteration = [&](int nb) {
-      pcg_matvec_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_p, M->d_q, M->d_red, M->d_counter,
-                                                               scal);
+    const int eg = em_grid<double, D2>(M), eg32 = em_grid<float, D2>(M);
+    double* Y = M->d_Y;
+    bool best_em = M->em64;
+    auto iteration = [&](int nb, bool em) {
+      if (em) {
+        em_apply_kernel<double, D2><<<eg, EmPass<double, D2>::NTHR, EmPass<double, D2>::SMEM, M->stream>>>(
+            M->d_C, M->d_p, M->d_fslot, M->nelt, Y, scal + S_DONE, M->d_status);
+        pcg_matvec_kernel<double, D2, true><<<nb, kNT, 0, M->stream>>>(F, Y, M->d_p, M->d_q, M->d_red, M->d_counter,
+                                                                       scal);
+      } else {
+        pcg_matvec_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_p, M->d_q, M->d_red, M->d_counter,
+                                                                 scal);
+      }
       pcg_update_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_BJ, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q,
                                                                M->d_red, M->d_counter, scal);
       pcg_dir_kernel<double><<<nb, kNT, 0, M->stream>>>(nv, M->d_z, M->d_p, scal);
     };
-    for (int cand : cands) {
-      M->face_blocks = cand;
-      const int nb = nblocks(M);
-      iteration(nb);  // warm-up
-      HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
-      for (int rep = 0; rep < 4; ++rep) iteration(nb);
-      HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
-      HDG_CUDA_TRY(cudaEventSynchronize(b));
-      float ms = 0.f;
-      HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
-      M->launches += 15;
-      if (ms < best_t) {
-        best_t = ms;
-        best = cand;
+    for (int form = 0; form < 2; ++form) {
+      const bool em = form == 1;
+      if (M->em_forced && em != M->em64) continue;
+      for (int cand : cands) {
+        M->face_blocks = cand;
+        const int nb = nblocks(M);
+        iteration(nb, em);  // warm-up
+        HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
+        for (int rep = 0; rep < 4; ++rep) iteration(nb, em);
+        HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
+        HDG_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        M->launches += em ? 20 : 15;
+        if (ms < best_t) {
+          best_t = ms;
+          best = cand;
+          best_em = em;
+        }
       }
     }
     M->face_blocks = best;
     // the same for the FP32 inner iteration (mixed precision), on FP32 copies of C^K and B^-1
     int best32 = M->face_blocks32;
     float best32_t = 1e30f;
+    bool best32_em = M->em32;
     {
       rc = ensure_workspace(M, true);
       if (rc) return rc;
@@ -1506,28 +1716,41 @@ struct Solver {
       HDG_CUDA_TRY(cudaMemsetAsync(M->d_x32, 0, sizeof(float) * nv, M->stream));
       HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
       float* q32 = reinterpret_cast<float*>(M->d_q);
-      auto iteration32 = [&](int nb) {
-        pcg_matvec_kernel<float, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C32, M->d_p32, q32, M->d_red, M->d_counter,
-                                                                scal);
+      float* Y32 = reinterpret_cast<float*>(M->d_Y);
+      auto iteration32 = [&](int nb, bool em) {
+        if (em) {
+          em_apply_kernel<float, D2><<<eg32, EmPass<float, D2>::NTHR, EmPass<float, D2>::SMEM, M->stream>>>(
+              M->d_C32, M->d_p32, M->d_fslot, M->nelt, Y32, scal + S_DONE, M->d_status);
+          pcg_matvec_kernel<float, D2, true><<<nb, kNT, 0, M->stream>>>(F, Y32, M->d_p32, q32, M->d_red,
+                                                                        M->d_counter, scal);
+        } else {
+          pcg_matvec_kernel<float, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C32, M->d_p32, q32, M->d_red,
+                                                                  M->d_counter, scal);
+        }
         pcg_update_kernel<float, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_BJ32, M->d_x32, M->d_r32, M->d_z32,
                                                                 M->d_p32, q32, M->d_red, M->d_counter, scal);
         pcg_dir_kernel<float><<<nb, kNT, 0, M->stream>>>(nv, M->d_z32, M->d_p32, scal);
       };
       const int keep = M->face_blocks;
-      for (int cand : cands) {
-        M->face_blocks = cand;
-        const int nb = nblocks(M);
-        iteration32(nb);
-        HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
-        for (int rep = 0; rep < 4; ++rep) iteration32(nb);
-        HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
-        HDG_CUDA_TRY(cudaEventSynchronize(b));
-        float ms = 0.f;
-        HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
-        M->launches += 15;
-        if (ms < best32_t) {
-          best32_t = ms;
-          best32 = cand;
+      for (int form = 0; form < 2; ++form) {
+        const bool em = form == 1;
+        if (M->em_forced && em != M->em32) continue;
+        for (int cand : cands) {
+          M->face_blocks = cand;
+          const int nb = nblocks(M);
+          iteration32(nb, em);
+          HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
+          for (int rep = 0; rep < 4; ++rep) iteration32(nb, em);
+          HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
+          HDG_CUDA_TRY(cudaEventSynchronize(b));
+          float ms = 0.f;
+          HDG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+          M->launches += em ? 20 : 15;
+          if (ms < best32_t) {
+            best32_t = ms;
+            best32 = cand;
+            best32_em = em;
+          }
         }
       }
       M->face_blocks = keep;
@@ -1535,8 +1758,10 @@ struct Solver {
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    const bool changed = best != old || best32 != M->face_blocks32;
+    const bool changed = best != old || best32 != M->face_blocks32 || best_em != M->em64 || best32_em != M->em32;
     M->face_blocks32 = best32;
+    M->em64 = best_em;
+    M->em32 = best32_em;
     if (changed) {
       cudaGraphExec_t* gs[] = {&M->graph64, &M->graph32, &M->wgraph64, &M->wgraph32, &M->graph_bicg,
                                &M->graph_bicg32, &M->wgraph_bicg, &M->wgraph_bicg32};
@@ -1551,6 +1776,8 @@ struct Solver {
       out->iter_ms = best_t / 4.0;
       out->face_blocks32 = best32;
       out->iter32_ms = best32_t < 1e29f ? best32_t / 4.0 : 0.0;
+      out->matvec_em64 = best_em ? 1 : 0;
+      out->matvec_em32 = best32_em ? 1 : 0;
     }
     return HDG_OK;
   }

@@ -22,6 +22,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
 
 #include "device_async.cuh"
 #include "device_common.cuh"
@@ -235,7 +238,281 @@ __global__ void mass_fp32_kernel(Args A, bool round_bf16) {
   A.out[e * A.np + p] = s;
 }
 
+// ------------------------------------------------------------------ split-BF16 masses
+// The masses of the HDG_MIXED_BF16 assembly, per element e
+//     out[e] = [ M_{kappa^-1} pairs (i <= j) | M_c pairs | f^K (the pairs (0, j), P_0 = 1) ]
+// (eq. 3.55 with g = |K| omega kappa^-1, |K| omega c and |K| omega f), FP32, on the tensor cores
+// from three-way BF16 splits of both operands: x = x0 + x1 + x2 with x0 the BF16 rounding of x
+// (taken in FP32) and x1, x2 the BF16 roundings of what the earlier parts leave.  The six products
+// a_i b_j with i + j <= 2 carry every term above 2^-24 of |a b|; they accumulate in FP32 in
+// tensor memory, so the masses carry FP32-level rounding (not the 2^-9 of single BF16 operands).
+//
+// Work per CTA (128 threads, persistent over tiles of 128 elements): jobs (coefficient, tile of
+// at most 256 pair columns); per job the nodes in chunks of 32 (two K = 16 steps): the threads
+// split their element's 32 coefficient values into sA (3 parts, K-major core layout, one 16-byte
+// store per part and 8 nodes) and copy the chunk's block of the split pair-product table (built
+// once per mesh on the host, L2-resident) into sB; one thread issues the 2 x 6 MMAs and commits
+// them to an mbarrier; the next chunk waits for them (bounded wait).  After the last chunk each
+// warp reads its 32 accumulator lanes.  Two CTAs per SM overlap one's split with the other's MMAs.
+namespace m3 {
+constexpr int KC = 32;                          // nodes per chunk
+constexpr int NTMAX = 256;                      // pair columns per job (accumulator columns)
+constexpr int kPartA = 128 * KC * 2;            // bytes of one BF16 part of the A chunk
+constexpr int kBlockBytes = 3 * NTMAX * KC * 2; // stride of the (tile, chunk) blocks of the table
+constexpr int kSmem = 3 * kPartA + kBlockBytes;
+
+struct Args {
+  const double *kappa, *c, *f, *geo, *w;
+  const unsigned char* B;  // [ntile][nchunk] blocks: [3 parts][rows_t][KC] BF16, K-major core layout
+  float* out;              // [nelt][ostride]
+  int32_t* status;
+  int64_t nelt;
+  int nq, n, np, nchunk, ntile, ostride;
+};
+
+__host__ __device__ inline int tile_rows(int np, int t) { return round16(np - t * NTMAX < NTMAX ? np - t * NTMAX : NTMAX); }
+
+// x = x0 + x1 + x2 (BF16 parts of the FP32 rounding of x)
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& x0, __nv_bfloat16& x1, __nv_bfloat16& x2) {
+  const float xf = (float)x;
+  x0 = __float2bfloat16_rn(xf);
+  const float r1 = xf - __bfloat162float(x0);
+  x1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(x1);
+  x2 = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) mass3_tc_kernel(Args A) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;               // [3][128][KC]
+  unsigned char* sB = smem + 3 * kPartA;  // [3][rows][KC]
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(NTMAX)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init(&bar, 1);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  const int64_t ntiles_e = (A.nelt + 127) / 128;
+  const int njobs = 2 * A.ntile + 1;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int64_t et = blockIdx.x; et < ntiles_e && !failed; et += gridDim.x) {
+    const int64_t e = et * 128 + tid;  // this thread's element (row of A, lane of the accumulator)
+    const bool act = e < A.nelt;
+    const double vol = act ? A.geo[e * kGeoStride + 25] : 0.0;
+    bool bad = false;
+    for (int j = 0; j < njobs && !failed; ++j) {
+      const int coef = j < A.ntile ? 0 : j < 2 * A.ntile ? 1 : 2;
+      const int t = coef < 2 ? j - coef * A.ntile : 0;
+      const int p0 = t * NTMAX;
+      const int pn = coef < 2 ? min(NTMAX, A.np - p0) : A.n;
+      const int N = round16(pn);
+      const int rows = tile_rows(A.np, t);
+      const int col0 = coef * A.np + p0;
+      const double* g = coef == 0 ? A.kappa : coef == 1 ? A.c : A.f;
+      const uint32_t idesc = idesc_bf16_f32(128, N);
+      for (int ch = 0; ch < A.nchunk && !failed; ++ch) {
+        // A chunk: split |K| omega_q g(p_q) of this thread's element, 8 nodes per 16-byte store
+#pragma unroll
+        for (int kg = 0; kg < KC / 8; ++kg) {
+          uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            __nv_bfloat16 h[2], m_[2], l[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              const int q = ch * KC + kg * 8 + u + v;
+              double a = 0.0;
+              if (act && q < A.nq) {
+                const double gv = g[e * A.nq + q];
+                if (coef == 0) {
+                  if (!(gv > 0.0) || !isfinite(gv)) bad = true;
+                  a = vol * A.w[q] / (gv > 0.0 ? gv : 1.0);
+                } else {
+                  if (!isfinite(gv) || (coef == 1 && !(gv >= 0.0))) bad = true;
+                  a = vol * A.w[q] * gv;
+                }
+              }
+              split3(a, h[v], m_[v], l[v]);
+            }
+            w0[u / 2] = pack2(h[0], h[1]);
+            w1[u / 2] = pack2(m_[0], m_[1]);
+            w2[u / 2] = pack2(l[0], l[1]);
+          }
+          const uint32_t off = kmajor_offset(tid, kg * 8, KC);
+          *reinterpret_cast<uint4*>(sA + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+          *reinterpret_cast<uint4*>(sA + kPartA + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+          *reinterpret_cast<uint4*>(sA + 2 * kPartA + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        }
+        // B chunk: the table block of (tile t, chunk ch), rows x KC per part
+        {
+          const uint4* src = reinterpret_cast<const uint4*>(A.B + (size_t)(t * A.nchunk + ch) * kBlockBytes);
+          uint4* dst = reinterpret_cast<uint4*>(sB);
+          const int nvec = 3 * rows * KC * 2 / 16;
+          for (int i = tid; i < nvec; i += kThreads) dst[i] = __ldg(src + i);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async proxy
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+          // the small products first: (a2 b0), (a1 b1), (a0 b2), (a1 b0), (a0 b1), (a0 b0)
+          const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+          for (int ks = 0; ks < KC / 16; ++ks)
+#pragma unroll
+            for (int pr = 0; pr < 6; ++pr) {
+              const uint64_t da = smem_desc(sA + pa[pr] * kPartA + ks * 256, 128, (KC / 8) * 128);
+              const uint64_t db = smem_desc(sB + pb[pr] * rows * KC * 2 + ks * 256, 128, (KC / 8) * 128);
+              mma_bf16(tmem, da, db, idesc, ch > 0 || ks > 0 || pr > 0);
+            }
+          mma_commit(&bar);
+        }
+        __syncwarp();
+        const bool ok = mbar_wait(&bar, phase, kWaitPolls);
+        if (__syncthreads_or(!ok)) {  // the same decision on every thread
+          if (tid == 0) atomicAdd(A.status + 6, 1);
+          failed = true;
+          break;
+        }
+        phase ^= 1u;
+        fence_after();
+      }
+      if (failed) break;
+      // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31 (its threads' elements)
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (act) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c0 + c < pn) A.out[e * A.ostride + col0 + c0 + c] = v[c];
+        }
+      }
+      fence_before();
+      __syncthreads();  // every lane read before the next job's MMAs overwrite the accumulator
+      fence_after();
+    }
+    if (act && bad) atomicAdd(A.status + 1, 1);
+  }
+  if (failed) mbar_wait(&bar, phase, kWaitPolls);  // the MMAs in flight, once more (bounded)
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NTMAX) : "memory");
+}
+}  // namespace m3
+
 }  // namespace tcm
+
+// The split pair-product table of the current volume rule (host, once per mesh): per pair tile
+// and node chunk, the three BF16 parts of P_i(p_q) P_j(p_q) in the K-major core layout.
+static int ensure_mass3_table(hdg_mesh* M) {
+  using namespace tcm;
+  const Tables& T = M->tab;
+  const int n = T.n, nq = T.nq, np = n * (n + 1) / 2;
+  const int ntile = (np + m3::NTMAX - 1) / m3::NTMAX, nchunk = (nq + m3::KC - 1) / m3::KC;
+  if (M->d_mass3B && M->mass3_rule == T.rule) return HDG_OK;
+  if (M->d_mass3B) {
+    cudaFree(M->d_mass3B);
+    M->d_mass3B = nullptr;
+  }
+  std::vector<int> pi, pj;
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) {
+      pi.push_back(i);
+      pj.push_back(j);
+    }
+  std::vector<uint16_t> h((size_t)ntile * nchunk * m3::kBlockBytes / 2, 0);
+  auto bf16_bits = [](float x) {  // round to nearest even (the table entries are finite)
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+  };
+  auto bf16_val = [](uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+  };
+  for (int t = 0; t < ntile; ++t) {
+    const int rows = m3::tile_rows(np, t);
+    for (int ch = 0; ch < nchunk; ++ch) {
+      uint16_t* blk = h.data() + (size_t)(t * nchunk + ch) * m3::kBlockBytes / 2;
+      for (int r = 0; r < rows; ++r) {
+        const int p = t * m3::NTMAX + r;
+        for (int kk = 0; kk < m3::KC; ++kk) {
+          const int q = ch * m3::KC + kk;
+          float x = 0.f;
+          if (p < np && q < nq) x = (float)(T.P[(size_t)q * n + pi[p]] * T.P[(size_t)q * n + pj[p]]);
+          const uint16_t b0 = bf16_bits(x);
+          const float r1 = x - bf16_val(b0);
+          const uint16_t b1 = bf16_bits(r1);
+          const uint16_t b2 = bf16_bits(r1 - bf16_val(b1));
+          const size_t off = (((size_t)(r >> 3) * (m3::KC >> 3) + (kk >> 3)) * 128 + (r & 7) * 16 + (kk & 7) * 2) / 2;
+          blk[off] = b0;
+          blk[(size_t)rows * m3::KC + off] = b1;
+          blk[(size_t)2 * rows * m3::KC + off] = b2;
+        }
+      }
+    }
+  }
+  HDG_CUDA_TRY(cudaMalloc(&M->d_mass3B, h.size() * 2));
+  HDG_CUDA_TRY(cudaMemcpy(M->d_mass3B, h.data(), h.size() * 2, cudaMemcpyHostToDevice));
+  M->mass3_rule = T.rule;
+  return HDG_OK;
+}
+
+int mass3_stride(int k) {
+  const int n = d3_of(k), np = n * (n + 1) / 2;
+  return (2 * np + n + 3) / 4 * 4;
+}
+
+int mass3_contraction(hdg_mesh* M, float* out) {
+  using namespace tcm;
+  int rc = ensure_mass3_table(M);
+  if (rc) return rc;
+  const int n = M->tab.n, np = n * (n + 1) / 2;
+  m3::Args a;
+  a.kappa = M->kappa;
+  a.c = M->c;
+  a.f = M->f;
+  a.geo = M->d_geo;
+  a.w = M->dt.vol_w;
+  a.B = reinterpret_cast<const unsigned char*>(M->d_mass3B);
+  a.out = out;
+  a.status = M->d_status;
+  a.nelt = M->nelt;
+  a.nq = M->tab.nq;
+  a.n = n;
+  a.np = np;
+  a.nchunk = (a.nq + m3::KC - 1) / m3::KC;
+  a.ntile = (np + m3::NTMAX - 1) / m3::NTMAX;
+  a.ostride = mass3_stride(M->k);
+  // at least 80 KB per CTA, so that at most two CTAs (2 x 256 tensor-memory columns) share an SM
+  const size_t req = std::max<size_t>(m3::kSmem, 80 * 1024);
+  HDG_CUDA_TRY(cudaFuncSetAttribute(m3::mass3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)req));
+  const int64_t tiles = (M->nelt + 127) / 128;
+  const int grid = (int)std::min<int64_t>(tiles, 2 * 152);
+  HDG_CUDA_TRY(cudaMemsetAsync(M->d_status + 6, 0, sizeof(int32_t), M->stream));
+  m3::mass3_tc_kernel<<<grid, kThreads, req, M->stream>>>(a);
+  M->launches++;
+  HDG_CUDA_TRY(cudaGetLastError());
+  return HDG_OK;
+}
 
 int mass_contraction(hdg_mesh* M, const double* g, int mode, float* out) {
   using namespace tcm;
@@ -281,6 +558,24 @@ int mass_contraction(hdg_mesh* M, const double* g, int mode, float* out) {
 }
 
 }  // namespace hdg
+
+extern "C" int hdg_mixed_masses(hdg_mesh* mesh, float* out, int* stride) {
+  if (!mesh) return hdg::fail(HDG_ERR_ARG, "NULL mesh");
+  if (mesh->k < 1 || mesh->tab.rule != HDG_RULE_CONICAL)
+    return hdg::fail(HDG_ERR_UNSUPPORTED, "the split-BF16 masses are built for k >= 1 on the conical volume rule");
+  if (stride) *stride = hdg::mass3_stride(mesh->k);
+  if (!out) return HDG_OK;
+  if (!mesh->kappa) return hdg::fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
+  HDG_CUDA_TRY(cudaMemsetAsync(mesh->d_status + 1, 0, sizeof(int32_t), mesh->stream));
+  int rc = hdg::mass3_contraction(mesh, out);
+  if (rc) return rc;
+  int32_t st[7];
+  HDG_CUDA_TRY(cudaMemcpyAsync(st, mesh->d_status, sizeof(st), cudaMemcpyDeviceToHost, mesh->stream));
+  HDG_CUDA_TRY(cudaStreamSynchronize(mesh->stream));
+  if (st[6]) return hdg::fail(HDG_ERR_CUDA, "tensor-core contraction: an MMA did not complete within the wait limit");
+  if (st[1]) return hdg::fail(HDG_ERR_COEFF, std::to_string(st[1]) + " element(s) with kappa <= 0, c < 0 or non-finite data");
+  return HDG_OK;
+}
 
 extern "C" int hdg_mass_contraction(hdg_mesh* mesh, const double* g, int mode, float* out) {
   if (!mesh || !g || !out) return hdg::fail(HDG_ERR_ARG, "NULL argument");

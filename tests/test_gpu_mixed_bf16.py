@@ -1,0 +1,164 @@
+"""The HDG_MIXED_BF16 assembly: the volume masses M_{kappa^-1}, M_c and f^K (eq. 3.55-3.56,
+Section 3 "Source terms") as one tensor-core contraction from three-way BF16 splits of both
+operands, then the double-float condensation of HDG_DF32 from them.
+
+Bars.
+* Masses against the oracle's literal eq. 3.55 sums, entry by entry: each operand x is carried as
+  x0 + x1 + x2 with x0 the BF16 rounding of fl32(x) and x1, x2 the BF16 roundings of the rest, so
+  |x - (x0 + x1 + x2)| <= 2^-24 |x| (float rounding) + 2^-24 |x| (the third part's rounding); the
+  dropped products a_i b_j with i + j > 2 are below 3 2^-24 |a b|; the FP32 accumulation of the
+  6 nq products adds at most 6 nq 2^-24 of the sum of their magnitudes.  So
+      |err_ij| <= (6 nq + 7) 2^-24 sum_q |vol w_q g_q P_i P_j|,
+  computed from the oracle's tables (the same bound for f^K with g = f).
+* The condensed blocks, the solution and the discretisation errors: the masses differ from the
+  exact ones by FP32-level rounding, which the condensation carries into C^K amplified by the
+  conditioning of M and S (a few units on these meshes); measured C^K 2.6e-7 (k = 1) to 2.4e-6
+  (k = 4) normwise, the fields 2.5e-8 to 4.1e-7.  Bars: C^K and C_f^K 1e-5, the solution fields
+  2e-6 (reaction-diffusion; 2e-5 and 5e-6 with convection, whose LU of S_u has no symmetric
+  structure to lean on), the errors of eq. 10.1 to 1e-3 of their values (the discretisation
+  errors are 1e-3 to 1e-6, so the split-BF16 rounding does not show in them).
+"""
+import numpy as np
+import pytest
+
+from oracle import convection as cv
+from oracle import hdg as ohdg
+from oracle.geometry import ExpandedMesh
+from workloads import get_problem
+
+from hdg_cases import gpu_setup, make_mesh, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1305_1489_gb300 import build
+    build()
+
+
+def _rd(k, s):
+    prob = get_problem("cube16_k3").at(k=k)
+    prob.jitter, prob.seed = 0.18, 7
+    return prob, make_mesh(prob, s=s)
+
+
+def _conv_mesh(prob, c, e, d, n):
+    from paper_1305_1489_gb300 import HDGMesh
+    M = HDGMesh(c, e, d, n, prob.k)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+    EX, EY, EZ = (t.cpu().numpy() for t in M.element_face_nodes())
+    tau = np.full((len(e), 4), prob.tau)
+    M.set_coefficients(dev(prob.kappa(X, Y, Z)), dev(prob.c(X, Y, Z)), dev(prob.f(X, Y, Z)), dev(tau),
+                       beta=dev(np.stack(prob.beta(X, Y, Z))), beta_faces=dev(np.stack(prob.beta(EX, EY, EZ))))
+    FX, FY, FZ = (t.cpu().numpy() for t in M.face_nodes())
+    M.set_boundary_data(dev(prob.uD(FX, FY, FZ)))
+    return M
+
+
+@pytest.mark.parametrize("k,s", [(1, 3), (2, 3), (3, 2), (4, 2)])
+def test_split_bf16_masses_within_bound(k, s):
+    prob, (c, e, d, n) = _rd(k, s)
+    M = gpu_setup(prob, c, e, d, n)
+    assert M.nelt % 128 != 0  # a ragged last tile of elements
+    got = M.mixed_masses().cpu().numpy()
+    nn = M.n
+    npair = nn * (nn + 1) // 2
+    assert got.shape[1] == (2 * npair + nn + 3) // 4 * 4
+    mesh = ExpandedMesh(c, e, d, n)
+    tab = ohdg.Tables(k)
+    X, Y, Z = ohdg.volume_nodes(mesh, tab)
+    kap, cq, fq = prob.kappa(X, Y, Z), prob.c(X, Y, Z), prob.f(X, Y, Z)
+    blk = ohdg.local_blocks(mesh, tab, kap, cq, fq)
+    iu = np.triu_indices(nn)
+    vol = mesh.volume[:, None]
+    eps = (6 * tab.w.size + 7) * 2.0 ** -24
+    aP = np.abs(tab.P)
+    for off, ref, g in ((0, blk["M_kinv"][:, iu[0], iu[1]], 1.0 / kap), (npair, blk["M_c"][:, iu[0], iu[1]], cq)):
+        mag = np.einsum("eq,q,qi,qj->eij", np.abs(vol * g), tab.w, aP, aP)[:, iu[0], iu[1]]
+        err = np.abs(got[:, off:off + npair] - ref)
+        assert np.all(err <= eps * mag + 1e-300), float((err / np.maximum(mag, 1e-300)).max())
+    magf = (np.abs(vol * fq) * tab.w[None, :]) @ aP
+    errf = np.abs(got[:, 2 * npair:2 * npair + nn] - blk["f"])
+    assert np.all(errf <= eps * magf + 1e-300), float((errf / np.maximum(magf, 1e-300)).max())
+    # far tighter than single BF16 operands (2^-9 per operand) would allow
+    assert rel(got[:, :npair], blk["M_kinv"][:, iu[0], iu[1]]) < 1e-5
+    M.close()
+
+
+def _check_pipeline(M, ref, prob, mesh_args, conv):
+    from paper_1305_1489_gb300 import HDG_FP64, HDG_MIXED_BF16
+    M.assemble_condense(HDG_MIXED_BF16)
+    Cm, Cf = (t.cpu().numpy() for t in M.condensed())
+    eC, eCf = rel(Cm, ref["CK"]), rel(Cf, ref["Cf"])
+    uhat, _, rr = M.solve_trace(rtol=1e-13, maxit=5000, precision=HDG_FP64)
+    assert rr <= 1e-13
+    q, u = M.recover(uhat)
+    us = M.postprocess(q, u)
+    got = dict(uhat=uhat.cpu().numpy(), q=q.cpu().numpy(), u=u.cpu().numpy(), ustar=us.cpu().numpy())
+    errs = {f: rel(got[f], ref[f]) for f in got if f in ref}
+    print(f"mixed_bf16 conv={conv} k={prob.k}: C {eC:.2e} Cf {eCf:.2e} " +
+          " ".join(f"{f} {v:.2e}" for f, v in errs.items()))
+    cbar, fbar = (2e-5, 5e-6) if conv else (1e-5, 2e-6)
+    assert eC < cbar and eCf < cbar
+    for f, v in errs.items():
+        assert v < fbar, f
+    if not conv:
+        mesh = ExpandedMesh(*mesh_args)
+        e_got = ohdg.errors(mesh, prob.k, got["q"], got["u"], got["uhat"], got["ustar"], prob)
+        e_ref = ohdg.errors(mesh, prob.k, ref["q"], ref["u"], ref["uhat"], ref["ustar"], prob)
+        for key in e_ref:
+            assert abs(e_got[key] - e_ref[key]) <= 1e-3 * e_ref[key], key
+
+
+@pytest.mark.parametrize("k,s", [(1, 3), (2, 3), (3, 2), (4, 1)])
+def test_mixed_bf16_reaction_diffusion_pipeline(k, s):
+    prob, mesh_args = _rd(k, s)
+    ref = ohdg.solve_problem(prob, *mesh_args)
+    M = gpu_setup(prob, *mesh_args)
+    _check_pipeline(M, ref, prob, mesh_args, conv=False)
+    M.close()
+
+
+@pytest.mark.parametrize("k,s", [(1, 3), (2, 2), (3, 1)])
+def test_mixed_bf16_convection_pipeline(k, s):
+    prob = get_problem("cube48_k2_conv").at(s=s, k=k)
+    mesh_args = make_mesh(prob)
+    ref = cv.solve_problem_conv(prob, *mesh_args)
+    M = _conv_mesh(prob, *mesh_args)
+    _check_pipeline(M, ref, prob, mesh_args, conv=True)
+    M.close()
+
+
+def test_mixed_bf16_refusals_and_coefficient_check():
+    from paper_1305_1489_gb300 import HDG_MIXED_BF16, HDG_RULE_SYMMETRIC, HDGError, HDGMesh
+    prob, (c, e, d, n) = _rd(2, 2)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    M = HDGMesh(c, e, d, n, 2)
+    M.set_volume_rule(HDG_RULE_SYMMETRIC)
+    X, Y, Z = (t.cpu().numpy() for t in M.volume_nodes())
+    M.set_coefficients(dev(prob.kappa(X, Y, Z)), dev(prob.c(X, Y, Z)), dev(prob.f(X, Y, Z)), None)
+    with pytest.raises(HDGError) as ei:
+        M.assemble_condense(HDG_MIXED_BF16)
+    assert ei.value.code == 9  # HDG_ERR_UNSUPPORTED
+    M.close()
+    prob0 = get_problem("cube16_k3").at(k=0)
+    M0 = gpu_setup(prob0, c, e, d, n)
+    with pytest.raises(HDGError) as ei:
+        M0.assemble_condense(HDG_MIXED_BF16)
+    assert ei.value.code == 9
+    M0.close()
+    # a non-positive kappa is reported by the contraction like the other assemblies report it
+    M2 = gpu_setup(prob, c, e, d, n)
+    X, Y, Z = (t.cpu().numpy() for t in M2.volume_nodes())
+    kap = prob.kappa(X, Y, Z).copy()
+    kap[3, 5] = -1.0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()  # noqa: E731
+    kt, ct, ft = dev(kap), dev(prob.c(X, Y, Z)), dev(prob.f(X, Y, Z))
+    M2.set_coefficients(kt, ct, ft, None)
+    with pytest.raises(HDGError) as ei:
+        M2.assemble_condense(HDG_MIXED_BF16)
+    assert ei.value.code == 8  # HDG_ERR_COEFF
+    M2.close()
