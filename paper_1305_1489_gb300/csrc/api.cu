@@ -96,7 +96,7 @@ static void release(hdg_mesh* M) {
                   M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
                   M->d_p32, M->d_q32, M->d_bicg, M->d_fverts, M->d_Tproj, M->d_norm, M->d_bicg32, M->d_Y,
-                  M->d_mass3B, M->d_mass3, M->d_fslot};
+                  M->d_mass3B, M->d_mass3, M->d_fslot, M->d_Y32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);

@@ -140,11 +140,14 @@ struct hdg_mesh {
   int face_blocks32 = 1216;       // the same for the FP32 inner iterations
   int grid_cap = 0;               // > 0: cap on the grids of the coarse-level kernels (HDG_FACE_BLOCKS)
   // form of the operator H x in the solve loops: element-major pass + face sum (true) or one
-  // face-major pass (false), per precision; hdg_autotune measures both unless HDG_MATVEC fixed it
-  bool em64 = true, em32 = true;
+  // face-major pass (false), per precision; hdg_autotune measures both unless HDG_MATVEC fixed it.
+  // FP64 defaults to the face-major form, the one its residual checks use (the FP64 product is
+  // bound by the FP64 pipe, where the element pass gains nothing), FP32 to the element pass
+  bool em64 = false, em32 = true;
   bool em_forced = false;
   int graphs_em = -1;             // (em64, em32) of the cached graphs
-  double* d_Y = nullptr;          // [nfc][2][d2] element-pass output per face side (FP64 or FP32 view)
+  double* d_Y = nullptr;          // [2][nvp] element-pass output per face side, FP64 ...
+  float* d_Y32 = nullptr;         // ... and FP32 (nvp = nfc d2 rounded up to 4)
   // HDG_MIXED_BF16 assembly: the split pair-product table of the tensor-core contraction (for
   // the volume rule mass3_rule) and the per-element FP32 masses [nelt][mass3_stride(k)]
   void* d_mass3B = nullptr;

@@ -150,12 +150,14 @@ int build_mesh(hdg_mesh* M, const double* coords, const int32_t* elems, const in
   HDG_CUDA_TRY(cudaMemcpy(M->d_owner, own.data(), sizeof(int32_t) * 2 * nfc, cudaMemcpyHostToDevice));
   HDG_CUDA_TRY(cudaMemcpy(M->d_ftype, ftype.data(), sizeof(int32_t) * nfc, cudaMemcpyHostToDevice));
   // fslot[4 K + l] = 2 f + side: face f of element K and which of its owners K is (the
-  // element pass of the trace operator writes its rows to that side of the face)
+  // element pass of the trace operator writes its rows to that side of the face); -(2 f +
+  // side) - 1 on Dirichlet faces, whose rows the trace system does not have
   std::vector<int32_t> fslot(4 * nelt);
   for (int64_t K = 0; K < nelt; ++K)
     for (int l = 0; l < 4; ++l) {
       const int32_t f = M->h_facebyele[4 * K + l];
-      fslot[4 * K + l] = 2 * f + (own[2 * f] == (int32_t)(4 * K + l) ? 0 : 1);
+      const int32_t v = 2 * f + (own[2 * f] == (int32_t)(4 * K + l) ? 0 : 1);
+      fslot[4 * K + l] = ftype[f] == 1 ? -v - 1 : v;
     }
   HDG_CUDA_TRY(cudaMalloc(&M->d_fslot, sizeof(int32_t) * 4 * nelt));
   HDG_CUDA_TRY(cudaMemcpy(M->d_fslot, fslot.data(), sizeof(int32_t) * 4 * nelt, cudaMemcpyHostToDevice));

@@ -470,16 +470,116 @@ __global__ void __launch_bounds__(32) recover_df_multi_kernel(const double* __re
   }
 }
 
+// The same recovery for small elements without staging the records: every record entry is read
+// once, by the lane of its row (the lanes of a group read consecutive entries) or by the whole
+// group (a pivot, the normals), so each lane loads its entries straight from global memory
+// (read-only, streaming) and no shared memory holds them.  Blocks of kRdWarps warps, each warp
+// on E = 32 / n elements as in recover_df_multi_kernel; without the 22 KB of staged records per
+// warp, the SM holds several times more warps to hide the memory and shuffle latencies of the
+// triangular solves.
+constexpr int kRdWarps = 4;
+
+__device__ __forceinline__ df ldcs_df(const df* p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  return df_make(v.x, v.y);
+}
+
+template <int K>
+__global__ void __launch_bounds__(32 * kRdWarps) recover_df_direct_kernel(const double* __restrict__ rec,
+                                                                        const int32_t* __restrict__ fbe,
+                                                                        const double* __restrict__ uhat, int64_t nelt,
+                                                                        double* __restrict__ q, double* __restrict__ u) {
+  using D = Dims<K>;
+  constexpr int n = D::n, m = D::m, d2 = D::d2, E = 32 / n;
+  static_assert(n <= 16, "one lane group of n lanes per element");
+  __shared__ df suh_[kRdWarps][E][m], su_[kRdWarps][E][n];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  df(*suh)[m] = suh_[w];
+  df(*su)[n] = su_[w];
+  const int g = lane / n < E ? lane / n : E - 1;  // the lanes past E n shadow the last group
+  const int l = lane - (lane / n) * n;
+  const int64_t K0 = ((int64_t)blockIdx.x * kRdWarps + w) * E;
+  if (K0 >= nelt) return;  // whole warps only: no block-wide barrier below
+  const int ne = (int)((nelt - K0) < E ? (nelt - K0) : E);  // elements of this warp
+  const bool act = lane / n < ne;
+  const int64_t Ke = K0 + (g < ne ? g : ne - 1);  // a shadow or idle group repeats a valid element
+  const int base = g * n;  // first lane of the group
+  for (int t = lane; t < ne * m; t += 32) {
+    const int e = t / m, r = t - e * m;
+    suh[e][r] = df_from_double(__ldg(uhat + (int64_t)__ldg(fbe + (K0 + e) * 4 + r / d2) * d2 + (r % d2)));
+  }
+  __syncwarp();
+  const df* HT = reinterpret_cast<const df*>(rec) + Ke * (int64_t)D::rec;
+  const df* VT = HT + n * (m + 1);
+  const df* WT = VT + n * m;
+  const df* Us = WT + 3 * n * n;
+  const df* UM = Us + D::tri;
+  const df* nrm = UM + D::tri;
+  const int ge = g < ne ? g : ne - 1;
+  // u = U_s^-1 (H u_dK + h)
+  dacc x = dacc_from(ldcs_df(HT + m * n + l));
+#pragma unroll 8
+  for (int r = 0; r < m; ++r) dacc_mac(x, ldcs_df(HT + r * n + l), suh[ge][r]);
+#pragma unroll
+  for (int i = n - 1; i >= 0; --i) {
+    const df* col = Us + i * (i + 1) / 2;
+    const df ci = ldcs_df(col + i);
+    const df cl = l < i ? ldcs_df(col + l) : df_make(0.f, 0.f);
+    const df xi = df_mul(shfl_df(dacc_result(x), base + i), ci);
+    if (l < i) dacc_msub(x, cl, xi);
+    else if (l == i) x = dacc_from(xi);
+  }
+  const df ui = dacc_result(x);
+  su[ge][l] = ui;
+  if (act) u[Ke * n + l] = df_to_double(ui);
+  __syncwarp();
+  // q_* = U_M^-1 (W_* u - V (n_* o u_dK))
+  dacc z[3] = {dacc_zero(), dacc_zero(), dacc_zero()};
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    const df uc = su[ge][c];
+    dacc_mac(z[0], ldcs_df(WT + (0 * n + c) * n + l), uc);
+    dacc_mac(z[1], ldcs_df(WT + (1 * n + c) * n + l), uc);
+    dacc_mac(z[2], ldcs_df(WT + (2 * n + c) * n + l), uc);
+  }
+#pragma unroll
+  for (int fl = 0; fl < 4; ++fl) {
+    dacc wv = dacc_zero();
+#pragma unroll
+    for (int a2 = 0; a2 < d2; ++a2) dacc_mac(wv, ldcs_df(VT + (fl * d2 + a2) * n + l), suh[ge][fl * d2 + a2]);
+    const df wr = dacc_result(wv);
+    dacc_msub(z[0], ldcs_df(nrm + 3 * fl + 0), wr);
+    dacc_msub(z[1], ldcs_df(nrm + 3 * fl + 1), wr);
+    dacc_msub(z[2], ldcs_df(nrm + 3 * fl + 2), wr);
+  }
+#pragma unroll
+  for (int i = n - 1; i >= 0; --i) {
+    const df* col = UM + i * (i + 1) / 2;
+    const df inv = ldcs_df(col + i);
+    const df uli = l < i ? ldcs_df(col + l) : df_make(0.f, 0.f);
+    df xi[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) xi[v] = df_mul(shfl_df(dacc_result(z[v]), base + i), inv);
+    if (l < i) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) dacc_msub(z[v], uli, xi[v]);
+    } else if (l == i) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) z[v] = dacc_from(xi[v]);
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) q[(Ke * 3 + v) * n + l] = df_to_double(dacc_result(z[v]));
+  }
+}
+
 template <int K>
 static cudaError_t launch_recover_df(hdg_mesh* M, const double* uhat, double* q, double* u) {
   if constexpr (Dims<K>::n <= 10) {
-    constexpr int E = 32 / Dims<K>::n;
-    const int smem = (int)(sizeof(df) * Dims<K>::rec * E);
-    cudaError_t e =
-        cudaFuncSetAttribute(recover_df_multi_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    recover_df_multi_kernel<K><<<(unsigned)((M->nelt + E - 1) / E), 32, smem, M->stream>>>(
-        M->d_rec, M->d_facebyele, uhat, M->nelt, q, u, M->d_status);
+    constexpr int E = 32 / Dims<K>::n, PER = E * kRdWarps;
+    recover_df_direct_kernel<K><<<(unsigned)((M->nelt + PER - 1) / PER), 32 * kRdWarps, 0, M->stream>>>(
+        M->d_rec, M->d_facebyele, uhat, M->nelt, q, u);
     return cudaSuccess;
   } else {
     const int smem = (int)(sizeof(df) * Dims<K>::rec);

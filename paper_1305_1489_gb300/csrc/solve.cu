@@ -17,6 +17,7 @@
 // batches of iterations are captured in a CUDA graph and the host reads the convergence flag
 // after each replay.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <cmath>
 #include <vector>
@@ -214,10 +215,12 @@ __device__ __forceinline__ T face_apply(const T* __restrict__ C, const T* __rest
 // ------------------------------------------------------------------ element-major operator
 // The same product H x in two passes (eq. 6.5 summed element by element):
 //   element pass  for every element K and row r = l d2 + a of C^K, the sum_s C^K[r][s] x_dK[s]
-//                 goes to Y[f][side][a], f the element's face l and side which of the face's
-//                 two owners K is (the per-mesh table fslot = 2 f + side);
-//   face sum      (H x)_e[a] = Y[e][0][a] + Y[e][1][a], fused into the kernel that consumes
-//                 H x: a coalesced stream, no gather (a boundary face reads side 0 only).
+//                 goes to Y[side][f d2 + a], f the element's face l and side which of the
+//                 face's two owners K is (the per-mesh table fslot = 2 f + side, negative on
+//                 Dirichlet faces, whose rows are not stored);
+//   face sum      (H x) = Y[0] + Y[1], a flat 16-byte-vectorised stream fused with the dot
+//                 products that consume H x (Y stays 0 where nothing is stored: Dirichlet
+//                 faces, and side 1 of the boundary faces, which have one owner).
 // The element pass is a persistent streaming kernel: the C^K of a group of EB consecutive
 // elements is one contiguous block, which one producer thread copies into a ring of NST
 // shared-memory stages with 1-D bulk copies (the tensor memory accelerator) completed on the
@@ -251,8 +254,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 template <typename T, int D2>
 __global__ void __launch_bounds__(EmPass<T, D2>::NTHR) em_apply_kernel(const T* __restrict__ C, const T* __restrict__ x,
                                                                        const int32_t* __restrict__ fslot, int64_t nelt,
-                                                                       T* __restrict__ Y, const double* done,
-                                                                       int32_t* status) {
+                                                                       int64_t nvp, T* __restrict__ Y,
+                                                                       const double* done, int32_t* status) {
   using P = EmPass<T, D2>;
   constexpr int m = P::m, EB = P::EB, NST = P::NST;
   constexpr int VW = 16 / sizeof(T);
@@ -297,11 +300,16 @@ __global__ void __launch_bounds__(EmPass<T, D2>::NTHR) em_apply_kernel(const T* 
     // the gather of x_dK is pipelined over the groups: the face number two groups ahead and
     // the value one group ahead are in flight while a group is computed, so that no iteration
     // waits on more than one memory latency
-    auto face_of = [&](int64_t g) -> int {  // 2 f + side of this thread's row of group g
+    constexpr int kNone = INT32_MIN;         // no row (past the last element)
+    auto face_of = [&](int64_t g) -> int {  // fslot of this thread's row of group g
       const int64_t K = g * EB + el;
-      return (lane_act && g < ngroups && K < nelt) ? __ldg(fslot + 4 * K + r / D2) : -1;
+      return (lane_act && g < ngroups && K < nelt) ? __ldg(fslot + 4 * K + r / D2) : kNone;
     };
-    auto x_of = [&](int fs) -> T { return fs >= 0 ? x[(int64_t)(fs >> 1) * D2 + (r % D2)] : (T)0; };
+    auto x_of = [&](int fs) -> T {
+      if (fs == kNone) return (T)0;
+      const int f2 = fs >= 0 ? fs : -fs - 1;  // 2 f + side
+      return x[(int64_t)(f2 >> 1) * D2 + (r % D2)];
+    };
     const int64_t G = gridDim.x;
     int fcur = face_of(blockIdx.x);
     T xn = x_of(fcur);
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(EmPass<T, D2>::NTHR) em_apply_kernel(const T* 
       asm volatile("bar.sync 1, %0;" ::"r"(32 * P::CW) : "memory");  // xb complete
       if (!mbar_wait(&full[s], (uint32_t)(it / NST) & 1u, kEmWaitPolls)) ++fails;
       const int64_t K = g * EB + el;
-      if (lane_act && K < nelt) {
+      if (lane_act && K < nelt && fs >= 0) {
         const V* row = reinterpret_cast<const V*>(ring + (size_t)s * EB * m * m + (size_t)(el * m + r) * m);
         const V* xr = reinterpret_cast<const V*>(xb + el * m);
         T acc0 = (T)0, acc1 = (T)0;
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(EmPass<T, D2>::NTHR) em_apply_kernel(const T* 
             acc1 = fma(cq.y, xq.y, acc1);
           }
         }
-        Y[(int64_t)fs * D2 + (r % D2)] = acc0 + acc1;
+        Y[(fs & 1) * nvp + (int64_t)(fs >> 1) * D2 + (r % D2)] = acc0 + acc1;
       }
       mbar_arrive(&empty[s]);
     }
@@ -364,21 +372,6 @@ static int em_grid(hdg_mesh* M) {
 }
 
 
-// (H x)_e entry a from the element pass: the face's two sides of Y (a boundary face, type != 0,
-// has one owner, so its side 1 holds nothing of this product)
-template <typename T, int D2>
-__device__ __forceinline__ T face_sum(const T* __restrict__ Y, const FaceArgs& F, int64_t e, int a) {
-  const T s0 = Y[(2 * e) * D2 + a];
-  return F.ftype[e] == 0 ? s0 + Y[(2 * e + 1) * D2 + a] : s0;
-}
-
-// (H x)_e entry a in one pass (face-major) or from Y of the element pass (EM)
-template <typename T, int D2, bool EM>
-__device__ __forceinline__ T face_op(const T* __restrict__ CY, const T* __restrict__ x, const FaceArgs& F,
-                                     int64_t e, int a) {
-  if constexpr (EM) return face_sum<T, D2>(CY, F, e, a);
-  else return face_apply<T, D2>(CY, x, F, e, a);
-}
 
 // row a of face e's block inverse times the face's d2 residual entries
 template <typename T, int D2>
@@ -596,8 +589,8 @@ __global__ void pcg_precond_kernel(FaceArgs F, const T* __restrict__ Binv, const
   }
 }
 
-// q = H p (free faces), alpha = rz / (p.q); with EM, C is Y of the element pass over p
-template <typename T, int D2, bool EM = false>
+// q = H p (free faces), alpha = rz / (p.q)
+template <typename T, int D2>
 __global__ void pcg_matvec_kernel(FaceArgs F, const T* __restrict__ C, const T* __restrict__ p, T* __restrict__ q,
                                   double* red, unsigned int* counter, double* scal) {
   if (scal[S_DONE] != 0.0) return;
@@ -605,7 +598,7 @@ __global__ void pcg_matvec_kernel(FaceArgs F, const T* __restrict__ C, const T* 
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const T qv = (F.ftype[T_.e] != 1) ? face_op<T, D2, EM>(C, p, F, T_.e, T_.a) : (T)0;
+    const T qv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, p, F, T_.e, T_.a) : (T)0;
     q[T_.t] = qv;
     v[0] = fma((double)p[T_.t], (double)qv, v[0]);
   }
@@ -807,8 +800,8 @@ __global__ void bicg_tl_kernel(FaceArgs F, CoarseArgs CA, const T* __restrict__ 
   }
 }
 
-// v = H ph;  alpha = rho / (rhat . v); with EM, C is Y of the element pass over ph
-template <typename T, int D2, bool EM = false>
+// v = H ph;  alpha = rho / (rhat . v)
+template <typename T, int D2>
 __global__ void bicg_v_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
@@ -816,7 +809,7 @@ __global__ void bicg_v_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const T vv = (F.ftype[T_.e] != 1) ? face_op<T, D2, EM>(C, V.ph, F, T_.e, T_.a) : (T)0;
+    const T vv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, V.ph, F, T_.e, T_.a) : (T)0;
     V.v[T_.t] = vv;
     v[0] = fma((double)V.rh[T_.t], (double)vv, v[0]);
   }
@@ -847,8 +840,8 @@ __global__ void bicg_s_kernel(FaceArgs F, const T* __restrict__ Binv, BicgVecs<T
   }
 }
 
-// t = H sh;  omega = (t.s) / (t.t); with EM, C is Y of the element pass over sh
-template <typename T, int D2, bool EM = false>
+// t = H sh;  omega = (t.s) / (t.t)
+template <typename T, int D2>
 __global__ void bicg_t_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V, double* red,
                               unsigned int* counter, double* scal) {
   if (scal[B_DONE] != 0.0) return;
@@ -856,7 +849,7 @@ __global__ void bicg_t_kernel(FaceArgs F, const T* __restrict__ C, BicgVecs<T> V
   for (int64_t tile = blockIdx.x; tile < ntiles<D2>(F); tile += gridDim.x) {
     Tile<D2> T_(F, tile);
     if (!T_.act) continue;
-    const T tv = (F.ftype[T_.e] != 1) ? face_op<T, D2, EM>(C, V.sh, F, T_.e, T_.a) : (T)0;
+    const T tv = (F.ftype[T_.e] != 1) ? face_apply<T, D2>(C, V.sh, F, T_.e, T_.a) : (T)0;
     V.t[T_.t] = tv;
     v[0] = fma((double)tv, (double)V.s[T_.t], v[0]);
     v[1] = fma((double)tv, (double)tv, v[1]);
@@ -1019,6 +1012,95 @@ __global__ void bicg_x_flat_kernel(int64_t nv, BicgVecs<T> V, double* red, unsig
     if (out[1] <= scal[B_TOL2] || scal[B_ITERS] >= scal[B_MAXIT]) scal[B_DONE] = 1.0;
   }
 }
+// The face sums of the element pass (H x = Y[0] + Y[1], 0 on Dirichlet rows), flat and fused
+// with the reductions of the kernels they replace: q = H p with p.q and alpha (PCG), v = H ph
+// with rhat.v and alpha, t = H sh with t.s, t.t and omega (BiCGStab).
+// out = Y[0] + Y[1];  v[0] += a.out;  with NS = 2 also v[1] += out.out
+template <typename T, int NS>
+__device__ __forceinline__ void em_sum_loop(int64_t nv, int64_t nvp, const T* __restrict__ Y, T* __restrict__ out,
+                                            const T* __restrict__ a, double (&v)[NS]) {
+  using VT = typename Vec16<T>::V;
+  const T* Y1 = Y + nvp;
+  flat_loop<T>(nv, [&](int64_t i, bool vec) {
+    if (vec) {
+      const VT y0 = HDG_LD(Y), y1 = HDG_LD(Y1), av = HDG_LD(a);
+      const T *p0 = reinterpret_cast<const T*>(&y0), *p1 = reinterpret_cast<const T*>(&y1),
+              *pa = reinterpret_cast<const T*>(&av);
+      VT o;
+      T* ow = reinterpret_cast<T*>(&o);
+#pragma unroll
+      for (int w = 0; w < Vec16<T>::W; ++w) {
+        ow[w] = p0[w] + p1[w];
+        v[0] = fma((double)pa[w], (double)ow[w], v[0]);
+        if (NS == 2) v[NS - 1] = fma((double)ow[w], (double)ow[w], v[NS - 1]);
+      }
+      HDG_ST(out, o);
+    } else {
+      const T o = Y[i] + Y1[i];
+      out[i] = o;
+      v[0] = fma((double)a[i], (double)o, v[0]);
+      if (NS == 2) v[NS - 1] = fma((double)o, (double)o, v[NS - 1]);
+    }
+  });
+}
+
+// y = H x from the element pass alone (hdg_trace_apply in the element form)
+template <typename T>
+__global__ void em_sum_kernel(int64_t nv, int64_t nvp, const T* __restrict__ Y, T* __restrict__ y) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) y[i] = Y[i] + Y[nvp + i];
+}
+
+// q = H p from the element pass;  alpha = rz / (p.q)
+template <typename T>
+__global__ void pcg_matvec_em_kernel(int64_t nv, int64_t nvp, const T* __restrict__ Y, const T* __restrict__ p,
+                                     T* __restrict__ q, double* red, unsigned int* counter, double* scal) {
+  if (scal[S_DONE] != 0.0) return;
+  double v[1] = {0.0};
+  em_sum_loop<T, 1>(nv, nvp, Y, q, p, v);
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
+    scal[S_PQ] = out[0];
+    if (!(out[0] > 0.0)) {  // breakdown: H not SPD on the Krylov space
+      scal[S_BAD] = 1.0;
+      scal[S_DONE] = 1.0;
+      scal[S_ALPHA] = 0.0;
+    } else {
+      scal[S_ALPHA] = scal[S_RZ] / out[0];
+    }
+  }
+}
+
+// v = H ph from the element pass;  alpha = rho / (rhat . v)
+template <typename T>
+__global__ void bicg_v_em_kernel(int64_t nv, int64_t nvp, const T* __restrict__ Y, BicgVecs<T> V, double* red,
+                                 unsigned int* counter, double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  double v[1] = {0.0};
+  em_sum_loop<T, 1>(nv, nvp, Y, V.v, V.rh, v);
+  double out[1];
+  if (grid_reduce<1>(v, red, counter, out) && threadIdx.x == 0) {
+    if (out[0] == 0.0 || !isfinite(out[0])) {
+      scal[B_BAD] = 1.0;
+      scal[B_DONE] = 1.0;
+      scal[B_ALPHA] = 0.0;
+    } else {
+      scal[B_ALPHA] = scal[B_RHO] / out[0];
+    }
+  }
+}
+
+// t = H sh from the element pass;  omega = (t.s) / (t.t)
+template <typename T>
+__global__ void bicg_t_em_kernel(int64_t nv, int64_t nvp, const T* __restrict__ Y, BicgVecs<T> V, double* red,
+                                 unsigned int* counter, double* scal) {
+  if (scal[B_DONE] != 0.0) return;
+  double v[2] = {0.0, 0.0};
+  em_sum_loop<T, 2>(nv, nvp, Y, V.t, V.s, v);
+  double out[2];
+  if (grid_reduce<2>(v, red, counter, out) && threadIdx.x == 0) scal[B_OMEGA] = (out[1] > 0.0) ? out[0] / out[1] : 0.0;
+}
+
 #undef HDG_LD
 #undef HDG_ST
 
@@ -1167,6 +1249,13 @@ static void match_graphs(hdg_mesh* M, bool tl) {
 
 static int64_t bicg_stride(int64_t nv, int w) { return (nv + w - 1) / w * w; }
 
+// the element-pass output buffer of a precision
+template <typename T>
+static T* em_buf(hdg_mesh* M) {
+  if constexpr (sizeof(T) == 8) return reinterpret_cast<T*>(M->d_Y);
+  else return reinterpret_cast<T*>(M->d_Y32);
+}
+
 static int ensure_workspace(hdg_mesh* M, bool mixed) {
   const int64_t nv = M->nfc * M->tab.d2;
   if (!M->d_b) {
@@ -1182,7 +1271,13 @@ static int ensure_workspace(hdg_mesh* M, bool mixed) {
     HDG_CUDA_TRY(cudaMalloc(&M->d_scal, sizeof(double) * 2 * S_NSCAL));
     HDG_CUDA_TRY(cudaMalloc(&M->d_counter, sizeof(unsigned int) * 4));
     HDG_CUDA_TRY(cudaMemsetAsync(M->d_counter, 0, sizeof(unsigned int) * 4, M->stream));
-    HDG_CUDA_TRY(cudaMalloc(&M->d_Y, sizeof(double) * 2 * M->nfc * M->tab.d2));
+    // element-pass outputs [2 sides][nvp], FP64 and FP32: the entries that the pass never stores
+    // (Dirichlet rows, side 1 of the boundary faces) stay 0
+    const int64_t nvp = bicg_stride(M->nfc * M->tab.d2, 4);
+    HDG_CUDA_TRY(cudaMalloc(&M->d_Y, sizeof(double) * 2 * nvp));
+    HDG_CUDA_TRY(cudaMalloc(&M->d_Y32, sizeof(float) * 2 * nvp));
+    HDG_CUDA_TRY(cudaMemsetAsync(M->d_Y, 0, sizeof(double) * 2 * nvp, M->stream));
+    HDG_CUDA_TRY(cudaMemsetAsync(M->d_Y32, 0, sizeof(float) * 2 * nvp, M->stream));
     M->red_blocks = kMaxBlocks;
   }
   if (M->beta_q && !M->d_bicg) HDG_CUDA_TRY(cudaMalloc(&M->d_bicg, sizeof(double) * 4 * bicg_stride(nv, 2)));
@@ -1292,7 +1387,8 @@ struct Solver {
     match_graphs(M, tl);
     const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
     const bool em = sizeof(T) == 8 ? M->em64 : M->em32;
-    T* Y = reinterpret_cast<T*>(M->d_Y);
+    T* Y = em_buf<T>(M);
+    const int64_t nvp = bicg_stride(M->nfc * D2, 4);
     const int eg = em ? em_grid<T, D2>(M) : 0;
     const int per_it = (tl ? 4 + coarse_cycle_kernels(M->coarse) : 3) + (em ? 1 : 0);  // kernels per iteration
     pcg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, x, have_x, r, M->d_red, M->d_counter, scal);
@@ -1309,9 +1405,9 @@ struct Solver {
     cudaStream_t cs = M->cap_stream;
     auto iteration = [&](cudaStream_t st) {
       if (em) {
-        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, p, M->d_fslot, M->nelt, Y,
-                                                                                   scal + S_DONE, M->d_status);
-        pcg_matvec_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Y, p, q, M->d_red, M->d_counter, scal);
+        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, p, M->d_fslot, M->nelt, nvp,
+                                                                                   Y, scal + S_DONE, M->d_status);
+        pcg_matvec_em_kernel<T><<<nb, kNT, 0, st>>>(nv, nvp, Y, p, q, M->d_red, M->d_counter, scal);
       } else {
         pcg_matvec_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, p, q, M->d_red, M->d_counter, scal);
       }
@@ -1382,7 +1478,8 @@ struct Solver {
     match_graphs(M, tl);
     const CoarseArgs CA = tl ? coarse_args(M) : CoarseArgs{};
     const bool em = sizeof(T) == 8 ? M->em64 : M->em32;
-    T* Y = reinterpret_cast<T*>(M->d_Y);
+    T* Y = em_buf<T>(M);
+    const int64_t nvp = bicg_stride(M->nfc * D2, 4);
     const int eg = em ? em_grid<T, D2>(M) : 0;
     const int per_it = (tl ? 7 + 2 * coarse_cycle_kernels(M->coarse) : 5) + (em ? 2 : 0);  // kernels per iteration
     bicg_init_kernel<T, D2><<<nb, kNT, 0, M->stream>>>(F, C, rhs, V, have_x, M->d_red, M->d_counter, scal);
@@ -1400,9 +1497,9 @@ struct Solver {
         bicg_p_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
       }
       if (em) {
-        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, V.ph, M->d_fslot, M->nelt, Y,
-                                                                                   scal + B_DONE, M->d_status);
-        bicg_v_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Y, V, M->d_red, M->d_counter, scal);
+        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, V.ph, M->d_fslot, M->nelt,
+                                                                                   nvp, Y, scal + B_DONE, M->d_status);
+        bicg_v_em_kernel<T><<<nb, kNT, 0, st>>>(nv, nvp, Y, V, M->d_red, M->d_counter, scal);
       } else {
         bicg_v_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
       }
@@ -1414,9 +1511,9 @@ struct Solver {
         bicg_s_kernel<T, D2, false><<<nb, kNT, 0, st>>>(F, Binv, V, scal);
       }
       if (em) {
-        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, V.sh, M->d_fslot, M->nelt, Y,
-                                                                                   scal + B_DONE, M->d_status);
-        bicg_t_kernel<T, D2, true><<<nb, kNT, 0, st>>>(F, Y, V, M->d_red, M->d_counter, scal);
+        em_apply_kernel<T, D2><<<eg, EmPass<T, D2>::NTHR, EmPass<T, D2>::SMEM, st>>>(C, V.sh, M->d_fslot, M->nelt,
+                                                                                   nvp, Y, scal + B_DONE, M->d_status);
+        bicg_t_em_kernel<T><<<nb, kNT, 0, st>>>(nv, nvp, Y, V, M->d_red, M->d_counter, scal);
       } else {
         bicg_t_kernel<T, D2><<<nb, kNT, 0, st>>>(F, C, V, M->d_red, M->d_counter, scal);
       }
@@ -1660,14 +1757,15 @@ struct Solver {
     float best_t = 1e30f;
     FaceArgs F = face_args(M);
     const int eg = em_grid<double, D2>(M), eg32 = em_grid<float, D2>(M);
+    const int64_t nvp = bicg_stride(nv, 4);
     double* Y = M->d_Y;
     bool best_em = M->em64;
     auto iteration = [&](int nb, bool em) {
       if (em) {
         em_apply_kernel<double, D2><<<eg, EmPass<double, D2>::NTHR, EmPass<double, D2>::SMEM, M->stream>>>(
-            M->d_C, M->d_p, M->d_fslot, M->nelt, Y, scal + S_DONE, M->d_status);
-        pcg_matvec_kernel<double, D2, true><<<nb, kNT, 0, M->stream>>>(F, Y, M->d_p, M->d_q, M->d_red, M->d_counter,
-                                                                       scal);
+            M->d_C, M->d_p, M->d_fslot, M->nelt, nvp, Y, scal + S_DONE, M->d_status);
+        pcg_matvec_em_kernel<double><<<nb, kNT, 0, M->stream>>>(nv, nvp, Y, M->d_p, M->d_q, M->d_red, M->d_counter,
+                                                                scal);
       } else {
         pcg_matvec_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_p, M->d_q, M->d_red, M->d_counter,
                                                                  scal);
@@ -1716,13 +1814,13 @@ struct Solver {
       HDG_CUDA_TRY(cudaMemsetAsync(M->d_x32, 0, sizeof(float) * nv, M->stream));
       HDG_CUDA_TRY(cudaMemcpyAsync(scal, hs, sizeof(hs), cudaMemcpyHostToDevice, M->stream));
       float* q32 = reinterpret_cast<float*>(M->d_q);
-      float* Y32 = reinterpret_cast<float*>(M->d_Y);
+      float* Y32 = M->d_Y32;
       auto iteration32 = [&](int nb, bool em) {
         if (em) {
           em_apply_kernel<float, D2><<<eg32, EmPass<float, D2>::NTHR, EmPass<float, D2>::SMEM, M->stream>>>(
-              M->d_C32, M->d_p32, M->d_fslot, M->nelt, Y32, scal + S_DONE, M->d_status);
-          pcg_matvec_kernel<float, D2, true><<<nb, kNT, 0, M->stream>>>(F, Y32, M->d_p32, q32, M->d_red,
-                                                                        M->d_counter, scal);
+              M->d_C32, M->d_p32, M->d_fslot, M->nelt, nvp, Y32, scal + S_DONE, M->d_status);
+          pcg_matvec_em_kernel<float><<<nb, kNT, 0, M->stream>>>(nv, nvp, Y32, M->d_p32, q32, M->d_red, M->d_counter,
+                                                                 scal);
         } else {
           pcg_matvec_kernel<float, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C32, M->d_p32, q32, M->d_red,
                                                                   M->d_counter, scal);
@@ -1808,9 +1906,22 @@ struct Solver {
     return HDG_OK;
   }
 
+  // y = H x in the operator form of the FP64 solve loops (face-major, or element pass + sum)
   static int apply(hdg_mesh* M, const double* x, double* y) {
-    apply_kernel<D2><<<nblocks(M), kNT, 0, M->stream>>>(face_args(M), M->d_C, x, y);
-    M->launches++;
+    if (M->em64) {
+      int rc = ensure_workspace(M, false);
+      if (rc) return rc;
+      double* never = M->d_scal + 2 * S_NSCAL - 1;  // a scratch slot, 0: the pass always runs
+      HDG_CUDA_TRY(cudaMemsetAsync(never, 0, sizeof(double), M->stream));
+      const int64_t nv = M->nfc * D2, nvp = bicg_stride(nv, 4);
+      em_apply_kernel<double, D2><<<em_grid<double, D2>(M), EmPass<double, D2>::NTHR, EmPass<double, D2>::SMEM,
+                                    M->stream>>>(M->d_C, x, M->d_fslot, M->nelt, nvp, M->d_Y, never, M->d_status);
+      em_sum_kernel<double><<<nblocks(M), kNT, 0, M->stream>>>(nv, nvp, M->d_Y, y);
+      M->launches += 2;
+    } else {
+      apply_kernel<D2><<<nblocks(M), kNT, 0, M->stream>>>(face_args(M), M->d_C, x, y);
+      M->launches++;
+    }
     HDG_CUDA_TRY(cudaGetLastError());
     return HDG_OK;
   }

@@ -262,7 +262,8 @@ constexpr int kBlockBytes = 3 * NTMAX * KC * 2; // stride of the (tile, chunk) b
 constexpr int kSmem = 3 * kPartA + kBlockBytes;
 
 struct Args {
-  const double *kappa, *c, *f, *geo, *w;
+  const double *kappa, *c, *f, *geo;
+  const float* wf;  // [nq][2] reference weights as double-float pairs: the hi part (nearest float) is read
   const unsigned char* B;  // [ntile][nchunk] blocks: [3 parts][rows_t][KC] BF16, K-major core layout
   float* out;              // [nelt][ostride]
   int32_t* status;
@@ -272,9 +273,8 @@ struct Args {
 
 __host__ __device__ inline int tile_rows(int np, int t) { return round16(np - t * NTMAX < NTMAX ? np - t * NTMAX : NTMAX); }
 
-// x = x0 + x1 + x2 (BF16 parts of the FP32 rounding of x)
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& x0, __nv_bfloat16& x1, __nv_bfloat16& x2) {
-  const float xf = (float)x;
+// xf = x0 + x1 + x2 exactly (BF16 parts of an FP32 value: 8 + 8 + 8 significant bits)
+__device__ __forceinline__ void split3(float xf, __nv_bfloat16& x0, __nv_bfloat16& x1, __nv_bfloat16& x2) {
   x0 = __float2bfloat16_rn(xf);
   const float r1 = xf - __bfloat162float(x0);
   x1 = __float2bfloat16_rn(r1);
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) mass3_tc_kernel(Args A) {
   for (int64_t et = blockIdx.x; et < ntiles_e && !failed; et += gridDim.x) {
     const int64_t e = et * 128 + tid;  // this thread's element (row of A, lane of the accumulator)
     const bool act = e < A.nelt;
-    const double vol = act ? A.geo[e * kGeoStride + 25] : 0.0;
+    const float volf = act ? (float)A.geo[e * kGeoStride + 25] : 0.f;
     bool bad = false;
     for (int j = 0; j < njobs && !failed; ++j) {
       const int coef = j < A.ntile ? 0 : j < 2 * A.ntile ? 1 : 2;
@@ -334,15 +334,16 @@ __global__ void __launch_bounds__(kThreads, 1) mass3_tc_kernel(Args A) {
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
               const int q = ch * KC + kg * 8 + u + v;
-              double a = 0.0;
-              if (act && q < A.nq) {
+              float a = 0.f;
+              if (act && q < A.nq) {  // FP32 arithmetic: a carries at most 6 roundings of 2^-24
                 const double gv = g[e * A.nq + q];
+                const float vw = volf * __ldg(A.wf + 2 * q);
                 if (coef == 0) {
                   if (!(gv > 0.0) || !isfinite(gv)) bad = true;
-                  a = vol * A.w[q] / (gv > 0.0 ? gv : 1.0);
+                  a = vw * __frcp_rn(gv > 0.0 ? (float)gv : 1.f);
                 } else {
                   if (!isfinite(gv) || (coef == 1 && !(gv >= 0.0))) bad = true;
-                  a = vol * A.w[q] * gv;
+                  a = vw * (float)gv;
                 }
               }
               split3(a, h[v], m_[v], l[v]);
@@ -491,7 +492,7 @@ int mass3_contraction(hdg_mesh* M, float* out) {
   a.c = M->c;
   a.f = M->f;
   a.geo = M->d_geo;
-  a.w = M->dt.vol_w;
+  a.wf = M->dt.vol_w_df;
   a.B = reinterpret_cast<const unsigned char*>(M->d_mass3B);
   a.out = out;
   a.status = M->d_status;
