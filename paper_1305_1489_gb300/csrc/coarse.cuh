@@ -123,8 +123,18 @@ __global__ void restrict_gather_kernel(CoarseArgs CA, const T* __restrict__ r, c
       const int64_t f = fi >> 2;
       const int i = fi & 3;
       float t = 0.f;
+      if constexpr (sizeof(T) == 4 && D2 % 2 == 0) {  // the face's entries start on 8 bytes: pairs
+        const float2* rf = reinterpret_cast<const float2*>(r + f * D2);
 #pragma unroll
-      for (int a = 0; a < D2; ++a) t = fmaf(CA.Tf[a * 3 + i], (float)r[f * D2 + a], t);
+        for (int a = 0; a < D2; a += 2) {
+          const float2 v = rf[a / 2];
+          t = fmaf(CA.Tf[a * 3 + i], v.x, t);
+          t = fmaf(CA.Tf[(a + 1) * 3 + i], v.y, t);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < D2; ++a) t = fmaf(CA.Tf[a * 3 + i], (float)r[f * D2 + a], t);
+      }
       s = fmaf(CA.gw[k], t, s);
     }
 #pragma unroll

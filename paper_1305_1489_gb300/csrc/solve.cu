@@ -1568,11 +1568,12 @@ struct Solver {
   }
 
   // ||b - H x||_2 over the free dofs in FP64, r written to `r`.
-  static int true_residual(hdg_mesh* M, const double* x, double* r, double* rnorm) {
+  // (have_x false: x is zero, so r = b without the product)
+  static int true_residual(hdg_mesh* M, const double* x, double* r, double* rnorm, bool have_x = true) {
     FaceArgs F = face_args(M);
     const int nb = nblocks(M);
     double* scal = M->d_scal + S_NSCAL;
-    pcg_init_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, const_cast<double*>(x), true, r,
+    pcg_init_kernel<double, D2><<<nb, kNT, 0, M->stream>>>(F, M->d_C, M->d_b, const_cast<double*>(x), have_x, r,
                                                            M->d_red, M->d_counter, scal);
     M->launches++;
     HDG_CUDA_TRY(cudaGetLastError());
@@ -1667,7 +1668,7 @@ struct Solver {
       double prev = INFINITY;
       bool fallback = false;
       for (int outer = 0; outer < 30; ++outer) {
-        rc = true_residual(M, M->d_x, M->d_r, &rnorm);
+        rc = true_residual(M, M->d_x, M->d_r, &rnorm, outer > 0 || x0 != nullptr);
         if (rc) return rc;
         if (rnorm <= tol || bnorm == 0.0) {
           converged = true;
