@@ -147,6 +147,26 @@ int hdg_set_boundary_data(hdg_mesh* mesh, const double* uD, const double* gN);
  * HDG_ERR_LOCAL_SINGULAR / HDG_ERR_COEFF (with the count of failing elements in the message). */
 int hdg_assemble_condense(hdg_mesh* mesh, int precision);
 
+/* The same assembly from host arrays, with the host -> device copies overlapped with the
+ * condensation (Sections 3-5): the library copies the inputs into device buffers of its own
+ * (allocated on first use, kept with the mesh), makes them the mesh's coefficients,
+ * convection field and boundary data (as hdg_set_coefficients, hdg_set_face_convection and
+ * hdg_set_boundary_data would), and with precision HDG_DF32 condenses the elements in
+ * `chunks` consecutive ranges, each range launched as soon as its inputs have landed while
+ * the next range is copied (a second stream and events).  Other precisions copy everything
+ * first and run hdg_assemble_condense.  Host arrays in the layouts of the device calls;
+ * page-locked (pinned) memory lets the copies run beside the kernels, pageable memory is
+ * copied through staging by the driver.  Synchronises; errors as hdg_assemble_condense, and
+ * HDG_ERR_ARG for missing kappa, c, f or only one of beta, beta_f.                        */
+typedef struct hdg_host_inputs {
+  const double *kappa, *c, *f;  /* [nelt][nq] (required)                                    */
+  const double *beta, *beta_f;  /* [3][nelt][nq] and [3][nelt][4][nf], both or neither      */
+  const double *tau;            /* [nelt][4] or NULL (tau = 1)                               */
+  const double *uD, *gN;        /* [nfc][nf] and [3][nfc][nf], each or NULL (as for
+                                   hdg_set_boundary_data; both NULL keeps the current data) */
+} hdg_host_inputs;
+int hdg_assemble_condense_host(hdg_mesh* mesh, int precision, const hdg_host_inputs* in, int chunks);
+
 /* Volume quadrature rule (eq. 3.1; the paper leaves the rule open and remarks that suitable
  * rules are easy to find):
  *   HDG_RULE_CONICAL (default): conical-product Gauss-Jacobi, (k+2)^3 nodes;
@@ -340,6 +360,11 @@ int hdg_trace_residual(hdg_mesh* mesh, const double* x, double* r, double* rnorm
  * record copy that never lands, which only a hardware fault could cause, leaves NaN and is
  * reported by the next assembly as HDG_ERR_CUDA).                                         */
 int hdg_recover(hdg_mesh* mesh, const double* uhat, double* q, double* u);
+
+/* The same recovery into host arrays q [nelt][3][n], u [nelt][n] (page-locked for overlap):
+ * the elements in `chunks` ranges, each range's device -> host copy running while the next
+ * range is recovered.  uhat device f64 [nfc][d2].  Synchronises.                          */
+int hdg_recover_host(hdg_mesh* mesh, const double* uhat, double* q, double* u, int chunks);
 
 /* Superconvergent postprocess (eq. 9.11): ustar [nelt][n1] device f64 (coefficients in the
  * degree-(k+1) Dubiner basis) from q, u of hdg_recover; kappa as set by

@@ -385,6 +385,51 @@ class HDGMesh:
         _lib.check(_lib.load().hdg_mass_contraction(self._h, g.data_ptr(), int(mode), out.data_ptr()))
         return out
 
+    def assemble_condense_host(self, host, precision=HDG_DF32, chunks=8):
+        """hdg_assemble_condense_host: the assembly from host arrays (numpy arrays or CPU
+        tensors, pinned for overlap) given in `host` by name (kappa, c, f required; beta,
+        beta_f, tau, uD, gN optional), copied chunk by chunk beside the condensation.  The host
+        arrays must stay alive until the call returns."""
+        class HostInputs(C.Structure):
+            _fields_ = [(nm, C.c_void_p) for nm in ("kappa", "c", "f", "beta", "beta_f", "tau", "uD", "gN")]
+
+        def hp(name, shape):
+            a = host.get(name)
+            if a is None:
+                return None
+            if hasattr(a, "is_cuda"):
+                if a.is_cuda or a.dtype != __import__("torch").float64 or not a.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous float64 CPU tensor")
+                if tuple(a.shape) != shape:
+                    raise ValueError(f"{name} must have shape {shape}")
+                return a.data_ptr()
+            a = np.asarray(a)
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.shape != shape:
+                raise ValueError(f"{name} must be a C-contiguous float64 array of shape {shape}")
+            return a.ctypes.data
+        nf = self.nf
+        hi = HostInputs(hp("kappa", (self.nelt, self.nq)), hp("c", (self.nelt, self.nq)), hp("f", (self.nelt, self.nq)),
+                        hp("beta", (3, self.nelt, self.nq)), hp("beta_f", (3, self.nelt, 4, nf)),
+                        hp("tau", (self.nelt, 4)), hp("uD", (self.nfc, nf)), hp("gN", (3, self.nfc, nf)))
+        self._host_keep = host  # the mesh now reads library copies; nothing else to keep alive
+        _lib.check(_lib.load().hdg_assemble_condense_host(self._h, int(precision), C.byref(hi), int(chunks)))
+
+    def recover_host(self, uhat, q_host, u_host, chunks=8):
+        """hdg_recover_host: q [nelt, 3, n] and u [nelt, n] written into host arrays (CPU
+        float64 tensors or numpy arrays, pinned for overlap), chunk by chunk."""
+        uhat = _dev_f64(uhat, (self.nfc, self.d2), "uhat")
+
+        def hp(a, shape, name):
+            if hasattr(a, "is_cuda"):
+                if a.is_cuda or tuple(a.shape) != shape or not a.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous CPU tensor of shape {shape}")
+                return a.data_ptr()
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.shape != shape:
+                raise ValueError(f"{name} must be a C-contiguous float64 array of shape {shape}")
+            return a.ctypes.data
+        _lib.check(_lib.load().hdg_recover_host(self._h, uhat.data_ptr(), hp(q_host, (self.nelt, 3, self.n), "q"),
+                                                hp(u_host, (self.nelt, self.n), "u"), int(chunks)))
+
     def mixed_masses(self):
         """hdg_mixed_masses: the FP32 masses of the HDG_MIXED_BF16 assembly for the current
         coefficients, [nelt, stride] = [M_{kappa^-1} pairs | M_c pairs | f^K | padding]."""

@@ -71,6 +71,8 @@ _SIGS = {
     "hdg_nn_fold_affine": [C.c_int, C.c_int, P, P, P, P, P],
     "hdg_set_coarse_space": [P, C.c_int, P, P, P],
     "hdg_autotune": [P, P],
+    "hdg_assemble_condense_host": [P, C.c_int, P, C.c_int],
+    "hdg_recover_host": [P, P, P, P, C.c_int],
     "hdg_mixed_masses": [P, P, P],
     "hdg_coarse_precond_apply": [P, P, P],
     "hdg_solve_trace_noalloc": [P, C.c_double, C.c_int, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)],

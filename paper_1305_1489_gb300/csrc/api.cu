@@ -3,6 +3,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
+#include <algorithm>
 
 #include "hdg_internal.h"
 
@@ -96,7 +98,8 @@ static void release(hdg_mesh* M) {
                   M->d_rec, M->d_status, M->d_b, M->d_x, M->d_r, M->d_z, M->d_p, M->d_q, M->d_uhatD, M->d_BJ,
                   M->d_red, M->d_scal, M->d_counter, M->d_C32, M->d_BJ32, M->d_r32, M->d_x32, M->d_z32,
                   M->d_p32, M->d_q32, M->d_bicg, M->d_fverts, M->d_Tproj, M->d_norm, M->d_bicg32, M->d_Y,
-                  M->d_mass3B, M->d_mass3, M->d_fslot, M->d_Y32};
+                  M->d_mass3B, M->d_mass3, M->d_fslot, M->d_Y32, M->in_kappa, M->in_c, M->in_f, M->in_beta,
+                  M->in_betaf, M->in_tau, M->in_uD, M->in_gN, M->out_q, M->out_u};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (M->graph64) cudaGraphExecDestroy(M->graph64);
@@ -108,6 +111,7 @@ static void release(hdg_mesh* M) {
   if (M->wgraph64) cudaGraphExecDestroy(M->wgraph64);
   if (M->wgraph32) cudaGraphExecDestroy(M->wgraph32);
   if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
+  if (M->copy_stream) cudaStreamDestroy(M->copy_stream);
 }
 
 static int check_status(hdg_mesh* M) {
@@ -277,8 +281,12 @@ int hdg_set_boundary_data(hdg_mesh* M, const double* uD, const double* gN) {
   return HDG_OK;
 }
 
-int hdg_assemble_condense(hdg_mesh* M, int precision) {
-  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+}  // extern "C"
+
+namespace hdg {
+
+// the checks of an assembly request (shared by the device- and host-input entry points)
+static int check_assembly(hdg_mesh* M, int precision) {
   if (!M->kappa) return fail(HDG_ERR_STATE, "hdg_set_coefficients was not called");
   if (precision != HDG_FP64 && precision != HDG_DF32 && precision != HDG_MIXED_BF16)
     return fail(HDG_ERR_UNSUPPORTED, "assembly precision must be HDG_FP64, HDG_DF32 or HDG_MIXED_BF16");
@@ -292,11 +300,38 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
     return fail(HDG_ERR_UNSUPPORTED, "the split-BF16 assembly is built for k >= 1 on the conical volume rule");
   if (M->k == 0 && (M->beta_q || M->method == HDG_METHOD_BDM))
     return fail(HDG_ERR_UNSUPPORTED, "k = 0 is built for the HDG method without convection");
+  return HDG_OK;
+}
+
+// after every assembly: what depended on the previous one is stale; the status is read
+static int finish_assembly(hdg_mesh* M, int precision) {
+  M->assembled = true;
+  M->asm_prec = precision;
+  M->c32_ready = false;
+  M->bj64_ready = M->bj32_ready = false;
+  if (M->coarse) coarse_invalidate(M);
+  M->rhs_ready = false;
+  return check_status(M);
+}
+
+static int ensure_buffer(double** p, int64_t n) {
+  if (!*p) HDG_CUDA_TRY(cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1)));
+  return HDG_OK;
+}
+
+}  // namespace hdg
+
+extern "C" {
+
+int hdg_assemble_condense(hdg_mesh* M, int precision) {
+  if (!M) return fail(HDG_ERR_ARG, "NULL mesh");
+  int rc = check_assembly(M, precision);
+  if (rc) return rc;
   HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   if (precision == HDG_MIXED_BF16) {
     const int stride = mass3_stride(M->k);
     if (!M->d_mass3) HDG_CUDA_TRY(cudaMalloc(&M->d_mass3, sizeof(float) * M->nelt * stride));
-    int rc = mass3_contraction(M, M->d_mass3);
+    rc = mass3_contraction(M, M->d_mass3);
     if (rc) return rc;
     int32_t st6 = 0;
     HDG_CUDA_TRY(cudaMemcpyAsync(&st6, M->d_status + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, M->stream));
@@ -306,12 +341,112 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
   } else {
     HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
   }
-  M->assembled = true;
-  M->asm_prec = precision;
-  M->c32_ready = false;
-  M->bj64_ready = M->bj32_ready = false;
-  if (M->coarse) coarse_invalidate(M);
-  M->rhs_ready = false;
+  return finish_assembly(M, precision);
+}
+
+int hdg_assemble_condense_host(hdg_mesh* M, int precision, const hdg_host_inputs* in, int chunks) {
+  if (!M || !in || !in->kappa || !in->c || !in->f) return fail(HDG_ERR_ARG, "kappa, c and f are required");
+  if ((in->beta == nullptr) != (in->beta_f == nullptr))
+    return fail(HDG_ERR_ARG, "beta and beta_f are given together or not at all");
+  const int64_t nelt = M->nelt, nq = M->tab.nq, nf = M->tab.nf, nfc = M->nfc;
+  int rc;
+  if ((rc = ensure_buffer(&M->in_kappa, nelt * nq)) || (rc = ensure_buffer(&M->in_c, nelt * nq)) ||
+      (rc = ensure_buffer(&M->in_f, nelt * nq)))
+    return rc;
+  if (in->beta && ((rc = ensure_buffer(&M->in_beta, 3 * nelt * nq)) || (rc = ensure_buffer(&M->in_betaf, 12 * nelt * nf))))
+    return rc;
+  if (in->tau && (rc = ensure_buffer(&M->in_tau, 4 * nelt))) return rc;
+  if (in->uD && (rc = ensure_buffer(&M->in_uD, nfc * nf))) return rc;
+  if (in->gN && (rc = ensure_buffer(&M->in_gN, 3 * nfc * nf))) return rc;
+  // from here on the mesh reads its inputs from the library's copies
+  if ((rc = hdg_set_coefficients(M, M->in_kappa, M->in_c, in->beta ? M->in_beta : nullptr, M->in_f,
+                                 in->tau ? M->in_tau : nullptr)))
+    return rc;
+  if (in->beta && (rc = hdg_set_face_convection(M, M->in_betaf))) return rc;
+  if ((in->uD || in->gN) &&
+      (rc = hdg_set_boundary_data(M, in->uD ? M->in_uD : nullptr, in->gN ? M->in_gN : nullptr)))
+    return rc;
+  if ((rc = check_assembly(M, precision))) return rc;
+  if (!M->copy_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->copy_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = M->copy_stream;
+  const size_t d = sizeof(double);
+  // the copy stream starts after the work already queued on the mesh stream (which may read
+  // the buffers being refilled)
+  cudaEvent_t ev0;
+  HDG_CUDA_TRY(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+  HDG_CUDA_TRY(cudaEventRecord(ev0, M->stream));
+  HDG_CUDA_TRY(cudaStreamWaitEvent(cs, ev0, 0));
+  cudaEventDestroy(ev0);
+  if (in->tau) HDG_CUDA_TRY(cudaMemcpyAsync(M->in_tau, in->tau, d * 4 * nelt, cudaMemcpyHostToDevice, cs));
+  // pipelined: the double-float condensation of each chunk of elements starts as soon as the
+  // chunk's inputs have landed, while the next chunk is copied
+  const bool pipe = precision == HDG_DF32 && M->k >= 1;
+  const int nch = pipe ? std::max(1, std::min<int>(chunks, (int)std::min<int64_t>(nelt, 1024))) : 1;
+  if (pipe) HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
+  std::vector<cudaEvent_t> evs(nch, nullptr);
+  for (int ch = 0; ch < nch; ++ch) {
+    const int64_t e0 = nelt * ch / nch, e1 = nelt * (ch + 1) / nch, ne = e1 - e0;
+    if (ne <= 0) continue;
+    HDG_CUDA_TRY(cudaMemcpyAsync(M->in_kappa + e0 * nq, in->kappa + e0 * nq, d * ne * nq, cudaMemcpyHostToDevice, cs));
+    HDG_CUDA_TRY(cudaMemcpyAsync(M->in_c + e0 * nq, in->c + e0 * nq, d * ne * nq, cudaMemcpyHostToDevice, cs));
+    HDG_CUDA_TRY(cudaMemcpyAsync(M->in_f + e0 * nq, in->f + e0 * nq, d * ne * nq, cudaMemcpyHostToDevice, cs));
+    if (in->beta)
+      for (int st = 0; st < 3; ++st) {
+        HDG_CUDA_TRY(cudaMemcpyAsync(M->in_beta + (st * nelt + e0) * nq, in->beta + (st * nelt + e0) * nq,
+                                     d * ne * nq, cudaMemcpyHostToDevice, cs));
+        HDG_CUDA_TRY(cudaMemcpyAsync(M->in_betaf + (st * nelt + e0) * 4 * nf, in->beta_f + (st * nelt + e0) * 4 * nf,
+                                     d * ne * 4 * nf, cudaMemcpyHostToDevice, cs));
+      }
+    if (pipe) {
+      HDG_CUDA_TRY(cudaEventCreateWithFlags(&evs[ch], cudaEventDisableTiming));
+      HDG_CUDA_TRY(cudaEventRecord(evs[ch], cs));
+      HDG_CUDA_TRY(cudaStreamWaitEvent(M->stream, evs[ch], 0));
+      HDG_CUDA_TRY(launch_assemble_df_range(M, e0, ne));
+    }
+  }
+  // the boundary data (read by the trace solve) behind the element data
+  if (in->uD) HDG_CUDA_TRY(cudaMemcpyAsync(M->in_uD, in->uD, d * nfc * nf, cudaMemcpyHostToDevice, cs));
+  if (in->gN) HDG_CUDA_TRY(cudaMemcpyAsync(M->in_gN, in->gN, d * 3 * nfc * nf, cudaMemcpyHostToDevice, cs));
+  cudaEvent_t evl;
+  HDG_CUDA_TRY(cudaEventCreateWithFlags(&evl, cudaEventDisableTiming));
+  HDG_CUDA_TRY(cudaEventRecord(evl, cs));
+  HDG_CUDA_TRY(cudaStreamWaitEvent(M->stream, evl, 0));
+  cudaEventDestroy(evl);
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (!pipe) return hdg_assemble_condense(M, precision);
+  return finish_assembly(M, precision);
+}
+
+int hdg_recover_host(hdg_mesh* M, const double* uhat, double* q, double* u, int chunks) {
+  if (!M || !uhat || !q || !u) return fail(HDG_ERR_ARG, "NULL argument");
+  if (!M->assembled) return fail(HDG_ERR_STATE, "recover before hdg_assemble_condense");
+  const int64_t nelt = M->nelt, n = M->tab.n;
+  int rc;
+  if ((rc = ensure_buffer(&M->out_q, 3 * nelt * n)) || (rc = ensure_buffer(&M->out_u, nelt * n))) return rc;
+  if (!M->copy_stream) HDG_CUDA_TRY(cudaStreamCreateWithFlags(&M->copy_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = M->copy_stream;
+  const int nch = std::max(1, std::min<int>(chunks, (int)std::min<int64_t>(nelt, 1024)));
+  std::vector<cudaEvent_t> evs(nch, nullptr);
+  int err = HDG_OK;
+  for (int ch = 0; ch < nch && !err; ++ch) {
+    const int64_t e0 = nelt * ch / nch, e1 = nelt * (ch + 1) / nch, ne = e1 - e0;
+    if (ne <= 0) continue;
+    cudaError_t e = launch_recover_range(M, uhat, M->out_q, M->out_u, e0, ne);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[ch], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(evs[ch], M->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evs[ch], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(q + e0 * 3 * n, M->out_q + e0 * 3 * n, sizeof(double) * ne * 3 * n, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(u + e0 * n, M->out_u + e0 * n, sizeof(double) * ne * n, cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) err = fail(HDG_ERR_CUDA, std::string("pipelined recovery: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(cs);
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  if (err) return err;
+  if (e != cudaSuccess) return fail(HDG_ERR_CUDA, std::string("pipelined recovery: ") + cudaGetErrorString(e));
   return check_status(M);
 }
 

@@ -95,7 +95,25 @@ AsmDfArgs df_args(hdg_mesh* M) {
   a.nelt = M->nelt;
   a.mass3 = nullptr;
   a.m3stride = 0;
+  a.e0 = 0;
+  a.count = M->nelt;
   return a;
+}
+
+// the condensation of elements e0 .. e0 + count - 1 only (pipelined host-input assembly)
+cudaError_t launch_assemble_df_range(hdg_mesh* M, int64_t e0, int64_t count) {
+  if (M->k == 0 || count <= 0) return cudaErrorInvalidValue;
+  M->rec_df = true;
+  AsmDfArgs a = df_args(M);
+  a.e0 = e0;
+  a.count = count;
+  switch (M->k) {
+    case 1: return launch_df_k<1>(M, a);
+    case 2: return launch_df_k<2>(M, a);
+    case 3: return launch_df_k<3>(M, a);
+    case 4: return launch_df_k<4>(M, a);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_assemble_df(hdg_mesh* M) {

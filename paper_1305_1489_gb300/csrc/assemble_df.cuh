@@ -46,6 +46,7 @@ struct AsmDfArgs {
   // tensor-core contraction (tc_mass.cu), stride m3stride floats; NULL otherwise
   const float* mass3;
   int m3stride;
+  int64_t e0, count;  // this launch's elements: e0 .. e0 + count - 1 (one CTA each)
 };
 
 // Shared-memory plan.  C is formed in one pass near the end (C = (n_l . n_l') o V^T V
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(NT, MINB) assemble_df_kernel(AsmDfArgs A) {
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int64_t Ke = blockIdx.x;
+  const int64_t Ke = A.e0 + blockIdx.x;
 
   // this thread's coefficient loads of the next phase, issued before the first barrier so that
   // they overlap the geometry loads (tasks t = tid, tid + NT: kappa, c, f at node t; with
@@ -661,7 +662,7 @@ static cudaError_t launch_df_shape(hdg_mesh* M, const AsmDfArgs& a) {
   e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV, MASSIN>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            100);
   if (e != cudaSuccess) return e;
-  assemble_df_kernel<K, NT, MINB, CONV, MASSIN><<<(unsigned)M->nelt, NT, smem, M->stream>>>(a);
+  assemble_df_kernel<K, NT, MINB, CONV, MASSIN><<<(unsigned)a.count, NT, smem, M->stream>>>(a);
   M->launches += 1;
   return cudaGetLastError();
 }

@@ -153,6 +153,11 @@ struct hdg_mesh {
   void* d_mass3B = nullptr;
   int mass3_rule = -1;
   float* d_mass3 = nullptr;
+  // library-owned device copies of host inputs (hdg_assemble_condense_host) and outputs
+  // (hdg_recover_host), and the stream that moves them beside the kernels
+  double *in_kappa = nullptr, *in_c = nullptr, *in_f = nullptr, *in_beta = nullptr, *in_betaf = nullptr,
+         *in_tau = nullptr, *in_uD = nullptr, *in_gN = nullptr, *out_q = nullptr, *out_u = nullptr;
+  cudaStream_t copy_stream = nullptr;
   int k1_variant = 0;             // launch shape of the double-float K1 (hdg_autotune)
   int asm_prec = -1;              // precision of the last hdg_assemble_condense
   hdg::Coarse* coarse = nullptr;  // two-level preconditioner (hdg_set_coarse_space), or NULL
@@ -176,6 +181,8 @@ cudaError_t launch_qnodes(hdg_mesh* M, double* X, double* Y, double* Z, double* 
 cudaError_t launch_assemble(hdg_mesh* M);
 cudaError_t launch_assemble_df(hdg_mesh* M);
 cudaError_t launch_assemble_df_mass(hdg_mesh* M, const float* mass3, int stride);
+cudaError_t launch_assemble_df_range(hdg_mesh* M, int64_t e0, int64_t count);
+cudaError_t launch_recover_range(hdg_mesh* M, const double* uhat, double* q, double* u, int64_t e0, int64_t count);
 int mass3_contraction(hdg_mesh* M, float* out);  // tc_mass.cu
 int mass3_stride(int k);
 cudaError_t launch_projection(hdg_mesh* M, const double* q_vol, const double* u_vol, const double* q_face,

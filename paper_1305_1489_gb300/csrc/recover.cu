@@ -574,30 +574,43 @@ __global__ void __launch_bounds__(32 * kRdWarps) recover_df_direct_kernel(const 
   }
 }
 
+// elements e0 .. e0 + count - 1 (q, u and the record offset to their first element; the
+// kernels see a mesh of count elements)
 template <int K>
-static cudaError_t launch_recover_df(hdg_mesh* M, const double* uhat, double* q, double* u) {
-  if constexpr (Dims<K>::n <= 10) {
-    constexpr int E = 32 / Dims<K>::n, PER = E * kRdWarps;
-    recover_df_direct_kernel<K><<<(unsigned)((M->nelt + PER - 1) / PER), 32 * kRdWarps, 0, M->stream>>>(
-        M->d_rec, M->d_facebyele, uhat, M->nelt, q, u);
+static cudaError_t launch_recover_df(hdg_mesh* M, const double* uhat, double* q, double* u, int64_t e0, int64_t count) {
+  using D = Dims<K>;
+  const double* rec = M->d_rec + e0 * (int64_t)D::rec;
+  const int32_t* fbe = M->d_facebyele + 4 * e0;
+  q += e0 * 3 * D::n;
+  u += e0 * D::n;
+  if constexpr (D::n <= 10) {
+    constexpr int E = 32 / D::n, PER = E * kRdWarps;
+    recover_df_direct_kernel<K><<<(unsigned)((count + PER - 1) / PER), 32 * kRdWarps, 0, M->stream>>>(rec, fbe, uhat,
+                                                                                                     count, q, u);
     return cudaSuccess;
   } else {
-    const int smem = (int)(sizeof(df) * Dims<K>::rec);
+    const int smem = (int)(sizeof(df) * D::rec);
     cudaError_t e = cudaFuncSetAttribute(recover_df_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    recover_df_kernel<K><<<(unsigned)M->nelt, 32, smem, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u,
-                                                                       M->d_status);
+    recover_df_kernel<K><<<(unsigned)count, 32, smem, M->stream>>>(rec, fbe, uhat, count, q, u, M->d_status);
     return cudaSuccess;
   }
 }
 
-cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
-  const unsigned g = (unsigned)((M->nelt + kRecWarps - 1) / kRecWarps);
-  const int nt = 32 * kRecWarps;
+template <int K>
+static void launch_recover_fp64(hdg_mesh* M, const double* uhat, double* q, double* u, int64_t e0, int64_t count) {
+  using D = Dims<K>;
+  const unsigned g = (unsigned)((count + kRecWarps - 1) / kRecWarps);
+  recover_kernel<K><<<g, 32 * kRecWarps, 0, M->stream>>>(M->d_rec + e0 * (int64_t)D::rec, M->d_facebyele + 4 * e0,
+                                                          uhat, count, q + e0 * 3 * D::n, u + e0 * D::n);
+}
+
+cudaError_t launch_recover_range(hdg_mesh* M, const double* uhat, double* q, double* u, int64_t e0, int64_t count) {
+  if (count <= 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
-#define HDG_REC(KK)                                 \
-  if (M->rec_df) e = launch_recover_df<KK>(M, uhat, q, u); \
-  else recover_kernel<KK><<<g, nt, 0, M->stream>>>(M->d_rec, M->d_facebyele, uhat, M->nelt, q, u)
+#define HDG_REC(KK)                                                  \
+  if (M->rec_df) e = launch_recover_df<KK>(M, uhat, q, u, e0, count); \
+  else launch_recover_fp64<KK>(M, uhat, q, u, e0, count)
   switch (M->k) {
     case 0: HDG_REC(0); break;
     case 1: HDG_REC(1); break;
@@ -610,6 +623,10 @@ cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u
   if (e != cudaSuccess) return e;
   M->launches++;
   return cudaGetLastError();
+}
+
+cudaError_t launch_recover(hdg_mesh* M, const double* uhat, double* q, double* u) {
+  return launch_recover_range(M, uhat, q, u, 0, M->nelt);
 }
 
 // ----------------------------------------------------------------------- postprocess
