@@ -579,34 +579,7 @@ def run_workload(W, args, stream, dev, world=1, full=True):
         M.assemble_condense(asm_prec)
 
     # end to end through the public API with host buffers (pinned) and copies in the region
-    pin = {k: torch.from_numpy(v).pin_memory() for k, v in W.host.items()}
-    hq = torch.empty((nelt, 3, M.n), dtype=torch.float64).pin_memory()
-    hu = torch.empty((nelt, M.n), dtype=torch.float64).pin_memory()
-    h2d = sum(v.numel() * 8 for v in pin.values())
-    d2h = (hq.numel() + hu.numel()) * 8
-    # through hdg_assemble_condense_host / hdg_recover_host: the library copies the host inputs
-    # chunk by chunk beside the condensation, and the recovered fields beside the recovery
-    e2e_ms = 0.0
-    for i in range(args.warmup + args.steps):
-        flush.fill_(1.0)
-        a, b, cc, dd = ev(), ev(), ev(), ev()
-        a.record(stream)
-        M.assemble_condense_host(pin, asm_prec, chunks=E2E_CHUNKS)
-        b.record(stream)
-        uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
-        cc.record(stream)
-        M.recover_host(uh, hq, hu, chunks=E2E_CHUNKS)
-        dd.record(stream)
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            e2e_ms += a.elapsed_time(b) + cc.elapsed_time(dd)
-    out["e2e"] = {"value": world * nelt * args.steps / (e2e_ms / 1e3), "unit": UNIT,
-                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                  "phases": "hdg_assemble_condense_host (H2D of " + ",".join(W.host) + " from pinned host memory "
-                            f"in {E2E_CHUNKS} chunks beside the condensation) + hdg_recover_host (recovery with "
-                            "the D2H of q, u beside it); the trace solve runs between them and is excluded, as in "
-                            "value"}
-    del pin, hq, hu
+    out["e2e"] = e2e_leg(W, args, stream, world, asm_prec, step_prec, flush)
 
     # roofline of the dominant kernel of the metric (K1).  Its work is the FP64 flop count of
     # the algorithm.  The double-float K1 executes it on the FP32 pipe as compensated
@@ -673,6 +646,44 @@ def h2_contraction(W, dev, stream, reps=5):
     res["note"] = (f"[{M.nelt} x {nq}] . [{nq} x {npair}] per launch; bytes = the FP64 coefficient in, the FP32 "
                    "masses out; HBM-bound at this contraction length")
     return res
+
+
+def e2e_leg(W, args, stream, world, asm_prec, step_prec, flush):
+    """The metric through hdg_assemble_condense_host / hdg_recover_host from pinned host
+    buffers: the library copies the inputs chunk by chunk beside the condensation, and the
+    recovered fields beside the recovery; the trace solve runs between them, untimed."""
+    import torch
+
+    M, nelt = W.M, W.M.nelt
+    pin = {k: torch.from_numpy(v).pin_memory() for k, v in W.host.items()}
+    hq = torch.empty((nelt, 3, M.n), dtype=torch.float64).pin_memory()
+    hu = torch.empty((nelt, M.n), dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in pin.values())
+    d2h = (hq.numel() + hu.numel()) * 8
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    e2e_ms, t_asm, t_rec = 0.0, [], []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        a, b, cc, dd = ev(), ev(), ev(), ev()
+        a.record(stream)
+        M.assemble_condense_host(pin, asm_prec, chunks=args.e2e_chunks)
+        b.record(stream)
+        uh, it, rr = M.solve_trace(rtol=1e-10, maxit=20000, precision=step_prec)
+        cc.record(stream)
+        M.recover_host(uh, hq, hu, chunks=args.e2e_chunks)
+        dd.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            t_asm.append(a.elapsed_time(b))
+            t_rec.append(cc.elapsed_time(dd))
+            e2e_ms += t_asm[-1] + t_rec[-1]
+    return {"value": world * nelt * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "assemble_host_ms": float(np.mean(t_asm)), "recover_host_ms": float(np.mean(t_rec)),
+            "phases": "hdg_assemble_condense_host (H2D of " + ",".join(W.host) + " from pinned host memory "
+                      f"in {args.e2e_chunks} chunks beside the condensation) + hdg_recover_host (recovery with "
+                      "the D2H of q, u beside it); the trace solve runs between them and is excluded, as in "
+                      "value"}
 
 
 def mixed_bf16_assembly(W, dev, stream, uh_ref, u_ref, step_prec, df32_ms, reps=5):
@@ -1098,6 +1109,8 @@ def main():
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--profile-k1", type=int, default=0, help="run K1 twice on an s^3 x 6 mesh and exit")
     ap.add_argument("--profile-workload", default=HEADLINE)
+    ap.add_argument("--e2e-only", action="store_true", help="the end-to-end leg alone (timing of the host pipeline)")
+    ap.add_argument("--e2e-chunks", type=int, default=E2E_CHUNKS, help="element ranges of the host pipeline")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="two-level mixed trace solves and two recoveries on an s^3 x 6 mesh of --profile-workload, "
                          "then exit")
@@ -1145,6 +1158,23 @@ def main():
             W.M.mixed_masses()
         torch.cuda.synchronize()
         print(json.dumps({"profile_tc": {"nelt": W.M.nelt, **res}}))
+        return
+    if args.e2e_only:
+        import torch
+
+        from paper_1305_1489_gb300 import HDG_DF32, HDG_MIXED_FP32, build
+        build()
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(device=dev)
+        torch.cuda.set_stream(stream)
+        W = Workload(args.workload, dev, stream)
+        W.M.set_inner_tolerance(INNER_RTOL.get(W.name, 1e-4))
+        W.M.set_coarse_space(*W.hierarchy())
+        W.M.assemble_condense(HDG_DF32)
+        tuned = W.M.autotune() if args.autotune else None
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"e2e_only": e2e_leg(W, args, stream, 1, HDG_DF32, HDG_MIXED_FP32, flush),
+                          "autotune": tuned}))
         return
     if args.only_steps:
         import torch

@@ -656,12 +656,16 @@ template <int K, int V, bool CONV, bool MASSIN = false>
 static cudaError_t launch_df_shape(hdg_mesh* M, const AsmDfArgs& a) {
   constexpr int NT = K1Shape<K, V>::NT, MINB = K1Shape<K, V>::MINB;
   const size_t smem = AsmDfSmem<K, CONV>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV, MASSIN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV, MASSIN>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           100);
-  if (e != cudaSuccess) return e;
+  static bool attrs_set = false;  // once per instantiation (the element-range launches repeat)
+  if (!attrs_set) {
+    cudaError_t e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV, MASSIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(assemble_df_kernel<K, NT, MINB, CONV, MASSIN>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    attrs_set = true;
+  }
   assemble_df_kernel<K, NT, MINB, CONV, MASSIN><<<(unsigned)a.count, NT, smem, M->stream>>>(a);
   M->launches += 1;
   return cudaGetLastError();
