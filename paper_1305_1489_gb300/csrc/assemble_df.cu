@@ -13,7 +13,7 @@ static cudaError_t launch_df_kc(hdg_mesh* M, const AsmDfArgs& a) {
   int v = M->k1_variant;
   if (const char* ev = std::getenv("HDG_K1_VARIANT")) v = std::atoi(ev);
   if (v == 1) return launch_df_shape<K, 1, CONV>(M, a);
-  if (K >= 3 && v == 2) return launch_df_shape<K, (K >= 3 ? 2 : 0), CONV>(M, a);
+  if (K >= 2 && v == 2) return launch_df_shape<K, (K >= 2 ? 2 : 0), CONV>(M, a);
   return launch_df_shape<K, 0, CONV>(M, a);
 }
 
@@ -22,12 +22,12 @@ static cudaError_t launch_df_k(hdg_mesh* M, const AsmDfArgs& a) {
   return a.beta_q ? launch_df_kc<K, true>(M, a) : launch_df_kc<K, false>(M, a);
 }
 
-int k1_variants(int k) { return k == 0 ? 1 : k >= 3 ? 3 : 2; }
+int k1_variants(int k) { return k == 0 ? 1 : k >= 2 ? 3 : 2; }
 int k1_threads(int k, int variant) {
   switch (k) {
     case 0: return K1Occupancy<0>::NT;  // k = 0 runs the FP64 kernel
     case 1: return variant ? K1Shape<1, 1>::NT : K1Shape<1, 0>::NT;
-    case 2: return variant ? K1Shape<2, 1>::NT : K1Shape<2, 0>::NT;
+    case 2: return variant == 2 ? K1Shape<2, 2>::NT : variant ? K1Shape<2, 1>::NT : K1Shape<2, 0>::NT;
     case 3: return variant == 2 ? K1Shape<3, 2>::NT : variant ? K1Shape<3, 1>::NT : K1Shape<3, 0>::NT;
     default: return variant == 2 ? K1Shape<4, 2>::NT : variant ? K1Shape<4, 1>::NT : K1Shape<4, 0>::NT;
   }

@@ -93,6 +93,7 @@ struct K1Shape {
 };
 template <> struct K1Shape<1, 1> { static constexpr int NT = 64, MINB = 16; };
 template <> struct K1Shape<2, 1> { static constexpr int NT = 128, MINB = 6; };
+template <> struct K1Shape<2, 2> { static constexpr int NT = 128, MINB = 9; };  // 56 registers
 template <> struct K1Shape<3, 1> { static constexpr int NT = 192, MINB = 4; };
 template <> struct K1Shape<3, 2> { static constexpr int NT = 128, MINB = 5; };
 template <> struct K1Shape<4, 1> { static constexpr int NT = 128, MINB = 2; };

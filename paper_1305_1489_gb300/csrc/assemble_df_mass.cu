@@ -14,7 +14,7 @@ static cudaError_t launch_mass_kc(hdg_mesh* M, const AsmDfArgs& a) {
   int v = M->k1_variant;
   if (const char* ev = std::getenv("HDG_K1_VARIANT")) v = std::atoi(ev);
   if (v == 1) return launch_df_shape<K, 1, CONV, true>(M, a);
-  if (K >= 3 && v == 2) return launch_df_shape<K, (K >= 3 ? 2 : 0), CONV, true>(M, a);
+  if (K >= 2 && v == 2) return launch_df_shape<K, (K >= 2 ? 2 : 0), CONV, true>(M, a);
   return launch_df_shape<K, 0, CONV, true>(M, a);
 }
 

@@ -50,7 +50,7 @@ def _case(k, s):
     return prob, c, e, d, n
 
 
-@pytest.mark.parametrize("k,s,shape", [(1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (3, 1, "0"),
+@pytest.mark.parametrize("k,s,shape", [(1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (2, 2, "2"), (3, 1, "0"),
                                        (3, 1, "1"), (3, 1, "2"), (4, 1, "0"), (4, 1, "1"), (4, 1, "2")])
 def test_double_float_convection_condensation(k, s, shape, monkeypatch):
     from paper_1305_1489_gb300 import HDG_DF32

@@ -147,7 +147,8 @@ def test_error_paths():
     assert ei.value.code == 2
 
 
-@pytest.mark.parametrize("k,s,shape", [(0, 3, "0"), (1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (3, 2, "0"), (3, 2, "1"),
+@pytest.mark.parametrize("k,s,shape", [(0, 3, "0"), (1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (2, 2, "2"),
+                                     (3, 2, "0"), (3, 2, "1"),
                                      (3, 2, "2"), (4, 1, "0"), (4, 2, "1"), (4, 1, "2")])
 def test_double_float_assembly(k, s, shape, monkeypatch):
     """HDG_DF32: the same condensation in double-float arithmetic on the FP32 pipe, for every
