@@ -64,18 +64,19 @@ E2E_CHUNKS = 8  # element ranges of the pipelined host-input assembly and host-o
 
 K1_TRAFFIC = {
     ("cube48_k2_conv", "assemble_df.cu"): {
-        "sha256": "e5dc7d42c71f777b0a1992e1c310ab466626b7a5d70b19614a2a0c29702ff7e9",
-        "bytes_per_element": (120072704 + 237390592) / 24576,
+        "sha256": "579987cdf75e34c3d582102c2c596cedd0e7c8fa3f286079bcb9aa3a5639976a",
+        "bytes_per_element": (120072448 + 237189632) / 24576,
         "captured": "ncu dram__bytes_read/write of the same kernel on the 16^3 x 6 mesh of the workload (24,576 "
                     "elements), profiles/assemble_df_kernel_conv_k2_cube16.md"},
     ("cube16_k3", "assemble_df.cu"): {
-        "sha256": "e5dc7d42c71f777b0a1992e1c310ab466626b7a5d70b19614a2a0c29702ff7e9",
-        "bytes_per_element": (79970304 + 901217280) / 24576,
+        "sha256": "579987cdf75e34c3d582102c2c596cedd0e7c8fa3f286079bcb9aa3a5639976a",
+        "bytes_per_element": (80775936 + 901166592) / 24576,
         "captured": "ncu dram__bytes_read/write of the same kernel on the workload's own mesh (24,576 elements), "
                     "profiles/assemble_df_kernel_cube16_k3.md"},
 }
 # the sources of each K1 translation unit (the kernel and the device headers it includes)
 K1_SOURCES = {"assemble_df.cu": ("assemble_df.cu", "assemble_df.cuh", "device_df.cuh", "device_common.cuh"),
+              "assemble_df_lean.cu": ("assemble_df_lean.cu", "assemble_df.cuh", "device_df.cuh", "device_common.cuh"),
               "assemble.cu": ("assemble.cu", "device_common.cuh")}
 
 
@@ -588,7 +589,8 @@ def run_workload(W, args, stream, dev, world=1, full=True):
     k1_ms = phases["assemble_condense"]
     fpe = flops_per_element_k1(prob.k, W.conv)
     achieved = fpe * nelt / (k1_ms / 1e3) / 1e12
-    k1_src = "assemble_df.cu" if args.asm == "df32" else "assemble.cu"
+    streamed = bool(tuned and tuned.get("k1_streamed"))  # the kernel that streams W_* (k = 4)
+    k1_src = ("assemble_df_lean.cu" if streamed else "assemble_df.cu") if args.asm == "df32" else "assemble.cu"
     sha = _sha(*(os.path.join(ROOT, "paper_1305_1489_gb300", "csrc", f) for f in K1_SOURCES[k1_src]))
     trec = K1_TRAFFIC.get((W.name, k1_src), {})
     bpe = trec.get("bytes_per_element") if trec.get("sha256") == sha else None
@@ -599,7 +601,9 @@ def run_workload(W, args, stream, dev, world=1, full=True):
         "traffic": bpe * nelt if bpe else None,
         "traffic_note": (f"ncu dram bytes per element x {nelt} elements ({trec.get('captured')})" if bpe else
                          "no ncu capture of the current K1 sources"),
-        "kernel": (f"assemble_df_kernel<{prob.k}, .., CONV={str(W.conv).lower()}> (K1, double-float on the FP32 pipe)"
+        "kernel": ((f"assemble_df_lean_kernel<{prob.k}, ..> (K1 with W_* streamed, double-float on the FP32 pipe)"
+                    if streamed else
+                    f"assemble_df_kernel<{prob.k}, .., CONV={str(W.conv).lower()}> (K1, double-float on the FP32 pipe)")
                    if df else f"assemble_kernel<{prob.k}> (K1, FP64)"),
         "work": "FP64-equivalent flops of the structured elimination (sum-factorised masses)",
         "flops_per_element": fpe, "algorithmic_bytes_per_launch": k1_bytes_per_element(prob.k, W.conv) * nelt,

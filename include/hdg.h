@@ -329,7 +329,9 @@ int hdg_coarse_precond_apply(hdg_mesh* mesh, const double* r, double* z);
  * precision (the environment variable HDG_MATVEC=face|element, read at mesh creation, fixes
  * the form);
  * (2) pick the launch shape of the double-float assembly (threads per element and resident
- * elements per SM; k = 1..3 have two shapes) by timing it.  The choices are kept by the
+ * elements per SM: two shapes at k = 1, three at k = 2..4, and for reaction-diffusion at
+ * k = 4 two more of a kernel that holds W_* = L^-1 C_*^T one direction at a time, so that
+ * three elements stay resident per SM) by timing it.  The choices are kept by the
  * mesh; the system of the caller's last hdg_assemble_condense is restored.  out (nullable,
  * host) receives the choices and the best times.  Requires hdg_assemble_condense
  * (HDG_ERR_STATE) and the boundary data.  Not in the paper.                                */
@@ -342,6 +344,7 @@ typedef struct hdg_tuning {
   double k1_ms;       /* one double-float assembly at the choice        */
   int matvec_em64;    /* FP64 solve loops: 1 = element pass + face sum,  */
   int matvec_em32;    /*   0 = one face-major pass; the same for FP32    */
+  int k1_streamed;    /* 1: the chosen K1 shape streams W_* (k = 4)      */
 } hdg_tuning;
 int hdg_autotune(hdg_mesh* mesh, hdg_tuning* out);
 

@@ -299,7 +299,7 @@ class HDGMesh:
         class Tuning(C.Structure):
             _fields_ = [("face_blocks", C.c_int), ("face_blocks32", C.c_int), ("k1_threads", C.c_int),
                         ("iter_ms", C.c_double), ("iter32_ms", C.c_double), ("k1_ms", C.c_double),
-                        ("matvec_em64", C.c_int), ("matvec_em32", C.c_int)]
+                        ("matvec_em64", C.c_int), ("matvec_em32", C.c_int), ("k1_streamed", C.c_int)]
         t = Tuning()
         _lib.check(_lib.load().hdg_autotune(self._h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Tuning._fields_}

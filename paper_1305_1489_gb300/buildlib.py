@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhdg.so")
-SOURCES = ["tables.cpp", "mesh.cpp", "assemble.cu", "assemble_df.cu", "assemble_df_mass.cu", "recover.cu", "solve.cu", "api.cu", "batch.cu", "learned.cu", "coarse.cu", "noalloc.cu", "projection.cu", "tc_mass.cu"]
+SOURCES = ["tables.cpp", "mesh.cpp", "assemble.cu", "assemble_df.cu", "assemble_df_mass.cu", "assemble_df_lean.cu", "recover.cu", "solve.cu", "api.cu", "batch.cu", "learned.cu", "coarse.cu", "noalloc.cu", "projection.cu", "tc_mass.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

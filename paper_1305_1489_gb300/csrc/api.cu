@@ -339,7 +339,7 @@ int hdg_assemble_condense(hdg_mesh* M, int precision) {
     if (st6) return fail(HDG_ERR_CUDA, "tensor-core contraction: an MMA did not complete within the wait limit");
     HDG_CUDA_TRY(launch_assemble_df_mass(M, M->d_mass3, stride));
   } else {
-    HDG_CUDA_TRY(precision == HDG_DF32 ? launch_assemble_df(M) : launch_assemble(M));
+    HDG_CUDA_TRY(precision == HDG_DF32 ? launch_k1(M) : launch_assemble(M));
   }
   return finish_assembly(M, precision);
 }
@@ -401,7 +401,7 @@ int hdg_assemble_condense_host(hdg_mesh* M, int precision, const hdg_host_inputs
       HDG_CUDA_TRY(cudaEventCreateWithFlags(&evs[ch], cudaEventDisableTiming));
       HDG_CUDA_TRY(cudaEventRecord(evs[ch], cs));
       HDG_CUDA_TRY(cudaStreamWaitEvent(M->stream, evs[ch], 0));
-      HDG_CUDA_TRY(launch_assemble_df_range(M, e0, ne));
+      HDG_CUDA_TRY(launch_k1_range(M, e0, ne));
     }
   }
   // the boundary data (read by the trace solve) behind the element data
@@ -521,12 +521,12 @@ int hdg_autotune(hdg_mesh* M, hdg_tuning* out) {
     cudaEvent_t a, b;
     HDG_CUDA_TRY(cudaEventCreate(&a));
     HDG_CUDA_TRY(cudaEventCreate(&b));
-    for (int v = 0; v < k1_variants(M->k); ++v) {
+    for (int v = 0; v < k1_shape_count(M); ++v) {
       M->k1_variant = v;
-      HDG_CUDA_TRY(launch_assemble_df(M));  // warm-up (sets the launch attributes)
+      HDG_CUDA_TRY(launch_k1(M));  // warm-up (sets the launch attributes)
       HDG_CUDA_TRY(cudaEventRecord(a, M->stream));
-      HDG_CUDA_TRY(launch_assemble_df(M));
-      HDG_CUDA_TRY(launch_assemble_df(M));
+      HDG_CUDA_TRY(launch_k1(M));
+      HDG_CUDA_TRY(launch_k1(M));
       HDG_CUDA_TRY(cudaEventRecord(b, M->stream));
       HDG_CUDA_TRY(cudaEventSynchronize(b));
       float ms = 0.f;
@@ -543,7 +543,8 @@ int hdg_autotune(hdg_mesh* M, hdg_tuning* out) {
     rc = hdg_assemble_condense(M, M->asm_prec >= 0 ? M->asm_prec : HDG_FP64);
     if (rc) return rc;
   }
-  t.k1_threads = k1_threads(M->k, M->k1_variant);
+  t.k1_threads = k1_shape_threads(M, M->k1_variant);
+  t.k1_streamed = M->k1_variant >= k1_variants(M->k) ? 1 : 0;
   t.k1_ms = best_t < 1e29f ? best_t / 2.0 : 0.0;
   if (out) *out = t;
   return HDG_OK;

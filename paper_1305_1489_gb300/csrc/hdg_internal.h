@@ -212,4 +212,10 @@ int coarse_precond_apply(hdg_mesh* M, const double* r, double* z);
 int autotune_face_grid(hdg_mesh* M, hdg_tuning* out);
 int k1_variants(int k);              // launch shapes of the double-float K1 for degree k
 int k1_threads(int k, int variant);  // threads per element of a shape
+// the double-float K1 over every shape of the mesh (assemble_df_lean.cu): the shapes of
+// assemble_df.cu first, then those of the kernel that streams W_* (reaction-diffusion, k = 4)
+int k1_shape_count(const hdg_mesh* M);
+int k1_shape_threads(const hdg_mesh* M, int variant);
+cudaError_t launch_k1(hdg_mesh* M);
+cudaError_t launch_k1_range(hdg_mesh* M, int64_t e0, int64_t count);
 }  // namespace hdg

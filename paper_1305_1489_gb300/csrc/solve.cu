@@ -2028,7 +2028,7 @@ static int record_group(hdg_mesh* M, cudaGraph_t graph, int asm_precision, int s
   HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   M->stream = cs;
   cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, cs);
-  cudaError_t e = (asm_precision == HDG_DF32) ? launch_assemble_df(M) : launch_assemble(M);
+  cudaError_t e = (asm_precision == HDG_DF32) ? launch_k1(M) : launch_assemble(M);
   bdata_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf, M->uD, M->gN,
                                        xD, phiN);
   rhs_kernel<D2><<<nb, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter,
@@ -2137,7 +2137,7 @@ static int record_group_mixed(hdg_mesh* M, cudaGraph_t graph, int asm_precision,
   HDG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   M->stream = cs;
   cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, cs);
-  cudaError_t e = (asm_precision == HDG_DF32) ? launch_assemble_df(M) : launch_assemble(M);
+  cudaError_t e = (asm_precision == HDG_DF32) ? launch_k1(M) : launch_assemble(M);
   bdata_kernel<D2><<<nb64, kNT, 0, cs>>>(F, M->d_fvx, M->d_vx, M->nelt, M->dt.D, M->dt.face_w, M->tab.nf, M->uD,
                                          M->gN, xD, phiN);
   rhs_kernel<D2><<<nb64, kNT, 0, cs>>>(F, M->d_C, M->d_Cf, xD, phiN, M->d_b, M->d_red, M->d_counter, si);

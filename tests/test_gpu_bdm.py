@@ -77,3 +77,30 @@ def test_bdm_method_argument_and_switch_back():
     ref = ohdg.solve_problem(prob, c, e, d, n)
     assert rel(Ch, ref["CK"]) < 1e-12
     assert rel(Cb, Ch) > 1e-3
+
+
+@pytest.mark.parametrize("k,shape", [(4, "3"), (4, "4")])
+def test_bdm_streamed_k1_shapes(k, shape, monkeypatch):
+    """The double-float kernel that streams W_* one direction at a time (reaction-diffusion,
+    k = 4): the BDM identity rows of S_u and the zero rows of G^T are set after its last
+    direction, and its condensed blocks match the oracle's like the other shapes'."""
+    from paper_1305_1489_gb300 import HDG_DF32, HDG_METHOD_BDM
+    monkeypatch.setenv("HDG_K1_VARIANT", shape)
+    prob = _prob(k)
+    c, e, d, n = make_mesh(prob, s=2, jitter=0.15, seed=6)
+    M = gpu_setup(prob, c, e, d, n)
+    M.set_method(HDG_METHOD_BDM)
+    M.assemble_condense(precision=HDG_DF32)
+    Cg, Cfg = (t.cpu().numpy() for t in M.condensed())
+    mesh = ExpandedMesh(c, e, d, n)
+    tab = ohdg.Tables(k)
+    X, Y, Z = ohdg.volume_nodes(mesh, tab)
+    blk = ohdg.local_blocks(mesh, tab, prob.kappa(X, Y, Z), prob.c(X, Y, Z), prob.f(X, Y, Z), tau=0.0)
+    CK, Cf, _, _ = obdm.local_solvers(blk, tab.d2)
+    assert rel(Cg, CK) < 1e-11
+    assert rel(Cfg, Cf) < 1e-11
+    ref = obdm.solve_problem(prob, c, e, d, n)
+    uhat, it, rr = M.solve_trace(rtol=1e-14, maxit=20000)
+    q, u = M.recover(uhat)
+    assert rel(u.cpu().numpy(), ref["u"]) < 1e-11
+    assert rel(q.cpu().numpy(), ref["q"]) < 1e-11

@@ -149,10 +149,12 @@ def test_error_paths():
 
 @pytest.mark.parametrize("k,s,shape", [(0, 3, "0"), (1, 3, "0"), (1, 3, "1"), (2, 2, "0"), (2, 2, "1"), (2, 2, "2"),
                                      (3, 2, "0"), (3, 2, "1"),
-                                     (3, 2, "2"), (4, 1, "0"), (4, 2, "1"), (4, 1, "2")])
+                                     (3, 2, "2"), (4, 1, "0"), (4, 2, "1"), (4, 1, "2"),
+                                     (4, 2, "3"), (4, 1, "4")])
 def test_double_float_assembly(k, s, shape, monkeypatch):
     """HDG_DF32: the same condensation in double-float arithmetic on the FP32 pipe, for every
-    launch shape the autotuner may pick (HDG_K1_VARIANT forces one)."""
+    launch shape the autotuner may pick (HDG_K1_VARIANT forces one; shapes 3 and 4 at k = 4
+    are the kernel that streams W_* one direction at a time)."""
     from paper_1305_1489_gb300 import HDG_DF32
     monkeypatch.setenv("HDG_K1_VARIANT", shape)
     prob = _varprob(k)
