@@ -60,7 +60,7 @@ HBM_FALLBACK_GBS = 6800.0
 # the ncu captures summarised under profiles/ (captured on a smaller mesh of the same workload
 # and scaled by the element count: K1 streams per-element data only, so traffic is proportional
 # to it), valid while the kernel's sources (K1_SOURCES, hashed together) are unchanged.
-E2E_CHUNKS = 8  # element ranges of the pipelined host-input assembly and host-output recovery
+E2E_CHUNKS = 16  # element ranges of the pipelined host-input assembly and host-output recovery
 
 K1_TRAFFIC = {
     ("cube48_k2_conv", "assemble_df.cu"): {
@@ -684,6 +684,7 @@ def e2e_leg(W, args, stream, world, asm_prec, step_prec, flush):
     return {"value": world * nelt * args.steps / (e2e_ms / 1e3), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "assemble_host_ms": float(np.mean(t_asm)), "recover_host_ms": float(np.mean(t_rec)),
+            "assemble_host_ms_median": float(np.median(t_asm)), "assemble_host_ms_max": float(np.max(t_asm)),
             "phases": "hdg_assemble_condense_host (H2D of " + ",".join(W.host) + " from pinned host memory "
                       f"in {args.e2e_chunks} chunks beside the condensation) + hdg_recover_host (recovery with "
                       "the D2H of q, u beside it); the trace solve runs between them and is excluded, as in "

@@ -385,7 +385,7 @@ class HDGMesh:
         _lib.check(_lib.load().hdg_mass_contraction(self._h, g.data_ptr(), int(mode), out.data_ptr()))
         return out
 
-    def assemble_condense_host(self, host, precision=HDG_DF32, chunks=8):
+    def assemble_condense_host(self, host, precision=HDG_DF32, chunks=16):
         """hdg_assemble_condense_host: the assembly from host arrays (numpy arrays or CPU
         tensors, pinned for overlap) given in `host` by name (kappa, c, f required; beta,
         beta_f, tau, uD, gN optional), copied chunk by chunk beside the condensation.  The host
@@ -414,7 +414,7 @@ class HDGMesh:
         self._host_keep = host  # the mesh now reads library copies; nothing else to keep alive
         _lib.check(_lib.load().hdg_assemble_condense_host(self._h, int(precision), C.byref(hi), int(chunks)))
 
-    def recover_host(self, uhat, q_host, u_host, chunks=8):
+    def recover_host(self, uhat, q_host, u_host, chunks=16):
         """hdg_recover_host: q [nelt, 3, n] and u [nelt, n] written into host arrays (CPU
         float64 tensors or numpy arrays, pinned for overlap), chunk by chunk."""
         uhat = _dev_f64(uhat, (self.nfc, self.d2), "uhat")
