@@ -152,7 +152,8 @@ int hdg_assemble_condense(hdg_mesh* mesh, int precision);
  * (allocated on first use, kept with the mesh), makes them the mesh's coefficients,
  * convection field and boundary data (as hdg_set_coefficients, hdg_set_face_convection and
  * hdg_set_boundary_data would), and with precision HDG_DF32 condenses the elements in
- * `chunks` consecutive ranges, each range launched as soon as its inputs have landed while
+ * `chunks` consecutive ranges (growing by a factor 1.25, so that the first copy, the only one
+ * nothing overlaps, is short), each range launched as soon as its inputs have landed while
  * the next range is copied (a second stream and events).  Other precisions copy everything
  * first and run hdg_assemble_condense.  Host arrays in the layouts of the device calls;
  * page-locked (pinned) memory lets the copies run beside the kernels, pageable memory is

@@ -1,6 +1,7 @@
 // C ABI of libhdg (declared in include/hdg.h): argument checking, ownership, dispatch.
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -314,6 +315,19 @@ static int finish_assembly(hdg_mesh* M, int precision) {
   return check_status(M);
 }
 
+// First element of range ch of nch over nelt elements, the ranges growing by the factor g
+// (g = 1: equal ranges).  In the host-input assembly the first range's copy is the only one
+// nothing overlaps; a range's copy takes about 0.6 of its condensation at the bench workload
+// (208 GB/s against 40 ns per element), so ranges that grow by 1.25 keep the copies ahead
+// while the first one shrinks to 0.7 % of the elements at 16 ranges.
+static int64_t range_start(int64_t nelt, int nch, int ch, double g) {
+  if (ch <= 0) return 0;
+  if (ch >= nch) return nelt;
+  const double frac = g == 1.0 ? (double)ch / nch : (std::pow(g, ch) - 1.0) / (std::pow(g, nch) - 1.0);
+  return std::min<int64_t>(nelt, std::max<int64_t>(0, (int64_t)std::llround(frac * (double)nelt)));
+}
+constexpr double kAsmRangeGrowth = 1.25;
+
 static int ensure_buffer(double** p, int64_t n) {
   if (!*p) HDG_CUDA_TRY(cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1)));
   return HDG_OK;
@@ -385,7 +399,8 @@ int hdg_assemble_condense_host(hdg_mesh* M, int precision, const hdg_host_inputs
   if (pipe) HDG_CUDA_TRY(cudaMemsetAsync(M->d_status, 0, sizeof(int32_t) * 4, M->stream));
   std::vector<cudaEvent_t> evs(nch, nullptr);
   for (int ch = 0; ch < nch; ++ch) {
-    const int64_t e0 = nelt * ch / nch, e1 = nelt * (ch + 1) / nch, ne = e1 - e0;
+    const int64_t e0 = range_start(nelt, nch, ch, kAsmRangeGrowth);
+    const int64_t ne = range_start(nelt, nch, ch + 1, kAsmRangeGrowth) - e0;
     if (ne <= 0) continue;
     HDG_CUDA_TRY(cudaMemcpyAsync(M->in_kappa + e0 * nq, in->kappa + e0 * nq, d * ne * nq, cudaMemcpyHostToDevice, cs));
     HDG_CUDA_TRY(cudaMemcpyAsync(M->in_c + e0 * nq, in->c + e0 * nq, d * ne * nq, cudaMemcpyHostToDevice, cs));
@@ -430,7 +445,7 @@ int hdg_recover_host(hdg_mesh* M, const double* uhat, double* q, double* u, int 
   std::vector<cudaEvent_t> evs(nch, nullptr);
   int err = HDG_OK;
   for (int ch = 0; ch < nch && !err; ++ch) {
-    const int64_t e0 = nelt * ch / nch, e1 = nelt * (ch + 1) / nch, ne = e1 - e0;
+    const int64_t e0 = range_start(nelt, nch, ch, 1.0), ne = range_start(nelt, nch, ch + 1, 1.0) - e0;
     if (ne <= 0) continue;
     cudaError_t e = launch_recover_range(M, uhat, M->out_q, M->out_u, e0, ne);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[ch], cudaEventDisableTiming);

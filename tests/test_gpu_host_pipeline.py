@@ -45,7 +45,7 @@ def _device_run(M, host, conv, precision):
 
 
 @pytest.mark.parametrize("conv,k,s", [(False, 2, 3), (False, 3, 2), (True, 1, 3), (True, 2, 3)])
-@pytest.mark.parametrize("chunks", [1, 3, 7])
+@pytest.mark.parametrize("chunks", [1, 3, 7, 16])
 def test_host_assembly_and_recovery_bitwise(conv, k, s, chunks):
     from paper_1305_1489_gb300 import HDG_DF32, HDG_MIXED_FP32, HDGMesh
     prob = get_problem("cube48_k2_conv" if conv else "cube16_k3").at(s=s, k=k)
