@@ -13,7 +13,8 @@
 // 24,576 elements: 14.5 ms against 12.8 ms for the best shape of assemble_df.cuh (the extra
 // products and the three rounds of triangular solves outweigh the third resident element), so
 // the autotuner keeps it as a candidate that does not win there.  Same algorithm as
-// assemble_df.cuh otherwise (Section 3's local solvers, eq. 3.59-3.61):
+// assemble_df.cuh otherwise (the elimination of eq. 5.1-5.2 with the blocks of eq. 3.55-3.56
+// and 4.5-4.10; C^K and C_f^K as eq. 5.5-5.6, the record of eq. 5.3):
 //   L L^T = M_{kappa^-1};  V = L^-1 E^T;  for * = 1..3: W_* = L^-1 C_*^T, S_u += W_*^T W_*,
 //   G += diag(n_*) V^T W_*  (G starts at diag(T) E);  L_s L_s^T = S_u;
 //   [H | h] = L_s^-1 [G^T | f];  C^K = (n_l . n_l') o V^T V - H^T H + tauDD;  C_f^K = H^T h;
