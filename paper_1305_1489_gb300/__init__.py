@@ -296,13 +296,9 @@ class HDGMesh:
         face-major pass) of the trace-solve kernels (FP64 and FP32) and the launch shape of the
         double-float assembly by timing (hdg_autotune); returns a dict of the choices and the
         best times."""
-        class Tuning(C.Structure):
-            _fields_ = [("face_blocks", C.c_int), ("face_blocks32", C.c_int), ("k1_threads", C.c_int),
-                        ("iter_ms", C.c_double), ("iter32_ms", C.c_double), ("k1_ms", C.c_double),
-                        ("matvec_em64", C.c_int), ("matvec_em32", C.c_int), ("k1_streamed", C.c_int)]
-        t = Tuning()
+        t = _lib.Tuning()
         _lib.check(_lib.load().hdg_autotune(self._h, C.byref(t)))
-        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+        return {f: getattr(t, f) for f, _ in _lib.Tuning._fields_}
 
     def apply(self, x):
         """y = H x on the free faces (hdg_trace_apply; Dirichlet rows 0)."""
@@ -390,9 +386,6 @@ class HDGMesh:
         tensors, pinned for overlap) given in `host` by name (kappa, c, f required; beta,
         beta_f, tau, uD, gN optional), copied chunk by chunk beside the condensation.  The host
         arrays must stay alive until the call returns."""
-        class HostInputs(C.Structure):
-            _fields_ = [(nm, C.c_void_p) for nm in ("kappa", "c", "f", "beta", "beta_f", "tau", "uD", "gN")]
-
         def hp(name, shape):
             a = host.get(name)
             if a is None:
@@ -408,7 +401,7 @@ class HDGMesh:
                 raise ValueError(f"{name} must be a C-contiguous float64 array of shape {shape}")
             return a.ctypes.data
         nf = self.nf
-        hi = HostInputs(hp("kappa", (self.nelt, self.nq)), hp("c", (self.nelt, self.nq)), hp("f", (self.nelt, self.nq)),
+        hi = _lib.HostInputs(hp("kappa", (self.nelt, self.nq)), hp("c", (self.nelt, self.nq)), hp("f", (self.nelt, self.nq)),
                         hp("beta", (3, self.nelt, self.nq)), hp("beta_f", (3, self.nelt, 4, nf)),
                         hp("tau", (self.nelt, 4)), hp("uD", (self.nfc, nf)), hp("gN", (3, self.nfc, nf)))
         self._host_keep = host  # the mesh now reads library copies; nothing else to keep alive

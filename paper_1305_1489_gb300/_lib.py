@@ -35,6 +35,18 @@ class MeshInfo(C.Structure):
                 ("has_convection", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    """hdg_tuning (hdg_autotune's choices and times)."""
+    _fields_ = [("face_blocks", C.c_int), ("face_blocks32", C.c_int), ("k1_threads", C.c_int),
+                ("iter_ms", C.c_double), ("iter32_ms", C.c_double), ("k1_ms", C.c_double),
+                ("matvec_em64", C.c_int), ("matvec_em32", C.c_int), ("k1_streamed", C.c_int)]
+
+
+class HostInputs(C.Structure):
+    """hdg_host_inputs (host arrays of hdg_assemble_condense_host)."""
+    _fields_ = [(nm, C.c_void_p) for nm in ("kappa", "c", "f", "beta", "beta_f", "tau", "uD", "gN")]
+
+
 P = C.c_void_p
 I64 = C.c_int64
 _SIGS = {

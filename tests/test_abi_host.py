@@ -147,3 +147,49 @@ def test_host_mesh_errors(lib):
     assert rc == 2  # HDG_ERR_ORIENTATION
     size = C.c_int64(0)
     assert lib.hdg_host_table(7, b"P", None, 0, C.byref(size)) == 9  # HDG_ERR_UNSUPPORTED
+
+
+# C structs of include/hdg.h and their ctypes mirrors in the binding
+_STRUCTS = {"hdg_mesh_info": "MeshInfo", "hdg_tuning": "Tuning", "hdg_host_inputs": "HostInputs"}
+
+
+def _struct_fields(src, name):
+    """Field names of `typedef struct [tag] { ... } name;` in declaration order."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct\s*\w*\s*\{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [re.sub(r"[\s*]", "", v) for v in re.sub(r"^(const\s+)?\w+", "", decl).split(",")]
+    return names
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's fields in its order, at the offsets
+    and with the sizes a C compiler gives them (gcc compiles a probe against include/hdg.h)."""
+    import shutil
+    import subprocess
+    from paper_1305_1489_gb300 import _lib
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = open(os.path.join(ROOT, "include", "hdg.h")).read()
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hdg.h"', "int main(void) {"]
+    expect = []
+    for cname, pyname in _STRUCTS.items():
+        fields = _struct_fields(src, cname)
+        py = getattr(_lib, pyname)
+        assert [f for f, _ in py._fields_] == fields, cname
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(C.sizeof(py))
+        for f in fields:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            expect.append(getattr(py, f).offset)
+    lines += ["  return 0;", "}"]
+    (tmp_path / "probe.c").write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(tmp_path / "probe.c"), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
